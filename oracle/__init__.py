@@ -1,0 +1,312 @@
+"""ctypes wrapper of the FP64 CPU oracle (``hdg_oracle.cpp``).
+
+TEST INFRASTRUCTURE ONLY: imported by ``tests/``, ``__graft_entry__.smoke()``
+and the CPU-baseline leg of ``bench.py``; the product package never imports
+it, and it never imports the product package.
+
+Every function returns NumPy float64/int arrays.  The oracle follows the
+paper's definitions (arXiv:1308.3995, Sec. 2 physics, Sec. 3.2 HDG weak form,
+Sec. 3.3 pseudo time, Sec. 3.4 hybridization); see ``hdg_oracle.cpp``.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+from dataclasses import dataclass
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "hdg_oracle.cpp")
+_LIB = os.path.join(_HERE, "liboracle.so")
+
+_c_double_p = ctypes.POINTER(ctypes.c_double)
+_c_i32_p = ctypes.POINTER(ctypes.c_int32)
+_c_i64_p = ctypes.POINTER(ctypes.c_int64)
+
+
+def build(force: bool = False) -> str:
+    """Compile the oracle with g++ (plain C++17, no FMA contraction)."""
+    if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < os.path.getmtime(_SRC):
+        tmp = _LIB + f".tmp{os.getpid()}"
+        subprocess.check_call(["g++", "-O2", "-std=c++17", "-ffp-contract=off", "-fPIC", "-shared",
+                               "-o", tmp, _SRC])
+        os.replace(tmp, _LIB)
+    return _LIB
+
+
+class OrcParams(ctypes.Structure):
+    _fields_ = [("model", ctypes.c_int32), ("reserved", ctypes.c_int32), ("gamma", ctypes.c_double),
+                ("prandtl", ctypes.c_double), ("reynolds", ctypes.c_double), ("mach", ctypes.c_double),
+                ("alpha", ctypes.c_double), ("cfl", ctypes.c_double), ("t_inf", ctypes.c_double)]
+
+
+_lib = None
+
+
+def lib():
+    global _lib
+    if _lib is None:
+        build()
+        L = ctypes.CDLL(_LIB)
+        L.orc_gauss_jacobi.argtypes = [ctypes.c_int, ctypes.c_double, ctypes.c_double, _c_double_p, _c_double_p]
+        L.orc_tri_rule.argtypes = [ctypes.c_int, _c_double_p, _c_double_p, _c_double_p]
+        L.orc_edge_rule.argtypes = [ctypes.c_int, _c_double_p, _c_double_p]
+        L.orc_dubiner.argtypes = [ctypes.c_int, ctypes.c_int, _c_double_p, _c_double_p, _c_double_p,
+                                  _c_double_p, _c_double_p]
+        L.orc_legendre01.argtypes = [ctypes.c_int, ctypes.c_int, _c_double_p, _c_double_p]
+        L.orc_euler_flux.argtypes = [_c_double_p, ctypes.c_double, _c_double_p]
+        L.orc_euler_flux.restype = None
+        L.orc_ns_viscous_flux.argtypes = [_c_double_p, _c_double_p, ctypes.POINTER(OrcParams), _c_double_p]
+        L.orc_ns_viscous_flux.restype = None
+        L.orc_mesh_create.argtypes = [ctypes.c_int, ctypes.c_int, _c_double_p, _c_i32_p,
+                                      ctypes.POINTER(ctypes.c_int8), ctypes.POINTER(ctypes.c_void_p)]
+        L.orc_mesh_destroy.argtypes = [ctypes.c_void_p]
+        L.orc_mesh_destroy.restype = None
+        L.orc_mesh_sizes.argtypes = [ctypes.c_void_p, _c_i64_p]
+        L.orc_mesh_sizes.restype = None
+        L.orc_mesh_arrays.argtypes = [ctypes.c_void_p] + [_c_i32_p] * 5 + [_c_i64_p] * 3 + [_c_i32_p, _c_i64_p]
+        L.orc_mesh_arrays.restype = None
+        P = ctypes.POINTER(OrcParams)
+        L.orc_element_residual.argtypes = [ctypes.c_void_p, P, ctypes.c_int, _c_double_p, _c_double_p,
+                                           _c_double_p, _c_double_p]
+        L.orc_element_blocks.argtypes = [ctypes.c_void_p, P, ctypes.c_int, _c_double_p, _c_double_p] + \
+            [_c_double_p] * 6
+        L.orc_element_condense.argtypes = [ctypes.c_void_p, P, ctypes.c_int, _c_double_p, _c_double_p,
+                                           _c_double_p, _c_double_p, _c_double_p]
+        L.orc_condense.argtypes = [ctypes.c_void_p, P, _c_double_p, _c_double_p] + [_c_double_p] * 5 + \
+            [_c_i32_p, ctypes.c_int, ctypes.c_int]
+        L.orc_recover.argtypes = [ctypes.c_void_p, _c_double_p, _c_double_p, _c_double_p]
+        L.orc_global_residual.argtypes = [ctypes.c_void_p, P, _c_double_p, _c_double_p, _c_double_p]
+        L.orc_monolithic.argtypes = [ctypes.c_void_p, P, _c_double_p, _c_double_p, _c_double_p, _c_double_p,
+                                     _c_double_p]
+        L.orc_dense_solve.argtypes = [ctypes.c_int, _c_double_p, _c_double_p]
+        _lib = L
+    return _lib
+
+
+def _d(a):
+    return a.ctypes.data_as(_c_double_p)
+
+
+def _i32(a):
+    return a.ctypes.data_as(_c_i32_p)
+
+
+def _i64(a):
+    return a.ctypes.data_as(_c_i64_p)
+
+
+def _f64(a):
+    return np.ascontiguousarray(a, dtype=np.float64)
+
+
+# --------------------------------------------------------------------------- tables
+def gauss_jacobi(n: int, alpha: float, beta: float):
+    x = np.zeros(n); w = np.zeros(n)
+    assert lib().orc_gauss_jacobi(n, alpha, beta, _d(x), _d(w)) == 0
+    return x, w
+
+
+def tri_rule(p: int):
+    m = (p + 2) ** 2
+    xi, eta, w = np.zeros(m), np.zeros(m), np.zeros(m)
+    assert lib().orc_tri_rule(p, _d(xi), _d(eta), _d(w)) == 0
+    return xi, eta, w
+
+
+def edge_rule(pe: int):
+    s, w = np.zeros(pe + 2), np.zeros(pe + 2)
+    assert lib().orc_edge_rule(pe, _d(s), _d(w)) == 0
+    return s, w
+
+
+def n_basis(p: int) -> int:
+    return (p + 1) * (p + 2) // 2
+
+
+def dubiner(p: int, xi, eta):
+    xi, eta = _f64(xi), _f64(eta)
+    m, nb = xi.size, n_basis(p)
+    phi, dx, de = np.zeros((m, nb)), np.zeros((m, nb)), np.zeros((m, nb))
+    assert lib().orc_dubiner(p, m, _d(xi), _d(eta), _d(phi), _d(dx), _d(de)) == 0
+    return phi, dx, de
+
+
+def legendre01(pe: int, s):
+    s = _f64(s)
+    psi = np.zeros((s.size, pe + 1))
+    lib().orc_legendre01(pe, s.size, _d(s), _d(psi))
+    return psi
+
+
+# --------------------------------------------------------------------------- physics
+def euler_flux(w, gamma=1.4):
+    w = _f64(w); f = np.zeros((2, 4))
+    lib().orc_euler_flux(_d(w), gamma, _d(f))
+    return f
+
+
+def ns_viscous_flux(w, q, params):
+    w = _f64(w); q = _f64(q).reshape(2, 4); f = np.zeros((2, 4))
+    P = params.c()
+    lib().orc_ns_viscous_flux(_d(w), _d(q), ctypes.byref(P), _d(f))
+    return f
+
+
+@dataclass
+class Params:
+    """Flow / discretisation parameters (model 0 = Euler, 1 = NS mixed form)."""
+    model: int = 0
+    gamma: float = 1.4
+    prandtl: float = 0.72
+    reynolds: float = 5000.0
+    mach: float = 0.5
+    alpha: float = 1.5
+    cfl: float = 0.0
+    t_inf: float = 288.15
+
+    def c(self) -> OrcParams:
+        return OrcParams(self.model, 0, self.gamma, self.prandtl, self.reynolds, self.mach, self.alpha,
+                         self.cfl, self.t_inf)
+
+    @property
+    def nfield(self) -> int:
+        return 12 if self.model == 1 else 4
+
+
+# --------------------------------------------------------------------------- mesh-level
+class Mesh:
+    """Oracle mesh: faces, sides and the documented layouts of U, Lambda, X, K."""
+
+    def __init__(self, elem_xy, elem_vid, elem_p, nfield: int):
+        xy = _f64(elem_xy).reshape(-1, 6)
+        vid = np.ascontiguousarray(elem_vid, dtype=np.int32).reshape(-1, 3)
+        p = np.ascontiguousarray(elem_p, dtype=np.int8).reshape(-1)
+        self.n_elem = int(p.size)
+        self.nfield = nfield
+        h = ctypes.c_void_p()
+        st = lib().orc_mesh_create(self.n_elem, nfield, _d(xy), _i32(vid),
+                                   p.ctypes.data_as(ctypes.POINTER(ctypes.c_int8)), ctypes.byref(h))
+        if st != 0:
+            raise ValueError(f"oracle rejected the mesh (status {st})")
+        self._h = h
+        sz = np.zeros(5, dtype=np.int64)
+        lib().orc_mesh_sizes(h, _i64(sz))
+        self.n_face, self.u_len, self.lam_len, self.x_len, self.k_len = (int(v) for v in sz)
+        nf, ne = self.n_face, self.n_elem
+        self.face_vid = np.zeros((nf, 2), np.int32)
+        self.face_el = np.zeros((nf, 2), np.int32)
+        self.face_lf = np.zeros((nf, 2), np.int32)
+        self.face_p = np.zeros(nf, np.int32)
+        self.elem_face = np.zeros((ne, 3), np.int32)
+        self.u_off = np.zeros(ne + 1, np.int64)
+        self.lam_off = np.zeros(nf + 1, np.int64)
+        self.x_off = np.zeros(ne + 1, np.int64)
+        self.k_col = np.zeros((nf, 5), np.int32)
+        self.k_blkoff = np.zeros(5 * nf + 1, np.int64)
+        lib().orc_mesh_arrays(h, _i32(self.face_vid), _i32(self.face_el), _i32(self.face_lf),
+                              _i32(self.face_p), _i32(self.elem_face), _i64(self.u_off), _i64(self.lam_off),
+                              _i64(self.x_off), _i32(self.k_col), _i64(self.k_blkoff))
+        self.elem_p = p.astype(np.int32)
+        self.elem_vid = vid
+        self.elem_xy = xy
+
+    def __del__(self):
+        h = getattr(self, "_h", None)
+        if h is not None and _lib is not None:
+            _lib.orc_mesh_destroy(h)
+            self._h = None
+
+    # sizes of element K
+    def n(self, K):
+        return self.nfield * n_basis(int(self.elem_p[K]))
+
+    def nt(self, K):
+        return int(sum(4 * (self.face_p[e] + 1) for e in self.elem_face[K]))
+
+    def element_residual(self, params, K, U, Lam):
+        n, nt = self.n(K), self.nt(K)
+        Nu, Nl = np.zeros(n), np.zeros(nt)
+        P = params.c()
+        lib().orc_element_residual(self._h, ctypes.byref(P), int(K), _d(_f64(U)), _d(_f64(Lam)), _d(Nu), _d(Nl))
+        return Nu, Nl
+
+    def element_blocks(self, params, K, U, Lam):
+        n, nt = self.n(K), self.nt(K)
+        A, B, C, D = np.zeros((n, n)), np.zeros((n, nt)), np.zeros((nt, n)), np.zeros((nt, nt))
+        F, H = np.zeros(n), np.zeros(nt)
+        P = params.c()
+        lib().orc_element_blocks(self._h, ctypes.byref(P), int(K), _d(_f64(U)), _d(_f64(Lam)),
+                                 _d(A), _d(B), _d(C), _d(D), _d(F), _d(H))
+        return A, B, C, D, F, H
+
+    def element_condense(self, params, K, U, Lam):
+        n, nt = self.n(K), self.nt(K)
+        X, S, E = np.zeros((n, nt + 1)), np.zeros((nt, nt)), np.zeros(nt)
+        P = params.c()
+        st = lib().orc_element_condense(self._h, ctypes.byref(P), int(K), _d(_f64(U)), _d(_f64(Lam)),
+                                        _d(X), _d(S), _d(E))
+        return X, S, E, st
+
+    def condense(self, params, U, Lam, k0=0, k1=0):
+        X = np.zeros(self.x_len); Kv = np.zeros(self.k_len); E = np.zeros(self.lam_len)
+        rU = np.zeros(self.u_len); rL = np.zeros(self.lam_len); st = np.zeros(self.n_elem, np.int32)
+        P = params.c()
+        lib().orc_condense(self._h, ctypes.byref(P), _d(_f64(U)), _d(_f64(Lam)), _d(X), _d(Kv), _d(E), _d(rU),
+                           _d(rL), _i32(st), int(k0), int(k1))
+        return dict(X=X, K=Kv, E=E, res_u=rU, res_lam=rL, status=st)
+
+    def recover(self, X, dLam):
+        dU = np.zeros(self.u_len)
+        lib().orc_recover(self._h, _d(_f64(X)), _d(_f64(dLam)), _d(dU))
+        return dU
+
+    def global_residual(self, params, U, Lam):
+        R = np.zeros(self.u_len + self.lam_len)
+        P = params.c()
+        lib().orc_global_residual(self._h, ctypes.byref(P), _d(_f64(U)), _d(_f64(Lam)), _d(R))
+        return R[:self.u_len], R[self.u_len:]
+
+    def monolithic(self, params, U, Lam, want_matrix=False):
+        N = self.u_len + self.lam_len
+        dU, dL = np.zeros(self.u_len), np.zeros(self.lam_len)
+        J = np.zeros((N, N)) if want_matrix else None
+        P = params.c()
+        st = lib().orc_monolithic(self._h, ctypes.byref(P), _d(_f64(U)), _d(_f64(Lam)), _d(dU), _d(dL),
+                                  _d(J) if want_matrix else None)
+        if st != 0:
+            raise RuntimeError(f"monolithic solve failed (status {st})")
+        return (dU, dL, J) if want_matrix else (dU, dL)
+
+    def global_jacobian(self, params, U, Lam):
+        """Dense Jacobian of the global residual (plus pseudo-time mass if cfl > 0); the
+        solve status is ignored, so a singular (pure-Newton periodic) matrix is returned too."""
+        N = self.u_len + self.lam_len
+        dU, dL, J = np.zeros(self.u_len), np.zeros(self.lam_len), np.zeros((N, N))
+        P = params.c()
+        st = lib().orc_monolithic(self._h, ctypes.byref(P), _d(_f64(U)), _d(_f64(Lam)), _d(dU), _d(dL), _d(J))
+        if st == 2:
+            raise ValueError("mesh too large for the dense Jacobian")
+        return J
+
+    def dense_K(self, Kv):
+        """Expand the block-sparse trace matrix into a dense lam_len x lam_len array."""
+        Kd = np.zeros((self.lam_len, self.lam_len))
+        for f in range(self.n_face):
+            nr = 4 * (self.face_p[f] + 1)
+            for b in range(5):
+                c = self.k_col[f, b]
+                nc = 4 * (self.face_p[c] + 1)
+                o = self.k_blkoff[5 * f + b]
+                Kd[self.lam_off[f]:self.lam_off[f] + nr, self.lam_off[c]:self.lam_off[c] + nc] = \
+                    Kv[o:o + nr * nc].reshape(nr, nc)
+        return Kd
+
+
+def dense_solve(A, b):
+    A = _f64(A); x = _f64(b).copy()
+    if lib().orc_dense_solve(A.shape[0], _d(A), _d(x)) != 0:
+        raise RuntimeError("singular")
+    return x

@@ -1,0 +1,937 @@
+// HDG oracle: plain, slow, obviously-correct FP64 CPU implementation of one
+// hybridized-DG Newton step for steady 2D Euler / mixed-form Navier-Stokes
+// (Woopen, Balan, May, Schuetz, arXiv:1308.3995).
+//
+// TEST INFRASTRUCTURE ONLY.  Nothing in the product path may link, import or
+// call this file; only the tests, the smoke check and the CPU-baseline leg of
+// the benchmark do.  It shares no code, header, table or constant generator
+// with the CUDA library.
+//
+// What it computes (section / equation of the paper):
+//   * physics: Euler convective flux and ideal-gas pressure (Sec. 2.1), viscous
+//     flux, temperature, Newtonian stress and Sutherland viscosity (Sec. 2.2);
+//   * the HDG residual N_h of Eq. (hdg_ls1)-(hdg_cont) with the combined
+//     Lax-Friedrichs/LDG-type numerical flux of Sec. 3.2 (source s = 0,
+//     no boundary operator: meshes are periodic, no shock capturing);
+//   * the Newton matrix N'_h (Eq. linearsystem) as the exact complex-step
+//     derivative of that residual, column by column, plus the optional
+//     backward-Euler pseudo-time mass term with the local time step of Sec. 3.3;
+//   * static condensation of Sec. 3.4: K = N - [L M][A B;C D]^{-1}[R;S],
+//     E = H - [L M][A B;C D]^{-1}[F;G], assembled element by element, the
+//     local solves stored for reconstruction, and the reconstruction of
+//     (dQ, dW) from dLambda by Eq. (ls);
+//   * for tiny meshes, the monolithic linearised system solved densely.
+//
+// Readings of points the paper leaves open are listed in the design doc and fixed
+// here: orthonormal Dubiner basis in the order (k=0..p, j=0..k, i=k-j);
+// collapsed Gauss volume rule with (p+2)x(p+2) points; (p_e+2)-point
+// Gauss-Legendre edge rule; orthonormal Legendre trace basis with the edge
+// parameter running from the lower to the higher global vertex id; the jump
+// in Eq. (hdg_cont) is the sum of both sides' outward fluxes; momentum flux
+// rho v (x) v + p Id; Sutherland's law non-dimensionalised with
+// rho_inf = c_inf = 1 and T = gamma p / rho.
+#include <algorithm>
+#include <cmath>
+#include <complex>
+#include <cstdint>
+#include <cstring>
+#include <mutex>
+#include <vector>
+
+typedef std::complex<double> cplx;
+
+extern "C" {
+typedef struct {
+  int32_t model;     // 0 = Euler (4 fields), 1 = Navier-Stokes mixed form (12 fields)
+  int32_t reserved;
+  double gamma;      // ratio of specific heats (Sec. 2.1)
+  double prandtl;    // Pr (Sec. 2.2)
+  double reynolds;   // Re based on free-stream speed, rho_inf = 1, L = 1
+  double mach;       // free-stream Mach number (c_inf = 1) -> mu_inf = mach / reynolds
+  double alpha;      // constant scalar stabilisation alpha = alpha_c + alpha_v (Sec. 3.2)
+  double cfl;        // <= 0: pure Newton (dt = inf); else backward-Euler pseudo time (Sec. 3.3)
+  double t_inf;      // dimensional free-stream temperature [K] for Sutherland's C2
+} orc_params;
+}
+
+// ---------------------------------------------------------------------------
+// Gauss quadrature by the Golub-Welsch method: the nodes are the eigenvalues
+// of the symmetric tridiagonal Jacobi matrix of the orthogonal polynomials,
+// the weights mu0 * (first eigenvector component)^2.
+// ---------------------------------------------------------------------------
+static void sym_eig_jacobi(int n, std::vector<double>& a, std::vector<double>& v) {
+  // cyclic Jacobi rotations on a symmetric n x n row-major matrix a;
+  // on exit the diagonal holds eigenvalues and the columns of v eigenvectors.
+  v.assign(n * n, 0.0);
+  for (int i = 0; i < n; ++i) v[i * n + i] = 1.0;
+  for (int sweep = 0; sweep < 100; ++sweep) {
+    double off = 0.0;
+    for (int i = 0; i < n; ++i)
+      for (int j = i + 1; j < n; ++j) off += a[i * n + j] * a[i * n + j];
+    if (off < 1e-34) break;
+    for (int p = 0; p < n; ++p)
+      for (int q = p + 1; q < n; ++q) {
+        double apq = a[p * n + q];
+        if (std::fabs(apq) < 1e-300) continue;
+        double theta = (a[q * n + q] - a[p * n + p]) / (2.0 * apq);
+        double t = (theta >= 0 ? 1.0 : -1.0) / (std::fabs(theta) + std::sqrt(theta * theta + 1.0));
+        double c = 1.0 / std::sqrt(t * t + 1.0), s = t * c;
+        for (int k = 0; k < n; ++k) {  // columns p, q
+          double akp = a[k * n + p], akq = a[k * n + q];
+          a[k * n + p] = c * akp - s * akq;
+          a[k * n + q] = s * akp + c * akq;
+        }
+        for (int k = 0; k < n; ++k) {  // rows p, q
+          double apk = a[p * n + k], aqk = a[q * n + k];
+          a[p * n + k] = c * apk - s * aqk;
+          a[q * n + k] = s * apk + c * aqk;
+        }
+        for (int k = 0; k < n; ++k) {
+          double vkp = v[k * n + p], vkq = v[k * n + q];
+          v[k * n + p] = c * vkp - s * vkq;
+          v[k * n + q] = s * vkp + c * vkq;
+        }
+      }
+  }
+}
+
+// n-point Gauss-Jacobi rule for weight (1-x)^al (1+x)^be on [-1,1], ascending nodes.
+static void gauss_jacobi(int n, double al, double be, double* x, double* w) {
+  std::vector<double> J(n * n, 0.0), V;
+  for (int k = 0; k < n; ++k) {
+    double s = 2.0 * k + al + be;
+    J[k * n + k] = (k == 0) ? (be - al) / (al + be + 2.0) : (be * be - al * al) / (s * (s + 2.0));
+    if (k >= 1) {
+      double kk = k;
+      double num = 4.0 * kk * (kk + al) * (kk + be) * (kk + al + be);
+      double den = s * s * (s + 1.0) * (s - 1.0);
+      J[k * n + k - 1] = J[(k - 1) * n + k] = std::sqrt(num / den);
+    }
+  }
+  sym_eig_jacobi(n, J, V);
+  double mu0 = std::pow(2.0, al + be + 1.0) * std::tgamma(al + 1.0) * std::tgamma(be + 1.0) /
+               std::tgamma(al + be + 2.0);
+  std::vector<std::pair<double, double>> xw(n);
+  for (int k = 0; k < n; ++k) xw[k] = {J[k * n + k], mu0 * V[0 * n + k] * V[0 * n + k]};
+  std::sort(xw.begin(), xw.end());
+  for (int k = 0; k < n; ++k) { x[k] = xw[k].first; w[k] = xw[k].second; }
+}
+
+// ---------------------------------------------------------------------------
+// Jacobi polynomials P_n^{(a,b)}(x) by the three-term recurrence, and their
+// derivative d/dx P_n^{(a,b)} = (n+a+b+1)/2 P_{n-1}^{(a+1,b+1)}.
+// ---------------------------------------------------------------------------
+static double jacobi_p(int n, double a, double b, double x) {
+  if (n == 0) return 1.0;
+  double p0 = 1.0, p1 = (a + 1.0) + (a + b + 2.0) * (x - 1.0) / 2.0;
+  for (int m = 2; m <= n; ++m) {
+    double c = 2.0 * m + a + b;
+    double a1 = 2.0 * m * (m + a + b) * (c - 2.0);
+    double a2 = (c - 1.0) * (c * (c - 2.0) * x + a * a - b * b);
+    double a3 = 2.0 * (m + a - 1.0) * (m + b - 1.0) * c;
+    double p2 = (a2 * p1 - a3 * p0) / a1;
+    p0 = p1; p1 = p2;
+  }
+  return p1;
+}
+static double jacobi_dp(int n, double a, double b, double x) {
+  if (n == 0) return 0.0;
+  return 0.5 * (n + a + b + 1.0) * jacobi_p(n - 1, a + 1.0, b + 1.0, x);
+}
+
+static inline int n_basis(int p) { return (p + 1) * (p + 2) / 2; }
+
+// Orthonormal Dubiner basis on the reference triangle (0,0),(1,0),(0,1):
+//   phi_ij = c_ij P_i(a) ((1-b)/2)^i P_j^{(2i+1,0)}(b),
+//   a = 2 xi/(1-eta) - 1, b = 2 eta - 1, c_ij = sqrt(2 (2i+1)(i+j+1)),
+// ordered k = 0..p, j = 0..k, i = k-j.  Gradients by the chain rule through
+// the collapsed coordinates (valid for eta < 1, i.e. away from vertex (0,1)).
+static void dubiner(int p, double xi, double eta, double* phi, double* dxi, double* deta) {
+  double om = 1.0 - eta;           // (1-b)/2
+  double a = 2.0 * xi / om - 1.0;  // collapsed coordinate
+  double b = 2.0 * eta - 1.0;
+  int m = 0;
+  for (int k = 0; k <= p; ++k)
+    for (int j = 0; j <= k; ++j) {
+      int i = k - j;
+      double c = std::sqrt(2.0 * (2 * i + 1) * (i + j + 1));
+      double Pa = jacobi_p(i, 0, 0, a), dPa = jacobi_dp(i, 0, 0, a);
+      double Pb = jacobi_p(j, 2 * i + 1, 0, b), dPb = jacobi_dp(j, 2 * i + 1, 0, b);
+      double omi = std::pow(om, i);
+      phi[m] = c * Pa * omi * Pb;
+      if (dxi) {
+        // d/dxi: da/dxi = 2/(1-eta)
+        double omi1 = (i >= 1) ? std::pow(om, i - 1) : 0.0;
+        dxi[m] = c * dPa * 2.0 * omi1 * Pb;
+        // d/deta: da/deta = (1+a)/(1-eta); d(om^i)/deta = -i om^(i-1); db/deta = 2
+        double t1 = (i >= 1) ? dPa * (1.0 + a) * omi1 * Pb : 0.0;
+        double t2 = (i >= 1) ? -Pa * i * omi1 * Pb : 0.0;
+        double t3 = Pa * omi * dPb * 2.0;
+        deta[m] = c * (t1 + t2 + t3);
+      }
+      ++m;
+    }
+}
+
+// Orthonormal Legendre trace basis on [0,1]: psi_k(s) = sqrt(2k+1) P_k(2s-1).
+static void legendre01(int pe, double s, double* psi) {
+  for (int k = 0; k <= pe; ++k) psi[k] = std::sqrt(2.0 * k + 1.0) * jacobi_p(k, 0, 0, 2.0 * s - 1.0);
+}
+
+// Reference point on local face lf at local parameter t (face lf runs from
+// local vertex lf to lf+1 mod 3).
+static void face_point(int lf, double t, double* xi, double* eta) {
+  if (lf == 0) { *xi = t; *eta = 0.0; }
+  else if (lf == 1) { *xi = 1.0 - t; *eta = t; }
+  else { *xi = 0.0; *eta = 1.0 - t; }
+}
+
+// ---------------------------------------------------------------------------
+// Cached tables per degree (filled once, read-only afterwards).
+// ---------------------------------------------------------------------------
+struct VolTab {
+  int p = 0, np = 0, nq = 0;
+  std::vector<double> w, phi, dxi, deta;  // [nq], [nq][np]
+};
+struct EdgeTab {  // element degree p, edge degree pe
+  int np = 0, nk = 0, ne = 0;
+  std::vector<double> s, w, psi;          // [ne], [ne], [ne][nk]
+  std::vector<double> phi[3][2];          // [lf][flip] -> [ne][np]
+};
+static VolTab g_vol[6];
+static EdgeTab g_edge[6][6];
+static std::once_flag g_once;
+
+static void tri_rule(int p, std::vector<double>& xi, std::vector<double>& eta, std::vector<double>& w) {
+  int n = p + 2;
+  std::vector<double> xa(n), wa(n), xb(n), wb(n);
+  gauss_jacobi(n, 0.0, 0.0, xa.data(), wa.data());
+  gauss_jacobi(n, 1.0, 0.0, xb.data(), wb.data());
+  xi.clear(); eta.clear(); w.clear();
+  for (int i = 0; i < n; ++i)
+    for (int j = 0; j < n; ++j) {
+      xi.push_back((1.0 + xa[i]) * (1.0 - xb[j]) / 4.0);
+      eta.push_back((1.0 + xb[j]) / 2.0);
+      w.push_back(wa[i] * wb[j] / 8.0);
+    }
+}
+static void edge_rule(int pe, std::vector<double>& s, std::vector<double>& w) {
+  int n = pe + 2;
+  std::vector<double> x(n), wx(n);
+  gauss_jacobi(n, 0.0, 0.0, x.data(), wx.data());
+  s.resize(n); w.resize(n);
+  for (int i = 0; i < n; ++i) { s[i] = (1.0 + x[i]) / 2.0; w[i] = wx[i] / 2.0; }
+}
+
+static void init_tables() {
+  for (int p = 1; p <= 5; ++p) {
+    VolTab& V = g_vol[p];
+    std::vector<double> xi, eta;
+    tri_rule(p, xi, eta, V.w);
+    V.p = p; V.np = n_basis(p); V.nq = (int)V.w.size();
+    V.phi.resize(V.nq * V.np); V.dxi.resize(V.nq * V.np); V.deta.resize(V.nq * V.np);
+    for (int q = 0; q < V.nq; ++q)
+      dubiner(p, xi[q], eta[q], &V.phi[q * V.np], &V.dxi[q * V.np], &V.deta[q * V.np]);
+  }
+  for (int p = 1; p <= 5; ++p)
+    for (int pe = p; pe <= 5; ++pe) {
+      EdgeTab& E = g_edge[p][pe];
+      E.np = n_basis(p); E.nk = pe + 1;
+      edge_rule(pe, E.s, E.w);
+      E.ne = (int)E.s.size();
+      E.psi.resize(E.ne * E.nk);
+      for (int g = 0; g < E.ne; ++g) legendre01(pe, E.s[g], &E.psi[g * E.nk]);
+      for (int lf = 0; lf < 3; ++lf)
+        for (int fl = 0; fl < 2; ++fl) {
+          E.phi[lf][fl].resize(E.ne * E.np);
+          for (int g = 0; g < E.ne; ++g) {
+            double t = fl ? 1.0 - E.s[g] : E.s[g], xi, eta;
+            face_point(lf, t, &xi, &eta);
+            dubiner(p, xi, eta, &E.phi[lf][fl][g * E.np], nullptr, nullptr);
+          }
+        }
+    }
+}
+static void ensure_tables() { std::call_once(g_once, init_tables); }
+
+// ---------------------------------------------------------------------------
+// Physics (Sec. 2), templated so that the complex-step derivative works.
+// w = (rho, rho u, rho v, E); f[k][f] = flux in direction k of field f.
+// ---------------------------------------------------------------------------
+template <class T>
+static void euler_flux(const T* w, double gam, T f[2][4]) {
+  T rho = w[0], mx = w[1], my = w[2], E = w[3];
+  T u = mx / rho, v = my / rho;
+  T p = (gam - 1.0) * (E - 0.5 * (mx * u + my * v));
+  f[0][0] = mx;      f[0][1] = mx * u + p; f[0][2] = mx * v;     f[0][3] = u * (E + p);
+  f[1][0] = my;      f[1][1] = my * u;     f[1][2] = my * v + p; f[1][3] = v * (E + p);
+}
+
+// viscous flux f_v(w, q) with q[k][f] = d w_f / d x_k (conserved-variable gradient)
+template <class T>
+static void ns_viscous_flux(const T* w, const T q[2][4], const orc_params& P, T fv[2][4]) {
+  const double gam = P.gamma;
+  T rho = w[0], u = w[1] / w[0], v = w[2] / w[0], E = w[3];
+  T p = (gam - 1.0) * (E - 0.5 * rho * (u * u + v * v));
+  T dudx[2], dvdx[2], dTdx[2];
+  for (int k = 0; k < 2; ++k) {
+    T dr = q[k][0];
+    dudx[k] = (q[k][1] - u * dr) / rho;
+    dvdx[k] = (q[k][2] - v * dr) / rho;
+    T dp = (gam - 1.0) * (q[k][3] - (u * q[k][1] + v * q[k][2]) + 0.5 * (u * u + v * v) * dr);
+    dTdx[k] = gam * (dp / rho - p * dr / (rho * rho));
+  }
+  T Tt = gam * p / rho;                                // T / T_inf
+  double S = 110.4 / P.t_inf;                          // Sutherland C2 / T_inf
+  double mu_inf = P.mach / P.reynolds;
+  T mu = mu_inf * Tt * std::sqrt(Tt) * (1.0 + S) / (Tt + S);
+  T kappa = mu / ((gam - 1.0) * P.prandtl);
+  T div = dudx[0] + dvdx[1];
+  T txx = mu * (2.0 * dudx[0] - (2.0 / 3.0) * div);
+  T tyy = mu * (2.0 * dvdx[1] - (2.0 / 3.0) * div);
+  T txy = mu * (dudx[1] + dvdx[0]);
+  fv[0][0] = 0.0; fv[0][1] = txx; fv[0][2] = txy; fv[0][3] = txx * u + txy * v + kappa * dTdx[0];
+  fv[1][0] = 0.0; fv[1][1] = txy; fv[1][2] = tyy; fv[1][3] = txy * u + tyy * v + kappa * dTdx[1];
+}
+
+// ---------------------------------------------------------------------------
+// Mesh: topology, faces and layouts (the layouts are the library's documented
+// conventions, re-derived here from their definition).
+// ---------------------------------------------------------------------------
+struct OMesh {
+  int ne = 0, nf = 0, nfield = 4;
+  std::vector<double> xy;        // [ne][3][2]
+  std::vector<int> vid, p;       // [ne][3], [ne]
+  std::vector<int> face_lo, face_hi, face_el0, face_el1, face_lf0, face_lf1, face_p;
+  std::vector<int> elem_face;    // [ne][3]
+  std::vector<int64_t> u_off, lam_off, x_off, k_blkoff;
+  std::vector<int> k_col;        // [nf][5]
+  int64_t u_len = 0, lam_len = 0, x_len = 0, k_len = 0;
+};
+
+struct Geom {
+  double J[2][2], Jinv[2][2], detJ, nrm[3][2], len[3], area, perim;
+};
+static void elem_geom(const OMesh& M, int K, Geom& g) {
+  const double* c = &M.xy[K * 6];
+  double x0 = c[0], y0 = c[1], x1 = c[2], y1 = c[3], x2 = c[4], y2 = c[5];
+  g.J[0][0] = x1 - x0; g.J[0][1] = x2 - x0;
+  g.J[1][0] = y1 - y0; g.J[1][1] = y2 - y0;
+  g.detJ = g.J[0][0] * g.J[1][1] - g.J[0][1] * g.J[1][0];
+  g.Jinv[0][0] = g.J[1][1] / g.detJ;  g.Jinv[0][1] = -g.J[0][1] / g.detJ;
+  g.Jinv[1][0] = -g.J[1][0] / g.detJ; g.Jinv[1][1] = g.J[0][0] / g.detJ;
+  g.perim = 0;
+  for (int lf = 0; lf < 3; ++lf) {
+    int a = lf, b = (lf + 1) % 3;
+    double dx = c[2 * b] - c[2 * a], dy = c[2 * b + 1] - c[2 * a + 1];
+    g.len[lf] = std::sqrt(dx * dx + dy * dy);
+    g.nrm[lf][0] = dy / g.len[lf];
+    g.nrm[lf][1] = -dx / g.len[lf];
+    g.perim += g.len[lf];
+  }
+  g.area = 0.5 * g.detJ;
+}
+
+static int elem_nt(const OMesh& M, int K) {
+  int nt = 0;
+  for (int lf = 0; lf < 3; ++lf) nt += 4 * (M.face_p[M.elem_face[K * 3 + lf]] + 1);
+  return nt;
+}
+static int elem_n(const OMesh& M, int K) { return M.nfield * n_basis(M.p[K]); }
+static inline int elem_flip(const OMesh& M, int K, int lf) {
+  return M.vid[K * 3 + lf] > M.vid[K * 3 + (lf + 1) % 3] ? 1 : 0;
+}
+
+// ---------------------------------------------------------------------------
+// Element residual (Eqs. hdg_ls1-hdg_ls3 and the element's share of
+// hdg_cont), for element K with its coefficient vectors U (Q then W) and the
+// traces L of its three faces in local order.  Nu has the layout of U, Nl of L.
+// ---------------------------------------------------------------------------
+template <class T>
+static void element_residual(const OMesh& M, const orc_params& P, int K, const Geom& g,
+                             const T* U, const T* L, T* Nu, T* Nl) {
+  const int p = M.p[K], np = n_basis(p);
+  const bool ns = (M.nfield == 12);
+  const int woff = ns ? 8 * np : 0;
+  const int n = M.nfield * np;
+  int nt = elem_nt(M, K);
+  for (int r = 0; r < n; ++r) Nu[r] = 0.0;
+  for (int r = 0; r < nt; ++r) Nl[r] = 0.0;
+  const VolTab& V = g_vol[p];
+  std::vector<double> gx(np), gy(np);
+  // volume terms
+  for (int q = 0; q < V.nq; ++q) {
+    const double* phi = &V.phi[q * np];
+    const double wq = V.w[q] * g.detJ;
+    for (int j = 0; j < np; ++j) {
+      double dx = V.dxi[q * np + j], de = V.deta[q * np + j];
+      gx[j] = g.Jinv[0][0] * dx + g.Jinv[1][0] * de;
+      gy[j] = g.Jinv[0][1] * dx + g.Jinv[1][1] * de;
+    }
+    T w[4], qv[2][4], fc[2][4], fv[2][4];
+    for (int f = 0; f < 4; ++f) {
+      w[f] = 0.0;
+      for (int j = 0; j < np; ++j) w[f] += U[woff + f * np + j] * phi[j];
+    }
+    euler_flux(w, P.gamma, fc);
+    if (ns) {
+      for (int k = 0; k < 2; ++k)
+        for (int f = 0; f < 4; ++f) {
+          qv[k][f] = 0.0;
+          for (int j = 0; j < np; ++j) qv[k][f] += U[(k * 4 + f) * np + j] * phi[j];
+        }
+      ns_viscous_flux(w, qv, P, fv);
+    } else {
+      for (int k = 0; k < 2; ++k) for (int f = 0; f < 4; ++f) fv[k][f] = 0.0;
+    }
+    // -(grad phi_i, f_c(w) - f_v(w,q))_K
+    for (int f = 0; f < 4; ++f)
+      for (int i = 0; i < np; ++i)
+        Nu[woff + f * np + i] -= wq * (gx[i] * (fc[0][f] - fv[0][f]) + gy[i] * (fc[1][f] - fv[1][f]));
+    // (tau, q)_K + (div tau, w)_K
+    if (ns)
+      for (int k = 0; k < 2; ++k)
+        for (int f = 0; f < 4; ++f)
+          for (int i = 0; i < np; ++i) {
+            double gk = (k == 0) ? gx[i] : gy[i];
+            Nu[(k * 4 + f) * np + i] += wq * (phi[i] * qv[k][f] + gk * w[f]);
+          }
+  }
+  // face terms
+  int loff = 0;
+  for (int lf = 0; lf < 3; ++lf) {
+    int e = M.elem_face[K * 3 + lf];
+    int pe = M.face_p[e], nk = pe + 1;
+    int fl = elem_flip(M, K, lf);
+    const EdgeTab& Et = g_edge[p][pe];
+    const double nx = g.nrm[lf][0], ny = g.nrm[lf][1];
+    for (int gq = 0; gq < Et.ne; ++gq) {
+      const double we = Et.w[gq] * g.len[lf];
+      const double* phi = &Et.phi[lf][fl][gq * np];
+      const double* psi = &Et.psi[gq * nk];
+      T w[4], lam[4], qv[2][4], fc[2][4], fv[2][4], fh[4];
+      for (int f = 0; f < 4; ++f) {
+        w[f] = 0.0;
+        for (int j = 0; j < np; ++j) w[f] += U[woff + f * np + j] * phi[j];
+        lam[f] = 0.0;
+        for (int k = 0; k < nk; ++k) lam[f] += L[loff + f * nk + k] * psi[k];
+      }
+      euler_flux(lam, P.gamma, fc);
+      if (ns) {
+        for (int k = 0; k < 2; ++k)
+          for (int f = 0; f < 4; ++f) {
+            qv[k][f] = 0.0;
+            for (int j = 0; j < np; ++j) qv[k][f] += U[(k * 4 + f) * np + j] * phi[j];
+          }
+        ns_viscous_flux(lam, qv, P, fv);
+      } else {
+        for (int k = 0; k < 2; ++k) for (int f = 0; f < 4; ++f) fv[k][f] = 0.0;
+      }
+      // numerical flux  (f_c(lam) - f_v(lam, q)).n - alpha (lam - w)
+      for (int f = 0; f < 4; ++f)
+        fh[f] = nx * (fc[0][f] - fv[0][f]) + ny * (fc[1][f] - fv[1][f]) - P.alpha * (lam[f] - w[f]);
+      for (int f = 0; f < 4; ++f)
+        for (int j = 0; j < np; ++j) Nu[woff + f * np + j] += we * phi[j] * fh[f];
+      if (ns)  // -<tau.n, lambda>_dK
+        for (int k = 0; k < 2; ++k) {
+          double nk_ = (k == 0) ? nx : ny;
+          for (int f = 0; f < 4; ++f)
+            for (int j = 0; j < np; ++j) Nu[(k * 4 + f) * np + j] -= we * phi[j] * nk_ * lam[f];
+        }
+      // this element's share of <mu, [[f_hat]]>_e
+      for (int f = 0; f < 4; ++f)
+        for (int k = 0; k < nk; ++k) Nl[loff + f * nk + k] += we * psi[k] * fh[f];
+    }
+    loff += 4 * nk;
+  }
+}
+
+// local time step of Sec. 3.3 from the element-mean state (real part of U)
+static double local_dt(const OMesh& M, const orc_params& P, int K, const Geom& g, const double* U) {
+  const int np = n_basis(M.p[K]);
+  const int woff = (M.nfield == 12) ? 8 * np : 0;
+  const double c0 = std::sqrt(2.0);  // value of the constant orthonormal mode
+  double rho = c0 * U[woff], u = c0 * U[woff + np] / rho, v = c0 * U[woff + 2 * np] / rho,
+         E = c0 * U[woff + 3 * np];
+  double p = (P.gamma - 1.0) * (E - 0.5 * rho * (u * u + v * v));
+  double c = std::sqrt(P.gamma * p / rho);
+  double lam_c = (std::sqrt(u * u + v * v) + c) * g.perim;
+  double lam_v = 0.0;
+  if (M.nfield == 12) {
+    double Tt = P.gamma * p / rho, S = 110.4 / P.t_inf;
+    double mu = (P.mach / P.reynolds) * Tt * std::sqrt(Tt) * (1.0 + S) / (Tt + S);
+    lam_v = P.gamma * mu / (P.prandtl * rho) * g.perim * g.perim / g.area;
+  }
+  return P.cfl * g.area / (lam_c + 4.0 * lam_v);
+}
+
+// Element blocks: A = dNu/dU, B = dNu/dL, C = dNl/dU, D = dNl/dL (complex
+// step, exact to rounding), F = -Nu, H = -Nl; pseudo-time mass on the W block.
+static const double CS_H = 1e-30;
+static void element_blocks(const OMesh& M, const orc_params& P, int K, const double* U, const double* L,
+                           std::vector<double>& A, std::vector<double>& B, std::vector<double>& C,
+                           std::vector<double>& D, std::vector<double>& F, std::vector<double>& H) {
+  Geom g;
+  elem_geom(M, K, g);
+  const int n = elem_n(M, K), nt = elem_nt(M, K);
+  A.assign(n * n, 0.0); B.assign(n * nt, 0.0); C.assign(nt * n, 0.0); D.assign(nt * nt, 0.0);
+  F.assign(n, 0.0); H.assign(nt, 0.0);
+  std::vector<cplx> Uc(n), Lc(nt), Nu(n), Nl(nt);
+  for (int r = 0; r < n; ++r) Uc[r] = U[r];
+  for (int r = 0; r < nt; ++r) Lc[r] = L[r];
+  element_residual<cplx>(M, P, K, g, Uc.data(), Lc.data(), Nu.data(), Nl.data());
+  for (int r = 0; r < n; ++r) F[r] = -Nu[r].real();
+  for (int r = 0; r < nt; ++r) H[r] = -Nl[r].real();
+  for (int c = 0; c < n + nt; ++c) {
+    if (c < n) Uc[c] += cplx(0.0, CS_H); else Lc[c - n] += cplx(0.0, CS_H);
+    element_residual<cplx>(M, P, K, g, Uc.data(), Lc.data(), Nu.data(), Nl.data());
+    if (c < n) Uc[c] = U[c]; else Lc[c - n] = L[c - n];
+    for (int r = 0; r < n; ++r) {
+      double d = Nu[r].imag() / CS_H;
+      if (c < n) A[r * n + c] = d; else B[r * nt + (c - n)] = d;
+    }
+    for (int r = 0; r < nt; ++r) {
+      double d = Nl[r].imag() / CS_H;
+      if (c < n) C[r * n + c] = d; else D[r * nt + (c - n)] = d;
+    }
+  }
+  if (P.cfl > 0.0) {
+    double dt = local_dt(M, P, K, g, U);
+    const int np = n_basis(M.p[K]);
+    const int woff = (M.nfield == 12) ? 8 * np : 0;
+    for (int r = woff; r < n; ++r) A[r * n + r] += g.detJ / dt;
+  }
+}
+
+// dense LU with partial pivoting (first maximal |pivot| wins), in place
+static int lu_factor(int n, std::vector<double>& A, std::vector<int>& piv) {
+  piv.resize(n);
+  for (int k = 0; k < n; ++k) {
+    int r = k;
+    double best = std::fabs(A[k * n + k]);
+    for (int i = k + 1; i < n; ++i)
+      if (std::fabs(A[i * n + k]) > best) { best = std::fabs(A[i * n + k]); r = i; }
+    piv[k] = r;
+    if (best == 0.0) return 1;
+    if (r != k)
+      for (int j = 0; j < n; ++j) std::swap(A[k * n + j], A[r * n + j]);
+    for (int i = k + 1; i < n; ++i) {
+      A[i * n + k] /= A[k * n + k];
+      double lik = A[i * n + k];
+      for (int j = k + 1; j < n; ++j) A[i * n + j] -= lik * A[k * n + j];
+    }
+  }
+  return 0;
+}
+// solve A x = b for nrhs columns of the row-major n x nrhs matrix X (in place)
+static void lu_solve(int n, const std::vector<double>& LU, const std::vector<int>& piv, int nrhs, double* X) {
+  for (int k = 0; k < n; ++k)
+    if (piv[k] != k)
+      for (int c = 0; c < nrhs; ++c) std::swap(X[k * nrhs + c], X[piv[k] * nrhs + c]);
+  for (int c = 0; c < nrhs; ++c) {
+    for (int i = 0; i < n; ++i) {
+      double s = X[i * nrhs + c];
+      for (int j = 0; j < i; ++j) s -= LU[i * n + j] * X[j * nrhs + c];
+      X[i * nrhs + c] = s;
+    }
+    for (int i = n - 1; i >= 0; --i) {
+      double s = X[i * nrhs + c];
+      for (int j = i + 1; j < n; ++j) s -= LU[i * n + j] * X[j * nrhs + c];
+      X[i * nrhs + c] = s / LU[i * n + i];
+    }
+  }
+}
+
+// gather of element K's trace vector from the global Lambda (faces in local order)
+static void gather_trace(const OMesh& M, int K, const double* Lam, std::vector<double>& L) {
+  L.clear();
+  for (int lf = 0; lf < 3; ++lf) {
+    int e = M.elem_face[K * 3 + lf];
+    int len = 4 * (M.face_p[e] + 1);
+    for (int r = 0; r < len; ++r) L.push_back(Lam[M.lam_off[e] + r]);
+  }
+}
+
+// Condensation of one element: X = A^{-1}[B | F] (n x (nt+1), row-major),
+// S = D - C X_B (nt x nt), Ek = H - C X_F (nt).  Returns 1 on a zero pivot.
+static int element_condense(const OMesh& M, const orc_params& P, int K, const double* U, const double* Lam,
+                            std::vector<double>& X, std::vector<double>& S, std::vector<double>& Ek,
+                            std::vector<double>* Nu_out, std::vector<double>* Nl_out) {
+  std::vector<double> L, A, B, C, D, F, H;
+  gather_trace(M, K, Lam, L);
+  const double* UK = U + M.u_off[K];
+  element_blocks(M, P, K, UK, L.data(), A, B, C, D, F, H);
+  const int n = elem_n(M, K), nt = elem_nt(M, K), nr = nt + 1;
+  if (Nu_out) { Nu_out->resize(n); for (int r = 0; r < n; ++r) (*Nu_out)[r] = -F[r]; }
+  if (Nl_out) { Nl_out->resize(nt); for (int r = 0; r < nt; ++r) (*Nl_out)[r] = -H[r]; }
+  X.assign(n * nr, 0.0);
+  for (int r = 0; r < n; ++r) {
+    for (int c = 0; c < nt; ++c) X[r * nr + c] = B[r * nt + c];
+    X[r * nr + nt] = F[r];
+  }
+  std::vector<int> piv;
+  int st = lu_factor(n, A, piv);
+  S.assign(nt * nt, 0.0);
+  Ek.assign(nt, 0.0);
+  if (st) return st;
+  lu_solve(n, A, piv, nr, X.data());
+  for (int r = 0; r < nt; ++r) {
+    for (int c = 0; c < nt; ++c) {
+      double s = D[r * nt + c];
+      for (int k = 0; k < n; ++k) s -= C[r * n + k] * X[k * nr + c];
+      S[r * nt + c] = s;
+    }
+    double s = H[r];
+    for (int k = 0; k < n; ++k) s -= C[r * n + k] * X[k * nr + nt];
+    Ek[r] = s;
+  }
+  return 0;
+}
+
+// ---------------------------------------------------------------------------
+// C interface (ctypes)
+// ---------------------------------------------------------------------------
+extern "C" {
+
+// n-point Gauss-Jacobi rule, weight (1-x)^alpha (1+x)^beta on [-1,1]
+int orc_gauss_jacobi(int n, double alpha, double beta, double* x, double* w) {
+  if (n < 1 || n > 64) return 1;
+  gauss_jacobi(n, alpha, beta, x, w);
+  return 0;
+}
+// collapsed Gauss rule on the reference triangle: (p+2)^2 points
+int orc_tri_rule(int p, double* xi, double* eta, double* w) {
+  if (p < 0 || p > 20) return 1;
+  std::vector<double> a, b, c;
+  tri_rule(p, a, b, c);
+  std::copy(a.begin(), a.end(), xi); std::copy(b.begin(), b.end(), eta); std::copy(c.begin(), c.end(), w);
+  return 0;
+}
+// (pe+2)-point Gauss-Legendre rule on [0,1]
+int orc_edge_rule(int pe, double* s, double* w) {
+  if (pe < 0 || pe > 40) return 1;
+  std::vector<double> a, b;
+  edge_rule(pe, a, b);
+  std::copy(a.begin(), a.end(), s); std::copy(b.begin(), b.end(), w);
+  return 0;
+}
+// Dubiner basis values/gradients at npts points: out arrays [npts][n_basis(p)]
+int orc_dubiner(int p, int npts, const double* xi, const double* eta, double* phi, double* dxi, double* deta) {
+  if (p < 0 || p > 12) return 1;
+  int np = n_basis(p);
+  for (int q = 0; q < npts; ++q)
+    dubiner(p, xi[q], eta[q], phi + q * np, dxi ? dxi + q * np : nullptr, deta ? deta + q * np : nullptr);
+  return 0;
+}
+int orc_legendre01(int pe, int npts, const double* s, double* psi) {
+  for (int q = 0; q < npts; ++q) legendre01(pe, s[q], psi + q * (pe + 1));
+  return 0;
+}
+// physics at one state: f[2][4]
+void orc_euler_flux(const double* w, double gamma, double* f) {
+  double ff[2][4];
+  euler_flux(w, gamma, ff);
+  std::memcpy(f, ff, sizeof(ff));
+}
+void orc_ns_viscous_flux(const double* w, const double* q, const orc_params* P, double* fv) {
+  double qq[2][4], ff[2][4];
+  std::memcpy(qq, q, sizeof(qq));
+  ns_viscous_flux(w, qq, *P, ff);
+  std::memcpy(fv, ff, sizeof(ff));
+}
+
+// Build the mesh.  Returns 0 ok, 2 bad input (non-positive det J, p out of
+// range, a face not shared by exactly two elements, two elements sharing two faces).
+int orc_mesh_create(int n_elem, int nfield, const double* elem_xy, const int32_t* elem_vid,
+                    const int8_t* elem_p, void** out) {
+  ensure_tables();
+  if (n_elem < 1 || (nfield != 4 && nfield != 12)) return 2;
+  OMesh* M = new OMesh();
+  M->ne = n_elem; M->nfield = nfield;
+  M->xy.assign(elem_xy, elem_xy + 6 * n_elem);
+  M->vid.assign(elem_vid, elem_vid + 3 * n_elem);
+  M->p.resize(n_elem);
+  for (int K = 0; K < n_elem; ++K) {
+    M->p[K] = elem_p[K];
+    Geom g;
+    elem_geom(*M, K, g);
+    if (M->p[K] < 1 || M->p[K] > 4 || !(g.detJ > 0.0)) { delete M; return 2; }
+  }
+  struct Ent { int lo, hi, K, lf; };
+  std::vector<Ent> ents;
+  for (int K = 0; K < n_elem; ++K)
+    for (int lf = 0; lf < 3; ++lf) {
+      int a = M->vid[K * 3 + lf], b = M->vid[K * 3 + (lf + 1) % 3];
+      ents.push_back({std::min(a, b), std::max(a, b), K, lf});
+    }
+  std::sort(ents.begin(), ents.end(), [](const Ent& x, const Ent& y) {
+    if (x.lo != y.lo) return x.lo < y.lo;
+    if (x.hi != y.hi) return x.hi < y.hi;
+    return x.K < y.K;
+  });
+  M->elem_face.assign(3 * n_elem, -1);
+  for (size_t i = 0; i < ents.size(); i += 2) {
+    if (i + 1 >= ents.size() || ents[i + 1].lo != ents[i].lo || ents[i + 1].hi != ents[i].hi ||
+        (i + 2 < ents.size() && ents[i + 2].lo == ents[i].lo && ents[i + 2].hi == ents[i].hi) ||
+        ents[i].K == ents[i + 1].K) {
+      delete M; return 2;
+    }
+    int f = M->nf++;
+    M->face_lo.push_back(ents[i].lo); M->face_hi.push_back(ents[i].hi);
+    M->face_el0.push_back(ents[i].K); M->face_lf0.push_back(ents[i].lf);
+    M->face_el1.push_back(ents[i + 1].K); M->face_lf1.push_back(ents[i + 1].lf);
+    M->face_p.push_back(std::max(M->p[ents[i].K], M->p[ents[i + 1].K]));
+    M->elem_face[ents[i].K * 3 + ents[i].lf] = f;
+    M->elem_face[ents[i + 1].K * 3 + ents[i + 1].lf] = f;
+  }
+  // layouts
+  M->u_off.resize(n_elem + 1); M->x_off.resize(n_elem + 1);
+  M->u_off[0] = 0; M->x_off[0] = 0;
+  for (int K = 0; K < n_elem; ++K) {
+    int n = elem_n(*M, K), nt = elem_nt(*M, K);
+    M->u_off[K + 1] = M->u_off[K] + n;
+    M->x_off[K + 1] = M->x_off[K] + (int64_t)n * (nt + 1);
+  }
+  M->u_len = M->u_off[n_elem]; M->x_len = M->x_off[n_elem];
+  M->lam_off.resize(M->nf + 1);
+  M->lam_off[0] = 0;
+  for (int f = 0; f < M->nf; ++f) M->lam_off[f + 1] = M->lam_off[f] + 4 * (M->face_p[f] + 1);
+  M->lam_len = M->lam_off[M->nf];
+  M->k_col.resize(5 * M->nf);
+  M->k_blkoff.resize(5 * M->nf + 1);
+  M->k_blkoff[0] = 0;
+  for (int f = 0; f < M->nf; ++f) {
+    std::vector<int> cols = {f};
+    for (int s = 0; s < 2; ++s) {
+      int K = s ? M->face_el1[f] : M->face_el0[f];
+      for (int lf = 0; lf < 3; ++lf) {
+        int e = M->elem_face[K * 3 + lf];
+        if (e != f) cols.push_back(e);
+      }
+    }
+    std::sort(cols.begin(), cols.end());
+    if (std::adjacent_find(cols.begin(), cols.end()) != cols.end()) { delete M; return 2; }
+    for (int b = 0; b < 5; ++b) {
+      M->k_col[5 * f + b] = cols[b];
+      int64_t sz = (int64_t)(4 * (M->face_p[f] + 1)) * (4 * (M->face_p[cols[b]] + 1));
+      M->k_blkoff[5 * f + b + 1] = M->k_blkoff[5 * f + b] + sz;
+    }
+  }
+  M->k_len = M->k_blkoff[5 * M->nf];
+  *out = M;
+  return 0;
+}
+void orc_mesh_destroy(void* h) { delete (OMesh*)h; }
+
+// sizes: [n_face, u_len, lam_len, x_len, k_len]
+void orc_mesh_sizes(void* h, int64_t* out) {
+  OMesh* M = (OMesh*)h;
+  out[0] = M->nf; out[1] = M->u_len; out[2] = M->lam_len; out[3] = M->x_len; out[4] = M->k_len;
+}
+// layout arrays; any pointer may be null
+void orc_mesh_arrays(void* h, int32_t* face_vid, int32_t* face_el, int32_t* face_lf, int32_t* face_p,
+                     int32_t* elem_face, int64_t* u_off, int64_t* lam_off, int64_t* x_off, int32_t* k_col,
+                     int64_t* k_blkoff) {
+  OMesh* M = (OMesh*)h;
+  for (int f = 0; f < M->nf; ++f) {
+    if (face_vid) { face_vid[2 * f] = M->face_lo[f]; face_vid[2 * f + 1] = M->face_hi[f]; }
+    if (face_el) { face_el[2 * f] = M->face_el0[f]; face_el[2 * f + 1] = M->face_el1[f]; }
+    if (face_lf) { face_lf[2 * f] = M->face_lf0[f]; face_lf[2 * f + 1] = M->face_lf1[f]; }
+    if (face_p) face_p[f] = M->face_p[f];
+  }
+  if (elem_face) std::copy(M->elem_face.begin(), M->elem_face.end(), elem_face);
+  if (u_off) std::copy(M->u_off.begin(), M->u_off.end(), u_off);
+  if (lam_off) std::copy(M->lam_off.begin(), M->lam_off.end(), lam_off);
+  if (x_off) std::copy(M->x_off.begin(), M->x_off.end(), x_off);
+  if (k_col) std::copy(M->k_col.begin(), M->k_col.end(), k_col);
+  if (k_blkoff) std::copy(M->k_blkoff.begin(), M->k_blkoff.end(), k_blkoff);
+}
+
+// Residual of element K (real): Nu [n], Nl [nt] (this element's share of the trace rows).
+int orc_element_residual(void* h, const orc_params* P, int K, const double* U, const double* Lam,
+                         double* Nu, double* Nl) {
+  OMesh* M = (OMesh*)h;
+  Geom g;
+  elem_geom(*M, K, g);
+  std::vector<double> L;
+  gather_trace(*M, K, Lam, L);
+  element_residual<double>(*M, *P, K, g, U + M->u_off[K], L.data(), Nu, Nl);
+  return 0;
+}
+
+// Element blocks of element K (row-major): A [n][n], B [n][nt], C [nt][n], D [nt][nt], F [n], H [nt]
+int orc_element_blocks(void* h, const orc_params* P, int K, const double* U, const double* Lam, double* A,
+                       double* B, double* C, double* D, double* F, double* H) {
+  OMesh* M = (OMesh*)h;
+  std::vector<double> L, a, b, c, d, f, hh;
+  gather_trace(*M, K, Lam, L);
+  element_blocks(*M, *P, K, U + M->u_off[K], L.data(), a, b, c, d, f, hh);
+  std::copy(a.begin(), a.end(), A); std::copy(b.begin(), b.end(), B);
+  std::copy(c.begin(), c.end(), C); std::copy(d.begin(), d.end(), D);
+  std::copy(f.begin(), f.end(), F); std::copy(hh.begin(), hh.end(), H);
+  return 0;
+}
+
+// Condensation of one element K: X [n][nt+1], S [nt][nt], Ek [nt]; status 0 ok / 1 zero pivot
+int orc_element_condense(void* h, const orc_params* P, int K, const double* U, const double* Lam, double* X,
+                         double* S, double* Ek) {
+  OMesh* M = (OMesh*)h;
+  std::vector<double> x, s, e;
+  int st = element_condense(*M, *P, K, U, Lam, x, s, e, nullptr, nullptr);
+  std::copy(x.begin(), x.end(), X); std::copy(s.begin(), s.end(), S); std::copy(e.begin(), e.end(), Ek);
+  return st;
+}
+
+// Whole-mesh condensation and assembly: X [x_len], K [k_len], E [lam_len],
+// resU [u_len], resLam [lam_len] (sum over both sides), status [n_elem].
+// Elements are processed in ascending id, so every diagonal block and every
+// entry of E is (lower element's contribution) + (higher element's).
+// Elements [k0, k1) only if k1 > k0 (then K/E/resLam hold partial sums).
+int orc_condense(void* h, const orc_params* P, const double* U, const double* Lam, double* X, double* Kv,
+                 double* E, double* resU, double* resLam, int32_t* status, int k0, int k1) {
+  OMesh* M = (OMesh*)h;
+  if (k1 <= k0) { k0 = 0; k1 = M->ne; }
+  std::fill(Kv, Kv + M->k_len, 0.0);
+  std::fill(E, E + M->lam_len, 0.0);
+  std::fill(resLam, resLam + M->lam_len, 0.0);
+  int bad = 0;
+  for (int K = k0; K < k1; ++K) {
+    std::vector<double> x, s, ek, nu, nl;
+    int st = element_condense(*M, *P, K, U, Lam, x, s, ek, &nu, &nl);
+    status[K] = st;
+    bad |= st;
+    std::copy(x.begin(), x.end(), X + M->x_off[K]);
+    std::copy(nu.begin(), nu.end(), resU + M->u_off[K]);
+    const int nt = elem_nt(*M, K);
+    int roff = 0;
+    for (int a = 0; a < 3; ++a) {
+      int ea = M->elem_face[K * 3 + a], na = 4 * (M->face_p[ea] + 1);
+      for (int r = 0; r < na; ++r) {
+        E[M->lam_off[ea] + r] += ek[roff + r];
+        resLam[M->lam_off[ea] + r] += nl[roff + r];
+      }
+      int coff = 0;
+      for (int b = 0; b < 3; ++b) {
+        int eb = M->elem_face[K * 3 + b], nb = 4 * (M->face_p[eb] + 1);
+        int slot = -1;
+        for (int t = 0; t < 5; ++t)
+          if (M->k_col[5 * ea + t] == eb) slot = t;
+        double* blk = Kv + M->k_blkoff[5 * ea + slot];
+        for (int r = 0; r < na; ++r)
+          for (int c = 0; c < nb; ++c) blk[r * nb + c] += s[(roff + r) * nt + coff + c];
+        coff += nb;
+      }
+      roff += na;
+    }
+  }
+  return bad ? 1 : 0;
+}
+
+// Reconstruction, Eq. (ls): dU_K = X_F - X_B dLambda_K for every element.
+int orc_recover(void* h, const double* X, const double* dLam, double* dU) {
+  OMesh* M = (OMesh*)h;
+  for (int K = 0; K < M->ne; ++K) {
+    std::vector<double> L;
+    gather_trace(*M, K, dLam, L);
+    const int n = elem_n(*M, K), nt = elem_nt(*M, K), nr = nt + 1;
+    const double* XK = X + M->x_off[K];
+    for (int r = 0; r < n; ++r) {
+      double s = XK[r * nr + nt];
+      for (int c = 0; c < nt; ++c) s -= XK[r * nr + c] * L[c];
+      dU[M->u_off[K] + r] = s;
+    }
+  }
+  return 0;
+}
+
+// Global residual (U rows then Lambda rows summed over both sides), real.
+int orc_global_residual(void* h, const orc_params* P, const double* U, const double* Lam, double* R) {
+  OMesh* M = (OMesh*)h;
+  std::fill(R, R + M->u_len + M->lam_len, 0.0);
+  for (int K = 0; K < M->ne; ++K) {
+    Geom g;
+    elem_geom(*M, K, g);
+    std::vector<double> L;
+    gather_trace(*M, K, Lam, L);
+    std::vector<double> nu(elem_n(*M, K)), nl(elem_nt(*M, K));
+    element_residual<double>(*M, *P, K, g, U + M->u_off[K], L.data(), nu.data(), nl.data());
+    std::copy(nu.begin(), nu.end(), R + M->u_off[K]);
+    int roff = 0;
+    for (int a = 0; a < 3; ++a) {
+      int ea = M->elem_face[K * 3 + a], na = 4 * (M->face_p[ea] + 1);
+      for (int r = 0; r < na; ++r) R[M->u_len + M->lam_off[ea] + r] += nl[roff + r];
+      roff += na;
+    }
+  }
+  return 0;
+}
+
+// Monolithic linearised system for tiny meshes: the Jacobian of the global
+// residual by complex step on every global unknown (U then Lambda), the
+// pseudo-time mass on each element's W block, solved densely:
+//   J [dU; dLam] = -R.   Returns 1 if the dense matrix is singular.
+// Jout (optional) receives the (u_len+lam_len)^2 row-major matrix.
+int orc_monolithic(void* h, const orc_params* P, const double* U, const double* Lam, double* dU,
+                   double* dLam, double* Jout) {
+  OMesh* M = (OMesh*)h;
+  const int64_t N = M->u_len + M->lam_len;
+  if (N > 4000) return 2;
+  std::vector<double> J(N * N, 0.0), R(N);
+  std::vector<cplx> Uc(U, U + M->u_len), Lc(Lam, Lam + M->lam_len);
+  orc_global_residual(h, P, U, Lam, R.data());
+  for (int64_t c = 0; c < N; ++c) {
+    if (c < M->u_len) Uc[c] += cplx(0.0, CS_H); else Lc[c - M->u_len] += cplx(0.0, CS_H);
+    std::vector<cplx> Rc(N, 0.0);
+    for (int K = 0; K < M->ne; ++K) {
+      Geom g;
+      elem_geom(*M, K, g);
+      std::vector<cplx> L;
+      for (int lf = 0; lf < 3; ++lf) {
+        int e = M->elem_face[K * 3 + lf];
+        for (int r = 0; r < 4 * (M->face_p[e] + 1); ++r) L.push_back(Lc[M->lam_off[e] + r]);
+      }
+      std::vector<cplx> nu(elem_n(*M, K)), nl(elem_nt(*M, K));
+      element_residual<cplx>(*M, *P, K, g, Uc.data() + M->u_off[K], L.data(), nu.data(), nl.data());
+      for (size_t r = 0; r < nu.size(); ++r) Rc[M->u_off[K] + r] = nu[r];
+      int roff = 0;
+      for (int a = 0; a < 3; ++a) {
+        int ea = M->elem_face[K * 3 + a], na = 4 * (M->face_p[ea] + 1);
+        for (int r = 0; r < na; ++r) Rc[M->u_len + M->lam_off[ea] + r] += nl[roff + r];
+        roff += na;
+      }
+    }
+    if (c < M->u_len) Uc[c] = U[c]; else Lc[c - M->u_len] = Lam[c - M->u_len];
+    for (int64_t r = 0; r < N; ++r) J[r * N + c] = Rc[r].imag() / CS_H;
+  }
+  if (P->cfl > 0.0)
+    for (int K = 0; K < M->ne; ++K) {
+      Geom g;
+      elem_geom(*M, K, g);
+      double dt = local_dt(*M, *P, K, g, U + M->u_off[K]);
+      const int np = n_basis(M->p[K]), woff = (M->nfield == 12) ? 8 * np : 0;
+      for (int r = woff; r < elem_n(*M, K); ++r) {
+        int64_t gr = M->u_off[K] + r;
+        J[gr * N + gr] += g.detJ / dt;
+      }
+    }
+  if (Jout) std::copy(J.begin(), J.end(), Jout);
+  std::vector<double> x(N);
+  for (int64_t r = 0; r < N; ++r) x[r] = -R[r];
+  std::vector<int> piv;
+  if (lu_factor((int)N, J, piv)) return 1;
+  lu_solve((int)N, J, piv, 1, x.data());
+  std::copy(x.begin(), x.begin() + M->u_len, dU);
+  std::copy(x.begin() + M->u_len, x.end(), dLam);
+  return 0;
+}
+
+// Dense LU solve helper for tests (A n x n row-major, b -> x in place).
+int orc_dense_solve(int n, const double* A, double* b) {
+  std::vector<double> a(A, A + (int64_t)n * n);
+  std::vector<int> piv;
+  if (lu_factor(n, a, piv)) return 1;
+  lu_solve(n, a, piv, 1, b);
+  return 0;
+}
+
+}  // extern "C"

@@ -1,0 +1,311 @@
+"""Seeded synthetic inputs: periodic jittered triangle meshes, degree maps and
+coefficient vectors of a Newton iterate.
+
+This module is data only.  It holds none of the HDG method's arithmetic (no
+basis, quadrature, flux, Jacobian or condensation): both the CUDA path and
+the CPU oracle receive exactly the arrays built here.  The flow conditions
+follow the paper's test cases (arXiv:1308.3995, Sec. 5: gamma = 1.4, Mach
+0.5/0.8/1.4, Re = 5000, Pr = 0.72; degrees p = 1..4); the meshes replace the
+NACA0012 meshes, which are not available, by periodic unit-square grids.
+
+Recipe (all random numbers from ``numpy.random.default_rng(seed)``):
+  * mesh: nx x ny cells of the unit square, periodic; cell (i, j) split along
+    its (i,j)-(i+1,j+1) diagonal into (a,b,c) and (a,c,d) (counter-clockwise);
+    each topological vertex moved by U(-j hx, j hx) x U(-j hy, j hy); element
+    vertex coordinates carry the periodic image (+1) where a cell wraps;
+  * state: the analytic primitive field (rho, u, v, p) of the case is turned
+    into conserved variables (rho, rho u, rho v, p/(gamma-1) + rho|v|^2/2);
+    mode 0 of each element's coefficients is the field at the centroid
+    divided by sqrt(2) (sqrt(2) is the value of the constant mode of an
+    orthonormal basis on a reference triangle of area 1/2), modes m >= 1 are
+    1e-3 * scale_f * N(0,1) / (m+1); Navier-Stokes gradient coefficients are
+    5e-2 * scale_f * N(0,1) for mode 0 and 1e-3 * scale_f * N(0,1)/(m+1)
+    otherwise; scale_f = |w_inf,f| + 0.1;
+  * trace: mode 0 of every face is the field at the face midpoint, modes
+    k >= 1 are 1e-3 * scale_f * N(0,1) / (k+1);
+  * trace update for the reconstruction: 1e-3 * N(0,1) per entry.
+"""
+from __future__ import annotations
+
+import math
+from dataclasses import dataclass, field
+
+import numpy as np
+
+SQRT2 = math.sqrt(2.0)
+
+
+# --------------------------------------------------------------------------- meshes
+@dataclass
+class MeshData:
+    nx: int
+    ny: int
+    elem_xy: np.ndarray      # [n_elem, 3, 2] float64, CCW, periodic images resolved
+    elem_vid: np.ndarray     # [n_elem, 3] int32 topological vertex ids
+    vert_xy: np.ndarray      # [n_vert, 2] jittered positions in [0,1)^2 (mod 1)
+
+    @property
+    def n_elem(self) -> int:
+        return int(self.elem_vid.shape[0])
+
+    @property
+    def h(self) -> float:
+        return 1.0 / max(self.nx, self.ny)
+
+
+def periodic_mesh(nx: int, ny: int, jitter: float, seed: int) -> MeshData:
+    if nx < 3 or ny < 3:
+        raise ValueError("periodic grids need at least 3 cells per direction")
+    rng = np.random.default_rng(seed)
+    hx, hy = 1.0 / nx, 1.0 / ny
+    ii, jj = np.meshgrid(np.arange(nx), np.arange(ny), indexing="xy")  # [ny, nx]
+    jx = rng.uniform(-jitter * hx, jitter * hx, size=(ny, nx)) if jitter > 0 else np.zeros((ny, nx))
+    jy = rng.uniform(-jitter * hy, jitter * hy, size=(ny, nx)) if jitter > 0 else np.zeros((ny, nx))
+    X = ii * hx + jx
+    Y = jj * hy + jy
+    vid = (jj * nx + ii).astype(np.int64)
+
+    def corner(di, dj):
+        i2 = (ii + di) % nx
+        j2 = (jj + dj) % ny
+        x = X[j2, i2] + (ii + di >= nx)
+        y = Y[j2, i2] + (jj + dj >= ny)
+        return np.stack([x, y], -1), vid[j2, i2]
+
+    a, va = corner(0, 0)
+    b, vb = corner(1, 0)
+    c, vc = corner(1, 1)
+    d, vd = corner(0, 1)
+    t1 = np.stack([a, b, c], -2)          # [ny, nx, 3, 2]
+    t2 = np.stack([a, c, d], -2)
+    v1 = np.stack([va, vb, vc], -1)
+    v2 = np.stack([va, vc, vd], -1)
+    elem_xy = np.stack([t1, t2], 2).reshape(-1, 3, 2)
+    elem_vid = np.stack([v1, v2], 2).reshape(-1, 3).astype(np.int32)
+    e = elem_xy
+    det = (e[:, 1, 0] - e[:, 0, 0]) * (e[:, 2, 1] - e[:, 0, 1]) - (e[:, 2, 0] - e[:, 0, 0]) * (e[:, 1, 1] - e[:, 0, 1])
+    if not np.all(det > 0):
+        raise ValueError("jitter produced a non-positive element")
+    vert_xy = np.stack([X.reshape(-1), Y.reshape(-1)], -1)
+    return MeshData(nx, ny, np.ascontiguousarray(elem_xy), elem_vid, vert_xy)
+
+
+def degree_map(n_elem: int, seed: int, p: int | None = None, probs=None) -> np.ndarray:
+    """Uniform degree p, or i.i.d. degrees 1..4 with the given probabilities."""
+    if p is not None:
+        return np.full(n_elem, p, dtype=np.int8)
+    rng = np.random.default_rng(seed)
+    return rng.choice(np.arange(1, 5), size=n_elem, p=probs).astype(np.int8)
+
+
+# --------------------------------------------------------------------------- flow fields
+def free_stream(mach: float, aoa_deg: float, gamma: float = 1.4):
+    a = math.radians(aoa_deg)
+    return 1.0, mach * math.cos(a), mach * math.sin(a), 1.0 / gamma
+
+
+def conserved(rho, u, v, p, gamma=1.4):
+    rho, u, v, p = (np.asarray(t, dtype=np.float64) for t in (rho, u, v, p))
+    return np.stack([rho, rho * u, rho * v, p / (gamma - 1.0) + 0.5 * rho * (u * u + v * v)], -1)
+
+
+class Field:
+    """Analytic periodic primitive field on [0,1)^2."""
+
+    def __init__(self, kind: str, mach: float, aoa: float, seed: int, gamma: float = 1.4, h: float = 1 / 64):
+        self.kind, self.gamma = kind, gamma
+        self.rho0, self.u0, self.v0, self.p0 = free_stream(mach, aoa, gamma)
+        rng = np.random.default_rng(seed)
+        if kind == "bump":
+            self.center = rng.uniform(0.0, 1.0, size=2)
+            self.amp, self.sigma = 0.05, 0.1
+        elif kind == "fourier":
+            ks = [(kx, ky) for kx in range(-2, 3) for ky in range(-2, 3) if (kx, ky) != (0, 0)]
+            self.k = np.array(ks, dtype=np.float64)
+            damp = 0.01 / (1.0 + (self.k ** 2).sum(1))
+            self.amp = damp[:, None] * rng.standard_normal((len(ks), 4))
+            self.phase = rng.uniform(0.0, 2 * math.pi, size=(len(ks), 4))
+        elif kind == "shock":
+            choices = [(1, 0), (2, 1), (3, 1), (1, 1), (2, -1), (3, -1)]
+            self.kvec = np.array(choices[int(rng.integers(len(choices)))], dtype=np.float64)
+            kn = np.linalg.norm(self.kvec)
+            nrm = self.kvec / kn
+            un1 = self.u0 * nrm[0] + self.v0 * nrm[1]
+            ut1 = -self.u0 * nrm[1] + self.v0 * nrm[0]
+            c1 = math.sqrt(gamma * self.p0 / self.rho0)
+            M = un1 / c1
+            if M <= 1.0:
+                raise ValueError("shock band needs a supersonic normal Mach number")
+            g = gamma
+            r = (g + 1) * M * M / ((g - 1) * M * M + 2)          # normal-shock density ratio
+            self.rho1 = self.rho0 * r
+            self.p1 = self.p0 * (1 + 2 * g / (g + 1) * (M * M - 1))
+            un2 = un1 / r
+            self.u1 = un2 * nrm[0] - ut1 * nrm[1]
+            self.v1 = un2 * nrm[1] + ut1 * nrm[0]
+            self.width = 2.0 * h * kn                             # tanh width in phase units
+        elif kind != "uniform":
+            raise ValueError(kind)
+
+    def primitive(self, x, y):
+        x = np.asarray(x, np.float64); y = np.asarray(y, np.float64)
+        rho = np.full_like(x, self.rho0); u = np.full_like(x, self.u0)
+        v = np.full_like(x, self.v0); p = np.full_like(x, self.p0)
+        if self.kind == "bump":
+            dx = (x - self.center[0] + 0.5) % 1.0 - 0.5
+            dy = (y - self.center[1] + 0.5) % 1.0 - 0.5
+            rho = rho + self.amp * np.exp(-(dx * dx + dy * dy) / (2 * self.sigma ** 2))
+        elif self.kind == "fourier":
+            arg = 2 * math.pi * (np.multiply.outer(x, self.k[:, 0]) + np.multiply.outer(y, self.k[:, 1]))
+            pert = [(self.amp[:, c] * np.cos(arg + self.phase[:, c])).sum(-1) for c in range(4)]
+            rho, u, v, p = rho + pert[0], u + pert[1], v + pert[2], p + pert[3]
+        elif self.kind == "shock":
+            th = (self.kvec[0] * x + self.kvec[1] * y) % 1.0
+            chi = 0.5 * (np.tanh((th - 0.25) / self.width) - np.tanh((th - 0.75) / self.width))
+            rho = (1 - chi) * self.rho0 + chi * self.rho1
+            u = (1 - chi) * self.u0 + chi * self.u1
+            v = (1 - chi) * self.v0 + chi * self.v1
+            p = (1 - chi) * self.p0 + chi * self.p1
+        return rho, u, v, p
+
+    def conserved(self, x, y):
+        return conserved(*self.primitive(x, y), gamma=self.gamma)
+
+    @property
+    def w_inf(self):
+        return conserved(self.rho0, self.u0, self.v0, self.p0, self.gamma)
+
+
+def _n_basis(p):
+    return (p + 1) * (p + 2) // 2
+
+
+def element_coeffs(mesh: MeshData, elem_p: np.ndarray, fld: Field, nfield: int, seed: int) -> np.ndarray:
+    """Coefficient vector U (elements in order; per element [fields][modes],
+    Navier-Stokes fields ordered q_x(4), q_y(4), w(4))."""
+    rng = np.random.default_rng(seed)
+    cen = mesh.elem_xy.mean(1) % 1.0
+    wc = fld.conserved(cen[:, 0], cen[:, 1])                  # [n_elem, 4]
+    scale = np.abs(fld.w_inf) + 0.1
+    out = []
+    for p in range(1, 5):
+        idx = np.nonzero(elem_p == p)[0]
+        if idx.size == 0:
+            continue
+        nb = _n_basis(p)
+        m = np.arange(nb)
+        hi = 1e-3 * scale[None, :, None] * rng.standard_normal((idx.size, 4, nb)) / (m + 1)[None, None, :]
+        w = hi.copy()
+        w[:, :, 0] = wc[idx] / SQRT2
+        blocks = [w]
+        if nfield == 12:
+            q = 1e-3 * scale[None, None, :, None] * rng.standard_normal((idx.size, 2, 4, nb)) / (m + 1)
+            q[:, :, :, 0] = 5e-2 * scale[None, None, :] * rng.standard_normal((idx.size, 2, 4))
+            blocks = [q.reshape(idx.size, 8, nb), w]
+        out.append((idx, np.concatenate(blocks, 1).reshape(idx.size, -1)))
+    n_of = np.array([nfield * _n_basis(int(p)) for p in elem_p], dtype=np.int64)
+    off = np.concatenate([[0], np.cumsum(n_of)])
+    U = np.zeros(int(off[-1]))
+    for idx, vals in out:
+        for r, K in enumerate(idx):
+            U[off[K]:off[K + 1]] = vals[r]
+    return U
+
+
+def trace_coeffs(mesh: MeshData, face_vid: np.ndarray, face_p: np.ndarray, fld: Field, seed: int) -> np.ndarray:
+    """Trace vector Lambda (faces in the given order; per face [fields][modes])."""
+    rng = np.random.default_rng(seed)
+    a = mesh.vert_xy[face_vid[:, 0]]
+    b = mesh.vert_xy[face_vid[:, 1]]
+    d = (b - a + 0.5) % 1.0 - 0.5                              # minimal periodic image
+    mid = (a + 0.5 * d) % 1.0
+    wm = fld.conserved(mid[:, 0], mid[:, 1])
+    scale = np.abs(fld.w_inf) + 0.1
+    parts = []
+    for f in range(face_vid.shape[0]):
+        nk = int(face_p[f]) + 1
+        k = np.arange(nk)
+        c = 1e-3 * scale[:, None] * rng.standard_normal((4, nk)) / (k + 1)[None, :]
+        c[:, 0] = wm[f]
+        parts.append(c.reshape(-1))
+    return np.concatenate(parts)
+
+
+def trace_update(lam_len: int, seed: int) -> np.ndarray:
+    return 1e-3 * np.random.default_rng(seed).standard_normal(lam_len)
+
+
+# --------------------------------------------------------------------------- named workloads
+@dataclass
+class Workload:
+    name: str
+    nx: int
+    ny: int
+    jitter: float
+    model: int                 # 0 Euler, 1 NS mixed form
+    p: int | None              # uniform degree, or None for the mix
+    probs: tuple | None
+    field: str
+    mach: float
+    aoa: float
+    reynolds: float = 5000.0
+    prandtl: float = 0.72
+    seed: int = 1234
+    extra: dict = field(default_factory=dict)
+
+    @property
+    def n_elem(self) -> int:
+        return 2 * self.nx * self.ny
+
+    @property
+    def alpha(self) -> float:
+        # free-stream maximal wave speed |v_inf| + c_inf with c_inf = 1
+        return self.mach + 1.0
+
+
+WORKLOADS = {
+    # 256 triangles, Euler p=1, Mach 0.5 / 2 deg + Gaussian density bump
+    "euler_p1_256": Workload("euler_p1_256", 8, 16, 0.0, 0, 1, None, "bump", 0.5, 2.0, seed=11),
+    # 16,384 jittered triangles, Euler p=3, Mach 0.8 / 1.25 deg + Fourier modes
+    "euler_p3_16k": Workload("euler_p3_16k", 64, 128, 0.2, 0, 3, None, "fourier", 0.8, 1.25, seed=22),
+    # 65,536 jittered triangles, NS mixed form, p in {1,2,3,4} at 40/30/20/10 %
+    "ns_mixp_65k": Workload("ns_mixp_65k", 128, 256, 0.2, 1, None, (0.4, 0.3, 0.2, 0.1), "fourier", 0.5, 1.0,
+                            seed=33),
+    # 262,144 jittered triangles, Euler p=3, Mach 1.5 oblique shock band
+    "euler_p3_262k_shock": Workload("euler_p3_262k_shock", 256, 512, 0.2, 0, 3, None, "shock", 1.5, 0.0, seed=44),
+}
+
+
+def small_variant(w: Workload, nx: int, ny: int, **kw) -> Workload:
+    d = dict(w.__dict__)
+    d.update(nx=nx, ny=ny, name=f"{w.name}@{nx}x{ny}")
+    d.update(kw)
+    return Workload(**d)
+
+
+@dataclass
+class Case:
+    wl: Workload
+    mesh: MeshData
+    elem_p: np.ndarray
+    fld: Field
+
+    @property
+    def nfield(self):
+        return 12 if self.wl.model == 1 else 4
+
+
+def make_case(wl: Workload) -> Case:
+    mesh = periodic_mesh(wl.nx, wl.ny, wl.jitter, wl.seed)
+    ep = degree_map(mesh.n_elem, wl.seed + 1, p=wl.p, probs=wl.probs)
+    fld = Field(wl.field, wl.mach, wl.aoa, wl.seed + 2, h=mesh.h)
+    return Case(wl, mesh, ep, fld)
+
+
+def case_state(case: Case, face_vid: np.ndarray, face_p: np.ndarray):
+    """U, Lambda and a trace update for a case, given the face list (lo, hi
+    vertex ids) and face degrees of its mesh."""
+    U = element_coeffs(case.mesh, case.elem_p, case.fld, case.nfield, case.wl.seed + 3)
+    Lam = trace_coeffs(case.mesh, face_vid, face_p, case.fld, case.wl.seed + 4)
+    dLam = trace_update(Lam.size, case.wl.seed + 5)
+    return U, Lam, dLam

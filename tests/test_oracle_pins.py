@@ -1,0 +1,478 @@
+"""Pins of the CPU oracle against facts fixed by the paper and by mathematics
+(closed forms, library routines, invariants, brute force), not against itself.
+
+Each test names what it pins and the passage of arXiv:1308.3995 it follows.
+"""
+import math
+
+import numpy as np
+import pytest
+import scipy.special as sp
+
+import oracle as O
+from paper_1308_3995_gb300 import inputs as G
+
+GAMMA = 1.4
+
+
+# ----------------------------------------------------------------------------- quadrature
+@pytest.mark.parametrize("n,a,b", [(2, 0, 0), (5, 0, 0), (6, 0, 0), (3, 1, 0), (6, 1, 0), (4, 2, 1)])
+def test_gauss_jacobi_matches_library(n, a, b):
+    """Golub-Welsch nodes/weights equal scipy's Gauss-Jacobi rule."""
+    x, w = O.gauss_jacobi(n, a, b)
+    xr, wr = sp.roots_jacobi(n, a, b)
+    assert np.allclose(x, np.sort(xr), atol=2e-15, rtol=0)
+    assert np.allclose(w, wr[np.argsort(xr)], atol=4e-15, rtol=0)
+
+
+@pytest.mark.parametrize("p", [1, 2, 3, 4])
+def test_triangle_rule_monomials(p):
+    """Volume rule integrates xi^a eta^b exactly (a!b!/(a+b+2)!) for a+b <= 2p+3."""
+    xi, eta, w = O.tri_rule(p)
+    assert len(w) == (p + 2) ** 2
+    for a in range(2 * p + 4):
+        for b in range(2 * p + 4 - a):
+            exact = math.factorial(a) * math.factorial(b) / math.factorial(a + b + 2)
+            assert abs((w * xi ** a * eta ** b).sum() - exact) < 2e-16 + 1e-14 * exact
+    # one degree higher is generally not exact (the rule is not over-specified)
+    errs = [abs((w * xi ** a * eta ** (2 * p + 4 - a)).sum()
+                - math.factorial(a) * math.factorial(2 * p + 4 - a) / math.factorial(2 * p + 6))
+            for a in range(2 * p + 5)]
+    assert max(errs) > 1e-12
+
+
+@pytest.mark.parametrize("pe", [1, 2, 3, 4])
+def test_edge_rule_monomials(pe):
+    s, w = O.edge_rule(pe)
+    for k in range(2 * pe + 4):
+        assert abs((w * s ** k).sum() - 1.0 / (k + 1)) < 1e-15
+    assert np.all((s > 0) & (s < 1))
+
+
+# ----------------------------------------------------------------------------- basis
+@pytest.mark.parametrize("p", [1, 2, 3, 4])
+def test_dubiner_orthonormal(p):
+    """Orthonormal Dubiner basis (readings: orthonormal, hierarchical; paper Sec. 4.2 cites Dubiner)."""
+    xi, eta, w = O.tri_rule(p + 1)
+    phi, _, _ = O.dubiner(p, xi, eta)
+    M = phi.T @ (w[:, None] * phi)
+    assert np.abs(M - np.eye(O.n_basis(p))).max() < 2e-14
+
+
+def test_dubiner_closed_forms():
+    """Low modes in the fixed order: sqrt(2), 2 sqrt(3)(2 xi + eta - 1), 2 (3 eta - 1)."""
+    rng = np.random.default_rng(0)
+    xi = rng.uniform(0, 0.5, 20); eta = rng.uniform(0, 0.5, 20)
+    phi, dx, de = O.dubiner(2, xi, eta)
+    assert np.allclose(phi[:, 0], math.sqrt(2), atol=1e-15)
+    assert np.allclose(phi[:, 1], 2 * math.sqrt(3) * (2 * xi + eta - 1), atol=1e-14)
+    assert np.allclose(phi[:, 2], 2 * (3 * eta - 1), atol=1e-14)
+    assert np.allclose(dx[:, 1], 4 * math.sqrt(3), atol=1e-13)
+    assert np.allclose(de[:, 1], 2 * math.sqrt(3), atol=1e-13)
+    assert np.allclose(dx[:, 2], 0, atol=1e-13) and np.allclose(de[:, 2], 6, atol=1e-13)
+
+
+@pytest.mark.parametrize("p", [2, 3, 4])
+def test_dubiner_hierarchical_and_gradients(p):
+    """Degree-p basis restricted to its first n(p-1) modes is the degree-(p-1) basis, spans P^{p-1};
+    gradients match a 4th-order central difference."""
+    rng = np.random.default_rng(p)
+    xi = rng.uniform(0.05, 0.45, 30); eta = rng.uniform(0.05, 0.45, 30)
+    hi, dxh, deh = O.dubiner(p, xi, eta)
+    lo, _, _ = O.dubiner(p - 1, xi, eta)
+    assert np.abs(hi[:, :lo.shape[1]] - lo).max() < 1e-13
+    # every monomial of degree <= p-1 lies in the span of the first n(p-1) modes
+    mon = np.stack([xi ** a * eta ** b for a in range(p) for b in range(p - a)], 1)
+    coef, *_ = np.linalg.lstsq(lo, mon, rcond=None)
+    assert np.abs(lo @ coef - mon).max() < 1e-12
+    h = 1e-3
+    f = lambda a, b: O.dubiner(p, a, b)[0]
+    fdx = (-f(xi + 2 * h, eta) + 8 * f(xi + h, eta) - 8 * f(xi - h, eta) + f(xi - 2 * h, eta)) / (12 * h)
+    fde = (-f(xi, eta + 2 * h) + 8 * f(xi, eta + h) - 8 * f(xi, eta - h) + f(xi, eta - 2 * h)) / (12 * h)
+    assert np.abs(fdx - dxh).max() < 1e-8 * max(1, np.abs(dxh).max())
+    assert np.abs(fde - deh).max() < 1e-8 * max(1, np.abs(deh).max())
+
+
+def test_trace_basis():
+    s, w = O.edge_rule(6)
+    psi = O.legendre01(4, s)
+    assert np.abs(psi.T @ (w[:, None] * psi) - np.eye(5)).max() < 1e-14
+    assert np.allclose(psi[:, 1], math.sqrt(3) * (2 * s - 1), atol=1e-15)
+
+
+# ----------------------------------------------------------------------------- physics
+def _cons(rho, u, v, p):
+    return np.array([rho, rho * u, rho * v, p / (GAMMA - 1) + 0.5 * rho * (u * u + v * v)])
+
+
+def test_euler_flux_closed_form_and_homogeneity():
+    """Sec. 2.1 flux with the momentum entry read as rho v (x) v + p Id; the flux is
+    homogeneous of degree one in w (which the garbled p Id + v (x) v would violate)."""
+    rho, u, v, p = 1.3, 0.4, -0.25, 0.9
+    w = _cons(rho, u, v, p)
+    E = w[3]
+    f = O.euler_flux(w)
+    ref = np.array([[rho * u, rho * u * u + p, rho * u * v, u * (E + p)],
+                    [rho * v, rho * u * v, rho * v * v + p, v * (E + p)]])
+    assert np.allclose(f, ref, rtol=1e-15, atol=1e-15)
+    for lam in (0.5, 2.0, 7.0):
+        assert np.allclose(O.euler_flux(lam * w), lam * f, rtol=1e-14)
+
+
+@pytest.mark.parametrize("M1", [1.2, 2.0, 3.5])
+def test_euler_flux_rankine_hugoniot(M1):
+    """A textbook normal shock (Mach-number relations) carries equal normal flux on both sides."""
+    g = GAMMA
+    rho1, p1 = 1.0, 1.0 / g
+    u1 = M1 * math.sqrt(g * p1 / rho1)
+    r = (g + 1) * M1 ** 2 / ((g - 1) * M1 ** 2 + 2)
+    p2 = p1 * (1 + 2 * g / (g + 1) * (M1 ** 2 - 1))
+    rho2, u2 = rho1 * r, u1 / r
+    th = 0.3  # rotate the shock normal; the tangential velocity is continuous
+    n = np.array([math.cos(th), math.sin(th)]); t = np.array([-n[1], n[0]]); vt = 0.17
+    v1 = u1 * n + vt * t; v2 = u2 * n + vt * t
+    fL = O.euler_flux(_cons(rho1, *v1, p1)); fR = O.euler_flux(_cons(rho2, *v2, p2))
+    assert np.allclose(n @ fL, n @ fR, rtol=1e-13, atol=1e-13)
+    if M1 == 2.0:  # standard normal-shock table, gamma 1.4, M1 = 2
+        assert abs(p2 / p1 - 4.5) < 1e-12 and abs(r - 8.0 / 3.0) < 1e-12
+
+
+def test_euler_flux_jacobian_eigenvalues():
+    """Eigenvalues of d(f.n)/dw are u_n - c, u_n, u_n, u_n + c (c^2 = gamma p / rho)."""
+    rho, u, v, p = 0.8, 0.6, 0.3, 0.55
+    w = _cons(rho, u, v, p)
+    n = np.array([0.6, 0.8])
+    h = 1e-6
+    A = np.zeros((4, 4))
+    for j in range(4):
+        e = np.zeros(4); e[j] = h
+        A[:, j] = (n @ O.euler_flux(w + e) - n @ O.euler_flux(w - e)) / (2 * h)
+    ev = np.sort(np.linalg.eigvals(A).real)
+    un, c = u * n[0] + v * n[1], math.sqrt(GAMMA * p / rho)
+    assert np.allclose(ev, np.sort([un - c, un, un, un + c]), atol=1e-7)
+
+
+def test_ns_viscous_flux_closed_forms():
+    """Sec. 2.2: f_v = (0, tau, tau v + k grad T), Newtonian stress, Sutherland's law with
+    T = gamma p / rho (T_inf = 1 -> mu = mu_inf = Ma/Re), k = mu / ((gamma-1) Pr)."""
+    P = O.Params(model=1, mach=0.5, reynolds=5000.0)
+    mu = P.mach / P.reynolds
+    a = 0.3
+    # simple shear u = a y at y0 (rho = 1, p = 1/gamma -> T = 1), v = 0
+    y0 = 0.4
+    w = _cons(1.0, a * y0, 0.0, 1 / GAMMA)
+    q = np.zeros((2, 4))
+    q[1, 1] = a                     # d(rho u)/dy
+    q[1, 3] = a * a * y0            # dE/dy = rho u du/dy
+    fv = O.ns_viscous_flux(w, q, P)
+    assert np.allclose(fv[0], [0, 0, mu * a, 0], atol=1e-17)
+    assert np.allclose(fv[1], [0, mu * a, 0, mu * a * a * y0], atol=1e-17)
+    # pure dilatation u = a x at x0
+    x0 = 0.2
+    w = _cons(1.0, a * x0, 0.0, 1 / GAMMA)
+    q = np.zeros((2, 4)); q[0, 1] = a; q[0, 3] = a * a * x0
+    fv = O.ns_viscous_flux(w, q, P)
+    assert np.allclose(fv[0], [0, 4 / 3 * mu * a, 0, 4 / 3 * mu * a * a * x0], atol=1e-17)
+    assert np.allclose(fv[1], [0, 0, -2 / 3 * mu * a, 0], atol=1e-17)
+    # heat conduction: fluid at rest, p = 1/gamma, rho(x) with d rho/dx = g -> dT/dx = -gamma p g/rho^2
+    rho, gx = 1.25, 0.2
+    w = _cons(rho, 0, 0, 1 / GAMMA)
+    q = np.zeros((2, 4)); q[0, 0] = gx
+    fv = O.ns_viscous_flux(w, q, P)
+    T = GAMMA * (1 / GAMMA) / rho
+    S = 110.4 / 288.15
+    muT = mu * T ** 1.5 * (1 + S) / (T + S)
+    dT = -gx / rho ** 2
+    assert np.allclose(fv[0], [0, 0, 0, muT / ((GAMMA - 1) * 0.72) * dT], rtol=1e-14, atol=1e-18)
+    assert np.allclose(fv[1], 0, atol=1e-18)
+
+
+# ----------------------------------------------------------------------------- helpers
+def _case(name, nx, ny, **kw):
+    wl = G.small_variant(G.WORKLOADS[name], nx, ny, **kw)
+    c = G.make_case(wl)
+    m = O.Mesh(c.mesh.elem_xy, c.mesh.elem_vid, c.elem_p, c.nfield)
+    P = O.Params(model=wl.model, mach=wl.mach, alpha=wl.alpha, reynolds=wl.reynolds, prandtl=wl.prandtl)
+    return wl, c, m, P
+
+
+def _uniform_state(m, winf):
+    U = np.zeros(m.u_len)
+    for K in range(m.n_elem):
+        nb = O.n_basis(int(m.elem_p[K]))
+        off = m.u_off[K] + (8 * nb if m.nfield == 12 else 0)
+        for f in range(4):
+            U[off + f * nb] = winf[f] / math.sqrt(2)
+    L = np.zeros(m.lam_len)
+    for e in range(m.n_face):
+        nk = m.face_p[e] + 1
+        for f in range(4):
+            L[m.lam_off[e] + f * nk] = winf[f]
+    return U, L
+
+
+# ----------------------------------------------------------------------------- mesh / layout
+def test_mesh_layout_periodic_counts():
+    """Sec. 3.4: n_f = 3N/2 interior faces on a closed (periodic) triangulation, one diagonal and
+    2d = 4 off-diagonal blocks per block row; p_e = max of the two sides (Sec. 3.1)."""
+    wl, c, m, P = _case("ns_mixp_65k", 5, 4, model=0)
+    assert m.n_face == 3 * m.n_elem // 2
+    assert np.all(np.sort(m.k_col, 1) == m.k_col)
+    for f in range(m.n_face):
+        assert f in m.k_col[f]
+        k0, k1 = m.face_el[f]
+        assert k0 < k1
+        assert m.face_p[f] == max(m.elem_p[k0], m.elem_p[k1])
+        assert m.face_vid[f, 0] < m.face_vid[f, 1]
+    assert np.all(np.diff(m.face_vid[:, 0]) >= 0)
+
+
+# ----------------------------------------------------------------------------- residual
+@pytest.mark.parametrize("model", [0, 1])
+def test_free_stream_preservation(model):
+    """Uniform w = lambda (q = 0) on a jittered periodic mesh with mixed degrees gives N = 0
+    (divergence theorem; pins geometry, normals, face orientation, quadrature and p_e = max)."""
+    wl, c, m, P = _case("ns_mixp_65k", 4, 5, model=model)
+    for mach, aoa in ((0.5, 1.0), (1.7, 33.0)):
+        winf = G.conserved(*G.free_stream(mach, aoa))
+        U, L = _uniform_state(m, winf)
+        P.mach = mach
+        ru, rl = m.global_residual(P, U, L)
+        scale = np.abs(O.euler_flux(winf)).max()
+        assert np.abs(ru).max() < 1e-13 * scale
+        assert np.abs(rl).max() < 1e-13 * scale
+
+
+def test_euler_trace_rows_closed_form():
+    """Euler, summed over both sides: N_lambda = alpha <mu, w+ + w- - 2 lambda>_e, because the
+    f_c(lambda).n terms cancel (n- = -n+); and the summed raw lambda-lambda block is
+    -2 alpha |e| I with the orthonormal trace basis."""
+    wl, c, m, P = _case("ns_mixp_65k", 4, 5, model=0)
+    U, L, _ = G.case_state(c, m.face_vid, m.face_p)
+    _, rl = m.global_residual(P, U, L)
+    # independent edge projection: scipy Gauss-Legendre with 12 points
+    xg, wg = sp.roots_legendre(12)
+    s = (xg + 1) / 2; ws = wg / 2
+    blocks = {}
+    for K in range(m.n_elem):
+        blocks[K] = m.element_blocks(P, K, U, L)
+    for f in range(m.n_face):
+        pe = int(m.face_p[f]); nk = pe + 1
+        psi = O.legendre01(pe, s)
+        acc = np.zeros((4, nk))
+        lenf = None
+        for side in range(2):
+            K = int(m.face_el[f, side]); lf = int(m.face_lf[f, side])
+            p = int(m.elem_p[K]); nb = O.n_basis(p)
+            v = m.elem_vid[K]; xy = m.elem_xy[K].reshape(3, 2)
+            flip = v[lf] > v[(lf + 1) % 3]
+            t = 1 - s if flip else s
+            xi, eta = [(t, 0 * t), (1 - t, t), (0 * t, 1 - t)][lf]
+            phi, _, _ = O.dubiner(p, xi, eta)
+            Uw = U[m.u_off[K]:m.u_off[K + 1]].reshape(4, nb)
+            wpt = phi @ Uw.T                                   # [npts, 4]
+            acc += ((psi * ws[:, None]).T @ wpt).T             # projection coefficients [4, nk]
+            lenf = np.linalg.norm(xy[(lf + 1) % 3] - xy[lf])
+            # raw lambda-lambda block of this side
+            A, B, C, D, F, H = blocks[K]
+            off = sum(4 * (m.face_p[e] + 1) for e in m.elem_face[K][:lf])
+            blocks.setdefault(("D", f), np.zeros((4 * nk, 4 * nk)))
+            blocks[("D", f)] += D[off:off + 4 * nk, off:off + 4 * nk]
+        lam = L[m.lam_off[f]:m.lam_off[f + 1]].reshape(4, nk)
+        expect = P.alpha * lenf * (acc - 2 * lam)
+        got = rl[m.lam_off[f]:m.lam_off[f + 1]].reshape(4, nk)
+        assert np.abs(got - expect).max() < 1e-13
+        assert np.abs(blocks[("D", f)] + 2 * P.alpha * lenf * np.eye(4 * nk)).max() < 1e-12
+
+
+def test_conservation_identity():
+    """With phi = 1 and mu = 1 (periodic mesh), sum_K N_w,K(1) = sum_e N_lambda,e(1):
+    both are the sum of all outward face fluxes (the volume term vanishes for a constant test)."""
+    for model in (0, 1):
+        wl, c, m, P = _case("ns_mixp_65k", 4, 3, model=model)
+        U, L, _ = G.case_state(c, m.face_vid, m.face_p)
+        ru, rl = m.global_residual(P, U, L)
+        sw = np.zeros(4); sl = np.zeros(4)
+        for K in range(m.n_elem):
+            nb = O.n_basis(int(m.elem_p[K]))
+            off = m.u_off[K] + (8 * nb if model else 0)
+            sw += ru[off:off + 4 * nb].reshape(4, nb)[:, 0] / math.sqrt(2)
+        for e in range(m.n_face):
+            nk = m.face_p[e] + 1
+            sl += rl[m.lam_off[e]:m.lam_off[e + 1]].reshape(4, nk)[:, 0]
+        assert np.allclose(sw, sl, atol=1e-13)
+
+
+def test_euler_polynomial_state_divergence():
+    """Euler, p = 1, rho = 1 and linear momentum/energy (flux cubic, integrated exactly), lambda the
+    exact edge trace of w: N_w,i = int_K phi_i div f(w) (integration by parts, Sec. 3.2)."""
+    wl, c, m, P = _case("euler_p1_256", 4, 3, jitter=0.2)
+    U = np.zeros(m.u_len); L = np.zeros(m.lam_len)
+    K = 5
+    xy = m.elem_xy[K].reshape(3, 2)
+    x0 = xy[0]; J = np.stack([xy[1] - x0, xy[2] - x0], 1)
+    gm = np.array([[0.0, 0.0], [0.3, -0.2], [0.1, 0.25], [0.4, -0.3]])   # gradients of w
+    w0 = np.array([1.0, 0.35, 0.1, 2.2])
+
+    def wfun(x):  # x [..., 2]
+        return w0 + (x - x0) @ gm.T
+
+    # coefficients by interpolation at 3 points with the oracle basis (pinned above)
+    rxi = np.array([0.1, 0.6, 0.2]); reta = np.array([0.1, 0.2, 0.6])
+    phi, _, _ = O.dubiner(1, rxi, reta)
+    pts = x0 + np.stack([rxi, reta], 1) @ J.T
+    coef = np.linalg.solve(phi, wfun(pts))                 # [3, 4]
+    U[m.u_off[K]:m.u_off[K + 1]] = coef.T.reshape(-1)
+    for lf in range(3):
+        e = m.elem_face[K][lf]
+        v = m.elem_vid[K]
+        a, b = (lf, (lf + 1) % 3) if v[lf] < v[(lf + 1) % 3] else ((lf + 1) % 3, lf)
+        wa, wb = wfun(xy[a]), wfun(xy[b])
+        pe = m.face_p[e]; nk = pe + 1
+        blk = np.zeros((4, nk))
+        blk[:, 0] = 0.5 * (wa + wb)
+        blk[:, 1] = (wb - wa) / (2 * math.sqrt(3))
+        L[m.lam_off[e]:m.lam_off[e + 1]] = blk.reshape(-1)
+    Nu, _ = m.element_residual(P, K, U, L)
+    # reference: int_K phi_i div f(w), scipy Gauss-Jacobi collapsed rule of 8x8 points,
+    # div f by a 5-point stencil (exact for the cubic flux up to rounding)
+    xa, wa_ = sp.roots_legendre(8); xb, wb_ = sp.roots_jacobi(8, 1, 0)
+    A_, B_ = np.meshgrid(xa, xb, indexing="ij")
+    xi = ((1 + A_) * (1 - B_) / 4).ravel(); eta = ((1 + B_) / 2).ravel()
+    wq = (np.outer(wa_, wb_) / 8).ravel() * np.linalg.det(J)
+    X = x0 + np.stack([xi, eta], 1) @ J.T
+    h = 1e-2
+
+    def flux_at(Xp):
+        return np.array([O.euler_flux(wfun(xp)) for xp in Xp])  # [n, 2, 4]
+
+    div = np.zeros((X.shape[0], 4))
+    for k in range(2):
+        e = np.zeros(2); e[k] = h
+        d = (-flux_at(X + 2 * e) + 8 * flux_at(X + e) - 8 * flux_at(X - e) + flux_at(X - 2 * e)) / (12 * h)
+        div += d[:, k, :]
+    phq, _, _ = O.dubiner(1, xi, eta)
+    ref = (phq * wq[:, None]).T @ div                      # [3, 4]
+    assert np.abs(Nu.reshape(4, 3) - ref.T).max() < 1e-11
+
+
+# ----------------------------------------------------------------------------- Jacobian
+@pytest.mark.parametrize("model", [0, 1])
+def test_jacobian_vs_central_differences(model):
+    """The complex-step Newton matrix blocks agree with central finite differences of the residual."""
+    wl, c, m, P = _case("ns_mixp_65k", 3, 4, model=model)
+    U, L, _ = G.case_state(c, m.face_vid, m.face_p)
+    rng = np.random.default_rng(7)
+    for K in rng.choice(m.n_elem, 3, replace=False):
+        A, B, C, D, F, H = m.element_blocks(P, K, U, L)
+        n, nt = A.shape[0], D.shape[0]
+        Kfaces = m.elem_face[K]
+        cols = list(range(n)) + list(range(n, n + nt))
+        for col in rng.choice(cols, 6, replace=False):
+            h = 1e-6
+            Up, Um, Lp, Lm = U.copy(), U.copy(), L.copy(), L.copy()
+            if col < n:
+                Up[m.u_off[K] + col] += h; Um[m.u_off[K] + col] -= h
+            else:
+                t = col - n; lf = 0
+                while t >= 4 * (m.face_p[Kfaces[lf]] + 1):
+                    t -= 4 * (m.face_p[Kfaces[lf]] + 1); lf += 1
+                Lp[m.lam_off[Kfaces[lf]] + t] += h; Lm[m.lam_off[Kfaces[lf]] + t] -= h
+            nup, nlp = m.element_residual(P, K, Up, Lp)
+            num, nlm = m.element_residual(P, K, Um, Lm)
+            du = (nup - num) / (2 * h); dl = (nlp - nlm) / (2 * h)
+            ju = A[:, col] if col < n else B[:, col - n]
+            jl = C[:, col] if col < n else D[:, col - n]
+            sc = max(1.0, np.abs(ju).max(), np.abs(jl).max())
+            assert np.abs(du - ju).max() < 1e-7 * sc
+            assert np.abs(dl - jl).max() < 1e-7 * sc
+
+
+def test_ns_q_equation_blocks():
+    """Mixed form (Eq. strmixed / hdg_ls1): dN_q/dQ is the element mass matrix det(J) I for the
+    orthonormal basis on an affine element, and dN_q/dW = (d_k phi_i, phi_j) delta_fg."""
+    wl, c, m, P = _case("ns_mixp_65k", 3, 3, model=1)
+    U, L, _ = G.case_state(c, m.face_vid, m.face_p)
+    for K in (0, 3, 7):
+        A, *_ = m.element_blocks(P, K, U, L)
+        p = int(m.elem_p[K]); nb = O.n_basis(p)
+        xy = m.elem_xy[K].reshape(3, 2)
+        J = np.stack([xy[1] - xy[0], xy[2] - xy[0]], 1); det = np.linalg.det(J)
+        assert np.abs(A[:8 * nb, :8 * nb] - det * np.eye(8 * nb)).max() < 1e-14 * det * 10
+        xi, eta, w = O.tri_rule(p)
+        phi, dxi, deta = O.dubiner(p, xi, eta)
+        Ji = np.linalg.inv(J)
+        for k in range(2):
+            gk = dxi * Ji[0, k] + deta * Ji[1, k]
+            Dk = det * (gk * w[:, None]).T @ phi
+            for f in range(4):
+                blk = A[(k * 4 + f) * nb:(k * 4 + f + 1) * nb, (8 + f) * nb:(9 + f) * nb]
+                assert np.abs(blk - Dk).max() < 1e-13
+                other = A[(k * 4 + f) * nb:(k * 4 + f + 1) * nb, 8 * nb:]
+                assert np.abs(other).sum() - np.abs(blk).sum() < 1e-12
+
+
+def test_euler_C_block_is_alpha_edge_mass():
+    """Euler: dN_lambda/dW = alpha <psi_k, phi_j>_e delta_fg (only the stabilisation depends on w)."""
+    wl, c, m, P = _case("euler_p1_256", 3, 4, jitter=0.2, p=2)
+    U, L, _ = G.case_state(c, m.face_vid, m.face_p)
+    K = 4
+    A, B, C, D, F, H = m.element_blocks(P, K, U, L)
+    xg, wg = sp.roots_legendre(10); s = (xg + 1) / 2; ws = wg / 2
+    xy = m.elem_xy[K].reshape(3, 2); v = m.elem_vid[K]
+    r0 = 0
+    for lf in range(3):
+        e = m.elem_face[K][lf]; nk = m.face_p[e] + 1
+        t = 1 - s if v[lf] > v[(lf + 1) % 3] else s
+        xi, eta = [(t, 0 * t), (1 - t, t), (0 * t, 1 - t)][lf]
+        phi, _, _ = O.dubiner(2, xi, eta)
+        psi = O.legendre01(int(m.face_p[e]), s)
+        ln = np.linalg.norm(xy[(lf + 1) % 3] - xy[lf])
+        Me = P.alpha * ln * (psi * ws[:, None]).T @ phi
+        ref = np.kron(np.eye(4), Me)
+        assert np.abs(C[r0:r0 + 4 * nk] - ref).max() < 1e-13
+        r0 += 4 * nk
+
+
+# ----------------------------------------------------------------------------- condensation
+@pytest.mark.parametrize("name,nx,ny,model", [("ns_mixp_65k", 4, 5, 0), ("euler_p3_16k", 3, 4, 0),
+                                              ("ns_mixp_65k", 3, 3, 1)])
+def test_condensed_then_recovered_equals_monolithic(name, nx, ny, model):
+    """Sec. 3.4: solving K dLambda = E and reconstructing (dQ, dW) by Eq. (ls) reproduces the
+    monolithic solve of the full linearised system (Jacobian of the global residual by complex
+    step on every global unknown; finite CFL makes the periodic system nonsingular)."""
+    wl, c, m, P = _case(name, nx, ny, model=model)
+    U, L, _ = G.case_state(c, m.face_vid, m.face_p)
+    P.cfl = 10.0
+    if m.u_len + m.lam_len > 4000:
+        pytest.skip("too large for the dense monolithic solve")
+    dU, dL = m.monolithic(P, U, L)
+    r = m.condense(P, U, L)
+    assert r["status"].max() == 0
+    dLc = O.dense_solve(m.dense_K(r["K"]), r["E"])
+    dUc = m.recover(r["X"], dLc)
+    assert np.abs(dLc - dL).max() < 1e-11 * np.abs(dL).max()
+    assert np.abs(dUc - dU).max() < 1e-11 * np.abs(dU).max()
+    # the stored local solves satisfy A X = [B | F] to rounding
+    K = 1
+    A, B, C, D, F, H = m.element_blocks(P, K, U, L)
+    nr = B.shape[1] + 1
+    XK = r["X"][m.x_off[K]:m.x_off[K + 1]].reshape(-1, nr)
+    R = A @ XK - np.concatenate([B, F[:, None]], 1)
+    assert np.abs(R).max() < 1e-12 * np.abs(A).max() * np.abs(XK).max()
+
+
+def test_periodic_pure_newton_row_dependence():
+    """Periodic mesh with dt = infinity: the phi = 1 rows summed equal the mu = 1 trace rows summed,
+    so the global Jacobian is singular (the reason the global tests use a finite CFL)."""
+    wl, c, m, P = _case("euler_p1_256", 3, 3, jitter=0.2)
+    U, L, _ = G.case_state(c, m.face_vid, m.face_p)
+    J0 = m.global_jacobian(P, U, L)
+    nb = O.n_basis(1)
+    for f in range(4):
+        rows_w = [m.u_off[K] + f * nb for K in range(m.n_elem)]
+        rows_l = [m.u_len + m.lam_off[e] + f * 2 for e in range(m.n_face)]
+        sw = J0[rows_w].sum(0) / math.sqrt(2)
+        sl = J0[rows_l].sum(0)
+        assert np.abs(sw - sl).max() < 1e-12 * np.abs(J0).max()
+    assert np.linalg.matrix_rank(J0) <= J0.shape[0] - 4
