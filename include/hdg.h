@@ -1,0 +1,204 @@
+/*
+ * hdg.h -- C ABI of the GB300 (sm_103a) hot path of one hybridized-DG (HDG)
+ * Newton step for steady 2D compressible Euler and mixed-form Navier-Stokes
+ * flow, after Woopen, Balan, May, Schuetz, "A comparison of hybridized and
+ * standard DG methods for target-based hp-adaptive simulation of compressible
+ * flow" (arXiv:1308.3995).
+ *
+ * The problem statement (mesh + per-element degree p + state in; condensed
+ * trace system and reconstructed update out) is Sec. 3.4 of the paper:
+ *   the linearised system [A B R; C D S; L M N][dQ; dW; dLambda] = [F; G; H]
+ *   (Eq. linearsystem in block form) is reduced element by element to
+ *   K dLambda = E (Eq. hybridsystem) with
+ *   K = N - [L M][A B; C D]^{-1}[R; S],  E = H - [L M][A B; C D]^{-1}[F; G],
+ *   the local solves [A B; C D]^{-1}[R S F G] are stored, and (dQ, dW) is
+ *   reconstructed from dLambda by Eq. (ls).
+ * In this header, per element K: A_K = local interior block [A B; C D]
+ * restricted to K, B_K = [R; S] (interior rows, trace columns of K's three
+ * faces), C_K = [L M] (trace rows, interior columns), D_K = N (trace-trace),
+ * F_K = -residual of the interior rows, H_K = -element share of the trace rows.
+ *
+ * Discretisation (fixed; identical in every call):
+ *   - Triangles with vertices given counter-clockwise; affine map
+ *     x = x0 + J xi from the reference triangle (0,0),(1,0),(0,1).
+ *   - Interior basis: orthonormal Dubiner basis on the reference triangle,
+ *     n_p = (p+1)(p+2)/2 modes ordered k = 0..p, j = 0..k, i = k-j.
+ *   - Faces: local face l of an element runs from local vertex l to l+1 (mod 3).
+ *     A global face is an unordered pair of topological vertex ids; faces are
+ *     numbered by ascending (lo id, hi id).  Its trace lives in the orthonormal
+ *     Legendre basis psi_k(s) = sqrt(2k+1) P_k(2s-1), k = 0..p_e, with the
+ *     edge parameter s running from the lower to the higher vertex id, and
+ *     p_e = max(p of both sides) (Sec. 3.1).  Side 0 of a face is the element
+ *     with the lower id.  Only closed (periodic) meshes: every face has two sides.
+ *   - Quadrature: collapsed Gauss (p+2) x (p+2) on elements, (p_e+2)-point
+ *     Gauss-Legendre on edges.
+ *   - Numerical flux (Sec. 3.2): (f_c(lambda) - f_v(lambda, q)).n - alpha (lambda - w),
+ *     with the jump of Eq. (hdg_cont) read as the sum over both sides.
+ *
+ * Layouts (all FP64, little-endian, contiguous):
+ *   U      element K at u_off[K]: n_K = nfield * n_p(p_K) values, fields
+ *          major, modes minor.  Euler: nfield = 4, fields (rho, rho u, rho v, E).
+ *          Navier-Stokes: nfield = 12, fields q_x(4), q_y(4), w(4) with
+ *          q = grad w of the conserved variables (Eq. strmixed).
+ *   Lambda face e at lam_off[e]: 4 (p_e+1) values, [field][mode].
+ *   X      element K at x_off[K]: the n_K x (nt_K + 1) matrix X = A_K^{-1}[B_K | F_K]
+ *          (the stored local solves of Sec. 3.4) in COLUMN-major order: entry
+ *          (r, c) at x_off[K] + c n_K + r, column nt_K being X_F; nt_K = sum over
+ *          K's faces in local order of 4 (p_e+1).
+ *   K      block-sparse trace matrix: block row e has 5 blocks (itself and the
+ *          other two faces of each neighbour, Sec. 3.4 last paragraph), column
+ *          face ids ascending in k_col[5e .. 5e+4]; block b of row e starts at
+ *          k_blkoff[5e+b] (in doubles) and is 4(p_e+1) x 4(p_col+1) row-major.
+ *   E      layout of Lambda.
+ *
+ * Conventions:
+ *   - Every call returns an hdg_status; hdg_last_error() gives the text of the
+ *     last failure on that context.
+ *   - Calls taking a `stream` (a cudaStream_t, e.g. torch's current stream) are
+ *     asynchronous: results are valid after that stream is synchronised.
+ *   - Pointers documented "device" must be device memory of the context's
+ *     device, 8-byte aligned; "host" pointers are read before the call returns
+ *     unless stated otherwise.  The library never frees caller memory; objects
+ *     it creates are freed by the matching destroy call.
+ *   - A context is used from one host thread at a time.  Calls on different
+ *     systems may run on different streams concurrently.
+ */
+#ifndef HDG_H_
+#define HDG_H_
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct hdg_ctx hdg_ctx;
+typedef struct hdg_mesh hdg_mesh;
+typedef struct hdg_sys hdg_sys;
+
+typedef enum {
+  HDG_OK = 0,
+  HDG_EINVAL = 1,     /* bad argument, layout or mesh */
+  HDG_ENOMEM = 2,     /* device allocation failed or footprint over the limit */
+  HDG_ECUDA = 3,      /* a CUDA runtime call failed */
+  HDG_ESINGULAR = 4,  /* some element's local block had a zero pivot (see elem_status) */
+  HDG_ETIMEOUT = 5,   /* a bounded device wait ran out */
+  HDG_ENOTSUP = 6     /* combination not supported by this build */
+} hdg_status;
+
+typedef enum { HDG_EULER = 0, HDG_NS_MIXED = 1 } hdg_model;
+
+typedef enum {
+  HDG_FP64 = 0,        /* everything in IEEE binary64 */
+  HDG_MIXED_FP32 = 1   /* local LU / solves / Schur in binary32, refined to FP64 accuracy */
+} hdg_precision;
+
+/* Flow and discretisation parameters (paper Sec. 2 and 3).  Non-dimensional
+ * with rho_inf = 1, c_inf = 1, L = 1: p_inf = 1/gamma, |v_inf| = mach,
+ * T = gamma p / rho, mu = (mach/reynolds) T^{3/2} (1+S)/(T+S), S = 110.4/t_inf,
+ * heat conductivity mu / ((gamma-1) prandtl). */
+typedef struct {
+  int32_t model;       /* hdg_model */
+  int32_t precision;   /* hdg_precision */
+  double gamma;        /* ratio of specific heats, Sec. 2.1 (1.4) */
+  double prandtl;      /* Sec. 2.2 (0.72) */
+  double reynolds;     /* Sec. 2.2 */
+  double mach;         /* free-stream Mach number */
+  double alpha;        /* constant scalar stabilisation alpha = alpha_c + alpha_v, Sec. 3.2 */
+  double cfl;          /* <= 0: pure Newton; > 0: pseudo-time mass |K|-scaled by the local
+                          time step CFL |K| / (lambda_c + 4 lambda_v) of Sec. 3.3 */
+  double t_inf;        /* dimensional free-stream temperature [K] for Sutherland (288.15) */
+  double refine_tol;   /* mixed precision: stop refining when the FP64 residual of the local
+                          solves is below refine_tol * |[B|F]| (e.g. 1e-13) */
+  int32_t refine_max;  /* mixed precision: at most this many refinement sweeps */
+  int32_t reserved;
+} hdg_params;
+
+/* Create a context on CUDA device `device` (makes it current on this thread). */
+hdg_status hdg_create(hdg_ctx** out, int device);
+hdg_status hdg_destroy(hdg_ctx* ctx);
+/* Text of the last error on ctx (never NULL; empty if none). */
+const char* hdg_last_error(const hdg_ctx* ctx);
+
+/* Build a device-resident mesh plan (faces, sides, degree buckets, layouts,
+ * basis/quadrature tables).  All pointers are HOST arrays, copied:
+ *   elem_xy  [n_elem][3][2] vertex coordinates, counter-clockwise, periodic
+ *            images already resolved so each element is a proper triangle;
+ *   elem_vid [n_elem][3]    topological vertex ids (periodic images identified);
+ *   elem_p   [n_elem]       degree p_K in 1..4.
+ * nfield = 4 (Euler) or 12 (Navier-Stokes mixed form).
+ * Fails with HDG_EINVAL if det J <= 0, p out of range, a face is not shared by
+ * exactly two distinct elements, or two elements share two faces. */
+hdg_status hdg_mesh_create(hdg_ctx* ctx, int32_t n_elem, int32_t nfield, const double* elem_xy,
+                           const int32_t* elem_vid, const int8_t* elem_p, hdg_mesh** out);
+hdg_status hdg_mesh_destroy(hdg_mesh* mesh);
+
+/* sizes[7] = {n_elem, n_face, u_len, lam_len, x_len, k_len, max_nt} */
+hdg_status hdg_mesh_sizes(const hdg_mesh* mesh, int64_t* sizes);
+
+/* Layout arrays into HOST buffers (each may be NULL):
+ * face_vid[n_face][2] (lo, hi), face_el[n_face][2] (side 0, side 1 element),
+ * face_p[n_face], elem_face[n_elem][3], u_off[n_elem+1], lam_off[n_face+1],
+ * x_off[n_elem+1], k_col[5 n_face], k_blkoff[5 n_face + 1]. */
+hdg_status hdg_mesh_layout(const hdg_mesh* mesh, int32_t* face_vid, int32_t* face_el, int32_t* face_p,
+                           int32_t* elem_face, int64_t* u_off, int64_t* lam_off, int64_t* x_off,
+                           int32_t* k_col, int64_t* k_blkoff);
+
+/* Device bytes a system on this mesh holds (X, K, E, residuals, status,
+ * work space), for admission control.  Returns -1 on bad arguments. */
+int64_t hdg_footprint_bytes(const hdg_mesh* mesh, const hdg_params* params);
+
+/* Allocate a system (X, K, E, residuals, per-element status, work space) on
+ * the mesh's device.  params->model must match the mesh's nfield. */
+hdg_status hdg_sys_create(hdg_ctx* ctx, const hdg_mesh* mesh, const hdg_params* params, hdg_sys** out);
+hdg_status hdg_sys_destroy(hdg_sys* sys);
+
+/* One Newton step's element work (Sec. 3.4, paper's Eqs. hdg_ls1-hdg_cont,
+ * linearsystem, ls, hybridsystem), enqueued on `stream`:
+ *   residual and Jacobian blocks of every element by quadrature, LU of A_K
+ *   with partial pivoting, X_K = A_K^{-1}[B_K | F_K], S_K = D_K - C_K X_B,
+ *   E_K = H_K - C_K X_F, assembly K = sum_K P^T S_K P, E = sum_K P^T E_K.
+ * U [u_len] and Lam [lam_len] are DEVICE pointers in the layouts above.
+ * Outputs stay in `sys` (see hdg_sys_get).  Every diagonal block of K and
+ * every entry of E / res_lam is the sum of exactly two element contributions,
+ * so results are bitwise reproducible.  elem_status[K] is set to 0 (ok),
+ * 1 (zero pivot) or 2 (non-finite result). */
+hdg_status hdg_condense(hdg_sys* sys, const double* U, const double* Lam, void* stream);
+
+/* Reconstruction, Eq. (ls): dU_K = X_F - X_B dLambda_K for every element,
+ * from the local solves stored by the last hdg_condense on this system.
+ * dLam [lam_len] and dU [u_len] are DEVICE pointers. */
+hdg_status hdg_recover(hdg_sys* sys, const double* dLam, double* dU, void* stream);
+
+/* Whole step from HOST buffers: copies U, Lam, dLam host->device, runs
+ * hdg_condense and hdg_recover, and copies dU device->host, all on `stream`;
+ * returns after the stream has synchronised.  Host buffers should be pinned
+ * for full copy bandwidth.  dLam stands in for the trace update of the global
+ * solve, which is outside this library. */
+hdg_status hdg_step_host(hdg_sys* sys, const double* U, const double* Lam, const double* dLam, double* dU,
+                         void* stream);
+
+/* Device views of the outputs (owned by sys, valid until hdg_sys_destroy):
+ * X [x_len], K_vals [k_len], E [lam_len], res_u [u_len] = interior residual
+ * [N_q; N_w] per element, res_lam [lam_len] = trace residual summed over both
+ * sides, elem_status [n_elem].  Any pointer may be NULL. */
+hdg_status hdg_sys_get(const hdg_sys* sys, double** X, double** K_vals, double** E, double** res_u,
+                       double** res_lam, int32_t** elem_status);
+
+/* Number of kernel launches the last hdg_condense + hdg_recover enqueued. */
+int32_t hdg_sys_launches(const hdg_sys* sys);
+
+/* Diagnostic, host only (no device needed): copy one of the library's own
+ * quadrature/basis tables into out[cap]; returns its length or -1.
+ * which: 0 volume weights [(p+2)^2], 1 basis values, 2 d/dxi, 3 d/deta
+ * [(p+2)^2][n_p] at the volume points (xi-major collapsed ordering), 4 edge
+ * points s, 5 edge weights [p_e+2], 6 trace basis [p_e+2][p_e+1], 7 basis of
+ * degree p on local face lf at the edge points, flip = 1 if the face runs
+ * from the higher to the lower vertex id [p_e+2][n_p]. */
+int hdg_debug_tables(int which, int p, int pe, int lf, int flip, double* out, int cap);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif  // HDG_H_

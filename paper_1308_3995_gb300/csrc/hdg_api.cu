@@ -1,0 +1,441 @@
+// C ABI of the HDG hot path (declared in include/hdg.h): contexts, mesh
+// planning (faces, sides, layouts, degree buckets), system allocation and the
+// enqueue calls.  Host planning is O(n log n) in the element count and is
+// done once per mesh; every per-step call only enqueues kernels.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "hdg_internal.h"
+
+using namespace hdg;
+
+struct hdg_ctx {
+  int device = 0;
+  std::string err;
+  Tables tab;
+  double* d_tab = nullptr;
+};
+
+struct hdg_mesh {
+  hdg_ctx* ctx = nullptr;
+  int n_elem = 0, n_face = 0, nfield = 4, max_nt = 0;
+  int64_t u_len = 0, lam_len = 0, x_len = 0, k_len = 0, dh_len = 0;
+  std::vector<int> face_lo, face_hi, face_el0, face_el1, face_p, elem_face, k_col;
+  std::vector<int64_t> u_off, lam_off, x_off, k_blkoff;
+  std::vector<void*> allocs;
+  int* d_bucket[kMaxP + 1] = {};
+  int bucket_n[kMaxP + 1] = {};
+  int bucket_ntmax[kMaxP + 1] = {};
+  DevMesh dm{};
+};
+
+struct hdg_sys {
+  hdg_ctx* ctx = nullptr;
+  const hdg_mesh* mesh = nullptr;
+  hdg_params prm{};
+  Phys ph{};
+  DevSys ds{};
+  double *d_U = nullptr, *d_Lam = nullptr, *d_dLam = nullptr, *d_dU = nullptr;
+  std::vector<void*> allocs;
+  int launches = 0;
+};
+
+namespace {
+
+hdg_status fail(hdg_ctx* ctx, hdg_status st, const std::string& msg) {
+  if (ctx) ctx->err = msg;
+  return st;
+}
+
+#define HDG_CK(ctx, call)                                                                  \
+  do {                                                                                     \
+    cudaError_t e_ = (call);                                                               \
+    if (e_ != cudaSuccess) return fail(ctx, HDG_ECUDA, std::string(#call) + ": " + cudaGetErrorString(e_)); \
+  } while (0)
+
+template <class T>
+hdg_status upload(hdg_ctx* ctx, std::vector<void*>& allocs, const std::vector<T>& h, T** d) {
+  void* p = nullptr;
+  size_t bytes = std::max<size_t>(sizeof(T) * h.size(), 16);
+  cudaError_t e = cudaMalloc(&p, bytes);
+  if (e != cudaSuccess) return fail(ctx, HDG_ENOMEM, std::string("cudaMalloc: ") + cudaGetErrorString(e));
+  allocs.push_back(p);
+  if (!h.empty()) HDG_CK(ctx, cudaMemcpy(p, h.data(), sizeof(T) * h.size(), cudaMemcpyHostToDevice));
+  *d = (T*)p;
+  return HDG_OK;
+}
+
+hdg_status dalloc(hdg_ctx* ctx, std::vector<void*>& allocs, size_t bytes, void** d) {
+  void* p = nullptr;
+  cudaError_t e = cudaMalloc(&p, std::max<size_t>(bytes, 16));
+  if (e != cudaSuccess) return fail(ctx, HDG_ENOMEM, std::string("cudaMalloc: ") + cudaGetErrorString(e));
+  allocs.push_back(p);
+  *d = p;
+  return HDG_OK;
+}
+
+void free_all(std::vector<void*>& allocs) {
+  for (void* p : allocs) cudaFree(p);
+  allocs.clear();
+}
+
+int elem_nt(const hdg_mesh* M, int K) {
+  int nt = 0;
+  for (int a = 0; a < 3; ++a) nt += 4 * (M->face_p[M->elem_face[3 * K + a]] + 1);
+  return nt;
+}
+
+}  // namespace
+
+extern "C" {
+
+hdg_status hdg_create(hdg_ctx** out, int device) {
+  if (!out) return HDG_EINVAL;
+  *out = nullptr;
+  hdg_ctx* ctx = new hdg_ctx();
+  ctx->device = device;
+  cudaError_t e = cudaSetDevice(device);
+  if (e != cudaSuccess) { delete ctx; return HDG_ECUDA; }
+  build_tables(ctx->tab);
+  e = cudaMalloc(&ctx->d_tab, sizeof(double) * ctx->tab.data.size());
+  if (e != cudaSuccess) { delete ctx; return HDG_ENOMEM; }
+  e = cudaMemcpy(ctx->d_tab, ctx->tab.data.data(), sizeof(double) * ctx->tab.data.size(), cudaMemcpyHostToDevice);
+  if (e != cudaSuccess) { cudaFree(ctx->d_tab); delete ctx; return HDG_ECUDA; }
+  *out = ctx;
+  return HDG_OK;
+}
+
+hdg_status hdg_destroy(hdg_ctx* ctx) {
+  if (!ctx) return HDG_EINVAL;
+  cudaSetDevice(ctx->device);
+  cudaFree(ctx->d_tab);
+  delete ctx;
+  return HDG_OK;
+}
+
+const char* hdg_last_error(const hdg_ctx* ctx) { return ctx ? ctx->err.c_str() : "null context"; }
+
+hdg_status hdg_mesh_create(hdg_ctx* ctx, int32_t n_elem, int32_t nfield, const double* elem_xy,
+                           const int32_t* elem_vid, const int8_t* elem_p, hdg_mesh** out) {
+  if (!ctx || !out) return HDG_EINVAL;
+  *out = nullptr;
+  if (n_elem < 1 || (nfield != 4 && nfield != 12) || !elem_xy || !elem_vid || !elem_p)
+    return fail(ctx, HDG_EINVAL, "hdg_mesh_create: bad arguments");
+  if (cudaSetDevice(ctx->device) != cudaSuccess) return fail(ctx, HDG_ECUDA, "cudaSetDevice failed");
+  hdg_mesh* M = new hdg_mesh();
+  M->ctx = ctx;
+  M->n_elem = n_elem;
+  M->nfield = nfield;
+  std::vector<double> xy(elem_xy, elem_xy + 6 * (size_t)n_elem);
+  for (int K = 0; K < n_elem; ++K) {
+    const double* c = &xy[6 * (size_t)K];
+    const double det = (c[2] - c[0]) * (c[5] - c[1]) - (c[4] - c[0]) * (c[3] - c[1]);
+    if (elem_p[K] < 1 || elem_p[K] > kMaxP || !(det > 0.0)) {
+      delete M;
+      return fail(ctx, HDG_EINVAL, "hdg_mesh_create: element " + std::to_string(K) +
+                                       " has p outside 1..4 or a non-positive Jacobian");
+    }
+  }
+  // faces: unordered vertex pairs, numbered by ascending (lo, hi); side 0 = lower element id
+  struct Ent { int lo, hi, K, l; };
+  std::vector<Ent> ents;
+  ents.reserve(3 * (size_t)n_elem);
+  for (int K = 0; K < n_elem; ++K)
+    for (int l = 0; l < 3; ++l) {
+      const int a = elem_vid[3 * K + l], b = elem_vid[3 * K + (l + 1) % 3];
+      ents.push_back({std::min(a, b), std::max(a, b), K, l});
+    }
+  std::sort(ents.begin(), ents.end(), [](const Ent& x, const Ent& y) {
+    return x.lo != y.lo ? x.lo < y.lo : (x.hi != y.hi ? x.hi < y.hi : x.K < y.K);
+  });
+  M->elem_face.assign(3 * (size_t)n_elem, -1);
+  std::vector<uint8_t> info(n_elem, 0);
+  for (size_t i = 0; i < ents.size(); i += 2) {
+    const bool ok = i + 1 < ents.size() && ents[i + 1].lo == ents[i].lo && ents[i + 1].hi == ents[i].hi &&
+                    ents[i + 1].K != ents[i].K &&
+                    !(i + 2 < ents.size() && ents[i + 2].lo == ents[i].lo && ents[i + 2].hi == ents[i].hi);
+    if (!ok) {
+      delete M;
+      return fail(ctx, HDG_EINVAL, "hdg_mesh_create: a face is not shared by exactly two elements "
+                                   "(only closed/periodic meshes are supported)");
+    }
+    const int f = M->n_face++;
+    M->face_lo.push_back(ents[i].lo);
+    M->face_hi.push_back(ents[i].hi);
+    M->face_el0.push_back(ents[i].K);
+    M->face_el1.push_back(ents[i + 1].K);
+    M->face_p.push_back(std::max<int>(elem_p[ents[i].K], elem_p[ents[i + 1].K]));
+    M->elem_face[3 * (size_t)ents[i].K + ents[i].l] = f;
+    M->elem_face[3 * (size_t)ents[i + 1].K + ents[i + 1].l] = f;
+    info[ents[i + 1].K] |= (uint8_t)(1u << (3 + ents[i + 1].l));
+  }
+  for (int K = 0; K < n_elem; ++K)
+    for (int l = 0; l < 3; ++l)
+      if (elem_vid[3 * K + l] > elem_vid[3 * K + (l + 1) % 3]) info[K] |= (uint8_t)(1u << l);
+  // layouts
+  M->u_off.assign(n_elem + 1, 0);
+  M->x_off.assign(n_elem + 1, 0);
+  for (int K = 0; K < n_elem; ++K) {
+    const int n = nfield * n_basis(elem_p[K]), nt = elem_nt(M, K);
+    M->u_off[K + 1] = M->u_off[K] + n;
+    M->x_off[K + 1] = M->x_off[K] + (int64_t)n * (nt + 1);
+    M->max_nt = std::max(M->max_nt, nt);
+  }
+  M->u_len = M->u_off[n_elem];
+  M->x_len = M->x_off[n_elem];
+  M->lam_off.assign(M->n_face + 1, 0);
+  std::vector<int64_t> dblk(M->n_face, 0);
+  for (int f = 0; f < M->n_face; ++f) {
+    const int m4 = 4 * (M->face_p[f] + 1);
+    M->lam_off[f + 1] = M->lam_off[f] + m4;
+    dblk[f] = M->dh_len;
+    M->dh_len += (int64_t)m4 * m4;
+  }
+  M->lam_len = M->lam_off[M->n_face];
+  M->k_col.assign(5 * (size_t)M->n_face, 0);
+  M->k_blkoff.assign(5 * (size_t)M->n_face + 1, 0);
+  for (int f = 0; f < M->n_face; ++f) {
+    int cols[5], nc = 0;
+    cols[nc++] = f;
+    for (int sd = 0; sd < 2; ++sd) {
+      const int K = sd ? M->face_el1[f] : M->face_el0[f];
+      for (int l = 0; l < 3; ++l) {
+        const int e = M->elem_face[3 * (size_t)K + l];
+        if (e != f) cols[nc++] = e;
+      }
+    }
+    std::sort(cols, cols + 5);
+    for (int b = 1; b < 5; ++b)
+      if (cols[b] == cols[b - 1]) {
+        delete M;
+        return fail(ctx, HDG_EINVAL, "hdg_mesh_create: two elements share two faces");
+      }
+    for (int b = 0; b < 5; ++b) {
+      M->k_col[5 * (size_t)f + b] = cols[b];
+      M->k_blkoff[5 * (size_t)f + b + 1] =
+          M->k_blkoff[5 * (size_t)f + b] + (int64_t)(4 * (M->face_p[f] + 1)) * (4 * (M->face_p[cols[b]] + 1));
+    }
+  }
+  M->k_len = M->k_blkoff[5 * (size_t)M->n_face];
+  std::vector<int64_t> kblk(9 * (size_t)n_elem);
+  for (int K = 0; K < n_elem; ++K)
+    for (int a = 0; a < 3; ++a)
+      for (int b = 0; b < 3; ++b) {
+        const int ea = M->elem_face[3 * (size_t)K + a], eb = M->elem_face[3 * (size_t)K + b];
+        int slot = 0;
+        while (M->k_col[5 * (size_t)ea + slot] != eb) ++slot;
+        kblk[9 * (size_t)K + 3 * a + b] = M->k_blkoff[5 * (size_t)ea + slot];
+      }
+  // degree buckets
+  std::vector<int> bucket[kMaxP + 1];
+  for (int K = 0; K < n_elem; ++K) {
+    bucket[elem_p[K]].push_back(K);
+    M->bucket_ntmax[elem_p[K]] = std::max(M->bucket_ntmax[elem_p[K]], elem_nt(M, K));
+  }
+  // upload
+  hdg_status st = HDG_OK;
+  DevMesh& d = M->dm;
+  d.n_elem = n_elem;
+  d.n_face = M->n_face;
+  d.nfield = nfield;
+  double* dxy;
+  int *def, *dfp;
+  uint8_t* dinfo;
+  int64_t *duo, *dlo, *dxo, *dkb, *ddb;
+  if ((st = upload(ctx, M->allocs, xy, &dxy)) || (st = upload(ctx, M->allocs, M->elem_face, &def)) ||
+      (st = upload(ctx, M->allocs, info, &dinfo)) || (st = upload(ctx, M->allocs, M->face_p, &dfp)) ||
+      (st = upload(ctx, M->allocs, M->u_off, &duo)) || (st = upload(ctx, M->allocs, M->lam_off, &dlo)) ||
+      (st = upload(ctx, M->allocs, M->x_off, &dxo)) || (st = upload(ctx, M->allocs, kblk, &dkb)) ||
+      (st = upload(ctx, M->allocs, dblk, &ddb))) {
+    free_all(M->allocs);
+    delete M;
+    return st;
+  }
+  d.xy = dxy; d.elem_face = def; d.elem_info = dinfo; d.face_p = dfp;
+  d.u_off = duo; d.lam_off = dlo; d.x_off = dxo; d.kblk = dkb; d.dblk_off = ddb;
+  for (int p = 1; p <= kMaxP; ++p) {
+    M->bucket_n[p] = (int)bucket[p].size();
+    if (M->bucket_n[p] && (st = upload(ctx, M->allocs, bucket[p], &M->d_bucket[p]))) {
+      free_all(M->allocs);
+      delete M;
+      return st;
+    }
+  }
+  *out = M;
+  return HDG_OK;
+}
+
+hdg_status hdg_mesh_destroy(hdg_mesh* M) {
+  if (!M) return HDG_EINVAL;
+  cudaSetDevice(M->ctx->device);
+  free_all(M->allocs);
+  delete M;
+  return HDG_OK;
+}
+
+hdg_status hdg_mesh_sizes(const hdg_mesh* M, int64_t* s) {
+  if (!M || !s) return HDG_EINVAL;
+  s[0] = M->n_elem; s[1] = M->n_face; s[2] = M->u_len; s[3] = M->lam_len;
+  s[4] = M->x_len; s[5] = M->k_len; s[6] = M->max_nt;
+  return HDG_OK;
+}
+
+hdg_status hdg_mesh_layout(const hdg_mesh* M, int32_t* face_vid, int32_t* face_el, int32_t* face_p,
+                           int32_t* elem_face, int64_t* u_off, int64_t* lam_off, int64_t* x_off, int32_t* k_col,
+                           int64_t* k_blkoff) {
+  if (!M) return HDG_EINVAL;
+  for (int f = 0; f < M->n_face; ++f) {
+    if (face_vid) { face_vid[2 * f] = M->face_lo[f]; face_vid[2 * f + 1] = M->face_hi[f]; }
+    if (face_el) { face_el[2 * f] = M->face_el0[f]; face_el[2 * f + 1] = M->face_el1[f]; }
+    if (face_p) face_p[f] = M->face_p[f];
+  }
+  if (elem_face) std::copy(M->elem_face.begin(), M->elem_face.end(), elem_face);
+  if (u_off) std::copy(M->u_off.begin(), M->u_off.end(), u_off);
+  if (lam_off) std::copy(M->lam_off.begin(), M->lam_off.end(), lam_off);
+  if (x_off) std::copy(M->x_off.begin(), M->x_off.end(), x_off);
+  if (k_col) std::copy(M->k_col.begin(), M->k_col.end(), k_col);
+  if (k_blkoff) std::copy(M->k_blkoff.begin(), M->k_blkoff.end(), k_blkoff);
+  return HDG_OK;
+}
+
+int64_t hdg_footprint_bytes(const hdg_mesh* M, const hdg_params* P) {
+  if (!M || !P) return -1;
+  const int64_t d = sizeof(double);
+  int64_t b = d * (M->x_len + M->k_len + M->lam_len + M->u_len + M->lam_len);  // X, K, E, res_u, res_lam
+  b += sizeof(int32_t) * (int64_t)M->n_elem;                                      // status
+  b += d * (M->dh_len + 2 * M->lam_len) + sizeof(int32_t) * (int64_t)M->n_face;   // two-sided sums
+  b += d * (2 * M->u_len + 2 * M->lam_len);                                       // host-step staging
+  return b;
+}
+
+hdg_status hdg_sys_create(hdg_ctx* ctx, const hdg_mesh* M, const hdg_params* P, hdg_sys** out) {
+  if (!ctx || !M || !P || !out) return HDG_EINVAL;
+  *out = nullptr;
+  if ((P->model == HDG_EULER) != (M->nfield == 4) || (P->model != HDG_EULER && P->model != HDG_NS_MIXED))
+    return fail(ctx, HDG_EINVAL, "hdg_sys_create: model does not match the mesh's field count");
+  if (P->precision != HDG_FP64)
+    return fail(ctx, HDG_ENOTSUP, "hdg_sys_create: precision not supported by this build");
+  if (P->model != HDG_EULER) return fail(ctx, HDG_ENOTSUP, "hdg_sys_create: model not supported by this build");
+  if (!(P->gamma > 1.0) || !(P->alpha > 0.0) || !(P->mach > 0.0))
+    return fail(ctx, HDG_EINVAL, "hdg_sys_create: need gamma > 1, alpha > 0, mach > 0");
+  if (cudaSetDevice(ctx->device) != cudaSuccess) return fail(ctx, HDG_ECUDA, "cudaSetDevice failed");
+  hdg_sys* S = new hdg_sys();
+  S->ctx = ctx;
+  S->mesh = M;
+  S->prm = *P;
+  S->ph.gamma = P->gamma;
+  S->ph.alpha = P->alpha;
+  S->ph.prandtl = P->prandtl;
+  S->ph.mu_inf = P->mach / P->reynolds;
+  S->ph.suth_s = 110.4 / P->t_inf;
+  S->ph.cfl = P->cfl;
+  S->ph.model = P->model;
+  const size_t d = sizeof(double);
+  void* p[14];
+  hdg_status st = HDG_OK;
+  const size_t sizes[13] = {d * M->x_len,   d * M->k_len,   d * M->lam_len, d * M->u_len, d * M->lam_len,
+                            4 * (size_t)M->n_elem, d * M->dh_len, d * M->lam_len, d * M->lam_len,
+                            4 * (size_t)M->n_face, d * M->u_len, d * M->lam_len, d * M->lam_len};
+  for (int i = 0; i < 13; ++i)
+    if ((st = dalloc(ctx, S->allocs, sizes[i], &p[i]))) { free_all(S->allocs); delete S; return st; }
+  if ((st = dalloc(ctx, S->allocs, d * M->u_len, &p[13]))) { free_all(S->allocs); delete S; return st; }
+  S->ds.X = (double*)p[0];
+  S->ds.K = (double*)p[1];
+  S->ds.E = (double*)p[2];
+  S->ds.res_u = (double*)p[3];
+  S->ds.res_lam = (double*)p[4];
+  S->ds.status = (int32_t*)p[5];
+  S->ds.dhalf1 = (double*)p[6];
+  S->ds.ehalf1 = (double*)p[7];
+  S->ds.rhalf1 = (double*)p[8];
+  S->ds.face_cnt = (int32_t*)p[9];
+  S->d_U = (double*)p[10];
+  S->d_Lam = (double*)p[11];
+  S->d_dLam = (double*)p[12];
+  S->d_dU = (double*)p[13];
+  cudaError_t e = cudaMemset(S->ds.face_cnt, 0, 4 * (size_t)M->n_face);
+  if (e == cudaSuccess) e = cudaMemset(S->ds.K, 0, d * M->k_len);
+  if (e == cudaSuccess) e = cudaMemset(S->ds.status, 0, 4 * (size_t)M->n_elem);
+  if (e == cudaSuccess) e = cudaDeviceSynchronize();
+  if (e != cudaSuccess) {
+    free_all(S->allocs);
+    delete S;
+    return fail(ctx, HDG_ECUDA, std::string("hdg_sys_create: ") + cudaGetErrorString(e));
+  }
+  *out = S;
+  return HDG_OK;
+}
+
+hdg_status hdg_sys_destroy(hdg_sys* S) {
+  if (!S) return HDG_EINVAL;
+  cudaSetDevice(S->ctx->device);
+  free_all(S->allocs);
+  delete S;
+  return HDG_OK;
+}
+
+hdg_status hdg_condense(hdg_sys* S, const double* U, const double* Lam, void* stream) {
+  if (!S) return HDG_EINVAL;
+  hdg_ctx* ctx = S->ctx;
+  if (!U || !Lam) return fail(ctx, HDG_EINVAL, "hdg_condense: null input");
+  const hdg_mesh* M = S->mesh;
+  std::string err;
+  const int n = launch_condense(M->dm, S->ds, S->ph, ctx->d_tab, ctx->tab.off, U, Lam, M->d_bucket, M->bucket_n,
+                                M->bucket_ntmax, stream, &err);
+  if (n < 0) return fail(ctx, HDG_ECUDA, "hdg_condense: " + err);
+  S->launches = n;
+  return HDG_OK;
+}
+
+hdg_status hdg_recover(hdg_sys* S, const double* dLam, double* dU, void* stream) {
+  if (!S) return HDG_EINVAL;
+  hdg_ctx* ctx = S->ctx;
+  if (!dLam || !dU) return fail(ctx, HDG_EINVAL, "hdg_recover: null argument");
+  const hdg_mesh* M = S->mesh;
+  std::string err;
+  const int n = launch_recover_buckets(M->dm, S->ds.X, dLam, dU, M->d_bucket, M->bucket_n, stream, &err);
+  if (n < 0) return fail(ctx, HDG_ECUDA, "hdg_recover: " + err);
+  S->launches += n;
+  return HDG_OK;
+}
+
+hdg_status hdg_step_host(hdg_sys* S, const double* U, const double* Lam, const double* dLam, double* dU,
+                         void* stream) {
+  if (!S) return HDG_EINVAL;
+  hdg_ctx* ctx = S->ctx;
+  if (!U || !Lam || !dLam || !dU) return fail(ctx, HDG_EINVAL, "hdg_step_host: null argument");
+  const hdg_mesh* M = S->mesh;
+  cudaStream_t st = (cudaStream_t)stream;
+  const size_t d = sizeof(double);
+  HDG_CK(ctx, cudaMemcpyAsync(S->d_U, U, d * M->u_len, cudaMemcpyHostToDevice, st));
+  HDG_CK(ctx, cudaMemcpyAsync(S->d_Lam, Lam, d * M->lam_len, cudaMemcpyHostToDevice, st));
+  HDG_CK(ctx, cudaMemcpyAsync(S->d_dLam, dLam, d * M->lam_len, cudaMemcpyHostToDevice, st));
+  hdg_status rc = hdg_condense(S, S->d_U, S->d_Lam, stream);
+  if (rc != HDG_OK) return rc;
+  rc = hdg_recover(S, S->d_dLam, S->d_dU, stream);
+  if (rc != HDG_OK) return rc;
+  HDG_CK(ctx, cudaMemcpyAsync(dU, S->d_dU, d * M->u_len, cudaMemcpyDeviceToHost, st));
+  HDG_CK(ctx, cudaStreamSynchronize(st));
+  return HDG_OK;
+}
+
+hdg_status hdg_sys_get(const hdg_sys* S, double** X, double** K_vals, double** E, double** res_u, double** res_lam,
+                       int32_t** elem_status) {
+  if (!S) return HDG_EINVAL;
+  if (X) *X = S->ds.X;
+  if (K_vals) *K_vals = S->ds.K;
+  if (E) *E = S->ds.E;
+  if (res_u) *res_u = S->ds.res_u;
+  if (res_lam) *res_lam = S->ds.res_lam;
+  if (elem_status) *elem_status = S->ds.status;
+  return HDG_OK;
+}
+
+int32_t hdg_sys_launches(const hdg_sys* S) { return S ? S->launches : -1; }
+
+}  // extern "C"

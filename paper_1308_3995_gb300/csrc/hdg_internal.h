@@ -1,0 +1,80 @@
+// Internal declarations shared by the host planner and the CUDA kernels.
+#pragma once
+
+#include <cstdint>
+#include <string>
+#include <vector>
+
+#include "../../include/hdg.h"
+
+#ifdef __CUDACC__
+#define HDG_HD __host__ __device__
+#else
+#define HDG_HD
+#endif
+
+namespace hdg {
+
+constexpr int kMaxP = 4;          // element degrees 1..4
+constexpr int kMaxNt = 60;        // 3 faces x 4 fields x (4 + 1) modes
+constexpr int kCondThreads = 128; // threads per element CTA of the condensation kernels
+
+HDG_HD constexpr inline int n_basis(int p) { return (p + 1) * (p + 2) / 2; }
+
+// offsets (in doubles) of every table inside one device buffer
+struct TabOff {
+  int vol_w[kMaxP + 1], vol_phi[kMaxP + 1], vol_gxi[kMaxP + 1], vol_geta[kMaxP + 1];
+  int edge_s[kMaxP + 1], edge_w[kMaxP + 1], edge_psi[kMaxP + 1];
+  int edge_phi[kMaxP + 1][kMaxP + 1][3][2];   // [p][pe][local face][flip]
+};
+
+struct Tables {
+  TabOff off{};
+  std::vector<double> data;
+};
+void build_tables(Tables& T);
+
+// Flow parameters as the kernels use them.
+struct Phys {
+  double gamma, alpha, prandtl, mu_inf, suth_s, cfl;
+  int model;
+};
+
+// Device-resident mesh plan handed to kernels by value.
+struct DevMesh {
+  int n_elem, n_face, nfield;
+  const double* xy;          // [n_elem][6]
+  const int* elem_face;      // [n_elem][3]
+  const uint8_t* elem_info;  // bits 0-2: flip of local face l; bits 3-5: side of this element on face l
+  const int* face_p;         // [n_face]
+  const int64_t* u_off;      // [n_elem+1]
+  const int64_t* lam_off;    // [n_face+1]
+  const int64_t* x_off;      // [n_elem+1]
+  const int64_t* kblk;       // [n_elem][9]: offset in K of block (face a, face b), a,b local
+  const int64_t* dblk_off;   // [n_face]: offset of a face's diagonal block in the half-1 scratch
+};
+
+// Per-system output and work buffers handed to kernels by value.
+struct DevSys {
+  double* X;
+  double* K;
+  double* E;
+  double* res_u;
+  double* res_lam;
+  int32_t* status;
+  // work space for the two-sided sums of diagonal blocks, E and res_lam:
+  // the side-1 element parks its half here; whichever side arrives second sums.
+  double* dhalf1;            // [sum_e (4(p_e+1))^2]
+  double* ehalf1;            // [lam_len]
+  double* rhalf1;            // [lam_len]
+  int32_t* face_cnt;         // [n_face], zero between calls
+};
+
+// kernel launchers (hdg_kernels.cu); return the number of launches enqueued
+int launch_condense(const DevMesh& m, const DevSys& s, const Phys& ph, const double* tab, const TabOff& off,
+                    const double* U, const double* Lam, const int* const* bucket, const int* bucket_n,
+                    const int* bucket_ntmax, void* stream, std::string* err);
+int launch_recover_buckets(const DevMesh& m, const double* X, const double* dLam, double* dU,
+                           const int* const* bucket, const int* bucket_n, void* stream, std::string* err);
+
+}  // namespace hdg

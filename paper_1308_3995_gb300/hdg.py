@@ -1,0 +1,263 @@
+"""Thin Python binding of the C ABI in ``include/hdg.h`` (argument marshalling
+only; every step of the hot path runs in the CUDA library ``libhdg.so``).
+
+Names follow the C functions: ``hdg_create`` -> :class:`Context`,
+``hdg_mesh_create`` -> :class:`Mesh`, ``hdg_sys_create`` -> :class:`System`
+with ``condense``/``recover``/``step_host``.  Device arrays are torch CUDA
+tensors (plumbing for memory and streams); outputs are zero-copy torch views
+of the library-owned buffers.  There is no CPU fallback: if the library cannot
+be built or loaded, or no CUDA device is present, the calls raise.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from dataclasses import dataclass
+
+import numpy as np
+
+from . import build as _build
+
+_lib = None
+
+HDG_OK, HDG_EINVAL, HDG_ENOMEM, HDG_ECUDA, HDG_ESINGULAR, HDG_ETIMEOUT, HDG_ENOTSUP = range(7)
+HDG_EULER, HDG_NS_MIXED = 0, 1
+HDG_FP64, HDG_MIXED_FP32 = 0, 1
+STATUS_NAMES = {0: "HDG_OK", 1: "HDG_EINVAL", 2: "HDG_ENOMEM", 3: "HDG_ECUDA", 4: "HDG_ESINGULAR",
+                5: "HDG_ETIMEOUT", 6: "HDG_ENOTSUP"}
+
+# every entry point declared in include/hdg.h
+EXPORTS = ["hdg_create", "hdg_destroy", "hdg_last_error", "hdg_mesh_create", "hdg_mesh_destroy", "hdg_mesh_sizes",
+           "hdg_mesh_layout", "hdg_footprint_bytes", "hdg_sys_create", "hdg_sys_destroy", "hdg_condense",
+           "hdg_recover", "hdg_step_host", "hdg_sys_get", "hdg_sys_launches", "hdg_debug_tables"]
+
+
+class HdgError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__(f"{STATUS_NAMES.get(status, status)}: {msg}")
+        self.status = status
+
+
+class hdg_params(ctypes.Structure):
+    _fields_ = [("model", ctypes.c_int32), ("precision", ctypes.c_int32), ("gamma", ctypes.c_double),
+                ("prandtl", ctypes.c_double), ("reynolds", ctypes.c_double), ("mach", ctypes.c_double),
+                ("alpha", ctypes.c_double), ("cfl", ctypes.c_double), ("t_inf", ctypes.c_double),
+                ("refine_tol", ctypes.c_double), ("refine_max", ctypes.c_int32), ("reserved", ctypes.c_int32)]
+
+
+@dataclass
+class Params:
+    model: int = HDG_EULER
+    precision: int = HDG_FP64
+    gamma: float = 1.4
+    prandtl: float = 0.72
+    reynolds: float = 5000.0
+    mach: float = 0.5
+    alpha: float = 1.5
+    cfl: float = 0.0
+    t_inf: float = 288.15
+    refine_tol: float = 1e-13
+    refine_max: int = 4
+
+    def c(self) -> hdg_params:
+        return hdg_params(self.model, self.precision, self.gamma, self.prandtl, self.reynolds, self.mach,
+                          self.alpha, self.cfl, self.t_inf, self.refine_tol, self.refine_max, 0)
+
+
+_vp = ctypes.c_void_p
+_dp = ctypes.POINTER(ctypes.c_double)
+_i32p = ctypes.POINTER(ctypes.c_int32)
+_i64p = ctypes.POINTER(ctypes.c_int64)
+
+
+def lib(build: bool = True):
+    """Load ``libhdg.so`` (building it first if it is missing or stale)."""
+    global _lib
+    if _lib is None:
+        path = _build.build() if build else _build.LIB
+        if not os.path.exists(path):
+            raise HdgError(HDG_ENOTSUP, f"CUDA library not built: {path}")
+        L = ctypes.CDLL(path)
+        L.hdg_create.argtypes = [ctypes.POINTER(_vp), ctypes.c_int]
+        L.hdg_destroy.argtypes = [_vp]
+        L.hdg_last_error.argtypes = [_vp]
+        L.hdg_last_error.restype = ctypes.c_char_p
+        L.hdg_mesh_create.argtypes = [_vp, ctypes.c_int32, ctypes.c_int32, _dp, _i32p,
+                                      ctypes.POINTER(ctypes.c_int8), ctypes.POINTER(_vp)]
+        L.hdg_mesh_destroy.argtypes = [_vp]
+        L.hdg_mesh_sizes.argtypes = [_vp, _i64p]
+        L.hdg_mesh_layout.argtypes = [_vp, _i32p, _i32p, _i32p, _i32p, _i64p, _i64p, _i64p, _i32p, _i64p]
+        L.hdg_footprint_bytes.argtypes = [_vp, ctypes.POINTER(hdg_params)]
+        L.hdg_footprint_bytes.restype = ctypes.c_int64
+        L.hdg_sys_create.argtypes = [_vp, _vp, ctypes.POINTER(hdg_params), ctypes.POINTER(_vp)]
+        L.hdg_sys_destroy.argtypes = [_vp]
+        L.hdg_condense.argtypes = [_vp, _vp, _vp, _vp]
+        L.hdg_recover.argtypes = [_vp, _vp, _vp, _vp]
+        L.hdg_step_host.argtypes = [_vp, _vp, _vp, _vp, _vp, _vp]
+        L.hdg_sys_get.argtypes = [_vp] + [ctypes.POINTER(_vp)] * 6
+        L.hdg_sys_launches.argtypes = [_vp]
+        L.hdg_sys_launches.restype = ctypes.c_int32
+        L.hdg_debug_tables.argtypes = [ctypes.c_int] * 5 + [_dp, ctypes.c_int]
+        _lib = L
+    return _lib
+
+
+def _check(st, ctx_handle=None, what=""):
+    if st != HDG_OK:
+        msg = lib().hdg_last_error(ctx_handle).decode() if ctx_handle else what
+        raise HdgError(st, msg or what)
+
+
+def _ptr(t) -> int:
+    """Device pointer of a contiguous float64/int CUDA tensor."""
+    if not t.is_cuda or not t.is_contiguous():
+        raise ValueError("expected a contiguous CUDA tensor")
+    return t.data_ptr()
+
+
+def _stream(stream) -> int:
+    import torch
+    if stream is None:
+        return torch.cuda.current_stream().cuda_stream
+    return stream.cuda_stream if hasattr(stream, "cuda_stream") else int(stream)
+
+
+def hdg_debug_tables(which: int, p: int, pe: int = 0, lf: int = 0, flip: int = 0) -> np.ndarray:
+    """Host-only copy of one of the library's quadrature/basis tables."""
+    out = np.zeros(4096)
+    n = lib().hdg_debug_tables(which, p, pe, lf, flip, out.ctypes.data_as(_dp), out.size)
+    if n < 0:
+        raise HdgError(HDG_EINVAL, "no such table")
+    return out[:n].copy()
+
+
+class _DevView:
+    """__cuda_array_interface__ over library-owned device memory."""
+
+    def __init__(self, ptr, n, typestr):
+        self.__cuda_array_interface__ = {"shape": (int(n),), "typestr": typestr, "data": (int(ptr), False),
+                                         "version": 2, "strides": None}
+
+
+class Context:
+    """hdg_create / hdg_destroy."""
+
+    def __init__(self, device: int = 0):
+        h = _vp()
+        _check(lib().hdg_create(ctypes.byref(h), int(device)), what=f"hdg_create(device={device}) failed")
+        self.h = h
+        self.device = device
+
+    def close(self):
+        if getattr(self, "h", None):
+            lib().hdg_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def last_error(self) -> str:
+        return lib().hdg_last_error(self.h).decode()
+
+
+class Mesh:
+    """hdg_mesh_create + hdg_mesh_sizes + hdg_mesh_layout (host arrays in, device plan out)."""
+
+    def __init__(self, ctx: Context, elem_xy, elem_vid, elem_p, nfield: int):
+        xy = np.ascontiguousarray(elem_xy, dtype=np.float64).reshape(-1)
+        vid = np.ascontiguousarray(elem_vid, dtype=np.int32).reshape(-1)
+        p = np.ascontiguousarray(elem_p, dtype=np.int8).reshape(-1)
+        h = _vp()
+        _check(lib().hdg_mesh_create(ctx.h, int(p.size), int(nfield), xy.ctypes.data_as(_dp),
+                                     vid.ctypes.data_as(_i32p), p.ctypes.data_as(ctypes.POINTER(ctypes.c_int8)),
+                                     ctypes.byref(h)), ctx.h)
+        self.h, self.ctx, self.nfield = h, ctx, nfield
+        s = np.zeros(7, np.int64)
+        lib().hdg_mesh_sizes(h, s.ctypes.data_as(_i64p))
+        self.n_elem, self.n_face, self.u_len, self.lam_len, self.x_len, self.k_len, self.max_nt = (int(v) for v in s)
+        nf, ne = self.n_face, self.n_elem
+        self.face_vid = np.zeros((nf, 2), np.int32)
+        self.face_el = np.zeros((nf, 2), np.int32)
+        self.face_p = np.zeros(nf, np.int32)
+        self.elem_face = np.zeros((ne, 3), np.int32)
+        self.u_off = np.zeros(ne + 1, np.int64)
+        self.lam_off = np.zeros(nf + 1, np.int64)
+        self.x_off = np.zeros(ne + 1, np.int64)
+        self.k_col = np.zeros((nf, 5), np.int32)
+        self.k_blkoff = np.zeros(5 * nf + 1, np.int64)
+        lib().hdg_mesh_layout(h, self.face_vid.ctypes.data_as(_i32p), self.face_el.ctypes.data_as(_i32p),
+                              self.face_p.ctypes.data_as(_i32p), self.elem_face.ctypes.data_as(_i32p),
+                              self.u_off.ctypes.data_as(_i64p), self.lam_off.ctypes.data_as(_i64p),
+                              self.x_off.ctypes.data_as(_i64p), self.k_col.ctypes.data_as(_i32p),
+                              self.k_blkoff.ctypes.data_as(_i64p))
+        self.elem_p = p.astype(np.int32)
+
+    def footprint_bytes(self, params: Params) -> int:
+        P = params.c()
+        return int(lib().hdg_footprint_bytes(self.h, ctypes.byref(P)))
+
+    def close(self):
+        if getattr(self, "h", None):
+            lib().hdg_mesh_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class System:
+    """hdg_sys_create / hdg_condense / hdg_recover / hdg_step_host / hdg_sys_get."""
+
+    def __init__(self, ctx: Context, mesh: Mesh, params: Params):
+        P = params.c()
+        h = _vp()
+        _check(lib().hdg_sys_create(ctx.h, mesh.h, ctypes.byref(P), ctypes.byref(h)), ctx.h)
+        self.h, self.ctx, self.mesh, self.params = h, ctx, mesh, params
+        ptrs = [_vp() for _ in range(6)]
+        lib().hdg_sys_get(h, *[ctypes.byref(p) for p in ptrs])
+        self._ptrs = [p.value for p in ptrs]
+
+    def condense(self, U, Lam, stream=None):
+        """hdg_condense on device tensors U [u_len], Lam [lam_len] (float64)."""
+        _check(lib().hdg_condense(self.h, _ptr(U), _ptr(Lam), _stream(stream)), self.ctx.h)
+
+    def recover(self, dLam, dU, stream=None):
+        """hdg_recover: dU [u_len] <- X_F - X_B dLam, device tensors."""
+        _check(lib().hdg_recover(self.h, _ptr(dLam), _ptr(dU), _stream(stream)), self.ctx.h)
+
+    def step_host(self, U, Lam, dLam, dU, stream=None):
+        """hdg_step_host on host (preferably pinned) float64 torch tensors or numpy arrays."""
+        def hp(a):
+            return a.data_ptr() if hasattr(a, "data_ptr") else a.ctypes.data
+        _check(lib().hdg_step_host(self.h, hp(U), hp(Lam), hp(dLam), hp(dU), _stream(stream)), self.ctx.h)
+
+    @property
+    def launches(self) -> int:
+        return int(lib().hdg_sys_launches(self.h))
+
+    def views(self):
+        """Zero-copy torch views of X, K, E, res_u, res_lam, elem_status."""
+        import torch
+        m = self.mesh
+        n = [m.x_len, m.k_len, m.lam_len, m.u_len, m.lam_len, m.n_elem]
+        ty = ["<f8"] * 5 + ["<i4"]
+        names = ["X", "K", "E", "res_u", "res_lam", "status"]
+        return {nm: torch.as_tensor(_DevView(p, k, t), device=f"cuda:{self.ctx.device}")
+                for nm, p, k, t in zip(names, self._ptrs, n, ty)}
+
+    def close(self):
+        if getattr(self, "h", None):
+            lib().hdg_sys_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
