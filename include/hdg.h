@@ -188,6 +188,35 @@ hdg_status hdg_sys_get(const hdg_sys* sys, double** X, double** K_vals, double**
 /* Number of kernel launches the last hdg_condense + hdg_recover enqueued. */
 int32_t hdg_sys_launches(const hdg_sys* sys);
 
+/* Allocation-free condensation.  The paper has no counterpart: this is an
+ * interface for callers that cannot allocate device memory when they call --
+ * serving loops with a latency budget (cudaMalloc and cudaFree can synchronise
+ * the whole device and take unbounded time) and hosts whose device memory is
+ * owned by another allocator or fixed at start-up.  It does the work of
+ * hdg_condense (same kernels, bitwise the same results) on the mesh's device,
+ * enqueued on `stream`, but writes to CALLER device buffers: X [x_len],
+ * K_vals [k_len], E [lam_len], res_u [u_len], res_lam [lam_len],
+ * elem_status [n_elem] (sizes from hdg_mesh_sizes; U, Lam as in hdg_condense).
+ * It calls no cudaMalloc, cudaFree or other allocating routine: the per-face
+ * work space lives in one fixed 64 MiB device array inside the library, which
+ * every GPU that loads the library holds until the process exits.
+ *   - Meshes whose work space is larger than 64 MiB are rejected with
+ *     HDG_EINVAL and a message naming the size (per face: 4 bytes + 8 (4(p_e+1))^2
+ *     + 16 * 4(p_e+1) bytes, each part of the array rounded up to 256 bytes;
+ *     about 19,000 faces at p_e = 4, 29,000 at p_e = 3).  Only the FP64 Euler
+ *     path is supported (else HDG_ENOTSUP).
+ *   - The first call on a device resolves the array's device address
+ *     (cudaGetSymbolAddress, with that device made current); make that first
+ *     call before any stream capture on the device.
+ *   - Every call shares the one array, which keeps the last call's contents;
+ *     the call clears the part that must start at zero (the arrival counters)
+ *     on `stream` before its kernels.  Calls whose work overlaps on the GPU
+ *     (other streams, other host threads, or another mesh) race on the array
+ *     and give wrong results: serialise them. */
+hdg_status hdg_condense_noalloc(const hdg_mesh* mesh, const hdg_params* params, const double* U,
+                                const double* Lam, double* X, double* K_vals, double* E, double* res_u,
+                                double* res_lam, int32_t* elem_status, void* stream);
+
 /* Diagnostic, host only (no device needed): copy one of the library's own
  * quadrature/basis tables into out[cap]; returns its length or -1.
  * which: 0 volume weights [(p+2)^2], 1 basis values, 2 d/dxi, 3 d/deta

@@ -92,6 +92,25 @@ int elem_nt(const hdg_mesh* M, int K) {
 
 }  // namespace
 
+namespace hdg {
+PlanRef plan_ref(const hdg_mesh* M) {
+  PlanRef r;
+  r.device = M->ctx->device;
+  r.tab = M->ctx->d_tab;
+  r.off = &M->ctx->tab.off;
+  r.dm = &M->dm;
+  r.bucket = M->d_bucket;
+  r.bucket_n = M->bucket_n;
+  r.bucket_ntmax = M->bucket_ntmax;
+  r.n_face = M->n_face;
+  r.nfield = M->nfield;
+  r.lam_len = M->lam_len;
+  r.dh_len = M->dh_len;
+  r.err = &M->ctx->err;
+  return r;
+}
+}  // namespace hdg
+
 extern "C" {
 
 hdg_status hdg_create(hdg_ctx** out, int device) {

@@ -70,6 +70,22 @@ struct DevSys {
   int32_t* face_cnt;         // [n_face], zero between calls
 };
 
+// Read-only view of a mesh plan and its context, for translation units other
+// than the one that owns the opaque structs (hdg_api.cu).
+struct PlanRef {
+  int device;
+  const double* tab;
+  const TabOff* off;
+  const DevMesh* dm;
+  const int* const* bucket;
+  const int* bucket_n;
+  const int* bucket_ntmax;
+  int n_face, nfield;
+  int64_t lam_len, dh_len;
+  std::string* err;
+};
+PlanRef plan_ref(const hdg_mesh* mesh);
+
 // kernel launchers (hdg_kernels.cu); return the number of launches enqueued
 int launch_condense(const DevMesh& m, const DevSys& s, const Phys& ph, const double* tab, const TabOff& off,
                     const double* U, const double* Lam, const int* const* bucket, const int* bucket_n,

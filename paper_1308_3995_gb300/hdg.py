@@ -29,7 +29,8 @@ STATUS_NAMES = {0: "HDG_OK", 1: "HDG_EINVAL", 2: "HDG_ENOMEM", 3: "HDG_ECUDA", 4
 # every entry point declared in include/hdg.h
 EXPORTS = ["hdg_create", "hdg_destroy", "hdg_last_error", "hdg_mesh_create", "hdg_mesh_destroy", "hdg_mesh_sizes",
            "hdg_mesh_layout", "hdg_footprint_bytes", "hdg_sys_create", "hdg_sys_destroy", "hdg_condense",
-           "hdg_recover", "hdg_step_host", "hdg_sys_get", "hdg_sys_launches", "hdg_debug_tables"]
+           "hdg_recover", "hdg_step_host", "hdg_sys_get", "hdg_sys_launches", "hdg_debug_tables",
+           "hdg_condense_noalloc"]
 
 
 class HdgError(RuntimeError):
@@ -98,6 +99,7 @@ def lib(build: bool = True):
         L.hdg_sys_launches.argtypes = [_vp]
         L.hdg_sys_launches.restype = ctypes.c_int32
         L.hdg_debug_tables.argtypes = [ctypes.c_int] * 5 + [_dp, ctypes.c_int]
+        L.hdg_condense_noalloc.argtypes = [_vp, ctypes.POINTER(hdg_params)] + [_vp] * 9
         _lib = L
     return _lib
 
@@ -129,6 +131,16 @@ def hdg_debug_tables(which: int, p: int, pe: int = 0, lf: int = 0, flip: int = 0
     if n < 0:
         raise HdgError(HDG_EINVAL, "no such table")
     return out[:n].copy()
+
+
+def hdg_condense_noalloc(mesh: "Mesh", params: Params, U, Lam, X, K, E, res_u, res_lam, status, stream=None):
+    """Allocation-free condensation into caller device tensors (for callers that
+    cannot allocate device memory at call time).  Outputs: X [x_len], K [k_len],
+    E [lam_len], res_u [u_len], res_lam [lam_len] float64, status [n_elem] int32.
+    Calls that overlap on the GPU share the library's fixed work array and race."""
+    P = params.c()
+    _check(lib().hdg_condense_noalloc(mesh.h, ctypes.byref(P), _ptr(U), _ptr(Lam), _ptr(X), _ptr(K), _ptr(E),
+                                      _ptr(res_u), _ptr(res_lam), _ptr(status), _stream(stream)), mesh.ctx.h)
 
 
 class _DevView:
