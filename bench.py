@@ -297,9 +297,13 @@ def main(argv=None):
     ap.add_argument("--workload", default="euler_p3_16k")
     ap.add_argument("--precision", type=int, default=0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cells", default=None, help="override the grid, e.g. 48x96 (profiling runs)")
     args = ap.parse_args(argv)
     from paper_1308_3995_gb300 import inputs as G
     wl = G.WORKLOADS[args.workload]
+    if args.cells:
+        nx, ny = (int(v) for v in args.cells.lower().split("x"))
+        wl = G.small_variant(wl, nx, ny)
     ws, rank, local = dist_env()
     if args.impl == "reference":
         return run_reference(args, wl, rank)
