@@ -26,6 +26,10 @@ struct TabOff {
   int vol_w[kMaxP + 1], vol_phi[kMaxP + 1], vol_gxi[kMaxP + 1], vol_geta[kMaxP + 1];
   int edge_s[kMaxP + 1], edge_w[kMaxP + 1], edge_psi[kMaxP + 1];
   int edge_phi[kMaxP + 1][kMaxP + 1][3][2];   // [p][pe][local face][flip]
+  // derived reference matrices (unit edge length, unit det J):
+  int vol_dref[kMaxP + 1];                    // [2][np][np]: sum_q w_q dphi_i/dxi_r phi_j
+  int face_mass[kMaxP + 1][kMaxP + 1][3];     // [np][np]: sum_g w_g phi_i phi_j on local face lf
+  int edge_cross[kMaxP + 1][kMaxP + 1][3][2]; // [pe+1][np]: sum_g w_g psi_k phi_j
 };
 
 struct Tables {

@@ -32,7 +32,7 @@ namespace hdg {
 // --------------------------------------------------------------------------
 __device__ __forceinline__ void euler_flux_jac(const double* w, double gam, double* fx, double* fy, double* Ax,
                                                double* Ay) {
-  const double rho = w[0], ir = 1.0 / rho, u = w[1] * ir, v = w[2] * ir, E = w[3];
+  const double rho = w[0], ir = __drcp_rn(rho), u = w[1] * ir, v = w[2] * ir, E = w[3];
   const double g1 = gam - 1.0;
   const double q2 = u * u + v * v;
   const double p = g1 * (E - 0.5 * rho * q2);
@@ -52,18 +52,29 @@ __device__ __forceinline__ void euler_flux_jac(const double* w, double gam, doub
 }
 
 // --------------------------------------------------------------------------
+// Bit-level helpers that keep pivot search and finiteness checks off the
+// binary64 pipe: for non-negative doubles, IEEE order is the order of the bit
+// patterns as unsigned integers.
+// --------------------------------------------------------------------------
+__device__ __forceinline__ unsigned long long abs_key(double v) {
+  return (unsigned long long)__double_as_longlong(v) & 0x7fffffffffffffffull;
+}
+__device__ __forceinline__ int not_finite(double v) {
+  return (__double2hiint(v) & 0x7ff00000) == 0x7ff00000;
+}
+
+// --------------------------------------------------------------------------
 // Shared-memory layout of the Euler element kernel (offsets in doubles).
 // --------------------------------------------------------------------------
 constexpr int kPtSlots = 6;            // edge points per face slot (p_e + 2 <= 6)
-constexpr int kDStride = 400;          // (4 * 5)^2: one face's trace-trace block
 template <int P>
 struct EulerLayout {
   static constexpr int NP = n_basis(P), NQ = (P + 2) * (P + 2), N = 4 * NP, LDA = N + 1;
   static constexpr int SCR_VOL = NQ * (4 + 8 + 32) + 4 * NP * NQ;
   static constexpr int SCR_FACE = 3 * kPtSlots * (4 + 16 * 5);
   static constexpr int SCR = SCR_VOL > SCR_FACE ? SCR_VOL : SCR_FACE;
-  int ldr, oA, oR, oU, oL, oNu, oNl, oEh, oD, oMe, oMf, oScr, total;
-  HDG_HD explicit EulerLayout(int ldr_) : ldr(ldr_) {
+  int ldr, dstride, oA, oR, oU, oL, oNu, oNl, oEh, oMe, oD, oScr, total;
+  HDG_HD EulerLayout(int ldr_, int nkmax) : ldr(ldr_), dstride(16 * nkmax * nkmax) {
     oA = 0;
     oR = oA + N * LDA;
     oU = oR + N * ldr;
@@ -71,15 +82,19 @@ struct EulerLayout {
     oNu = oL + kMaxNt;
     oNl = oNu + N;
     oEh = oNl + kMaxNt;
-    oD = oEh + kMaxNt;
-    oMe = oD + 3 * kDStride;
-    oMf = oMe + 3 * 5 * NP;
-    oScr = oMf + NP * NP;
+    oMe = oEh + kMaxNt;
+    oD = oMe + 3 * 5 * NP;
+    oScr = oD + 3 * dstride;
     total = oScr + SCR;
   }
 };
 
 inline int ldr_for(int ntmax) { return (ntmax + 1) | 1; }  // odd leading dimension
+// largest single-face trace size in a bucket of degree p: every face has p_e >= p
+inline int nkmax_for(int p, int ntmax) {
+  int nk = ntmax / 4 - 2 * (p + 1);
+  return nk > kMaxP + 1 ? kMaxP + 1 : nk;
+}
 
 // --------------------------------------------------------------------------
 // Condensation kernel, Euler, binary64: one element per CTA iteration.
@@ -87,12 +102,13 @@ inline int ldr_for(int ntmax) { return (ntmax + 1) | 1; }  // odd leading dimens
 template <int P>
 __global__ void __launch_bounds__(kCondThreads) k_condense_euler_f64(
     DevMesh m, DevSys s, Phys ph, const double* __restrict__ tab, TabOff to, const double* __restrict__ U,
-    const double* __restrict__ Lam, const int* __restrict__ elems, int n_elems, int ldr) {
+    const double* __restrict__ Lam, const int* __restrict__ elems, int n_elems, int ldr, int nkmax) {
   using L = EulerLayout<P>;
   constexpr int NP = L::NP, NQ = L::NQ, N = L::N, LDA = L::LDA;
   constexpr int NT = kCondThreads;
   extern __shared__ double smem[];
-  const L lay(ldr);
+  const L lay(ldr, nkmax);
+  const int DS = lay.dstride;
   double* sA = smem + lay.oA;
   double* sR = smem + lay.oR;
   double* sU = smem + lay.oU;
@@ -100,9 +116,8 @@ __global__ void __launch_bounds__(kCondThreads) k_condense_euler_f64(
   double* sNu = smem + lay.oNu;
   double* sNl = smem + lay.oNl;
   double* sEh = smem + lay.oEh;
-  double* sD = smem + lay.oD;
   double* sMe = smem + lay.oMe;
-  double* sMf = smem + lay.oMf;
+  double* sD = smem + lay.oD;
   double* scr = smem + lay.oScr;
   // volume scratch
   double* sWq = scr;                  // [4][NQ]
@@ -123,40 +138,45 @@ __global__ void __launch_bounds__(kCondThreads) k_condense_euler_f64(
   const double* vphi = tab + to.vol_phi[P];
   const double* vgx = tab + to.vol_gxi[P];
   const double* vge = tab + to.vol_geta[P];
+  const double* dref = tab + to.vol_dref[P];
   const double alpha = ph.alpha;
+  const double g1 = ph.gamma - 1.0;
 
   for (int it = blockIdx.x; it < n_elems; it += gridDim.x) {
     const int K = elems[it];
     // ---------------- a1: geometry, faces, state ----------------
-    if (tid == 0) {
+    if (tid < 3) {  // one lane per local face, one warp instruction for all three
       const double* c = m.xy + 6 * (size_t)K;
-      const double J00 = c[2] - c[0], J01 = c[4] - c[0], J10 = c[3] - c[1], J11 = c[5] - c[1];
-      const double det = J00 * J11 - J01 * J10;
-      const double inv = 1.0 / det;
-      g_det = det;
-      g_Ji[0][0] = J11 * inv; g_Ji[0][1] = -J01 * inv;
-      g_Ji[1][0] = -J10 * inv; g_Ji[1][1] = J00 * inv;
+      const int a = tid, b = (tid + 1) % 3;
+      const double dx = c[2 * b] - c[2 * a], dy = c[2 * b + 1] - c[2 * a + 1];
+      const double len = sqrt(dx * dx + dy * dy);
+      const double il = __drcp_rn(len);
+      g_len[a] = len;
+      g_n[a][0] = dy * il;
+      g_n[a][1] = -dx * il;
+      const int e = m.elem_face[3 * (size_t)K + a];
       const int info = m.elem_info[K];
-      double perim = 0.0;
-      int toff = 0;
-      for (int a = 0; a < 3; ++a) {
-        const int b = (a + 1) % 3;
-        const double dx = c[2 * b] - c[2 * a], dy = c[2 * b + 1] - c[2 * a + 1];
-        const double len = sqrt(dx * dx + dy * dy);
-        g_len[a] = len;
-        g_n[a][0] = dy / len;
-        g_n[a][1] = -dx / len;
-        perim += len;
-        const int e = m.elem_face[3 * (size_t)K + a];
-        g_e[a] = e;
-        g_pe[a] = m.face_p[e];
-        g_nk[a] = g_pe[a] + 1;
-        g_fl[a] = (info >> a) & 1;
-        g_side[a] = (info >> (3 + a)) & 1;
-        g_toff[a] = toff;
-        toff += 4 * g_nk[a];
+      g_e[a] = e;
+      g_pe[a] = m.face_p[e];
+      g_nk[a] = g_pe[a] + 1;
+      g_fl[a] = (info >> a) & 1;
+      g_side[a] = (info >> (3 + a)) & 1;
+      if (tid == 0) {
+        const double J00 = c[2] - c[0], J01 = c[4] - c[0], J10 = c[3] - c[1], J11 = c[5] - c[1];
+        const double det = J00 * J11 - J01 * J10;
+        const double inv = __drcp_rn(det);
+        g_det = det;
+        g_Ji[0][0] = J11 * inv; g_Ji[0][1] = -J01 * inv;
+        g_Ji[1][0] = -J10 * inv; g_Ji[1][1] = J00 * inv;
+        s_bad = 0;
       }
-      g_toff[3] = toff;
+    }
+    __syncthreads();
+    if (tid == 0) {
+      g_toff[0] = 0;
+      g_toff[1] = 4 * g_nk[0];
+      g_toff[2] = 4 * (g_nk[0] + g_nk[1]);
+      g_toff[3] = 4 * (g_nk[0] + g_nk[1] + g_nk[2]);
       // pseudo-time mass det(J)/dt_K (Sec. 3.3), from the element-mean state
       g_mt = 0.0;
       if (ph.cfl > 0.0) {
@@ -164,12 +184,12 @@ __global__ void __launch_bounds__(kCondThreads) k_condense_euler_f64(
         const double c0 = 1.4142135623730951;  // value of the constant orthonormal mode
         const double rho = c0 * u0[0], uu = c0 * u0[NP] / rho, vv = c0 * u0[2 * NP] / rho;
         const double E = c0 * u0[3 * NP];
-        const double p = (ph.gamma - 1.0) * (E - 0.5 * rho * (uu * uu + vv * vv));
+        const double p = g1 * (E - 0.5 * rho * (uu * uu + vv * vv));
+        const double perim = g_len[0] + g_len[1] + g_len[2];
         const double lam_c = (sqrt(uu * uu + vv * vv) + sqrt(ph.gamma * p / rho)) * perim;
-        const double dt = ph.cfl * 0.5 * det / lam_c;
-        g_mt = det / dt;
+        const double dt = ph.cfl * 0.5 * g_det / lam_c;
+        g_mt = g_det / dt;
       }
-      s_bad = 0;
     }
     __syncthreads();
     const int nt = g_toff[3];
@@ -203,8 +223,9 @@ __global__ void __launch_bounds__(kCondThreads) k_condense_euler_f64(
         const double a0 = c * g_Ji[r][0], a1 = c * g_Ji[r][1];
 #pragma unroll
         for (int f = 0; f < 4; ++f) sFh[(r * 4 + f) * NQ + q] = a0 * fx[f] + a1 * fy[f];
+        // rows 1..3 only: row 0 of both flux Jacobians is constant
 #pragma unroll
-        for (int fg = 0; fg < 16; ++fg) sAh[(r * 16 + fg) * NQ + q] = a0 * Ax[fg] + a1 * Ay[fg];
+        for (int fg = 4; fg < 16; ++fg) sAh[(r * 16 + fg) * NQ + q] = a0 * Ax[fg] + a1 * Ay[fg];
       }
     }
     __syncthreads();
@@ -212,25 +233,44 @@ __global__ void __launch_bounds__(kCondThreads) k_condense_euler_f64(
     for (int t = tid; t < N; t += NT) {
       const int f = t / NP, i = t - f * NP;
       double acc = 0.0;
-      for (int q = 0; q < NQ; ++q)
-        acc += vgx[q * NP + i] * sFh[f * NQ + q] + vge[q * NP + i] * sFh[(4 + f) * NQ + q];
-      sNu[t] = -acc;
+      for (int q = 0; q < NQ; ++q) {
+        acc -= vgx[q * NP + i] * sFh[f * NQ + q];
+        acc -= vge[q * NP + i] * sFh[(4 + f) * NQ + q];
+      }
+      sNu[t] = acc;
     }
-    // volume Jacobian, one block row f at a time:
+    // volume Jacobian A_fg = -sum_k (dF_k/dw)_fg D_k.  Blocks whose flux-Jacobian
+    // entries are constants (row 0: (0,1) = -D_x, (0,2) = -D_y, (0,0) = (0,3) = 0;
+    // (1,3) = -(gamma-1) D_x; (2,3) = -(gamma-1) D_y) use D_k = det J sum_r Ji[r][k] Dref_r.
+    for (int t = tid; t < NP * NP; t += NT) {
+      const int i = t / NP, j = t - i * NP;
+      const double d0 = dref[t], d1 = dref[NP * NP + t];
+      const double Dx = g_det * (g_Ji[0][0] * d0 + g_Ji[1][0] * d1);
+      const double Dy = g_det * (g_Ji[0][1] * d0 + g_Ji[1][1] * d1);
+      double* a0 = sA + i * LDA + j;  // block row 0
+      a0[0] = 0.0;
+      a0[NP] = -Dx;
+      a0[2 * NP] = -Dy;
+      a0[3 * NP] = 0.0;
+      sA[(NP + i) * LDA + 3 * NP + j] = -g1 * Dx;
+      sA[(2 * NP + i) * LDA + 3 * NP + j] = -g1 * Dy;
+    }
+    // state-dependent blocks, one block row f = 1..3 at a time (row 3 has four):
     //   Z_g[i][q] = sum_r dphi_i/dxi_r (q) Ahat_r,fg(q);  A_fg[i][j] = -sum_q Z_g[i][q] phi_j(q)
-    for (int f = 0; f < 4; ++f) {
-      for (int t = tid; t < 4 * NP * NQ; t += NT) {
+    for (int f = 1; f < 4; ++f) {
+      const int ng = (f == 3) ? 4 : 3;
+      for (int t = tid; t < ng * NP * NQ; t += NT) {
         const int g = t / (NP * NQ), rem = t - g * NP * NQ, i = rem / NQ, q = rem - i * NQ;
         sZ[t] = vgx[q * NP + i] * sAh[(f * 4 + g) * NQ + q] + vge[q * NP + i] * sAh[(16 + f * 4 + g) * NQ + q];
       }
       __syncthreads();
-      for (int t = tid; t < 4 * NP * NP; t += NT) {
+      for (int t = tid; t < ng * NP * NP; t += NT) {
         const int g = t / (NP * NP), rem = t - g * NP * NP, i = rem / NP, j = rem - i * NP;
         const double* z = sZ + (g * NP + i) * NQ;
         double acc = 0.0;
 #pragma unroll 5
-        for (int q = 0; q < NQ; ++q) acc += z[q] * vphi[q * NP + j];
-        sA[(f * NP + i) * LDA + g * NP + j] = -acc;
+        for (int q = 0; q < NQ; ++q) acc -= z[q] * vphi[q * NP + j];
+        sA[(f * NP + i) * LDA + g * NP + j] = acc;
       }
       __syncthreads();
     }
@@ -285,35 +325,13 @@ __global__ void __launch_bounds__(kCondThreads) k_condense_euler_f64(
         const int r = t / m4, c = t - r * m4, f = r / nk, k = r - f * nk, g = c / nk, l = c - g * nk;
         double acc = 0.0;
         for (int q = 0; q < nk + 1; ++q) acc += ps[q * nk + k] * sW[((a * kPtSlots + q) * 16 + f * 4 + g) * 5 + l];
-        sD[a * kDStride + t] = acc;
+        sD[a * DS + t] = acc;
       }
     }
-    // C_a = alpha <psi_k, phi_j>_e delta_fg, kept as the scalar edge matrix Me_a[k][j]
+    // C_a = alpha |e_a| <psi_k, phi_j> delta_fg, kept as the scalar edge matrix
     for (int t = tid; t < 3 * 5 * NP; t += NT) {
-      const int a = t / (5 * NP), rem = t - a * 5 * NP, k = rem / NP, j = rem - k * NP;
-      if (k < g_nk[a]) {
-        const int pe = g_pe[a], nk = pe + 1;
-        const double* phe = tab + to.edge_phi[P][pe][a][g_fl[a]];
-        const double* ps = tab + to.edge_psi[pe];
-        const double* ew = tab + to.edge_w[pe];
-        double acc = 0.0;
-        for (int q = 0; q < pe + 2; ++q) acc += ew[q] * ps[q * nk + k] * phe[q * NP + j];
-        sMe[t] = alpha * g_len[a] * acc;
-      }
-    }
-    // face mass alpha <phi_i, phi_j>_dK (same for every field), plus the pseudo-time mass
-    for (int t = tid; t < NP * NP; t += NT) {
-      const int i = t / NP, j = t - i * NP;
-      double acc = 0.0;
-      for (int a = 0; a < 3; ++a) {
-        const int pe = g_pe[a];
-        const double* phe = tab + to.edge_phi[P][pe][a][g_fl[a]];
-        const double* ew = tab + to.edge_w[pe];
-        double sa = 0.0;
-        for (int q = 0; q < pe + 2; ++q) sa += ew[q] * phe[q * NP + i] * phe[q * NP + j];
-        acc += g_len[a] * sa;
-      }
-      sMf[t] = alpha * acc + ((i == j) ? g_mt : 0.0);
+      const int a = t / (5 * NP), rem = t - a * 5 * NP, k = rem / NP;
+      if (k < g_nk[a]) sMe[t] = alpha * g_len[a] * tab[to.edge_cross[P][g_pe[a]][a][g_fl[a]] + rem];
     }
     // face parts of the residuals
     for (int t = tid; t < N; t += NT) {
@@ -335,9 +353,12 @@ __global__ void __launch_bounds__(kCondThreads) k_condense_euler_f64(
       sEh[t] = -acc;  // H
     }
     __syncthreads();
+    // face mass alpha <phi_i, phi_j>_dK on every field's diagonal block, plus the pseudo-time mass
     for (int t = tid; t < NP * NP; t += NT) {
       const int i = t / NP, j = t - i * NP;
-      const double v = sMf[t];
+      double v = 0.0;
+      for (int a = 0; a < 3; ++a) v += g_len[a] * tab[to.face_mass[P][g_pe[a]][a] + t];
+      v = alpha * v + ((i == j) ? g_mt : 0.0);
 #pragma unroll
       for (int f = 0; f < 4; ++f) sA[(f * NP + i) * LDA + f * NP + j] += v;
     }
@@ -348,22 +369,21 @@ __global__ void __launch_bounds__(kCondThreads) k_condense_euler_f64(
     const int nr1 = nt + 1;
     for (int k = 0; k < N; ++k) {
       if (tid < 32) {
-        double best = -1.0;
+        unsigned long long best = 0ull;
         int bi = k;
         for (int i = k + tid; i < N; i += 32) {
-          const double v = fabs(sA[i * LDA + k]);
+          const unsigned long long v = abs_key(sA[i * LDA + k]);
           if (v > best) { best = v; bi = i; }
         }
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) {
-          const double ob = __shfl_down_sync(0xffffffffu, best, o);
+          const unsigned long long ob = __shfl_down_sync(0xffffffffu, best, o);
           const int oi = __shfl_down_sync(0xffffffffu, bi, o);
           if (ob > best || (ob == best && oi < bi)) { best = ob; bi = oi; }
         }
         if (tid == 0) {
           s_piv = bi;
-          const double pv = sA[bi * LDA + k];
-          if (pv == 0.0) { s_bad = 1; s_pinv[k] = 0.0; } else { s_pinv[k] = 1.0 / pv; }
+          if (best == 0ull) { s_bad |= 1; s_pinv[k] = 0.0; } else { s_pinv[k] = __drcp_rn(sA[bi * LDA + k]); }
         }
       }
       __syncthreads();
@@ -408,24 +428,21 @@ __global__ void __launch_bounds__(kCondThreads) k_condense_euler_f64(
       const int a = (r >= g_toff[2]) ? 2 : (r >= g_toff[1] ? 1 : 0);
       const int nka = g_nk[a], rl = r - g_toff[a], f = rl / nka, k = rl - f * nka;
       const double* me = sMe + (a * 5 + k) * NP;
-      double acc = 0.0;
-#pragma unroll
-      for (int j = 0; j < NP; ++j) acc += me[j] * sR[(f * NP + j) * ldr + c];
       if (c == nt) {
-        const double v = sEh[r] - acc;
+        double v = sEh[r];
+#pragma unroll
+        for (int j = 0; j < NP; ++j) v -= me[j] * sR[(f * NP + j) * ldr + c];
         sEh[r] = v;
-        bad |= !isfinite(v);
+        bad |= not_finite(v);
       } else {
         const int b = (c >= g_toff[2]) ? 2 : (c >= g_toff[1] ? 1 : 0);
         const int cl = c - g_toff[b], m4b = 4 * g_nk[b];
-        if (b == a) {
-          const double v = sD[a * kDStride + rl * m4b + cl] - acc;
-          sD[a * kDStride + rl * m4b + cl] = v;
-          bad |= !isfinite(v);
-        } else {
-          s.K[m.kblk[9 * (size_t)K + 3 * a + b] + rl * m4b + cl] = -acc;
-          bad |= !isfinite(acc);
-        }
+        double v = (b == a) ? sD[a * DS + rl * m4b + cl] : 0.0;
+#pragma unroll
+        for (int j = 0; j < NP; ++j) v -= me[j] * sR[(f * NP + j) * ldr + c];
+        if (b == a) sD[a * DS + rl * m4b + cl] = v;
+        else s.K[m.kblk[9 * (size_t)K + 3 * a + b] + rl * m4b + cl] = v;
+        bad |= not_finite(v);
       }
     }
     // X (column-major n x (nt+1)) and the interior residual
@@ -435,7 +452,7 @@ __global__ void __launch_bounds__(kCondThreads) k_condense_euler_f64(
         const int c = t / N, r = t - c * N;
         const double v = sR[r * ldr + c];
         xk[t] = v;
-        bad |= !isfinite(v);
+        bad |= not_finite(v);
       }
       double* ru = s.res_u + m.u_off[K];
       for (int t = tid; t < N; t += NT) ru[t] = sNu[t];
@@ -449,7 +466,7 @@ __global__ void __launch_bounds__(kCondThreads) k_condense_euler_f64(
       double* dd = g_side[a] ? s.dhalf1 + m.dblk_off[e] : s.K + m.kblk[9 * (size_t)K + 4 * a];
       double* de = g_side[a] ? s.ehalf1 + lo : s.E + lo;
       double* dr = g_side[a] ? s.rhalf1 + lo : s.res_lam + lo;
-      for (int t = tid; t < m4 * m4; t += NT) dd[t] = sD[a * kDStride + t];
+      for (int t = tid; t < m4 * m4; t += NT) dd[t] = sD[a * DS + t];
       for (int t = tid; t < m4; t += NT) { de[t] = sEh[g_toff[a] + t]; dr[t] = sNl[g_toff[a] + t]; }
     }
     __threadfence();
@@ -468,7 +485,7 @@ __global__ void __launch_bounds__(kCondThreads) k_condense_euler_f64(
       const int side = g_side[a];
       // sum in the fixed order side 0 + side 1
       for (int t = tid; t < m4 * m4; t += NT) {
-        const double mine = sD[a * kDStride + t];
+        const double mine = sD[a * DS + t];
         const double other = side ? __ldcg(k0 + t) : __ldcg(k1 + t);
         k0[t] = side ? other + mine : mine + other;
       }
@@ -516,8 +533,8 @@ template <int P>
 static bool launch_euler_bucket(const DevMesh& m, const DevSys& s, const Phys& ph, const double* tab,
                                 const TabOff& to, const double* U, const double* Lam, const int* elems, int n,
                                 int ntmax, cudaStream_t st, std::string* err) {
-  const int ldr = ldr_for(ntmax);
-  const EulerLayout<P> lay(ldr);
+  const int ldr = ldr_for(ntmax), nkmax = nkmax_for(P, ntmax);
+  const EulerLayout<P> lay(ldr, nkmax);
   const size_t bytes = sizeof(double) * (size_t)lay.total;
   cudaError_t ce = cudaFuncSetAttribute(k_condense_euler_f64<P>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                         (int)bytes);
@@ -529,7 +546,7 @@ static bool launch_euler_bucket(const DevMesh& m, const DevSys& s, const Phys& p
   if (per_sm < 1) { *err = "condensation kernel does not fit on an SM"; return false; }
   long grid = (long)sms * per_sm;
   if (grid > n) grid = n;
-  k_condense_euler_f64<P><<<(int)grid, kCondThreads, bytes, st>>>(m, s, ph, tab, to, U, Lam, elems, n, ldr);
+  k_condense_euler_f64<P><<<(int)grid, kCondThreads, bytes, st>>>(m, s, ph, tab, to, U, Lam, elems, n, ldr, nkmax);
   ce = cudaGetLastError();
   if (ce != cudaSuccess) { *err = cudaGetErrorString(ce); return false; }
   return true;

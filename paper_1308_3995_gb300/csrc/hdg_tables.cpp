@@ -158,6 +158,46 @@ void build_tables(Tables& T) {
         }
     }
   }
+  // derived matrices (products of the tables above, summed in double)
+  for (int p = 1; p <= kMaxP; ++p) {
+    const int np = n_basis(p), nq = (p + 2) * (p + 2);
+    int o = reserve(2 * np * np);
+    T.off.vol_dref[p] = o;
+    for (int r = 0; r < 2; ++r)
+      for (int i = 0; i < np; ++i)
+        for (int j = 0; j < np; ++j) {
+          double acc = 0.0;
+          const int g = r == 0 ? T.off.vol_gxi[p] : T.off.vol_geta[p];
+          for (int q = 0; q < nq; ++q) acc += d[T.off.vol_w[p] + q] * d[g + q * np + i] * d[T.off.vol_phi[p] + q * np + j];
+          d[o + (r * np + i) * np + j] = acc;
+        }
+    for (int pe = p; pe <= kMaxP; ++pe) {
+      const int ne = pe + 2, nk = pe + 1;
+      for (int lf = 0; lf < 3; ++lf) {
+        o = reserve(np * np);
+        T.off.face_mass[p][pe][lf] = o;
+        const int ph = T.off.edge_phi[p][pe][lf][0];
+        for (int i = 0; i < np; ++i)
+          for (int j = 0; j < np; ++j) {
+            double acc = 0.0;
+            for (int g = 0; g < ne; ++g) acc += d[T.off.edge_w[pe] + g] * d[ph + g * np + i] * d[ph + g * np + j];
+            d[o + i * np + j] = acc;
+          }
+        for (int fl = 0; fl < 2; ++fl) {
+          o = reserve(nk * np);
+          T.off.edge_cross[p][pe][lf][fl] = o;
+          const int phf = T.off.edge_phi[p][pe][lf][fl];
+          for (int k = 0; k < nk; ++k)
+            for (int j = 0; j < np; ++j) {
+              double acc = 0.0;
+              for (int g = 0; g < ne; ++g)
+                acc += d[T.off.edge_w[pe] + g] * d[T.off.edge_psi[pe] + g * nk + k] * d[phf + g * np + j];
+              d[o + k * np + j] = acc;
+            }
+        }
+      }
+    }
+  }
 }
 
 // exported for the table cross-check tests (host only, no device needed)
