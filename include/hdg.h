@@ -89,8 +89,12 @@ typedef enum {
 typedef enum { HDG_EULER = 0, HDG_NS_MIXED = 1 } hdg_model;
 
 typedef enum {
-  HDG_FP64 = 0,        /* everything in IEEE binary64 */
-  HDG_MIXED_FP32 = 1   /* local LU / solves / Schur in binary32, refined to FP64 accuracy */
+  HDG_FP64 = 0,    /* element work in IEEE binary64 (the FP64 pipe) */
+  HDG_FLOAT2 = 1   /* element work in float-float arithmetic: every value a pair of
+                      binary32 words (hi + lo, ~48-bit significand) computed with
+                      error-free transformations on the binary32 pipe; inputs and
+                      outputs stay binary64; accuracy ~1e-13 relative (FP64-class),
+                      far above binary32 */
 } hdg_precision;
 
 /* Flow and discretisation parameters (paper Sec. 2 and 3).  Non-dimensional
@@ -108,9 +112,8 @@ typedef struct {
   double cfl;          /* <= 0: pure Newton; > 0: pseudo-time mass |K|-scaled by the local
                           time step CFL |K| / (lambda_c + 4 lambda_v) of Sec. 3.3 */
   double t_inf;        /* dimensional free-stream temperature [K] for Sutherland (288.15) */
-  double refine_tol;   /* mixed precision: stop refining when the FP64 residual of the local
-                          solves is below refine_tol * |[B|F]| (e.g. 1e-13) */
-  int32_t refine_max;  /* mixed precision: at most this many refinement sweeps */
+  double refine_tol;   /* reserved for refinement-based precisions (unused) */
+  int32_t refine_max;  /* reserved for refinement-based precisions (unused) */
   int32_t reserved;
 } hdg_params;
 

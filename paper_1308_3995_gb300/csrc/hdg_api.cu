@@ -18,7 +18,8 @@ struct hdg_ctx {
   int device = 0;
   std::string err;
   Tables tab;
-  double* d_tab = nullptr;
+  double* d_tab = nullptr;   // tables in binary64
+  void* d_tab_ff = nullptr;  // the same tables split into float-float pairs (hi, lo)
 };
 
 struct hdg_mesh {
@@ -97,6 +98,7 @@ PlanRef plan_ref(const hdg_mesh* M) {
   PlanRef r;
   r.device = M->ctx->device;
   r.tab = M->ctx->d_tab;
+  r.tab_ff = M->ctx->d_tab_ff;
   r.off = &M->ctx->tab.off;
   r.dm = &M->dm;
   r.bucket = M->d_bucket;
@@ -125,6 +127,17 @@ hdg_status hdg_create(hdg_ctx** out, int device) {
   if (e != cudaSuccess) { delete ctx; return HDG_ENOMEM; }
   e = cudaMemcpy(ctx->d_tab, ctx->tab.data.data(), sizeof(double) * ctx->tab.data.size(), cudaMemcpyHostToDevice);
   if (e != cudaSuccess) { cudaFree(ctx->d_tab); delete ctx; return HDG_ECUDA; }
+  std::vector<float> split(2 * ctx->tab.data.size());
+  for (size_t i = 0; i < ctx->tab.data.size(); ++i) {
+    const double d = ctx->tab.data[i];
+    const float h = (float)d;
+    split[2 * i] = h;
+    split[2 * i + 1] = (float)(d - (double)h);
+  }
+  e = cudaMalloc(&ctx->d_tab_ff, sizeof(float) * split.size());
+  if (e == cudaSuccess)
+    e = cudaMemcpy(ctx->d_tab_ff, split.data(), sizeof(float) * split.size(), cudaMemcpyHostToDevice);
+  if (e != cudaSuccess) { cudaFree(ctx->d_tab); cudaFree(ctx->d_tab_ff); delete ctx; return HDG_ECUDA; }
   *out = ctx;
   return HDG_OK;
 }
@@ -133,6 +146,7 @@ hdg_status hdg_destroy(hdg_ctx* ctx) {
   if (!ctx) return HDG_EINVAL;
   cudaSetDevice(ctx->device);
   cudaFree(ctx->d_tab);
+  cudaFree(ctx->d_tab_ff);
   delete ctx;
   return HDG_OK;
 }
@@ -337,7 +351,7 @@ hdg_status hdg_sys_create(hdg_ctx* ctx, const hdg_mesh* M, const hdg_params* P, 
   *out = nullptr;
   if ((P->model == HDG_EULER) != (M->nfield == 4) || (P->model != HDG_EULER && P->model != HDG_NS_MIXED))
     return fail(ctx, HDG_EINVAL, "hdg_sys_create: model does not match the mesh's field count");
-  if (P->precision != HDG_FP64)
+  if (P->precision != HDG_FP64 && P->precision != HDG_FLOAT2)
     return fail(ctx, HDG_ENOTSUP, "hdg_sys_create: precision not supported by this build");
   if (P->model != HDG_EULER) return fail(ctx, HDG_ENOTSUP, "hdg_sys_create: model not supported by this build");
   if (!(P->gamma > 1.0) || !(P->alpha > 0.0) || !(P->mach > 0.0))
@@ -354,6 +368,7 @@ hdg_status hdg_sys_create(hdg_ctx* ctx, const hdg_mesh* M, const hdg_params* P, 
   S->ph.suth_s = 110.4 / P->t_inf;
   S->ph.cfl = P->cfl;
   S->ph.model = P->model;
+  S->ph.precision = P->precision;
   const size_t d = sizeof(double);
   void* p[14];
   hdg_status st = HDG_OK;
@@ -404,7 +419,7 @@ hdg_status hdg_condense(hdg_sys* S, const double* U, const double* Lam, void* st
   if (!U || !Lam) return fail(ctx, HDG_EINVAL, "hdg_condense: null input");
   const hdg_mesh* M = S->mesh;
   std::string err;
-  const int n = launch_condense(M->dm, S->ds, S->ph, ctx->d_tab, ctx->tab.off, U, Lam, M->d_bucket, M->bucket_n,
+  const int n = launch_condense(M->dm, S->ds, S->ph, ctx->d_tab, ctx->d_tab_ff, ctx->tab.off, U, Lam, M->d_bucket, M->bucket_n,
                                 M->bucket_ntmax, stream, &err);
   if (n < 0) return fail(ctx, HDG_ECUDA, "hdg_condense: " + err);
   S->launches = n;

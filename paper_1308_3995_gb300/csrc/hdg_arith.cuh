@@ -1,0 +1,166 @@
+// Scalar arithmetic the element kernels are written against, in two flavours:
+//
+//   Ar<double>: IEEE binary64 on the FP64 pipe.
+//   Ar<ff>:     "float-float" (double-word) numbers, value = hi + lo with two
+//               binary32 words, i.e. a ~48-bit significand, computed entirely
+//               on the FP32 pipe, which on GB300 is ~58x wider than the FP64
+//               one.  Built from the classical error-free transformations:
+//               TwoSum (Knuth), FastTwoSum (Dekker, |a| >= |b|) and the
+//               FMA-based exact product error a*b - fl(a*b).  Products follow
+//               the usual double-word scheme (exact hi*hi product plus the two
+//               cross terms, renormalised); sums of double-words add the two
+//               high and the two low words with TwoSum and renormalise twice
+//               (the "accurate" double-word addition).  Accumulations in the
+//               kernels (dot products, LU updates) use a compensated
+//               multiply-add that keeps the running error in the low word
+//               unnormalised; values are renormalised before they are used as
+//               factors.
+//
+// Both flavours expose the same static functions, so one kernel template
+// serves the FP64 path and the float-float path.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <cstdint>
+
+namespace hdg {
+
+struct __align__(8) ff {
+  float hi, lo;
+};
+
+// ------------------------------------------------------------------ error-free transformations
+__device__ __forceinline__ ff two_sum(float a, float b) {
+  const float s = a + b;
+  const float bb = s - a;
+  return {s, (a - (s - bb)) + (b - bb)};
+}
+__device__ __forceinline__ ff fast_two_sum(float a, float b) {  // requires |a| >= |b| (or a == 0)
+  const float s = a + b;
+  return {s, b - (s - a)};
+}
+
+// double -> float-float (hi = nearest float, lo = nearest float of the remainder)
+__device__ __forceinline__ ff ff_from_double(double d) {
+  const float h = __double2float_rn(d);
+  return {h, __double2float_rn(d - (double)h)};
+}
+
+// float-float -> double without the FP64 pipe: hi's exact binary64 pattern is
+// assembled from its bits and lo (|lo| <= half an ulp of hi when normalised)
+// is added to that pattern's significand in integer arithmetic, in units of
+// hi's binary64 ulp (bits of lo below that unit are truncated: < 1 ulp).  A
+// subtraction from a power-of-two hi borrows into the binade below, where the
+// ulp is half as large, so there the integer difference is doubled.
+__device__ __forceinline__ double ff_to_double(ff v) {
+  const unsigned int hb = __float_as_uint(v.hi), lb = __float_as_uint(v.lo);
+  const unsigned int he = (hb >> 23) & 0xffu;
+  const unsigned long long sign = (unsigned long long)(hb & 0x80000000u) << 32;
+  if (he == 0u) return __longlong_as_double((long long)sign);  // zero (subnormal hi flushes to zero)
+  if (he == 0xffu)                                               // inf / nan
+    return __longlong_as_double((long long)(sign | (0x7ffull << 52) | ((unsigned long long)(hb & 0x7fffffu) << 29)));
+  unsigned long long d = sign | ((unsigned long long)(he + 896u) << 52) | ((unsigned long long)(hb & 0x7fffffu) << 29);
+  const unsigned int le = (lb >> 23) & 0xffu;
+  const int sh = (int)le - (int)he + 29;  // lo's significand LSB relative to hi's binary64 ulp
+  const unsigned long long m = 0x800000ull | (unsigned long long)(lb & 0x7fffffu);
+  unsigned long long add = (sh >= 0) ? (m << sh) : (sh > -24 ? (m >> (-sh)) : 0ull);
+  add = (le == 0u) ? 0ull : add;
+  const bool same = ((hb ^ lb) & 0x80000000u) == 0u;
+  const bool pow2 = (hb & 0x7fffffu) == 0u;
+  d = same ? d + add : d - (pow2 ? 2ull * add : add);
+  return __longlong_as_double((long long)d);
+}
+
+template <class T>
+struct Ar;
+
+// ------------------------------------------------------------------ binary64
+template <>
+struct Ar<double> {
+  using T = double;
+  static __device__ __forceinline__ T zero() { return 0.0; }
+  static __device__ __forceinline__ T from_d(double d) { return d; }
+  static __device__ __forceinline__ double to_d(T a) { return a; }
+  static __device__ __forceinline__ T add(T a, T b) { return a + b; }
+  static __device__ __forceinline__ T sub(T a, T b) { return a - b; }
+  static __device__ __forceinline__ T mul(T a, T b) { return a * b; }
+  static __device__ __forceinline__ T neg(T a) { return -a; }
+  // acc += a*b and acc -= a*b (one rounding each)
+  static __device__ __forceinline__ void madd(T& acc, T a, T b) { acc = fma(a, b, acc); }
+  static __device__ __forceinline__ void msub(T& acc, T a, T b) { acc = fma(-a, b, acc); }
+  static __device__ __forceinline__ T norm(T a) { return a; }
+  static __device__ __forceinline__ T rcp(T a) { return __drcp_rn(a); }
+  // |a| as an ordered integer key (for pivot search off the FP pipe) and a non-finite test
+  static __device__ __forceinline__ unsigned long long key(T a) {
+    return (unsigned long long)__double_as_longlong(a) & 0x7fffffffffffffffull;
+  }
+  static __device__ __forceinline__ int bad(T a) { return (__double2hiint(a) & 0x7ff00000) == 0x7ff00000; }
+};
+
+// ------------------------------------------------------------------ float-float
+template <>
+struct Ar<ff> {
+  using T = ff;
+  static __device__ __forceinline__ T zero() { return {0.0f, 0.0f}; }
+  static __device__ __forceinline__ T from_d(double d) { return ff_from_double(d); }
+  static __device__ __forceinline__ double to_d(T a) { return ff_to_double(a); }
+  static __device__ __forceinline__ T add(T a, T b) {
+    ff s = two_sum(a.hi, b.hi);
+    const ff t = two_sum(a.lo, b.lo);
+    s.lo += t.hi;
+    s = fast_two_sum(s.hi, s.lo);
+    s.lo += t.lo;
+    return fast_two_sum(s.hi, s.lo);
+  }
+  static __device__ __forceinline__ T neg(T a) { return {-a.hi, -a.lo}; }
+  static __device__ __forceinline__ T sub(T a, T b) { return add(a, neg(b)); }
+  static __device__ __forceinline__ T mul(T a, T b) {
+    const float p = a.hi * b.hi;
+    float e = fmaf(a.hi, b.hi, -p);
+    e = fmaf(a.hi, b.lo, e);
+    e = fmaf(a.lo, b.hi, e);
+    return fast_two_sum(p, e);
+  }
+  // compensated acc += a*b: the exact error of the leading product and of the
+  // running high-word sum go to the (unnormalised) low word
+  static __device__ __forceinline__ void madd(T& acc, T a, T b) {
+    const float p = a.hi * b.hi;
+    float e = fmaf(a.hi, b.hi, -p);
+    e = fmaf(a.hi, b.lo, e);
+    e = fmaf(a.lo, b.hi, e);
+    const ff s = two_sum(acc.hi, p);
+    acc.hi = s.hi;
+    acc.lo += s.lo + e;
+  }
+  static __device__ __forceinline__ void msub(T& acc, T a, T b) {
+    const float p = a.hi * b.hi;
+    float e = fmaf(a.hi, b.hi, -p);
+    e = fmaf(a.hi, b.lo, e);
+    e = fmaf(a.lo, b.hi, e);
+    const ff s = two_sum(acc.hi, -p);
+    acc.hi = s.hi;
+    acc.lo += s.lo - e;
+  }
+  static __device__ __forceinline__ T norm(T a) { return two_sum(a.hi, a.lo); }
+  // 1/a: binary32 reciprocal refined by one Newton step in double-word arithmetic
+  static __device__ __forceinline__ T rcp(T a) {
+    const float r = __frcp_rn(a.hi);
+    // e = 1 - a*r exactly enough: a*r = 1 + small, computed with the product error
+    const float p = a.hi * r;
+    float e = fmaf(a.hi, r, -p);      // a.hi*r = p + e exactly
+    e = fmaf(a.lo, r, e);
+    const float res = (1.0f - p) - e; // 1 - a*r, |.| ~ 2^-24
+    const ff rr = fast_two_sum(r, r * res);
+    return rr;
+  }
+  static __device__ __forceinline__ unsigned long long key(T a) {
+    return (unsigned long long)(__float_as_uint(a.hi) & 0x7fffffffu);
+  }
+  static __device__ __forceinline__ int bad(T a) { return (__float_as_uint(a.hi) & 0x7f800000u) == 0x7f800000u; }
+};
+
+// table element of type T (double table or its float-float split)
+template <class T>
+__device__ __forceinline__ T tload(const T* p) { return *p; }
+
+}  // namespace hdg

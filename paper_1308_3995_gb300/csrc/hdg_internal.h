@@ -41,7 +41,7 @@ void build_tables(Tables& T);
 // Flow parameters as the kernels use them.
 struct Phys {
   double gamma, alpha, prandtl, mu_inf, suth_s, cfl;
-  int model;
+  int model, precision;
 };
 
 // Device-resident mesh plan handed to kernels by value.
@@ -79,6 +79,7 @@ struct DevSys {
 struct PlanRef {
   int device;
   const double* tab;
+  const void* tab_ff;
   const TabOff* off;
   const DevMesh* dm;
   const int* const* bucket;
@@ -91,9 +92,9 @@ struct PlanRef {
 PlanRef plan_ref(const hdg_mesh* mesh);
 
 // kernel launchers (hdg_kernels.cu); return the number of launches enqueued
-int launch_condense(const DevMesh& m, const DevSys& s, const Phys& ph, const double* tab, const TabOff& off,
-                    const double* U, const double* Lam, const int* const* bucket, const int* bucket_n,
-                    const int* bucket_ntmax, void* stream, std::string* err);
+int launch_condense(const DevMesh& m, const DevSys& s, const Phys& ph, const double* tab, const void* tab_ff,
+                    const TabOff& off, const double* U, const double* Lam, const int* const* bucket,
+                    const int* bucket_n, const int* bucket_ntmax, void* stream, std::string* err);
 int launch_recover_buckets(const DevMesh& m, const double* X, const double* dLam, double* dU,
                            const int* const* bucket, const int* bucket_n, void* stream, std::string* err);
 

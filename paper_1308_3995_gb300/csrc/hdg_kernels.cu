@@ -20,7 +20,9 @@
 
 #include <cmath>
 #include <cstdio>
+#include <type_traits>
 
+#include "hdg_arith.cuh"
 #include "hdg_internal.h"
 
 namespace hdg {
@@ -30,37 +32,34 @@ namespace hdg {
 // p = (gamma - 1)(E - rho |v|^2 / 2), and the flux Jacobians dF_x/dw, dF_y/dw
 // (row-major 4x4), derived by hand from those formulas.
 // --------------------------------------------------------------------------
-__device__ __forceinline__ void euler_flux_jac(const double* w, double gam, double* fx, double* fy, double* Ax,
-                                               double* Ay) {
-  const double rho = w[0], ir = __drcp_rn(rho), u = w[1] * ir, v = w[2] * ir, E = w[3];
-  const double g1 = gam - 1.0;
-  const double q2 = u * u + v * v;
-  const double p = g1 * (E - 0.5 * rho * q2);
-  const double Ep = E + p;
-  const double H = Ep * ir;
-  const double ph2 = 0.5 * g1 * q2;
-  fx[0] = w[1]; fx[1] = w[1] * u + p; fx[2] = w[1] * v; fx[3] = u * Ep;
-  fy[0] = w[2]; fy[1] = w[2] * u;     fy[2] = w[2] * v + p; fy[3] = v * Ep;
-  Ax[0] = 0.0;            Ax[1] = 1.0;              Ax[2] = 0.0;              Ax[3] = 0.0;
-  Ax[4] = ph2 - u * u;    Ax[5] = (3.0 - gam) * u;  Ax[6] = -g1 * v;          Ax[7] = g1;
-  Ax[8] = -u * v;         Ax[9] = v;                Ax[10] = u;               Ax[11] = 0.0;
-  Ax[12] = u * (ph2 - H); Ax[13] = H - g1 * u * u;  Ax[14] = -g1 * u * v;     Ax[15] = gam * u;
-  Ay[0] = 0.0;            Ay[1] = 0.0;              Ay[2] = 1.0;              Ay[3] = 0.0;
-  Ay[4] = -u * v;         Ay[5] = v;                Ay[6] = u;                Ay[7] = 0.0;
-  Ay[8] = ph2 - v * v;    Ay[9] = -g1 * u;          Ay[10] = (3.0 - gam) * v; Ay[11] = g1;
-  Ay[12] = v * (ph2 - H); Ay[13] = -g1 * u * v;     Ay[14] = H - g1 * v * v;  Ay[15] = gam * v;
-}
+template <class T>
+struct EulerConst {  // constants of the physics in the kernel's arithmetic
+  T gam, g1, three_m_gam, half, one;
+};
 
-// --------------------------------------------------------------------------
-// Bit-level helpers that keep pivot search and finiteness checks off the
-// binary64 pipe: for non-negative doubles, IEEE order is the order of the bit
-// patterns as unsigned integers.
-// --------------------------------------------------------------------------
-__device__ __forceinline__ unsigned long long abs_key(double v) {
-  return (unsigned long long)__double_as_longlong(v) & 0x7fffffffffffffffull;
-}
-__device__ __forceinline__ int not_finite(double v) {
-  return (__double2hiint(v) & 0x7ff00000) == 0x7ff00000;
+template <class T>
+__device__ __forceinline__ void euler_flux_jac(const T* w, const EulerConst<T>& C, T* fx, T* fy, T* Ax, T* Ay) {
+  using A = Ar<T>;
+  const T rho = w[0], ir = A::rcp(rho), u = A::mul(w[1], ir), v = A::mul(w[2], ir), E = w[3];
+  const T uu = A::mul(u, u), vv = A::mul(v, v), uv = A::mul(u, v);
+  const T q2 = A::add(uu, vv);
+  const T p = A::mul(C.g1, A::sub(E, A::mul(A::mul(C.half, rho), q2)));
+  const T Ep = A::add(E, p);
+  const T H = A::mul(Ep, ir);
+  const T ph2 = A::mul(A::mul(C.half, C.g1), q2);
+  const T z = A::zero();
+  fx[0] = w[1]; fx[1] = A::add(A::mul(w[1], u), p); fx[2] = A::mul(w[1], v); fx[3] = A::mul(u, Ep);
+  fy[0] = w[2]; fy[1] = A::mul(w[2], u); fy[2] = A::add(A::mul(w[2], v), p); fy[3] = A::mul(v, Ep);
+  const T g1u = A::mul(C.g1, u), g1v = A::mul(C.g1, v), g1uv = A::mul(C.g1, uv);
+  const T phH = A::sub(ph2, H);
+  Ax[0] = z;                 Ax[1] = C.one;                      Ax[2] = z;                        Ax[3] = z;
+  Ax[4] = A::sub(ph2, uu);   Ax[5] = A::mul(C.three_m_gam, u);   Ax[6] = A::neg(g1v);              Ax[7] = C.g1;
+  Ax[8] = A::neg(uv);        Ax[9] = v;                          Ax[10] = u;                       Ax[11] = z;
+  Ax[12] = A::mul(u, phH);   Ax[13] = A::sub(H, A::mul(g1u, u)); Ax[14] = A::neg(g1uv);            Ax[15] = A::mul(C.gam, u);
+  Ay[0] = z;                 Ay[1] = z;                          Ay[2] = C.one;                    Ay[3] = z;
+  Ay[4] = A::neg(uv);        Ay[5] = v;                          Ay[6] = u;                        Ay[7] = z;
+  Ay[8] = A::sub(ph2, vv);   Ay[9] = A::neg(g1u);                Ay[10] = A::mul(C.three_m_gam, v); Ay[11] = C.g1;
+  Ay[12] = A::mul(v, phH);   Ay[13] = A::neg(g1uv);              Ay[14] = A::sub(H, A::mul(g1v, v)); Ay[15] = A::mul(C.gam, v);
 }
 
 // --------------------------------------------------------------------------
@@ -97,63 +96,77 @@ inline int nkmax_for(int p, int ntmax) {
 }
 
 // --------------------------------------------------------------------------
-// Condensation kernel, Euler, binary64: one element per CTA iteration.
+// Condensation kernel, Euler: one element per CTA iteration, in the
+// arithmetic T (binary64, or float-float on the FP32 pipe).  `tab` holds the
+// library's tables in that arithmetic.  Inputs and outputs are binary64.
 // --------------------------------------------------------------------------
-template <int P>
-__global__ void __launch_bounds__(kCondThreads) k_condense_euler_f64(
-    DevMesh m, DevSys s, Phys ph, const double* __restrict__ tab, TabOff to, const double* __restrict__ U,
+template <int P, class T>
+__global__ void __launch_bounds__(kCondThreads, 4) k_condense_euler(
+    DevMesh m, DevSys s, Phys ph, const T* __restrict__ tab, TabOff to, const double* __restrict__ U,
     const double* __restrict__ Lam, const int* __restrict__ elems, int n_elems, int ldr, int nkmax) {
   using L = EulerLayout<P>;
+  using A = Ar<T>;
   constexpr int NP = L::NP, NQ = L::NQ, N = L::N, LDA = L::LDA;
   constexpr int NT = kCondThreads;
-  extern __shared__ double smem[];
+  extern __shared__ double smem_raw[];
+  T* smem = reinterpret_cast<T*>(smem_raw);
   const L lay(ldr, nkmax);
   const int DS = lay.dstride;
-  double* sA = smem + lay.oA;
-  double* sR = smem + lay.oR;
-  double* sU = smem + lay.oU;
-  double* sL = smem + lay.oL;
-  double* sNu = smem + lay.oNu;
-  double* sNl = smem + lay.oNl;
-  double* sEh = smem + lay.oEh;
-  double* sMe = smem + lay.oMe;
-  double* sD = smem + lay.oD;
-  double* scr = smem + lay.oScr;
+  T* sA = smem + lay.oA;
+  T* sR = smem + lay.oR;
+  T* sU = smem + lay.oU;
+  T* sL = smem + lay.oL;
+  T* sNu = smem + lay.oNu;
+  T* sNl = smem + lay.oNl;
+  T* sEh = smem + lay.oEh;
+  T* sMe = smem + lay.oMe;
+  T* sD = smem + lay.oD;
+  T* scr = smem + lay.oScr;
   // volume scratch
-  double* sWq = scr;                  // [4][NQ]
-  double* sFh = sWq + 4 * NQ;         // [2][4][NQ]
-  double* sAh = sFh + 8 * NQ;         // [2][16][NQ]
-  double* sZ = sAh + 32 * NQ;         // [4][NP][NQ]
+  T* sWq = scr;                  // [4][NQ]
+  T* sFh = sWq + 4 * NQ;         // [2][4][NQ]
+  T* sAh = sFh + 8 * NQ;         // [2][16][NQ]
+  T* sZ = sAh + 32 * NQ;         // [4][NP][NQ]
   // face scratch (aliases the volume scratch)
-  double* sFhat = scr;                // [3*6][4]
-  double* sW = sFhat + 3 * kPtSlots * 4;  // [3*6][16][5]
+  T* sFhat = scr;                // [3*6][4]
+  T* sW = sFhat + 3 * kPtSlots * 4;  // [3*6][16][5]
 
-  __shared__ double g_det, g_Ji[2][2], g_n[3][2], g_len[3], g_mt;
+  __shared__ T g_det, g_Ji[2][2], g_n[3][2], g_len[3], g_mt;
   __shared__ int g_e[3], g_pe[3], g_nk[3], g_toff[4], g_fl[3], g_side[3], g_old[3];
-  __shared__ double s_pinv[64];
+  // per trace index c < nt of the element: local face, field, mode
+  __shared__ unsigned char g_cf[kMaxNt], g_cg[kMaxNt], g_cl[kMaxNt];
+  __shared__ T s_pinv[64];
   __shared__ int s_piv, s_bad;
 
   const int tid = threadIdx.x;
-  const double* vw = tab + to.vol_w[P];
-  const double* vphi = tab + to.vol_phi[P];
-  const double* vgx = tab + to.vol_gxi[P];
-  const double* vge = tab + to.vol_geta[P];
-  const double* dref = tab + to.vol_dref[P];
-  const double alpha = ph.alpha;
-  const double g1 = ph.gamma - 1.0;
+  const int tx = tid & 31, ty = tid >> 5;   // lane, warp: 2-D layouts without index division
+  constexpr int NW = NT / 32;
+  const T* vw = tab + to.vol_w[P];
+  const T* vphi = tab + to.vol_phi[P];
+  const T* vgx = tab + to.vol_gxi[P];
+  const T* vge = tab + to.vol_geta[P];
+  const T* dref = tab + to.vol_dref[P];
+  EulerConst<T> C;
+  C.gam = A::from_d(ph.gamma);
+  C.g1 = A::from_d(ph.gamma - 1.0);
+  C.three_m_gam = A::from_d(3.0 - ph.gamma);
+  C.half = A::from_d(0.5);
+  C.one = A::from_d(1.0);
+  const T alpha = A::from_d(ph.alpha);
+  const T zero = A::zero();
 
   for (int it = blockIdx.x; it < n_elems; it += gridDim.x) {
     const int K = elems[it];
-    // ---------------- a1: geometry, faces, state ----------------
-    if (tid < 3) {  // one lane per local face, one warp instruction for all three
+    // ---------------- a1: geometry (binary64, three lanes), faces, state ----------------
+    if (tid < 3) {
       const double* c = m.xy + 6 * (size_t)K;
       const int a = tid, b = (tid + 1) % 3;
       const double dx = c[2 * b] - c[2 * a], dy = c[2 * b + 1] - c[2 * a + 1];
       const double len = sqrt(dx * dx + dy * dy);
       const double il = __drcp_rn(len);
-      g_len[a] = len;
-      g_n[a][0] = dy * il;
-      g_n[a][1] = -dx * il;
+      g_len[a] = A::from_d(len);
+      g_n[a][0] = A::from_d(dy * il);
+      g_n[a][1] = A::from_d(-dx * il);
       const int e = m.elem_face[3 * (size_t)K + a];
       const int info = m.elem_info[K];
       g_e[a] = e;
@@ -165,9 +178,28 @@ __global__ void __launch_bounds__(kCondThreads) k_condense_euler_f64(
         const double J00 = c[2] - c[0], J01 = c[4] - c[0], J10 = c[3] - c[1], J11 = c[5] - c[1];
         const double det = J00 * J11 - J01 * J10;
         const double inv = __drcp_rn(det);
-        g_det = det;
-        g_Ji[0][0] = J11 * inv; g_Ji[0][1] = -J01 * inv;
-        g_Ji[1][0] = -J10 * inv; g_Ji[1][1] = J00 * inv;
+        g_det = A::from_d(det);
+        g_Ji[0][0] = A::from_d(J11 * inv); g_Ji[0][1] = A::from_d(-J01 * inv);
+        g_Ji[1][0] = A::from_d(-J10 * inv); g_Ji[1][1] = A::from_d(J00 * inv);
+        // pseudo-time mass det(J)/dt_K (Sec. 3.3), from the element-mean state
+        double mt = 0.0;
+        if (ph.cfl > 0.0) {
+          const double* u0 = U + m.u_off[K];
+          const double c0 = 1.4142135623730951;  // value of the constant orthonormal mode
+          const double rho = c0 * u0[0], uu = c0 * u0[NP] / rho, vv = c0 * u0[2 * NP] / rho;
+          const double E = c0 * u0[3 * NP];
+          const double p = (ph.gamma - 1.0) * (E - 0.5 * rho * (uu * uu + vv * vv));
+          double perim = 0.0;
+          for (int l = 0; l < 3; ++l) {
+            const int l2 = (l + 1) % 3;
+            const double ex = c[2 * l2] - c[2 * l], ey = c[2 * l2 + 1] - c[2 * l + 1];
+            perim += sqrt(ex * ex + ey * ey);
+          }
+          const double lam_c = (sqrt(uu * uu + vv * vv) + sqrt(ph.gamma * p / rho)) * perim;
+          const double dt = ph.cfl * 0.5 * det / lam_c;
+          mt = det / dt;
+        }
+        g_mt = A::from_d(mt);
         s_bad = 0;
       }
     }
@@ -177,83 +209,77 @@ __global__ void __launch_bounds__(kCondThreads) k_condense_euler_f64(
       g_toff[1] = 4 * g_nk[0];
       g_toff[2] = 4 * (g_nk[0] + g_nk[1]);
       g_toff[3] = 4 * (g_nk[0] + g_nk[1] + g_nk[2]);
-      // pseudo-time mass det(J)/dt_K (Sec. 3.3), from the element-mean state
-      g_mt = 0.0;
-      if (ph.cfl > 0.0) {
-        const double* u0 = U + m.u_off[K];
-        const double c0 = 1.4142135623730951;  // value of the constant orthonormal mode
-        const double rho = c0 * u0[0], uu = c0 * u0[NP] / rho, vv = c0 * u0[2 * NP] / rho;
-        const double E = c0 * u0[3 * NP];
-        const double p = g1 * (E - 0.5 * rho * (uu * uu + vv * vv));
-        const double perim = g_len[0] + g_len[1] + g_len[2];
-        const double lam_c = (sqrt(uu * uu + vv * vv) + sqrt(ph.gamma * p / rho)) * perim;
-        const double dt = ph.cfl * 0.5 * g_det / lam_c;
-        g_mt = g_det / dt;
-      }
+    }
+    {
+      const double* uk = U + m.u_off[K];
+      for (int t = tid; t < N; t += NT) sU[t] = A::from_d(uk[t]);
     }
     __syncthreads();
     const int nt = g_toff[3];
-    {
-      const double* uk = U + m.u_off[K];
-      for (int t = tid; t < N; t += NT) sU[t] = uk[t];
-      for (int a = 0; a < 3; ++a) {
-        const double* lk = Lam + m.lam_off[g_e[a]];
-        for (int t = tid; t < 4 * g_nk[a]; t += NT) sL[g_toff[a] + t] = lk[t];
-      }
+    for (int c = tid; c < nt; c += NT) {
+      const int a = (c >= g_toff[2]) ? 2 : (c >= g_toff[1] ? 1 : 0);
+      const int nk = g_nk[a], cl = c - g_toff[a], g = cl / nk;
+      g_cf[c] = (unsigned char)a;
+      g_cg[c] = (unsigned char)g;
+      g_cl[c] = (unsigned char)(cl - g * nk);
+    }
+    for (int a = 0; a < 3; ++a) {
+      const double* lk = Lam + m.lam_off[g_e[a]];
+      for (int t = tid; t < 4 * g_nk[a]; t += NT) sL[g_toff[a] + t] = A::from_d(lk[t]);
     }
     __syncthreads();
 
     // ---------------- a2: volume quadrature ----------------
     for (int t = tid; t < 4 * NQ; t += NT) {
       const int f = t / NQ, q = t - f * NQ;
-      double acc = 0.0;
+      T acc = zero;
 #pragma unroll
-      for (int j = 0; j < NP; ++j) acc += sU[f * NP + j] * vphi[q * NP + j];
-      sWq[t] = acc;
+      for (int j = 0; j < NP; ++j) A::madd(acc, sU[f * NP + j], vphi[q * NP + j]);
+      sWq[t] = A::norm(acc);
     }
     __syncthreads();
     for (int q = tid; q < NQ; q += NT) {
-      double w[4], fx[4], fy[4], Ax[16], Ay[16];
+      T w[4], fx[4], fy[4], Ax[16], Ay[16];
 #pragma unroll
       for (int f = 0; f < 4; ++f) w[f] = sWq[f * NQ + q];
-      euler_flux_jac(w, ph.gamma, fx, fy, Ax, Ay);
-      const double c = vw[q] * g_det;
+      euler_flux_jac(w, C, fx, fy, Ax, Ay);
+      const T c = A::mul(vw[q], g_det);
 #pragma unroll
       for (int r = 0; r < 2; ++r) {
-        const double a0 = c * g_Ji[r][0], a1 = c * g_Ji[r][1];
+        const T a0 = A::mul(c, g_Ji[r][0]), a1 = A::mul(c, g_Ji[r][1]);
 #pragma unroll
-        for (int f = 0; f < 4; ++f) sFh[(r * 4 + f) * NQ + q] = a0 * fx[f] + a1 * fy[f];
+        for (int f = 0; f < 4; ++f) sFh[(r * 4 + f) * NQ + q] = A::add(A::mul(a0, fx[f]), A::mul(a1, fy[f]));
         // rows 1..3 only: row 0 of both flux Jacobians is constant
 #pragma unroll
-        for (int fg = 4; fg < 16; ++fg) sAh[(r * 16 + fg) * NQ + q] = a0 * Ax[fg] + a1 * Ay[fg];
+        for (int fg = 4; fg < 16; ++fg) sAh[(r * 16 + fg) * NQ + q] = A::add(A::mul(a0, Ax[fg]), A::mul(a1, Ay[fg]));
       }
     }
     __syncthreads();
     // interior residual, volume part: N_w = -(grad phi, f_c(w))_K
     for (int t = tid; t < N; t += NT) {
       const int f = t / NP, i = t - f * NP;
-      double acc = 0.0;
+      T acc0 = zero, acc1 = zero;
       for (int q = 0; q < NQ; ++q) {
-        acc -= vgx[q * NP + i] * sFh[f * NQ + q];
-        acc -= vge[q * NP + i] * sFh[(4 + f) * NQ + q];
+        A::msub(acc0, vgx[q * NP + i], sFh[f * NQ + q]);
+        A::msub(acc1, vge[q * NP + i], sFh[(4 + f) * NQ + q]);
       }
-      sNu[t] = acc;
+      sNu[t] = A::add(A::norm(acc0), A::norm(acc1));
     }
     // volume Jacobian A_fg = -sum_k (dF_k/dw)_fg D_k.  Blocks whose flux-Jacobian
     // entries are constants (row 0: (0,1) = -D_x, (0,2) = -D_y, (0,0) = (0,3) = 0;
     // (1,3) = -(gamma-1) D_x; (2,3) = -(gamma-1) D_y) use D_k = det J sum_r Ji[r][k] Dref_r.
     for (int t = tid; t < NP * NP; t += NT) {
       const int i = t / NP, j = t - i * NP;
-      const double d0 = dref[t], d1 = dref[NP * NP + t];
-      const double Dx = g_det * (g_Ji[0][0] * d0 + g_Ji[1][0] * d1);
-      const double Dy = g_det * (g_Ji[0][1] * d0 + g_Ji[1][1] * d1);
-      double* a0 = sA + i * LDA + j;  // block row 0
-      a0[0] = 0.0;
-      a0[NP] = -Dx;
-      a0[2 * NP] = -Dy;
-      a0[3 * NP] = 0.0;
-      sA[(NP + i) * LDA + 3 * NP + j] = -g1 * Dx;
-      sA[(2 * NP + i) * LDA + 3 * NP + j] = -g1 * Dy;
+      const T d0 = dref[t], d1 = dref[NP * NP + t];
+      const T Dx = A::mul(g_det, A::add(A::mul(g_Ji[0][0], d0), A::mul(g_Ji[1][0], d1)));
+      const T Dy = A::mul(g_det, A::add(A::mul(g_Ji[0][1], d0), A::mul(g_Ji[1][1], d1)));
+      T* a0 = sA + i * LDA + j;  // block row 0
+      a0[0] = zero;
+      a0[NP] = A::neg(Dx);
+      a0[2 * NP] = A::neg(Dy);
+      a0[3 * NP] = zero;
+      sA[(NP + i) * LDA + 3 * NP + j] = A::neg(A::mul(C.g1, Dx));
+      sA[(2 * NP + i) * LDA + 3 * NP + j] = A::neg(A::mul(C.g1, Dy));
     }
     // state-dependent blocks, one block row f = 1..3 at a time (row 3 has four):
     //   Z_g[i][q] = sum_r dphi_i/dxi_r (q) Ahat_r,fg(q);  A_fg[i][j] = -sum_q Z_g[i][q] phi_j(q)
@@ -261,16 +287,21 @@ __global__ void __launch_bounds__(kCondThreads) k_condense_euler_f64(
       const int ng = (f == 3) ? 4 : 3;
       for (int t = tid; t < ng * NP * NQ; t += NT) {
         const int g = t / (NP * NQ), rem = t - g * NP * NQ, i = rem / NQ, q = rem - i * NQ;
-        sZ[t] = vgx[q * NP + i] * sAh[(f * 4 + g) * NQ + q] + vge[q * NP + i] * sAh[(16 + f * 4 + g) * NQ + q];
+        sZ[t] = A::add(A::mul(vgx[q * NP + i], sAh[(f * 4 + g) * NQ + q]),
+                       A::mul(vge[q * NP + i], sAh[(16 + f * 4 + g) * NQ + q]));
       }
       __syncthreads();
       for (int t = tid; t < ng * NP * NP; t += NT) {
         const int g = t / (NP * NP), rem = t - g * NP * NP, i = rem / NP, j = rem - i * NP;
-        const double* z = sZ + (g * NP + i) * NQ;
-        double acc = 0.0;
-#pragma unroll 5
-        for (int q = 0; q < NQ; ++q) acc -= z[q] * vphi[q * NP + j];
-        sA[(f * NP + i) * LDA + g * NP + j] = acc;
+        const T* z = sZ + (g * NP + i) * NQ;
+        T acc0 = zero, acc1 = zero;
+#pragma unroll 4
+        for (int q = 0; q + 1 < NQ; q += 2) {
+          A::msub(acc0, z[q], vphi[q * NP + j]);
+          A::msub(acc1, z[q + 1], vphi[(q + 1) * NP + j]);
+        }
+        if (NQ & 1) A::msub(acc0, z[NQ - 1], vphi[(NQ - 1) * NP + j]);
+        sA[(f * NP + i) * LDA + g * NP + j] = A::add(A::norm(acc0), A::norm(acc1));
       }
       __syncthreads();
     }
@@ -280,100 +311,115 @@ __global__ void __launch_bounds__(kCondThreads) k_condense_euler_f64(
       const int a = t / kPtSlots, g = t - a * kPtSlots;
       const int pe = g_pe[a], nk = pe + 1;
       if (g < pe + 2) {
-        const double* phe = tab + to.edge_phi[P][pe][a][g_fl[a]] + g * NP;
-        const double* ps = tab + to.edge_psi[pe] + g * nk;
-        const double we = tab[to.edge_w[pe] + g] * g_len[a];
-        double w[4], lam[4], fx[4], fy[4], Ax[16], Ay[16];
+        const T* phe = tab + to.edge_phi[P][pe][a][g_fl[a]] + g * NP;
+        const T* ps = tab + to.edge_psi[pe] + g * nk;
+        const T we = A::mul(tab[to.edge_w[pe] + g], g_len[a]);
+        T w[4], lam[4], fx[4], fy[4], Ax[16], Ay[16];
 #pragma unroll
         for (int f = 0; f < 4; ++f) {
-          double acc = 0.0;
+          T acc = zero;
 #pragma unroll
-          for (int j = 0; j < NP; ++j) acc += sU[f * NP + j] * phe[j];
-          w[f] = acc;
-          double al = 0.0;
-          for (int k = 0; k < nk; ++k) al += sL[g_toff[a] + f * nk + k] * ps[k];
-          lam[f] = al;
+          for (int j = 0; j < NP; ++j) A::madd(acc, sU[f * NP + j], phe[j]);
+          w[f] = A::norm(acc);
+          T al = zero;
+          for (int k = 0; k < nk; ++k) A::madd(al, sL[g_toff[a] + f * nk + k], ps[k]);
+          lam[f] = A::norm(al);
         }
-        euler_flux_jac(lam, ph.gamma, fx, fy, Ax, Ay);
-        const double nx = g_n[a][0], ny = g_n[a][1];
+        euler_flux_jac(lam, C, fx, fy, Ax, Ay);
+        const T nx = g_n[a][0], ny = g_n[a][1];
 #pragma unroll
-        for (int f = 0; f < 4; ++f) sFhat[t * 4 + f] = we * (nx * fx[f] + ny * fy[f] - alpha * (lam[f] - w[f]));
+        for (int f = 0; f < 4; ++f)
+          sFhat[t * 4 + f] = A::mul(we, A::sub(A::add(A::mul(nx, fx[f]), A::mul(ny, fy[f])),
+                                               A::mul(alpha, A::sub(lam[f], w[f]))));
 #pragma unroll
         for (int fg = 0; fg < 16; ++fg) {
-          const double at = we * (nx * Ax[fg] + ny * Ay[fg] - ((fg % 5 == 0) ? alpha : 0.0));
-          for (int l = 0; l < nk; ++l) sW[(t * 16 + fg) * 5 + l] = at * ps[l];
+          T an = A::add(A::mul(nx, Ax[fg]), A::mul(ny, Ay[fg]));
+          if (fg % 5 == 0) an = A::sub(an, alpha);
+          const T at = A::mul(we, an);
+          for (int l = 0; l < nk; ++l) sW[(t * 16 + fg) * 5 + l] = A::mul(at, ps[l]);
         }
       }
     }
     __syncthreads();
-    // B = d N_w / d Lambda: rows (f,i), columns (face a; g, l)
-    for (int t = tid; t < N * nt; t += NT) {
-      const int r = t / nt, c = t - r * nt;
+    // B = d N_w / d Lambda: rows (f,i) over warps, columns (face a; g, l) over lanes
+    for (int r = ty; r < N; r += NW) {
       const int f = r / NP, i = r - f * NP;
-      const int a = (c >= g_toff[2]) ? 2 : (c >= g_toff[1] ? 1 : 0);
-      const int nk = g_nk[a], cl = c - g_toff[a], g = cl / nk, l = cl - g * nk;
-      const double* phe = tab + to.edge_phi[P][g_pe[a]][a][g_fl[a]];
-      double acc = 0.0;
-      for (int q = 0; q < nk + 1; ++q) acc += phe[q * NP + i] * sW[((a * kPtSlots + q) * 16 + f * 4 + g) * 5 + l];
-      sR[r * ldr + c] = acc;
+      for (int c = tx; c < nt; c += 32) {
+        const int a = g_cf[c], g = g_cg[c], l = g_cl[c], nk = g_nk[a];
+        const T* phe = tab + to.edge_phi[P][g_pe[a]][a][g_fl[a]];
+        T acc = zero;
+        for (int q = 0; q < nk + 1; ++q) A::madd(acc, phe[q * NP + i], sW[((a * kPtSlots + q) * 16 + f * 4 + g) * 5 + l]);
+        sR[r * ldr + c] = A::norm(acc);
+      }
     }
-    // D_a = d N_lambda,a / d Lambda_a (block diagonal in faces)
+    // D_a = d N_lambda,a / d Lambda_a (block diagonal in faces): rows over warps, columns over lanes
     for (int a = 0; a < 3; ++a) {
-      const int nk = g_nk[a], m4 = 4 * nk;
-      const double* ps = tab + to.edge_psi[g_pe[a]];
-      for (int t = tid; t < m4 * m4; t += NT) {
-        const int r = t / m4, c = t - r * m4, f = r / nk, k = r - f * nk, g = c / nk, l = c - g * nk;
-        double acc = 0.0;
-        for (int q = 0; q < nk + 1; ++q) acc += ps[q * nk + k] * sW[((a * kPtSlots + q) * 16 + f * 4 + g) * 5 + l];
-        sD[a * DS + t] = acc;
+      const int nk = g_nk[a], m4 = 4 * nk, o = g_toff[a];
+      const T* ps = tab + to.edge_psi[g_pe[a]];
+      for (int r = ty; r < m4; r += NW) {
+        const int f = g_cg[o + r], k = g_cl[o + r];
+        for (int c = tx; c < m4; c += 32) {
+          const int g = g_cg[o + c], l = g_cl[o + c];
+          T acc = zero;
+          for (int q = 0; q < nk + 1; ++q) A::madd(acc, ps[q * nk + k], sW[((a * kPtSlots + q) * 16 + f * 4 + g) * 5 + l]);
+          sD[a * DS + r * m4 + c] = A::norm(acc);
+        }
       }
     }
     // C_a = alpha |e_a| <psi_k, phi_j> delta_fg, kept as the scalar edge matrix
     for (int t = tid; t < 3 * 5 * NP; t += NT) {
       const int a = t / (5 * NP), rem = t - a * 5 * NP, k = rem / NP;
-      if (k < g_nk[a]) sMe[t] = alpha * g_len[a] * tab[to.edge_cross[P][g_pe[a]][a][g_fl[a]] + rem];
+      if (k < g_nk[a]) sMe[t] = A::mul(A::mul(alpha, g_len[a]), tab[to.edge_cross[P][g_pe[a]][a][g_fl[a]] + rem]);
     }
     // face parts of the residuals
     for (int t = tid; t < N; t += NT) {
       const int f = t / NP, i = t - f * NP;
-      double acc = 0.0;
+      T acc = sNu[t];
       for (int a = 0; a < 3; ++a) {
-        const double* phe = tab + to.edge_phi[P][g_pe[a]][a][g_fl[a]];
-        for (int q = 0; q < g_pe[a] + 2; ++q) acc += phe[q * NP + i] * sFhat[(a * kPtSlots + q) * 4 + f];
+        const T* phe = tab + to.edge_phi[P][g_pe[a]][a][g_fl[a]];
+        for (int q = 0; q < g_pe[a] + 2; ++q) A::madd(acc, phe[q * NP + i], sFhat[(a * kPtSlots + q) * 4 + f]);
       }
-      sNu[t] += acc;
+      sNu[t] = A::norm(acc);
     }
     for (int t = tid; t < nt; t += NT) {
       const int a = (t >= g_toff[2]) ? 2 : (t >= g_toff[1] ? 1 : 0);
       const int nk = g_nk[a], tl = t - g_toff[a], f = tl / nk, k = tl - f * nk;
-      const double* ps = tab + to.edge_psi[g_pe[a]];
-      double acc = 0.0;
-      for (int q = 0; q < nk + 1; ++q) acc += ps[q * nk + k] * sFhat[(a * kPtSlots + q) * 4 + f];
+      const T* ps = tab + to.edge_psi[g_pe[a]];
+      T acc = zero;
+      for (int q = 0; q < nk + 1; ++q) A::madd(acc, ps[q * nk + k], sFhat[(a * kPtSlots + q) * 4 + f]);
+      acc = A::norm(acc);
       sNl[t] = acc;
-      sEh[t] = -acc;  // H
+      sEh[t] = A::neg(acc);  // H
     }
     __syncthreads();
     // face mass alpha <phi_i, phi_j>_dK on every field's diagonal block, plus the pseudo-time mass
     for (int t = tid; t < NP * NP; t += NT) {
       const int i = t / NP, j = t - i * NP;
-      double v = 0.0;
-      for (int a = 0; a < 3; ++a) v += g_len[a] * tab[to.face_mass[P][g_pe[a]][a] + t];
-      v = alpha * v + ((i == j) ? g_mt : 0.0);
+      T v = zero;
+      for (int a = 0; a < 3; ++a) A::madd(v, g_len[a], tab[to.face_mass[P][g_pe[a]][a] + t]);
+      v = A::mul(alpha, A::norm(v));
+      if (i == j) v = A::add(v, g_mt);
 #pragma unroll
-      for (int f = 0; f < 4; ++f) sA[(f * NP + i) * LDA + f * NP + j] += v;
+      for (int f = 0; f < 4; ++f) {
+        T* p = &sA[(f * NP + i) * LDA + f * NP + j];
+        *p = A::add(*p, v);
+      }
     }
-    for (int t = tid; t < N; t += NT) sR[t * ldr + nt] = -sNu[t];  // F
+    for (int t = tid; t < N; t += NT) sR[t * ldr + nt] = A::neg(sNu[t]);  // F
     __syncthreads();
 
     // ---------------- a4/a5: LU with partial pivoting on [A | B | F] ----------------
     const int nr1 = nt + 1;
     for (int k = 0; k < N; ++k) {
       if (tid < 32) {
+        // renormalise column k (the multipliers of this step), then pick the pivot
         unsigned long long best = 0ull;
         int bi = k;
         for (int i = k + tid; i < N; i += 32) {
-          const unsigned long long v = abs_key(sA[i * LDA + k]);
-          if (v > best) { best = v; bi = i; }
+          const T v = A::norm(sA[i * LDA + k]);
+          sA[i * LDA + k] = v;
+          const unsigned long long kv = A::key(v);
+          if (kv > best) { best = kv; bi = i; }
         }
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) {
@@ -383,79 +429,128 @@ __global__ void __launch_bounds__(kCondThreads) k_condense_euler_f64(
         }
         if (tid == 0) {
           s_piv = bi;
-          if (best == 0ull) { s_bad |= 1; s_pinv[k] = 0.0; } else { s_pinv[k] = __drcp_rn(sA[bi * LDA + k]); }
+          if (best == 0ull) { s_bad |= 1; s_pinv[k] = zero; } else { s_pinv[k] = A::rcp(sA[bi * LDA + k]); }
         }
       }
       __syncthreads();
       // swap rows k and piv (columns k..N-1 of A and all of [B|F]); scale the new row k by 1/pivot
       {
         const int piv = s_piv;
-        const double pinv = s_pinv[k];
+        const T pinv = s_pinv[k];
         const int wa = N - k;
         for (int t = tid; t < wa + nr1; t += NT) {
-          double* pk = (t < wa) ? &sA[k * LDA + k + t] : &sR[k * ldr + (t - wa)];
-          double* pp = (t < wa) ? &sA[piv * LDA + k + t] : &sR[piv * ldr + (t - wa)];
-          const double vk = *pk, vp = *pp;
+          T* pk = (t < wa) ? &sA[k * LDA + k + t] : &sR[k * ldr + (t - wa)];
+          T* pp = (t < wa) ? &sA[piv * LDA + k + t] : &sR[piv * ldr + (t - wa)];
+          const T vk = *pk, vp = *pp;
           if (piv != k) *pp = vk;
-          *pk = vp * pinv;
+          *pk = A::mul(A::norm(vp), pinv);
         }
       }
       __syncthreads();
       {
-        const int nr = N - k - 1, wa = N - k - 1, nc = wa + nr1;
-        for (int t = tid; t < nr * nc; t += NT) {
-          const int ii = t / nc, c = t - ii * nc, i = k + 1 + ii;
-          const double l = sA[i * LDA + k];
-          if (c < wa) sA[i * LDA + k + 1 + c] -= l * sA[k * LDA + k + 1 + c];
-          else sR[i * ldr + (c - wa)] -= l * sR[k * ldr + (c - wa)];
+        // rows over warps, the combined columns [A(k+1..N-1) | B | F] over lanes
+        const int wa = N - k - 1, nc = wa + nr1;
+        if constexpr (std::is_same<T, double>::value) {
+          for (int i = k + 1 + ty; i < N; i += NW) {
+            const T l = sA[i * LDA + k];
+            for (int c = tx; c < nc; c += 32) {
+              const bool inA = c < wa;
+              T* dst = inA ? &sA[i * LDA + k + 1 + c] : &sR[i * ldr + (c - wa)];
+              const T* src = inA ? &sA[k * LDA + k + 1 + c] : &sR[k * ldr + (c - wa)];
+              A::msub(*dst, l, *src);
+            }
+          }
+        } else {
+          for (int i = k + 1 + ty; i < N; i += NW) {
+            const T l = sA[i * LDA + k];
+            for (int c0 = 0; c0 < nc; c0 += 128) {
+              // up to four independent update chains per thread: loads, arithmetic, stores
+              T dv[4], sv[4];
+              T* dp[4];
+#pragma unroll
+              for (int u = 0; u < 4; ++u) {
+                const int c = c0 + tx + 32 * u;
+                const bool inA = c < wa;
+                dp[u] = inA ? &sA[i * LDA + k + 1 + c] : &sR[i * ldr + (c - wa)];
+                if (c < nc) {
+                  dv[u] = *dp[u];
+                  sv[u] = inA ? sA[k * LDA + k + 1 + c] : sR[k * ldr + (c - wa)];
+                }
+              }
+#pragma unroll
+              for (int u = 0; u < 4; ++u)
+                if (c0 + tx + 32 * u < nc) A::msub(dv[u], l, sv[u]);
+#pragma unroll
+              for (int u = 0; u < 4; ++u)
+                if (c0 + tx + 32 * u < nc) *dp[u] = dv[u];
+            }
+          }
         }
       }
       __syncthreads();
     }
-    // back substitution with the unit upper triangle
+    // back substitution with the unit upper triangle (row k is renormalised before use)
     for (int k = N - 1; k > 0; --k) {
-      for (int t = tid; t < k * nr1; t += NT) {
-        const int i = t / nr1, c = t - i * nr1;
-        sR[i * ldr + c] -= sA[i * LDA + k] * sR[k * ldr + c];
+      if constexpr (!std::is_same<T, double>::value) {
+        for (int t = tid; t < nr1; t += NT) sR[k * ldr + t] = A::norm(sR[k * ldr + t]);
+        __syncthreads();
+      }
+      for (int i = ty; i < k; i += NW) {
+        const T u = sA[i * LDA + k];
+        for (int c0 = 0; c0 < nr1; c0 += 64) {
+          const int ca = c0 + tx, cb = c0 + tx + 32;
+          T da, db, sa, sb;
+          if (ca < nr1) { da = sR[i * ldr + ca]; sa = sR[k * ldr + ca]; }
+          if (cb < nr1) { db = sR[i * ldr + cb]; sb = sR[k * ldr + cb]; }
+          if (ca < nr1) A::msub(da, u, sa);
+          if (cb < nr1) A::msub(db, u, sb);
+          if (ca < nr1) sR[i * ldr + ca] = da;
+          if (cb < nr1) sR[i * ldr + cb] = db;
+        }
       }
       __syncthreads();
     }
-
-    // ---------------- a6/a7: Schur complement, E_K, assembly ----------------
+    // X (column-major n x (nt+1)) and the interior residual; X renormalised in place
     int bad = 0;
-    for (int t = tid; t < nt * nr1; t += NT) {
-      const int r = t / nr1, c = t - r * nr1;
-      const int a = (r >= g_toff[2]) ? 2 : (r >= g_toff[1] ? 1 : 0);
-      const int nka = g_nk[a], rl = r - g_toff[a], f = rl / nka, k = rl - f * nka;
-      const double* me = sMe + (a * 5 + k) * NP;
-      if (c == nt) {
-        double v = sEh[r];
-#pragma unroll
-        for (int j = 0; j < NP; ++j) v -= me[j] * sR[(f * NP + j) * ldr + c];
-        sEh[r] = v;
-        bad |= not_finite(v);
-      } else {
-        const int b = (c >= g_toff[2]) ? 2 : (c >= g_toff[1] ? 1 : 0);
-        const int cl = c - g_toff[b], m4b = 4 * g_nk[b];
-        double v = (b == a) ? sD[a * DS + rl * m4b + cl] : 0.0;
-#pragma unroll
-        for (int j = 0; j < NP; ++j) v -= me[j] * sR[(f * NP + j) * ldr + c];
-        if (b == a) sD[a * DS + rl * m4b + cl] = v;
-        else s.K[m.kblk[9 * (size_t)K + 3 * a + b] + rl * m4b + cl] = v;
-        bad |= not_finite(v);
-      }
-    }
-    // X (column-major n x (nt+1)) and the interior residual
     {
       double* xk = s.X + m.x_off[K];
       for (int t = tid; t < N * nr1; t += NT) {
         const int c = t / N, r = t - c * N;
-        const double v = sR[r * ldr + c];
-        xk[t] = v;
-        bad |= not_finite(v);
+        const T v = A::norm(sR[r * ldr + c]);
+        sR[r * ldr + c] = v;
+        xk[t] = A::to_d(v);
+        bad |= A::bad(v);
       }
       double* ru = s.res_u + m.u_off[K];
-      for (int t = tid; t < N; t += NT) ru[t] = sNu[t];
+      for (int t = tid; t < N; t += NT) ru[t] = A::to_d(sNu[t]);
+    }
+    __syncthreads();
+
+    // ---------------- a6/a7: Schur complement, E_K, assembly ----------------
+    // rows (face a; f, k) over warps, columns (face b; g, l | E) over lanes
+    for (int r = ty; r < nt; r += NW) {
+      const int a = g_cf[r], f = g_cg[r], k = g_cl[r], rl = r - g_toff[a];
+      const T* me = sMe + (a * 5 + k) * NP;
+      for (int c = tx; c < nr1; c += 32) {
+        if (c == nt) {
+          T v = sEh[r];
+#pragma unroll
+          for (int j = 0; j < NP; ++j) A::msub(v, me[j], sR[(f * NP + j) * ldr + c]);
+          v = A::norm(v);
+          sEh[r] = v;
+          bad |= A::bad(v);
+        } else {
+          const int b = g_cf[c];
+          const int cl = c - g_toff[b], m4b = 4 * g_nk[b];
+          T v = (b == a) ? sD[a * DS + rl * m4b + cl] : zero;
+#pragma unroll
+          for (int j = 0; j < NP; ++j) A::msub(v, me[j], sR[(f * NP + j) * ldr + c]);
+          v = A::norm(v);
+          if (b == a) sD[a * DS + rl * m4b + cl] = v;
+          else s.K[m.kblk[9 * (size_t)K + 3 * a + b] + rl * m4b + cl] = A::to_d(v);
+          bad |= A::bad(v);
+        }
+      }
     }
     if (bad) atomicOr(&s_bad, 2);
     __syncthreads();
@@ -466,8 +561,11 @@ __global__ void __launch_bounds__(kCondThreads) k_condense_euler_f64(
       double* dd = g_side[a] ? s.dhalf1 + m.dblk_off[e] : s.K + m.kblk[9 * (size_t)K + 4 * a];
       double* de = g_side[a] ? s.ehalf1 + lo : s.E + lo;
       double* dr = g_side[a] ? s.rhalf1 + lo : s.res_lam + lo;
-      for (int t = tid; t < m4 * m4; t += NT) dd[t] = sD[a * DS + t];
-      for (int t = tid; t < m4; t += NT) { de[t] = sEh[g_toff[a] + t]; dr[t] = sNl[g_toff[a] + t]; }
+      for (int t = tid; t < m4 * m4; t += NT) dd[t] = A::to_d(sD[a * DS + t]);
+      for (int t = tid; t < m4; t += NT) {
+        de[t] = A::to_d(sEh[g_toff[a] + t]);
+        dr[t] = A::to_d(sNl[g_toff[a] + t]);
+      }
     }
     __threadfence();
     __syncthreads();
@@ -483,14 +581,14 @@ __global__ void __launch_bounds__(kCondThreads) k_condense_euler_f64(
       double* k0 = s.K + m.kblk[9 * (size_t)K + 4 * a];
       const double* k1 = s.dhalf1 + m.dblk_off[e];
       const int side = g_side[a];
-      // sum in the fixed order side 0 + side 1
+      // sum in binary64, in the fixed order side 0 + side 1
       for (int t = tid; t < m4 * m4; t += NT) {
-        const double mine = sD[a * DS + t];
+        const double mine = A::to_d(sD[a * DS + t]);
         const double other = side ? __ldcg(k0 + t) : __ldcg(k1 + t);
         k0[t] = side ? other + mine : mine + other;
       }
       for (int t = tid; t < m4; t += NT) {
-        const double me_ = sEh[g_toff[a] + t], mr = sNl[g_toff[a] + t];
+        const double me_ = A::to_d(sEh[g_toff[a] + t]), mr = A::to_d(sNl[g_toff[a] + t]);
         const double oe = side ? __ldcg(s.E + lo + t) : __ldcg(s.ehalf1 + lo + t);
         const double orr = side ? __ldcg(s.res_lam + lo + t) : __ldcg(s.rhalf1 + lo + t);
         s.E[lo + t] = side ? oe + me_ : me_ + oe;
@@ -529,44 +627,57 @@ __global__ void k_recover_f64(DevMesh m, const double* __restrict__ X, const dou
 // --------------------------------------------------------------------------
 // launchers
 // --------------------------------------------------------------------------
-template <int P>
-static bool launch_euler_bucket(const DevMesh& m, const DevSys& s, const Phys& ph, const double* tab,
-                                const TabOff& to, const double* U, const double* Lam, const int* elems, int n,
-                                int ntmax, cudaStream_t st, std::string* err) {
+template <int P, class T>
+static bool launch_euler_bucket(const DevMesh& m, const DevSys& s, const Phys& ph, const T* tab, const TabOff& to,
+                                const double* U, const double* Lam, const int* elems, int n, int ntmax,
+                                cudaStream_t st, std::string* err) {
   const int ldr = ldr_for(ntmax), nkmax = nkmax_for(P, ntmax);
   const EulerLayout<P> lay(ldr, nkmax);
-  const size_t bytes = sizeof(double) * (size_t)lay.total;
-  cudaError_t ce = cudaFuncSetAttribute(k_condense_euler_f64<P>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+  const size_t bytes = sizeof(T) * (size_t)lay.total;
+  cudaError_t ce = cudaFuncSetAttribute(k_condense_euler<P, T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                         (int)bytes);
   if (ce != cudaSuccess) { *err = cudaGetErrorString(ce); return false; }
   int dev = 0, sms = 0, per_sm = 0;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_condense_euler_f64<P>, kCondThreads, bytes);
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_condense_euler<P, T>, kCondThreads, bytes);
   if (per_sm < 1) { *err = "condensation kernel does not fit on an SM"; return false; }
   long grid = (long)sms * per_sm;
   if (grid > n) grid = n;
-  k_condense_euler_f64<P><<<(int)grid, kCondThreads, bytes, st>>>(m, s, ph, tab, to, U, Lam, elems, n, ldr, nkmax);
+  k_condense_euler<P, T><<<(int)grid, kCondThreads, bytes, st>>>(m, s, ph, tab, to, U, Lam, elems, n, ldr, nkmax);
   ce = cudaGetLastError();
   if (ce != cudaSuccess) { *err = cudaGetErrorString(ce); return false; }
   return true;
 }
 
-int launch_condense(const DevMesh& m, const DevSys& s, const Phys& ph, const double* tab, const TabOff& to,
-                    const double* U, const double* Lam, const int* const* bucket, const int* bucket_n,
-                    const int* bucket_ntmax, void* stream, std::string* err) {
+template <class T>
+static bool launch_euler_p(int p, const DevMesh& m, const DevSys& s, const Phys& ph, const T* tab, const TabOff& to,
+                           const double* U, const double* Lam, const int* elems, int n, int ntmax, cudaStream_t st,
+                           std::string* err) {
+  switch (p) {
+    case 1: return launch_euler_bucket<1, T>(m, s, ph, tab, to, U, Lam, elems, n, ntmax, st, err);
+    case 2: return launch_euler_bucket<2, T>(m, s, ph, tab, to, U, Lam, elems, n, ntmax, st, err);
+    case 3: return launch_euler_bucket<3, T>(m, s, ph, tab, to, U, Lam, elems, n, ntmax, st, err);
+    case 4: return launch_euler_bucket<4, T>(m, s, ph, tab, to, U, Lam, elems, n, ntmax, st, err);
+  }
+  *err = "degree out of range";
+  return false;
+}
+
+int launch_condense(const DevMesh& m, const DevSys& s, const Phys& ph, const double* tab, const void* tab_ff,
+                    const TabOff& to, const double* U, const double* Lam, const int* const* bucket,
+                    const int* bucket_n, const int* bucket_ntmax, void* stream, std::string* err) {
   cudaStream_t st = (cudaStream_t)stream;
   int launches = 0;
+  if (ph.model != 0) { *err = "model not supported by this kernel set"; return -1; }
   for (int p = 1; p <= kMaxP; ++p) {
     if (bucket_n[p] == 0) continue;
-    bool ok = false;
-    if (ph.model != 0) { *err = "model not supported by this kernel set"; return -1; }
-    switch (p) {
-      case 1: ok = launch_euler_bucket<1>(m, s, ph, tab, to, U, Lam, bucket[p], bucket_n[p], bucket_ntmax[p], st, err); break;
-      case 2: ok = launch_euler_bucket<2>(m, s, ph, tab, to, U, Lam, bucket[p], bucket_n[p], bucket_ntmax[p], st, err); break;
-      case 3: ok = launch_euler_bucket<3>(m, s, ph, tab, to, U, Lam, bucket[p], bucket_n[p], bucket_ntmax[p], st, err); break;
-      case 4: ok = launch_euler_bucket<4>(m, s, ph, tab, to, U, Lam, bucket[p], bucket_n[p], bucket_ntmax[p], st, err); break;
-    }
+    bool ok;
+    if (ph.precision == HDG_FP64)
+      ok = launch_euler_p<double>(p, m, s, ph, tab, to, U, Lam, bucket[p], bucket_n[p], bucket_ntmax[p], st, err);
+    else
+      ok = launch_euler_p<ff>(p, m, s, ph, (const ff*)tab_ff, to, U, Lam, bucket[p], bucket_n[p], bucket_ntmax[p],
+                              st, err);
     if (!ok) return -1;
     ++launches;
   }

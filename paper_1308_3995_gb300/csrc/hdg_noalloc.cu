@@ -116,8 +116,9 @@ extern "C" hdg_status hdg_condense_noalloc(const hdg_mesh* mesh, const hdg_param
   ph.suth_s = 110.4 / P->t_inf;
   ph.cfl = P->cfl;
   ph.model = P->model;
+  ph.precision = P->precision;
   std::string err;
-  const int n = launch_condense(*pr.dm, ds, ph, pr.tab, *pr.off, U, Lam, pr.bucket, pr.bucket_n, pr.bucket_ntmax,
+  const int n = launch_condense(*pr.dm, ds, ph, pr.tab, pr.tab_ff, *pr.off, U, Lam, pr.bucket, pr.bucket_n, pr.bucket_ntmax,
                                 stream, &err);
   if (n < 0) {
     *pr.err = "hdg_condense_noalloc: " + err;

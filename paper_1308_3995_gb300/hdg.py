@@ -22,7 +22,7 @@ _lib = None
 
 HDG_OK, HDG_EINVAL, HDG_ENOMEM, HDG_ECUDA, HDG_ESINGULAR, HDG_ETIMEOUT, HDG_ENOTSUP = range(7)
 HDG_EULER, HDG_NS_MIXED = 0, 1
-HDG_FP64, HDG_MIXED_FP32 = 0, 1
+HDG_FP64, HDG_FLOAT2 = 0, 1
 STATUS_NAMES = {0: "HDG_OK", 1: "HDG_EINVAL", 2: "HDG_ENOMEM", 3: "HDG_ECUDA", 4: "HDG_ESINGULAR",
                 5: "HDG_ETIMEOUT", 6: "HDG_ENOTSUP"}
 

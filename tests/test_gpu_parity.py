@@ -29,10 +29,10 @@ def build_case(wl):
     return case, om, U, Lam, dLam
 
 
-def run_gpu(ctx, case, wl, U, Lam, dLam, cfl=0.0, repeat=1):
+def run_gpu(ctx, case, wl, U, Lam, dLam, cfl=0.0, repeat=1, precision=0):
     from paper_1308_3995_gb300 import hdg
     mesh = hdg.Mesh(ctx, case.mesh.elem_xy, case.mesh.elem_vid, case.elem_p, case.nfield)
-    sysm = hdg.System(ctx, mesh, lib_params(wl, cfl))
+    sysm = hdg.System(ctx, mesh, lib_params(wl, cfl, precision))
     dev = torch.device("cuda:0")
     Ut = torch.from_numpy(U).to(dev)
     Lt = torch.from_numpy(Lam).to(dev)
@@ -56,10 +56,10 @@ def assert_layout_equal(mesh, om):
         assert np.array_equal(np.asarray(a).ravel(), np.asarray(b).ravel()), name
 
 
-def full_parity(ctx, wl, cfl=0.0):
+def full_parity(ctx, wl, cfl=0.0, precision=0, tol=TOL):
     """Every element and every face of a small case, element by element."""
     case, om, U, Lam, dLam = build_case(wl)
-    mesh, sysm, (g,) = run_gpu(ctx, case, wl, U, Lam, dLam, cfl)
+    mesh, sysm, (g,) = run_gpu(ctx, case, wl, U, Lam, dLam, cfl, precision=precision)
     assert_layout_equal(mesh, om)
     assert np.all(g["status"] == 0)
     chk = ParityChecker(om, oracle_params(wl, cfl), U, Lam, dLam, g)
@@ -67,10 +67,47 @@ def full_parity(ctx, wl, cfl=0.0):
     # plain normwise relative errors over the mesh, for the record
     r = om.condense(oracle_params(wl, cfl), U, Lam)
     info = {"normwise E": rel_err(g["E"], r["E"]), "normwise dU": rel_err(g["dU"], om.recover(r["X"], dLam))}
-    print(wl.name, {k: f"{v:.1e}" for k, v in {**errs, **info}.items()})
+    print(wl.name, ["fp64", "float2"][precision], {k: f"{v:.1e}" for k, v in {**errs, **info}.items()})
     for k, v in errs.items():
-        assert v < TOL, (k, v)
+        assert v < tol, (k, v)
     return errs
+
+
+# float-float path (binary32 pairs on the FP32 pipe): bar 1e-10 (mixed-precision tolerance)
+TOL_MIXED = 1e-10
+
+
+@pytest.mark.parametrize("name,nx,ny,kw", [
+    ("euler_p1_256", 8, 16, {}),
+    ("euler_p3_16k", 6, 8, {}),
+    ("euler_p3_16k", 5, 6, {"p": 4}),
+    ("ns_mixp_65k", 7, 5, {"model": 0}),
+    ("euler_p3_262k_shock", 8, 12, {}),
+])
+def test_float2_parity(ctx, name, nx, ny, kw):
+    wl = G.small_variant(G.WORKLOADS[name], nx, ny, **kw)
+    errs = full_parity(ctx, wl, precision=1, tol=TOL_MIXED)
+    # float-float carries ~48 bits: it lands far inside the mixed bar
+    assert max(errs.values()) < 1e-11
+
+
+def test_float2_pseudo_time(ctx):
+    wl = G.small_variant(G.WORKLOADS["euler_p3_16k"], 5, 6, p=3)
+    full_parity(ctx, wl, cfl=10.0, precision=1, tol=TOL_MIXED)
+
+
+def test_float2_full_size_config2_sampled(ctx):
+    wl = G.WORKLOADS["euler_p3_16k"]
+    case, om, U, Lam, dLam = build_case(wl)
+    mesh, sysm, (g,) = run_gpu(ctx, case, wl, U, Lam, dLam, precision=1)
+    assert np.all(g["status"] == 0)
+    rng = np.random.default_rng(6)
+    faces = rng.choice(om.n_face, 16, replace=False)
+    elems = sorted(set(int(k) for f in faces for k in om.face_el[f]) | set(int(k) for k in rng.choice(om.n_elem, 16)))
+    errs = ParityChecker(om, oracle_params(wl), U, Lam, dLam, g).run(elems, faces)
+    print(wl.name, "float2", {k: f"{v:.1e}" for k, v in errs.items()})
+    for k, v in errs.items():
+        assert v < TOL_MIXED, (k, v)
 
 
 def test_config1_euler_p1_256(ctx):
