@@ -353,7 +353,8 @@ hdg_status hdg_sys_create(hdg_ctx* ctx, const hdg_mesh* M, const hdg_params* P, 
     return fail(ctx, HDG_EINVAL, "hdg_sys_create: model does not match the mesh's field count");
   if (P->precision != HDG_FP64 && P->precision != HDG_FLOAT2)
     return fail(ctx, HDG_ENOTSUP, "hdg_sys_create: precision not supported by this build");
-  if (P->model != HDG_EULER) return fail(ctx, HDG_ENOTSUP, "hdg_sys_create: model not supported by this build");
+  if (P->model == HDG_NS_MIXED && !(P->reynolds > 0.0 && P->prandtl > 0.0 && P->t_inf > 0.0))
+    return fail(ctx, HDG_EINVAL, "hdg_sys_create: Navier-Stokes needs reynolds, prandtl, t_inf > 0");
   if (!(P->gamma > 1.0) || !(P->alpha > 0.0) || !(P->mach > 0.0))
     return fail(ctx, HDG_EINVAL, "hdg_sys_create: need gamma > 1, alpha > 0, mach > 0");
   if (cudaSetDevice(ctx->device) != cudaSuccess) return fail(ctx, HDG_ECUDA, "cudaSetDevice failed");

@@ -159,8 +159,80 @@ struct Ar<ff> {
   static __device__ __forceinline__ int bad(T a) { return (__float_as_uint(a.hi) & 0x7f800000u) == 0x7f800000u; }
 };
 
-// table element of type T (double table or its float-float split)
-template <class T>
-__device__ __forceinline__ T tload(const T* p) { return *p; }
+// square roots (used only by the viscous flux: T^{3/2} in Sutherland's law)
+__device__ __forceinline__ double ar_sqrt(double a) { return sqrt(a); }
+__device__ __forceinline__ ff ar_sqrt(ff a) {
+  // binary32 root refined by one Newton step in double-word arithmetic: r + (a - r^2) / (2 r)
+  const float r = sqrtf(a.hi);
+  const float p = r * r;
+  const float e = fmaf(r, r, -p);                      // r^2 = p + e exactly
+  const float res = ((a.hi - p) - e) + a.lo;           // a - r^2
+  return fast_two_sum(r, res * (0.5f / r));
+}
+
+// Forward-mode dual number with ND tangent directions, over the arithmetic T.
+template <class T, int ND>
+struct Dual {
+  T v;
+  T d[ND];
+};
+template <class T, int ND>
+__device__ __forceinline__ Dual<T, ND> dconst(T c) {
+  Dual<T, ND> r;
+  r.v = c;
+#pragma unroll
+  for (int i = 0; i < ND; ++i) r.d[i] = Ar<T>::zero();
+  return r;
+}
+template <class T, int ND>
+__device__ __forceinline__ Dual<T, ND> dadd(const Dual<T, ND>& a, const Dual<T, ND>& b) {
+  Dual<T, ND> r;
+  r.v = Ar<T>::add(a.v, b.v);
+#pragma unroll
+  for (int i = 0; i < ND; ++i) r.d[i] = Ar<T>::add(a.d[i], b.d[i]);
+  return r;
+}
+template <class T, int ND>
+__device__ __forceinline__ Dual<T, ND> dsub(const Dual<T, ND>& a, const Dual<T, ND>& b) {
+  Dual<T, ND> r;
+  r.v = Ar<T>::sub(a.v, b.v);
+#pragma unroll
+  for (int i = 0; i < ND; ++i) r.d[i] = Ar<T>::sub(a.d[i], b.d[i]);
+  return r;
+}
+template <class T, int ND>
+__device__ __forceinline__ Dual<T, ND> dmul(const Dual<T, ND>& a, const Dual<T, ND>& b) {
+  Dual<T, ND> r;
+  r.v = Ar<T>::mul(a.v, b.v);
+#pragma unroll
+  for (int i = 0; i < ND; ++i) r.d[i] = Ar<T>::add(Ar<T>::mul(a.v, b.d[i]), Ar<T>::mul(a.d[i], b.v));
+  return r;
+}
+template <class T, int ND>
+__device__ __forceinline__ Dual<T, ND> dscale(const Dual<T, ND>& a, T s) {
+  Dual<T, ND> r;
+  r.v = Ar<T>::mul(a.v, s);
+#pragma unroll
+  for (int i = 0; i < ND; ++i) r.d[i] = Ar<T>::mul(a.d[i], s);
+  return r;
+}
+template <class T, int ND>
+__device__ __forceinline__ Dual<T, ND> drcp(const Dual<T, ND>& a) {  // 1/a, d(1/a) = -da / a^2
+  Dual<T, ND> r;
+  r.v = Ar<T>::rcp(a.v);
+  const T m = Ar<T>::neg(Ar<T>::mul(r.v, r.v));
+#pragma unroll
+  for (int i = 0; i < ND; ++i) r.d[i] = Ar<T>::mul(a.d[i], m);
+  return r;
+}
+template <class T, int ND>
+__device__ __forceinline__ Dual<T, ND> dsqrt(const Dual<T, ND>& a) {  // d sqrt(a) = da / (2 sqrt(a))
+  Dual<T, ND> r;
+  r.v = ar_sqrt(a.v);
+  const T h = Ar<T>::mul(Ar<T>::from_d(0.5), Ar<T>::rcp(r.v));
+#pragma unroll
+  for (int i = 0; i < ND; ++i) r.d[i] = Ar<T>::mul(a.d[i], h);
+  return r;
+}
 
 }  // namespace hdg

@@ -95,6 +95,9 @@ PlanRef plan_ref(const hdg_mesh* mesh);
 int launch_condense(const DevMesh& m, const DevSys& s, const Phys& ph, const double* tab, const void* tab_ff,
                     const TabOff& off, const double* U, const double* Lam, const int* const* bucket,
                     const int* bucket_n, const int* bucket_ntmax, void* stream, std::string* err);
+int launch_condense_ns(const DevMesh& m, const DevSys& s, const Phys& ph, const double* tab, const void* tab_ff,
+                       const TabOff& off, const double* U, const double* Lam, const int* const* bucket,
+                       const int* bucket_n, const int* bucket_ntmax, void* stream, std::string* err);
 int launch_recover_buckets(const DevMesh& m, const double* X, const double* dLam, double* dU,
                            const int* const* bucket, const int* bucket_n, void* stream, std::string* err);
 

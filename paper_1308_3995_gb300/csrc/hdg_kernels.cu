@@ -23,44 +23,10 @@
 #include <type_traits>
 
 #include "hdg_arith.cuh"
+#include "hdg_physics.cuh"
 #include "hdg_internal.h"
 
 namespace hdg {
-
-// --------------------------------------------------------------------------
-// Euler physics (Sec. 2.1): flux f_c = (rho v, rho v (x) v + p Id, v (E + p)),
-// p = (gamma - 1)(E - rho |v|^2 / 2), and the flux Jacobians dF_x/dw, dF_y/dw
-// (row-major 4x4), derived by hand from those formulas.
-// --------------------------------------------------------------------------
-template <class T>
-struct EulerConst {  // constants of the physics in the kernel's arithmetic
-  T gam, g1, three_m_gam, half, one;
-};
-
-template <class T>
-__device__ __forceinline__ void euler_flux_jac(const T* w, const EulerConst<T>& C, T* fx, T* fy, T* Ax, T* Ay) {
-  using A = Ar<T>;
-  const T rho = w[0], ir = A::rcp(rho), u = A::mul(w[1], ir), v = A::mul(w[2], ir), E = w[3];
-  const T uu = A::mul(u, u), vv = A::mul(v, v), uv = A::mul(u, v);
-  const T q2 = A::add(uu, vv);
-  const T p = A::mul(C.g1, A::sub(E, A::mul(A::mul(C.half, rho), q2)));
-  const T Ep = A::add(E, p);
-  const T H = A::mul(Ep, ir);
-  const T ph2 = A::mul(A::mul(C.half, C.g1), q2);
-  const T z = A::zero();
-  fx[0] = w[1]; fx[1] = A::add(A::mul(w[1], u), p); fx[2] = A::mul(w[1], v); fx[3] = A::mul(u, Ep);
-  fy[0] = w[2]; fy[1] = A::mul(w[2], u); fy[2] = A::add(A::mul(w[2], v), p); fy[3] = A::mul(v, Ep);
-  const T g1u = A::mul(C.g1, u), g1v = A::mul(C.g1, v), g1uv = A::mul(C.g1, uv);
-  const T phH = A::sub(ph2, H);
-  Ax[0] = z;                 Ax[1] = C.one;                      Ax[2] = z;                        Ax[3] = z;
-  Ax[4] = A::sub(ph2, uu);   Ax[5] = A::mul(C.three_m_gam, u);   Ax[6] = A::neg(g1v);              Ax[7] = C.g1;
-  Ax[8] = A::neg(uv);        Ax[9] = v;                          Ax[10] = u;                       Ax[11] = z;
-  Ax[12] = A::mul(u, phH);   Ax[13] = A::sub(H, A::mul(g1u, u)); Ax[14] = A::neg(g1uv);            Ax[15] = A::mul(C.gam, u);
-  Ay[0] = z;                 Ay[1] = z;                          Ay[2] = C.one;                    Ay[3] = z;
-  Ay[4] = A::neg(uv);        Ay[5] = v;                          Ay[6] = u;                        Ay[7] = z;
-  Ay[8] = A::sub(ph2, vv);   Ay[9] = A::neg(g1u);                Ay[10] = A::mul(C.three_m_gam, v); Ay[11] = C.g1;
-  Ay[12] = A::mul(v, phH);   Ay[13] = A::neg(g1uv);              Ay[14] = A::sub(H, A::mul(g1v, v)); Ay[15] = A::mul(C.gam, v);
-}
 
 // --------------------------------------------------------------------------
 // Shared-memory layout of the Euler element kernel (offsets in doubles).
@@ -669,7 +635,8 @@ int launch_condense(const DevMesh& m, const DevSys& s, const Phys& ph, const dou
                     const int* bucket_n, const int* bucket_ntmax, void* stream, std::string* err) {
   cudaStream_t st = (cudaStream_t)stream;
   int launches = 0;
-  if (ph.model != 0) { *err = "model not supported by this kernel set"; return -1; }
+  if (ph.model == HDG_NS_MIXED)
+    return launch_condense_ns(m, s, ph, tab, tab_ff, to, U, Lam, bucket, bucket_n, bucket_ntmax, stream, err);
   for (int p = 1; p <= kMaxP; ++p) {
     if (bucket_n[p] == 0) continue;
     bool ok;

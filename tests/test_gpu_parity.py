@@ -110,6 +110,26 @@ def test_float2_full_size_config2_sampled(ctx):
         assert v < TOL_MIXED, (k, v)
 
 
+@pytest.mark.parametrize("p", [1, 2, 3, 4])
+@pytest.mark.parametrize("precision", [0, 1])
+def test_ns_uniform_p(ctx, p, precision):
+    """Navier-Stokes mixed form (12 fields), Re 5000, Pr 0.72: q eliminated in-element."""
+    wl = G.small_variant(G.WORKLOADS["ns_mixp_65k"], 4, 3, p=p, probs=None)
+    full_parity(ctx, wl, precision=precision, tol=[TOL, TOL_MIXED][precision])
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+def test_ns_mixed_p(ctx, precision):
+    """Config-3 degree mix (40/30/20/10 %, p_e = max) on a small jittered mesh."""
+    wl = G.small_variant(G.WORKLOADS["ns_mixp_65k"], 5, 4)
+    full_parity(ctx, wl, precision=precision, tol=[TOL, TOL_MIXED][precision])
+
+
+def test_ns_pseudo_time(ctx):
+    wl = G.small_variant(G.WORKLOADS["ns_mixp_65k"], 4, 3, p=2, probs=None)
+    full_parity(ctx, wl, cfl=10.0)
+
+
 def test_config1_euler_p1_256(ctx):
     """256 triangles, Euler p = 1, Mach 0.5 + density bump: every output element by element."""
     full_parity(ctx, G.WORKLOADS["euler_p1_256"])
