@@ -154,6 +154,20 @@ int64_t hdg_footprint_bytes(const hdg_mesh* mesh, const hdg_params* params);
 /* Allocate a system (X, K, E, residuals, per-element status, work space) on
  * the mesh's device.  params->model must match the mesh's nfield. */
 hdg_status hdg_sys_create(hdg_ctx* ctx, const hdg_mesh* mesh, const hdg_params* params, hdg_sys** out);
+
+/* Bytes of device workspace a system on this mesh needs (the same figure as
+ * hdg_footprint_bytes): every buffer of the system rounded up to 256 bytes. */
+int64_t hdg_sys_workspace_bytes(const hdg_mesh* mesh, const hdg_params* params);
+
+/* Like hdg_sys_create, but every buffer of the system is carved out of the
+ * caller's DEVICE workspace (256-byte aligned, at least
+ * hdg_sys_workspace_bytes); the library allocates no device memory for it and
+ * hdg_sys_destroy frees nothing of it.  The workspace must outlive the system.
+ * Lets a scheduler admit requests against its own pre-allocated arena (and
+ * never call cudaMalloc/cudaFree, which synchronise the device, while other
+ * requests are running). */
+hdg_status hdg_sys_create_in(hdg_ctx* ctx, const hdg_mesh* mesh, const hdg_params* params, void* workspace,
+                             int64_t workspace_bytes, hdg_sys** out);
 hdg_status hdg_sys_destroy(hdg_sys* sys);
 
 /* One Newton step's element work (Sec. 3.4, paper's Eqs. hdg_ls1-hdg_cont,
@@ -180,6 +194,14 @@ hdg_status hdg_recover(hdg_sys* sys, const double* dLam, double* dU, void* strea
  * solve, which is outside this library. */
 hdg_status hdg_step_host(hdg_sys* sys, const double* U, const double* Lam, const double* dLam, double* dU,
                          void* stream);
+
+/* hdg_step_host without the final synchronisation: everything is enqueued on
+ * `stream` and the call returns at once; dU is valid (and U, Lam, dLam may be
+ * reused) only after the stream has synchronised.  The host buffers must be
+ * page-locked (pinned) for the copies to be asynchronous.  This is the call a
+ * scheduler uses to keep several requests in flight on several streams. */
+hdg_status hdg_step_host_async(hdg_sys* sys, const double* U, const double* Lam, const double* dLam, double* dU,
+                               void* stream);
 
 /* Device views of the outputs (owned by sys, valid until hdg_sys_destroy):
  * X [x_len], K_vals [k_len], E [lam_len], res_u [u_len] = interior residual

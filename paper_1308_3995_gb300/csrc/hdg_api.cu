@@ -44,6 +44,7 @@ struct hdg_sys {
   double *d_U = nullptr, *d_Lam = nullptr, *d_dLam = nullptr, *d_dU = nullptr;
   std::vector<void*> allocs;
   int launches = 0;
+  bool need_zero = true;
 };
 
 namespace {
@@ -336,28 +337,38 @@ hdg_status hdg_mesh_layout(const hdg_mesh* M, int32_t* face_vid, int32_t* face_e
   return HDG_OK;
 }
 
-int64_t hdg_footprint_bytes(const hdg_mesh* M, const hdg_params* P) {
-  if (!M || !P) return -1;
-  const int64_t d = sizeof(double);
-  int64_t b = d * (M->x_len + M->k_len + M->lam_len + M->u_len + M->lam_len);  // X, K, E, res_u, res_lam
-  b += sizeof(int32_t) * (int64_t)M->n_elem;                                      // status
-  b += d * (M->dh_len + 2 * M->lam_len) + sizeof(int32_t) * (int64_t)M->n_face;   // two-sided sums
-  b += d * (2 * M->u_len + 2 * M->lam_len);                                       // host-step staging
-  return b;
+int64_t hdg_footprint_bytes(const hdg_mesh* M, const hdg_params* P) { return hdg_sys_workspace_bytes(M, P); }
+
+}  // extern "C"
+
+namespace {
+
+constexpr int kSysBufs = 14;  // X, K, E, res_u, res_lam, status, dhalf1, ehalf1, rhalf1, face_cnt, U, Lam, dLam, dU
+
+void sys_sizes(const hdg_mesh* M, size_t* sz) {
+  const size_t d = sizeof(double);
+  const size_t v[kSysBufs] = {d * M->x_len,   d * M->k_len,   d * M->lam_len, d * M->u_len,   d * M->lam_len,
+                              4 * (size_t)M->n_elem, d * M->dh_len, d * M->lam_len, d * M->lam_len,
+                              4 * (size_t)M->n_face, d * M->u_len,  d * M->lam_len, d * M->lam_len, d * M->u_len};
+  for (int i = 0; i < kSysBufs; ++i) sz[i] = v[i];
+}
+inline size_t round256(size_t b) { return (b + 255) & ~size_t(255); }
+
+hdg_status sys_validate(hdg_ctx* ctx, const hdg_mesh* M, const hdg_params* P, const char* who) {
+  const std::string w(who);
+  if ((P->model == HDG_EULER) != (M->nfield == 4) || (P->model != HDG_EULER && P->model != HDG_NS_MIXED))
+    return fail(ctx, HDG_EINVAL, w + ": model does not match the mesh's field count");
+  if (P->precision != HDG_FP64 && P->precision != HDG_FLOAT2)
+    return fail(ctx, HDG_ENOTSUP, w + ": precision not supported by this build");
+  if (P->model == HDG_NS_MIXED && !(P->reynolds > 0.0 && P->prandtl > 0.0 && P->t_inf > 0.0))
+    return fail(ctx, HDG_EINVAL, w + ": Navier-Stokes needs reynolds, prandtl, t_inf > 0");
+  if (!(P->gamma > 1.0) || !(P->alpha > 0.0) || !(P->mach > 0.0))
+    return fail(ctx, HDG_EINVAL, w + ": need gamma > 1, alpha > 0, mach > 0");
+  if (cudaSetDevice(ctx->device) != cudaSuccess) return fail(ctx, HDG_ECUDA, "cudaSetDevice failed");
+  return HDG_OK;
 }
 
-hdg_status hdg_sys_create(hdg_ctx* ctx, const hdg_mesh* M, const hdg_params* P, hdg_sys** out) {
-  if (!ctx || !M || !P || !out) return HDG_EINVAL;
-  *out = nullptr;
-  if ((P->model == HDG_EULER) != (M->nfield == 4) || (P->model != HDG_EULER && P->model != HDG_NS_MIXED))
-    return fail(ctx, HDG_EINVAL, "hdg_sys_create: model does not match the mesh's field count");
-  if (P->precision != HDG_FP64 && P->precision != HDG_FLOAT2)
-    return fail(ctx, HDG_ENOTSUP, "hdg_sys_create: precision not supported by this build");
-  if (P->model == HDG_NS_MIXED && !(P->reynolds > 0.0 && P->prandtl > 0.0 && P->t_inf > 0.0))
-    return fail(ctx, HDG_EINVAL, "hdg_sys_create: Navier-Stokes needs reynolds, prandtl, t_inf > 0");
-  if (!(P->gamma > 1.0) || !(P->alpha > 0.0) || !(P->mach > 0.0))
-    return fail(ctx, HDG_EINVAL, "hdg_sys_create: need gamma > 1, alpha > 0, mach > 0");
-  if (cudaSetDevice(ctx->device) != cudaSuccess) return fail(ctx, HDG_ECUDA, "cudaSetDevice failed");
+hdg_sys* sys_new(hdg_ctx* ctx, const hdg_mesh* M, const hdg_params* P) {
   hdg_sys* S = new hdg_sys();
   S->ctx = ctx;
   S->mesh = M;
@@ -370,15 +381,10 @@ hdg_status hdg_sys_create(hdg_ctx* ctx, const hdg_mesh* M, const hdg_params* P, 
   S->ph.cfl = P->cfl;
   S->ph.model = P->model;
   S->ph.precision = P->precision;
-  const size_t d = sizeof(double);
-  void* p[14];
-  hdg_status st = HDG_OK;
-  const size_t sizes[13] = {d * M->x_len,   d * M->k_len,   d * M->lam_len, d * M->u_len, d * M->lam_len,
-                            4 * (size_t)M->n_elem, d * M->dh_len, d * M->lam_len, d * M->lam_len,
-                            4 * (size_t)M->n_face, d * M->u_len, d * M->lam_len, d * M->lam_len};
-  for (int i = 0; i < 13; ++i)
-    if ((st = dalloc(ctx, S->allocs, sizes[i], &p[i]))) { free_all(S->allocs); delete S; return st; }
-  if ((st = dalloc(ctx, S->allocs, d * M->u_len, &p[13]))) { free_all(S->allocs); delete S; return st; }
+  return S;
+}
+
+void sys_bind(hdg_sys* S, void* const* p) {
   S->ds.X = (double*)p[0];
   S->ds.K = (double*)p[1];
   S->ds.E = (double*)p[2];
@@ -393,15 +399,57 @@ hdg_status hdg_sys_create(hdg_ctx* ctx, const hdg_mesh* M, const hdg_params* P, 
   S->d_Lam = (double*)p[11];
   S->d_dLam = (double*)p[12];
   S->d_dU = (double*)p[13];
-  cudaError_t e = cudaMemset(S->ds.face_cnt, 0, 4 * (size_t)M->n_face);
-  if (e == cudaSuccess) e = cudaMemset(S->ds.K, 0, d * M->k_len);
-  if (e == cudaSuccess) e = cudaMemset(S->ds.status, 0, 4 * (size_t)M->n_elem);
-  if (e == cudaSuccess) e = cudaDeviceSynchronize();
-  if (e != cudaSuccess) {
-    free_all(S->allocs);
-    delete S;
-    return fail(ctx, HDG_ECUDA, std::string("hdg_sys_create: ") + cudaGetErrorString(e));
+  S->need_zero = true;  // arrival counters are cleared on the stream of the first condensation
+}
+
+}  // namespace
+
+extern "C" {
+
+int64_t hdg_sys_workspace_bytes(const hdg_mesh* M, const hdg_params* P) {
+  if (!M || !P) return -1;
+  size_t sz[kSysBufs], tot = 0;
+  sys_sizes(M, sz);
+  for (int i = 0; i < kSysBufs; ++i) tot += round256(sz[i]);
+  return (int64_t)tot;
+}
+
+hdg_status hdg_sys_create(hdg_ctx* ctx, const hdg_mesh* M, const hdg_params* P, hdg_sys** out) {
+  if (!ctx || !M || !P || !out) return HDG_EINVAL;
+  *out = nullptr;
+  hdg_status st = sys_validate(ctx, M, P, "hdg_sys_create");
+  if (st != HDG_OK) return st;
+  hdg_sys* S = sys_new(ctx, M, P);
+  size_t sz[kSysBufs];
+  sys_sizes(M, sz);
+  void* p[kSysBufs];
+  for (int i = 0; i < kSysBufs; ++i)
+    if ((st = dalloc(ctx, S->allocs, sz[i], &p[i]))) { free_all(S->allocs); delete S; return st; }
+  sys_bind(S, p);
+  *out = S;
+  return HDG_OK;
+}
+
+hdg_status hdg_sys_create_in(hdg_ctx* ctx, const hdg_mesh* M, const hdg_params* P, void* workspace,
+                             int64_t workspace_bytes, hdg_sys** out) {
+  if (!ctx || !M || !P || !out) return HDG_EINVAL;
+  *out = nullptr;
+  hdg_status st = sys_validate(ctx, M, P, "hdg_sys_create_in");
+  if (st != HDG_OK) return st;
+  const int64_t need = hdg_sys_workspace_bytes(M, P);
+  if (!workspace || ((uintptr_t)workspace & 255u) != 0 || workspace_bytes < need)
+    return fail(ctx, HDG_EINVAL, "hdg_sys_create_in: workspace must be 256-byte aligned and hold " +
+                                     std::to_string(need) + " bytes");
+  hdg_sys* S = sys_new(ctx, M, P);
+  size_t sz[kSysBufs];
+  sys_sizes(M, sz);
+  void* p[kSysBufs];
+  unsigned char* w = (unsigned char*)workspace;
+  for (int i = 0; i < kSysBufs; ++i) {
+    p[i] = w;
+    w += round256(sz[i]);
   }
+  sys_bind(S, p);
   *out = S;
   return HDG_OK;
 }
@@ -419,6 +467,10 @@ hdg_status hdg_condense(hdg_sys* S, const double* U, const double* Lam, void* st
   hdg_ctx* ctx = S->ctx;
   if (!U || !Lam) return fail(ctx, HDG_EINVAL, "hdg_condense: null input");
   const hdg_mesh* M = S->mesh;
+  if (S->need_zero) {
+    HDG_CK(ctx, cudaMemsetAsync(S->ds.face_cnt, 0, 4 * (size_t)M->n_face, (cudaStream_t)stream));
+    S->need_zero = false;
+  }
   std::string err;
   const int n = launch_condense(M->dm, S->ds, S->ph, ctx->d_tab, ctx->d_tab_ff, ctx->tab.off, U, Lam, M->d_bucket, M->bucket_n,
                                 M->bucket_ntmax, stream, &err);
@@ -439,11 +491,11 @@ hdg_status hdg_recover(hdg_sys* S, const double* dLam, double* dU, void* stream)
   return HDG_OK;
 }
 
-hdg_status hdg_step_host(hdg_sys* S, const double* U, const double* Lam, const double* dLam, double* dU,
-                         void* stream) {
+hdg_status hdg_step_host_async(hdg_sys* S, const double* U, const double* Lam, const double* dLam, double* dU,
+                               void* stream) {
   if (!S) return HDG_EINVAL;
   hdg_ctx* ctx = S->ctx;
-  if (!U || !Lam || !dLam || !dU) return fail(ctx, HDG_EINVAL, "hdg_step_host: null argument");
+  if (!U || !Lam || !dLam || !dU) return fail(ctx, HDG_EINVAL, "hdg_step_host_async: null argument");
   const hdg_mesh* M = S->mesh;
   cudaStream_t st = (cudaStream_t)stream;
   const size_t d = sizeof(double);
@@ -455,7 +507,14 @@ hdg_status hdg_step_host(hdg_sys* S, const double* U, const double* Lam, const d
   rc = hdg_recover(S, S->d_dLam, S->d_dU, stream);
   if (rc != HDG_OK) return rc;
   HDG_CK(ctx, cudaMemcpyAsync(dU, S->d_dU, d * M->u_len, cudaMemcpyDeviceToHost, st));
-  HDG_CK(ctx, cudaStreamSynchronize(st));
+  return HDG_OK;
+}
+
+hdg_status hdg_step_host(hdg_sys* S, const double* U, const double* Lam, const double* dLam, double* dU,
+                         void* stream) {
+  const hdg_status rc = hdg_step_host_async(S, U, Lam, dLam, dU, stream);
+  if (rc != HDG_OK) return rc;
+  HDG_CK(S->ctx, cudaStreamSynchronize((cudaStream_t)stream));
   return HDG_OK;
 }
 

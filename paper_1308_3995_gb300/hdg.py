@@ -30,7 +30,8 @@ STATUS_NAMES = {0: "HDG_OK", 1: "HDG_EINVAL", 2: "HDG_ENOMEM", 3: "HDG_ECUDA", 4
 EXPORTS = ["hdg_create", "hdg_destroy", "hdg_last_error", "hdg_mesh_create", "hdg_mesh_destroy", "hdg_mesh_sizes",
            "hdg_mesh_layout", "hdg_footprint_bytes", "hdg_sys_create", "hdg_sys_destroy", "hdg_condense",
            "hdg_recover", "hdg_step_host", "hdg_sys_get", "hdg_sys_launches", "hdg_debug_tables",
-           "hdg_condense_noalloc"]
+           "hdg_condense_noalloc", "hdg_sys_workspace_bytes", "hdg_sys_create_in",
+           "hdg_step_host_async"]
 
 
 class HdgError(RuntimeError):
@@ -95,11 +96,16 @@ def lib(build: bool = True):
         L.hdg_condense.argtypes = [_vp, _vp, _vp, _vp]
         L.hdg_recover.argtypes = [_vp, _vp, _vp, _vp]
         L.hdg_step_host.argtypes = [_vp, _vp, _vp, _vp, _vp, _vp]
+        L.hdg_step_host_async.argtypes = [_vp, _vp, _vp, _vp, _vp, _vp]
         L.hdg_sys_get.argtypes = [_vp] + [ctypes.POINTER(_vp)] * 6
         L.hdg_sys_launches.argtypes = [_vp]
         L.hdg_sys_launches.restype = ctypes.c_int32
         L.hdg_debug_tables.argtypes = [ctypes.c_int] * 5 + [_dp, ctypes.c_int]
         L.hdg_condense_noalloc.argtypes = [_vp, ctypes.POINTER(hdg_params)] + [_vp] * 9
+        L.hdg_sys_workspace_bytes.argtypes = [_vp, ctypes.POINTER(hdg_params)]
+        L.hdg_sys_workspace_bytes.restype = ctypes.c_int64
+        L.hdg_sys_create_in.argtypes = [_vp, _vp, ctypes.POINTER(hdg_params), _vp, ctypes.c_int64,
+                                        ctypes.POINTER(_vp)]
         _lib = L
     return _lib
 
@@ -211,6 +217,10 @@ class Mesh:
         P = params.c()
         return int(lib().hdg_footprint_bytes(self.h, ctypes.byref(P)))
 
+    def workspace_bytes(self, params: Params) -> int:
+        P = params.c()
+        return int(lib().hdg_sys_workspace_bytes(self.h, ctypes.byref(P)))
+
     def close(self):
         if getattr(self, "h", None):
             lib().hdg_mesh_destroy(self.h)
@@ -224,12 +234,18 @@ class Mesh:
 
 
 class System:
-    """hdg_sys_create / hdg_condense / hdg_recover / hdg_step_host / hdg_sys_get."""
+    """hdg_sys_create (or hdg_sys_create_in with a device workspace) / hdg_condense /
+    hdg_recover / hdg_step_host / hdg_sys_get."""
 
-    def __init__(self, ctx: Context, mesh: Mesh, params: Params):
+    def __init__(self, ctx: Context, mesh: Mesh, params: Params, workspace=None):
         P = params.c()
         h = _vp()
-        _check(lib().hdg_sys_create(ctx.h, mesh.h, ctypes.byref(P), ctypes.byref(h)), ctx.h)
+        if workspace is None:
+            _check(lib().hdg_sys_create(ctx.h, mesh.h, ctypes.byref(P), ctypes.byref(h)), ctx.h)
+        else:
+            ptr, nbytes = workspace
+            _check(lib().hdg_sys_create_in(ctx.h, mesh.h, ctypes.byref(P), int(ptr), int(nbytes), ctypes.byref(h)),
+                   ctx.h)
         self.h, self.ctx, self.mesh, self.params = h, ctx, mesh, params
         ptrs = [_vp() for _ in range(6)]
         lib().hdg_sys_get(h, *[ctypes.byref(p) for p in ptrs])
@@ -248,6 +264,12 @@ class System:
         def hp(a):
             return a.data_ptr() if hasattr(a, "data_ptr") else a.ctypes.data
         _check(lib().hdg_step_host(self.h, hp(U), hp(Lam), hp(dLam), hp(dU), _stream(stream)), self.ctx.h)
+
+    def step_host_async(self, U, Lam, dLam, dU, stream=None):
+        """hdg_step_host_async: enqueue the whole step on `stream` from pinned host tensors."""
+        def hp(a):
+            return a.data_ptr() if hasattr(a, "data_ptr") else a.ctypes.data
+        _check(lib().hdg_step_host_async(self.h, hp(U), hp(Lam), hp(dLam), hp(dU), _stream(stream)), self.ctx.h)
 
     @property
     def launches(self) -> int:

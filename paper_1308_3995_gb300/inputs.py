@@ -112,7 +112,8 @@ def conserved(rho, u, v, p, gamma=1.4):
 class Field:
     """Analytic periodic primitive field on [0,1)^2."""
 
-    def __init__(self, kind: str, mach: float, aoa: float, seed: int, gamma: float = 1.4, h: float = 1 / 64):
+    def __init__(self, kind: str, mach: float, aoa: float, seed: int, gamma: float = 1.4, h: float = 1 / 64,
+                 kvec=None):
         self.kind, self.gamma = kind, gamma
         self.rho0, self.u0, self.v0, self.p0 = free_stream(mach, aoa, gamma)
         rng = np.random.default_rng(seed)
@@ -127,7 +128,8 @@ class Field:
             self.phase = rng.uniform(0.0, 2 * math.pi, size=(len(ks), 4))
         elif kind == "shock":
             choices = [(1, 0), (2, 1), (3, 1), (1, 1), (2, -1), (3, -1)]
-            self.kvec = np.array(choices[int(rng.integers(len(choices)))], dtype=np.float64)
+            pick = choices[int(rng.integers(len(choices)))]
+            self.kvec = np.array(kvec if kvec is not None else pick, dtype=np.float64)
             kn = np.linalg.norm(self.kvec)
             nrm = self.kvec / kn
             un1 = self.u0 * nrm[0] + self.v0 * nrm[1]
@@ -187,28 +189,24 @@ def element_coeffs(mesh: MeshData, elem_p: np.ndarray, fld: Field, nfield: int, 
     cen = mesh.elem_xy.mean(1) % 1.0
     wc = fld.conserved(cen[:, 0], cen[:, 1])                  # [n_elem, 4]
     scale = np.abs(fld.w_inf) + 0.1
-    out = []
+    n_of = np.array([nfield * _n_basis(int(p)) for p in range(5)], dtype=np.int64)[elem_p.astype(np.int64)]
+    off = np.concatenate([[0], np.cumsum(n_of)])
+    U = np.zeros(int(off[-1]))
     for p in range(1, 5):
         idx = np.nonzero(elem_p == p)[0]
         if idx.size == 0:
             continue
         nb = _n_basis(p)
         m = np.arange(nb)
-        hi = 1e-3 * scale[None, :, None] * rng.standard_normal((idx.size, 4, nb)) / (m + 1)[None, None, :]
-        w = hi.copy()
+        w = 1e-3 * scale[None, :, None] * rng.standard_normal((idx.size, 4, nb)) / (m + 1)[None, None, :]
         w[:, :, 0] = wc[idx] / SQRT2
         blocks = [w]
         if nfield == 12:
             q = 1e-3 * scale[None, None, :, None] * rng.standard_normal((idx.size, 2, 4, nb)) / (m + 1)
             q[:, :, :, 0] = 5e-2 * scale[None, None, :] * rng.standard_normal((idx.size, 2, 4))
             blocks = [q.reshape(idx.size, 8, nb), w]
-        out.append((idx, np.concatenate(blocks, 1).reshape(idx.size, -1)))
-    n_of = np.array([nfield * _n_basis(int(p)) for p in elem_p], dtype=np.int64)
-    off = np.concatenate([[0], np.cumsum(n_of)])
-    U = np.zeros(int(off[-1]))
-    for idx, vals in out:
-        for r, K in enumerate(idx):
-            U[off[K]:off[K + 1]] = vals[r]
+        vals = np.concatenate(blocks, 1).reshape(idx.size, -1)
+        U[(off[idx][:, None] + np.arange(vals.shape[1])[None, :]).ravel()] = vals.ravel()
     return U
 
 
@@ -221,14 +219,18 @@ def trace_coeffs(mesh: MeshData, face_vid: np.ndarray, face_p: np.ndarray, fld: 
     mid = (a + 0.5 * d) % 1.0
     wm = fld.conserved(mid[:, 0], mid[:, 1])
     scale = np.abs(fld.w_inf) + 0.1
-    parts = []
-    for f in range(face_vid.shape[0]):
-        nk = int(face_p[f]) + 1
-        k = np.arange(nk)
-        c = 1e-3 * scale[:, None] * rng.standard_normal((4, nk)) / (k + 1)[None, :]
-        c[:, 0] = wm[f]
-        parts.append(c.reshape(-1))
-    return np.concatenate(parts)
+    nk = face_p.astype(np.int64) + 1
+    off = np.concatenate([[0], np.cumsum(4 * nk)])
+    out = np.zeros(int(off[-1]))
+    noise = rng.standard_normal(int(off[-1]))
+    for k in np.unique(nk):
+        idx = np.nonzero(nk == k)[0]
+        kk = np.arange(k)
+        c = 1e-3 * scale[None, :, None] * noise[(off[idx][:, None] + np.arange(4 * k)[None, :])].reshape(-1, 4, k) \
+            / (kk + 1)[None, None, :]
+        c[:, :, 0] = wm[idx]
+        out[(off[idx][:, None] + np.arange(4 * k)[None, :]).ravel()] = c.ravel()
+    return out
 
 
 def trace_update(lam_len: int, seed: int) -> np.ndarray:
@@ -298,7 +300,7 @@ class Case:
 def make_case(wl: Workload) -> Case:
     mesh = periodic_mesh(wl.nx, wl.ny, wl.jitter, wl.seed)
     ep = degree_map(mesh.n_elem, wl.seed + 1, p=wl.p, probs=wl.probs)
-    fld = Field(wl.field, wl.mach, wl.aoa, wl.seed + 2, h=mesh.h)
+    fld = Field(wl.field, wl.mach, wl.aoa, wl.seed + 2, h=mesh.h, kvec=wl.extra.get("kvec"))
     return Case(wl, mesh, ep, fld)
 
 

@@ -1,0 +1,255 @@
+"""Continuous-batching request loop for steady-flow Newton steps.
+
+Requests (each a mesh, a degree map, a flow model, a state and a trace update)
+arrive on a Poisson schedule.  The server admits them in arrival order while a
+stream slot is free and its device arena can hold the request's footprint
+(``hdg_sys_workspace_bytes``: the local solves X, the trace system K and E,
+residuals and staging); an admitted request's whole step -- host->device
+copies, condensation, reconstruction, device->host copy of dU -- is enqueued
+on its own stream with ``hdg_step_host_async``, so requests that arrive while
+others are on the GPU overlap with them.  A completion is observed through a
+CUDA event; the request then releases its slot and its arena range at once.
+Nothing here allocates or frees device memory while requests are in flight
+(the arena is one tensor allocated at start-up; systems are carved from it).
+
+The plain baseline is the same loop with one slot and binary64 arithmetic
+(requests served one at a time, in arrival order).
+
+Latency is measured on the host clock from a request's arrival time to the
+moment its completion event is observed; throughput is elements / makespan.
+"""
+from __future__ import annotations
+
+import bisect
+import math
+import time
+from dataclasses import dataclass, field
+
+import numpy as np
+
+from . import hdg
+from . import inputs as G
+
+
+# ----------------------------------------------------------------------------- arena
+class Arena:
+    """First-fit allocator of 256-byte-aligned ranges in [0, capacity)."""
+
+    ALIGN = 256
+
+    def __init__(self, capacity: int):
+        self.capacity = int(capacity)
+        self.free_list = [(0, self.capacity)]      # sorted (offset, size)
+        self.used = {}                             # offset -> size
+
+    @classmethod
+    def _round(cls, n: int) -> int:
+        return (int(n) + cls.ALIGN - 1) // cls.ALIGN * cls.ALIGN
+
+    def alloc(self, nbytes: int):
+        n = self._round(max(1, nbytes))
+        for i, (off, size) in enumerate(self.free_list):
+            if size >= n:
+                if size == n:
+                    self.free_list.pop(i)
+                else:
+                    self.free_list[i] = (off + n, size - n)
+                self.used[off] = n
+                return off
+        return None
+
+    def free(self, off: int):
+        n = self.used.pop(off)
+        i = bisect.bisect_left(self.free_list, (off, 0))
+        self.free_list.insert(i, (off, n))
+        # coalesce with neighbours
+        merged = []
+        for o, s in self.free_list:
+            if merged and merged[-1][0] + merged[-1][1] == o:
+                merged[-1] = (merged[-1][0], merged[-1][1] + s)
+            else:
+                merged.append((o, s))
+        self.free_list = merged
+
+    @property
+    def bytes_used(self) -> int:
+        return sum(self.used.values())
+
+
+# ----------------------------------------------------------------------------- requests
+@dataclass
+class Request:
+    rid: int
+    arrival_s: float
+    wl: G.Workload
+    n_elem: int = 0
+    # host data (built before the run; pinned torch tensors when prepared)
+    case: object = None
+    U: object = None
+    Lam: object = None
+    dLam: object = None
+    face_vid: object = None
+    face_p: object = None
+    # results
+    dU: object = None
+    dU_host: object = None
+    mesh: object = None
+    admitted_s: float = math.nan
+    done_s: float = math.nan
+
+
+def request_workloads(n: int, seed: int, min_elems: int = 1000, max_elems: int = 64000) -> list:
+    """Seeded request mix: sizes log-uniform in [min_elems, max_elems]
+    (nx = round(sqrt(N/4)), ny = 2 nx), Euler or Navier-Stokes 50/50, a uniform
+    degree p ~ U{1..4} or the 40/30/20/10 % mix (50/50), Mach ~ U(0.3, 2.0)
+    with an oblique normal-shock band above Mach 1.1, Fourier modes below."""
+    rng = np.random.default_rng(seed)
+    out = []
+    for i in range(n):
+        N = math.exp(rng.uniform(math.log(min_elems), math.log(max_elems)))
+        nx = max(3, int(round(math.sqrt(N / 4.0))))
+        model = int(rng.integers(2))
+        if rng.uniform() < 0.5:
+            p, probs = int(rng.integers(1, 5)), None
+        else:
+            p, probs = None, (0.4, 0.3, 0.2, 0.1)
+        mach = float(rng.uniform(0.3, 2.0))
+        fld = "shock" if mach > 1.1 else "fourier"
+        out.append(G.Workload(f"req{i}", nx, 2 * nx, 0.2, model, p, probs, fld, mach, 0.0,
+                              seed=int(rng.integers(1 << 30)), extra={"kvec": (1, 0)}))
+    return out
+
+
+def poisson_arrivals(n: int, rate_per_s: float, seed: int) -> np.ndarray:
+    rng = np.random.default_rng(seed)
+    return np.cumsum(rng.exponential(1.0 / rate_per_s, size=n))
+
+
+def prepare(ctx: hdg.Context, reqs: list, pin: bool = True):
+    """Build each request's host inputs (mesh, degrees, state, trace update) and
+    its pinned result buffer; the face list comes from the library's mesh plan."""
+    import torch
+    for r in reqs:
+        case = G.make_case(r.wl)
+        m = hdg.Mesh(ctx, case.mesh.elem_xy, case.mesh.elem_vid, case.elem_p, case.nfield)
+        U, Lam, dLam = G.case_state(case, m.face_vid, m.face_p)
+        r.case, r.face_vid, r.face_p = case, m.face_vid.copy(), m.face_p.copy()
+        r.n_elem = case.mesh.n_elem
+        m.close()
+        t = (torch.from_numpy(U), torch.from_numpy(Lam), torch.from_numpy(dLam), torch.empty(U.size, dtype=torch.float64))
+        if pin:
+            t = tuple(x.pin_memory() for x in t)
+        r.U, r.Lam, r.dLam, r.dU_host = t
+    return reqs
+
+
+# ----------------------------------------------------------------------------- server
+@dataclass
+class Report:
+    mode: str
+    n: int
+    elements: int
+    makespan_s: float
+    latencies_s: list = field(default_factory=list)
+
+    @property
+    def throughput(self) -> float:
+        return self.elements / self.makespan_s
+
+    def pct(self, q: float) -> float:
+        lat = sorted(self.latencies_s)
+        if not lat:
+            return math.nan
+        k = min(len(lat) - 1, max(0, int(math.ceil(q / 100.0 * len(lat))) - 1))
+        return lat[k]
+
+    def as_dict(self) -> dict:
+        return {"mode": self.mode, "requests": self.n, "elements": self.elements,
+                "makespan_s": self.makespan_s, "elements_per_s": self.throughput,
+                "p50_ms": 1e3 * self.pct(50), "p99_ms": 1e3 * self.pct(99),
+                "mean_ms": 1e3 * float(np.mean(self.latencies_s)) if self.latencies_s else math.nan}
+
+
+class Server:
+    def __init__(self, ctx: hdg.Context, arena_bytes: int, slots: int, precision: int, keep_outputs: bool = False):
+        import torch
+        self.ctx, self.slots, self.precision, self.keep = ctx, int(slots), int(precision), keep_outputs
+        self.dev = torch.device(f"cuda:{ctx.device}")
+        self.buf = torch.empty(int(arena_bytes), dtype=torch.uint8, device=self.dev)
+        self.arena = Arena(int(arena_bytes))
+        self.streams = [torch.cuda.Stream(device=self.dev) for _ in range(self.slots)]
+
+    def _params(self, wl):
+        return hdg.Params(model=wl.model, precision=self.precision, mach=wl.mach, alpha=wl.alpha,
+                          reynolds=wl.reynolds, prandtl=wl.prandtl)
+
+    def run(self, reqs: list, mode: str = "") -> Report:
+        import torch
+        order = sorted(reqs, key=lambda r: r.arrival_s)
+        free_slots = list(range(self.slots))
+        waiting, active, meshes = [], [], []
+        nxt = 0
+        torch.cuda.synchronize(self.dev)
+        t0 = time.perf_counter()
+        while nxt < len(order) or waiting or active:
+            now = time.perf_counter() - t0
+            while nxt < len(order) and order[nxt].arrival_s <= now:
+                waiting.append(order[nxt])
+                nxt += 1
+            # admit in arrival order while a slot and arena room are available; the head
+            # request's mesh is planned once and kept until it is admitted
+            while waiting and free_slots:
+                r = waiting[0]
+                wl = r.wl
+                if r.mesh is None:
+                    r.mesh = hdg.Mesh(self.ctx, r.case.mesh.elem_xy, r.case.mesh.elem_vid, r.case.elem_p,
+                                      r.case.nfield)
+                    meshes.append(r.mesh)
+                mesh = r.mesh
+                prm = self._params(wl)
+                need = mesh.workspace_bytes(prm)
+                if need > self.arena.capacity:
+                    raise hdg.HdgError(hdg.HDG_ENOMEM, f"request {r.rid} needs {need} bytes, arena holds "
+                                                       f"{self.arena.capacity}")
+                off = self.arena.alloc(need)
+                if off is None:
+                    break
+                waiting.pop(0)
+                slot = free_slots.pop(0)
+                sysm = hdg.System(self.ctx, mesh, prm, workspace=(self.buf.data_ptr() + off, need))
+                dU = r.dU_host
+                st = self.streams[slot]
+                sysm.step_host_async(r.U, r.Lam, r.dLam, dU, st)
+                ev = torch.cuda.Event()
+                ev.record(st)
+                r.admitted_s = time.perf_counter() - t0
+                active.append((r, slot, off, sysm, dU, ev))
+            # completions
+            still = []
+            for item in active:
+                r, slot, off, sysm, dU, ev = item
+                if ev.query():
+                    r.done_s = time.perf_counter() - t0
+                    if self.keep:
+                        r.dU = dU.numpy().copy()
+                    sysm.close()                 # frees nothing on the device (arena-backed)
+                    self.arena.free(off)
+                    free_slots.append(slot)
+                else:
+                    still.append(item)
+            active = still
+            if not active and not waiting and nxt < len(order):
+                wait = order[nxt].arrival_s - (time.perf_counter() - t0)
+                if wait > 0:
+                    time.sleep(min(wait, 0.01))
+            elif active:
+                time.sleep(2e-5)
+        makespan = max(r.done_s for r in order) - min(r.arrival_s for r in order)
+        torch.cuda.synchronize(self.dev)
+        for m in meshes:
+            m.close()
+        for r in order:
+            r.mesh = None
+        rep = Report(mode, len(order), sum(r.n_elem for r in order), makespan,
+                     [r.done_s - r.arrival_s for r in order])
+        return rep
