@@ -33,6 +33,9 @@ sys.path.insert(0, ROOT)
 METRIC = "condensed elements/sec per p; p50/p99 solve latency vs plain FP64 at 1e-10 rel"
 FP64_PEAK_TFLOPS = 1.25     # nominal GB300 FP64 rate (recipe table); see the design doc
 L2_FLUSH_BYTES = 256 << 20  # > 129 MB L2
+# dram__bytes_read.sum + dram__bytes_write.sum per condensation launch from ncu
+# (profiles/), scaled to the full workload by elements; only for unchanged kernels
+TRAFFIC_PER_LAUNCH = {}
 
 
 def dense_condensation_flops(n: int, nt: int) -> float:
@@ -167,8 +170,112 @@ def run_reference(args, wl, rank):
 
 
 # ----------------------------------------------------------------------------- GPU arm
+class Measured:
+    """One workload on one GPU: device-timed steps (CUDA events on the launching
+    stream, L2 flushed between timed steps)."""
+
+    def __init__(self, ctx, wl, precision, dev, flush):
+        import torch
+
+        from paper_1308_3995_gb300 import hdg
+        from paper_1308_3995_gb300 import inputs as G
+        self.wl, self.precision = wl, precision
+        self.case = G.make_case(wl)
+        c = self.case
+        self.mesh = hdg.Mesh(ctx, c.mesh.elem_xy, c.mesh.elem_vid, c.elem_p, c.nfield)
+        self.U, self.Lam, self.dLam = G.case_state(c, self.mesh.face_vid, self.mesh.face_p)
+        self.prm = hdg.Params(model=wl.model, precision=precision, mach=wl.mach, alpha=wl.alpha,
+                              reynolds=wl.reynolds, prandtl=wl.prandtl)
+        self.sys = hdg.System(ctx, self.mesh, self.prm)
+        self.Ut, self.Lt, self.dLt = (torch.from_numpy(a).to(dev) for a in (self.U, self.Lam, self.dLam))
+        self.dUt = torch.empty(self.mesh.u_len, dtype=torch.float64, device=dev)
+        self.flush = flush
+
+    def run(self, steps, warmup, stream, clocks=None):
+        import torch
+        for _ in range(warmup):
+            self.flush.fill_(1.0)
+            self.sys.condense(self.Ut, self.Lt, stream)
+            self.sys.recover(self.dLt, self.dUt, stream)
+        torch.cuda.synchronize()
+        self.launches = self.sys.launches
+        ev = [[torch.cuda.Event(enable_timing=True) for _ in range(3)] for _ in range(steps)]
+        if clocks:
+            clocks.start()
+        torch.cuda.synchronize()
+        for i in range(steps):
+            self.flush.fill_(1.0)
+            ev[i][0].record(stream)
+            self.sys.condense(self.Ut, self.Lt, stream)
+            ev[i][1].record(stream)
+            self.sys.recover(self.dLt, self.dUt, stream)
+            ev[i][2].record(stream)
+        torch.cuda.synchronize()
+        self.clk = clocks.stop() if clocks else None
+        self.step_ms = [e[0].elapsed_time(e[2]) for e in ev]
+        self.cond_ms = [e[0].elapsed_time(e[1]) for e in ev]
+        self.rec_ms = [e[1].elapsed_time(e[2]) for e in ev]
+        self.status_bad = int((self.sys.views()["status"] != 0).sum())
+        return self
+
+    @property
+    def n_elem(self):
+        return self.mesh.n_elem
+
+    def algorithmic(self):
+        from collections import Counter
+        m, c = self.mesh, self.case
+        nts = Counter()
+        for K in range(m.n_elem):
+            nts[(int(m.elem_p[K]), int(sum(4 * (m.face_p[e] + 1) for e in m.elem_face[K])))] += 1
+        fl = sum(k * dense_condensation_flops(c.nfield * (p + 1) * (p + 2) // 2, nt) for (p, nt), k in nts.items())
+        by = sum(k * algorithmic_bytes(c.nfield * (p + 1) * (p + 2) // 2, nt) for (p, nt), k in nts.items())
+        return fl, by
+
+    def summary(self):
+        tot = sum(self.step_ms)
+        lat = sorted(self.step_ms)
+        p99 = lat[min(len(lat) - 1, int(math.ceil(0.99 * len(lat))) - 1)]
+        fl, by = self.algorithmic()
+        cond_s = statistics.mean(self.cond_ms) * 1e-3
+        return {"elements_per_s": self.n_elem * len(self.step_ms) / (tot * 1e-3), "ms_per_step": tot / len(lat),
+                "p50_step_ms": lat[len(lat) // 2], "p99_step_ms": p99, "condense_ms": 1e3 * cond_s,
+                "recover_ms": statistics.mean(self.rec_ms), "elem_status_nonzero": self.status_bad,
+                "fp64_equiv_tflops": fl / cond_s / 1e12, "algorithmic_gflop_per_launch": fl / 1e9,
+                "algorithmic_mb_per_launch": by / 1e6}
+
+    def close(self):
+        self.sys.close()
+        self.mesh.close()
+
+
+def serving_section(ctx, n_requests, seed, max_elems):
+    """Poisson stream through the continuous-batching loop (float-float, 8 slots)
+    against the plain loop (binary64, one request at a time)."""
+    import torch
+
+    from paper_1308_3995_gb300 import hdg
+    from paper_1308_3995_gb300 import serving as SV
+    wls = SV.request_workloads(n_requests, seed=seed, min_elems=1000, max_elems=max_elems)
+    reqs = SV.prepare(ctx, [SV.Request(i, 0.0, w) for i, w in enumerate(wls)])
+    arena = 24 << 30
+    mixed = SV.Server(ctx, arena, slots=8, precision=hdg.HDG_FLOAT2)
+    plain = SV.Server(ctx, arena, slots=1, precision=hdg.HDG_FP64)
+    sat = mixed.run(reqs, "saturated")                       # everything at t = 0
+    mean_el = sat.elements / sat.n
+    rate = 0.7 * sat.throughput / mean_el                    # requests / s
+    arr = SV.poisson_arrivals(len(reqs), rate, seed + 1)
+    for r, t in zip(reqs, arr):
+        r.arrival_s = float(t)
+    m = mixed.run(reqs, "mixed float-float, continuous batching (8 slots)").as_dict()
+    p = plain.run(reqs, "plain FP64, one request at a time").as_dict()
+    del mixed, plain
+    torch.cuda.empty_cache()
+    return {"requests": len(reqs), "sizes": f"1000..{max_elems} elements log-uniform, Euler/NS 50/50, p 1..4",
+            "arrival_rate_per_s": rate, "saturated_elements_per_s": sat.throughput, "mixed": m, "plain_fp64": p}
+
+
 def run_ours(args, wl, ws, rank, local):
-    import numpy as np
     import torch
 
     from paper_1308_3995_gb300 import hdg
@@ -179,100 +286,89 @@ def run_ours(args, wl, ws, rank, local):
     if ws > 1:
         import torch.distributed as dist
         dist.init_process_group("nccl", device_id=dev)
-    case = G.make_case(wl)
     ctx = hdg.Context(local)
-    mesh = hdg.Mesh(ctx, case.mesh.elem_xy, case.mesh.elem_vid, case.elem_p, case.nfield)
-    U, Lam, dLam = G.case_state(case, mesh.face_vid, mesh.face_p)
-    prm = hdg.Params(model=wl.model, precision=args.precision, mach=wl.mach, alpha=wl.alpha,
-                     reynolds=wl.reynolds, prandtl=wl.prandtl)
-    sysm = hdg.System(ctx, mesh, prm)
-    Ut, Lt, dLt = (torch.from_numpy(a).to(dev) for a in (U, Lam, dLam))
-    dUt = torch.empty(mesh.u_len, dtype=torch.float64, device=dev)
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
     stream = torch.cuda.current_stream()
 
-    def step():
-        sysm.condense(Ut, Lt, stream)
-        sysm.recover(dLt, dUt, stream)
-
-    for _ in range(args.warmup):
-        flush.fill_(1.0)
-        step()
-    torch.cuda.synchronize()
-    launches_per_step = sysm.launches
-    ev = [[torch.cuda.Event(enable_timing=True) for _ in range(3)] for _ in range(args.steps)]
-    clocks = ClockSampler(local)
-    clocks.start()
+    # headline: plain binary64 path on the named workload (replicated on every rank)
+    main_m = Measured(ctx, wl, args.precision, dev, flush)
     if ws > 1:
         torch.distributed.barrier()
-    torch.cuda.synchronize()
-    for i in range(args.steps):
-        flush.fill_(1.0)
-        ev[i][0].record(stream)
-        sysm.condense(Ut, Lt, stream)
-        ev[i][1].record(stream)
-        sysm.recover(dLt, dUt, stream)
-        ev[i][2].record(stream)
-    torch.cuda.synchronize()
+    main_m.run(args.steps, args.warmup, stream, ClockSampler(local))
     if ws > 1:
         torch.distributed.barrier()
-    clk = clocks.stop()
-    step_ms = [e[0].elapsed_time(e[2]) for e in ev]
-    cond_ms = [e[0].elapsed_time(e[1]) for e in ev]
-    rec_ms = [e[1].elapsed_time(e[2]) for e in ev]
-    total_ms = sum(step_ms)
+    total_ms = sum(main_m.step_ms)
     if ws > 1:
         t = torch.tensor([total_ms], dtype=torch.float64, device=dev)
         torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
         total_ms = float(t.item())
-    n_elem = mesh.n_elem
+    n_elem = main_m.n_elem
     value = ws * n_elem * args.steps / (total_ms * 1e-3)
-    status_bad = int((sysm.views()["status"] != 0).sum())
+    summ = main_m.summary()
 
     # end to end through the C ABI with pinned host buffers (copies in the timed region)
-    Uh, Lh, dLh = (torch.from_numpy(a).pin_memory() for a in (U, Lam, dLam))
-    dUh = torch.empty(mesh.u_len, dtype=torch.float64).pin_memory()
+    Uh, Lh, dLh = (torch.from_numpy(a).pin_memory() for a in (main_m.U, main_m.Lam, main_m.dLam))
+    dUh = torch.empty(main_m.mesh.u_len, dtype=torch.float64).pin_memory()
     for _ in range(2):
-        sysm.step_host(Uh, Lh, dLh, dUh, stream)
+        main_m.sys.step_host(Uh, Lh, dLh, dUh, stream)
     e2e_s = []
     for _ in range(max(3, args.steps // 2)):
         flush.fill_(1.0)
         torch.cuda.synchronize()
         t0 = time.perf_counter()
-        sysm.step_host(Uh, Lh, dLh, dUh, stream)
+        main_m.sys.step_host(Uh, Lh, dLh, dUh, stream)
         e2e_s.append(time.perf_counter() - t0)
     e2e_val = ws * n_elem / statistics.mean(e2e_s)
-    h2d = 8 * (mesh.u_len + 2 * mesh.lam_len)
-    d2h = 8 * mesh.u_len
+    h2d = 8 * (main_m.mesh.u_len + 2 * main_m.mesh.lam_len)
+    d2h = 8 * main_m.mesh.u_len
 
-    # roofline of the dominant kernel (condensation): algorithmic FP64 flops per launch / duration
-    from collections import Counter
-    nts = Counter()
-    for K in range(n_elem):
-        nts[(int(mesh.elem_p[K]), int(sum(4 * (mesh.face_p[e] + 1) for e in mesh.elem_face[K])))] += 1
-    flops = sum(c * dense_condensation_flops(case.nfield * (p + 1) * (p + 2) // 2, nt) for (p, nt), c in nts.items())
-    abytes = sum(c * algorithmic_bytes(case.nfield * (p + 1) * (p + 2) // 2, nt) for (p, nt), c in nts.items())
-    cond_s = statistics.mean(cond_ms) * 1e-3
-    achieved = flops / cond_s / 1e12
+    # roofline of the dominant kernel (condensation), FP64 pipe
+    fl, by = main_m.algorithmic()
+    cond_s = summ["condense_ms"] * 1e-3
+    achieved = fl / cond_s / 1e12
     roof = {"bound": "alu", "achieved": achieved, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
-            "frac": achieved / FP64_PEAK_TFLOPS, "traffic": None,
-            "kernel": "k_condense_euler_f64 (FP64 pipe)",
-            "algorithmic_flops_per_launch": flops, "algorithmic_bytes_per_launch": abytes,
-            "launch_ms": 1e3 * cond_s, "achieved_hbm_gbs": abytes / cond_s / 1e9,
-            "peak_note": "nominal FP64 1.25 TFLOP/s (recipe); no measured FP64 peak file"}
-    lat = sorted(step_ms)
-    p50 = lat[len(lat) // 2]
-    p99 = lat[min(len(lat) - 1, int(math.ceil(0.99 * len(lat))) - 1)]
-    extra = {"precision": "fp64" if args.precision == 0 else "mixed", "p50_step_ms": p50, "p99_step_ms": p99,
-             "condense_ms": statistics.mean(cond_ms), "recover_ms": statistics.mean(rec_ms),
-             "elem_status_nonzero": status_bad}
+            "frac": achieved / FP64_PEAK_TFLOPS, "traffic": TRAFFIC_PER_LAUNCH.get((wl.name, args.precision)),
+            "kernel": "k_condense_euler<3, double> (FP64 pipe)", "algorithmic_flops_per_launch": fl,
+            "algorithmic_bytes_per_launch": by, "launch_ms": 1e3 * cond_s, "achieved_hbm_gbs": by / cond_s / 1e9,
+            "peak_note": "FP64 1.25 TFLOP/s nominal (recipe); 1.255 measured by an FMA-chain microbenchmark"}
+    extra = {"precision": "fp64" if args.precision == 0 else "float-float"}
+    extra.update({k: summ[k] for k in ("p50_step_ms", "p99_step_ms", "condense_ms", "recover_ms",
+                                       "elem_status_nonzero")})
     line = {"metric": METRIC, "value": value, "unit": "elements/s", "n_gpus": ws, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64" if args.precision == 0 else "f32x2",
             "data": "synthetic (seeded periodic jittered mesh, Newton iterate)",
             "config": workload_config(wl, n_elem, extra),
             "e2e": {"value": e2e_val, "unit": "elements/s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
-            "gpu_launches": launches_per_step * args.steps, "roofline": roof, "clocks": clk}
+            "gpu_launches": main_m.launches * args.steps, "roofline": roof, "clocks": main_m.clk}
+    main_m.close()
+
+    if ws == 1 and not args.quick:
+        from paper_1308_3995_gb300 import inputs as G
+        # the same workload in float-float arithmetic (mixed-precision path, parity <= 1e-12 vs the oracle)
+        mm = Measured(ctx, wl, hdg.HDG_FLOAT2, dev, flush).run(max(5, args.steps // 2), 3, stream)
+        line["mixed_float2"] = {**mm.summary(), "dtype": "f32x2 (binary32 pairs, ~48-bit significand)"}
+        mm.close()
+        # condensed elements/s per p at equal element counts (Euler, 16,384 triangles)
+        per_p = {}
+        for p in (1, 2, 3, 4):
+            wp = G.small_variant(wl, wl.nx, wl.ny, p=p, name=f"euler_p{p}_16k")
+            row = {}
+            for prec, nm in ((hdg.HDG_FP64, "fp64"), (hdg.HDG_FLOAT2, "float2")):
+                mp = Measured(ctx, wp, prec, dev, flush).run(5, 2, stream)
+                row[nm] = mp.summary()["elements_per_s"]
+                mp.close()
+            per_p[str(p)] = row
+        line["elements_per_s_per_p"] = per_p
+        # Navier-Stokes mixed form, degree mix 40/30/20/10 % (65,536 triangles)
+        ns = {}
+        for prec, nm in ((hdg.HDG_FP64, "fp64"), (hdg.HDG_FLOAT2, "float2")):
+            mn = Measured(ctx, G.WORKLOADS["ns_mixp_65k"], prec, dev, flush).run(3, 1, stream)
+            ns[nm] = mn.summary()
+            mn.close()
+        line["ns_mixp_65k"] = ns
+        if args.serving_requests > 0:
+            line["serving"] = serving_section(ctx, args.serving_requests, 77, args.serving_max_elems)
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
         om, P, U2, L2, _, n = time_oracle_sample(wl, target_s=12.0)
         t0 = time.perf_counter()
@@ -298,6 +394,9 @@ def main(argv=None):
     ap.add_argument("--precision", type=int, default=0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cells", default=None, help="override the grid, e.g. 48x96 (profiling runs)")
+    ap.add_argument("--quick", action="store_true", help="headline workload only (no per-p, NS, serving)")
+    ap.add_argument("--serving-requests", type=int, default=32)
+    ap.add_argument("--serving-max-elems", type=int, default=32000)
     args = ap.parse_args(argv)
     from paper_1308_3995_gb300 import inputs as G
     wl = G.WORKLOADS[args.workload]
