@@ -49,6 +49,21 @@ def algorithmic_bytes(n: int, nt: int) -> float:
     return 8.0 * ((n + nt + 6) + nt * nt + nt + n * (nt + 1))
 
 
+def max_over_ranks(x: float, ws: int, device) -> float:
+    """Largest value of x over all ranks (the slowest rank sets the job's time)."""
+    if ws <= 1:
+        return float(x)
+    import torch
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_rate(units_per_rank: int, ws: int, steps: int, total_ms: float) -> float:
+    """Units processed by all ranks per second of the slowest rank's timed region."""
+    return ws * units_per_rank * steps / (total_ms * 1e-3)
+
+
 def dist_env():
     ws = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -297,13 +312,9 @@ def run_ours(args, wl, ws, rank, local):
     main_m.run(args.steps, args.warmup, stream, ClockSampler(local))
     if ws > 1:
         torch.distributed.barrier()
-    total_ms = sum(main_m.step_ms)
-    if ws > 1:
-        t = torch.tensor([total_ms], dtype=torch.float64, device=dev)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        total_ms = float(t.item())
+    total_ms = max_over_ranks(sum(main_m.step_ms), ws, dev)
     n_elem = main_m.n_elem
-    value = ws * n_elem * args.steps / (total_ms * 1e-3)
+    value = whole_job_rate(n_elem, ws, args.steps, total_ms)
     summ = main_m.summary()
 
     # end to end through the C ABI with pinned host buffers (copies in the timed region)

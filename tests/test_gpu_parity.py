@@ -130,6 +130,61 @@ def test_ns_pseudo_time(ctx):
     full_parity(ctx, wl, cfl=10.0)
 
 
+def _sampled(ctx, wl, precision, n_faces, n_elems, seed, tol):
+    case, om, U, Lam, dLam = build_case(wl)
+    mesh, sysm, (g,) = run_gpu(ctx, case, wl, U, Lam, dLam, precision=precision)
+    assert_layout_equal(mesh, om)
+    assert np.all(g["status"] == 0)
+    rng = np.random.default_rng(seed)
+    faces = rng.choice(om.n_face, n_faces, replace=False)
+    elems = sorted(set(int(k) for f in faces for k in om.face_el[f]) |
+                   set(int(k) for k in rng.choice(om.n_elem, n_elems)))
+    chk = ParityChecker(om, oracle_params(wl), U, Lam, dLam, g)
+    errs = chk.run(elems, faces)
+    # error per field of the stored local solves (rows grouped by field)
+    nf = case.nfield
+    per_field = np.zeros(nf)
+    for K in elems:
+        e = chk.element(K)
+        nt = e["D"].shape[0]
+        Xg = chk.gpu_X(K)
+        nb = Xg.shape[0] // nf
+        for f in range(nf):
+            rows = slice(f * nb, (f + 1) * nb)
+            per_field[f] = max(per_field[f], rel_err(Xg[rows, :nt], e["X"][rows, :nt]))
+    print(wl.name, ["fp64", "float2"][precision], {k: f"{v:.1e}" for k, v in errs.items()},
+          "X_B per field", " ".join(f"{v:.1e}" for v in per_field))
+    for k, v in errs.items():
+        assert v < tol, (k, v)
+    assert per_field.max() < tol
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+def test_config3_ns_mixp_full_size_sampled(ctx, precision):
+    """65,536-triangle Navier-Stokes workload with the 40/30/20/10 % degree mix."""
+    _sampled(ctx, G.WORKLOADS["ns_mixp_65k"], precision, 8, 8, 7, [TOL, TOL_MIXED][precision])
+
+
+@pytest.mark.parametrize("precision", [1, 0])
+def test_config4_shock_full_size_sampled(ctx, precision):
+    """262,144-triangle Euler p = 3 workload, Mach 1.5 with an oblique shock band:
+    the float-float path against the FP64 oracle, error per field."""
+    _sampled(ctx, G.WORKLOADS["euler_p3_262k_shock"], precision, 12, 12, 8, [TOL, TOL_MIXED][precision])
+
+
+def test_nonfinite_state_flags_its_element_only(ctx):
+    """Failure detection: a non-finite coefficient in one element's state sets that
+    element's status to 2 (non-finite) and leaves every other element at 0."""
+    wl = G.small_variant(G.WORKLOADS["euler_p3_16k"], 6, 6)
+    case, om, U, Lam, dLam = build_case(wl)
+    K = 17
+    U[om.u_off[K] + 3] = np.nan
+    for precision in (0, 1):
+        _, _, (g,) = run_gpu(ctx, case, wl, U, Lam, dLam, precision=precision)
+        bad = np.nonzero(g["status"])[0]
+        assert list(bad) == [K] and g["status"][K] == 2
+
+
 def test_config1_euler_p1_256(ctx):
     """256 triangles, Euler p = 1, Mach 0.5 + density bump: every output element by element."""
     full_parity(ctx, G.WORKLOADS["euler_p1_256"])
