@@ -25,6 +25,7 @@
 #include "hdg_arith.cuh"
 #include "hdg_physics.cuh"
 #include "hdg_internal.h"
+#include "hdg_lu.cuh"
 
 namespace hdg {
 
@@ -376,106 +377,7 @@ __global__ void __launch_bounds__(kCondThreads, 4) k_condense_euler(
 
     // ---------------- a4/a5: LU with partial pivoting on [A | B | F] ----------------
     const int nr1 = nt + 1;
-    for (int k = 0; k < N; ++k) {
-      if (tid < 32) {
-        // renormalise column k (the multipliers of this step), then pick the pivot
-        unsigned long long best = 0ull;
-        int bi = k;
-        for (int i = k + tid; i < N; i += 32) {
-          const T v = A::norm(sA[i * LDA + k]);
-          sA[i * LDA + k] = v;
-          const unsigned long long kv = A::key(v);
-          if (kv > best) { best = kv; bi = i; }
-        }
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) {
-          const unsigned long long ob = __shfl_down_sync(0xffffffffu, best, o);
-          const int oi = __shfl_down_sync(0xffffffffu, bi, o);
-          if (ob > best || (ob == best && oi < bi)) { best = ob; bi = oi; }
-        }
-        if (tid == 0) {
-          s_piv = bi;
-          if (best == 0ull) { s_bad |= 1; s_pinv[k] = zero; } else { s_pinv[k] = A::rcp(sA[bi * LDA + k]); }
-        }
-      }
-      __syncthreads();
-      // swap rows k and piv (columns k..N-1 of A and all of [B|F]); scale the new row k by 1/pivot
-      {
-        const int piv = s_piv;
-        const T pinv = s_pinv[k];
-        const int wa = N - k;
-        for (int t = tid; t < wa + nr1; t += NT) {
-          T* pk = (t < wa) ? &sA[k * LDA + k + t] : &sR[k * ldr + (t - wa)];
-          T* pp = (t < wa) ? &sA[piv * LDA + k + t] : &sR[piv * ldr + (t - wa)];
-          const T vk = *pk, vp = *pp;
-          if (piv != k) *pp = vk;
-          *pk = A::mul(A::norm(vp), pinv);
-        }
-      }
-      __syncthreads();
-      {
-        // rows over warps, the combined columns [A(k+1..N-1) | B | F] over lanes
-        const int wa = N - k - 1, nc = wa + nr1;
-        if constexpr (std::is_same<T, double>::value) {
-          for (int i = k + 1 + ty; i < N; i += NW) {
-            const T l = sA[i * LDA + k];
-            for (int c = tx; c < nc; c += 32) {
-              const bool inA = c < wa;
-              T* dst = inA ? &sA[i * LDA + k + 1 + c] : &sR[i * ldr + (c - wa)];
-              const T* src = inA ? &sA[k * LDA + k + 1 + c] : &sR[k * ldr + (c - wa)];
-              A::msub(*dst, l, *src);
-            }
-          }
-        } else {
-          for (int i = k + 1 + ty; i < N; i += NW) {
-            const T l = sA[i * LDA + k];
-            for (int c0 = 0; c0 < nc; c0 += 128) {
-              // up to four independent update chains per thread: loads, arithmetic, stores
-              T dv[4], sv[4];
-              T* dp[4];
-#pragma unroll
-              for (int u = 0; u < 4; ++u) {
-                const int c = c0 + tx + 32 * u;
-                const bool inA = c < wa;
-                dp[u] = inA ? &sA[i * LDA + k + 1 + c] : &sR[i * ldr + (c - wa)];
-                if (c < nc) {
-                  dv[u] = *dp[u];
-                  sv[u] = inA ? sA[k * LDA + k + 1 + c] : sR[k * ldr + (c - wa)];
-                }
-              }
-#pragma unroll
-              for (int u = 0; u < 4; ++u)
-                if (c0 + tx + 32 * u < nc) A::msub(dv[u], l, sv[u]);
-#pragma unroll
-              for (int u = 0; u < 4; ++u)
-                if (c0 + tx + 32 * u < nc) *dp[u] = dv[u];
-            }
-          }
-        }
-      }
-      __syncthreads();
-    }
-    // back substitution with the unit upper triangle (row k is renormalised before use)
-    for (int k = N - 1; k > 0; --k) {
-      if constexpr (!std::is_same<T, double>::value) {
-        for (int t = tid; t < nr1; t += NT) sR[k * ldr + t] = A::norm(sR[k * ldr + t]);
-        __syncthreads();
-      }
-      for (int i = ty; i < k; i += NW) {
-        const T u = sA[i * LDA + k];
-        for (int c0 = 0; c0 < nr1; c0 += 64) {
-          const int ca = c0 + tx, cb = c0 + tx + 32;
-          T da, db, sa, sb;
-          if (ca < nr1) { da = sR[i * ldr + ca]; sa = sR[k * ldr + ca]; }
-          if (cb < nr1) { db = sR[i * ldr + cb]; sb = sR[k * ldr + cb]; }
-          if (ca < nr1) A::msub(da, u, sa);
-          if (cb < nr1) A::msub(db, u, sb);
-          if (ca < nr1) sR[i * ldr + ca] = da;
-          if (cb < nr1) sR[i * ldr + cb] = db;
-        }
-      }
-      __syncthreads();
-    }
+    lu_solve<T, N, NT>(sA, LDA, sR, ldr, nr1, &s_piv, s_pinv, &s_bad, tid);
     // X (column-major n x (nt+1)) and the interior residual; X renormalised in place
     int bad = 0;
     {

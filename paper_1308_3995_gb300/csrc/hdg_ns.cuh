@@ -1,0 +1,669 @@
+// Navier-Stokes mixed-form element kernel (12 fields: q_x, q_y, w; paper
+// Eq. strmixed and Eqs. hdg_ls1-hdg_cont with the viscous numerical flux of
+// Sec. 3.2).  Same outputs as the Euler kernel: X = A^{-1}[B | F] over the
+// element's [Q; W] unknowns, S = D - C X_B, E = H - C X_F, the residuals, and
+// the assembly into the trace system.
+//
+// Structure exploited (exact in exact arithmetic, so the outputs are the same
+// linear-algebra objects the oracle forms densely):
+//   * dN_q/dQ = (phi_i, phi_j)_K = det J * I for the orthonormal basis on an
+//     affine element, so the q unknowns are eliminated first (block Gaussian
+//     elimination with the pivot block det J * I):
+//       A' = A_ww - A_wq A_qw / det,  R'_w = R_w - A_wq R_q / det,
+//       A' X_w = R'_w (LU with partial pivoting, 4 n_p unknowns),
+//       X_q = (R_q - A_qw X_w) / det,
+//       S = D - C_q B_q / det - (C_w - C_q A_qw / det) X_w,B,
+//       E = H - C_q F_q / det - (C_w - C_q A_qw / det) X_w,F;
+//   * A_qw = (d_k phi_i, phi_j) delta_fg, B_q = -<phi_i n_k, psi_l> delta_fg and
+//     C_w = alpha <psi_l, phi_j> delta_fg come from reference tables;
+//   * A_wq and C_q are produced one (direction k', field g) block column at a
+//     time and consumed at once, so they are never stored whole.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <string>
+#include <type_traits>
+
+#include "hdg_arith.cuh"
+#include "hdg_internal.h"
+#include "hdg_lu.cuh"
+#include "hdg_physics.cuh"
+
+namespace hdg {
+
+constexpr int kNsThreads = 256;
+constexpr int kNsPt = 6;   // edge point slots per face
+
+template <int P>
+struct NsLayout {
+  static constexpr int NP = n_basis(P), NQ = (P + 2) * (P + 2), NW4 = 4 * NP, N = 12 * NP, LDA = NW4 + 1;
+  int ldr, lds, ldc;
+  int oA, oR, oCp, oS, oU, oNu, oL, oNl, oE, oDk, oPv, oPf, oW, oZ, oBc, oCc, total;
+  HDG_HD NsLayout(int ntmax) {
+    ldr = (ntmax + 1) | 1;
+    lds = (ntmax + 1) | 1;
+    ldc = (NW4 + 1) | 1;
+    oA = 0;
+    oR = oA + NW4 * LDA;
+    oCp = oR + NW4 * ldr;
+    oS = oCp + ntmax * ldc;
+    oU = oS + ntmax * lds;
+    oNu = oU + N;
+    oL = oNu + N;
+    oNl = oL + kMaxNt;
+    oE = oNl + kMaxNt;
+    oDk = oE + kMaxNt;
+    oPv = oDk + 2 * NP * NP;
+    oPf = oPv + NQ * (12 + 8 + 24 + 48);   // point values (12) + Fh (8) + Aww (24) + Awq (48)
+    oW = oPf + 3 * kNsPt * (4 + 16 + 24);
+    oZ = oW + 3 * kNsPt * 16 * 5;
+    oBc = oZ + 4 * NP * NQ;
+    oCc = oBc + NW4 * NP;
+    total = oCc + ntmax * NP;
+  }
+};
+
+template <int P, class T>
+__global__ void __launch_bounds__(kNsThreads) k_condense_ns(DevMesh m, DevSys s, Phys ph, const T* __restrict__ tab,
+                                                             TabOff to, const double* __restrict__ U,
+                                                             const double* __restrict__ Lam,
+                                                             const int* __restrict__ elems, int n_elems, int ntmax) {
+  using L = NsLayout<P>;
+  using A = Ar<T>;
+  constexpr int NP = L::NP, NQ = L::NQ, NW4 = L::NW4, N = L::N, LDA = L::LDA;
+  constexpr int NT = kNsThreads, NW = NT / 32;
+  extern __shared__ double smem_raw[];
+  T* smem = reinterpret_cast<T*>(smem_raw);
+  const L lay(ntmax);
+  const int ldr = lay.ldr, lds = lay.lds, ldc = lay.ldc;
+  T* sA = smem + lay.oA;     // A' (4 n_p x 4 n_p)
+  T* sR = smem + lay.oR;     // R'_w = [B_w | F_w] - A_wq R_q / det, then X_w
+  T* sCp = smem + lay.oCp;   // C' = C_w - C_q A_qw / det  (nt x 4 n_p)
+  T* sS = smem + lay.oS;     // S0 = D - C_q B_q / det, then S  (nt x nt)
+  T* sU = smem + lay.oU;     // element coefficients [Q; W]
+  T* sNu = smem + lay.oNu;   // interior residual [N_q; N_w]
+  T* sL = smem + lay.oL;     // traces of the three faces
+  T* sNl = smem + lay.oNl;   // this element's share of the trace residual
+  T* sE = smem + lay.oE;     // E0 = H - C_q F_q / det, then E
+  T* sDk = smem + lay.oDk;   // D_k[i][j] = (d_k phi_i, phi_j)_K, k = x, y
+  T* sPv = smem + lay.oPv;   // volume point data
+  T* sVal = sPv;             // [12][NQ] w and q at the points (fields q_x(4), q_y(4), w(4))
+  T* sFh = sVal + 12 * NQ;   // [2][4][NQ]   contravariant (f_c - f_v), weighted
+  T* sAww = sFh + 8 * NQ;    // [2][12][NQ]  contravariant d(f_c - f_v)/dw, rows 1..3
+  T* sAwq = sAww + 24 * NQ;  // [2][24][NQ]  contravariant d f_v/dq, rows 1..3
+  T* sPf = smem + lay.oPf;   // face point data per slot t = a*6 + g
+  T* sFhat = sPf;            // [18][4]  weighted numerical flux
+  T* sAl = sFhat + 18 * 4;   // [18][16] weighted d f_hat/d lambda
+  T* sAq = sAl + 18 * 16;    // [18][24] weighted d f_hat/d q, rows 1..3
+  T* sW = smem + lay.oW;     // [18][16][5] sAl * psi_l
+  T* sZ = smem + lay.oZ;     // [4][NP][NQ]
+  T* sBc = smem + lay.oBc;   // A_wq block column [4 n_p][n_p]
+  T* sCc = smem + lay.oCc;   // C_q block column [nt][n_p]
+
+  __shared__ T g_det, g_ic, g_Ji[2][2], g_n[3][2], g_len[3], g_mt;
+  __shared__ int g_e[3], g_pe[3], g_nk[3], g_toff[4], g_fl[3], g_side[3], g_old[3];
+  __shared__ unsigned char g_cf[kMaxNt], g_cg[kMaxNt], g_cl[kMaxNt];
+  __shared__ T s_pinv[64];
+  __shared__ int s_piv, s_bad;
+
+  const int tid = threadIdx.x, tx = tid & 31, ty = tid >> 5;
+  const T* vw = tab + to.vol_w[P];
+  const T* vphi = tab + to.vol_phi[P];
+  const T* vgx = tab + to.vol_gxi[P];
+  const T* vge = tab + to.vol_geta[P];
+  const T* dref = tab + to.vol_dref[P];
+  EulerConst<T> C;
+  C.gam = A::from_d(ph.gamma);
+  C.g1 = A::from_d(ph.gamma - 1.0);
+  C.three_m_gam = A::from_d(3.0 - ph.gamma);
+  C.half = A::from_d(0.5);
+  C.one = A::from_d(1.0);
+  NsConst<T> V;
+  V.half = C.half;
+  V.g1 = C.g1;
+  V.gam = C.gam;
+  V.two = A::from_d(2.0);
+  V.twothirds = A::from_d(2.0 / 3.0);
+  V.suth = A::from_d(ph.suth_s);
+  V.mu_fac = A::from_d(ph.mu_inf * (1.0 + ph.suth_s));
+  V.kfac = A::from_d(1.0 / ((ph.gamma - 1.0) * ph.prandtl));
+  const T alpha = A::from_d(ph.alpha);
+  const T zero = A::zero();
+
+  for (int it = blockIdx.x; it < n_elems; it += gridDim.x) {
+    const int K = elems[it];
+    // ---------------- a1: geometry, faces, state ----------------
+    if (tid < 3) {
+      const double* c = m.xy + 6 * (size_t)K;
+      const int a = tid, b = (tid + 1) % 3;
+      const double dx = c[2 * b] - c[2 * a], dy = c[2 * b + 1] - c[2 * a + 1];
+      const double len = sqrt(dx * dx + dy * dy);
+      const double il = __drcp_rn(len);
+      g_len[a] = A::from_d(len);
+      g_n[a][0] = A::from_d(dy * il);
+      g_n[a][1] = A::from_d(-dx * il);
+      const int e = m.elem_face[3 * (size_t)K + a];
+      const int info = m.elem_info[K];
+      g_e[a] = e;
+      g_pe[a] = m.face_p[e];
+      g_nk[a] = g_pe[a] + 1;
+      g_fl[a] = (info >> a) & 1;
+      g_side[a] = (info >> (3 + a)) & 1;
+      if (tid == 0) {
+        const double J00 = c[2] - c[0], J01 = c[4] - c[0], J10 = c[3] - c[1], J11 = c[5] - c[1];
+        const double det = J00 * J11 - J01 * J10;
+        const double inv = __drcp_rn(det);
+        g_det = A::from_d(det);
+        g_ic = A::from_d(inv);
+        g_Ji[0][0] = A::from_d(J11 * inv); g_Ji[0][1] = A::from_d(-J01 * inv);
+        g_Ji[1][0] = A::from_d(-J10 * inv); g_Ji[1][1] = A::from_d(J00 * inv);
+        double mt = 0.0;
+        if (ph.cfl > 0.0) {  // pseudo-time mass det(J)/dt_K (Sec. 3.3), element-mean state
+          const double* u0 = U + m.u_off[K] + 8 * NP;
+          const double c0 = 1.4142135623730951;  // value of the constant orthonormal mode
+          const double rho = c0 * u0[0], uu = c0 * u0[NP] / rho, vv = c0 * u0[2 * NP] / rho;
+          const double E = c0 * u0[3 * NP];
+          const double p = (ph.gamma - 1.0) * (E - 0.5 * rho * (uu * uu + vv * vv));
+          double perim = 0.0;
+          for (int l = 0; l < 3; ++l) {
+            const int l2 = (l + 1) % 3;
+            const double ex = c[2 * l2] - c[2 * l], ey = c[2 * l2 + 1] - c[2 * l + 1];
+            perim += sqrt(ex * ex + ey * ey);
+          }
+          const double Tt = ph.gamma * p / rho;
+          const double mu = ph.mu_inf * Tt * sqrt(Tt) * (1.0 + ph.suth_s) / (Tt + ph.suth_s);
+          const double lam_c = (sqrt(uu * uu + vv * vv) + sqrt(ph.gamma * p / rho)) * perim;
+          const double lam_v = ph.gamma * mu / (ph.prandtl * rho) * perim * perim / (0.5 * det);
+          const double dt = ph.cfl * 0.5 * det / (lam_c + 4.0 * lam_v);
+          mt = det / dt;
+        }
+        g_mt = A::from_d(mt);
+        s_bad = 0;
+      }
+    }
+    __syncthreads();
+    if (tid == 0) {
+      g_toff[0] = 0;
+      g_toff[1] = 4 * g_nk[0];
+      g_toff[2] = 4 * (g_nk[0] + g_nk[1]);
+      g_toff[3] = 4 * (g_nk[0] + g_nk[1] + g_nk[2]);
+    }
+    {
+      const double* uk = U + m.u_off[K];
+      for (int t = tid; t < N; t += NT) sU[t] = A::from_d(uk[t]);
+    }
+    // D_k = det * sum_r Ji[r][k] Dref_r
+    for (int t = tid; t < NP * NP; t += NT) {
+      const T d0 = dref[t], d1 = dref[NP * NP + t];
+      sDk[t] = A::mul(g_det, A::add(A::mul(g_Ji[0][0], d0), A::mul(g_Ji[1][0], d1)));
+      sDk[NP * NP + t] = A::mul(g_det, A::add(A::mul(g_Ji[0][1], d0), A::mul(g_Ji[1][1], d1)));
+    }
+    __syncthreads();
+    const int nt = g_toff[3], nr1 = nt + 1;
+    for (int c = tid; c < nt; c += NT) {
+      const int a = (c >= g_toff[2]) ? 2 : (c >= g_toff[1] ? 1 : 0);
+      const int nk = g_nk[a], cl = c - g_toff[a], g = cl / nk;
+      g_cf[c] = (unsigned char)a;
+      g_cg[c] = (unsigned char)g;
+      g_cl[c] = (unsigned char)(cl - g * nk);
+    }
+    for (int a = 0; a < 3; ++a) {
+      const double* lk = Lam + m.lam_off[g_e[a]];
+      for (int t = tid; t < 4 * g_nk[a]; t += NT) sL[g_toff[a] + t] = A::from_d(lk[t]);
+    }
+    // values of q (fields 0..7) and w (8..11) at the volume points
+    for (int t = tid; t < 12 * NQ; t += NT) {
+      const int f = t / NQ, q = t - f * NQ;
+      T acc = zero;
+#pragma unroll
+      for (int j = 0; j < NP; ++j) A::madd(acc, sU[f * NP + j], vphi[q * NP + j]);
+      sVal[t] = A::norm(acc);
+    }
+    __syncthreads();
+
+    // ---------------- a2: pointwise fluxes and Jacobians at the volume points ----------------
+    for (int q = tid; q < NQ; q += NT) {
+      T w[4], qv[2][4], fx[4], fy[4], Ax[16], Ay[16], fv[2][4], dw[2][4][4], dq[2][4][8];
+#pragma unroll
+      for (int f = 0; f < 4; ++f) {
+        w[f] = sVal[(8 + f) * NQ + q];
+        qv[0][f] = sVal[f * NQ + q];
+        qv[1][f] = sVal[(4 + f) * NQ + q];
+      }
+      euler_flux_jac(w, C, fx, fy, Ax, Ay);
+      visc_all(w, qv, V, fv, dw, dq);
+      const T c = A::mul(vw[q], g_det);
+#pragma unroll
+      for (int r = 0; r < 2; ++r) {
+        const T a0 = A::mul(c, g_Ji[r][0]), a1 = A::mul(c, g_Ji[r][1]);
+#pragma unroll
+        for (int f = 0; f < 4; ++f)
+          sFh[(r * 4 + f) * NQ + q] = A::add(A::mul(a0, A::sub(fx[f], fv[0][f])), A::mul(a1, A::sub(fy[f], fv[1][f])));
+#pragma unroll
+        for (int f = 1; f < 4; ++f)
+#pragma unroll
+          for (int g = 0; g < 4; ++g)
+            sAww[(r * 12 + (f - 1) * 4 + g) * NQ + q] =
+                A::add(A::mul(a0, A::sub(Ax[f * 4 + g], dw[0][f][g])), A::mul(a1, A::sub(Ay[f * 4 + g], dw[1][f][g])));
+#pragma unroll
+        for (int f = 1; f < 4; ++f)
+#pragma unroll
+          for (int kg = 0; kg < 8; ++kg)
+            sAwq[(r * 24 + (f - 1) * 8 + kg) * NQ + q] = A::add(A::mul(a0, dq[0][f][kg]), A::mul(a1, dq[1][f][kg]));
+      }
+    }
+    // ---------------- a3: pointwise data at the face points ----------------
+    for (int t = tid; t < 3 * kNsPt; t += NT) {
+      const int a = t / kNsPt, g = t - a * kNsPt;
+      const int pe = g_pe[a], nk = pe + 1;
+      if (g < pe + 2) {
+        const T* phe = tab + to.edge_phi[P][pe][a][g_fl[a]] + g * NP;
+        const T* ps = tab + to.edge_psi[pe] + g * nk;
+        const T we = A::mul(tab[to.edge_w[pe] + g], g_len[a]);
+        T w[4], lam[4], qv[2][4], fx[4], fy[4], Ax[16], Ay[16], fv[2][4], dw[2][4][4], dq[2][4][8];
+#pragma unroll
+        for (int f = 0; f < 12; ++f) {
+          T acc = zero;
+#pragma unroll
+          for (int j = 0; j < NP; ++j) A::madd(acc, sU[f * NP + j], phe[j]);
+          acc = A::norm(acc);
+          if (f < 4) qv[0][f] = acc; else if (f < 8) qv[1][f - 4] = acc; else w[f - 8] = acc;
+        }
+#pragma unroll
+        for (int f = 0; f < 4; ++f) {
+          T al = zero;
+          for (int k = 0; k < nk; ++k) A::madd(al, sL[g_toff[a] + f * nk + k], ps[k]);
+          lam[f] = A::norm(al);
+        }
+        euler_flux_jac(lam, C, fx, fy, Ax, Ay);
+        visc_all(lam, qv, V, fv, dw, dq);  // f_v(lambda, q_K) and its derivatives
+        const T nx = g_n[a][0], ny = g_n[a][1];
+#pragma unroll
+        for (int f = 0; f < 4; ++f)
+          sFhat[t * 4 + f] = A::mul(we, A::sub(A::add(A::mul(nx, A::sub(fx[f], fv[0][f])), A::mul(ny, A::sub(fy[f], fv[1][f]))),
+                                               A::mul(alpha, A::sub(lam[f], w[f]))));
+#pragma unroll
+        for (int f = 0; f < 4; ++f)
+#pragma unroll
+          for (int g2 = 0; g2 < 4; ++g2) {
+            T an = A::add(A::mul(nx, A::sub(Ax[f * 4 + g2], dw[0][f][g2])), A::mul(ny, A::sub(Ay[f * 4 + g2], dw[1][f][g2])));
+            if (f == g2) an = A::sub(an, alpha);
+            const T at = A::mul(we, an);
+            sAl[t * 16 + f * 4 + g2] = at;
+            for (int l = 0; l < nk; ++l) sW[(t * 16 + f * 4 + g2) * 5 + l] = A::mul(at, ps[l]);
+          }
+#pragma unroll
+        for (int f = 1; f < 4; ++f)
+#pragma unroll
+          for (int kg = 0; kg < 8; ++kg)
+            sAq[t * 24 + (f - 1) * 8 + kg] = A::neg(A::mul(we, A::add(A::mul(nx, dq[0][f][kg]), A::mul(ny, dq[1][f][kg]))));
+      }
+    }
+    __syncthreads();
+
+    // ---------------- residuals ----------------
+    // N_q[(k,f),i] = det Q[(k,f),i] + sum_j D_k[i][j] W[f][j] - sum_a n_k |e_a| sum_l Me_a[l][i] Lam_a[f][l]
+    for (int t = tid; t < 8 * NP; t += NT) {
+      const int kf = t / NP, i = t - kf * NP, k = kf >> 2, f = kf & 3;
+      T acc = zero;
+      A::madd(acc, g_det, sU[t]);
+      for (int j = 0; j < NP; ++j) A::madd(acc, sDk[k * NP * NP + i * NP + j], sU[(8 + f) * NP + j]);
+      for (int a = 0; a < 3; ++a) {
+        const int nk = g_nk[a];
+        const T* me = tab + to.edge_cross[P][g_pe[a]][a][g_fl[a]];
+        const T sc = A::mul(g_n[a][k], g_len[a]);
+        T s2 = zero;
+        for (int l = 0; l < nk; ++l) A::madd(s2, me[l * NP + i], sL[g_toff[a] + f * nk + l]);
+        A::msub(acc, sc, A::norm(s2));
+      }
+      sNu[t] = A::norm(acc);
+    }
+    // N_w = -(grad phi, f_c - f_v)_K + <phi, f_hat>_dK
+    for (int t = tid; t < NW4; t += NT) {
+      const int f = t / NP, i = t - f * NP;
+      T acc0 = zero, acc1 = zero;
+      for (int q = 0; q < NQ; ++q) {
+        A::msub(acc0, vgx[q * NP + i], sFh[f * NQ + q]);
+        A::msub(acc1, vge[q * NP + i], sFh[(4 + f) * NQ + q]);
+      }
+      T acc = A::add(A::norm(acc0), A::norm(acc1));
+      for (int a = 0; a < 3; ++a) {
+        const T* phe = tab + to.edge_phi[P][g_pe[a]][a][g_fl[a]];
+        for (int q = 0; q < g_pe[a] + 2; ++q) A::madd(acc, phe[q * NP + i], sFhat[(a * kNsPt + q) * 4 + f]);
+      }
+      sNu[8 * NP + t] = A::norm(acc);
+    }
+    for (int t = tid; t < nt; t += NT) {
+      const int a = g_cf[t], f = g_cg[t], k = g_cl[t], nk = g_nk[a];
+      const T* ps = tab + to.edge_psi[g_pe[a]];
+      T acc = zero;
+      for (int q = 0; q < nk + 1; ++q) A::madd(acc, ps[q * nk + k], sFhat[(a * kNsPt + q) * 4 + f]);
+      acc = A::norm(acc);
+      sNl[t] = acc;
+      sE[t] = A::neg(acc);  // H
+    }
+    // ---------------- A_ww (volume), B_w, D, C_w ----------------
+    // constant row 0: A_00 = A_03 = 0, A_01 = -D_x, A_02 = -D_y (the mass flux has no viscous part)
+    for (int t = tid; t < NP * NP; t += NT) {
+      const int i = t / NP, j = t - i * NP;
+      T* a0 = sA + i * LDA + j;
+      a0[0] = zero;
+      a0[NP] = A::neg(sDk[t]);
+      a0[2 * NP] = A::neg(sDk[NP * NP + t]);
+      a0[3 * NP] = zero;
+    }
+    // B_w: rows (f,i) over warps, trace columns over lanes
+    for (int r = ty; r < NW4; r += NW) {
+      const int f = r / NP, i = r - f * NP;
+      for (int c = tx; c < nt; c += 32) {
+        const int a = g_cf[c], g = g_cg[c], l = g_cl[c], nk = g_nk[a];
+        const T* phe = tab + to.edge_phi[P][g_pe[a]][a][g_fl[a]];
+        T acc = zero;
+        for (int q = 0; q < nk + 1; ++q) A::madd(acc, phe[q * NP + i], sW[((a * kNsPt + q) * 16 + f * 4 + g) * 5 + l]);
+        sR[r * ldr + c] = A::norm(acc);
+      }
+    }
+    // S0 = D (block diagonal over faces), zero elsewhere
+    for (int r = ty; r < nt; r += NW) {
+      const int a = g_cf[r], f = g_cg[r], k = g_cl[r], nk = g_nk[a];
+      const T* ps = tab + to.edge_psi[g_pe[a]];
+      for (int c = tx; c < nt; c += 32) {
+        T acc = zero;
+        if (g_cf[c] == a) {
+          const int g = g_cg[c], l = g_cl[c];
+          for (int q = 0; q < nk + 1; ++q) A::madd(acc, ps[q * nk + k], sW[((a * kNsPt + q) * 16 + f * 4 + g) * 5 + l]);
+          acc = A::norm(acc);
+        }
+        sS[r * lds + c] = acc;
+      }
+    }
+    // C' starts as C_w = alpha |e_a| <psi_l, phi_j> delta_fg
+    for (int r = ty; r < nt; r += NW) {
+      const int a = g_cf[r], f = g_cg[r], l = g_cl[r];
+      const T* me = tab + to.edge_cross[P][g_pe[a]][a][g_fl[a]];
+      const T sc = A::mul(alpha, g_len[a]);
+      for (int c = tx; c < NW4; c += 32) {
+        const int g = c / NP, j = c - g * NP;
+        sCp[r * ldc + c] = (g == f) ? A::mul(sc, me[l * NP + j]) : zero;
+      }
+    }
+    // state-dependent rows f = 1..3 of A_ww: Z_g[i][q] = sum_r dphi_i/dxi_r Ahat_r,fg; A_fg = -Z phi^T
+    for (int f = 1; f < 4; ++f) {
+      for (int t = tid; t < 4 * NP * NQ; t += NT) {
+        const int g = t / (NP * NQ), rem = t - g * NP * NQ, i = rem / NQ, q = rem - i * NQ;
+        sZ[t] = A::add(A::mul(vgx[q * NP + i], sAww[((f - 1) * 4 + g) * NQ + q]),
+                       A::mul(vge[q * NP + i], sAww[(12 + (f - 1) * 4 + g) * NQ + q]));
+      }
+      __syncthreads();
+      for (int t = tid; t < 4 * NP * NP; t += NT) {
+        const int g = t / (NP * NP), rem = t - g * NP * NP, i = rem / NP, j = rem - i * NP;
+        const T* z = sZ + (g * NP + i) * NQ;
+        T acc0 = zero, acc1 = zero;
+        for (int q = 0; q + 1 < NQ; q += 2) {
+          A::msub(acc0, z[q], vphi[q * NP + j]);
+          A::msub(acc1, z[q + 1], vphi[(q + 1) * NP + j]);
+        }
+        if (NQ & 1) A::msub(acc0, z[NQ - 1], vphi[(NQ - 1) * NP + j]);
+        sA[(f * NP + i) * LDA + g * NP + j] = A::add(A::norm(acc0), A::norm(acc1));
+      }
+      __syncthreads();
+    }
+    // face mass alpha <phi_i, phi_j>_dK and the pseudo-time mass on the diagonal blocks; F_w
+    for (int t = tid; t < NP * NP; t += NT) {
+      const int i = t / NP, j = t - i * NP;
+      T v = zero;
+      for (int a = 0; a < 3; ++a) A::madd(v, g_len[a], tab[to.face_mass[P][g_pe[a]][a] + t]);
+      v = A::mul(alpha, A::norm(v));
+      if (i == j) v = A::add(v, g_mt);
+#pragma unroll
+      for (int f = 0; f < 4; ++f) {
+        T* p = &sA[(f * NP + i) * LDA + f * NP + j];
+        *p = A::add(*p, v);
+      }
+    }
+    for (int t = tid; t < NW4; t += NT) sR[t * ldr + nt] = A::neg(sNu[8 * NP + t]);
+    __syncthreads();
+
+    // ---------------- q elimination, one (k', g) block column at a time ----------------
+    const T ic = g_ic;
+    for (int kk = 0; kk < 8; ++kk) {
+      const int kd = kk >> 2, gq = kk & 3;
+      // Z'_f[i][q] = sum_r dphi_i/dxi_r Ahat^wq_r,f,kk (rows f = 1..3)
+      for (int t = tid; t < 3 * NP * NQ; t += NT) {
+        const int f1 = t / (NP * NQ), rem = t - f1 * NP * NQ, i = rem / NQ, q = rem - i * NQ;
+        sZ[t] = A::add(A::mul(vgx[q * NP + i], sAwq[(f1 * 8 + kk) * NQ + q]),
+                       A::mul(vge[q * NP + i], sAwq[(24 + f1 * 8 + kk) * NQ + q]));
+      }
+      // C_q block column: rows (a, f, l), C_q = <psi_l, (-n.df_v/dq)_f,kk phi_j>_e
+      for (int r = ty; r < nt; r += NW) {
+        const int a = g_cf[r], f = g_cg[r], l = g_cl[r], nk = g_nk[a];
+        const T* phe = tab + to.edge_phi[P][g_pe[a]][a][g_fl[a]];
+        const T* ps = tab + to.edge_psi[g_pe[a]];
+        for (int j = tx; j < NP; j += 32) {
+          T acc = zero;
+          if (f > 0)
+            for (int q = 0; q < nk + 1; ++q)
+              A::madd(acc, A::mul(ps[q * nk + l], sAq[(a * kNsPt + q) * 24 + (f - 1) * 8 + kk]), phe[q * NP + j]);
+          sCc[r * NP + j] = A::norm(acc);
+        }
+      }
+      __syncthreads();
+      // A_wq block column: volume (Z' phi^T) + face <phi_i, (-n.df_v/dq) phi_j>_dK; row 0 is zero
+      for (int t = tid; t < NW4 * NP; t += NT) {
+        const int r = t / NP, j = t - r * NP, f = r / NP, i = r - f * NP;
+        T acc = zero;
+        if (f > 0) {
+          const T* z = sZ + ((f - 1) * NP + i) * NQ;
+          for (int q = 0; q < NQ; ++q) A::madd(acc, z[q], vphi[q * NP + j]);
+          for (int a = 0; a < 3; ++a) {
+            const T* phe = tab + to.edge_phi[P][g_pe[a]][a][g_fl[a]];
+            for (int q = 0; q < g_pe[a] + 2; ++q)
+              A::madd(acc, A::mul(phe[q * NP + i], sAq[(a * kNsPt + q) * 24 + (f - 1) * 8 + kk]), phe[q * NP + j]);
+          }
+        }
+        sBc[t] = A::norm(acc);
+      }
+      __syncthreads();
+      const T* Dk = sDk + kd * NP * NP;
+      // (i) A'[(f,i),(g,j)] -= 1/det sum_i' A_wq[(f,i),i'] D_k'[i'][j]
+      for (int t = tid; t < NW4 * NP; t += NT) {
+        const int r = t / NP, j = t - r * NP;
+        T acc = zero;
+        for (int i2 = 0; i2 < NP; ++i2) A::madd(acc, sBc[r * NP + i2], Dk[i2 * NP + j]);
+        T* p = &sA[r * LDA + gq * NP + j];
+        A::msub(*p, ic, A::norm(acc));
+        *p = A::norm(*p);
+      }
+      // (ii)+(iii) R'_w -= 1/det A_wq R_q, with B_q = -n_k' |e_a| <phi_i', psi_l> on columns of field g
+      for (int r = ty; r < NW4; r += NW) {
+        for (int c = tx; c < nr1; c += 32) {
+          T acc = zero;
+          if (c == nt) {
+            for (int i2 = 0; i2 < NP; ++i2) A::msub(acc, sBc[r * NP + i2], sNu[kk * NP + i2]);  // F_q = -N_q
+          } else if (g_cg[c] == gq) {
+            const int a = g_cf[c], l = g_cl[c];
+            const T* me = tab + to.edge_cross[P][g_pe[a]][a][g_fl[a]];
+            T s2 = zero;
+            for (int i2 = 0; i2 < NP; ++i2) A::madd(s2, sBc[r * NP + i2], me[l * NP + i2]);
+            acc = A::neg(A::mul(A::mul(g_n[a][kd], g_len[a]), A::norm(s2)));   // A_wq B_q
+          } else {
+            continue;
+          }
+          T* p = &sR[r * ldr + c];
+          A::msub(*p, ic, A::norm(acc));
+          *p = A::norm(*p);
+        }
+      }
+      // (iv) C' -= 1/det C_q A_qw;  (v)+(vi) S0 -= 1/det C_q B_q, E0 -= 1/det C_q F_q
+      for (int r = ty; r < nt; r += NW) {
+        for (int c = tx; c < NP; c += 32) {
+          T acc = zero;
+          for (int i2 = 0; i2 < NP; ++i2) A::madd(acc, sCc[r * NP + i2], Dk[i2 * NP + c]);
+          T* p = &sCp[r * ldc + gq * NP + c];
+          A::msub(*p, ic, A::norm(acc));
+          *p = A::norm(*p);
+        }
+        for (int c = tx; c < nr1; c += 32) {
+          T acc = zero;
+          if (c == nt) {
+            for (int i2 = 0; i2 < NP; ++i2) A::msub(acc, sCc[r * NP + i2], sNu[kk * NP + i2]);
+            T* p = &sE[r];
+            A::msub(*p, ic, A::norm(acc));
+            *p = A::norm(*p);
+          } else if (g_cg[c] == gq) {
+            const int a = g_cf[c], l = g_cl[c];
+            const T* me = tab + to.edge_cross[P][g_pe[a]][a][g_fl[a]];
+            T s2 = zero;
+            for (int i2 = 0; i2 < NP; ++i2) A::madd(s2, sCc[r * NP + i2], me[l * NP + i2]);
+            acc = A::neg(A::mul(A::mul(g_n[a][kd], g_len[a]), A::norm(s2)));   // C_q B_q
+            T* p = &sS[r * lds + c];
+            A::msub(*p, ic, A::norm(acc));
+            *p = A::norm(*p);
+          }
+        }
+      }
+      __syncthreads();
+    }
+
+    // ---------------- a4/a5: LU with partial pivoting on [A' | R'_w] ----------------
+    lu_solve<T, NW4, NT>(sA, LDA, sR, ldr, nr1, &s_piv, s_pinv, &s_bad, tid);
+    int bad = 0;
+    // X_w (renormalised in place) and the interior residual
+    {
+      double* xk = s.X + m.x_off[K];
+      for (int t = tid; t < NW4 * nr1; t += NT) {
+        const int c = t / NW4, r = t - c * NW4;
+        const T v = A::norm(sR[r * ldr + c]);
+        sR[r * ldr + c] = v;
+        xk[(size_t)c * N + 8 * NP + r] = A::to_d(v);
+        bad |= A::bad(v);
+      }
+      double* ru = s.res_u + m.u_off[K];
+      for (int t = tid; t < N; t += NT) ru[t] = A::to_d(sNu[t]);
+    }
+    __syncthreads();
+    // X_q = (R_q - A_qw X_w) / det
+    {
+      double* xk = s.X + m.x_off[K];
+      for (int t = tid; t < 8 * NP * nr1; t += NT) {
+        const int c = t / (8 * NP), r = t - c * (8 * NP), kf = r / NP, i = r - kf * NP, k = kf >> 2, f = kf & 3;
+        T acc = zero;
+        if (c == nt) {
+          acc = A::neg(sNu[r]);                           // F_q
+        } else if (g_cg[c] == f) {
+          const int a = g_cf[c], l = g_cl[c];
+          const T* me = tab + to.edge_cross[P][g_pe[a]][a][g_fl[a]];
+          acc = A::neg(A::mul(A::mul(g_n[a][k], g_len[a]), me[l * NP + i]));   // B_q
+        }
+        for (int j = 0; j < NP; ++j) A::msub(acc, sDk[k * NP * NP + i * NP + j], sR[(f * NP + j) * ldr + c]);
+        const T v = A::mul(A::norm(acc), ic);
+        xk[(size_t)c * N + r] = A::to_d(v);
+        bad |= A::bad(v);
+      }
+    }
+    // ---------------- a6/a7: S = S0 - C' X_w,B, E = E0 - C' X_w,F, assembly ----------------
+    for (int r = ty; r < nt; r += NW) {
+      const int a = g_cf[r], rl = r - g_toff[a];
+      for (int c = tx; c < nr1; c += 32) {
+        T v = (c == nt) ? sE[r] : sS[r * lds + c];
+        for (int j = 0; j < NW4; ++j) A::msub(v, sCp[r * ldc + j], sR[j * ldr + c]);
+        v = A::norm(v);
+        bad |= A::bad(v);
+        if (c == nt) {
+          sE[r] = v;
+        } else {
+          const int b = g_cf[c];
+          if (b == a) sS[r * lds + c] = v;
+          else s.K[m.kblk[9 * (size_t)K + 3 * a + b] + rl * (4 * g_nk[b]) + (c - g_toff[b])] = A::to_d(v);
+        }
+      }
+    }
+    if (bad) atomicOr(&s_bad, 2);
+    __syncthreads();
+    // two-sided sums: side 0 parks its halves in K/E/res_lam, side 1 in the work space
+    for (int a = 0; a < 3; ++a) {
+      const int e = g_e[a], m4 = 4 * g_nk[a], o = g_toff[a];
+      const int64_t lo = m.lam_off[e];
+      double* dd = g_side[a] ? s.dhalf1 + m.dblk_off[e] : s.K + m.kblk[9 * (size_t)K + 4 * a];
+      double* de = g_side[a] ? s.ehalf1 + lo : s.E + lo;
+      double* dr = g_side[a] ? s.rhalf1 + lo : s.res_lam + lo;
+      for (int t = tid; t < m4 * m4; t += NT) {
+        const int r = t / m4, c = t - r * m4;
+        dd[t] = A::to_d(sS[(o + r) * lds + o + c]);
+      }
+      for (int t = tid; t < m4; t += NT) {
+        de[t] = A::to_d(sE[o + t]);
+        dr[t] = A::to_d(sNl[o + t]);
+      }
+    }
+    __threadfence();
+    __syncthreads();
+    if (tid < 3) {
+      g_old[tid] = atomicAdd(&s.face_cnt[g_e[tid]], 1);
+      __threadfence();
+    }
+    __syncthreads();
+    for (int a = 0; a < 3; ++a) {
+      if (g_old[a] != 1) continue;
+      const int e = g_e[a], m4 = 4 * g_nk[a], o = g_toff[a];
+      const int64_t lo = m.lam_off[e];
+      double* k0 = s.K + m.kblk[9 * (size_t)K + 4 * a];
+      const double* k1 = s.dhalf1 + m.dblk_off[e];
+      const int side = g_side[a];
+      for (int t = tid; t < m4 * m4; t += NT) {
+        const int r = t / m4, c = t - r * m4;
+        const double mine = A::to_d(sS[(o + r) * lds + o + c]);
+        const double other = side ? __ldcg(k0 + t) : __ldcg(k1 + t);
+        k0[t] = side ? other + mine : mine + other;
+      }
+      for (int t = tid; t < m4; t += NT) {
+        const double me_ = A::to_d(sE[o + t]), mr = A::to_d(sNl[o + t]);
+        const double oe = side ? __ldcg(s.E + lo + t) : __ldcg(s.ehalf1 + lo + t);
+        const double orr = side ? __ldcg(s.res_lam + lo + t) : __ldcg(s.rhalf1 + lo + t);
+        s.E[lo + t] = side ? oe + me_ : me_ + oe;
+        s.res_lam[lo + t] = side ? orr + mr : mr + orr;
+      }
+      if (tid == 0) s.face_cnt[e] = 0;
+    }
+    if (tid == 0) s.status[K] = (s_bad & 1) ? 1 : ((s_bad & 2) ? 2 : 0);
+    __syncthreads();
+  }
+}
+
+template <int P, class T>
+inline bool launch_ns_bucket(const DevMesh& m, const DevSys& s, const Phys& ph, const T* tab, const TabOff& to,
+                             const double* U, const double* Lam, const int* elems, int n, int ntmax, cudaStream_t st,
+                             std::string* err) {
+  const NsLayout<P> lay(ntmax);
+  const size_t bytes = sizeof(T) * (size_t)lay.total;
+  cudaError_t ce = cudaFuncSetAttribute(k_condense_ns<P, T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+  if (ce != cudaSuccess) { *err = std::string("NS kernel shared memory: ") + cudaGetErrorString(ce); return false; }
+  int dev = 0, sms = 0, per_sm = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_condense_ns<P, T>, kNsThreads, bytes);
+  if (per_sm < 1) { *err = "NS condensation kernel does not fit on an SM"; return false; }
+  long grid = (long)sms * per_sm;
+  if (grid > n) grid = n;
+  k_condense_ns<P, T><<<(int)grid, kNsThreads, bytes, st>>>(m, s, ph, tab, to, U, Lam, elems, n, ntmax);
+  ce = cudaGetLastError();
+  if (ce != cudaSuccess) { *err = cudaGetErrorString(ce); return false; }
+  return true;
+}
+
+template <class T>
+inline bool launch_ns_p(int p, const DevMesh& m, const DevSys& s, const Phys& ph, const T* tab, const TabOff& to,
+                        const double* U, const double* Lam, const int* elems, int n, int ntmax, cudaStream_t st,
+                        std::string* err) {
+  switch (p) {
+    case 1: return launch_ns_bucket<1, T>(m, s, ph, tab, to, U, Lam, elems, n, ntmax, st, err);
+    case 2: return launch_ns_bucket<2, T>(m, s, ph, tab, to, U, Lam, elems, n, ntmax, st, err);
+    case 3: return launch_ns_bucket<3, T>(m, s, ph, tab, to, U, Lam, elems, n, ntmax, st, err);
+    case 4: return launch_ns_bucket<4, T>(m, s, ph, tab, to, U, Lam, elems, n, ntmax, st, err);
+  }
+  *err = "degree out of range";
+  return false;
+}
+
+}  // namespace hdg
