@@ -203,6 +203,17 @@ hdg_status hdg_step_host(hdg_sys* sys, const double* U, const double* Lam, const
 hdg_status hdg_step_host_async(hdg_sys* sys, const double* U, const double* Lam, const double* dLam, double* dU,
                                void* stream);
 
+/* Capture one whole step on this system -- arrival-counter reset, the
+ * condensation of every degree bucket (buckets on their own streams, joined),
+ * and the reconstruction -- into a CUDA graph owned by sys, for the DEVICE
+ * buffers U, Lam, dLam, dU given here (their addresses are baked into the
+ * graph).  Runs the step once outside the capture first (results valid after
+ * the call).  A later call replaces the graph. */
+hdg_status hdg_graph_create(hdg_sys* sys, const double* U, const double* Lam, const double* dLam, double* dU);
+/* Replay the captured step on `stream` (asynchronous); inputs are read from the
+ * buffers given to hdg_graph_create. */
+hdg_status hdg_graph_launch(hdg_sys* sys, void* stream);
+
 /* Device views of the outputs (owned by sys, valid until hdg_sys_destroy):
  * X [x_len], K_vals [k_len], E [lam_len], res_u [u_len] = interior residual
  * [N_q; N_w] per element, res_lam [lam_len] = trace residual summed over both

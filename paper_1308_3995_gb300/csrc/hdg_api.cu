@@ -45,6 +45,14 @@ struct hdg_sys {
   std::vector<void*> allocs;
   int launches = 0;
   bool need_zero = true;
+  // degree buckets launched concurrently: one stream and one event per degree, a fork event
+  cudaStream_t bstream[kMaxP + 1] = {};
+  cudaEvent_t bevent[kMaxP + 1] = {};
+  cudaEvent_t fork = nullptr;
+  bool have_streams = false;
+  // captured step (hdg_graph_create)
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t gexec = nullptr;
 };
 
 namespace {
@@ -381,7 +389,25 @@ hdg_sys* sys_new(hdg_ctx* ctx, const hdg_mesh* M, const hdg_params* P) {
   S->ph.cfl = P->cfl;
   S->ph.model = P->model;
   S->ph.precision = P->precision;
+  S->ph.persistent = 1;
   return S;
+}
+
+int n_buckets(const hdg_mesh* M) {
+  int nb = 0;
+  for (int p = 1; p <= kMaxP; ++p) nb += M->bucket_n[p] > 0;
+  return nb;
+}
+
+hdg_status ensure_streams(hdg_sys* S) {
+  if (S->have_streams) return HDG_OK;
+  for (int p = 1; p <= kMaxP; ++p) {
+    HDG_CK(S->ctx, cudaStreamCreateWithFlags(&S->bstream[p], cudaStreamNonBlocking));
+    HDG_CK(S->ctx, cudaEventCreateWithFlags(&S->bevent[p], cudaEventDisableTiming));
+  }
+  HDG_CK(S->ctx, cudaEventCreateWithFlags(&S->fork, cudaEventDisableTiming));
+  S->have_streams = true;
+  return HDG_OK;
 }
 
 void sys_bind(hdg_sys* S, void* const* p) {
@@ -457,6 +483,15 @@ hdg_status hdg_sys_create_in(hdg_ctx* ctx, const hdg_mesh* M, const hdg_params* 
 hdg_status hdg_sys_destroy(hdg_sys* S) {
   if (!S) return HDG_EINVAL;
   cudaSetDevice(S->ctx->device);
+  if (S->gexec) cudaGraphExecDestroy(S->gexec);
+  if (S->graph) cudaGraphDestroy(S->graph);
+  if (S->have_streams) {
+    for (int p = 1; p <= kMaxP; ++p) {
+      cudaStreamDestroy(S->bstream[p]);
+      cudaEventDestroy(S->bevent[p]);
+    }
+    cudaEventDestroy(S->fork);
+  }
   free_all(S->allocs);
   delete S;
   return HDG_OK;
@@ -467,13 +502,38 @@ hdg_status hdg_condense(hdg_sys* S, const double* U, const double* Lam, void* st
   hdg_ctx* ctx = S->ctx;
   if (!U || !Lam) return fail(ctx, HDG_EINVAL, "hdg_condense: null input");
   const hdg_mesh* M = S->mesh;
+  cudaStream_t st = (cudaStream_t)stream;
   if (S->need_zero) {
-    HDG_CK(ctx, cudaMemsetAsync(S->ds.face_cnt, 0, 4 * (size_t)M->n_face, (cudaStream_t)stream));
+    HDG_CK(ctx, cudaMemsetAsync(S->ds.face_cnt, 0, 4 * (size_t)M->n_face, st));
     S->need_zero = false;
   }
   std::string err;
-  const int n = launch_condense(M->dm, S->ds, S->ph, ctx->d_tab, ctx->d_tab_ff, ctx->tab.off, U, Lam, M->d_bucket, M->bucket_n,
-                                M->bucket_ntmax, stream, &err);
+  int n;
+  if (n_buckets(M) > 1) {
+    // degree buckets run concurrently: fork onto one stream per degree, join back;
+    // one CTA per element so the CTAs of the buckets interleave on the SMs
+    hdg_status rs = ensure_streams(S);
+    if (rs != HDG_OK) return rs;
+    HDG_CK(ctx, cudaEventRecord(S->fork, st));
+    void* bs[kMaxP + 1] = {};
+    for (int p = 1; p <= kMaxP; ++p) {
+      bs[p] = S->bstream[p];
+      if (M->bucket_n[p]) HDG_CK(ctx, cudaStreamWaitEvent(S->bstream[p], S->fork, 0));
+    }
+    Phys ph = S->ph;
+    ph.persistent = 0;
+    n = launch_condense(M->dm, S->ds, ph, ctx->d_tab, ctx->d_tab_ff, ctx->tab.off, U, Lam, M->d_bucket, M->bucket_n,
+                        M->bucket_ntmax, stream, &err, bs);
+    if (n >= 0)
+      for (int p = 1; p <= kMaxP; ++p)
+        if (M->bucket_n[p]) {
+          HDG_CK(ctx, cudaEventRecord(S->bevent[p], S->bstream[p]));
+          HDG_CK(ctx, cudaStreamWaitEvent(st, S->bevent[p], 0));
+        }
+  } else {
+    n = launch_condense(M->dm, S->ds, S->ph, ctx->d_tab, ctx->d_tab_ff, ctx->tab.off, U, Lam, M->d_bucket,
+                        M->bucket_n, M->bucket_ntmax, stream, &err);
+  }
   if (n < 0) return fail(ctx, HDG_ECUDA, "hdg_condense: " + err);
   S->launches = n;
   return HDG_OK;
@@ -515,6 +575,46 @@ hdg_status hdg_step_host(hdg_sys* S, const double* U, const double* Lam, const d
   const hdg_status rc = hdg_step_host_async(S, U, Lam, dLam, dU, stream);
   if (rc != HDG_OK) return rc;
   HDG_CK(S->ctx, cudaStreamSynchronize((cudaStream_t)stream));
+  return HDG_OK;
+}
+
+hdg_status hdg_graph_create(hdg_sys* S, const double* U, const double* Lam, const double* dLam, double* dU) {
+  if (!S) return HDG_EINVAL;
+  hdg_ctx* ctx = S->ctx;
+  if (!U || !Lam || !dLam || !dU) return fail(ctx, HDG_EINVAL, "hdg_graph_create: null argument");
+  const hdg_mesh* M = S->mesh;
+  if (S->gexec) { cudaGraphExecDestroy(S->gexec); S->gexec = nullptr; }
+  if (S->graph) { cudaGraphDestroy(S->graph); S->graph = nullptr; }
+  cudaStream_t cs;
+  HDG_CK(ctx, cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
+  // one plain step first: kernel attributes are set outside the capture
+  hdg_status rc = hdg_condense(S, U, Lam, cs);
+  if (rc == HDG_OK) rc = hdg_recover(S, dLam, dU, cs);
+  cudaError_t e = cudaStreamSynchronize(cs);
+  if (rc == HDG_OK && e != cudaSuccess) rc = fail(ctx, HDG_ECUDA, std::string("hdg_graph_create: ") + cudaGetErrorString(e));
+  if (rc == HDG_OK) {
+    e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeRelaxed);
+    if (e == cudaSuccess) e = cudaMemsetAsync(S->ds.face_cnt, 0, 4 * (size_t)M->n_face, cs);
+    if (e == cudaSuccess) {
+      rc = hdg_condense(S, U, Lam, cs);
+      if (rc == HDG_OK) rc = hdg_recover(S, dLam, dU, cs);
+    }
+    cudaGraph_t g = nullptr;
+    const cudaError_t e2 = cudaStreamEndCapture(cs, &g);
+    if (e == cudaSuccess) e = e2;
+    if (e == cudaSuccess && rc == HDG_OK) e = cudaGraphInstantiate(&S->gexec, g, 0);
+    S->graph = g;
+    if (rc == HDG_OK && e != cudaSuccess)
+      rc = fail(ctx, HDG_ECUDA, std::string("hdg_graph_create: ") + cudaGetErrorString(e));
+  }
+  cudaStreamDestroy(cs);
+  return rc;
+}
+
+hdg_status hdg_graph_launch(hdg_sys* S, void* stream) {
+  if (!S) return HDG_EINVAL;
+  if (!S->gexec) return fail(S->ctx, HDG_EINVAL, "hdg_graph_launch: no graph (call hdg_graph_create)");
+  HDG_CK(S->ctx, cudaGraphLaunch(S->gexec, (cudaStream_t)stream));
   return HDG_OK;
 }
 

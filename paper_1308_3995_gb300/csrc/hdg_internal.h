@@ -42,6 +42,7 @@ void build_tables(Tables& T);
 struct Phys {
   double gamma, alpha, prandtl, mu_inf, suth_s, cfl;
   int model, precision;
+  int persistent;  // 1: grid = SMs x resident CTAs (loop over elements); 0: one CTA per element
 };
 
 // Device-resident mesh plan handed to kernels by value.
@@ -92,12 +93,15 @@ struct PlanRef {
 PlanRef plan_ref(const hdg_mesh* mesh);
 
 // kernel launchers (hdg_kernels.cu); return the number of launches enqueued
+// bucket_streams (optional, indexed by degree p): stream of each degree bucket's launch
 int launch_condense(const DevMesh& m, const DevSys& s, const Phys& ph, const double* tab, const void* tab_ff,
                     const TabOff& off, const double* U, const double* Lam, const int* const* bucket,
-                    const int* bucket_n, const int* bucket_ntmax, void* stream, std::string* err);
+                    const int* bucket_n, const int* bucket_ntmax, void* stream, std::string* err,
+                    void* const* bucket_streams = nullptr);
 int launch_condense_ns(const DevMesh& m, const DevSys& s, const Phys& ph, const double* tab, const void* tab_ff,
                        const TabOff& off, const double* U, const double* Lam, const int* const* bucket,
-                       const int* bucket_n, const int* bucket_ntmax, void* stream, std::string* err);
+                       const int* bucket_n, const int* bucket_ntmax, void* stream, std::string* err,
+                       void* const* bucket_streams = nullptr);
 int launch_recover_buckets(const DevMesh& m, const double* X, const double* dLam, double* dU,
                            const int* const* bucket, const int* bucket_n, void* stream, std::string* err);
 

@@ -510,7 +510,7 @@ static bool launch_euler_bucket(const DevMesh& m, const DevSys& s, const Phys& p
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
   cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_condense_euler<P, T>, kCondThreads, bytes);
   if (per_sm < 1) { *err = "condensation kernel does not fit on an SM"; return false; }
-  long grid = (long)sms * per_sm;
+  long grid = ph.persistent ? (long)sms * per_sm : (long)n;
   if (grid > n) grid = n;
   k_condense_euler<P, T><<<(int)grid, kCondThreads, bytes, st>>>(m, s, ph, tab, to, U, Lam, elems, n, ldr, nkmax);
   ce = cudaGetLastError();
@@ -534,13 +534,15 @@ static bool launch_euler_p(int p, const DevMesh& m, const DevSys& s, const Phys&
 
 int launch_condense(const DevMesh& m, const DevSys& s, const Phys& ph, const double* tab, const void* tab_ff,
                     const TabOff& to, const double* U, const double* Lam, const int* const* bucket,
-                    const int* bucket_n, const int* bucket_ntmax, void* stream, std::string* err) {
-  cudaStream_t st = (cudaStream_t)stream;
-  int launches = 0;
+                    const int* bucket_n, const int* bucket_ntmax, void* stream, std::string* err,
+                    void* const* bucket_streams) {
   if (ph.model == HDG_NS_MIXED)
-    return launch_condense_ns(m, s, ph, tab, tab_ff, to, U, Lam, bucket, bucket_n, bucket_ntmax, stream, err);
+    return launch_condense_ns(m, s, ph, tab, tab_ff, to, U, Lam, bucket, bucket_n, bucket_ntmax, stream, err,
+                              bucket_streams);
+  int launches = 0;
   for (int p = 1; p <= kMaxP; ++p) {
     if (bucket_n[p] == 0) continue;
+    cudaStream_t st = (cudaStream_t)(bucket_streams ? bucket_streams[p] : stream);
     bool ok;
     if (ph.precision == HDG_FP64)
       ok = launch_euler_p<double>(p, m, s, ph, tab, to, U, Lam, bucket[p], bucket_n[p], bucket_ntmax[p], st, err);

@@ -9,11 +9,12 @@ bool launch_ns_ff(int p, const DevMesh& m, const DevSys& s, const Phys& ph, cons
 
 int launch_condense_ns(const DevMesh& m, const DevSys& s, const Phys& ph, const double* tab, const void* tab_ff,
                        const TabOff& to, const double* U, const double* Lam, const int* const* bucket,
-                       const int* bucket_n, const int* bucket_ntmax, void* stream, std::string* err) {
-  cudaStream_t st = (cudaStream_t)stream;
+                       const int* bucket_n, const int* bucket_ntmax, void* stream, std::string* err,
+                       void* const* bucket_streams) {
   int launches = 0;
   for (int p = 1; p <= kMaxP; ++p) {
     if (bucket_n[p] == 0) continue;
+    cudaStream_t st = (cudaStream_t)(bucket_streams ? bucket_streams[p] : stream);
     bool ok;
     if (ph.precision == HDG_FP64)
       ok = launch_ns_p<double>(p, m, s, ph, tab, to, U, Lam, bucket[p], bucket_n[p], bucket_ntmax[p], st, err);

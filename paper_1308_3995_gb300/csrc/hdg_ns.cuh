@@ -644,7 +644,7 @@ inline bool launch_ns_bucket(const DevMesh& m, const DevSys& s, const Phys& ph, 
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
   cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_condense_ns<P, T>, kNsThreads, bytes);
   if (per_sm < 1) { *err = "NS condensation kernel does not fit on an SM"; return false; }
-  long grid = (long)sms * per_sm;
+  long grid = ph.persistent ? (long)sms * per_sm : (long)n;
   if (grid > n) grid = n;
   k_condense_ns<P, T><<<(int)grid, kNsThreads, bytes, st>>>(m, s, ph, tab, to, U, Lam, elems, n, ntmax);
   ce = cudaGetLastError();

@@ -31,7 +31,7 @@ EXPORTS = ["hdg_create", "hdg_destroy", "hdg_last_error", "hdg_mesh_create", "hd
            "hdg_mesh_layout", "hdg_footprint_bytes", "hdg_sys_create", "hdg_sys_destroy", "hdg_condense",
            "hdg_recover", "hdg_step_host", "hdg_sys_get", "hdg_sys_launches", "hdg_debug_tables",
            "hdg_condense_noalloc", "hdg_sys_workspace_bytes", "hdg_sys_create_in",
-           "hdg_step_host_async"]
+           "hdg_step_host_async", "hdg_graph_create", "hdg_graph_launch"]
 
 
 class HdgError(RuntimeError):
@@ -97,6 +97,8 @@ def lib(build: bool = True):
         L.hdg_recover.argtypes = [_vp, _vp, _vp, _vp]
         L.hdg_step_host.argtypes = [_vp, _vp, _vp, _vp, _vp, _vp]
         L.hdg_step_host_async.argtypes = [_vp, _vp, _vp, _vp, _vp, _vp]
+        L.hdg_graph_create.argtypes = [_vp, _vp, _vp, _vp, _vp]
+        L.hdg_graph_launch.argtypes = [_vp, _vp]
         L.hdg_sys_get.argtypes = [_vp] + [ctypes.POINTER(_vp)] * 6
         L.hdg_sys_launches.argtypes = [_vp]
         L.hdg_sys_launches.restype = ctypes.c_int32
@@ -270,6 +272,14 @@ class System:
         def hp(a):
             return a.data_ptr() if hasattr(a, "data_ptr") else a.ctypes.data
         _check(lib().hdg_step_host_async(self.h, hp(U), hp(Lam), hp(dLam), hp(dU), _stream(stream)), self.ctx.h)
+
+    def graph_create(self, U, Lam, dLam, dU):
+        """hdg_graph_create: capture the whole step for these device tensors."""
+        _check(lib().hdg_graph_create(self.h, _ptr(U), _ptr(Lam), _ptr(dLam), _ptr(dU)), self.ctx.h)
+
+    def graph_launch(self, stream=None):
+        """hdg_graph_launch: replay the captured step on `stream`."""
+        _check(lib().hdg_graph_launch(self.h, _stream(stream)), self.ctx.h)
 
     @property
     def launches(self) -> int:
