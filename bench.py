@@ -35,7 +35,7 @@ FP64_PEAK_TFLOPS = 1.25     # nominal GB300 FP64 rate (recipe table); see DESIGN
 L2_FLUSH_BYTES = 256 << 20  # > 129 MB L2
 # dram__bytes_read.sum + dram__bytes_write.sum per condensation launch from ncu
 # (profiles/), scaled to the full workload by elements; only for unchanged kernels
-TRAFFIC_PER_LAUNCH = {}
+TRAFFIC_PER_LAUNCH = {("euler_p3_16k", 0): 12720128 + 516691712}
 
 
 def dense_condensation_flops(n: int, nt: int) -> float:
