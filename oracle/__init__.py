@@ -39,7 +39,8 @@ def build(force: bool = False) -> str:
 class OrcParams(ctypes.Structure):
     _fields_ = [("model", ctypes.c_int32), ("reserved", ctypes.c_int32), ("gamma", ctypes.c_double),
                 ("prandtl", ctypes.c_double), ("reynolds", ctypes.c_double), ("mach", ctypes.c_double),
-                ("alpha", ctypes.c_double), ("cfl", ctypes.c_double), ("t_inf", ctypes.c_double)]
+                ("alpha", ctypes.c_double), ("cfl", ctypes.c_double), ("t_inf", ctypes.c_double),
+                ("sc_eps0", ctypes.c_double), ("sc_beta", ctypes.c_double)]
 
 
 _lib = None
@@ -82,6 +83,8 @@ def lib():
         L.orc_monolithic.argtypes = [ctypes.c_void_p, P, _c_double_p, _c_double_p, _c_double_p, _c_double_p,
                                      _c_double_p]
         L.orc_dense_solve.argtypes = [ctypes.c_int, _c_double_p, _c_double_p]
+        L.orc_sc_epsilon.argtypes = [ctypes.c_void_p, P, ctypes.c_int, _c_double_p]
+        L.orc_sc_epsilon.restype = ctypes.c_double
         _lib = L
     return _lib
 
@@ -166,10 +169,12 @@ class Params:
     alpha: float = 1.5
     cfl: float = 0.0
     t_inf: float = 288.15
+    sc_eps0: float = 0.0     # shock capturing off unless > 0 (paper's value: 0.2)
+    sc_beta: float = 0.0
 
     def c(self) -> OrcParams:
         return OrcParams(self.model, 0, self.gamma, self.prandtl, self.reynolds, self.mach, self.alpha,
-                         self.cfl, self.t_inf)
+                         self.cfl, self.t_inf, self.sc_eps0, self.sc_beta)
 
     @property
     def nfield(self) -> int:
@@ -232,6 +237,11 @@ class Mesh:
         P = params.c()
         lib().orc_element_residual(self._h, ctypes.byref(P), int(K), _d(_f64(U)), _d(_f64(Lam)), _d(Nu), _d(Nl))
         return Nu, Nl
+
+    def sc_epsilon(self, params, K, U):
+        """Shock-capturing viscosity eps_K of element K (Sec. 3.2); 0 when off."""
+        P = params.c()
+        return float(lib().orc_sc_epsilon(self._h, ctypes.byref(P), int(K), _d(_f64(U))))
 
     def element_blocks(self, params, K, U, Lam):
         n, nt = self.n(K), self.nt(K)

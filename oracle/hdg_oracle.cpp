@@ -12,9 +12,12 @@
 //     flux, temperature, Newtonian stress and Sutherland viscosity (Sec. 2.2);
 //   * the HDG residual N_h of Eq. (hdg_ls1)-(hdg_cont) with the combined
 //     Lax-Friedrichs/LDG-type numerical flux of Sec. 3.2 (source s = 0,
-//     no boundary operator: meshes are periodic, no shock capturing);
+//     no boundary operator: meshes are periodic), optionally with the
+//     shock-capturing volume term of Sec. 3.2 (artificial viscosity eps_K from
+//     the L1 norm of the strong convective residual, effective size h_K / p_K);
 //   * the Newton matrix N'_h (Eq. linearsystem) as the exact complex-step
-//     derivative of that residual, column by column, plus the optional
+//     derivative of that residual, column by column (eps_K frozen at the
+//     current state: it is evaluated from the real part only), plus the optional
 //     backward-Euler pseudo-time mass term with the local time step of Sec. 3.3;
 //   * static condensation of Sec. 3.4: K = N - [L M][A B;C D]^{-1}[R;S],
 //     E = H - [L M][A B;C D]^{-1}[F;G], assembled element by element, the
@@ -51,6 +54,8 @@ typedef struct {
   double alpha;      // constant scalar stabilisation alpha = alpha_c + alpha_v (Sec. 3.2)
   double cfl;        // <= 0: pure Newton (dt = inf); else backward-Euler pseudo time (Sec. 3.3)
   double t_inf;      // dimensional free-stream temperature [K] for Sutherland's C2
+  double sc_eps0;    // shock capturing factor eps_0 (Sec. 3.2); <= 0: no shock capturing
+  double sc_beta;    // exponent beta of the effective mesh size h_K / p_K
 } orc_params;
 }
 
@@ -258,6 +263,7 @@ static void ensure_tables() { std::call_once(g_once, init_tables); }
 // Physics (Sec. 2), templated so that the complex-step derivative works.
 // w = (rho, rho u, rho v, E); f[k][f] = flux in direction k of field f.
 // ---------------------------------------------------------------------------
+static const double CS_H_SC = 1e-30;  // complex step of the divergence in sc_epsilon
 template <class T>
 static void euler_flux(const T* w, double gam, T f[2][4]) {
   T rho = w[0], mx = w[1], my = w[2], E = w[3];
@@ -347,9 +353,58 @@ static inline int elem_flip(const OMesh& M, int K, int lf) {
 // hdg_cont), for element K with its coefficient vectors U (Q then W) and the
 // traces L of its three faces in local order.  Nu has the layout of U, Nl of L.
 // ---------------------------------------------------------------------------
+// Shock-capturing viscosity of Sec. 3.2, from the real state U of element K:
+//   eps_K = eps_0 (h_K / p_K)^(2 - beta) / |K| * int_K d(w) dx,
+//   d(w) = sum over the 4 fields of |(div f_c(w))_f|,
+// with h_K the longest edge of K.  The divergence of the convective flux of
+// the polynomial w_h is the chain rule sum_k (d f_k / d w)(w) d w / d x_k,
+// each term taken as the complex-step derivative of f_k along d w / d x_k.
+// For Navier-Stokes the gradient d w / d x_k is the q_h unknown.
+static double sc_epsilon(const OMesh& M, const orc_params& P, int K, const Geom& g, const double* U) {
+  if (!(P.sc_eps0 > 0.0)) return 0.0;
+  const int p = M.p[K], np = n_basis(p);
+  const bool ns = (M.nfield == 12);
+  const int woff = ns ? 8 * np : 0;
+  const VolTab& V = g_vol[p];
+  double integral = 0.0;
+  for (int q = 0; q < V.nq; ++q) {
+    const double* phi = &V.phi[q * np];
+    double w[4], grad[2][4];
+    for (int f = 0; f < 4; ++f) {
+      w[f] = 0.0;
+      grad[0][f] = 0.0;
+      grad[1][f] = 0.0;
+      for (int j = 0; j < np; ++j) {
+        const double dx = V.dxi[q * np + j], de = V.deta[q * np + j];
+        w[f] += U[woff + f * np + j] * phi[j];
+        if (ns) {
+          grad[0][f] += U[f * np + j] * phi[j];
+          grad[1][f] += U[(4 + f) * np + j] * phi[j];
+        } else {
+          grad[0][f] += U[f * np + j] * (g.Jinv[0][0] * dx + g.Jinv[1][0] * de);
+          grad[1][f] += U[f * np + j] * (g.Jinv[0][1] * dx + g.Jinv[1][1] * de);
+        }
+      }
+    }
+    double div[4] = {0.0, 0.0, 0.0, 0.0};
+    for (int k = 0; k < 2; ++k) {
+      cplx wc[4], fc[2][4];
+      for (int f = 0; f < 4; ++f) wc[f] = cplx(w[f], CS_H_SC * grad[k][f]);
+      euler_flux(wc, P.gamma, fc);
+      for (int f = 0; f < 4; ++f) div[f] += fc[k][f].imag() / CS_H_SC;
+    }
+    double d = 0.0;
+    for (int f = 0; f < 4; ++f) d += std::fabs(div[f]);
+    integral += V.w[q] * g.detJ * d;
+  }
+  const double hK = std::max(g.len[0], std::max(g.len[1], g.len[2]));
+  return P.sc_eps0 * std::pow(hK / p, 2.0 - P.sc_beta) / g.area * integral;
+}
+
+// eps is the element's shock-capturing viscosity (0: none), a constant here.
 template <class T>
 static void element_residual(const OMesh& M, const orc_params& P, int K, const Geom& g,
-                             const T* U, const T* L, T* Nu, T* Nl) {
+                             const T* U, const T* L, T* Nu, T* Nl, double eps) {
   const int p = M.p[K], np = n_basis(p);
   const bool ns = (M.nfield == 12);
   const int woff = ns ? 8 * np : 0;
@@ -388,6 +443,21 @@ static void element_residual(const OMesh& M, const orc_params& P, int K, const G
     for (int f = 0; f < 4; ++f)
       for (int i = 0; i < np; ++i)
         Nu[woff + f * np + i] -= wq * (gx[i] * (fc[0][f] - fv[0][f]) + gy[i] * (fc[1][f] - fv[1][f]));
+    // shock capturing: + eps (grad phi_i, grad w_f)_K (Euler) or (grad phi_i, q_f)_K (NS)
+    if (eps != 0.0)
+      for (int f = 0; f < 4; ++f) {
+        T gwx = 0.0, gwy = 0.0;
+        if (ns) {
+          gwx = qv[0][f];
+          gwy = qv[1][f];
+        } else {
+          for (int j = 0; j < np; ++j) {
+            gwx += U[woff + f * np + j] * gx[j];
+            gwy += U[woff + f * np + j] * gy[j];
+          }
+        }
+        for (int i = 0; i < np; ++i) Nu[woff + f * np + i] += wq * eps * (gx[i] * gwx + gy[i] * gwy);
+      }
     // (tau, q)_K + (div tau, w)_K
     if (ns)
       for (int k = 0; k < 2; ++k)
@@ -479,12 +549,13 @@ static void element_blocks(const OMesh& M, const orc_params& P, int K, const dou
   std::vector<cplx> Uc(n), Lc(nt), Nu(n), Nl(nt);
   for (int r = 0; r < n; ++r) Uc[r] = U[r];
   for (int r = 0; r < nt; ++r) Lc[r] = L[r];
-  element_residual<cplx>(M, P, K, g, Uc.data(), Lc.data(), Nu.data(), Nl.data());
+  const double eps = sc_epsilon(M, P, K, g, U);  // frozen: not differentiated
+  element_residual<cplx>(M, P, K, g, Uc.data(), Lc.data(), Nu.data(), Nl.data(), eps);
   for (int r = 0; r < n; ++r) F[r] = -Nu[r].real();
   for (int r = 0; r < nt; ++r) H[r] = -Nl[r].real();
   for (int c = 0; c < n + nt; ++c) {
     if (c < n) Uc[c] += cplx(0.0, CS_H); else Lc[c - n] += cplx(0.0, CS_H);
-    element_residual<cplx>(M, P, K, g, Uc.data(), Lc.data(), Nu.data(), Nl.data());
+    element_residual<cplx>(M, P, K, g, Uc.data(), Lc.data(), Nu.data(), Nl.data(), eps);
     if (c < n) Uc[c] = U[c]; else Lc[c - n] = L[c - n];
     for (int r = 0; r < n; ++r) {
       double d = Nu[r].imag() / CS_H;
@@ -755,7 +826,8 @@ int orc_element_residual(void* h, const orc_params* P, int K, const double* U, c
   elem_geom(*M, K, g);
   std::vector<double> L;
   gather_trace(*M, K, Lam, L);
-  element_residual<double>(*M, *P, K, g, U + M->u_off[K], L.data(), Nu, Nl);
+  element_residual<double>(*M, *P, K, g, U + M->u_off[K], L.data(), Nu, Nl,
+                           sc_epsilon(*M, *P, K, g, U + M->u_off[K]));
   return 0;
 }
 
@@ -854,7 +926,8 @@ int orc_global_residual(void* h, const orc_params* P, const double* U, const dou
     std::vector<double> L;
     gather_trace(*M, K, Lam, L);
     std::vector<double> nu(elem_n(*M, K)), nl(elem_nt(*M, K));
-    element_residual<double>(*M, *P, K, g, U + M->u_off[K], L.data(), nu.data(), nl.data());
+    element_residual<double>(*M, *P, K, g, U + M->u_off[K], L.data(), nu.data(), nl.data(),
+                             sc_epsilon(*M, *P, K, g, U + M->u_off[K]));
     std::copy(nu.begin(), nu.end(), R + M->u_off[K]);
     int roff = 0;
     for (int a = 0; a < 3; ++a) {
@@ -891,7 +964,8 @@ int orc_monolithic(void* h, const orc_params* P, const double* U, const double* 
         for (int r = 0; r < 4 * (M->face_p[e] + 1); ++r) L.push_back(Lc[M->lam_off[e] + r]);
       }
       std::vector<cplx> nu(elem_n(*M, K)), nl(elem_nt(*M, K));
-      element_residual<cplx>(*M, *P, K, g, Uc.data() + M->u_off[K], L.data(), nu.data(), nl.data());
+      element_residual<cplx>(*M, *P, K, g, Uc.data() + M->u_off[K], L.data(), nu.data(), nl.data(),
+                             sc_epsilon(*M, *P, K, g, U + M->u_off[K]));
       for (size_t r = 0; r < nu.size(); ++r) Rc[M->u_off[K] + r] = nu[r];
       int roff = 0;
       for (int a = 0; a < 3; ++a) {
@@ -923,6 +997,14 @@ int orc_monolithic(void* h, const orc_params* P, const double* U, const double* 
   std::copy(x.begin(), x.begin() + M->u_len, dU);
   std::copy(x.begin() + M->u_len, x.end(), dLam);
   return 0;
+}
+
+// Shock-capturing viscosity eps_K of element K (0 when P->sc_eps0 <= 0).
+double orc_sc_epsilon(void* h, const orc_params* P, int K, const double* U) {
+  OMesh* M = (OMesh*)h;
+  Geom g;
+  elem_geom(*M, K, g);
+  return sc_epsilon(*M, *P, K, g, U + M->u_off[K]);
 }
 
 // Dense LU solve helper for tests (A n x n row-major, b -> x in place).

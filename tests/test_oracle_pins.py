@@ -476,3 +476,150 @@ def test_periodic_pure_newton_row_dependence():
         sl = J0[rows_l].sum(0)
         assert np.abs(sw - sl).max() < 1e-12 * np.abs(J0).max()
     assert np.linalg.matrix_rank(J0) <= J0.shape[0] - 4
+
+
+# ----------------------------------------------------------------------------- shock capturing
+def _linear_density_state(m, K, rho0, grad_rho, u0, v0, p0, q_scale=1.0):
+    """Element K of an otherwise zero state: rho linear in x, velocity and pressure constant, so all
+    four conserved variables are linear (exactly representable for p >= 1; coefficients by least
+    squares on the pinned basis).  NS: q = q_scale * grad w (constant, mode 0 only).  Returns U, the
+    conserved gradients [2][4] and the element's area and longest edge."""
+    p = int(m.elem_p[K]); nb = O.n_basis(p)
+    xy = m.elem_xy[K].reshape(3, 2); x0 = xy[0]
+    J = np.stack([xy[1] - x0, xy[2] - x0], 1)
+    gr = np.asarray(grad_rho, dtype=float)
+    vv = 0.5 * (u0 * u0 + v0 * v0)
+    gw = np.stack([gr, u0 * gr, v0 * gr, vv * gr], 1)            # [2][4]: d w_f / d x_k
+
+    def wfun(x):
+        rho = rho0 + (x - x0) @ gr
+        return np.stack([rho, rho * u0, rho * v0, p0 / (GAMMA - 1) + rho * vv], -1)
+
+    xi, eta, _ = O.tri_rule(p + 1)
+    phi, _, _ = O.dubiner(p, xi, eta)
+    coef, *_ = np.linalg.lstsq(phi, wfun(x0 + np.stack([xi, eta], 1) @ J.T), rcond=None)   # [nb, 4]
+    U = np.zeros(m.u_len)
+    off = m.u_off[K]
+    if m.nfield == 12:
+        for k in range(2):
+            for f in range(4):
+                U[off + (k * 4 + f) * nb] = q_scale * gw[k, f] / math.sqrt(2)
+        off += 8 * nb
+    U[off:off + 4 * nb] = coef.T.reshape(-1)
+    edges = [np.linalg.norm(xy[(i + 1) % 3] - xy[i]) for i in range(3)]
+    return U, gw, 0.5 * np.linalg.det(J), max(edges)
+
+
+@pytest.mark.parametrize("p,beta", [(1, 0.0), (3, 0.0), (2, 1.0)])
+def test_sc_epsilon_closed_form_linear_state(p, beta):
+    """Sec. 3.2 shock capturing: for rho linear and (u0, v0, p0) constant, div f_c(w) =
+    (s, u0 s, v0 s, |v|^2/2 s) with s = v . grad rho, constant on K, so
+    eps_K = eps0 (h_K / p_K)^(2 - beta) |s| (1 + |u0| + |v0| + |v|^2/2) (h_K = longest edge)."""
+    wl, c, m, P = _case("euler_p1_256", 4, 3, jitter=0.2, p=p)
+    P.sc_eps0, P.sc_beta = 0.2, beta
+    u0, v0 = 0.7, -0.3
+    for K in (2, 9):
+        U, gw, area, hK = _linear_density_state(m, K, 1.1, [0.4, -0.25], u0, v0, 0.8)
+        s = u0 * 0.4 + v0 * (-0.25)
+        d = abs(s) * (1 + abs(u0) + abs(v0) + 0.5 * (u0 * u0 + v0 * v0))
+        ref = 0.2 * (hK / p) ** (2 - beta) * d
+        assert abs(m.sc_epsilon(P, K, U) - ref) < 1e-13 * ref
+    P.sc_eps0 = 0.0
+    assert m.sc_epsilon(P, 2, U) == 0.0
+
+
+@pytest.mark.parametrize("model", [0, 1])
+def test_sc_free_stream_has_no_viscosity(model):
+    """A constant state has div f_c = 0, hence eps_K = 0 and an unchanged residual (Sec. 3.2)."""
+    wl, c, m, P = _case("ns_mixp_65k", 3, 3, model=model)
+    U, L = _uniform_state(m, G.conserved(*G.free_stream(0.5, 1.0)))
+    P.sc_eps0 = 0.2
+    for K in range(0, m.n_elem, 5):
+        assert m.sc_epsilon(P, K, U) == 0.0
+
+
+@pytest.mark.parametrize("p", [1, 3])
+def test_sc_residual_energy_identity_linear_state(p):
+    """Euler: the shock-capturing term adds eps (grad phi_i, grad w_f)_K to N_w, so with the
+    coefficients W of a linear state, W . dN = eps |K| sum_f |grad w_f|^2; the constant mode is
+    untouched (grad phi_0 = 0)."""
+    wl, c, m, P = _case("euler_p1_256", 4, 3, jitter=0.2, p=p)
+    K = 7
+    U, gw, area, hK = _linear_density_state(m, K, 0.9, [-0.3, 0.5], 0.6, 0.2, 0.7)
+    _, L = _uniform_state(m, _cons(1.0, 0.5, 0.1, 0.7))   # any admissible trace
+    n0, _ = m.element_residual(P, K, U, L)
+    P.sc_eps0 = 0.2
+    eps = m.sc_epsilon(P, K, U)
+    assert eps > 0
+    n1, _ = m.element_residual(P, K, U, L)
+    dN = n1 - n0
+    W = U[m.u_off[K]:m.u_off[K + 1]]
+    ref = eps * area * (gw ** 2).sum()
+    assert abs(W @ dN - ref) < 1e-12 * ref
+    nb = O.n_basis(p)
+    assert np.abs(dN.reshape(4, nb)[:, 0]).max() < 1e-15 * np.abs(dN).max()
+
+
+def test_sc_ns_uses_q_in_place_of_grad_w():
+    """Navier-Stokes (Sec. 3.2): the gradient in both d(w) and the volume term is q_h.  With
+    q = grad w the viscosity equals the Euler closed form; with q = 2 grad w it doubles, and
+    W . dN_w = eps |K| sum_f grad w_f . q_f."""
+    wl, c, m, P = _case("ns_mixp_65k", 3, 3, model=1)
+    K = 4
+    p = int(m.elem_p[K]); nb = O.n_basis(p)
+    u0, v0 = 0.5, 0.1
+    s = u0 * 0.3 + v0 * 0.2
+    d = abs(s) * (1 + abs(u0) + abs(v0) + 0.5 * (u0 * u0 + v0 * v0))
+    _, L = _uniform_state(m, _cons(1.0, 0.5, 0.1, 0.7))   # any admissible trace
+    for qs in (1.0, 2.0):
+        U, gw, area, hK = _linear_density_state(m, K, 1.0, [0.3, 0.2], u0, v0, 0.7, q_scale=qs)
+        P.sc_eps0 = 0.0
+        n0, _ = m.element_residual(P, K, U, L)
+        P.sc_eps0 = 0.2
+        eps = m.sc_epsilon(P, K, U)
+        assert abs(eps - qs * 0.2 * (hK / p) ** 2 * d) < 1e-13 * eps
+        n1, _ = m.element_residual(P, K, U, L)
+        dN = (n1 - n0)[8 * nb:]
+        W = U[m.u_off[K] + 8 * nb:m.u_off[K + 1]]
+        ref = eps * area * qs * (gw ** 2).sum()
+        assert abs(W @ dN - ref) < 1e-12 * ref
+        assert np.abs((n1 - n0)[:8 * nb]).max() == 0.0        # the q equations have no sc term
+
+
+@pytest.mark.parametrize("model", [0, 1])
+def test_sc_jacobian_is_frozen_viscosity_times_stiffness(model):
+    """Sec. 3.2 term with eps_K frozen at the current state: only the W rows change; Euler: the W-W
+    block gains eps (grad phi_i, grad phi_j)_K per field (symmetric, constants in its null space);
+    NS: the W-Q block gains eps (d_k phi_i, phi_j)_K per field; in both cases dA U = dN (the term
+    is linear in U once eps is fixed) and B, C, D are unchanged."""
+    wl, c, m, P = _case("euler_p3_262k_shock", 4, 4, model=model)
+    U, L, _ = G.case_state(c, m.face_vid, m.face_p)
+    for K in (1, 6):
+        P.sc_eps0 = 0.0
+        A0, B0, C0, D0, F0, H0 = m.element_blocks(P, K, U, L)
+        P.sc_eps0 = 0.2
+        eps = m.sc_epsilon(P, K, U)
+        assert eps > 0
+        A1, B1, C1, D1, F1, H1 = m.element_blocks(P, K, U, L)
+        assert np.array_equal(B0, B1) and np.array_equal(C0, C1) and np.array_equal(D0, D1)
+        assert np.array_equal(H0, H1)
+        p = int(m.elem_p[K]); nb = O.n_basis(p)
+        xy = m.elem_xy[K].reshape(3, 2)
+        J = np.stack([xy[1] - xy[0], xy[2] - xy[0]], 1); det = np.linalg.det(J); Ji = np.linalg.inv(J)
+        xi, eta, w = O.tri_rule(p)
+        phi, dxi, deta = O.dubiner(p, xi, eta)
+        g = [dxi * Ji[0, k] + deta * Ji[1, k] for k in range(2)]
+        dA = A1 - A0
+        UK = U[m.u_off[K]:m.u_off[K + 1]]
+        if model == 0:
+            St = det * sum((gk * w[:, None]).T @ gk for gk in g)
+            assert np.abs(dA - eps * np.kron(np.eye(4), St)).max() < 1e-13 * np.abs(A1).max()
+        else:
+            ref = np.zeros_like(dA)
+            for k in range(2):
+                Dk = det * (g[k] * w[:, None]).T @ phi
+                for f in range(4):
+                    ref[(8 + f) * nb:(9 + f) * nb, (k * 4 + f) * nb:(k * 4 + f + 1) * nb] = eps * Dk
+            assert np.abs(dA - ref).max() < 1e-13 * np.abs(A1).max()
+        dN = -(F1 - F0)      # a difference of O(|F|) residuals: rounding ~ u |F|
+        assert np.abs(dA @ UK - dN).max() < 1e-12 * np.abs(dN).max() + 1e-13 * np.abs(F0).max()
