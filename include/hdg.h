@@ -115,6 +115,15 @@ typedef struct {
   double refine_tol;   /* reserved for refinement-based precisions (unused) */
   int32_t refine_max;  /* reserved for refinement-based precisions (unused) */
   int32_t reserved;
+  /* Shock capturing, Sec. 3.2 (artificial viscosity, volume term only):
+   *   N_w += eps_K (grad phi, grad w)_K   (Euler)   or   eps_K (grad phi, q)_K   (NS),
+   *   eps_K = sc_eps0 (h_K / p_K)^(2 - sc_beta) / |K| * int_K sum_f |(div f_c(w))_f| dx,
+   * h_K the longest edge of K; for NS the gradient in div f_c is q.  eps_K is
+   * evaluated at the given state and held fixed in the Newton matrix (the
+   * Jacobian does not differentiate it).  sc_eps0 <= 0 disables the term
+   * (paper's values when needed: sc_eps0 = 0.2, sc_beta = 0). */
+  double sc_eps0;
+  double sc_beta;
 } hdg_params;
 
 /* Create a context on CUDA device `device` (makes it current on this thread). */

@@ -31,7 +31,7 @@ def build(force: bool = False) -> str:
     if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < os.path.getmtime(_SRC):
         tmp = _LIB + f".tmp{os.getpid()}"
         subprocess.check_call(["g++", "-O2", "-std=c++17", "-ffp-contract=off", "-fPIC", "-shared",
-                               "-o", tmp, _SRC])
+                               "-pthread", "-o", tmp, _SRC])
         os.replace(tmp, _LIB)
     return _LIB
 
@@ -78,6 +78,8 @@ def lib():
                                            _c_double_p, _c_double_p, _c_double_p]
         L.orc_condense.argtypes = [ctypes.c_void_p, P, _c_double_p, _c_double_p] + [_c_double_p] * 5 + \
             [_c_i32_p, ctypes.c_int, ctypes.c_int]
+        L.orc_condense_mt.argtypes = [ctypes.c_void_p, P, _c_double_p, _c_double_p] + [_c_double_p] * 5 + \
+            [_c_i32_p, ctypes.c_int, ctypes.c_int, ctypes.c_int]
         L.orc_recover.argtypes = [ctypes.c_void_p, _c_double_p, _c_double_p, _c_double_p]
         L.orc_global_residual.argtypes = [ctypes.c_void_p, P, _c_double_p, _c_double_p, _c_double_p]
         L.orc_monolithic.argtypes = [ctypes.c_void_p, P, _c_double_p, _c_double_p, _c_double_p, _c_double_p,
@@ -260,12 +262,14 @@ class Mesh:
                                         _d(X), _d(S), _d(E))
         return X, S, E, st
 
-    def condense(self, params, U, Lam, k0=0, k1=0):
+    def condense(self, params, U, Lam, k0=0, k1=0, threads=1):
+        """Condensation and assembly of elements [k0, k1) (all if k1 <= k0); `threads` > 1 spreads the
+        per-element work over host threads (bitwise the same outputs)."""
         X = np.zeros(self.x_len); Kv = np.zeros(self.k_len); E = np.zeros(self.lam_len)
         rU = np.zeros(self.u_len); rL = np.zeros(self.lam_len); st = np.zeros(self.n_elem, np.int32)
         P = params.c()
-        lib().orc_condense(self._h, ctypes.byref(P), _d(_f64(U)), _d(_f64(Lam)), _d(X), _d(Kv), _d(E), _d(rU),
-                           _d(rL), _i32(st), int(k0), int(k1))
+        lib().orc_condense_mt(self._h, ctypes.byref(P), _d(_f64(U)), _d(_f64(Lam)), _d(X), _d(Kv), _d(E), _d(rU),
+                              _d(rL), _i32(st), int(k0), int(k1), int(threads))
         return dict(X=X, K=Kv, E=E, res_u=rU, res_lam=rL, status=st)
 
     def recover(self, X, dLam):

@@ -39,6 +39,7 @@
 #include <cstdint>
 #include <cstring>
 #include <mutex>
+#include <thread>
 #include <vector>
 
 typedef std::complex<double> cplx;
@@ -854,6 +855,71 @@ int orc_element_condense(void* h, const orc_params* P, int K, const double* U, c
   return st;
 }
 
+// Assembly of one element's condensed blocks into K, E and the trace residual
+// (the element's 3x3 face-pair blocks of S_K into the 5-block rows of its faces).
+static void scatter_element(const OMesh& M, int K, const std::vector<double>& s, const std::vector<double>& ek,
+                            const std::vector<double>& nl, double* Kv, double* E, double* resLam) {
+  const int nt = elem_nt(M, K);
+  int roff = 0;
+  for (int a = 0; a < 3; ++a) {
+    int ea = M.elem_face[K * 3 + a], na = 4 * (M.face_p[ea] + 1);
+    for (int r = 0; r < na; ++r) {
+      E[M.lam_off[ea] + r] += ek[roff + r];
+      resLam[M.lam_off[ea] + r] += nl[roff + r];
+    }
+    int coff = 0;
+    for (int b = 0; b < 3; ++b) {
+      int eb = M.elem_face[K * 3 + b], nb = 4 * (M.face_p[eb] + 1);
+      int slot = -1;
+      for (int t = 0; t < 5; ++t)
+        if (M.k_col[5 * ea + t] == eb) slot = t;
+      double* blk = Kv + M.k_blkoff[5 * ea + slot];
+      for (int r = 0; r < na; ++r)
+        for (int c = 0; c < nb; ++c) blk[r * nb + c] += s[(roff + r) * nt + coff + c];
+      coff += nb;
+    }
+    roff += na;
+  }
+}
+
+// Same, with the per-element work of [k0, k1) spread over nthreads threads
+// (std::thread; each element's arithmetic is unchanged); the assembly runs
+// afterwards in ascending element order, so every output is bitwise the same
+// as with one thread.
+int orc_condense_mt(void* h, const orc_params* P, const double* U, const double* Lam, double* X, double* Kv,
+                    double* E, double* resU, double* resLam, int32_t* status, int k0, int k1, int nthreads) {
+  OMesh* M = (OMesh*)h;
+  if (k1 <= k0) { k0 = 0; k1 = M->ne; }
+  if (nthreads < 1) nthreads = 1;
+  std::fill(Kv, Kv + M->k_len, 0.0);
+  std::fill(E, E + M->lam_len, 0.0);
+  std::fill(resLam, resLam + M->lam_len, 0.0);
+  const int cnt = k1 - k0;
+  std::vector<std::vector<double>> S(cnt), EK(cnt), NL(cnt);
+  auto work = [&](int t) {
+    for (int i = t; i < cnt; i += nthreads) {
+      const int K = k0 + i;
+      std::vector<double> x, nu;
+      status[K] = element_condense(*M, *P, K, U, Lam, x, S[i], EK[i], &nu, &NL[i]);
+      std::copy(x.begin(), x.end(), X + M->x_off[K]);
+      std::copy(nu.begin(), nu.end(), resU + M->u_off[K]);
+    }
+  };
+  if (nthreads == 1) {
+    work(0);
+  } else {
+    std::vector<std::thread> th;
+    for (int t = 0; t < nthreads; ++t) th.emplace_back(work, t);
+    for (auto& t : th) t.join();
+  }
+  int bad = 0;
+  for (int i = 0; i < cnt; ++i) {
+    bad |= status[k0 + i];
+    scatter_element(*M, k0 + i, S[i], EK[i], NL[i], Kv, E, resLam);
+  }
+  return bad ? 1 : 0;
+}
+
 // Whole-mesh condensation and assembly: X [x_len], K [k_len], E [lam_len],
 // resU [u_len], resLam [lam_len] (sum over both sides), status [n_elem].
 // Elements are processed in ascending id, so every diagonal block and every
@@ -861,42 +927,7 @@ int orc_element_condense(void* h, const orc_params* P, int K, const double* U, c
 // Elements [k0, k1) only if k1 > k0 (then K/E/resLam hold partial sums).
 int orc_condense(void* h, const orc_params* P, const double* U, const double* Lam, double* X, double* Kv,
                  double* E, double* resU, double* resLam, int32_t* status, int k0, int k1) {
-  OMesh* M = (OMesh*)h;
-  if (k1 <= k0) { k0 = 0; k1 = M->ne; }
-  std::fill(Kv, Kv + M->k_len, 0.0);
-  std::fill(E, E + M->lam_len, 0.0);
-  std::fill(resLam, resLam + M->lam_len, 0.0);
-  int bad = 0;
-  for (int K = k0; K < k1; ++K) {
-    std::vector<double> x, s, ek, nu, nl;
-    int st = element_condense(*M, *P, K, U, Lam, x, s, ek, &nu, &nl);
-    status[K] = st;
-    bad |= st;
-    std::copy(x.begin(), x.end(), X + M->x_off[K]);
-    std::copy(nu.begin(), nu.end(), resU + M->u_off[K]);
-    const int nt = elem_nt(*M, K);
-    int roff = 0;
-    for (int a = 0; a < 3; ++a) {
-      int ea = M->elem_face[K * 3 + a], na = 4 * (M->face_p[ea] + 1);
-      for (int r = 0; r < na; ++r) {
-        E[M->lam_off[ea] + r] += ek[roff + r];
-        resLam[M->lam_off[ea] + r] += nl[roff + r];
-      }
-      int coff = 0;
-      for (int b = 0; b < 3; ++b) {
-        int eb = M->elem_face[K * 3 + b], nb = 4 * (M->face_p[eb] + 1);
-        int slot = -1;
-        for (int t = 0; t < 5; ++t)
-          if (M->k_col[5 * ea + t] == eb) slot = t;
-        double* blk = Kv + M->k_blkoff[5 * ea + slot];
-        for (int r = 0; r < na; ++r)
-          for (int c = 0; c < nb; ++c) blk[r * nb + c] += s[(roff + r) * nt + coff + c];
-        coff += nb;
-      }
-      roff += na;
-    }
-  }
-  return bad ? 1 : 0;
+  return orc_condense_mt(h, P, U, Lam, X, Kv, E, resU, resLam, status, k0, k1, 1);
 }
 
 // Reconstruction, Eq. (ls): dU_K = X_F - X_B dLambda_K for every element.

@@ -372,6 +372,8 @@ hdg_status sys_validate(hdg_ctx* ctx, const hdg_mesh* M, const hdg_params* P, co
     return fail(ctx, HDG_EINVAL, w + ": Navier-Stokes needs reynolds, prandtl, t_inf > 0");
   if (!(P->gamma > 1.0) || !(P->alpha > 0.0) || !(P->mach > 0.0))
     return fail(ctx, HDG_EINVAL, w + ": need gamma > 1, alpha > 0, mach > 0");
+  if (P->sc_eps0 > 0.0 && !(std::isfinite(P->sc_eps0) && std::isfinite(P->sc_beta)))
+    return fail(ctx, HDG_EINVAL, w + ": shock capturing needs finite sc_eps0 and sc_beta");
   if (cudaSetDevice(ctx->device) != cudaSuccess) return fail(ctx, HDG_ECUDA, "cudaSetDevice failed");
   return HDG_OK;
 }
@@ -387,6 +389,8 @@ hdg_sys* sys_new(hdg_ctx* ctx, const hdg_mesh* M, const hdg_params* P) {
   S->ph.mu_inf = P->mach / P->reynolds;
   S->ph.suth_s = 110.4 / P->t_inf;
   S->ph.cfl = P->cfl;
+  S->ph.sc_eps0 = P->sc_eps0 > 0.0 ? P->sc_eps0 : 0.0;
+  S->ph.sc_beta = P->sc_beta;
   S->ph.model = P->model;
   S->ph.precision = P->precision;
   S->ph.persistent = 1;

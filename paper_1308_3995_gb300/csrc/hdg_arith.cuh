@@ -85,6 +85,7 @@ struct Ar<double> {
   static __device__ __forceinline__ T sub(T a, T b) { return a - b; }
   static __device__ __forceinline__ T mul(T a, T b) { return a * b; }
   static __device__ __forceinline__ T neg(T a) { return -a; }
+  static __device__ __forceinline__ T abs(T a) { return fabs(a); }
   // acc += a*b and acc -= a*b (one rounding each)
   static __device__ __forceinline__ void madd(T& acc, T a, T b) { acc = fma(a, b, acc); }
   static __device__ __forceinline__ void msub(T& acc, T a, T b) { acc = fma(-a, b, acc); }
@@ -113,6 +114,8 @@ struct Ar<ff> {
     return fast_two_sum(s.hi, s.lo);
   }
   static __device__ __forceinline__ T neg(T a) { return {-a.hi, -a.lo}; }
+  // |a| of a normalised value (the sign is the high word's)
+  static __device__ __forceinline__ T abs(T a) { return a.hi < 0.0f ? neg(a) : a; }
   static __device__ __forceinline__ T sub(T a, T b) { return add(a, neg(b)); }
   static __device__ __forceinline__ T mul(T a, T b) {
     const float p = a.hi * b.hi;

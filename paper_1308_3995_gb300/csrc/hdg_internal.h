@@ -41,6 +41,7 @@ void build_tables(Tables& T);
 // Flow parameters as the kernels use them.
 struct Phys {
   double gamma, alpha, prandtl, mu_inf, suth_s, cfl;
+  double sc_eps0, sc_beta;  // shock capturing (Sec. 3.2); off unless sc_eps0 > 0
   int model, precision;
   int persistent;  // 1: grid = SMs x resident CTAs (loop over elements); 0: one CTA per element
 };

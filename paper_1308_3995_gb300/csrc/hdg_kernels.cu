@@ -222,6 +222,57 @@ __global__ void __launch_bounds__(kCondThreads, 4) k_condense_euler(
       }
     }
     __syncthreads();
+    // shock-capturing viscosity (Sec. 3.2), held fixed in the Jacobian:
+    //   eps_K = eps_0 (h_K/p)^(2-beta) / |K| int_K sum_f |(div f_c(w))_f|.
+    // With Ahat_r = c (Ji[r][0] A_x + Ji[r][1] A_y), c = w_q det J, and the reference
+    // gradients g_r of w: c div f_c = sum_r Ahat_r g_r (row 0 of A_x, A_y is constant).
+    T eps = zero;
+    const bool shock = ph.sc_eps0 > 0.0;
+    if (shock) {
+      for (int q = tid; q < NQ; q += NT) {
+        T gr[2][4];
+#pragma unroll
+        for (int f = 0; f < 4; ++f) {
+          T a0 = zero, a1 = zero;
+#pragma unroll
+          for (int j = 0; j < NP; ++j) {
+            A::madd(a0, sU[f * NP + j], vgx[q * NP + j]);
+            A::madd(a1, sU[f * NP + j], vge[q * NP + j]);
+          }
+          gr[0][f] = A::norm(a0);
+          gr[1][f] = A::norm(a1);
+        }
+        const T c = A::mul(vw[q], g_det);
+        T d0 = zero;
+#pragma unroll
+        for (int r = 0; r < 2; ++r) {
+          A::madd(d0, A::mul(c, g_Ji[r][0]), gr[r][1]);
+          A::madd(d0, A::mul(c, g_Ji[r][1]), gr[r][2]);
+        }
+        T d = A::abs(A::norm(d0));
+#pragma unroll
+        for (int f = 1; f < 4; ++f) {
+          T v = zero;
+#pragma unroll
+          for (int r = 0; r < 2; ++r)
+#pragma unroll
+            for (int g = 0; g < 4; ++g) A::madd(v, sAh[(r * 16 + f * 4 + g) * NQ + q], gr[r][g]);
+          d = A::add(d, A::abs(A::norm(v)));
+        }
+        sEh[q] = d;  // sEh and sNl are free until the face quadrature
+      }
+      __syncthreads();
+      if (tid == 0) {
+        T sum = zero;
+        for (int q = 0; q < NQ; ++q) sum = A::add(sum, sEh[q]);
+        const double l0 = A::to_d(g_len[0]), l1 = A::to_d(g_len[1]), l2 = A::to_d(g_len[2]);
+        const double hk = fmax(l0, fmax(l1, l2)) / P;
+        const double fac = ph.sc_eps0 * pow(hk, 2.0 - ph.sc_beta) * 2.0 / A::to_d(g_det);  // 1/|K| = 2/det J
+        sNl[0] = A::mul(sum, A::from_d(fac));
+      }
+      __syncthreads();
+      eps = sNl[0];
+    }
     // interior residual, volume part: N_w = -(grad phi, f_c(w))_K
     for (int t = tid; t < N; t += NT) {
       const int f = t / NP, i = t - f * NP;
@@ -359,17 +410,44 @@ __global__ void __launch_bounds__(kCondThreads, 4) k_condense_euler(
       sEh[t] = A::neg(acc);  // H
     }
     __syncthreads();
-    // face mass alpha <phi_i, phi_j>_dK on every field's diagonal block, plus the pseudo-time mass
+    // face mass alpha <phi_i, phi_j>_dK on every field's diagonal block, plus the pseudo-time
+    // mass and the frozen shock-capturing stiffness eps (grad phi_i, grad phi_j)_K
+    T* sSt = scr;  // [NP][NP] eps * stiffness (the face scratch is dead here)
     for (int t = tid; t < NP * NP; t += NT) {
       const int i = t / NP, j = t - i * NP;
       T v = zero;
       for (int a = 0; a < 3; ++a) A::madd(v, g_len[a], tab[to.face_mass[P][g_pe[a]][a] + t]);
       v = A::mul(alpha, A::norm(v));
       if (i == j) v = A::add(v, g_mt);
+      if (shock) {  // grad phi_i . grad phi_j = sum_rs G_rs d_r phi_i d_s phi_j, G = Ji Ji^T
+        const T G00 = A::add(A::mul(g_Ji[0][0], g_Ji[0][0]), A::mul(g_Ji[0][1], g_Ji[0][1]));
+        const T G01 = A::add(A::mul(g_Ji[0][0], g_Ji[1][0]), A::mul(g_Ji[0][1], g_Ji[1][1]));
+        const T G11 = A::add(A::mul(g_Ji[1][0], g_Ji[1][0]), A::mul(g_Ji[1][1], g_Ji[1][1]));
+        T st = zero;
+        for (int q = 0; q < NQ; ++q) {
+          const T xi = vgx[q * NP + i], ei = vge[q * NP + i], xj = vgx[q * NP + j], ej = vge[q * NP + j];
+          T k = A::mul(G00, A::mul(xi, xj));
+          A::madd(k, G01, A::add(A::mul(xi, ej), A::mul(ei, xj)));
+          A::madd(k, G11, A::mul(ei, ej));
+          A::madd(st, vw[q], A::norm(k));
+        }
+        st = A::mul(A::mul(eps, g_det), A::norm(st));
+        sSt[t] = st;
+        v = A::add(v, st);
+      }
 #pragma unroll
       for (int f = 0; f < 4; ++f) {
         T* p = &sA[(f * NP + i) * LDA + f * NP + j];
         *p = A::add(*p, v);
+      }
+    }
+    if (shock) {  // N_w += eps (grad phi_i, grad w_f)_K
+      __syncthreads();
+      for (int t = tid; t < N; t += NT) {
+        const int f = t / NP, i = t - f * NP;
+        T acc = sNu[t];
+        for (int j = 0; j < NP; ++j) A::madd(acc, sSt[i * NP + j], sU[f * NP + j]);
+        sNu[t] = A::norm(acc);
       }
     }
     for (int t = tid; t < N; t += NT) sR[t * ldr + nt] = A::neg(sNu[t]);  // F

@@ -115,6 +115,8 @@ extern "C" hdg_status hdg_condense_noalloc(const hdg_mesh* mesh, const hdg_param
   ph.mu_inf = P->mach / P->reynolds;
   ph.suth_s = 110.4 / P->t_inf;
   ph.cfl = P->cfl;
+  ph.sc_eps0 = P->sc_eps0 > 0.0 ? P->sc_eps0 : 0.0;
+  ph.sc_beta = P->sc_beta;
   ph.model = P->model;
   ph.precision = P->precision;
   ph.persistent = 1;

@@ -301,6 +301,38 @@ __global__ void __launch_bounds__(kNsThreads) k_condense_ns(DevMesh m, DevSys s,
       }
     }
     __syncthreads();
+    // shock-capturing viscosity (Sec. 3.2) with q in place of grad w, held fixed in the Jacobian:
+    //   eps_K = eps_0 (h_K/p)^(2-beta) / |K| int_K sum_f |(A_x q_x + A_y q_y)_f|
+    T eps = zero;
+    const bool shock = ph.sc_eps0 > 0.0;
+    if (shock) {
+      for (int q = tid; q < NQ; q += NT) {
+        T w[4], fx[4], fy[4], Ax[16], Ay[16];
+#pragma unroll
+        for (int f = 0; f < 4; ++f) w[f] = sVal[(8 + f) * NQ + q];
+        euler_flux_jac(w, C, fx, fy, Ax, Ay);
+        T d = zero;
+#pragma unroll
+        for (int f = 0; f < 4; ++f) {
+          T v = zero;
+#pragma unroll
+          for (int g = 0; g < 4; ++g) {
+            A::madd(v, Ax[f * 4 + g], sVal[g * NQ + q]);
+            A::madd(v, Ay[f * 4 + g], sVal[(4 + g) * NQ + q]);
+          }
+          d = A::add(d, A::abs(A::norm(v)));
+        }
+        sNl[q] = A::mul(A::mul(vw[q], g_det), d);  // sNl is free until the residuals
+      }
+      __syncthreads();
+      T sum = zero;
+      for (int q = 0; q < NQ; ++q) sum = A::add(sum, sNl[q]);
+      const double l0 = A::to_d(g_len[0]), l1 = A::to_d(g_len[1]), l2 = A::to_d(g_len[2]);
+      const double hk = fmax(l0, fmax(l1, l2)) / P;
+      const double fac = ph.sc_eps0 * pow(hk, 2.0 - ph.sc_beta) * 2.0 / A::to_d(g_det);  // 1/|K| = 2/det J
+      eps = A::mul(sum, A::from_d(fac));
+      __syncthreads();
+    }
 
     // ---------------- residuals ----------------
     // N_q[(k,f),i] = det Q[(k,f),i] + sum_j D_k[i][j] W[f][j] - sum_a n_k |e_a| sum_l Me_a[l][i] Lam_a[f][l]
@@ -331,6 +363,12 @@ __global__ void __launch_bounds__(kNsThreads) k_condense_ns(DevMesh m, DevSys s,
       for (int a = 0; a < 3; ++a) {
         const T* phe = tab + to.edge_phi[P][g_pe[a]][a][g_fl[a]];
         for (int q = 0; q < g_pe[a] + 2; ++q) A::madd(acc, phe[q * NP + i], sFhat[(a * kNsPt + q) * 4 + f]);
+      }
+      if (shock) {  // + eps (grad phi_i, q_f)_K = eps sum_k D_k Q_(k,f)
+        T v = zero;
+        for (int k = 0; k < 2; ++k)
+          for (int j = 0; j < NP; ++j) A::madd(v, sDk[k * NP * NP + i * NP + j], sU[(k * 4 + f) * NP + j]);
+        A::madd(acc, eps, A::norm(v));
       }
       sNu[8 * NP + t] = A::norm(acc);
     }
@@ -462,6 +500,7 @@ __global__ void __launch_bounds__(kNsThreads) k_condense_ns(DevMesh m, DevSys s,
               A::madd(acc, A::mul(phe[q * NP + i], sAq[(a * kNsPt + q) * 24 + (f - 1) * 8 + kk]), phe[q * NP + j]);
           }
         }
+        if (shock && f == gq) A::madd(acc, eps, sDk[kd * NP * NP + i * NP + j]);  // frozen shock capturing
         sBc[t] = A::norm(acc);
       }
       __syncthreads();

@@ -44,7 +44,8 @@ class hdg_params(ctypes.Structure):
     _fields_ = [("model", ctypes.c_int32), ("precision", ctypes.c_int32), ("gamma", ctypes.c_double),
                 ("prandtl", ctypes.c_double), ("reynolds", ctypes.c_double), ("mach", ctypes.c_double),
                 ("alpha", ctypes.c_double), ("cfl", ctypes.c_double), ("t_inf", ctypes.c_double),
-                ("refine_tol", ctypes.c_double), ("refine_max", ctypes.c_int32), ("reserved", ctypes.c_int32)]
+                ("refine_tol", ctypes.c_double), ("refine_max", ctypes.c_int32), ("reserved", ctypes.c_int32),
+                ("sc_eps0", ctypes.c_double), ("sc_beta", ctypes.c_double)]
 
 
 @dataclass
@@ -60,10 +61,13 @@ class Params:
     t_inf: float = 288.15
     refine_tol: float = 1e-13
     refine_max: int = 4
+    sc_eps0: float = 0.0     # shock capturing (Sec. 3.2) off unless > 0 (paper's value 0.2)
+    sc_beta: float = 0.0
 
     def c(self) -> hdg_params:
         return hdg_params(self.model, self.precision, self.gamma, self.prandtl, self.reynolds, self.mach,
-                          self.alpha, self.cfl, self.t_inf, self.refine_tol, self.refine_max, 0)
+                          self.alpha, self.cfl, self.t_inf, self.refine_tol, self.refine_max, 0,
+                          self.sc_eps0, self.sc_beta)
 
 
 _vp = ctypes.c_void_p

@@ -8,15 +8,15 @@ import oracle as O
 from paper_1308_3995_gb300 import inputs as G
 
 
-def oracle_params(wl, cfl=0.0):
+def oracle_params(wl, cfl=0.0, sc=0.0):
     return O.Params(model=wl.model, mach=wl.mach, alpha=wl.alpha, reynolds=wl.reynolds, prandtl=wl.prandtl,
-                    cfl=cfl)
+                    cfl=cfl, sc_eps0=sc)
 
 
-def lib_params(wl, cfl=0.0, precision=0):
+def lib_params(wl, cfl=0.0, precision=0, sc=0.0):
     from paper_1308_3995_gb300 import hdg
     return hdg.Params(model=wl.model, precision=precision, mach=wl.mach, alpha=wl.alpha, reynolds=wl.reynolds,
-                      prandtl=wl.prandtl, cfl=cfl)
+                      prandtl=wl.prandtl, cfl=cfl, sc_eps0=sc)
 
 
 def rel_err(a, b, floor=1e-300):

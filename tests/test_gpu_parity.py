@@ -29,10 +29,10 @@ def build_case(wl):
     return case, om, U, Lam, dLam
 
 
-def run_gpu(ctx, case, wl, U, Lam, dLam, cfl=0.0, repeat=1, precision=0):
+def run_gpu(ctx, case, wl, U, Lam, dLam, cfl=0.0, repeat=1, precision=0, sc=0.0):
     from paper_1308_3995_gb300 import hdg
     mesh = hdg.Mesh(ctx, case.mesh.elem_xy, case.mesh.elem_vid, case.elem_p, case.nfield)
-    sysm = hdg.System(ctx, mesh, lib_params(wl, cfl, precision))
+    sysm = hdg.System(ctx, mesh, lib_params(wl, cfl, precision, sc))
     dev = torch.device("cuda:0")
     Ut = torch.from_numpy(U).to(dev)
     Lt = torch.from_numpy(Lam).to(dev)
@@ -56,16 +56,16 @@ def assert_layout_equal(mesh, om):
         assert np.array_equal(np.asarray(a).ravel(), np.asarray(b).ravel()), name
 
 
-def full_parity(ctx, wl, cfl=0.0, precision=0, tol=TOL):
+def full_parity(ctx, wl, cfl=0.0, precision=0, tol=TOL, sc=0.0):
     """Every element and every face of a small case, element by element."""
     case, om, U, Lam, dLam = build_case(wl)
-    mesh, sysm, (g,) = run_gpu(ctx, case, wl, U, Lam, dLam, cfl, precision=precision)
+    mesh, sysm, (g,) = run_gpu(ctx, case, wl, U, Lam, dLam, cfl, precision=precision, sc=sc)
     assert_layout_equal(mesh, om)
     assert np.all(g["status"] == 0)
-    chk = ParityChecker(om, oracle_params(wl, cfl), U, Lam, dLam, g)
+    chk = ParityChecker(om, oracle_params(wl, cfl, sc), U, Lam, dLam, g)
     errs = chk.run(range(om.n_elem), range(om.n_face))
     # plain normwise relative errors over the mesh, for the record
-    r = om.condense(oracle_params(wl, cfl), U, Lam)
+    r = om.condense(oracle_params(wl, cfl, sc), U, Lam)
     info = {"normwise E": rel_err(g["E"], r["E"]), "normwise dU": rel_err(g["dU"], om.recover(r["X"], dLam))}
     print(wl.name, ["fp64", "float2"][precision], {k: f"{v:.1e}" for k, v in {**errs, **info}.items()})
     for k, v in errs.items():
@@ -130,16 +130,16 @@ def test_ns_pseudo_time(ctx):
     full_parity(ctx, wl, cfl=10.0)
 
 
-def _sampled(ctx, wl, precision, n_faces, n_elems, seed, tol):
+def _sampled(ctx, wl, precision, n_faces, n_elems, seed, tol, sc=0.0):
     case, om, U, Lam, dLam = build_case(wl)
-    mesh, sysm, (g,) = run_gpu(ctx, case, wl, U, Lam, dLam, precision=precision)
+    mesh, sysm, (g,) = run_gpu(ctx, case, wl, U, Lam, dLam, precision=precision, sc=sc)
     assert_layout_equal(mesh, om)
     assert np.all(g["status"] == 0)
     rng = np.random.default_rng(seed)
     faces = rng.choice(om.n_face, n_faces, replace=False)
     elems = sorted(set(int(k) for f in faces for k in om.face_el[f]) |
                    set(int(k) for k in rng.choice(om.n_elem, n_elems)))
-    chk = ParityChecker(om, oracle_params(wl), U, Lam, dLam, g)
+    chk = ParityChecker(om, oracle_params(wl, 0.0, sc), U, Lam, dLam, g)
     errs = chk.run(elems, faces)
     # error per field of the stored local solves (rows grouped by field)
     nf = case.nfield
@@ -170,6 +170,39 @@ def test_config4_shock_full_size_sampled(ctx, precision):
     """262,144-triangle Euler p = 3 workload, Mach 1.5 with an oblique shock band:
     the float-float path against the FP64 oracle, error per field."""
     _sampled(ctx, G.WORKLOADS["euler_p3_262k_shock"], precision, 12, 12, 8, [TOL, TOL_MIXED][precision])
+
+
+# shock capturing (Sec. 3.2): eps_0 = 0.2, beta = 0 (the paper's values), eps_K frozen in the Jacobian
+SC_EPS0 = 0.2
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+def test_config4_shock_capturing_full_size_sampled(ctx, precision):
+    """The 262,144-triangle Mach 1.5 shock-band workload with shock capturing on."""
+    _sampled(ctx, G.WORKLOADS["euler_p3_262k_shock"], precision, 8, 8, 9, [TOL, TOL_MIXED][precision], sc=SC_EPS0)
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+@pytest.mark.parametrize("name,nx,ny,kw", [
+    ("euler_p3_262k_shock", 8, 12, {}),                   # Euler p = 3, shock band
+    ("euler_p3_262k_shock", 6, 7, {"p": 4}),               # Euler p = 4
+    ("ns_mixp_65k", 5, 6, {"model": 0}),                   # Euler, ragged p mix
+    ("ns_mixp_65k", 4, 5, {}),                             # Navier-Stokes, p mix (q in place of grad w)
+    ("ns_mixp_65k", 3, 4, {"p": 4}),                       # Navier-Stokes p = 4
+])
+def test_shock_capturing_parity(ctx, precision, name, nx, ny, kw):
+    wl = G.small_variant(G.WORKLOADS[name], nx, ny, **kw)
+    full_parity(ctx, wl, precision=precision, tol=[TOL, TOL_MIXED][precision], sc=SC_EPS0)
+    # the term is not negligible here: switching it off moves the local solves far beyond the bar
+    case, om, U, Lam, dLam = build_case(wl)
+    x_on, *_ = om.element_condense(oracle_params(wl, 0.0, SC_EPS0), 0, U, Lam)
+    x_off, *_ = om.element_condense(oracle_params(wl), 0, U, Lam)
+    assert rel_err(x_on, x_off) > 1e-6
+
+
+def test_shock_capturing_with_pseudo_time(ctx):
+    wl = G.small_variant(G.WORKLOADS["euler_p3_262k_shock"], 5, 6)
+    full_parity(ctx, wl, cfl=10.0, sc=SC_EPS0)
 
 
 def test_nonfinite_state_flags_its_element_only(ctx):

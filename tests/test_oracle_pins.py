@@ -623,3 +623,18 @@ def test_sc_jacobian_is_frozen_viscosity_times_stiffness(model):
             assert np.abs(dA - ref).max() < 1e-13 * np.abs(A1).max()
         dN = -(F1 - F0)      # a difference of O(|F|) residuals: rounding ~ u |F|
         assert np.abs(dA @ UK - dN).max() < 1e-12 * np.abs(dN).max() + 1e-13 * np.abs(F0).max()
+
+
+def test_threaded_condensation_is_bitwise_single_threaded():
+    """The host-thread driver of the oracle (used for the all-cores CPU baseline) only spreads the
+    per-element work: every output equals the single-thread run bit for bit."""
+    wl, c, m, P = _case("ns_mixp_65k", 4, 5, model=0)
+    U, L, _ = G.case_state(c, m.face_vid, m.face_p)
+    a = m.condense(P, U, L)
+    b = m.condense(P, U, L, threads=3)
+    for k in a:
+        assert np.array_equal(a[k], b[k]), k
+    c1 = m.condense(P, U, L, 3, 17, threads=4)
+    c0 = m.condense(P, U, L, 3, 17)
+    for k in a:
+        assert np.array_equal(c0[k], c1[k]), k
