@@ -316,7 +316,7 @@ def run_ours(args, wl, ws, rank, local):
     stream = torch.cuda.current_stream()
 
     # headline: plain binary64 path on the named workload (replicated on every rank)
-    main_m = Measured(ctx, wl, args.precision, dev, flush)
+    main_m = Measured(ctx, wl, args.precision, dev, flush, args.sc_eps0)
     if ws > 1:
         torch.distributed.barrier()
     main_m.run(args.steps, args.warmup, stream, ClockSampler(local))
@@ -352,7 +352,7 @@ def run_ours(args, wl, ws, rank, local):
             "kernel": "k_condense_euler<3, double> (FP64 pipe)", "algorithmic_flops_per_launch": fl,
             "algorithmic_bytes_per_launch": by, "launch_ms": 1e3 * cond_s, "achieved_hbm_gbs": by / cond_s / 1e9,
             "peak_note": "FP64 1.25 TFLOP/s nominal (recipe); 1.255 measured by an FMA-chain microbenchmark"}
-    extra = {"precision": "fp64" if args.precision == 0 else "float-float"}
+    extra = {"precision": "fp64" if args.precision == 0 else "float-float", "sc_eps0": args.sc_eps0}
     extra.update({k: summ[k] for k in ("p50_step_ms", "p99_step_ms", "condense_ms", "recover_ms",
                                        "elem_status_nonzero")})
     line = {"metric": METRIC, "value": value, "unit": "elements/s", "n_gpus": ws, "steps": args.steps,
@@ -428,6 +428,7 @@ def main(argv=None):
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--workload", default="euler_p3_16k")
     ap.add_argument("--precision", type=int, default=0)
+    ap.add_argument("--sc-eps0", type=float, default=0.0, help="shock capturing eps_0 on the headline workload")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cells", default=None, help="override the grid, e.g. 48x96 (profiling runs)")
     ap.add_argument("--quick", action="store_true", help="headline workload only (no per-p, NS, serving)")

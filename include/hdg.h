@@ -268,7 +268,9 @@ hdg_status hdg_condense_noalloc(const hdg_mesh* mesh, const hdg_params* params, 
  * [(p+2)^2][n_p] at the volume points (xi-major collapsed ordering), 4 edge
  * points s, 5 edge weights [p_e+2], 6 trace basis [p_e+2][p_e+1], 7 basis of
  * degree p on local face lf at the edge points, flip = 1 if the face runs
- * from the higher to the lower vertex id [p_e+2][n_p]. */
+ * from the higher to the lower vertex id [p_e+2][n_p], 8 reference stiffness
+ * parts [3][n_p][n_p] (sum_q w_q of dxi phi_i dxi phi_j, dxi phi_i deta phi_j +
+ * deta phi_i dxi phi_j, deta phi_i deta phi_j). */
 int hdg_debug_tables(int which, int p, int pe, int lf, int flip, double* out, int cap);
 
 #ifdef __cplusplus

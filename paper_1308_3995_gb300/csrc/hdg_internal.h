@@ -28,6 +28,7 @@ struct TabOff {
   int edge_phi[kMaxP + 1][kMaxP + 1][3][2];   // [p][pe][local face][flip]
   // derived reference matrices (unit edge length, unit det J):
   int vol_dref[kMaxP + 1];                    // [2][np][np]: sum_q w_q dphi_i/dxi_r phi_j
+  int vol_stiff[kMaxP + 1];                   // [3][np][np]: sum_q w_q of d0i d0j, d0i d1j + d1i d0j, d1i d1j
   int face_mass[kMaxP + 1][kMaxP + 1][3];     // [np][np]: sum_g w_g phi_i phi_j on local face lf
   int edge_cross[kMaxP + 1][kMaxP + 1][3][2]; // [pe+1][np]: sum_g w_g psi_k phi_j
 };

@@ -423,14 +423,10 @@ __global__ void __launch_bounds__(kCondThreads, 4) k_condense_euler(
         const T G00 = A::add(A::mul(g_Ji[0][0], g_Ji[0][0]), A::mul(g_Ji[0][1], g_Ji[0][1]));
         const T G01 = A::add(A::mul(g_Ji[0][0], g_Ji[1][0]), A::mul(g_Ji[0][1], g_Ji[1][1]));
         const T G11 = A::add(A::mul(g_Ji[1][0], g_Ji[1][0]), A::mul(g_Ji[1][1], g_Ji[1][1]));
-        T st = zero;
-        for (int q = 0; q < NQ; ++q) {
-          const T xi = vgx[q * NP + i], ei = vge[q * NP + i], xj = vgx[q * NP + j], ej = vge[q * NP + j];
-          T k = A::mul(G00, A::mul(xi, xj));
-          A::madd(k, G01, A::add(A::mul(xi, ej), A::mul(ei, xj)));
-          A::madd(k, G11, A::mul(ei, ej));
-          A::madd(st, vw[q], A::norm(k));
-        }
+        const T* sref = tab + to.vol_stiff[P];  // reference stiffness parts (rr, rs + sr, ss)
+        T st = A::mul(G00, sref[t]);
+        A::madd(st, G01, sref[NP * NP + t]);
+        A::madd(st, G11, sref[2 * NP * NP + t]);
         st = A::mul(A::mul(eps, g_det), A::norm(st));
         sSt[t] = st;
         v = A::add(v, st);

@@ -171,6 +171,23 @@ void build_tables(Tables& T) {
           for (int q = 0; q < nq; ++q) acc += d[T.off.vol_w[p] + q] * d[g + q * np + i] * d[T.off.vol_phi[p] + q * np + j];
           d[o + (r * np + i) * np + j] = acc;
         }
+    o = reserve(3 * np * np);
+    T.off.vol_stiff[p] = o;
+    for (int i = 0; i < np; ++i)
+      for (int j = 0; j < np; ++j) {
+        double s00 = 0.0, s01 = 0.0, s11 = 0.0;
+        for (int q = 0; q < nq; ++q) {
+          const double w = d[T.off.vol_w[p] + q];
+          const double xi = d[T.off.vol_gxi[p] + q * np + i], ei = d[T.off.vol_geta[p] + q * np + i];
+          const double xj = d[T.off.vol_gxi[p] + q * np + j], ej = d[T.off.vol_geta[p] + q * np + j];
+          s00 += w * xi * xj;
+          s01 += w * (xi * ej + ei * xj);
+          s11 += w * ei * ej;
+        }
+        d[o + i * np + j] = s00;
+        d[o + np * np + i * np + j] = s01;
+        d[o + 2 * np * np + i * np + j] = s11;
+      }
     for (int pe = p; pe <= kMaxP; ++pe) {
       const int ne = pe + 2, nk = pe + 1;
       for (int lf = 0; lf < 3; ++lf) {
@@ -216,6 +233,7 @@ extern "C" int hdg_debug_tables(int which, int p, int pe, int lf, int fl, double
     case 5: off = T.off.edge_w[pe]; len = ne; break;
     case 6: off = T.off.edge_psi[pe]; len = ne * (pe + 1); break;
     case 7: off = T.off.edge_phi[p][pe][lf][fl]; len = ne * np; break;
+    case 8: off = T.off.vol_stiff[p]; len = 3 * np * np; break;
     default: return -1;
   }
   if (off < 0 || len > cap) return -1;

@@ -43,6 +43,11 @@ def test_library_volume_tables_match_oracle(p):
     assert np.abs(hdg.hdg_debug_tables(1, p).reshape(phi.shape) - phi).max() < 1e-13
     assert np.abs(hdg.hdg_debug_tables(2, p).reshape(phi.shape) - dx).max() < 1e-12
     assert np.abs(hdg.hdg_debug_tables(3, p).reshape(phi.shape) - de).max() < 1e-12
+    # reference stiffness parts (shock capturing): exact integrals of products of the gradients
+    st = hdg.hdg_debug_tables(8, p).reshape(3, len(phi[0]), len(phi[0]))
+    ref = [(dx * w[:, None]).T @ dx, (dx * w[:, None]).T @ de + (de * w[:, None]).T @ dx, (de * w[:, None]).T @ de]
+    for k in range(3):
+        assert np.abs(st[k] - ref[k]).max() < 1e-12 * max(1.0, np.abs(ref[k]).max())
 
 
 @pytest.mark.parametrize("pe", [1, 2, 3, 4])
