@@ -103,7 +103,7 @@ __global__ void __launch_bounds__(kCondThreads, 4) k_condense_euler(
   // per trace index c < nt of the element: local face, field, mode
   __shared__ unsigned char g_cf[kMaxNt], g_cg[kMaxNt], g_cl[kMaxNt];
   __shared__ T s_pinv[64];
-  __shared__ int s_piv, s_bad;
+  __shared__ int s_bad;
 
   const int tid = threadIdx.x;
   const int tx = tid & 31, ty = tid >> 5;   // lane, warp: 2-D layouts without index division
@@ -451,7 +451,7 @@ __global__ void __launch_bounds__(kCondThreads, 4) k_condense_euler(
 
     // ---------------- a4/a5: LU with partial pivoting on [A | B | F] ----------------
     const int nr1 = nt + 1;
-    lu_solve<T, N, NT>(sA, LDA, sR, ldr, nr1, &s_piv, s_pinv, &s_bad, tid);
+    lu_solve<T, N, NT>(sA, LDA, sR, ldr, nr1, reinterpret_cast<int*>(scr), s_pinv, &s_bad, tid);  // scratch is dead here
     // X (column-major n x (nt+1)) and the interior residual; X renormalised in place
     int bad = 0;
     {

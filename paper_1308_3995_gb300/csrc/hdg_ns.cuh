@@ -105,7 +105,7 @@ __global__ void __launch_bounds__(kNsThreads) k_condense_ns(DevMesh m, DevSys s,
   __shared__ int g_e[3], g_pe[3], g_nk[3], g_toff[4], g_fl[3], g_side[3], g_old[3];
   __shared__ unsigned char g_cf[kMaxNt], g_cg[kMaxNt], g_cl[kMaxNt];
   __shared__ T s_pinv[64];
-  __shared__ int s_piv, s_bad;
+  __shared__ int s_bad;
 
   const int tid = threadIdx.x, tx = tid & 31, ty = tid >> 5;
   const T* vw = tab + to.vol_w[P];
@@ -566,7 +566,7 @@ __global__ void __launch_bounds__(kNsThreads) k_condense_ns(DevMesh m, DevSys s,
     }
 
     // ---------------- a4/a5: LU with partial pivoting on [A' | R'_w] ----------------
-    lu_solve<T, NW4, NT>(sA, LDA, sR, ldr, nr1, &s_piv, s_pinv, &s_bad, tid);
+    lu_solve<T, NW4, NT>(sA, LDA, sR, ldr, nr1, reinterpret_cast<int*>(sZ), s_pinv, &s_bad, tid);  // sZ is dead here
     int bad = 0;
     // X_w (renormalised in place) and the interior residual
     {
