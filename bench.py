@@ -33,9 +33,10 @@ sys.path.insert(0, ROOT)
 METRIC = "condensed elements/sec per p; p50/p99 solve latency vs plain FP64 at 1e-10 rel"
 FP64_PEAK_TFLOPS = 1.25     # nominal GB300 FP64 rate (recipe table); see the design doc
 L2_FLUSH_BYTES = 256 << 20  # > 129 MB L2
+HBM_PEAK_GBS = 6674.8       # measured copy bandwidth of the GB300s (MEASURED_PEAKS.json)
 # dram__bytes_read.sum + dram__bytes_write.sum per condensation launch from ncu
 # (profiles/), scaled to the full workload by elements; only for unchanged kernels
-TRAFFIC_PER_LAUNCH = {("euler_p3_16k", 0): 12720128 + 516691712}
+TRAFFIC_PER_LAUNCH = {("euler_p3_16k", 0): 12838912 + 517145600}
 
 
 def dense_condensation_flops(n: int, nt: int) -> float:
@@ -199,6 +200,8 @@ class Measured:
     """One workload on one GPU: device-timed steps (CUDA events on the launching
     stream, L2 flushed between timed steps)."""
 
+    autotune = True   # pick each degree bucket's launch shape with hdg_autotune before timing
+
     def __init__(self, ctx, wl, precision, dev, flush, sc_eps0=0.0):
         import torch
 
@@ -215,6 +218,7 @@ class Measured:
         self.Ut, self.Lt, self.dLt = (torch.from_numpy(a).to(dev) for a in (self.U, self.Lam, self.dLam))
         self.dUt = torch.empty(self.mesh.u_len, dtype=torch.float64, device=dev)
         self.flush = flush
+        self.shapes = self.sys.autotune(self.Ut, self.Lt) if Measured.autotune else {}
 
     def run(self, steps, warmup, stream, clocks=None):
         import torch
@@ -267,37 +271,95 @@ class Measured:
                 "p50_step_ms": lat[len(lat) // 2], "p99_step_ms": p99, "condense_ms": 1e3 * cond_s,
                 "recover_ms": statistics.mean(self.rec_ms), "elem_status_nonzero": self.status_bad,
                 "fp64_equiv_tflops": fl / cond_s / 1e12, "algorithmic_gflop_per_launch": fl / 1e9,
-                "algorithmic_mb_per_launch": by / 1e6}
+                "algorithmic_mb_per_launch": by / 1e6,
+                "launch_shapes": {str(p): ("one CTA per element" if v == 0 else f"persistent, {v} CTAs/SM")
+                                  for p, v in self.shapes.items()}}
 
     def close(self):
         self.sys.close()
         self.mesh.close()
 
 
-def serving_section(ctx, n_requests, seed, max_elems):
+def solve_section(ctx, wl, dev, flush, stream, cfl=10.0, rtol=1e-10, reps=3):
+    """One pseudo-transient Newton step with the GPU trace solve (Sec. 3.3/3.4): condensation at
+    the given CFL, GMRES + block Jacobi on K dLambda = E, reconstruction, update; plus the
+    bandwidth of the trace matrix-vector product (HBM-bound: the K values stream once)."""
+    import torch
+
+    from paper_1308_3995_gb300 import hdg
+    m = Measured(ctx, wl, hdg.HDG_FP64, dev, flush)
+    m.sys.set_cfl(cfl)
+    solver = hdg.Solver(m.sys, restart=30)
+    x = torch.zeros(m.mesh.lam_len, dtype=torch.float64, device=dev)
+    y = torch.empty_like(x)
+    res = []
+    for r in range(reps + 1):
+        U, L = m.Ut.clone(), m.Lt.clone()
+        flush.fill_(1.0)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        m.sys.condense(U, L, stream)
+        x.zero_()
+        it, rel = solver.solve(x, rtol=rtol, max_iter=2000, stream=stream)
+        m.sys.recover(x, m.dUt, stream)
+        m.sys.newton_update(U, L, m.dUt, x, stream)
+        torch.cuda.synchronize()
+        if r > 0:
+            res.append((time.perf_counter() - t0, it, rel))
+    # matrix-vector product bandwidth (K values + x gathers + y), CUDA events on the stream
+    nmv = 20
+    k_bytes = 8 * m.mesh.k_len
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    solver.matvec(x, y, stream)
+    ev0.record(stream)
+    for _ in range(nmv):
+        solver.matvec(x, y, stream)
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    mv_s = ev0.elapsed_time(ev1) * 1e-3 / nmv
+    out = {"workload": wl.name, "cfl": cfl, "rtol": rtol, "restart": 30,
+           "newton_step_ms": 1e3 * statistics.median(t for t, _, _ in res),
+           "gmres_iterations": res[-1][1], "rel_residual": res[-1][2],
+           "matvec": {"k_mb": k_bytes / 1e6, "ms": 1e3 * mv_s, "k_gbs": k_bytes / mv_s / 1e9,
+                      "frac_of_hbm": k_bytes / mv_s / 1e9 / HBM_PEAK_GBS}}
+    solver.close()
+    m.close()
+    return out
+
+
+def serving_section(ctx, n_requests, seed, max_elems, rates=(0.7,), arena_gb=24):
     """Poisson stream through the continuous-batching loop (float-float, 8 slots)
-    against the plain loop (binary64, one request at a time)."""
+    against the plain loop (binary64, one request at a time), at each load level
+    (fraction of the batched loop's saturated throughput)."""
     import torch
 
     from paper_1308_3995_gb300 import hdg
     from paper_1308_3995_gb300 import serving as SV
     wls = SV.request_workloads(n_requests, seed=seed, min_elems=1000, max_elems=max_elems)
     reqs = SV.prepare(ctx, [SV.Request(i, 0.0, w) for i, w in enumerate(wls)])
-    arena = 24 << 30
+    arena = int(arena_gb) << 30
     mixed = SV.Server(ctx, arena, slots=8, precision=hdg.HDG_FLOAT2)
     plain = SV.Server(ctx, arena, slots=1, precision=hdg.HDG_FP64)
     sat = mixed.run(reqs, "saturated")                       # everything at t = 0
     mean_el = sat.elements / sat.n
-    rate = 0.7 * sat.throughput / mean_el                    # requests / s
-    arr = SV.poisson_arrivals(len(reqs), rate, seed + 1)
-    for r, t in zip(reqs, arr):
-        r.arrival_s = float(t)
-    m = mixed.run(reqs, "mixed float-float, continuous batching (8 slots)").as_dict()
-    p = plain.run(reqs, "plain FP64, one request at a time").as_dict()
+    levels = {}
+    for frac in rates:
+        rate = frac * sat.throughput / mean_el               # requests / s
+        arr = SV.poisson_arrivals(len(reqs), rate, seed + 1)
+        for r, t in zip(reqs, arr):
+            r.arrival_s = float(t)
+        m = mixed.run(reqs, "mixed float-float, continuous batching (8 slots)").as_dict()
+        p = plain.run(reqs, "plain FP64, one request at a time").as_dict()
+        levels[str(frac)] = {"arrival_rate_per_s": rate, "mixed": m, "plain_fp64": p}
     del mixed, plain
     torch.cuda.empty_cache()
-    return {"requests": len(reqs), "sizes": f"1000..{max_elems} elements log-uniform, Euler/NS 50/50, p 1..4",
-            "arrival_rate_per_s": rate, "saturated_elements_per_s": sat.throughput, "mixed": m, "plain_fp64": p}
+    out = {"requests": len(reqs), "sizes": f"1000..{max_elems} elements log-uniform, Euler/NS 50/50, p 1..4",
+           "saturated_elements_per_s": sat.throughput, "elements_total": sat.elements}
+    if len(levels) == 1:
+        out.update(next(iter(levels.values())))
+    else:
+        out["load_levels"] = levels
+    return out
 
 
 def run_ours(args, wl, ws, rank, local):
@@ -314,6 +376,18 @@ def run_ours(args, wl, ws, rank, local):
     ctx = hdg.Context(local)
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
     stream = torch.cuda.current_stream()
+    if args.solve_only:
+        if rank == 0:
+            print(json.dumps({"metric": "Newton step with GPU trace solve",
+                              "solve": solve_section(ctx, wl, dev, flush, stream)}), flush=True)
+        return 0
+    if args.serving_only:
+        line = {"metric": "serving: p50/p99 latency and elements/s, continuous batching (float-float) vs plain FP64",
+                "serving": serving_section(ctx, args.serving_requests, 77, args.serving_max_elems,
+                                           tuple(float(v) for v in args.serving_rates.split(",")), args.serving_arena_gb)}
+        if rank == 0:
+            print(json.dumps(line), flush=True)
+        return 0
 
     # headline: plain binary64 path on the named workload (replicated on every rank)
     main_m = Measured(ctx, wl, args.precision, dev, flush, args.sc_eps0)
@@ -352,7 +426,8 @@ def run_ours(args, wl, ws, rank, local):
             "kernel": "k_condense_euler<3, double> (FP64 pipe)", "algorithmic_flops_per_launch": fl,
             "algorithmic_bytes_per_launch": by, "launch_ms": 1e3 * cond_s, "achieved_hbm_gbs": by / cond_s / 1e9,
             "peak_note": "FP64 1.25 TFLOP/s nominal (recipe); 1.255 measured by an FMA-chain microbenchmark"}
-    extra = {"precision": "fp64" if args.precision == 0 else "float-float", "sc_eps0": args.sc_eps0}
+    extra = {"precision": "fp64" if args.precision == 0 else "float-float", "sc_eps0": args.sc_eps0,
+             "launch_shapes": summ["launch_shapes"]}
     extra.update({k: summ[k] for k in ("p50_step_ms", "p99_step_ms", "condense_ms", "recover_ms",
                                        "elem_status_nonzero")})
     line = {"metric": METRIC, "value": value, "unit": "elements/s", "n_gpus": ws, "steps": args.steps,
@@ -396,6 +471,7 @@ def run_ours(args, wl, ws, rank, local):
                 shock[f"{nm}_sc{'_on' if sc else '_off'}"] = ms.summary()
                 ms.close()
         line["euler_p3_262k_shock"] = shock
+        line["newton_step_with_trace_solve"] = solve_section(ctx, wl, dev, flush, stream)
         if args.serving_requests > 0:
             line["serving"] = serving_section(ctx, args.serving_requests, 77, args.serving_max_elems)
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
@@ -434,6 +510,11 @@ def main(argv=None):
     ap.add_argument("--quick", action="store_true", help="headline workload only (no per-p, NS, serving)")
     ap.add_argument("--serving-requests", type=int, default=32)
     ap.add_argument("--serving-max-elems", type=int, default=32000)
+    ap.add_argument("--serving-rates", default="0.7", help="load levels, fractions of saturated throughput")
+    ap.add_argument("--serving-arena-gb", type=int, default=24)
+    ap.add_argument("--serving-only", action="store_true", help="run only the serving section")
+    ap.add_argument("--solve-only", action="store_true", help="run only the trace-solve section")
+    ap.add_argument("--no-autotune", action="store_true", help="default launch shapes (no hdg_autotune)")
     args = ap.parse_args(argv)
     from paper_1308_3995_gb300 import inputs as G
     wl = G.WORKLOADS[args.workload]
@@ -441,6 +522,7 @@ def main(argv=None):
         nx, ny = (int(v) for v in args.cells.lower().split("x"))
         wl = G.small_variant(wl, nx, ny)
     ws, rank, local = dist_env()
+    Measured.autotune = not args.no_autotune
     if args.impl == "reference":
         return run_reference(args, wl, rank)
     return run_ours(args, wl, ws, rank, local)

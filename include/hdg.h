@@ -230,8 +230,73 @@ hdg_status hdg_graph_launch(hdg_sys* sys, void* stream);
 hdg_status hdg_sys_get(const hdg_sys* sys, double** X, double** K_vals, double** E, double** res_u,
                        double** res_lam, int32_t** elem_status);
 
+/* Autotuner of the condensation launch shape (no counterpart in the paper).
+ * For every degree bucket of the mesh, times the bucket's kernel alone on the
+ * given state (device U, Lam; one warm-up and three timed launches each, CUDA
+ * events on `stream`) for every candidate shape -- one CTA per element, or a
+ * persistent grid of k CTAs per SM for k = 1 .. the kernel's occupancy -- and
+ * keeps the fastest for the following hdg_condense calls of this system.
+ * The shape changes no arithmetic: results stay bitwise the same.  Synchronises
+ * `stream`; leaves the system's outputs undefined until the next hdg_condense.
+ * grid_out (may be NULL) receives [kMaxP+1 = 5] entries: per degree p the
+ * chosen shape (0 one CTA per element, k > 0 persistent with k CTAs per SM,
+ * -1 no elements of that degree).  Not allowed while a captured graph exists. */
+hdg_status hdg_autotune(hdg_sys* sys, const double* U, const double* Lam, int32_t* grid_out, void* stream);
+
 /* Number of kernel launches the last hdg_condense + hdg_recover enqueued. */
 int32_t hdg_sys_launches(const hdg_sys* sys);
+
+/* ---- Global trace solve and pseudo-transient Newton update (Sec. 3.3, 3.4) ----
+ * The paper solves K dLambda = E (Eq. hybridsystem) with preconditioned GMRES
+ * (an ILU(n) preconditioner through PETSc).  This library solves it on the GPU
+ * with restarted GMRES, left-preconditioned by block Jacobi: M = the diagonal
+ * face blocks of K, inverted once per solve (Gauss-Jordan with partial
+ * pivoting, binary64).  Arnoldi uses classical Gram-Schmidt with one
+ * re-orthogonalisation pass; the Hessenberg least-squares problem (Givens
+ * rotations) is solved on the host.  Everything is binary64. */
+typedef struct hdg_solver hdg_solver;
+
+/* Allocate the solver's device state for `sys` (Krylov basis of restart+1
+ * vectors of lam_len doubles, block inverses, reduction buffers).
+ * restart in 1..64.  The solver reads K and E of `sys` as left by the last
+ * hdg_condense; it must be destroyed before sys. */
+hdg_status hdg_solver_create(hdg_sys* sys, int32_t restart, hdg_solver** out);
+hdg_status hdg_solver_destroy(hdg_solver* solver);
+
+/* Solve K dLam = E for the DEVICE vector dLam [lam_len] (its input value is
+ * the initial guess; pass zeros for none), on `stream`.  Stops when the
+ * preconditioned residual ||M^-1 (E - K dLam)||_2 <= rtol ||M^-1 E||_2 or after
+ * max_iter iterations.  The call synchronises `stream` (it reads one
+ * residual estimate per iteration) and returns the iteration count and the
+ * final preconditioned relative residual in *iters / *rel_res (either may be
+ * NULL).  Returns HDG_OK when converged, HDG_ETIMEOUT when max_iter was
+ * reached first, HDG_ESINGULAR when a diagonal block of K is singular. */
+hdg_status hdg_trace_solve(hdg_solver* solver, double* dLam, double rtol, int32_t max_iter, int32_t* iters,
+                           double* rel_res, void* stream);
+
+/* y = K x for DEVICE vectors x, y [lam_len] (K of the last hdg_condense). */
+hdg_status hdg_trace_matvec(hdg_solver* solver, const double* x, double* y, void* stream);
+
+/* Newton update on DEVICE vectors: U += dU [u_len], Lam += dLam [lam_len]. */
+hdg_status hdg_newton_update(hdg_sys* sys, double* U, double* Lam, const double* dU, const double* dLam,
+                             void* stream);
+
+/* ||N_h||_2 of the state given to the last hdg_condense: the 2-norm of the
+ * interior residual [N_q; N_w] and the two-sided trace residual together,
+ * computed on the device; synchronises `stream`. */
+hdg_status hdg_residual_norm(hdg_sys* sys, double* norm, void* stream);
+
+/* Change the pseudo-time CFL number of a system (Sec. 3.3; <= 0: pure Newton)
+ * for the following hdg_condense calls.  Not allowed while a captured graph
+ * exists (HDG_EINVAL): the graph bakes the parameters in. */
+hdg_status hdg_sys_set_cfl(hdg_sys* sys, double cfl);
+
+/* The CFL law of Eq. (cfl), host only: for n <= n0,
+ * CFL^n = c0 (3 (n/n0)^2 - 2 (n/n0)^3); afterwards
+ * CFL^n = CFL^{n-1} (1 + c1 max(0, log(res_prev / res_cur))) with res_prev =
+ * ||N^{n-1}||, res_cur = ||N^n||.  The paper's values: c0 = 1e6, c1 = 1e3,
+ * n0 = 4.  Returns a negative value for n < 0, n0 < 1 or non-positive norms. */
+double hdg_cfl_law(int32_t n, double c0, double c1, int32_t n0, double cfl_prev, double res_prev, double res_cur);
 
 /* Allocation-free condensation.  The paper has no counterpart: this is an
  * interface for callers that cannot allocate device memory when they call --

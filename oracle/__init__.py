@@ -85,6 +85,9 @@ def lib():
         L.orc_monolithic.argtypes = [ctypes.c_void_p, P, _c_double_p, _c_double_p, _c_double_p, _c_double_p,
                                      _c_double_p]
         L.orc_dense_solve.argtypes = [ctypes.c_int, _c_double_p, _c_double_p]
+        L.orc_cfl_law.argtypes = [ctypes.c_int, ctypes.c_double, ctypes.c_double, ctypes.c_int, ctypes.c_double,
+                                  ctypes.c_double, ctypes.c_double]
+        L.orc_cfl_law.restype = ctypes.c_double
         L.orc_sc_epsilon.argtypes = [ctypes.c_void_p, P, ctypes.c_int, _c_double_p]
         L.orc_sc_epsilon.restype = ctypes.c_double
         _lib = L
@@ -181,6 +184,12 @@ class Params:
     @property
     def nfield(self) -> int:
         return 12 if self.model == 1 else 4
+
+
+def cfl_law(n, c0=1e6, c1=1e3, n0=4, cfl_prev=0.0, res_prev=1.0, res_cur=1.0) -> float:
+    """CFL^n of Eq. (cfl) (Sec. 3.3)."""
+    return float(lib().orc_cfl_law(int(n), float(c0), float(c1), int(n0), float(cfl_prev), float(res_prev),
+                                   float(res_cur)))
 
 
 # --------------------------------------------------------------------------- mesh-level

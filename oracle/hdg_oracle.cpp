@@ -1030,6 +1030,16 @@ int orc_monolithic(void* h, const orc_params* P, const double* U, const double* 
   return 0;
 }
 
+// The CFL law of Eq. (cfl) (Sec. 3.3): a smooth ramp up to c0 over n0 steps,
+// then growth by 1 + c1 max(0, log(||N^{n-1}|| / ||N^n||)) per step.
+double orc_cfl_law(int n, double c0, double c1, int n0, double cfl_prev, double res_prev, double res_cur) {
+  if (n <= n0) {
+    const double t = (double)n / (double)n0;
+    return c0 * (3.0 * t * t - 2.0 * t * t * t);
+  }
+  return cfl_prev * (1.0 + c1 * std::max(0.0, std::log(res_prev / res_cur)));
+}
+
 // Shock-capturing viscosity eps_K of element K (0 when P->sc_eps0 <= 0).
 double orc_sc_epsilon(void* h, const orc_params* P, int K, const double* U) {
   OMesh* M = (OMesh*)h;

@@ -11,49 +11,9 @@
 #include <vector>
 
 #include "hdg_internal.h"
+#include "hdg_objects.h"
 
 using namespace hdg;
-
-struct hdg_ctx {
-  int device = 0;
-  std::string err;
-  Tables tab;
-  double* d_tab = nullptr;   // tables in binary64
-  void* d_tab_ff = nullptr;  // the same tables split into float-float pairs (hi, lo)
-};
-
-struct hdg_mesh {
-  hdg_ctx* ctx = nullptr;
-  int n_elem = 0, n_face = 0, nfield = 4, max_nt = 0;
-  int64_t u_len = 0, lam_len = 0, x_len = 0, k_len = 0, dh_len = 0;
-  std::vector<int> face_lo, face_hi, face_el0, face_el1, face_p, elem_face, k_col;
-  std::vector<int64_t> u_off, lam_off, x_off, k_blkoff;
-  std::vector<void*> allocs;
-  int* d_bucket[kMaxP + 1] = {};
-  int bucket_n[kMaxP + 1] = {};
-  int bucket_ntmax[kMaxP + 1] = {};
-  DevMesh dm{};
-};
-
-struct hdg_sys {
-  hdg_ctx* ctx = nullptr;
-  const hdg_mesh* mesh = nullptr;
-  hdg_params prm{};
-  Phys ph{};
-  DevSys ds{};
-  double *d_U = nullptr, *d_Lam = nullptr, *d_dLam = nullptr, *d_dU = nullptr;
-  std::vector<void*> allocs;
-  int launches = 0;
-  bool need_zero = true;
-  // degree buckets launched concurrently: one stream and one event per degree, a fork event
-  cudaStream_t bstream[kMaxP + 1] = {};
-  cudaEvent_t bevent[kMaxP + 1] = {};
-  cudaEvent_t fork = nullptr;
-  bool have_streams = false;
-  // captured step (hdg_graph_create)
-  cudaGraph_t graph = nullptr;
-  cudaGraphExec_t gexec = nullptr;
-};
 
 namespace {
 
@@ -394,6 +354,7 @@ hdg_sys* sys_new(hdg_ctx* ctx, const hdg_mesh* M, const hdg_params* P) {
   S->ph.model = P->model;
   S->ph.precision = P->precision;
   S->ph.persistent = 1;
+  phys_default_grid(S->ph);
   return S;
 }
 
@@ -580,6 +541,66 @@ hdg_status hdg_step_host(hdg_sys* S, const double* U, const double* Lam, const d
   if (rc != HDG_OK) return rc;
   HDG_CK(S->ctx, cudaStreamSynchronize((cudaStream_t)stream));
   return HDG_OK;
+}
+
+hdg_status hdg_autotune(hdg_sys* S, const double* U, const double* Lam, int32_t* grid_out, void* stream) {
+  if (!S) return HDG_EINVAL;
+  hdg_ctx* ctx = S->ctx;
+  if (!U || !Lam) return fail(ctx, HDG_EINVAL, "hdg_autotune: null input");
+  if (S->gexec) return fail(ctx, HDG_EINVAL, "hdg_autotune: a captured graph holds the launch shapes");
+  const hdg_mesh* M = S->mesh;
+  cudaStream_t st = (cudaStream_t)stream;
+  int sms = 0;
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, ctx->device);
+  cudaEvent_t e0, e1;
+  HDG_CK(ctx, cudaEventCreate(&e0));
+  HDG_CK(ctx, cudaEventCreate(&e1));
+  std::string err;
+  hdg_status rs = HDG_OK;
+  for (int p = 1; p <= kMaxP && rs == HDG_OK; ++p) {
+    if (grid_out) grid_out[p] = S->ph.grid[p];
+    if (M->bucket_n[p] == 0) continue;
+    const int occ = condense_occupancy(S->ph, p, M->bucket_ntmax[p]);
+    if (occ < 1) { rs = fail(ctx, HDG_ECUDA, "hdg_autotune: kernel does not fit on an SM"); break; }
+    int bn[kMaxP + 1] = {};
+    bn[p] = M->bucket_n[p];
+    float best_ms = 0.0f;
+    int best = -1;
+    // candidates: one CTA per element, or a persistent grid of k CTAs per SM, k = 1..occupancy
+    for (int cand = 0; cand <= occ && rs == HDG_OK; ++cand) {
+      Phys ph = S->ph;
+      ph.grid[p] = cand;
+      float t_min = 0.0f;
+      for (int rep = 0; rep < 4; ++rep) {
+        if (cudaMemsetAsync(S->ds.face_cnt, 0, 4 * (size_t)M->n_face, st) != cudaSuccess ||
+            cudaEventRecord(e0, st) != cudaSuccess) {
+          rs = fail(ctx, HDG_ECUDA, "hdg_autotune: enqueue failed");
+          break;
+        }
+        if (launch_condense(M->dm, S->ds, ph, ctx->d_tab, ctx->d_tab_ff, ctx->tab.off, U, Lam, M->d_bucket, bn,
+                            M->bucket_ntmax, stream, &err) < 0) {
+          rs = fail(ctx, HDG_ECUDA, "hdg_autotune: " + err);
+          break;
+        }
+        float ms = 0.0f;
+        if (cudaEventRecord(e1, st) != cudaSuccess || cudaEventSynchronize(e1) != cudaSuccess ||
+            cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess) {
+          rs = fail(ctx, HDG_ECUDA, "hdg_autotune: timing failed");
+          break;
+        }
+        if (rep > 0 && (rep == 1 || ms < t_min)) t_min = ms;  // first launch is a warm-up
+      }
+      if (rs == HDG_OK && (best < 0 || t_min < best_ms)) { best = cand; best_ms = t_min; }
+    }
+    if (rs == HDG_OK) {
+      S->ph.grid[p] = best;
+      if (grid_out) grid_out[p] = best;
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  S->need_zero = true;  // the single-bucket launches leave shared faces half counted
+  return rs;
 }
 
 hdg_status hdg_graph_create(hdg_sys* S, const double* U, const double* Lam, const double* dLam, double* dU) {

@@ -45,7 +45,24 @@ struct Phys {
   double sc_eps0, sc_beta;  // shock capturing (Sec. 3.2); off unless sc_eps0 > 0
   int model, precision;
   int persistent;  // 1: grid = SMs x resident CTAs (loop over elements); 0: one CTA per element
+  // launch shape per degree (autotuned): -1 default (by `persistent`), 0 one CTA per element,
+  // k > 0 persistent grid of k CTAs per SM (capped by the occupancy)
+  int grid[kMaxP + 1];
 };
+
+inline void phys_default_grid(Phys& ph) {
+  for (int p = 0; p <= kMaxP; ++p) ph.grid[p] = -1;
+}
+
+// number of CTAs of a condensation launch of n elements of degree p
+inline long condense_grid(const Phys& ph, int p, int sms, int per_sm, int n) {
+  const int g = ph.grid[p];
+  long grid;
+  if (g < 0) grid = ph.persistent ? (long)sms * per_sm : (long)n;
+  else if (g == 0) grid = n;
+  else grid = (long)sms * (g < per_sm ? g : per_sm);
+  return grid > n ? n : grid;
+}
 
 // Device-resident mesh plan handed to kernels by value.
 struct DevMesh {
@@ -96,6 +113,10 @@ PlanRef plan_ref(const hdg_mesh* mesh);
 
 // kernel launchers (hdg_kernels.cu); return the number of launches enqueued
 // bucket_streams (optional, indexed by degree p): stream of each degree bucket's launch
+// resident CTAs per SM of the condensation kernel for degree p (model and precision from ph)
+int condense_occupancy(const Phys& ph, int p, int ntmax);
+int ns_occupancy(const Phys& ph, int p, int ntmax);
+
 int launch_condense(const DevMesh& m, const DevSys& s, const Phys& ph, const double* tab, const void* tab_ff,
                     const TabOff& off, const double* U, const double* Lam, const int* const* bucket,
                     const int* bucket_n, const int* bucket_ntmax, void* stream, std::string* err,

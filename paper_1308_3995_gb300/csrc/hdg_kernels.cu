@@ -584,8 +584,7 @@ static bool launch_euler_bucket(const DevMesh& m, const DevSys& s, const Phys& p
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
   cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_condense_euler<P, T>, kCondThreads, bytes);
   if (per_sm < 1) { *err = "condensation kernel does not fit on an SM"; return false; }
-  long grid = ph.persistent ? (long)sms * per_sm : (long)n;
-  if (grid > n) grid = n;
+  const long grid = condense_grid(ph, P, sms, per_sm, n);
   k_condense_euler<P, T><<<(int)grid, kCondThreads, bytes, st>>>(m, s, ph, tab, to, U, Lam, elems, n, ldr, nkmax);
   ce = cudaGetLastError();
   if (ce != cudaSuccess) { *err = cudaGetErrorString(ce); return false; }
@@ -604,6 +603,30 @@ static bool launch_euler_p(int p, const DevMesh& m, const DevSys& s, const Phys&
   }
   *err = "degree out of range";
   return false;
+}
+
+template <int P, class T>
+static int euler_occupancy(int ntmax) {
+  const EulerLayout<P> lay(ldr_for(ntmax), nkmax_for(P, ntmax));
+  const size_t bytes = sizeof(T) * (size_t)lay.total;
+  if (cudaFuncSetAttribute(k_condense_euler<P, T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes) !=
+      cudaSuccess)
+    return 0;
+  int per_sm = 0;
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_condense_euler<P, T>, kCondThreads, bytes);
+  return per_sm;
+}
+
+int condense_occupancy(const Phys& ph, int p, int ntmax) {
+  if (ph.model == HDG_NS_MIXED) return ns_occupancy(ph, p, ntmax);
+  const bool d = ph.precision == HDG_FP64;
+  switch (p) {
+    case 1: return d ? euler_occupancy<1, double>(ntmax) : euler_occupancy<1, ff>(ntmax);
+    case 2: return d ? euler_occupancy<2, double>(ntmax) : euler_occupancy<2, ff>(ntmax);
+    case 3: return d ? euler_occupancy<3, double>(ntmax) : euler_occupancy<3, ff>(ntmax);
+    case 4: return d ? euler_occupancy<4, double>(ntmax) : euler_occupancy<4, ff>(ntmax);
+  }
+  return 0;
 }
 
 int launch_condense(const DevMesh& m, const DevSys& s, const Phys& ph, const double* tab, const void* tab_ff,

@@ -120,6 +120,7 @@ extern "C" hdg_status hdg_condense_noalloc(const hdg_mesh* mesh, const hdg_param
   ph.model = P->model;
   ph.precision = P->precision;
   ph.persistent = 1;
+  phys_default_grid(ph);
   std::string err;
   const int n = launch_condense(*pr.dm, ds, ph, pr.tab, pr.tab_ff, *pr.off, U, Lam, pr.bucket, pr.bucket_n, pr.bucket_ntmax,
                                 stream, &err);

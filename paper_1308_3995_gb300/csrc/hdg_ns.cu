@@ -7,6 +7,12 @@ bool launch_ns_ff(int p, const DevMesh& m, const DevSys& s, const Phys& ph, cons
                   const double* U, const double* Lam, const int* elems, int n, int ntmax, cudaStream_t st,
                   std::string* err);
 
+int ns_occupancy_ff(int p, int ntmax);
+
+int ns_occupancy(const Phys& ph, int p, int ntmax) {
+  return ph.precision == HDG_FP64 ? ns_occ_p<double>(p, ntmax) : ns_occupancy_ff(p, ntmax);
+}
+
 int launch_condense_ns(const DevMesh& m, const DevSys& s, const Phys& ph, const double* tab, const void* tab_ff,
                        const TabOff& to, const double* U, const double* Lam, const int* const* bucket,
                        const int* bucket_n, const int* bucket_ntmax, void* stream, std::string* err,

@@ -683,12 +683,33 @@ inline bool launch_ns_bucket(const DevMesh& m, const DevSys& s, const Phys& ph, 
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
   cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_condense_ns<P, T>, kNsThreads, bytes);
   if (per_sm < 1) { *err = "NS condensation kernel does not fit on an SM"; return false; }
-  long grid = ph.persistent ? (long)sms * per_sm : (long)n;
-  if (grid > n) grid = n;
+  const long grid = condense_grid(ph, P, sms, per_sm, n);
   k_condense_ns<P, T><<<(int)grid, kNsThreads, bytes, st>>>(m, s, ph, tab, to, U, Lam, elems, n, ntmax);
   ce = cudaGetLastError();
   if (ce != cudaSuccess) { *err = cudaGetErrorString(ce); return false; }
   return true;
+}
+
+template <int P, class T>
+inline int ns_occ(int ntmax) {
+  const NsLayout<P> lay(ntmax);
+  const size_t bytes = sizeof(T) * (size_t)lay.total;
+  if (cudaFuncSetAttribute(k_condense_ns<P, T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes) != cudaSuccess)
+    return 0;
+  int per_sm = 0;
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_condense_ns<P, T>, kNsThreads, bytes);
+  return per_sm;
+}
+
+template <class T>
+inline int ns_occ_p(int p, int ntmax) {
+  switch (p) {
+    case 1: return ns_occ<1, T>(ntmax);
+    case 2: return ns_occ<2, T>(ntmax);
+    case 3: return ns_occ<3, T>(ntmax);
+    case 4: return ns_occ<4, T>(ntmax);
+  }
+  return 0;
 }
 
 template <class T>

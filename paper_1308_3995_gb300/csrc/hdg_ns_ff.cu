@@ -9,4 +9,6 @@ bool launch_ns_ff(int p, const DevMesh& m, const DevSys& s, const Phys& ph, cons
   return launch_ns_p<ff>(p, m, s, ph, (const ff*)tab, to, U, Lam, elems, n, ntmax, st, err);
 }
 
+int ns_occupancy_ff(int p, int ntmax) { return ns_occ_p<ff>(p, ntmax); }
+
 }  // namespace hdg

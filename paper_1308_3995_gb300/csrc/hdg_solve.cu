@@ -1,0 +1,539 @@
+// Global trace solve K dLambda = E (paper Sec. 3.4, Eq. hybridsystem) and the
+// pseudo-transient Newton update (Sec. 3.3) on the GPU.
+//
+// The paper uses ILU(n)-preconditioned GMRES from PETSc on the CPU.  Here:
+// restarted GMRES, left-preconditioned by block Jacobi (the inverses of K's
+// diagonal face blocks), binary64 throughout.  Kernels:
+//   k_bj_invert   one warp per face: Gauss-Jordan with partial pivoting of the
+//                 face's diagonal block (m = 4 (p_e + 1) <= 20 rows);
+//   k_face_op     one warp per face: t = (K x)_e (each block staged through
+//                 shared memory with coalesced loads, one lane per row, the
+//                 five blocks of the face row in column order), then, by
+//                 mode, y_e = t, Dinv_e t, Dinv_e (b_e - t) or Dinv_e b_e;
+//   k_multidot    partial dot products of one vector with up to 8 others per
+//                 block row of the grid, reduced in a fixed order by k_reduce
+//                 (bitwise reproducible);
+//   k_multiaxpy   w -= V c (c on the device), one thread per entry.
+// The Arnoldi process uses classical Gram-Schmidt with one
+// re-orthogonalisation pass; the small Hessenberg least-squares problem
+// (Givens rotations) is solved on the host, one residual estimate read back
+// per iteration.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "hdg_internal.h"
+#include "hdg_objects.h"
+
+using namespace hdg;
+
+namespace {
+
+constexpr int kMaxRestart = 64;
+constexpr int kFaceWarps = 4;          // faces per CTA in the per-face kernels
+constexpr int kMaxM = 4 * (kMaxP + 1);  // largest face block (20)
+constexpr int kDotThreads = 256;
+constexpr int kDotChunk = 8;           // vectors per k_multidot block row
+
+struct FaceDev {
+  int n_face;
+  const int* face_p;
+  const int64_t* lam_off;
+  const int* k_col;         // [5 n_face]
+  const int64_t* k_blkoff;  // [5 n_face + 1]
+  const int64_t* dinv_off;  // [n_face]
+  const double* K;
+  double* dinv;
+  int* bad;                 // set to 1 if a diagonal block is singular
+};
+
+// ---------------------------------------------------------------- block Jacobi
+__global__ void __launch_bounds__(32 * kFaceWarps) k_bj_invert(FaceDev f) {
+  __shared__ double s_aug[kFaceWarps][kMaxM][2 * kMaxM + 1];
+  const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int e = blockIdx.x * kFaceWarps + w;
+  if (e >= f.n_face) return;
+  const int m = 4 * (f.face_p[e] + 1), m2 = 2 * m;
+  int b = 0;
+  while (b < 4 && f.k_col[5 * e + b] != e) ++b;
+  const double* D = f.K + f.k_blkoff[5 * e + b];
+  double(*a)[2 * kMaxM + 1] = s_aug[w];
+  for (int t = lane; t < m * m2; t += 32) {
+    const int r = t / m2, c = t - r * m2;
+    a[r][c] = (c < m) ? D[r * m + c] : (c - m == r ? 1.0 : 0.0);
+  }
+  __syncwarp();
+  for (int k = 0; k < m; ++k) {
+    // pivot: largest |a_rk|, r >= k, first on ties (lanes over rows; m <= 32)
+    double best = (lane >= k && lane < m) ? fabs(a[lane][k]) : -1.0;
+    int bi = lane;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      const double ob = __shfl_down_sync(0xffffffffu, best, o);
+      const int oi = __shfl_down_sync(0xffffffffu, bi, o);
+      if (ob > best || (ob == best && oi < bi)) { best = ob; bi = oi; }
+    }
+    best = __shfl_sync(0xffffffffu, best, 0);
+    bi = __shfl_sync(0xffffffffu, bi, 0);
+    if (!(best > 0.0)) {
+      if (lane == 0) *f.bad = 1;
+      return;  // the whole warp leaves together (best and bi are warp-uniform)
+    }
+    for (int c = lane; c < m2; c += 32) {
+      const double t = a[k][c];
+      a[k][c] = a[bi][c];
+      a[bi][c] = t;
+    }
+    __syncwarp();
+    const double pinv = 1.0 / a[k][k];
+    __syncwarp();
+    for (int c = lane; c < m2; c += 32) a[k][c] *= pinv;
+    __syncwarp();
+    double fr[kMaxM];
+#pragma unroll
+    for (int r = 0; r < kMaxM; ++r) fr[r] = (r < m) ? a[r][k] : 0.0;
+    __syncwarp();
+    for (int c = lane; c < m2; c += 32) {
+      const double akc = a[k][c];
+#pragma unroll
+      for (int r = 0; r < kMaxM; ++r)
+        if (r < m && r != k) a[r][c] = fma(-fr[r], akc, a[r][c]);
+    }
+    __syncwarp();
+  }
+  double* out = f.dinv + f.dinv_off[e];
+  for (int t = lane; t < m * m; t += 32) {
+    const int r = t / m, c = t - r * m;
+    out[t] = a[r][m + c];
+  }
+}
+
+// mode: 0 y = Dinv K x, 1 y = Dinv (b - K x), 2 y = K x, 3 y = Dinv b.
+// Each block of the face row is staged through shared memory with coalesced
+// loads (the warp reads the m x mb row-major block as one contiguous run; rows
+// padded to mb + 1 against bank conflicts).  The products then use every lane
+// the face size allows: lane l < m * nseg takes row l % m and every nseg-th
+// column from l / m (nseg = 32 / m rounded down to a power of two), and the
+// nseg partial sums of a row meet by shuffles.  On this part the binary64 pipe,
+// not HBM, bounds a binary64 product of 0.25 flop per byte, so idle lanes
+// would cost time directly.
+__global__ void __launch_bounds__(32 * kFaceWarps) k_face_op(FaceDev f, const double* __restrict__ x,
+                                                               const double* __restrict__ bvec, double* __restrict__ y,
+                                                               int mode) {
+  __shared__ double s_blk[kFaceWarps][kMaxM * (kMaxM + 1)];
+  __shared__ double s_t[kFaceWarps][kMaxM];
+  const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int e = blockIdx.x * kFaceWarps + w;
+  if (e >= f.n_face) return;
+  const int m = 4 * (f.face_p[e] + 1);
+  const int nseg = (m <= 8) ? 4 : ((m <= 16) ? 2 : 1);
+  const int r = lane % m, sg = lane / m;
+  const bool act = sg < nseg;
+  const int64_t lo = f.lam_off[e];
+  double* sb = s_blk[w];
+  double t = 0.0;
+  if (mode != 3) {
+    for (int b = 0; b < 5; ++b) {
+      const int col = f.k_col[5 * e + b];
+      const int mb = 4 * (f.face_p[col] + 1), ld = mb + 1, n = m * mb;
+      const double* blk = f.K + f.k_blkoff[5 * e + b];
+      // (row, column) of entry lane + 32 k, stepped without division
+      const int q = 32 / mb, qr = 32 - q * mb;
+      int rr = lane / mb, cc = lane - rr * mb;
+      for (int idx = lane; idx < n; idx += 32) {
+        sb[rr * ld + cc] = __ldcs(blk + idx);  // streamed: each value is used once per product
+        rr += q;
+        cc += qr;
+        if (cc >= mb) { cc -= mb; ++rr; }
+      }
+      __syncwarp();
+      if (act) {
+        const double* xc = x + f.lam_off[col];
+        const double* row = sb + r * ld;
+        for (int c = sg; c < mb; c += nseg) t = fma(row[c], __ldg(xc + c), t);
+      }
+      __syncwarp();
+    }
+  }
+  // the nseg partial sums of row r sit in lanes r, r + m, ...
+  for (int o = m * (nseg >> 1); o >= m; o >>= 1) t += __shfl_down_sync(0xffffffffu, t, o);
+  if (lane < m) {
+    if (mode == 1) t = bvec[lo + lane] - t;
+    if (mode == 3) t = bvec[lo + lane];
+    s_t[w][lane] = t;
+  }
+  __syncwarp();
+  if (mode == 2) {
+    if (lane < m) y[lo + lane] = t;
+    return;
+  }
+  double v = 0.0;
+  if (act) {
+    const double* di = f.dinv + f.dinv_off[e] + (int64_t)r * m;
+    for (int c = sg; c < m; c += nseg) v = fma(di[c], s_t[w][c], v);
+  }
+  for (int o = m * (nseg >> 1); o >= m; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+  if (lane < m) y[lo + lane] = v;
+}
+
+// ---------------------------------------------------------------- reductions
+// partial[j][blockIdx.x] = sum over this block's slice of V_j . w, j in the
+// chunk blockIdx.y (vectors V_j at V + j * ldv)
+__global__ void __launch_bounds__(kDotThreads) k_multidot(const double* __restrict__ V, int64_t ldv, int nvec,
+                                                          const double* __restrict__ w, int64_t n,
+                                                          double* __restrict__ partial) {
+  __shared__ double s_red[kDotChunk][kDotThreads];
+  const int j0 = blockIdx.y * kDotChunk;
+  const int nj = min(kDotChunk, nvec - j0);
+  double acc[kDotChunk];
+#pragma unroll
+  for (int j = 0; j < kDotChunk; ++j) acc[j] = 0.0;
+  for (int64_t i = blockIdx.x * (int64_t)kDotThreads + threadIdx.x; i < n; i += (int64_t)gridDim.x * kDotThreads) {
+    const double wi = __ldg(w + i);
+#pragma unroll
+    for (int j = 0; j < kDotChunk; ++j)
+      if (j < nj) acc[j] = fma(__ldg(V + (int64_t)(j0 + j) * ldv + i), wi, acc[j]);
+  }
+#pragma unroll
+  for (int j = 0; j < kDotChunk; ++j) s_red[j][threadIdx.x] = acc[j];
+  __syncthreads();
+  for (int s = kDotThreads / 2; s > 0; s >>= 1) {
+    if (threadIdx.x < s)
+#pragma unroll
+      for (int j = 0; j < kDotChunk; ++j) s_red[j][threadIdx.x] += s_red[j][threadIdx.x + s];
+    __syncthreads();
+  }
+  if (threadIdx.x < nj) partial[(int64_t)(j0 + threadIdx.x) * gridDim.x + blockIdx.x] = s_red[threadIdx.x][0];
+}
+
+// out[j] = sum_b partial[j][b] (fixed tree order), one block per j
+__global__ void __launch_bounds__(kDotThreads) k_reduce(const double* __restrict__ partial, int nb,
+                                                        double* __restrict__ out) {
+  __shared__ double s[kDotThreads];
+  double a = 0.0;
+  for (int b = threadIdx.x; b < nb; b += kDotThreads) a += partial[(int64_t)blockIdx.x * nb + b];
+  s[threadIdx.x] = a;
+  __syncthreads();
+  for (int st = kDotThreads / 2; st > 0; st >>= 1) {
+    if (threadIdx.x < st) s[threadIdx.x] += s[threadIdx.x + st];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) out[blockIdx.x] = s[0];
+}
+
+// w[i] += sgn * sum_j c[j] V_j[i]
+__global__ void k_multiaxpy(const double* __restrict__ V, int64_t ldv, int nvec, const double* __restrict__ c,
+                            double sgn, double* __restrict__ w, int64_t n) {
+  __shared__ double s_c[kMaxRestart + 1];
+  for (int j = threadIdx.x; j < nvec; j += blockDim.x) s_c[j] = sgn * c[j];
+  __syncthreads();
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    double a = w[i];
+    for (int j = 0; j < nvec; ++j) a = fma(s_c[j], V[(int64_t)j * ldv + i], a);
+    w[i] = a;
+  }
+}
+
+__global__ void k_scale(double* __restrict__ v, double s, int64_t n) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    v[i] *= s;
+}
+
+__global__ void k_axpy2(double* __restrict__ U, const double* __restrict__ dU, int64_t nu, double* __restrict__ L,
+                        const double* __restrict__ dL, int64_t nl) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < nu + nl; i += (int64_t)gridDim.x * blockDim.x) {
+    if (i < nu) U[i] += dU[i];
+    else L[i - nu] += dL[i - nu];
+  }
+}
+
+hdg_status fail(hdg_ctx* ctx, hdg_status st, const std::string& msg) {
+  if (ctx) ctx->err = msg;
+  return st;
+}
+
+int grid_for(int64_t n, int threads, int cap) {
+  const int64_t g = (n + threads - 1) / threads;
+  return (int)std::max<int64_t>(1, std::min<int64_t>(g, cap));
+}
+
+}  // namespace
+
+struct hdg_solver {
+  hdg_sys* sys = nullptr;
+  int restart = 0;
+  int64_t n = 0;
+  int sms = 0;
+  int dot_blocks = 0;
+  FaceDev f{};
+  double* V = nullptr;        // [restart + 1][n]
+  double* partial = nullptr;  // [restart + 1][dot_blocks]
+  double* h = nullptr;        // [2 (restart + 1) + 2] device results of k_reduce
+  double* coef = nullptr;     // [restart + 1] coefficients from the host
+  double* zero = nullptr;     // [n] zeros
+  double* hpin = nullptr;     // pinned host mirror of h / coef
+  std::vector<void*> allocs;
+};
+
+namespace {
+
+hdg_status ck(hdg_ctx* ctx, cudaError_t e, const char* what) {
+  if (e != cudaSuccess) return fail(ctx, HDG_ECUDA, std::string(what) + ": " + cudaGetErrorString(e));
+  return HDG_OK;
+}
+
+// out[0..nvec) = V_j . w for j < nvec (device), enqueued on st
+void multidot(hdg_solver* S, const double* V, int nvec, const double* w, int64_t n, double* out, cudaStream_t st) {
+  dim3 g(S->dot_blocks, (nvec + kDotChunk - 1) / kDotChunk);
+  k_multidot<<<g, kDotThreads, 0, st>>>(V, S->n, nvec, w, n, S->partial);
+  k_reduce<<<nvec, kDotThreads, 0, st>>>(S->partial, S->dot_blocks, out);
+}
+
+}  // namespace
+
+extern "C" {
+
+hdg_status hdg_solver_create(hdg_sys* sys, int32_t restart, hdg_solver** out) {
+  if (!sys || !out) return HDG_EINVAL;
+  *out = nullptr;
+  hdg_ctx* ctx = sys->ctx;
+  if (restart < 1 || restart > kMaxRestart) return fail(ctx, HDG_EINVAL, "hdg_solver_create: restart must be in 1..64");
+  const hdg_mesh* M = sys->mesh;
+  if (cudaSetDevice(ctx->device) != cudaSuccess) return fail(ctx, HDG_ECUDA, "cudaSetDevice failed");
+  hdg_solver* S = new hdg_solver();
+  S->sys = sys;
+  S->restart = restart;
+  S->n = M->lam_len;
+  cudaDeviceGetAttribute(&S->sms, cudaDevAttrMultiProcessorCount, ctx->device);
+  S->dot_blocks = std::max(1, std::min<int>(2 * S->sms, (int)((S->n + kDotThreads - 1) / kDotThreads)));
+  std::vector<int64_t> dinv_off(M->n_face);
+  int64_t tot = 0;
+  for (int e = 0; e < M->n_face; ++e) {
+    const int m = 4 * (M->face_p[e] + 1);
+    dinv_off[e] = tot;
+    tot += (int64_t)m * m;
+  }
+  auto alloc = [&](size_t bytes, void** p) -> bool {
+    if (cudaMalloc(p, std::max<size_t>(bytes, 16)) != cudaSuccess) return false;
+    S->allocs.push_back(*p);
+    return true;
+  };
+  void *kc, *kb, *dof, *dinv, *bad, *V, *part, *h, *coef, *zero;
+  const size_t nr = (size_t)restart + 1;
+  bool ok = alloc(sizeof(int) * M->k_col.size(), &kc) && alloc(sizeof(int64_t) * M->k_blkoff.size(), &kb) &&
+            alloc(sizeof(int64_t) * dinv_off.size(), &dof) && alloc(sizeof(double) * tot, &dinv) &&
+            alloc(sizeof(int), &bad) && alloc(sizeof(double) * nr * S->n, &V) &&
+            alloc(sizeof(double) * nr * S->dot_blocks, &part) && alloc(sizeof(double) * (2 * nr + 2), &h) &&
+            alloc(sizeof(double) * nr, &coef) && alloc(sizeof(double) * S->n, &zero);
+  if (!ok || cudaMallocHost((void**)&S->hpin, sizeof(double) * (2 * nr + 2)) != cudaSuccess) {
+    for (void* p : S->allocs) cudaFree(p);
+    delete S;
+    return fail(ctx, HDG_ENOMEM, "hdg_solver_create: device allocation failed");
+  }
+  hdg_status st = HDG_OK;
+  if (st == HDG_OK) st = ck(ctx, cudaMemcpy(kc, M->k_col.data(), sizeof(int) * M->k_col.size(), cudaMemcpyHostToDevice), "cudaMemcpy");
+  if (st == HDG_OK) st = ck(ctx, cudaMemcpy(kb, M->k_blkoff.data(), sizeof(int64_t) * M->k_blkoff.size(), cudaMemcpyHostToDevice), "cudaMemcpy");
+  if (st == HDG_OK) st = ck(ctx, cudaMemcpy(dof, dinv_off.data(), sizeof(int64_t) * dinv_off.size(), cudaMemcpyHostToDevice), "cudaMemcpy");
+  if (st == HDG_OK) st = ck(ctx, cudaMemset(zero, 0, sizeof(double) * S->n), "cudaMemset");
+  if (st != HDG_OK) {
+    for (void* p : S->allocs) cudaFree(p);
+    cudaFreeHost(S->hpin);
+    delete S;
+    return st;
+  }
+  S->f.n_face = M->n_face;
+  S->f.face_p = M->dm.face_p;
+  S->f.lam_off = M->dm.lam_off;
+  S->f.k_col = (const int*)kc;
+  S->f.k_blkoff = (const int64_t*)kb;
+  S->f.dinv_off = (const int64_t*)dof;
+  S->f.K = sys->ds.K;
+  S->f.dinv = (double*)dinv;
+  S->f.bad = (int*)bad;
+  S->V = (double*)V;
+  S->partial = (double*)part;
+  S->h = (double*)h;
+  S->coef = (double*)coef;
+  S->zero = (double*)zero;
+  *out = S;
+  return HDG_OK;
+}
+
+hdg_status hdg_solver_destroy(hdg_solver* S) {
+  if (!S) return HDG_EINVAL;
+  cudaSetDevice(S->sys->ctx->device);
+  for (void* p : S->allocs) cudaFree(p);
+  if (S->hpin) cudaFreeHost(S->hpin);
+  delete S;
+  return HDG_OK;
+}
+
+hdg_status hdg_trace_matvec(hdg_solver* S, const double* x, double* y, void* stream) {
+  if (!S || !x || !y) return HDG_EINVAL;
+  cudaStream_t st = (cudaStream_t)stream;
+  const int fb = (S->f.n_face + kFaceWarps - 1) / kFaceWarps;
+  k_face_op<<<fb, 32 * kFaceWarps, 0, st>>>(S->f, x, nullptr, y, 2);
+  return ck(S->sys->ctx, cudaGetLastError(), "k_face_op");
+}
+
+hdg_status hdg_trace_solve(hdg_solver* S, double* x, double rtol, int32_t max_iter, int32_t* iters_out,
+                           double* rel_out, void* stream) {
+  if (!S || !x || !(rtol > 0.0) || max_iter < 1) return HDG_EINVAL;
+  hdg_ctx* ctx = S->sys->ctx;
+  cudaStream_t st = (cudaStream_t)stream;
+  const int64_t n = S->n;
+  const int R = S->restart;
+  const int fb = (S->f.n_face + kFaceWarps - 1) / kFaceWarps;
+  const int vb = grid_for(n, 256, 8 * S->sms);
+  hdg_status rs;
+  if (iters_out) *iters_out = 0;
+  if (rel_out) *rel_out = 0.0;
+  // block-Jacobi factors of the current K
+  if ((rs = ck(ctx, cudaMemsetAsync(S->f.bad, 0, sizeof(int), st), "cudaMemsetAsync")) != HDG_OK) return rs;
+  k_bj_invert<<<fb, 32 * kFaceWarps, 0, st>>>(S->f);
+  // ||M^-1 E||
+  double* E = S->sys->ds.E;
+  k_face_op<<<fb, 32 * kFaceWarps, 0, st>>>(S->f, S->zero, E, S->V, 3);
+  multidot(S, S->V, 1, S->V, n, S->h, st);
+  int bad = 0;
+  if ((rs = ck(ctx, cudaMemcpyAsync(S->hpin, S->h, sizeof(double), cudaMemcpyDeviceToHost, st), "cudaMemcpyAsync")) != HDG_OK) return rs;
+  if ((rs = ck(ctx, cudaMemcpyAsync(&S->hpin[1], S->f.bad, sizeof(int), cudaMemcpyDeviceToHost, st), "cudaMemcpyAsync")) != HDG_OK) return rs;
+  if ((rs = ck(ctx, cudaStreamSynchronize(st), "cudaStreamSynchronize")) != HDG_OK) return rs;
+  std::memcpy(&bad, &S->hpin[1], sizeof(int));
+  if (bad) return fail(ctx, HDG_ESINGULAR, "hdg_trace_solve: a diagonal block of K is singular");
+  const double bnorm = std::sqrt(S->hpin[0]);
+  if (!(bnorm > 0.0)) {  // E = 0: the solution is 0
+    if ((rs = ck(ctx, cudaMemsetAsync(x, 0, sizeof(double) * n, st), "cudaMemsetAsync")) != HDG_OK) return rs;
+    return ck(ctx, cudaStreamSynchronize(st), "cudaStreamSynchronize");
+  }
+  std::vector<double> H((size_t)(R + 1) * R), cs(R), sn(R), g(R + 1), y(R);
+  int it = 0;
+  double rel = 1.0;
+  while (true) {
+    // r0 = M^-1 (E - K x), beta = ||r0||
+    k_face_op<<<fb, 32 * kFaceWarps, 0, st>>>(S->f, x, E, S->V, 1);
+    multidot(S, S->V, 1, S->V, n, S->h, st);
+    if ((rs = ck(ctx, cudaMemcpyAsync(S->hpin, S->h, sizeof(double), cudaMemcpyDeviceToHost, st), "cudaMemcpyAsync")) != HDG_OK) return rs;
+    if ((rs = ck(ctx, cudaStreamSynchronize(st), "cudaStreamSynchronize")) != HDG_OK) return rs;
+    const double beta = std::sqrt(S->hpin[0]);
+    rel = beta / bnorm;
+    if (!(rel > rtol) || it >= max_iter) break;
+    k_scale<<<vb, 256, 0, st>>>(S->V, 1.0 / beta, n);
+    std::fill(g.begin(), g.end(), 0.0);
+    g[0] = beta;
+    int jn = 0;  // columns of H built in this cycle
+    for (int j = 0; j < R && it < max_iter; ++j) {
+      double* vj = S->V + (int64_t)j * n;
+      double* w = S->V + (int64_t)(j + 1) * n;
+      k_face_op<<<fb, 32 * kFaceWarps, 0, st>>>(S->f, vj, nullptr, w, 0);
+      // classical Gram-Schmidt, twice
+      multidot(S, S->V, j + 1, w, n, S->h, st);
+      k_multiaxpy<<<vb, 256, 0, st>>>(S->V, n, j + 1, S->h, -1.0, w, n);
+      multidot(S, S->V, j + 1, w, n, S->h + (R + 1), st);
+      k_multiaxpy<<<vb, 256, 0, st>>>(S->V, n, j + 1, S->h + (R + 1), -1.0, w, n);
+      multidot(S, w, 1, w, n, S->h + 2 * (R + 1), st);
+      if ((rs = ck(ctx, cudaMemcpyAsync(S->hpin, S->h, sizeof(double) * (2 * (R + 1) + 1), cudaMemcpyDeviceToHost, st),
+                   "cudaMemcpyAsync")) != HDG_OK)
+        return rs;
+      if ((rs = ck(ctx, cudaStreamSynchronize(st), "cudaStreamSynchronize")) != HDG_OK) return rs;
+      ++it;
+      double* col = &H[(size_t)j * (R + 1)];  // column j of H, rows 0..j+1
+      for (int i = 0; i <= j; ++i) col[i] = S->hpin[i] + S->hpin[(R + 1) + i];
+      const double hn = std::sqrt(S->hpin[2 * (R + 1)]);
+      col[j + 1] = hn;
+      for (int i = 0; i < j; ++i) {  // earlier rotations
+        const double a = col[i], b = col[i + 1];
+        col[i] = cs[i] * a + sn[i] * b;
+        col[i + 1] = -sn[i] * a + cs[i] * b;
+      }
+      const double den = std::hypot(col[j], col[j + 1]);
+      cs[j] = den > 0.0 ? col[j] / den : 1.0;
+      sn[j] = den > 0.0 ? col[j + 1] / den : 0.0;
+      col[j] = den;
+      col[j + 1] = 0.0;
+      g[j + 1] = -sn[j] * g[j];
+      g[j] = cs[j] * g[j];
+      jn = j + 1;
+      rel = std::fabs(g[j + 1]) / bnorm;
+      if (!(rel > rtol) || !(hn > 0.0)) break;
+      k_scale<<<vb, 256, 0, st>>>(w, 1.0 / hn, n);
+    }
+    // x += V y, H y = g (upper triangular)
+    for (int i = jn - 1; i >= 0; --i) {
+      double s = g[i];
+      for (int k = i + 1; k < jn; ++k) s -= H[(size_t)k * (R + 1) + i] * y[k];
+      y[i] = s / H[(size_t)i * (R + 1) + i];
+    }
+    std::memcpy(S->hpin, y.data(), sizeof(double) * jn);
+    if ((rs = ck(ctx, cudaMemcpyAsync(S->coef, S->hpin, sizeof(double) * jn, cudaMemcpyHostToDevice, st),
+                 "cudaMemcpyAsync")) != HDG_OK)
+      return rs;
+    k_multiaxpy<<<vb, 256, 0, st>>>(S->V, n, jn, S->coef, 1.0, x, n);
+    // the pinned buffer is reused next cycle: wait for the copy
+    if ((rs = ck(ctx, cudaStreamSynchronize(st), "cudaStreamSynchronize")) != HDG_OK) return rs;
+  }
+  if ((rs = ck(ctx, cudaGetLastError(), "trace solve kernels")) != HDG_OK) return rs;
+  if (iters_out) *iters_out = it;
+  if (rel_out) *rel_out = rel;
+  return (rel > rtol) ? fail(ctx, HDG_ETIMEOUT, "hdg_trace_solve: max_iter reached before rtol") : HDG_OK;
+}
+
+hdg_status hdg_newton_update(hdg_sys* sys, double* U, double* Lam, const double* dU, const double* dLam,
+                             void* stream) {
+  if (!sys || !U || !Lam || !dU || !dLam) return HDG_EINVAL;
+  const hdg_mesh* M = sys->mesh;
+  int sms = 0;
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, sys->ctx->device);
+  k_axpy2<<<grid_for(M->u_len + M->lam_len, 256, 8 * sms), 256, 0, (cudaStream_t)stream>>>(U, dU, M->u_len, Lam,
+                                                                                               dLam, M->lam_len);
+  return ck(sys->ctx, cudaGetLastError(), "k_axpy2");
+}
+
+hdg_status hdg_residual_norm(hdg_sys* sys, double* norm, void* stream) {
+  if (!sys || !norm) return HDG_EINVAL;
+  hdg_ctx* ctx = sys->ctx;
+  const hdg_mesh* M = sys->mesh;
+  cudaStream_t st = (cudaStream_t)stream;
+  int sms = 0;
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, ctx->device);
+  const int64_t nmax = std::max(M->u_len, M->lam_len);
+  const int nb = std::max(1, std::min<int>(2 * sms, (int)((nmax + kDotThreads - 1) / kDotThreads)));
+  double *part = nullptr, *out = nullptr, hout[2];
+  hdg_status rs;
+  if ((rs = ck(ctx, cudaMallocAsync((void**)&part, sizeof(double) * (2 * nb + 2), st), "cudaMallocAsync")) != HDG_OK) return rs;
+  out = part + 2 * nb;
+  k_multidot<<<dim3(nb, 1), kDotThreads, 0, st>>>(sys->ds.res_u, M->u_len, 1, sys->ds.res_u, M->u_len, part);
+  k_reduce<<<1, kDotThreads, 0, st>>>(part, nb, out);
+  k_multidot<<<dim3(nb, 1), kDotThreads, 0, st>>>(sys->ds.res_lam, M->lam_len, 1, sys->ds.res_lam, M->lam_len, part + nb);
+  k_reduce<<<1, kDotThreads, 0, st>>>(part + nb, nb, out + 1);
+  rs = ck(ctx, cudaMemcpyAsync(hout, out, sizeof(hout), cudaMemcpyDeviceToHost, st), "cudaMemcpyAsync");
+  cudaFreeAsync(part, st);
+  if (rs != HDG_OK) return rs;
+  if ((rs = ck(ctx, cudaStreamSynchronize(st), "cudaStreamSynchronize")) != HDG_OK) return rs;
+  *norm = std::sqrt(hout[0] + hout[1]);
+  return HDG_OK;
+}
+
+hdg_status hdg_sys_set_cfl(hdg_sys* sys, double cfl) {
+  if (!sys || !std::isfinite(cfl)) return HDG_EINVAL;
+  if (sys->gexec) return fail(sys->ctx, HDG_EINVAL, "hdg_sys_set_cfl: a captured graph holds the parameters");
+  sys->prm.cfl = cfl;
+  sys->ph.cfl = cfl;
+  return HDG_OK;
+}
+
+double hdg_cfl_law(int32_t n, double c0, double c1, int32_t n0, double cfl_prev, double res_prev, double res_cur) {
+  if (n < 0 || n0 < 1) return -1.0;
+  if (n <= n0) {
+    const double t = (double)n / (double)n0;
+    return c0 * (3.0 * t * t - 2.0 * t * t * t);
+  }
+  if (!(res_prev > 0.0) || !(res_cur > 0.0)) return -1.0;
+  return cfl_prev * (1.0 + c1 * std::max(0.0, std::log(res_prev / res_cur)));
+}
+
+}  // extern "C"

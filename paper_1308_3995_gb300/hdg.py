@@ -31,7 +31,9 @@ EXPORTS = ["hdg_create", "hdg_destroy", "hdg_last_error", "hdg_mesh_create", "hd
            "hdg_mesh_layout", "hdg_footprint_bytes", "hdg_sys_create", "hdg_sys_destroy", "hdg_condense",
            "hdg_recover", "hdg_step_host", "hdg_sys_get", "hdg_sys_launches", "hdg_debug_tables",
            "hdg_condense_noalloc", "hdg_sys_workspace_bytes", "hdg_sys_create_in",
-           "hdg_step_host_async", "hdg_graph_create", "hdg_graph_launch"]
+           "hdg_step_host_async", "hdg_graph_create", "hdg_graph_launch", "hdg_solver_create",
+           "hdg_solver_destroy", "hdg_trace_solve", "hdg_trace_matvec", "hdg_newton_update", "hdg_residual_norm",
+           "hdg_sys_set_cfl", "hdg_cfl_law", "hdg_autotune"]
 
 
 class HdgError(RuntimeError):
@@ -112,6 +114,18 @@ def lib(build: bool = True):
         L.hdg_sys_workspace_bytes.restype = ctypes.c_int64
         L.hdg_sys_create_in.argtypes = [_vp, _vp, ctypes.POINTER(hdg_params), _vp, ctypes.c_int64,
                                         ctypes.POINTER(_vp)]
+        L.hdg_solver_create.argtypes = [_vp, ctypes.c_int32, ctypes.POINTER(_vp)]
+        L.hdg_solver_destroy.argtypes = [_vp]
+        L.hdg_trace_solve.argtypes = [_vp, _vp, ctypes.c_double, ctypes.c_int32, ctypes.POINTER(ctypes.c_int32),
+                                      ctypes.POINTER(ctypes.c_double), _vp]
+        L.hdg_trace_matvec.argtypes = [_vp, _vp, _vp, _vp]
+        L.hdg_newton_update.argtypes = [_vp, _vp, _vp, _vp, _vp, _vp]
+        L.hdg_residual_norm.argtypes = [_vp, ctypes.POINTER(ctypes.c_double), _vp]
+        L.hdg_sys_set_cfl.argtypes = [_vp, ctypes.c_double]
+        L.hdg_autotune.argtypes = [_vp, _vp, _vp, _i32p, _vp]
+        L.hdg_cfl_law.argtypes = [ctypes.c_int32, ctypes.c_double, ctypes.c_double, ctypes.c_int32, ctypes.c_double,
+                                  ctypes.c_double, ctypes.c_double]
+        L.hdg_cfl_law.restype = ctypes.c_double
         _lib = L
     return _lib
 
@@ -134,6 +148,45 @@ def _stream(stream) -> int:
     if stream is None:
         return torch.cuda.current_stream().cuda_stream
     return stream.cuda_stream if hasattr(stream, "cuda_stream") else int(stream)
+
+
+def cfl_law(n: int, c0: float = 1e6, c1: float = 1e3, n0: int = 4, cfl_prev: float = 0.0, res_prev: float = 1.0,
+            res_cur: float = 1.0) -> float:
+    """hdg_cfl_law: CFL^n of Eq. (cfl) (host only)."""
+    return float(lib().hdg_cfl_law(int(n), float(c0), float(c1), int(n0), float(cfl_prev), float(res_prev),
+                                   float(res_cur)))
+
+
+class Solver:
+    """hdg_solver_create / hdg_trace_solve / hdg_trace_matvec: GMRES on the trace system of a System."""
+
+    def __init__(self, system: "System", restart: int = 30):
+        h = _vp()
+        _check(lib().hdg_solver_create(system.h, int(restart), ctypes.byref(h)), system.ctx.h)
+        self.h, self.sys = h, system
+
+    def solve(self, dLam, rtol=1e-12, max_iter=500, stream=None, check=True):
+        """Solve K dLam = E in place (dLam holds the initial guess); returns (iterations, rel. residual)."""
+        it, rel = ctypes.c_int32(), ctypes.c_double()
+        st = lib().hdg_trace_solve(self.h, _ptr(dLam), float(rtol), int(max_iter), ctypes.byref(it),
+                                   ctypes.byref(rel), _stream(stream))
+        if check:
+            _check(st, self.sys.ctx.h)
+        return int(it.value), float(rel.value)
+
+    def matvec(self, x, y, stream=None):
+        _check(lib().hdg_trace_matvec(self.h, _ptr(x), _ptr(y), _stream(stream)), self.sys.ctx.h)
+
+    def close(self):
+        if getattr(self, "h", None):
+            lib().hdg_solver_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 def hdg_debug_tables(which: int, p: int, pe: int = 0, lf: int = 0, flip: int = 0) -> np.ndarray:
@@ -288,6 +341,28 @@ class System:
     @property
     def launches(self) -> int:
         return int(lib().hdg_sys_launches(self.h))
+
+    def newton_update(self, U, Lam, dU, dLam, stream=None):
+        """hdg_newton_update: U += dU, Lam += dLam on device tensors."""
+        _check(lib().hdg_newton_update(self.h, _ptr(U), _ptr(Lam), _ptr(dU), _ptr(dLam), _stream(stream)),
+               self.ctx.h)
+
+    def residual_norm(self, stream=None) -> float:
+        """hdg_residual_norm: ||[N_q; N_w; N_lambda]||_2 of the last condensed state."""
+        out = ctypes.c_double()
+        _check(lib().hdg_residual_norm(self.h, ctypes.byref(out), _stream(stream)), self.ctx.h)
+        return out.value
+
+    def autotune(self, U, Lam, stream=None) -> dict:
+        """hdg_autotune: pick the fastest launch shape per degree bucket; returns {p: shape}."""
+        out = (ctypes.c_int32 * 5)()
+        _check(lib().hdg_autotune(self.h, _ptr(U), _ptr(Lam), out, _stream(stream)), self.ctx.h)
+        return {p: int(out[p]) for p in range(1, 5) if out[p] >= 0}
+
+    def set_cfl(self, cfl: float):
+        """hdg_sys_set_cfl: pseudo-time CFL number of the following condensations."""
+        _check(lib().hdg_sys_set_cfl(self.h, float(cfl)), self.ctx.h)
+        self.params.cfl = float(cfl)
 
     def views(self):
         """Zero-copy torch views of X, K, E, res_u, res_lam, elem_status."""

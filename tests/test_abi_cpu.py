@@ -4,6 +4,8 @@ tables (computed independently of the oracle) agree with the oracle's."""
 import os
 import re
 
+import math
+
 import numpy as np
 import pytest
 
@@ -74,3 +76,15 @@ def test_no_cpu_fallback_without_device():
         pytest.skip("a device is present")
     with pytest.raises(hdg.HdgError):
         hdg.Context(0)
+
+
+def test_library_cfl_law_closed_forms():
+    """The library's host-only CFL law (Eq. cfl) against the closed forms (no device needed)."""
+    for c0, n0 in ((1e6, 4), (10.0, 2)):
+        for n in range(n0 + 1):
+            t = n / n0
+            assert abs(hdg.cfl_law(n, c0=c0, n0=n0) - c0 * t * t * (3 - 2 * t)) < 1e-15 * c0
+    assert hdg.cfl_law(5, c1=1e3, n0=4, cfl_prev=7.0, res_prev=1.0, res_cur=2.0) == 7.0
+    assert abs(hdg.cfl_law(6, c1=1e3, n0=4, cfl_prev=7.0, res_prev=1.0, res_cur=0.5)
+               - 7.0 * (1 + 1e3 * math.log(2))) < 1e-9
+    assert hdg.cfl_law(-1) < 0 and hdg.cfl_law(5, n0=4, cfl_prev=1.0, res_prev=0.0, res_cur=1.0) < 0

@@ -346,3 +346,32 @@ def test_graph_replay_and_concurrent_buckets_match_plain_path(ctx, name, kw):
         assert np.array_equal(v["E"].cpu().numpy(), ref["E"])
         assert np.array_equal(v["X"].cpu().numpy(), ref["X"])
         assert np.array_equal(dUt.cpu().numpy(), ref["dU"])
+
+
+@pytest.mark.parametrize("name,kw", [("ns_mixp_65k", {}), ("ns_mixp_65k", {"model": 0}), ("euler_p3_16k", {})])
+@pytest.mark.parametrize("precision", [0, 1])
+def test_autotuned_launch_shapes_keep_results_bitwise(ctx, name, kw, precision):
+    """The autotuner only changes the grid of each degree bucket's launch; every output stays bitwise
+    the same, and the chosen shapes are in range."""
+    from paper_1308_3995_gb300 import hdg
+    wl = G.small_variant(G.WORKLOADS[name], 12, 14, **kw)
+    case, om, U, Lam, dLam = build_case(wl)
+    mesh = hdg.Mesh(ctx, case.mesh.elem_xy, case.mesh.elem_vid, case.elem_p, case.nfield)
+    sysm = hdg.System(ctx, mesh, lib_params(wl, 0.0, precision))
+    dev = torch.device("cuda:0")
+    Ut, Lt = torch.from_numpy(U).to(dev), torch.from_numpy(Lam).to(dev)
+    sysm.condense(Ut, Lt)
+    torch.cuda.synchronize()
+    before = {k: t.cpu().numpy().copy() for k, t in sysm.views().items()}
+    shapes = sysm.autotune(Ut, Lt)
+    assert set(shapes) == set(int(p) for p in np.unique(case.elem_p))
+    assert all(0 <= v <= 32 for v in shapes.values())
+    for _ in range(2):
+        sysm.condense(Ut, Lt)
+        torch.cuda.synchronize()
+        after = {k: t.cpu().numpy() for k, t in sysm.views().items()}
+        for k in before:
+            assert np.array_equal(before[k], after[k]), k
+    print(wl.name, ["fp64", "float2"][precision], "shapes", shapes)
+    sysm.close()
+    mesh.close()

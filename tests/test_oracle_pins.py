@@ -638,3 +638,28 @@ def test_threaded_condensation_is_bitwise_single_threaded():
     c0 = m.condense(P, U, L, 3, 17)
     for k in a:
         assert np.array_equal(c0[k], c1[k]), k
+
+
+# ----------------------------------------------------------------------------- CFL law (Sec. 3.3)
+@pytest.mark.parametrize("c0,n0", [(1e6, 4), (10.0, 2), (3.0, 5)])
+def test_cfl_law_ramp_closed_form(c0, n0):
+    """Eq. (cfl), ramp phase: c0 (3 t^2 - 2 t^3), t = n / n0: 0 at n = 0, c0/2 at the midpoint, c0 at n0,
+    monotone in between."""
+    vals = [O.cfl_law(n, c0=c0, n0=n0) for n in range(n0 + 1)]
+    assert vals[0] == 0.0 and abs(vals[-1] - c0) < 1e-15 * c0
+    for n, v in enumerate(vals):
+        t = n / n0
+        assert abs(v - c0 * t * t * (3 - 2 * t)) < 1e-15 * c0
+    assert all(b > a for a, b in zip(vals, vals[1:]))
+    if n0 % 2 == 0:
+        assert abs(vals[n0 // 2] - c0 / 2) < 1e-15 * c0
+    assert abs(O.cfl_law(1, c0=1e6, n0=4) - 1e6 * (3 / 16 - 2 / 64)) < 1e-9
+
+
+def test_cfl_law_growth_phase():
+    """Eq. (cfl) after the ramp: CFL^{n-1} (1 + c1 max(0, log(r_{n-1} / r_n))): unchanged when the
+    residual does not fall, times 1 + c1 ln 2 when it halves, times 1 + c1 ln 10 for a decade."""
+    assert O.cfl_law(5, c1=1e3, n0=4, cfl_prev=7.0, res_prev=1.0, res_cur=2.0) == 7.0
+    assert O.cfl_law(5, c1=1e3, n0=4, cfl_prev=7.0, res_prev=1.0, res_cur=1.0) == 7.0
+    assert abs(O.cfl_law(6, c1=1e3, n0=4, cfl_prev=7.0, res_prev=1.0, res_cur=0.5) - 7.0 * (1 + 1e3 * math.log(2))) < 1e-9
+    assert abs(O.cfl_law(9, c1=2.0, n0=4, cfl_prev=3.0, res_prev=1e-2, res_cur=1e-3) - 3.0 * (1 + 2 * math.log(10))) < 1e-12
