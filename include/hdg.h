@@ -274,8 +274,31 @@ hdg_status hdg_solver_destroy(hdg_solver* solver);
 hdg_status hdg_trace_solve(hdg_solver* solver, double* dLam, double rtol, int32_t max_iter, int32_t* iters,
                            double* rel_res, void* stream);
 
-/* y = K x for DEVICE vectors x, y [lam_len] (K of the last hdg_condense). */
-hdg_status hdg_trace_matvec(hdg_solver* solver, const double* x, double* y, void* stream);
+/* Like hdg_trace_solve, with a right-hand side other than the system's E
+ * (DEVICE rhs [lam_len]; NULL: E) and, when transpose != 0, the transposed
+ * system K^T x = rhs (block Jacobi then uses the transposed diagonal blocks):
+ * the hybridized adjoint system of Sec. 4.2. */
+hdg_status hdg_trace_solve_ex(hdg_solver* solver, const double* rhs, int32_t transpose, double* dLam, double rtol,
+                              int32_t max_iter, int32_t* iters, double* rel_res, void* stream);
+
+/* y = K x, or y = K^T x when transpose != 0, for DEVICE vectors x, y
+ * [lam_len] (K of the last hdg_condense). */
+hdg_status hdg_trace_matvec(hdg_solver* solver, const double* x, double* y, int32_t transpose, void* stream);
+
+/* Hybridized adjoint (Sec. 4.2, Euler in this build).  The adjoint system is
+ * the transpose of the Newton matrix of `primal` (same mesh and parameters,
+ * pseudo-time mass included), right-hand side [F~; 0] (F~ = J'(U) for a target
+ * functional J of the interior unknowns; the trace part is zero in the
+ * paper's formulation).  Given DEVICE U, Lam (the state of the primal's last
+ * hdg_condense) and Ftilde [u_len], this enqueues on `stream`:
+ *   X~_K = A_K^{-T} [C_K^T | F~_K] into adj's X (the adjoint local solves),
+ *   E~ = sum_K -X_B,K^T F~_K into adj's E (from primal's stored local solves).
+ * Then solve K^T Lambda~ = E~ with hdg_trace_solve_ex(solver of primal,
+ * E~ of adj, transpose = 1, ...) and reconstruct U~ = X~_F - X~_C Lambda~ with
+ * hdg_recover(adj, Lambda~, U~).  adj must be a separate system on the same
+ * mesh with the same parameters (HDG_EINVAL otherwise; HDG_ENOTSUP for NS). */
+hdg_status hdg_adjoint_condense(hdg_sys* adj, const hdg_sys* primal, const double* U, const double* Lam,
+                                const double* Ftilde, void* stream);
 
 /* Newton update on DEVICE vectors: U += dU [u_len], Lam += dLam [lam_len]. */
 hdg_status hdg_newton_update(hdg_sys* sys, double* U, double* Lam, const double* dU, const double* dLam,

@@ -45,6 +45,7 @@ struct Phys {
   double sc_eps0, sc_beta;  // shock capturing (Sec. 3.2); off unless sc_eps0 > 0
   int model, precision;
   int persistent;  // 1: grid = SMs x resident CTAs (loop over elements); 0: one CTA per element
+  int adjoint;     // 1: adjoint local solves X~ = A^{-T} [C^T | F~] only (Sec. 4.2; Euler)
   // launch shape per degree (autotuned): -1 default (by `persistent`), 0 one CTA per element,
   // k > 0 persistent grid of k CTAs per SM (capped by the occupancy)
   int grid[kMaxP + 1];
@@ -92,6 +93,7 @@ struct DevSys {
   double* ehalf1;            // [lam_len]
   double* rhalf1;            // [lam_len]
   int32_t* face_cnt;         // [n_face], zero between calls
+  const double* ftilde;      // [u_len] adjoint right-hand side (adjoint mode only)
 };
 
 // Read-only view of a mesh plan and its context, for translation units other

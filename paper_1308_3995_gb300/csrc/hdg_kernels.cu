@@ -359,8 +359,9 @@ __global__ void __launch_bounds__(kCondThreads, 4) k_condense_euler(
       }
     }
     __syncthreads();
+    const bool adjoint = ph.adjoint != 0;
     // B = d N_w / d Lambda: rows (f,i) over warps, columns (face a; g, l) over lanes
-    for (int r = ty; r < N; r += NW) {
+    for (int r = ty; r < (adjoint ? 0 : N); r += NW) {
       const int f = r / NP, i = r - f * NP;
       for (int c = tx; c < nt; c += 32) {
         const int a = g_cf[c], g = g_cg[c], l = g_cl[c], nk = g_nk[a];
@@ -371,7 +372,7 @@ __global__ void __launch_bounds__(kCondThreads, 4) k_condense_euler(
       }
     }
     // D_a = d N_lambda,a / d Lambda_a (block diagonal in faces): rows over warps, columns over lanes
-    for (int a = 0; a < 3; ++a) {
+    for (int a = 0; a < (adjoint ? 0 : 3); ++a) {
       const int nk = g_nk[a], m4 = 4 * nk, o = g_toff[a];
       const T* ps = tab + to.edge_psi[g_pe[a]];
       for (int r = ty; r < m4; r += NW) {
@@ -446,8 +447,29 @@ __global__ void __launch_bounds__(kCondThreads, 4) k_condense_euler(
         sNu[t] = A::norm(acc);
       }
     }
-    for (int t = tid; t < N; t += NT) sR[t * ldr + nt] = A::neg(sNu[t]);  // F
+    for (int t = tid; t < N; t += NT)  // F, or the adjoint right-hand side F~
+      sR[t * ldr + nt] = adjoint ? A::from_d(s.ftilde[m.u_off[K] + t]) : A::neg(sNu[t]);
     __syncthreads();
+    if (adjoint) {
+      // transposed local system (Sec. 4.2): A^T against [C^T | F~],
+      // C^T[(f,i), (a,g,l)] = alpha |e_a| <psi_l, phi_i> delta_fg
+      for (int t = tid; t < N * N; t += NT) {
+        const int i = t / N, j = t - i * N;
+        if (i < j) {
+          const T v = sA[i * LDA + j];
+          sA[i * LDA + j] = sA[j * LDA + i];
+          sA[j * LDA + i] = v;
+        }
+      }
+      for (int r = ty; r < N; r += NW) {
+        const int f = r / NP, i = r - f * NP;
+        for (int c = tx; c < nt; c += 32) {
+          const int a = g_cf[c], g = g_cg[c], l = g_cl[c];
+          sR[r * ldr + c] = (g == f) ? sMe[(a * 5 + l) * NP + i] : zero;
+        }
+      }
+      __syncthreads();
+    }
 
     // ---------------- a4/a5: LU with partial pivoting on [A | B | F] ----------------
     const int nr1 = nt + 1;
@@ -467,6 +489,12 @@ __global__ void __launch_bounds__(kCondThreads, 4) k_condense_euler(
       for (int t = tid; t < N; t += NT) ru[t] = A::to_d(sNu[t]);
     }
     __syncthreads();
+    if (adjoint) {  // the adjoint needs only the local solves
+      if (bad) atomicOr(&s_bad, 2);
+      __syncthreads();
+      if (tid == 0) s.status[K] = (s_bad & 1) ? 1 : ((s_bad & 2) ? 2 : 0);
+      continue;
+    }
 
     // ---------------- a6/a7: Schur complement, E_K, assembly ----------------
     // rows (face a; f, k) over warps, columns (face b; g, l | E) over lanes

@@ -37,6 +37,7 @@ struct hdg_sys {
   hdg::Phys ph{};
   hdg::DevSys ds{};
   double *d_U = nullptr, *d_Lam = nullptr, *d_dLam = nullptr, *d_dU = nullptr;
+  int* d_face_el = nullptr;  // [n_face][2], uploaded by the first hdg_adjoint_condense
   std::vector<void*> allocs;
   int launches = 0;
   bool need_zero = true;

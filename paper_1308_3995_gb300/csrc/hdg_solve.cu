@@ -46,6 +46,7 @@ struct FaceDev {
   const int* k_col;         // [5 n_face]
   const int64_t* k_blkoff;  // [5 n_face + 1]
   const int64_t* dinv_off;  // [n_face]
+  const int64_t* k_tblk;    // [5 n_face]: offset of block (k_col[5e+b], e), for products with K^T
   const double* K;
   double* dinv;
   int* bad;                 // set to 1 if a diagonal block is singular
@@ -121,6 +122,8 @@ __global__ void __launch_bounds__(32 * kFaceWarps) k_bj_invert(FaceDev f) {
 // nseg partial sums of a row meet by shuffles.  On this part the binary64 pipe,
 // not HBM, bounds a binary64 product of 0.25 flop per byte, so idle lanes
 // would cost time directly.
+// TR: the same with K^T (block (k_col[5e+b], e) transposed) and Dinv^T.
+template <bool TR>
 __global__ void __launch_bounds__(32 * kFaceWarps) k_face_op(FaceDev f, const double* __restrict__ x,
                                                                const double* __restrict__ bvec, double* __restrict__ y,
                                                                int mode) {
@@ -139,22 +142,28 @@ __global__ void __launch_bounds__(32 * kFaceWarps) k_face_op(FaceDev f, const do
   if (mode != 3) {
     for (int b = 0; b < 5; ++b) {
       const int col = f.k_col[5 * e + b];
-      const int mb = 4 * (f.face_p[col] + 1), ld = mb + 1, n = m * mb;
-      const double* blk = f.K + f.k_blkoff[5 * e + b];
+      const int mb = 4 * (f.face_p[col] + 1), n = m * mb;
+      // stored block: K (e, col) is m x mb; for K^T, block (col, e) is mb x m
+      const double* blk = f.K + (TR ? f.k_tblk[5 * e + b] : f.k_blkoff[5 * e + b]);
+      const int rl = TR ? m : mb, ld = rl + 1;  // stored row length and padded stride
       // (row, column) of entry lane + 32 k, stepped without division
-      const int q = 32 / mb, qr = 32 - q * mb;
-      int rr = lane / mb, cc = lane - rr * mb;
+      const int q = 32 / rl, qr = 32 - q * rl;
+      int rr = lane / rl, cc = lane - rr * rl;
       for (int idx = lane; idx < n; idx += 32) {
         sb[rr * ld + cc] = __ldcs(blk + idx);  // streamed: each value is used once per product
         rr += q;
         cc += qr;
-        if (cc >= mb) { cc -= mb; ++rr; }
+        if (cc >= rl) { cc -= rl; ++rr; }
       }
       __syncwarp();
       if (act) {
         const double* xc = x + f.lam_off[col];
-        const double* row = sb + r * ld;
-        for (int c = sg; c < mb; c += nseg) t = fma(row[c], __ldg(xc + c), t);
+        if (TR) {
+          for (int c = sg; c < mb; c += nseg) t = fma(sb[c * ld + r], __ldg(xc + c), t);
+        } else {
+          const double* row = sb + r * ld;
+          for (int c = sg; c < mb; c += nseg) t = fma(row[c], __ldg(xc + c), t);
+        }
       }
       __syncwarp();
     }
@@ -173,8 +182,8 @@ __global__ void __launch_bounds__(32 * kFaceWarps) k_face_op(FaceDev f, const do
   }
   double v = 0.0;
   if (act) {
-    const double* di = f.dinv + f.dinv_off[e] + (int64_t)r * m;
-    for (int c = sg; c < m; c += nseg) v = fma(di[c], s_t[w][c], v);
+    const double* di = f.dinv + f.dinv_off[e];
+    for (int c = sg; c < m; c += nseg) v = fma(TR ? di[c * m + r] : di[r * m + c], s_t[w][c], v);
   }
   for (int o = m * (nseg >> 1); o >= m; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
   if (lane < m) y[lo + lane] = v;
@@ -286,6 +295,12 @@ hdg_status ck(hdg_ctx* ctx, cudaError_t e, const char* what) {
   return HDG_OK;
 }
 
+void face_op(hdg_solver* S, bool tr, const double* x, const double* b, double* y, int mode, cudaStream_t st) {
+  const int fb = (S->f.n_face + kFaceWarps - 1) / kFaceWarps;
+  if (tr) k_face_op<true><<<fb, 32 * kFaceWarps, 0, st>>>(S->f, x, b, y, mode);
+  else k_face_op<false><<<fb, 32 * kFaceWarps, 0, st>>>(S->f, x, b, y, mode);
+}
+
 // out[0..nvec) = V_j . w for j < nvec (device), enqueued on st
 void multidot(hdg_solver* S, const double* V, int nvec, const double* w, int64_t n, double* out, cudaStream_t st) {
   dim3 g(S->dot_blocks, (nvec + kDotChunk - 1) / kDotChunk);
@@ -310,6 +325,13 @@ hdg_status hdg_solver_create(hdg_sys* sys, int32_t restart, hdg_solver** out) {
   S->n = M->lam_len;
   cudaDeviceGetAttribute(&S->sms, cudaDevAttrMultiProcessorCount, ctx->device);
   S->dot_blocks = std::max(1, std::min<int>(2 * S->sms, (int)((S->n + kDotThreads - 1) / kDotThreads)));
+  std::vector<int64_t> tblk(5 * (size_t)M->n_face, -1);
+  for (int e = 0; e < M->n_face; ++e)
+    for (int b = 0; b < 5; ++b) {
+      const int f = M->k_col[5 * e + b];
+      for (int t = 0; t < 5; ++t)
+        if (M->k_col[5 * f + t] == e) tblk[5 * e + b] = M->k_blkoff[5 * f + t];
+    }
   std::vector<int64_t> dinv_off(M->n_face);
   int64_t tot = 0;
   for (int e = 0; e < M->n_face; ++e) {
@@ -322,9 +344,10 @@ hdg_status hdg_solver_create(hdg_sys* sys, int32_t restart, hdg_solver** out) {
     S->allocs.push_back(*p);
     return true;
   };
-  void *kc, *kb, *dof, *dinv, *bad, *V, *part, *h, *coef, *zero;
+  void *kc, *kb, *kt, *dof, *dinv, *bad, *V, *part, *h, *coef, *zero;
   const size_t nr = (size_t)restart + 1;
   bool ok = alloc(sizeof(int) * M->k_col.size(), &kc) && alloc(sizeof(int64_t) * M->k_blkoff.size(), &kb) &&
+            alloc(sizeof(int64_t) * tblk.size(), &kt) &&
             alloc(sizeof(int64_t) * dinv_off.size(), &dof) && alloc(sizeof(double) * tot, &dinv) &&
             alloc(sizeof(int), &bad) && alloc(sizeof(double) * nr * S->n, &V) &&
             alloc(sizeof(double) * nr * S->dot_blocks, &part) && alloc(sizeof(double) * (2 * nr + 2), &h) &&
@@ -338,6 +361,7 @@ hdg_status hdg_solver_create(hdg_sys* sys, int32_t restart, hdg_solver** out) {
   if (st == HDG_OK) st = ck(ctx, cudaMemcpy(kc, M->k_col.data(), sizeof(int) * M->k_col.size(), cudaMemcpyHostToDevice), "cudaMemcpy");
   if (st == HDG_OK) st = ck(ctx, cudaMemcpy(kb, M->k_blkoff.data(), sizeof(int64_t) * M->k_blkoff.size(), cudaMemcpyHostToDevice), "cudaMemcpy");
   if (st == HDG_OK) st = ck(ctx, cudaMemcpy(dof, dinv_off.data(), sizeof(int64_t) * dinv_off.size(), cudaMemcpyHostToDevice), "cudaMemcpy");
+  if (st == HDG_OK) st = ck(ctx, cudaMemcpy(kt, tblk.data(), sizeof(int64_t) * tblk.size(), cudaMemcpyHostToDevice), "cudaMemcpy");
   if (st == HDG_OK) st = ck(ctx, cudaMemset(zero, 0, sizeof(double) * S->n), "cudaMemset");
   if (st != HDG_OK) {
     for (void* p : S->allocs) cudaFree(p);
@@ -351,6 +375,7 @@ hdg_status hdg_solver_create(hdg_sys* sys, int32_t restart, hdg_solver** out) {
   S->f.k_col = (const int*)kc;
   S->f.k_blkoff = (const int64_t*)kb;
   S->f.dinv_off = (const int64_t*)dof;
+  S->f.k_tblk = (const int64_t*)kt;
   S->f.K = sys->ds.K;
   S->f.dinv = (double*)dinv;
   S->f.bad = (int*)bad;
@@ -372,17 +397,21 @@ hdg_status hdg_solver_destroy(hdg_solver* S) {
   return HDG_OK;
 }
 
-hdg_status hdg_trace_matvec(hdg_solver* S, const double* x, double* y, void* stream) {
+hdg_status hdg_trace_matvec(hdg_solver* S, const double* x, double* y, int32_t transpose, void* stream) {
   if (!S || !x || !y) return HDG_EINVAL;
-  cudaStream_t st = (cudaStream_t)stream;
-  const int fb = (S->f.n_face + kFaceWarps - 1) / kFaceWarps;
-  k_face_op<<<fb, 32 * kFaceWarps, 0, st>>>(S->f, x, nullptr, y, 2);
+  face_op(S, transpose != 0, x, nullptr, y, 2, (cudaStream_t)stream);
   return ck(S->sys->ctx, cudaGetLastError(), "k_face_op");
 }
 
 hdg_status hdg_trace_solve(hdg_solver* S, double* x, double rtol, int32_t max_iter, int32_t* iters_out,
                            double* rel_out, void* stream) {
+  return hdg_trace_solve_ex(S, nullptr, 0, x, rtol, max_iter, iters_out, rel_out, stream);
+}
+
+hdg_status hdg_trace_solve_ex(hdg_solver* S, const double* rhs, int32_t transpose, double* x, double rtol,
+                              int32_t max_iter, int32_t* iters_out, double* rel_out, void* stream) {
   if (!S || !x || !(rtol > 0.0) || max_iter < 1) return HDG_EINVAL;
+  const bool tr = transpose != 0;
   hdg_ctx* ctx = S->sys->ctx;
   cudaStream_t st = (cudaStream_t)stream;
   const int64_t n = S->n;
@@ -396,8 +425,8 @@ hdg_status hdg_trace_solve(hdg_solver* S, double* x, double rtol, int32_t max_it
   if ((rs = ck(ctx, cudaMemsetAsync(S->f.bad, 0, sizeof(int), st), "cudaMemsetAsync")) != HDG_OK) return rs;
   k_bj_invert<<<fb, 32 * kFaceWarps, 0, st>>>(S->f);
   // ||M^-1 E||
-  double* E = S->sys->ds.E;
-  k_face_op<<<fb, 32 * kFaceWarps, 0, st>>>(S->f, S->zero, E, S->V, 3);
+  const double* E = rhs ? rhs : S->sys->ds.E;
+  face_op(S, tr, S->zero, E, S->V, 3, st);
   multidot(S, S->V, 1, S->V, n, S->h, st);
   int bad = 0;
   if ((rs = ck(ctx, cudaMemcpyAsync(S->hpin, S->h, sizeof(double), cudaMemcpyDeviceToHost, st), "cudaMemcpyAsync")) != HDG_OK) return rs;
@@ -415,7 +444,7 @@ hdg_status hdg_trace_solve(hdg_solver* S, double* x, double rtol, int32_t max_it
   double rel = 1.0;
   while (true) {
     // r0 = M^-1 (E - K x), beta = ||r0||
-    k_face_op<<<fb, 32 * kFaceWarps, 0, st>>>(S->f, x, E, S->V, 1);
+    face_op(S, tr, x, E, S->V, 1, st);
     multidot(S, S->V, 1, S->V, n, S->h, st);
     if ((rs = ck(ctx, cudaMemcpyAsync(S->hpin, S->h, sizeof(double), cudaMemcpyDeviceToHost, st), "cudaMemcpyAsync")) != HDG_OK) return rs;
     if ((rs = ck(ctx, cudaStreamSynchronize(st), "cudaStreamSynchronize")) != HDG_OK) return rs;
@@ -429,7 +458,7 @@ hdg_status hdg_trace_solve(hdg_solver* S, double* x, double rtol, int32_t max_it
     for (int j = 0; j < R && it < max_iter; ++j) {
       double* vj = S->V + (int64_t)j * n;
       double* w = S->V + (int64_t)(j + 1) * n;
-      k_face_op<<<fb, 32 * kFaceWarps, 0, st>>>(S->f, vj, nullptr, w, 0);
+      face_op(S, tr, vj, nullptr, w, 0, st);
       // classical Gram-Schmidt, twice
       multidot(S, S->V, j + 1, w, n, S->h, st);
       k_multiaxpy<<<vb, 256, 0, st>>>(S->V, n, j + 1, S->h, -1.0, w, n);

@@ -33,7 +33,7 @@ EXPORTS = ["hdg_create", "hdg_destroy", "hdg_last_error", "hdg_mesh_create", "hd
            "hdg_condense_noalloc", "hdg_sys_workspace_bytes", "hdg_sys_create_in",
            "hdg_step_host_async", "hdg_graph_create", "hdg_graph_launch", "hdg_solver_create",
            "hdg_solver_destroy", "hdg_trace_solve", "hdg_trace_matvec", "hdg_newton_update", "hdg_residual_norm",
-           "hdg_sys_set_cfl", "hdg_cfl_law", "hdg_autotune"]
+           "hdg_sys_set_cfl", "hdg_cfl_law", "hdg_autotune", "hdg_trace_solve_ex", "hdg_adjoint_condense"]
 
 
 class HdgError(RuntimeError):
@@ -118,7 +118,10 @@ def lib(build: bool = True):
         L.hdg_solver_destroy.argtypes = [_vp]
         L.hdg_trace_solve.argtypes = [_vp, _vp, ctypes.c_double, ctypes.c_int32, ctypes.POINTER(ctypes.c_int32),
                                       ctypes.POINTER(ctypes.c_double), _vp]
-        L.hdg_trace_matvec.argtypes = [_vp, _vp, _vp, _vp]
+        L.hdg_trace_matvec.argtypes = [_vp, _vp, _vp, ctypes.c_int32, _vp]
+        L.hdg_trace_solve_ex.argtypes = [_vp, _vp, ctypes.c_int32, _vp, ctypes.c_double, ctypes.c_int32,
+                                         ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(ctypes.c_double), _vp]
+        L.hdg_adjoint_condense.argtypes = [_vp, _vp, _vp, _vp, _vp, _vp]
         L.hdg_newton_update.argtypes = [_vp, _vp, _vp, _vp, _vp, _vp]
         L.hdg_residual_norm.argtypes = [_vp, ctypes.POINTER(ctypes.c_double), _vp]
         L.hdg_sys_set_cfl.argtypes = [_vp, ctypes.c_double]
@@ -165,17 +168,20 @@ class Solver:
         _check(lib().hdg_solver_create(system.h, int(restart), ctypes.byref(h)), system.ctx.h)
         self.h, self.sys = h, system
 
-    def solve(self, dLam, rtol=1e-12, max_iter=500, stream=None, check=True):
-        """Solve K dLam = E in place (dLam holds the initial guess); returns (iterations, rel. residual)."""
+    def solve(self, dLam, rtol=1e-12, max_iter=500, stream=None, check=True, rhs=None, transpose=False):
+        """Solve K dLam = E (or K^T dLam = rhs) in place (dLam holds the initial guess);
+        returns (iterations, rel. residual)."""
         it, rel = ctypes.c_int32(), ctypes.c_double()
-        st = lib().hdg_trace_solve(self.h, _ptr(dLam), float(rtol), int(max_iter), ctypes.byref(it),
-                                   ctypes.byref(rel), _stream(stream))
+        st = lib().hdg_trace_solve_ex(self.h, _ptr(rhs) if rhs is not None else None, int(bool(transpose)),
+                                      _ptr(dLam), float(rtol), int(max_iter), ctypes.byref(it),
+                                      ctypes.byref(rel), _stream(stream))
         if check:
             _check(st, self.sys.ctx.h)
         return int(it.value), float(rel.value)
 
-    def matvec(self, x, y, stream=None):
-        _check(lib().hdg_trace_matvec(self.h, _ptr(x), _ptr(y), _stream(stream)), self.sys.ctx.h)
+    def matvec(self, x, y, stream=None, transpose=False):
+        _check(lib().hdg_trace_matvec(self.h, _ptr(x), _ptr(y), int(bool(transpose)), _stream(stream)),
+               self.sys.ctx.h)
 
     def close(self):
         if getattr(self, "h", None):
@@ -358,6 +364,11 @@ class System:
         out = (ctypes.c_int32 * 5)()
         _check(lib().hdg_autotune(self.h, _ptr(U), _ptr(Lam), out, _stream(stream)), self.ctx.h)
         return {p: int(out[p]) for p in range(1, 5) if out[p] >= 0}
+
+    def adjoint_condense(self, primal: "System", U, Lam, Ftilde, stream=None):
+        """hdg_adjoint_condense: adjoint local solves into this system's X, E~ into its E."""
+        _check(lib().hdg_adjoint_condense(self.h, primal.h, _ptr(U), _ptr(Lam), _ptr(Ftilde), _stream(stream)),
+               self.ctx.h)
 
     def set_cfl(self, cfl: float):
         """hdg_sys_set_cfl: pseudo-time CFL number of the following condensations."""

@@ -148,3 +148,61 @@ def test_trace_solve_reports_timeout_and_singular_blocks(ctx):
         solver.solve(x.zero_(), rtol=1e-10, max_iter=10)
     assert ei.value.status == hdg.HDG_ESINGULAR
     solver.close(); sysm.close(); mesh.close()
+
+
+@pytest.mark.parametrize("name,nx,ny,kw,precision", [("euler_p1_256", 3, 3, {"jitter": 0.2}, 0),
+                                                     ("euler_p3_16k", 3, 3, {}, 0),
+                                                     ("ns_mixp_65k", 3, 4, {"model": 0}, 0),
+                                                     ("euler_p3_16k", 3, 3, {}, 1)])
+def test_hybridized_adjoint_matches_transposed_monolithic_solve(ctx, name, nx, ny, kw, precision):
+    """Sec. 4.2: the adjoint of the Newton matrix (pseudo-time mass included, CFL 10) with right-hand
+    side [F~; 0]: GPU adjoint local solves, E~ = -X_B^T F~, GMRES on K^T, reconstruction -- against
+    the dense solve of the transposed monolithic Jacobian of the oracle (complex step)."""
+    from paper_1308_3995_gb300 import hdg
+    wl = G.small_variant(G.WORKLOADS[name], nx, ny, **kw)
+    cfl = 10.0
+    case, om, U, Lam, mesh, primal, Ut, Lt = setup(ctx, wl, cfl, precision)
+    adj = hdg.System(ctx, mesh, lib_params(wl, cfl, precision))
+    Ft = np.random.default_rng(11).standard_normal(mesh.u_len)       # stands in for J'(U)
+    Ftt = torch.from_numpy(Ft).to("cuda:0")
+    primal.condense(Ut, Lt)
+    adj.adjoint_condense(primal, Ut, Lt, Ftt)
+    solver = hdg.Solver(primal, restart=40)
+    lt = torch.zeros(mesh.lam_len, dtype=torch.float64, device="cuda:0")
+    ut = torch.zeros(mesh.u_len, dtype=torch.float64, device="cuda:0")
+    it, rel = solver.solve(lt, rtol=1e-14, max_iter=1000, rhs=adj.views()["E"], transpose=True)
+    adj.recover(lt, ut)
+    torch.cuda.synchronize()
+    _, _, J = om.monolithic(oracle_params(wl, cfl), U, Lam, want_matrix=True)
+    z = np.linalg.solve(J.T, np.concatenate([Ft, np.zeros(om.lam_len)]))
+    eu, el = rel_err(ut.cpu().numpy(), z[:om.u_len]), rel_err(lt.cpu().numpy(), z[om.u_len:])
+    print(wl.name, ["fp64", "float2"][precision], "iterations", it, f"adjoint U~ {eu:.1e} Lambda~ {el:.1e}")
+    tol = [1e-10, 1e-9][precision]
+    assert eu < tol and el < tol
+    # the transposed product against the oracle's dense K^T
+    r = om.condense(oracle_params(wl, cfl), U, Lam)
+    v = torch.from_numpy(np.random.default_rng(4).standard_normal(mesh.lam_len)).to("cuda:0")
+    y = torch.empty_like(v)
+    solver.matvec(v, y, transpose=True)
+    torch.cuda.synchronize()
+    assert rel_err(y.cpu().numpy(), om.dense_K(r["K"]).T @ v.cpu().numpy()) < [1e-13, 1e-11][precision]
+    solver.close(); adj.close(); primal.close(); mesh.close()
+
+
+def test_adjoint_rejects_mismatched_systems(ctx):
+    from paper_1308_3995_gb300 import hdg
+    wl = G.small_variant(G.WORKLOADS["euler_p3_16k"], 3, 3)
+    case, om, U, Lam, mesh, primal, Ut, Lt = setup(ctx, wl, 10.0)
+    other = hdg.System(ctx, mesh, lib_params(wl, 5.0))
+    Ft = torch.zeros(mesh.u_len, dtype=torch.float64, device="cuda:0")
+    with pytest.raises(hdg.HdgError) as ei:
+        other.adjoint_condense(primal, Ut, Lt, Ft)
+    assert ei.value.status == hdg.HDG_EINVAL
+    other.close(); primal.close(); mesh.close()
+    wl = G.small_variant(G.WORKLOADS["ns_mixp_65k"], 3, 3)
+    case, om, U, Lam, mesh, primal, Ut, Lt = setup(ctx, wl, 10.0)
+    adj = hdg.System(ctx, mesh, lib_params(wl, 10.0))
+    with pytest.raises(hdg.HdgError) as ei:
+        adj.adjoint_condense(primal, Ut, Lt, torch.zeros(mesh.u_len, dtype=torch.float64, device="cuda:0"))
+    assert ei.value.status == hdg.HDG_ENOTSUP
+    adj.close(); primal.close(); mesh.close()
