@@ -88,6 +88,10 @@ def lib():
         L.orc_cfl_law.argtypes = [ctypes.c_int, ctypes.c_double, ctypes.c_double, ctypes.c_int, ctypes.c_double,
                                   ctypes.c_double, ctypes.c_double]
         L.orc_cfl_law.restype = ctypes.c_double
+        L.orc_smoothness.argtypes = [ctypes.c_void_p, ctypes.c_int, _c_double_p]
+        L.orc_smoothness.restype = ctypes.c_double
+        L.orc_adapt_mark.argtypes = [ctypes.c_int, _c_double_p, _c_double_p, ctypes.c_double, ctypes.c_double,
+                                     ctypes.POINTER(ctypes.c_int8)]
         L.orc_sc_epsilon.argtypes = [ctypes.c_void_p, P, ctypes.c_int, _c_double_p]
         L.orc_sc_epsilon.restype = ctypes.c_double
         _lib = L
@@ -192,6 +196,15 @@ def cfl_law(n, c0=1e6, c1=1e3, n0=4, cfl_prev=0.0, res_prev=1.0, res_cur=1.0) ->
                                    float(res_cur)))
 
 
+def adapt_mark(eta2, sensor, theta=0.05, eps_s=1e-6):
+    """Doerfler marking with the h/p choice (Sec. 4.3-4.4): codes 0 / 1 (p) / 2 (h), count marked."""
+    eta2 = _f64(eta2); sensor = _f64(sensor)
+    code = np.zeros(eta2.size, np.int8)
+    nm = lib().orc_adapt_mark(int(eta2.size), _d(eta2), _d(sensor), float(theta), float(eps_s),
+                              code.ctypes.data_as(ctypes.POINTER(ctypes.c_int8)))
+    return code, int(nm)
+
+
 # --------------------------------------------------------------------------- mesh-level
 class Mesh:
     """Oracle mesh: faces, sides and the documented layouts of U, Lambda, X, K."""
@@ -248,6 +261,10 @@ class Mesh:
         P = params.c()
         lib().orc_element_residual(self._h, ctypes.byref(P), int(K), _d(_f64(U)), _d(_f64(Lam)), _d(Nu), _d(Nl))
         return Nu, Nl
+
+    def smoothness(self, K, U):
+        """Smoothness sensor S_K of Sec. 4.4."""
+        return float(lib().orc_smoothness(self._h, int(K), _d(_f64(U))))
 
     def sc_epsilon(self, params, K, U):
         """Shock-capturing viscosity eps_K of element K (Sec. 3.2); 0 when off."""

@@ -1048,6 +1048,86 @@ double orc_sc_epsilon(void* h, const orc_params* P, int K, const double* U) {
   return sc_epsilon(*M, *P, K, g, U + M->u_off[K]);
 }
 
+// ---------------------------------------------------------------------------
+// Adaptation decisions (Sec. 4): smoothness sensor, element indicator, Doerfler
+// marking, choice between h- and p-refinement.
+// ---------------------------------------------------------------------------
+// S_K = (w - w*, w - w*)_K / (w, w)_K, w* the L2 projection of w onto degree
+// p_K - 1 (Sec. 4.4).  The inner product of the vector w sums its four
+// conserved components; with the orthonormal hierarchical basis (mass det J * I)
+// w - w* is the part of w on the degree-p_K modes, so S_K is a ratio of sums of
+// squared coefficients.  Written here as the quotient of the two L2 norms
+// integrated by the element's volume rule (the same number, by orthonormality).
+double orc_smoothness(void* h, int K, const double* U) {
+  OMesh* M = (OMesh*)h;
+  const int p = M->p[K], np = n_basis(p), npl = n_basis(p - 1);
+  const int woff = (M->nfield == 12) ? 8 * np : 0;
+  const double* c = U + M->u_off[K] + woff;
+  const VolTab& V = g_vol[p];
+  double num = 0.0, den = 0.0;
+  for (int q = 0; q < V.nq; ++q) {
+    const double* phi = &V.phi[q * np];
+    for (int f = 0; f < 4; ++f) {
+      double w = 0.0, wh = 0.0;
+      for (int j = 0; j < np; ++j) {
+        w += c[f * np + j] * phi[j];
+        if (j >= npl) wh += c[f * np + j] * phi[j];
+      }
+      num += V.w[q] * wh * wh;
+      den += V.w[q] * w * w;
+    }
+  }
+  return den > 0.0 ? num / den : 0.0;
+}
+
+// Doerfler marking (Sec. 4.3): the smallest set M with eta_M >= (1 - theta) eta_T,
+// eta_M^2 = sum_{K in M} eta_K^2.  Order-independent sums: each eta_K^2 is taken
+// in fixed point, v_K = floor(eta_K^2 / max eta^2 * 2^bits), bits = 62 -
+// ceil(log2(n + 1)); the set is the first elements in the order (v descending,
+// index ascending) whose cumulative v reaches ceil((1 - theta)^2 sum v).
+// Then (Sec. 4.4) marked elements with S_K < eps_s get p-enrichment (1), the
+// others mesh refinement (2); unmarked 0.  Returns the number marked.
+static int fixed_bits(int n) {
+  int lg = 0;
+  while ((1LL << lg) < (long long)n + 1) ++lg;
+  return 62 - lg;
+}
+int orc_adapt_mark(int n, const double* eta2, const double* sensor, double theta, double eps_s, int8_t* code) {
+  double mx = 0.0;
+  for (int K = 0; K < n; ++K) mx = std::max(mx, eta2[K]);
+  std::vector<long long> v(n, 0);
+  const int bits = fixed_bits(n);
+  if (mx > 0.0)
+    for (int K = 0; K < n; ++K) v[K] = (long long)std::floor(std::ldexp(eta2[K] / mx, bits));
+  unsigned long long tot = 0;
+  for (int K = 0; K < n; ++K) tot += (unsigned long long)v[K];
+  // target = ceil(tot * q), q = (1 - theta)^2 in binary64, exactly: q = mant * 2^ex
+  const double q = (1.0 - theta) * (1.0 - theta);
+  unsigned long long target = 0;
+  if (q > 0.0 && tot > 0) {
+    int ex = 0;
+    const double fr = std::frexp(q, &ex);                                  // q = fr 2^ex, fr in [0.5, 1)
+    const unsigned long long mant = (unsigned long long)std::ldexp(fr, 53);  // q = mant 2^(ex - 53)
+    const unsigned __int128 prod = (unsigned __int128)tot * mant;
+    const int sh = 53 - ex;                                                  // >= 52 for q <= 1
+    const unsigned __int128 one = 1;
+    target = sh >= 120 ? 1ULL : (unsigned long long)((prod + (one << sh) - 1) >> sh);
+  }
+  std::vector<int> idx(n);
+  for (int K = 0; K < n; ++K) idx[K] = K;
+  std::stable_sort(idx.begin(), idx.end(), [&](int a, int b) { return v[a] > v[b]; });
+  for (int K = 0; K < n; ++K) code[K] = 0;
+  unsigned long long cum = 0;
+  int marked = 0;
+  for (int t = 0; t < n && cum < target; ++t) {
+    const int K = idx[t];
+    cum += (unsigned long long)v[K];
+    code[K] = sensor[K] < eps_s ? 1 : 2;
+    ++marked;
+  }
+  return marked;
+}
+
 // Dense LU solve helper for tests (A n x n row-major, b -> x in place).
 int orc_dense_solve(int n, const double* A, double* b) {
   std::vector<double> a(A, A + (int64_t)n * n);

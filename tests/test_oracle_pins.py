@@ -663,3 +663,57 @@ def test_cfl_law_growth_phase():
     assert O.cfl_law(5, c1=1e3, n0=4, cfl_prev=7.0, res_prev=1.0, res_cur=1.0) == 7.0
     assert abs(O.cfl_law(6, c1=1e3, n0=4, cfl_prev=7.0, res_prev=1.0, res_cur=0.5) - 7.0 * (1 + 1e3 * math.log(2))) < 1e-9
     assert abs(O.cfl_law(9, c1=2.0, n0=4, cfl_prev=3.0, res_prev=1e-2, res_cur=1e-3) - 3.0 * (1 + 2 * math.log(10))) < 1e-12
+
+
+# ----------------------------------------------------------------------------- adaptation (Sec. 4)
+@pytest.mark.parametrize("model", [0, 1])
+def test_smoothness_sensor_closed_forms(model):
+    """Sec. 4.4: S_K = |w - w*|^2 / |w|^2 with w* the projection onto degree p-1: 0 for a state of
+    degree p-1, 1 for a state on the degree-p modes only, and, by the orthonormality of the
+    hierarchical basis, the share of the squared degree-p coefficients; scale invariant."""
+    wl, c, m, P = _case("ns_mixp_65k", 3, 3, model=model)
+    U, L, _ = G.case_state(c, m.face_vid, m.face_p)
+    for K in range(0, m.n_elem, 4):
+        p = int(m.elem_p[K]); nb = O.n_basis(p); nl = O.n_basis(p - 1)
+        woff = m.u_off[K] + (8 * nb if m.nfield == 12 else 0)
+        w = U[woff:woff + 4 * nb].reshape(4, nb)
+        ref = (w[:, nl:] ** 2).sum() / (w ** 2).sum()
+        assert abs(m.smoothness(K, U) - ref) < 1e-13 * max(ref, 1e-30) + 1e-30
+        assert abs(m.smoothness(K, 3.5 * U) - ref) < 1e-13 * max(ref, 1e-30) + 1e-30
+        U2 = U.copy(); U2[woff:woff + 4 * nb].reshape(4, nb)[:, nl:] = 0.0
+        assert m.smoothness(K, U2) == 0.0
+        U3 = U.copy(); U3[woff:woff + 4 * nb].reshape(4, nb)[:, :nl] = 0.0
+        assert abs(m.smoothness(K, U3) - 1.0) < 1e-14
+
+
+def test_dorfler_marking_hand_examples():
+    """Sec. 4.3: the smallest set M with eta_M >= (1 - theta) eta_T, eta^2 summed; ties by index."""
+    S = np.array([1e-9, 1e-3, 1e-8, 0.5])
+    code, nm = O.adapt_mark([1.0, 4.0, 9.0, 16.0], S, theta=0.05, eps_s=1e-6)
+    # 0.9025 * 30 = 27.075: 16 + 9 = 25 < 27.075 <= 29 = 16 + 9 + 4 -> elements 3, 2, 1
+    assert nm == 3 and list(code) == [0, 2, 1, 2]
+    code, nm = O.adapt_mark([1.0, 4.0, 9.0, 16.0], S, theta=0.5)
+    assert nm == 1 and list(code) == [0, 0, 0, 2]
+    code, nm = O.adapt_mark([1.0, 1.0, 1.0, 1.0], S, theta=0.5)       # ties: lowest index first
+    assert nm == 1 and list(code) == [1, 0, 0, 0]
+    code, nm = O.adapt_mark([2.0, 0.0, 2.0, 0.0], S, theta=0.0)       # everything with a share
+    assert nm == 2 and list(code) == [1, 0, 1, 0]
+    code, nm = O.adapt_mark(np.zeros(5), np.zeros(5), theta=0.05)
+    assert nm == 0 and not code.any()
+
+
+def test_dorfler_marking_is_minimal_on_random_indicators():
+    """Brute-force check of minimality and of the threshold on random indicators."""
+    rng = np.random.default_rng(2)
+    for trial in range(20):
+        n = int(rng.integers(1, 60))
+        eta2 = rng.exponential(size=n) ** 3
+        theta = float(rng.uniform(0.0, 0.9))
+        code, nm = O.adapt_mark(eta2, np.zeros(n), theta=theta)
+        mk = code > 0
+        order = np.argsort(-eta2, kind="stable")
+        tot = eta2.sum()
+        assert eta2[mk].sum() >= (1 - theta) ** 2 * tot * (1 - 1e-12)
+        if nm > 0:   # dropping the smallest marked element falls below the fraction
+            assert eta2[order[:nm - 1]].sum() < (1 - theta) ** 2 * tot * (1 + 1e-12)
+        assert set(np.nonzero(mk)[0]) == set(order[:nm])
