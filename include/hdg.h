@@ -243,6 +243,34 @@ hdg_status hdg_sys_get(const hdg_sys* sys, double** X, double** K_vals, double**
  * -1 no elements of that degree).  Not allowed while a captured graph exists. */
 hdg_status hdg_autotune(hdg_sys* sys, const double* U, const double* Lam, int32_t* grid_out, void* stream);
 
+/* ---- Adaptation decisions (Sec. 4) ----
+ * Per element, into DEVICE arrays [n_elem] (either output may be NULL):
+ *   sensor[K] = S_K = |w - w*|^2_K / |w|^2_K (Sec. 4.4): w* the L2 projection
+ *     of the element's conserved state onto degree p_K - 1; the inner product
+ *     of the vector w sums its four components; with the orthonormal
+ *     hierarchical basis this is the share of the squared degree-p_K
+ *     coefficients;
+ *   eta2[K] = eta_K^2, eta_K = |N_h(x_h; q~, w~, 0)|_K| (Sec. 4.1): the interior
+ *     residual rows of K (res_u of the last hdg_condense of sys) weighted by the
+ *     adjoint's interior coefficients Uadj [u_len], in the discrete space itself
+ *     (the paper evaluates it in an enriched space, which this library does not
+ *     build).  Needs Uadj (else eta2 is left alone).
+ * U and Uadj are DEVICE vectors [u_len]; enqueued on `stream`. */
+hdg_status hdg_adapt_indicators(hdg_sys* sys, const double* U, const double* Uadj, double* eta2, double* sensor,
+                                void* stream);
+
+/* Doerfler marking and the h/p choice (Sec. 4.3, 4.4) on DEVICE eta2, sensor
+ * [n]: the smallest set M with eta_M >= (1 - theta) eta_T (eta^2 summed),
+ * taken in the order eta descending, index ascending; the sums are exact
+ * integer sums of v_K = floor(eta_K^2 / max_K eta_K^2 * 2^bits), bits =
+ * 62 - ceil(log2(n + 1)), so the set does not depend on a summation order.
+ * code[K] (DEVICE int8 [n]) = 0 unmarked, 1 p-enrichment (marked and
+ * S_K < eps_s), 2 mesh refinement (marked, S_K >= eps_s); *n_marked (may be
+ * NULL) the size of M.  The paper's values: theta = 0.05, eps_s = 1e-6.
+ * Uses a stream-ordered temporary of 8 n bytes; synchronises `stream`. */
+hdg_status hdg_adapt_mark(hdg_ctx* ctx, int32_t n, const double* eta2, const double* sensor, double theta,
+                          double eps_s, int8_t* code, int32_t* n_marked, void* stream);
+
 /* Number of kernel launches the last hdg_condense + hdg_recover enqueued. */
 int32_t hdg_sys_launches(const hdg_sys* sys);
 

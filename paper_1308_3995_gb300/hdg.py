@@ -33,7 +33,8 @@ EXPORTS = ["hdg_create", "hdg_destroy", "hdg_last_error", "hdg_mesh_create", "hd
            "hdg_condense_noalloc", "hdg_sys_workspace_bytes", "hdg_sys_create_in",
            "hdg_step_host_async", "hdg_graph_create", "hdg_graph_launch", "hdg_solver_create",
            "hdg_solver_destroy", "hdg_trace_solve", "hdg_trace_matvec", "hdg_newton_update", "hdg_residual_norm",
-           "hdg_sys_set_cfl", "hdg_cfl_law", "hdg_autotune", "hdg_trace_solve_ex", "hdg_adjoint_condense"]
+           "hdg_sys_set_cfl", "hdg_cfl_law", "hdg_autotune", "hdg_trace_solve_ex", "hdg_adjoint_condense",
+           "hdg_adapt_indicators", "hdg_adapt_mark"]
 
 
 class HdgError(RuntimeError):
@@ -122,6 +123,9 @@ def lib(build: bool = True):
         L.hdg_trace_solve_ex.argtypes = [_vp, _vp, ctypes.c_int32, _vp, ctypes.c_double, ctypes.c_int32,
                                          ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(ctypes.c_double), _vp]
         L.hdg_adjoint_condense.argtypes = [_vp, _vp, _vp, _vp, _vp, _vp]
+        L.hdg_adapt_indicators.argtypes = [_vp, _vp, _vp, _vp, _vp, _vp]
+        L.hdg_adapt_mark.argtypes = [_vp, ctypes.c_int32, _vp, _vp, ctypes.c_double, ctypes.c_double, _vp,
+                                     ctypes.POINTER(ctypes.c_int32), _vp]
         L.hdg_newton_update.argtypes = [_vp, _vp, _vp, _vp, _vp, _vp]
         L.hdg_residual_norm.argtypes = [_vp, ctypes.POINTER(ctypes.c_double), _vp]
         L.hdg_sys_set_cfl.argtypes = [_vp, ctypes.c_double]
@@ -158,6 +162,14 @@ def cfl_law(n: int, c0: float = 1e6, c1: float = 1e3, n0: int = 4, cfl_prev: flo
     """hdg_cfl_law: CFL^n of Eq. (cfl) (host only)."""
     return float(lib().hdg_cfl_law(int(n), float(c0), float(c1), int(n0), float(cfl_prev), float(res_prev),
                                    float(res_cur)))
+
+
+def adapt_mark(ctx: "Context", eta2, sensor, code, theta=0.05, eps_s=1e-6, stream=None) -> int:
+    """hdg_adapt_mark: Doerfler marking and h/p choice into the int8 device tensor `code`; returns |M|."""
+    nm = ctypes.c_int32()
+    _check(lib().hdg_adapt_mark(ctx.h, int(eta2.numel()), _ptr(eta2), _ptr(sensor), float(theta), float(eps_s),
+                                _ptr(code), ctypes.byref(nm), _stream(stream)), ctx.h)
+    return int(nm.value)
 
 
 class Solver:
@@ -369,6 +381,12 @@ class System:
         """hdg_adjoint_condense: adjoint local solves into this system's X, E~ into its E."""
         _check(lib().hdg_adjoint_condense(self.h, primal.h, _ptr(U), _ptr(Lam), _ptr(Ftilde), _stream(stream)),
                self.ctx.h)
+
+    def adapt_indicators(self, U, Uadj, eta2, sensor, stream=None):
+        """hdg_adapt_indicators: eta_K^2 (needs Uadj) and the smoothness sensor S_K per element."""
+        _check(lib().hdg_adapt_indicators(self.h, _ptr(U), _ptr(Uadj) if Uadj is not None else None,
+                                          _ptr(eta2) if eta2 is not None else None,
+                                          _ptr(sensor) if sensor is not None else None, _stream(stream)), self.ctx.h)
 
     def set_cfl(self, cfl: float):
         """hdg_sys_set_cfl: pseudo-time CFL number of the following condensations."""
