@@ -327,6 +327,59 @@ def solve_section(ctx, wl, dev, flush, stream, cfl=10.0, rtol=1e-10, reps=3):
     return out
 
 
+def adjoint_section(ctx, wl, dev, flush, stream, cfl=10.0, rtol=1e-10, reps=3):
+    """Hybridized adjoint (Sec. 4.2) and the adaptation decisions (Sec. 4.1, 4.3, 4.4) on the
+    workload: primal condensation, adjoint local solves + E~, GMRES on K^T, adjoint reconstruction,
+    indicators, Doerfler marking (theta 0.05) and the h/p choice (eps_s 1e-6).  The target
+    functional is the integral of density (F~ on each element's density constant mode)."""
+    import torch
+
+    from paper_1308_3995_gb300 import hdg
+    m = Measured(ctx, wl, hdg.HDG_FP64, dev, flush)
+    m.sys.set_cfl(cfl)
+    adj = hdg.System(ctx, m.mesh, hdg.Params(model=wl.model, mach=wl.mach, alpha=wl.alpha, reynolds=wl.reynolds,
+                                              prandtl=wl.prandtl, cfl=cfl))
+    nb = (wl.p + 1) * (wl.p + 2) // 2
+    Ft = torch.zeros(m.mesh.u_len, dtype=torch.float64, device=dev)
+    Ft.view(-1, 4 * nb)[:, 0] = 1.0
+    solver = hdg.Solver(m.sys, restart=30)
+    lt = torch.zeros(m.mesh.lam_len, dtype=torch.float64, device=dev)
+    ua = torch.zeros(m.mesh.u_len, dtype=torch.float64, device=dev)
+    eta2 = torch.empty(m.mesh.n_elem, dtype=torch.float64, device=dev)
+    sens = torch.empty_like(eta2)
+    code = torch.empty(m.mesh.n_elem, dtype=torch.int8, device=dev)
+    rows = []
+    for r in range(reps + 1):
+        flush.fill_(1.0)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        m.sys.condense(m.Ut, m.Lt, stream)
+        adj.adjoint_condense(m.sys, m.Ut, m.Lt, Ft, stream)
+        torch.cuda.synchronize()
+        t1 = time.perf_counter()
+        lt.zero_()
+        it, rel = solver.solve(lt, rtol=rtol, max_iter=3000, rhs=adj.views()["E"], transpose=True, stream=stream)
+        adj.recover(lt, ua, stream)
+        torch.cuda.synchronize()
+        t2 = time.perf_counter()
+        m.sys.adapt_indicators(m.Ut, ua, eta2, sens, stream)
+        nm = hdg.adapt_mark(ctx, eta2, sens, code, theta=0.05, eps_s=1e-6, stream=stream)
+        torch.cuda.synchronize()
+        t3 = time.perf_counter()
+        if r > 0:
+            rows.append((t1 - t0, t2 - t1, t3 - t2, it, rel, nm))
+    c = code.cpu().numpy()
+    med = lambda k: 1e3 * statistics.median(x[k] for x in rows)
+    out = {"workload": wl.name, "cfl": cfl, "functional": "integral of density",
+           "primal_and_adjoint_condense_ms": med(0), "adjoint_trace_solve_and_recover_ms": med(1),
+           "indicators_and_marking_ms": med(2), "gmres_iterations": rows[-1][3], "rel_residual": rows[-1][4],
+           "marked": rows[-1][5], "p_enrichment": int((c == 1).sum()), "h_refinement": int((c == 2).sum())}
+    solver.close()
+    adj.close()
+    m.close()
+    return out
+
+
 def serving_section(ctx, n_requests, seed, max_elems, rates=(0.7,), arena_gb=24):
     """Poisson stream through the continuous-batching loop (float-float, 8 slots)
     against the plain loop (binary64, one request at a time), at each load level
@@ -378,8 +431,9 @@ def run_ours(args, wl, ws, rank, local):
     stream = torch.cuda.current_stream()
     if args.solve_only:
         if rank == 0:
-            print(json.dumps({"metric": "Newton step with GPU trace solve",
-                              "solve": solve_section(ctx, wl, dev, flush, stream)}), flush=True)
+            print(json.dumps({"metric": "Newton step with GPU trace solve; adjoint and adaptation",
+                              "solve": solve_section(ctx, wl, dev, flush, stream),
+                              "adjoint": adjoint_section(ctx, wl, dev, flush, stream)}), flush=True)
         return 0
     if args.serving_only:
         line = {"metric": "serving: p50/p99 latency and elements/s, continuous batching (float-float) vs plain FP64",
@@ -472,6 +526,7 @@ def run_ours(args, wl, ws, rank, local):
                 ms.close()
         line["euler_p3_262k_shock"] = shock
         line["newton_step_with_trace_solve"] = solve_section(ctx, wl, dev, flush, stream)
+        line["adjoint_and_adaptation"] = adjoint_section(ctx, wl, dev, flush, stream)
         if args.serving_requests > 0:
             line["serving"] = serving_section(ctx, args.serving_requests, 77, args.serving_max_elems)
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
