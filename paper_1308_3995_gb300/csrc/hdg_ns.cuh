@@ -464,7 +464,13 @@ __global__ void __launch_bounds__(kNsThreads) k_condense_ns(DevMesh m, DevSys s,
     __syncthreads();
 
     // ---------------- q elimination, one (k', g) block column at a time ----------------
+    // Every product below runs over its (row, column) pairs flattened across the
+    // CTA.  Rows of field 0 of A_wq and C_q vanish (the mass flux has no viscous
+    // part), so they are skipped unless shock capturing adds eps D_k there.  The
+    // trace columns of field g are enumerated directly (nt / 4 of them: face a,
+    // mode l -> column toff[a] + g nk_a + l) instead of being filtered.
     const T ic = g_ic;
+    const int nq4 = nt / 4;  // trace columns per field
     for (int kk = 0; kk < 8; ++kk) {
       const int kd = kk >> 2, gq = kk & 3;
       // Z'_f[i][q] = sum_r dphi_i/dxi_r Ahat^wq_r,f,kk (rows f = 1..3)
@@ -474,84 +480,100 @@ __global__ void __launch_bounds__(kNsThreads) k_condense_ns(DevMesh m, DevSys s,
                        A::mul(vge[q * NP + i], sAwq[(24 + f1 * 8 + kk) * NQ + q]));
       }
       // C_q block column: rows (a, f, l), C_q = <psi_l, (-n.df_v/dq)_f,kk phi_j>_e
-      for (int r = ty; r < nt; r += NW) {
+      for (int t = tid; t < nt * NP; t += NT) {
+        const int r = t / NP, jj = t - r * NP;
         const int a = g_cf[r], f = g_cg[r], l = g_cl[r], nk = g_nk[a];
-        const T* phe = tab + to.edge_phi[P][g_pe[a]][a][g_fl[a]];
-        const T* ps = tab + to.edge_psi[g_pe[a]];
-        for (int j = tx; j < NP; j += 32) {
-          T acc = zero;
-          if (f > 0)
-            for (int q = 0; q < nk + 1; ++q)
-              A::madd(acc, A::mul(ps[q * nk + l], sAq[(a * kNsPt + q) * 24 + (f - 1) * 8 + kk]), phe[q * NP + j]);
-          sCc[r * NP + j] = A::norm(acc);
-        }
-      }
-      __syncthreads();
-      // A_wq block column: volume (Z' phi^T) + face <phi_i, (-n.df_v/dq) phi_j>_dK; row 0 is zero
-      for (int t = tid; t < NW4 * NP; t += NT) {
-        const int r = t / NP, j = t - r * NP, f = r / NP, i = r - f * NP;
         T acc = zero;
         if (f > 0) {
+          const T* phe = tab + to.edge_phi[P][g_pe[a]][a][g_fl[a]];
+          const T* ps = tab + to.edge_psi[g_pe[a]];
+          for (int q = 0; q < nk + 1; ++q)
+            A::madd(acc, A::mul(ps[q * nk + l], sAq[(a * kNsPt + q) * 24 + (f - 1) * 8 + kk]), phe[q * NP + jj]);
+        }
+        sCc[t] = A::norm(acc);
+      }
+      __syncthreads();
+      // A_wq block column: volume (Z' phi^T) + face <phi_i, (-n.df_v/dq) phi_j>_dK; rows of field 0
+      // are zero (plus eps D_k on field gq under shock capturing)
+      const int r0 = (shock && gq == 0) ? 0 : NP;  // first row that can be nonzero
+      for (int t = tid; t < NW4 * NP; t += NT) {
+        const int r = t / NP, jj = t - r * NP, f = r / NP, i = r - f * NP;
+        T acc0 = zero, acc1 = zero;
+        if (f > 0) {
           const T* z = sZ + ((f - 1) * NP + i) * NQ;
-          for (int q = 0; q < NQ; ++q) A::madd(acc, z[q], vphi[q * NP + j]);
+          for (int q = 0; q < NQ; ++q) A::madd(acc0, z[q], vphi[q * NP + jj]);
           for (int a = 0; a < 3; ++a) {
             const T* phe = tab + to.edge_phi[P][g_pe[a]][a][g_fl[a]];
             for (int q = 0; q < g_pe[a] + 2; ++q)
-              A::madd(acc, A::mul(phe[q * NP + i], sAq[(a * kNsPt + q) * 24 + (f - 1) * 8 + kk]), phe[q * NP + j]);
+              A::madd(acc1, A::mul(phe[q * NP + i], sAq[(a * kNsPt + q) * 24 + (f - 1) * 8 + kk]), phe[q * NP + jj]);
           }
         }
-        if (shock && f == gq) A::madd(acc, eps, sDk[kd * NP * NP + i * NP + j]);  // frozen shock capturing
+        T acc = A::add(A::norm(acc0), A::norm(acc1));
+        if (shock && f == gq) A::madd(acc, eps, sDk[kd * NP * NP + i * NP + jj]);  // frozen shock capturing
         sBc[t] = A::norm(acc);
       }
       __syncthreads();
       const T* Dk = sDk + kd * NP * NP;
       // (i) A'[(f,i),(g,j)] -= 1/det sum_i' A_wq[(f,i),i'] D_k'[i'][j]
-      for (int t = tid; t < NW4 * NP; t += NT) {
-        const int r = t / NP, j = t - r * NP;
+      for (int t = r0 * NP + tid; t < NW4 * NP; t += NT) {
+        const int r = t / NP, jj = t - r * NP;
         T acc = zero;
-        for (int i2 = 0; i2 < NP; ++i2) A::madd(acc, sBc[r * NP + i2], Dk[i2 * NP + j]);
-        T* p = &sA[r * LDA + gq * NP + j];
+        for (int i2 = 0; i2 < NP; ++i2) A::madd(acc, sBc[r * NP + i2], Dk[i2 * NP + jj]);
+        T* p = &sA[r * LDA + gq * NP + jj];
         A::msub(*p, ic, A::norm(acc));
         *p = A::norm(*p);
       }
-      // (ii)+(iii) R'_w -= 1/det A_wq R_q, with B_q = -n_k' |e_a| <phi_i', psi_l> on columns of field g
-      for (int r = ty; r < NW4; r += NW) {
-        for (int c = tx; c < nr1; c += 32) {
+      // (ii)+(iii) R'_w -= 1/det A_wq R_q on the columns of field g and the F column,
+      // B_q = -n_k' |e_a| <phi_i', psi_l>
+      {
+        const int ncol = nq4 + 1;
+        for (int t = tid; t < (NW4 - r0) * ncol; t += NT) {
+          const int r = r0 + t / ncol, cc = t - (t / ncol) * ncol;
           T acc = zero;
-          if (c == nt) {
+          int c;
+          if (cc == nq4) {
+            c = nt;
             for (int i2 = 0; i2 < NP; ++i2) A::msub(acc, sBc[r * NP + i2], sNu[kk * NP + i2]);  // F_q = -N_q
-          } else if (g_cg[c] == gq) {
-            const int a = g_cf[c], l = g_cl[c];
+          } else {
+            const int a = (cc < g_nk[0]) ? 0 : (cc < g_nk[0] + g_nk[1] ? 1 : 2);
+            const int l = cc - (a > 0 ? g_nk[0] : 0) - (a > 1 ? g_nk[1] : 0);
+            c = g_toff[a] + gq * g_nk[a] + l;
             const T* me = tab + to.edge_cross[P][g_pe[a]][a][g_fl[a]];
             T s2 = zero;
             for (int i2 = 0; i2 < NP; ++i2) A::madd(s2, sBc[r * NP + i2], me[l * NP + i2]);
             acc = A::neg(A::mul(A::mul(g_n[a][kd], g_len[a]), A::norm(s2)));   // A_wq B_q
-          } else {
-            continue;
           }
           T* p = &sR[r * ldr + c];
           A::msub(*p, ic, A::norm(acc));
           *p = A::norm(*p);
         }
       }
-      // (iv) C' -= 1/det C_q A_qw;  (v)+(vi) S0 -= 1/det C_q B_q, E0 -= 1/det C_q F_q
-      for (int r = ty; r < nt; r += NW) {
-        for (int c = tx; c < NP; c += 32) {
+      // (iv) C' -= 1/det C_q A_qw
+      for (int t = tid; t < nt * NP; t += NT) {
+        const int r = t / NP, cc = t - r * NP;
+        if (g_cg[r] == 0) continue;  // C_q row of field 0 is zero
+        T acc = zero;
+        for (int i2 = 0; i2 < NP; ++i2) A::madd(acc, sCc[r * NP + i2], Dk[i2 * NP + cc]);
+        T* p = &sCp[r * ldc + gq * NP + cc];
+        A::msub(*p, ic, A::norm(acc));
+        *p = A::norm(*p);
+      }
+      // (v)+(vi) S0 -= 1/det C_q B_q on the columns of field g, E0 -= 1/det C_q F_q
+      {
+        const int ncol = nq4 + 1;
+        for (int t = tid; t < nt * ncol; t += NT) {
+          const int r = t / ncol, cc = t - r * ncol;
+          if (g_cg[r] == 0) continue;  // C_q row of field 0 is zero
           T acc = zero;
-          for (int i2 = 0; i2 < NP; ++i2) A::madd(acc, sCc[r * NP + i2], Dk[i2 * NP + c]);
-          T* p = &sCp[r * ldc + gq * NP + c];
-          A::msub(*p, ic, A::norm(acc));
-          *p = A::norm(*p);
-        }
-        for (int c = tx; c < nr1; c += 32) {
-          T acc = zero;
-          if (c == nt) {
+          if (cc == nq4) {
             for (int i2 = 0; i2 < NP; ++i2) A::msub(acc, sCc[r * NP + i2], sNu[kk * NP + i2]);
             T* p = &sE[r];
             A::msub(*p, ic, A::norm(acc));
             *p = A::norm(*p);
-          } else if (g_cg[c] == gq) {
-            const int a = g_cf[c], l = g_cl[c];
+          } else {
+            const int a = (cc < g_nk[0]) ? 0 : (cc < g_nk[0] + g_nk[1] ? 1 : 2);
+            const int l = cc - (a > 0 ? g_nk[0] : 0) - (a > 1 ? g_nk[1] : 0);
+            const int c = g_toff[a] + gq * g_nk[a] + l;
             const T* me = tab + to.edge_cross[P][g_pe[a]][a][g_fl[a]];
             T s2 = zero;
             for (int i2 = 0; i2 < NP; ++i2) A::madd(s2, sCc[r * NP + i2], me[l * NP + i2]);
