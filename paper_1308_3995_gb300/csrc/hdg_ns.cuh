@@ -254,7 +254,9 @@ __global__ void __launch_bounds__(kNsThreads) k_condense_ns(DevMesh m, DevSys s,
       }
     }
     // ---------------- a3: pointwise data at the face points ----------------
-    for (int t = tid; t < 3 * kNsPt; t += NT) {
+    // (on warps 2 and 3, while warps 0 and 1 work on the volume points above: NQ <= 64)
+    static_assert(NQ <= 64 && 64 + 3 * kNsPt <= NT, "volume and face point threads must not overlap");
+    for (int t = tid - 64; t >= 0 && t < 3 * kNsPt; t += NT) {
       const int a = t / kNsPt, g = t - a * kNsPt;
       const int pe = g_pe[a], nk = pe + 1;
       if (g < pe + 2) {
