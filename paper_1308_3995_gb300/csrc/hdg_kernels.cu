@@ -360,29 +360,31 @@ __global__ void __launch_bounds__(kCondThreads, 4) k_condense_euler(
     }
     __syncthreads();
     const bool adjoint = ph.adjoint != 0;
-    // B = d N_w / d Lambda: rows (f,i) over warps, columns (face a; g, l) over lanes
-    for (int r = ty; r < (adjoint ? 0 : N); r += NW) {
+    // B = d N_w / d Lambda: the (row (f,i), column (face a; g, l)) pairs flattened over the CTA
+    for (int t = tid; t < (adjoint ? 0 : N * nt); t += NT) {
+      const int r = t / nt, c = t - r * nt;
       const int f = r / NP, i = r - f * NP;
-      for (int c = tx; c < nt; c += 32) {
-        const int a = g_cf[c], g = g_cg[c], l = g_cl[c], nk = g_nk[a];
-        const T* phe = tab + to.edge_phi[P][g_pe[a]][a][g_fl[a]];
-        T acc = zero;
-        for (int q = 0; q < nk + 1; ++q) A::madd(acc, phe[q * NP + i], sW[((a * kPtSlots + q) * 16 + f * 4 + g) * 5 + l]);
-        sR[r * ldr + c] = A::norm(acc);
-      }
+      const int a = g_cf[c], g = g_cg[c], l = g_cl[c], nk = g_nk[a];
+      const T* phe = tab + to.edge_phi[P][g_pe[a]][a][g_fl[a]];
+      T acc = zero;
+      for (int q = 0; q < nk + 1; ++q) A::madd(acc, phe[q * NP + i], sW[((a * kPtSlots + q) * 16 + f * 4 + g) * 5 + l]);
+      sR[r * ldr + c] = A::norm(acc);
     }
-    // D_a = d N_lambda,a / d Lambda_a (block diagonal in faces): rows over warps, columns over lanes
-    for (int a = 0; a < (adjoint ? 0 : 3); ++a) {
-      const int nk = g_nk[a], m4 = 4 * nk, o = g_toff[a];
-      const T* ps = tab + to.edge_psi[g_pe[a]];
-      for (int r = ty; r < m4; r += NW) {
-        const int f = g_cg[o + r], k = g_cl[o + r];
-        for (int c = tx; c < m4; c += 32) {
-          const int g = g_cg[o + c], l = g_cl[o + c];
-          T acc = zero;
-          for (int q = 0; q < nk + 1; ++q) A::madd(acc, ps[q * nk + k], sW[((a * kPtSlots + q) * 16 + f * 4 + g) * 5 + l]);
-          sD[a * DS + r * m4 + c] = A::norm(acc);
-        }
+    // D_a = d N_lambda,a / d Lambda_a (block diagonal in faces): the entries of the three
+    // diagonal blocks flattened over the CTA
+    {
+      const int s1 = 16 * g_nk[0] * g_nk[0], s2 = s1 + 16 * g_nk[1] * g_nk[1];
+      const int tot = s2 + 16 * g_nk[2] * g_nk[2];
+      for (int t = tid; t < (adjoint ? 0 : tot); t += NT) {
+        const int a = (t >= s2) ? 2 : (t >= s1 ? 1 : 0);
+        const int nk = g_nk[a], m4 = 4 * nk, o = g_toff[a];
+        const int tl = t - (a == 0 ? 0 : (a == 1 ? s1 : s2));
+        const int r = tl / m4, c = tl - r * m4;
+        const int f = g_cg[o + r], k = g_cl[o + r], g = g_cg[o + c], l = g_cl[o + c];
+        const T* ps = tab + to.edge_psi[g_pe[a]];
+        T acc = zero;
+        for (int q = 0; q < nk + 1; ++q) A::madd(acc, ps[q * nk + k], sW[((a * kPtSlots + q) * 16 + f * 4 + g) * 5 + l]);
+        sD[a * DS + r * m4 + c] = A::norm(acc);
       }
     }
     // C_a = alpha |e_a| <psi_k, phi_j> delta_fg, kept as the scalar edge matrix
@@ -497,28 +499,50 @@ __global__ void __launch_bounds__(kCondThreads, 4) k_condense_euler(
     }
 
     // ---------------- a6/a7: Schur complement, E_K, assembly ----------------
-    // rows (face a; f, k) over warps, columns (face b; g, l | E) over lanes
-    for (int r = ty; r < nt; r += NW) {
-      const int a = g_cf[r], f = g_cg[r], k = g_cl[r], rl = r - g_toff[a];
-      const T* me = sMe + (a * 5 + k) * NP;
-      for (int c = tx; c < nr1; c += 32) {
-        if (c == nt) {
-          T v = sEh[r];
+    // the (row, column) pairs -- rows (face a; f, k), columns (face b; g, l | E) -- flattened
+    // over the CTA, two per thread (independent chains, full warps)
+    {
+      const int cnt = nt * nr1;
+      for (int e0 = tid; e0 < cnt; e0 += 2 * NT) {
+        T v[2];
+        int rr[2], cc[2];
+        const bool two = e0 + NT < cnt;
 #pragma unroll
-          for (int j = 0; j < NP; ++j) A::msub(v, me[j], sR[(f * NP + j) * ldr + c]);
-          v = A::norm(v);
-          sEh[r] = v;
-          bad |= A::bad(v);
-        } else {
-          const int b = g_cf[c];
-          const int cl = c - g_toff[b], m4b = 4 * g_nk[b];
-          T v = (b == a) ? sD[a * DS + rl * m4b + cl] : zero;
+        for (int u = 0; u < 2; ++u) {
+          const int e = (u == 1 && two) ? e0 + NT : e0;
+          const int r = e / nr1, c = e - r * nr1;
+          rr[u] = r;
+          cc[u] = c;
+          const int a = g_cf[r], rl = r - g_toff[a];
+          if (c == nt) {
+            v[u] = sEh[r];
+          } else {
+            const int b = g_cf[c];
+            v[u] = (b == a) ? sD[a * DS + rl * 4 * g_nk[b] + c - g_toff[b]] : zero;
+          }
+        }
+        const T* me0 = sMe + (g_cf[rr[0]] * 5 + g_cl[rr[0]]) * NP;
+        const T* me1 = sMe + (g_cf[rr[1]] * 5 + g_cl[rr[1]]) * NP;
+        const T* x0 = sR + g_cg[rr[0]] * NP * ldr + cc[0];
+        const T* x1 = sR + g_cg[rr[1]] * NP * ldr + cc[1];
 #pragma unroll
-          for (int j = 0; j < NP; ++j) A::msub(v, me[j], sR[(f * NP + j) * ldr + c]);
-          v = A::norm(v);
-          if (b == a) sD[a * DS + rl * m4b + cl] = v;
-          else s.K[m.kblk[9 * (size_t)K + 3 * a + b] + rl * m4b + cl] = A::to_d(v);
-          bad |= A::bad(v);
+        for (int jj = 0; jj < NP; ++jj) {
+          A::msub(v[0], me0[jj], x0[jj * ldr]);
+          A::msub(v[1], me1[jj], x1[jj * ldr]);
+        }
+#pragma unroll
+        for (int u = 0; u < 2; ++u) {
+          if (u == 1 && !two) break;
+          const int r = rr[u], c = cc[u], a = g_cf[r], rl = r - g_toff[a];
+          const T w = A::norm(v[u]);
+          bad |= A::bad(w);
+          if (c == nt) {
+            sEh[r] = w;
+          } else {
+            const int b = g_cf[c], cl = c - g_toff[b], m4b = 4 * g_nk[b];
+            if (b == a) sD[a * DS + rl * m4b + cl] = w;
+            else s.K[m.kblk[9 * (size_t)K + 3 * a + b] + rl * m4b + cl] = A::to_d(w);
+          }
         }
       }
     }
