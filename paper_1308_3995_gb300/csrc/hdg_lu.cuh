@@ -33,6 +33,7 @@ constexpr int kLuNB = 8;
 template <class T, int NROWS, int NT>
 __device__ __forceinline__ void lu_solve(T* sA, int lda, T* sR, int ldr, int nr1, int* s_pv, T* s_pinv, int* s_bad,
                                          int tid) {
+  static_assert(NROWS <= 64, "the pivot search holds at most two rows per lane");
   using A = Ar<T>;
   constexpr int NW = NT / 32;
   const int tx = tid & 31, ty = tid >> 5;
@@ -45,22 +46,28 @@ __device__ __forceinline__ void lu_solve(T* sA, int lda, T* sR, int ldr, int nr1
     // ---- 1. panel factorisation (warp pw) ----
     if (ty == pw) {
       for (int j = k0; j < kend; ++j) {
-        unsigned long long best = 0ull;
-        int bi = j;
-        for (int i = j + tx; i < NROWS; i += 32) {
-          const T v = A::norm(sA[i * lda + j]);
-          sA[i * lda + j] = v;
-          const unsigned long long kv = A::key(v);
-          if (kv > best) { best = kv; bi = i; }
+        // pivot search over rows j.. (at most two per lane): the largest |a| as an integer
+        // key, by two warp max-reductions (high, then low 32 bits), the first row on ties
+        // by ballots over the lanes' first, then second, rows
+        const int i1 = j + tx, i2 = j + tx + 32;
+        unsigned long long k1 = 0ull, k2 = 0ull;
+        if (i1 < NROWS) {
+          const T v = A::norm(sA[i1 * lda + j]);
+          sA[i1 * lda + j] = v;
+          k1 = A::key(v);
         }
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) {
-          const unsigned long long ob = __shfl_down_sync(0xffffffffu, best, o);
-          const int oi = __shfl_down_sync(0xffffffffu, bi, o);
-          if (ob > best || (ob == best && oi < bi)) { best = ob; bi = oi; }
+        if (i2 < NROWS) {
+          const T v = A::norm(sA[i2 * lda + j]);
+          sA[i2 * lda + j] = v;
+          k2 = A::key(v);
         }
-        best = __shfl_sync(0xffffffffu, best, 0);
-        bi = __shfl_sync(0xffffffffu, bi, 0);
+        const unsigned long long km = k1 > k2 ? k1 : k2;
+        const unsigned mhi = __reduce_max_sync(0xffffffffu, (unsigned)(km >> 32));
+        const unsigned mlo = __reduce_max_sync(0xffffffffu, (unsigned)(km >> 32) == mhi ? (unsigned)km : 0u);
+        const unsigned long long best = ((unsigned long long)mhi << 32) | mlo;
+        const unsigned b1 = __ballot_sync(0xffffffffu, i1 < NROWS && k1 == best);
+        const unsigned b2 = __ballot_sync(0xffffffffu, i2 < NROWS && k2 == best);
+        const int bi = b1 ? j + __ffs(b1) - 1 : j + 32 + __ffs(b2) - 1;
         __syncwarp();
         const T piv = sA[bi * lda + j];
         __syncwarp();
