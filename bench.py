@@ -154,7 +154,7 @@ def time_oracle_sample(wl, target_s: float = 12.0, max_elems: int | None = None)
     import oracle as O
     from paper_1308_3995_gb300 import inputs as G
     case = G.make_case(wl)
-    om = O.Mesh(case.mesh.elem_xy, case.mesh.elem_vid, case.elem_p, case.nfield)
+    om = O.Mesh(case.mesh.elem_xy, case.mesh.elem_vid, case.elem_p, case.nfield, case.mesh.elem_bc)
     U, Lam, dLam = G.case_state(case, om.face_vid, om.face_p)
     P = O.Params(model=wl.model, mach=wl.mach, alpha=wl.alpha, reynolds=wl.reynolds, prandtl=wl.prandtl)
     # calibrate on 32 elements, then size the sample to about target_s seconds

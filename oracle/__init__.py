@@ -40,7 +40,7 @@ class OrcParams(ctypes.Structure):
     _fields_ = [("model", ctypes.c_int32), ("reserved", ctypes.c_int32), ("gamma", ctypes.c_double),
                 ("prandtl", ctypes.c_double), ("reynolds", ctypes.c_double), ("mach", ctypes.c_double),
                 ("alpha", ctypes.c_double), ("cfl", ctypes.c_double), ("t_inf", ctypes.c_double),
-                ("sc_eps0", ctypes.c_double), ("sc_beta", ctypes.c_double)]
+                ("sc_eps0", ctypes.c_double), ("sc_beta", ctypes.c_double), ("aoa", ctypes.c_double)]
 
 
 _lib = None
@@ -62,7 +62,8 @@ def lib():
         L.orc_ns_viscous_flux.argtypes = [_c_double_p, _c_double_p, ctypes.POINTER(OrcParams), _c_double_p]
         L.orc_ns_viscous_flux.restype = None
         L.orc_mesh_create.argtypes = [ctypes.c_int, ctypes.c_int, _c_double_p, _c_i32_p,
-                                      ctypes.POINTER(ctypes.c_int8), ctypes.POINTER(ctypes.c_void_p)]
+                                      ctypes.POINTER(ctypes.c_int8), ctypes.POINTER(ctypes.c_int8),
+                                      ctypes.POINTER(ctypes.c_void_p)]
         L.orc_mesh_destroy.argtypes = [ctypes.c_void_p]
         L.orc_mesh_destroy.restype = None
         L.orc_mesh_sizes.argtypes = [ctypes.c_void_p, _c_i64_p]
@@ -85,6 +86,9 @@ def lib():
         L.orc_monolithic.argtypes = [ctypes.c_void_p, P, _c_double_p, _c_double_p, _c_double_p, _c_double_p,
                                      _c_double_p]
         L.orc_dense_solve.argtypes = [ctypes.c_int, _c_double_p, _c_double_p]
+        L.orc_boundary_state.argtypes = [ctypes.c_int, _c_double_p, ctypes.c_double, ctypes.c_double, P,
+                                         _c_double_p]
+        L.orc_boundary_state.restype = None
         L.orc_cfl_law.argtypes = [ctypes.c_int, ctypes.c_double, ctypes.c_double, ctypes.c_int, ctypes.c_double,
                                   ctypes.c_double, ctypes.c_double]
         L.orc_cfl_law.restype = ctypes.c_double
@@ -180,14 +184,23 @@ class Params:
     t_inf: float = 288.15
     sc_eps0: float = 0.0     # shock capturing off unless > 0 (paper's value: 0.2)
     sc_beta: float = 0.0
+    aoa: float = 0.0         # free-stream angle of attack [degrees] (far-field state)
 
     def c(self) -> OrcParams:
         return OrcParams(self.model, 0, self.gamma, self.prandtl, self.reynolds, self.mach, self.alpha,
-                         self.cfl, self.t_inf, self.sc_eps0, self.sc_beta)
+                         self.cfl, self.t_inf, self.sc_eps0, self.sc_beta, self.aoa)
 
     @property
     def nfield(self) -> int:
         return 12 if self.model == 1 else 4
+
+
+def boundary_state(kind, w, n, params) -> np.ndarray:
+    """Boundary state w_b(w) of Sec. 2.1: kind 1 slip wall, 2 far field (characteristic), normal n."""
+    wb = np.zeros(4)
+    P = params.c()
+    lib().orc_boundary_state(int(kind), _d(_f64(w)), float(n[0]), float(n[1]), ctypes.byref(P), _d(wb))
+    return wb
 
 
 def cfl_law(n, c0=1e6, c1=1e3, n0=4, cfl_prev=0.0, res_prev=1.0, res_cur=1.0) -> float:
@@ -209,15 +222,19 @@ def adapt_mark(eta2, sensor, theta=0.05, eps_s=1e-6):
 class Mesh:
     """Oracle mesh: faces, sides and the documented layouts of U, Lambda, X, K."""
 
-    def __init__(self, elem_xy, elem_vid, elem_p, nfield: int):
+    def __init__(self, elem_xy, elem_vid, elem_p, nfield: int, elem_bc=None):
         xy = _f64(elem_xy).reshape(-1, 6)
         vid = np.ascontiguousarray(elem_vid, dtype=np.int32).reshape(-1, 3)
         p = np.ascontiguousarray(elem_p, dtype=np.int8).reshape(-1)
         self.n_elem = int(p.size)
         self.nfield = nfield
+        bc = None if elem_bc is None else np.ascontiguousarray(elem_bc, dtype=np.int8).reshape(-1, 3)
+        self.elem_bc = bc
         h = ctypes.c_void_p()
         st = lib().orc_mesh_create(self.n_elem, nfield, _d(xy), _i32(vid),
-                                   p.ctypes.data_as(ctypes.POINTER(ctypes.c_int8)), ctypes.byref(h))
+                                   p.ctypes.data_as(ctypes.POINTER(ctypes.c_int8)),
+                                   bc.ctypes.data_as(ctypes.POINTER(ctypes.c_int8)) if bc is not None else None,
+                                   ctypes.byref(h))
         if st != 0:
             raise ValueError(f"oracle rejected the mesh (status {st})")
         self._h = h
@@ -253,7 +270,7 @@ class Mesh:
         return self.nfield * n_basis(int(self.elem_p[K]))
 
     def nt(self, K):
-        return int(sum(4 * (self.face_p[e] + 1) for e in self.elem_face[K]))
+        return int(sum(4 * (self.face_p[e] + 1) for e in self.elem_face[K] if e >= 0))
 
     def element_residual(self, params, K, U, Lam):
         n, nt = self.n(K), self.nt(K)
@@ -338,6 +355,8 @@ class Mesh:
             nr = 4 * (self.face_p[f] + 1)
             for b in range(5):
                 c = self.k_col[f, b]
+                if c < 0:
+                    continue      # unused slot next to a boundary face
                 nc = 4 * (self.face_p[c] + 1)
                 o = self.k_blkoff[5 * f + b]
                 Kd[self.lam_off[f]:self.lam_off[f] + nr, self.lam_off[c]:self.lam_off[c] + nc] = \

@@ -11,8 +11,9 @@
 //   * physics: Euler convective flux and ideal-gas pressure (Sec. 2.1), viscous
 //     flux, temperature, Newtonian stress and Sutherland viscosity (Sec. 2.2);
 //   * the HDG residual N_h of Eq. (hdg_ls1)-(hdg_cont) with the combined
-//     Lax-Friedrichs/LDG-type numerical flux of Sec. 3.2 (source s = 0,
-//     no boundary operator: meshes are periodic), optionally with the
+//     Lax-Friedrichs/LDG-type numerical flux of Sec. 3.2 (source s = 0), the
+//     Euler boundary operator of Sec. 3.2 on tagged boundary faces (slip wall
+//     and characteristic far field, boundary states of Sec. 2.1), optionally with the
 //     shock-capturing volume term of Sec. 3.2 (artificial viscosity eps_K from
 //     the L1 norm of the strong convective residual, effective size h_K / p_K);
 //   * the Newton matrix N'_h (Eq. linearsystem) as the exact complex-step
@@ -57,6 +58,7 @@ typedef struct {
   double t_inf;      // dimensional free-stream temperature [K] for Sutherland's C2
   double sc_eps0;    // shock capturing factor eps_0 (Sec. 3.2); <= 0: no shock capturing
   double sc_beta;    // exponent beta of the effective mesh size h_K / p_K
+  double aoa;        // free-stream angle of attack [degrees] (the far-field state of Sec. 2.1)
 } orc_params;
 }
 
@@ -310,7 +312,8 @@ struct OMesh {
   std::vector<double> xy;        // [ne][3][2]
   std::vector<int> vid, p;       // [ne][3], [ne]
   std::vector<int> face_lo, face_hi, face_el0, face_el1, face_lf0, face_lf1, face_p;
-  std::vector<int> elem_face;    // [ne][3]
+  std::vector<int> elem_face;    // [ne][3], -1 on a boundary face
+  std::vector<int> bc;           // [ne][3] boundary kind of local face (0 interior, 1 slip wall, 2 far field)
   std::vector<int64_t> u_off, lam_off, x_off, k_blkoff;
   std::vector<int> k_col;        // [nf][5]
   int64_t u_len = 0, lam_len = 0, x_len = 0, k_len = 0;
@@ -339,9 +342,10 @@ static void elem_geom(const OMesh& M, int K, Geom& g) {
   g.area = 0.5 * g.detJ;
 }
 
+static inline int face_len(const OMesh& M, int e) { return e < 0 ? 0 : 4 * (M.face_p[e] + 1); }
 static int elem_nt(const OMesh& M, int K) {
   int nt = 0;
-  for (int lf = 0; lf < 3; ++lf) nt += 4 * (M.face_p[M.elem_face[K * 3 + lf]] + 1);
+  for (int lf = 0; lf < 3; ++lf) nt += face_len(M, M.elem_face[K * 3 + lf]);
   return nt;
 }
 static int elem_n(const OMesh& M, int K) { return M.nfield * n_basis(M.p[K]); }
@@ -400,6 +404,66 @@ static double sc_epsilon(const OMesh& M, const orc_params& P, int K, const Geom&
   }
   const double hK = std::max(g.len[0], std::max(g.len[1], g.len[2]));
   return P.sc_eps0 * std::pow(hK / p, 2.0 - P.sc_beta) / g.area * integral;
+}
+
+// Boundary states of Sec. 2.1 (Euler), for the outward unit normal n:
+//   slip wall: w_b = (rho, m - (m . n) n, E), so that v_b . n = 0;
+//   far field (characteristic upwinding): with f_c'(w) . n = Q Lambda Q^{-1},
+//     w_b = Q (P+ Q^{-1} w + P- Q^{-1} w_inf), P+ / P- selecting the
+//     characteristics with eigenvalue >= 0 / < 0 (outgoing from the interior /
+//     incoming from the far field); equivalently w_b = w + Q P- Q^{-1}(w_inf - w).
+// Q holds the right eigenvectors of the normal flux Jacobian at w:
+//   (1, u - c n, H - c v_n), (1, u, v, |v|^2/2), (0, t, v_t), (1, u + c n, H + c v_n),
+// t = (-n_y, n_x), eigenvalues v_n - c, v_n, v_n, v_n + c.  The upwinding
+// decision uses the real part (it is not differentiated).
+static double re(double x) { return x; }
+static double re(const cplx& x) { return x.real(); }
+template <class T>
+static void boundary_state(int kind, const T* w, double nx, double ny, const orc_params& P, T* wb) {
+  if (kind == 1) {
+    T mn = w[1] * nx + w[2] * ny;
+    wb[0] = w[0]; wb[1] = w[1] - mn * nx; wb[2] = w[2] - mn * ny; wb[3] = w[3];
+    return;
+  }
+  const double gam = P.gamma, a = P.aoa * 3.14159265358979323846 / 180.0;
+  const double ui = P.mach * std::cos(a), vi = P.mach * std::sin(a), pi = 1.0 / gam;
+  const double winf[4] = {1.0, ui, vi, pi / (gam - 1.0) + 0.5 * (ui * ui + vi * vi)};
+  T rho = w[0], u = w[1] / rho, v = w[2] / rho;
+  T p = (gam - 1.0) * (w[3] - 0.5 * rho * (u * u + v * v));
+  T c = std::sqrt(gam * p / rho), H = (w[3] + p) / rho;
+  T vn = u * nx + v * ny, vt = -u * ny + v * nx;
+  T Q[4][4] = {{1.0, 1.0, 0.0, 1.0},
+               {u - c * nx, u, -ny, u + c * nx},
+               {v - c * ny, v, nx, v + c * ny},
+               {H - c * vn, 0.5 * (u * u + v * v), vt, H + c * vn}};
+  const double lam[4] = {re(vn - c), re(vn), re(vn), re(vn + c)};
+  // y = Q^{-1} (w_inf - w): Gaussian elimination with partial pivoting (by real part)
+  T A[4][5];
+  for (int i = 0; i < 4; ++i) {
+    for (int j = 0; j < 4; ++j) A[i][j] = Q[i][j];
+    A[i][4] = winf[i] - w[i];
+  }
+  for (int k = 0; k < 4; ++k) {
+    int pv = k;
+    for (int i = k + 1; i < 4; ++i)
+      if (std::fabs(re(A[i][k])) > std::fabs(re(A[pv][k]))) pv = i;
+    for (int j = 0; j < 5; ++j) std::swap(A[k][j], A[pv][j]);
+    for (int i = k + 1; i < 4; ++i) {
+      T f = A[i][k] / A[k][k];
+      for (int j = k; j < 5; ++j) A[i][j] -= f * A[k][j];
+    }
+  }
+  T y[4];
+  for (int i = 3; i >= 0; --i) {
+    T sacc = A[i][4];
+    for (int j = i + 1; j < 4; ++j) sacc -= A[i][j] * y[j];
+    y[i] = sacc / A[i][i];
+  }
+  for (int i = 0; i < 4; ++i) {
+    wb[i] = w[i];
+    for (int j = 0; j < 4; ++j)
+      if (lam[j] < 0.0) wb[i] += Q[i][j] * y[j];
+  }
 }
 
 // eps is the element's shock-capturing viscosity (0: none), a constant here.
@@ -472,6 +536,25 @@ static void element_residual(const OMesh& M, const orc_params& P, int K, const G
   int loff = 0;
   for (int lf = 0; lf < 3; ++lf) {
     int e = M.elem_face[K * 3 + lf];
+    if (e < 0) {  // boundary operator of Sec. 3.2 (Euler): <phi, f_c(w_b(w)) . n>, no lambda
+      const EdgeTab& Eb = g_edge[p][p];
+      const int fl = elem_flip(M, K, lf);
+      const double nx = g.nrm[lf][0], ny = g.nrm[lf][1];
+      for (int gq = 0; gq < Eb.ne; ++gq) {
+        const double we = Eb.w[gq] * g.len[lf];
+        const double* phi = &Eb.phi[lf][fl][gq * np];
+        T w[4], wb[4], fc[2][4];
+        for (int f = 0; f < 4; ++f) {
+          w[f] = 0.0;
+          for (int j = 0; j < np; ++j) w[f] += U[woff + f * np + j] * phi[j];
+        }
+        boundary_state(M.bc[K * 3 + lf], w, nx, ny, P, wb);
+        euler_flux(wb, P.gamma, fc);
+        for (int f = 0; f < 4; ++f)
+          for (int j = 0; j < np; ++j) Nu[woff + f * np + j] += we * phi[j] * (nx * fc[0][f] + ny * fc[1][f]);
+      }
+      continue;
+    }
     int pe = M.face_p[e], nk = pe + 1;
     int fl = elem_flip(M, K, lf);
     const EdgeTab& Et = g_edge[p][pe];
@@ -619,7 +702,8 @@ static void gather_trace(const OMesh& M, int K, const double* Lam, std::vector<d
   L.clear();
   for (int lf = 0; lf < 3; ++lf) {
     int e = M.elem_face[K * 3 + lf];
-    int len = 4 * (M.face_p[e] + 1);
+    if (e < 0) continue;  // boundary face: no trace unknowns
+    int len = face_len(M, e);
     for (int r = 0; r < len; ++r) L.push_back(Lam[M.lam_off[e] + r]);
   }
 }
@@ -714,8 +798,10 @@ void orc_ns_viscous_flux(const double* w, const double* q, const orc_params* P, 
 
 // Build the mesh.  Returns 0 ok, 2 bad input (non-positive det J, p out of
 // range, a face not shared by exactly two elements, two elements sharing two faces).
+// elem_bc (may be null: every face interior) [n_elem][3]: 0 interior, 1 slip
+// wall, 2 far field; boundary faces carry no trace unknowns (Euler only).
 int orc_mesh_create(int n_elem, int nfield, const double* elem_xy, const int32_t* elem_vid,
-                    const int8_t* elem_p, void** out) {
+                    const int8_t* elem_p, const int8_t* elem_bc, void** out) {
   ensure_tables();
   if (n_elem < 1 || (nfield != 4 && nfield != 12)) return 2;
   OMesh* M = new OMesh();
@@ -723,6 +809,11 @@ int orc_mesh_create(int n_elem, int nfield, const double* elem_xy, const int32_t
   M->xy.assign(elem_xy, elem_xy + 6 * n_elem);
   M->vid.assign(elem_vid, elem_vid + 3 * n_elem);
   M->p.resize(n_elem);
+  M->bc.assign(3 * n_elem, 0);
+  for (int t = 0; elem_bc && t < 3 * n_elem; ++t) {
+    M->bc[t] = elem_bc[t];
+    if (M->bc[t] < 0 || M->bc[t] > 2 || (M->bc[t] != 0 && nfield != 4)) { delete M; return 2; }
+  }
   for (int K = 0; K < n_elem; ++K) {
     M->p[K] = elem_p[K];
     Geom g;
@@ -733,6 +824,7 @@ int orc_mesh_create(int n_elem, int nfield, const double* elem_xy, const int32_t
   std::vector<Ent> ents;
   for (int K = 0; K < n_elem; ++K)
     for (int lf = 0; lf < 3; ++lf) {
+      if (M->bc[K * 3 + lf]) continue;  // boundary face: no partner, no trace
       int a = M->vid[K * 3 + lf], b = M->vid[K * 3 + (lf + 1) % 3];
       ents.push_back({std::min(a, b), std::max(a, b), K, lf});
     }
@@ -778,14 +870,16 @@ int orc_mesh_create(int n_elem, int nfield, const double* elem_xy, const int32_t
       int K = s ? M->face_el1[f] : M->face_el0[f];
       for (int lf = 0; lf < 3; ++lf) {
         int e = M->elem_face[K * 3 + lf];
-        if (e != f) cols.push_back(e);
+        if (e != f && e >= 0) cols.push_back(e);
       }
     }
     std::sort(cols.begin(), cols.end());
     if (std::adjacent_find(cols.begin(), cols.end()) != cols.end()) { delete M; return 2; }
+    // columns ascending, then unused slots (-1, empty blocks) next to boundary faces
     for (int b = 0; b < 5; ++b) {
-      M->k_col[5 * f + b] = cols[b];
-      int64_t sz = (int64_t)(4 * (M->face_p[f] + 1)) * (4 * (M->face_p[cols[b]] + 1));
+      const int cb = b < (int)cols.size() ? cols[b] : -1;
+      M->k_col[5 * f + b] = cb;
+      int64_t sz = (int64_t)(4 * (M->face_p[f] + 1)) * face_len(*M, cb);
       M->k_blkoff[5 * f + b + 1] = M->k_blkoff[5 * f + b] + sz;
     }
   }
@@ -862,14 +956,16 @@ static void scatter_element(const OMesh& M, int K, const std::vector<double>& s,
   const int nt = elem_nt(M, K);
   int roff = 0;
   for (int a = 0; a < 3; ++a) {
-    int ea = M.elem_face[K * 3 + a], na = 4 * (M.face_p[ea] + 1);
+    int ea = M.elem_face[K * 3 + a], na = face_len(M, ea);
+    if (ea < 0) continue;
     for (int r = 0; r < na; ++r) {
       E[M.lam_off[ea] + r] += ek[roff + r];
       resLam[M.lam_off[ea] + r] += nl[roff + r];
     }
     int coff = 0;
     for (int b = 0; b < 3; ++b) {
-      int eb = M.elem_face[K * 3 + b], nb = 4 * (M.face_p[eb] + 1);
+      int eb = M.elem_face[K * 3 + b], nb = face_len(M, eb);
+      if (eb < 0) continue;
       int slot = -1;
       for (int t = 0; t < 5; ++t)
         if (M.k_col[5 * ea + t] == eb) slot = t;
@@ -962,7 +1058,7 @@ int orc_global_residual(void* h, const orc_params* P, const double* U, const dou
     std::copy(nu.begin(), nu.end(), R + M->u_off[K]);
     int roff = 0;
     for (int a = 0; a < 3; ++a) {
-      int ea = M->elem_face[K * 3 + a], na = 4 * (M->face_p[ea] + 1);
+      int ea = M->elem_face[K * 3 + a], na = face_len(*M, ea);
       for (int r = 0; r < na; ++r) R[M->u_len + M->lam_off[ea] + r] += nl[roff + r];
       roff += na;
     }
@@ -992,7 +1088,7 @@ int orc_monolithic(void* h, const orc_params* P, const double* U, const double* 
       std::vector<cplx> L;
       for (int lf = 0; lf < 3; ++lf) {
         int e = M->elem_face[K * 3 + lf];
-        for (int r = 0; r < 4 * (M->face_p[e] + 1); ++r) L.push_back(Lc[M->lam_off[e] + r]);
+        for (int r = 0; r < face_len(*M, e); ++r) L.push_back(Lc[M->lam_off[e] + r]);
       }
       std::vector<cplx> nu(elem_n(*M, K)), nl(elem_nt(*M, K));
       element_residual<cplx>(*M, *P, K, g, Uc.data() + M->u_off[K], L.data(), nu.data(), nl.data(),
@@ -1000,7 +1096,7 @@ int orc_monolithic(void* h, const orc_params* P, const double* U, const double* 
       for (size_t r = 0; r < nu.size(); ++r) Rc[M->u_off[K] + r] = nu[r];
       int roff = 0;
       for (int a = 0; a < 3; ++a) {
-        int ea = M->elem_face[K * 3 + a], na = 4 * (M->face_p[ea] + 1);
+        int ea = M->elem_face[K * 3 + a], na = face_len(*M, ea);
         for (int r = 0; r < na; ++r) Rc[M->u_len + M->lam_off[ea] + r] += nl[roff + r];
         roff += na;
       }
@@ -1038,6 +1134,11 @@ double orc_cfl_law(int n, double c0, double c1, int n0, double cfl_prev, double 
     return c0 * (3.0 * t * t - 2.0 * t * t * t);
   }
   return cfl_prev * (1.0 + c1 * std::max(0.0, std::log(res_prev / res_cur)));
+}
+
+// Boundary state w_b(w) of Sec. 2.1 for kind 1 (slip wall) or 2 (far field), normal n.
+void orc_boundary_state(int kind, const double* w, double nx, double ny, const orc_params* P, double* wb) {
+  boundary_state(kind, w, nx, ny, *P, wb);
 }
 
 // Shock-capturing viscosity eps_K of element K (0 when P->sc_eps0 <= 0).

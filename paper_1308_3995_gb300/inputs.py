@@ -43,6 +43,7 @@ class MeshData:
     elem_xy: np.ndarray      # [n_elem, 3, 2] float64, CCW, periodic images resolved
     elem_vid: np.ndarray     # [n_elem, 3] int32 topological vertex ids
     vert_xy: np.ndarray      # [n_vert, 2] jittered positions in [0,1)^2 (mod 1)
+    elem_bc: np.ndarray | None = None   # [n_elem, 3] int8 boundary kind of local face l (0 interior)
 
     @property
     def n_elem(self) -> int:
@@ -88,6 +89,55 @@ def periodic_mesh(nx: int, ny: int, jitter: float, seed: int) -> MeshData:
         raise ValueError("jitter produced a non-positive element")
     vert_xy = np.stack([X.reshape(-1), Y.reshape(-1)], -1)
     return MeshData(nx, ny, np.ascontiguousarray(elem_xy), elem_vid, vert_xy)
+
+
+BC_SLIP_WALL, BC_FAR_FIELD = 1, 2
+
+
+def channel_mesh(nx: int, ny: int, jitter: float, seed: int, bottom: int = BC_SLIP_WALL,
+                 top: int = BC_FAR_FIELD) -> MeshData:
+    """Unit square, periodic in x, bounded in y: a slip wall along y = 0 and a far-field boundary
+    along y = 1 (boundary kinds as given).  Same cell split as the periodic mesh; interior vertex rows
+    jittered in x and y, the two boundary rows in x only."""
+    if nx < 3 or ny < 2:
+        raise ValueError("channel grids need nx >= 3 and ny >= 2")
+    rng = np.random.default_rng(seed)
+    hx, hy = 1.0 / nx, 1.0 / ny
+    ii, jj = np.meshgrid(np.arange(nx), np.arange(ny + 1), indexing="xy")  # [ny+1, nx]
+    jx = rng.uniform(-jitter * hx, jitter * hx, size=(ny + 1, nx)) if jitter > 0 else np.zeros((ny + 1, nx))
+    jy = rng.uniform(-jitter * hy, jitter * hy, size=(ny + 1, nx)) if jitter > 0 else np.zeros((ny + 1, nx))
+    jy[0, :] = 0.0
+    jy[ny, :] = 0.0
+    X = ii * hx + jx
+    Y = jj * hy + jy
+    vid = (jj * nx + ii).astype(np.int64)
+    ic, jc = np.meshgrid(np.arange(nx), np.arange(ny), indexing="xy")      # cells [ny, nx]
+
+    def corner(di, dj):
+        i2 = (ic + di) % nx
+        j2 = jc + dj
+        x = X[j2, i2] + (ic + di >= nx)
+        return np.stack([x, Y[j2, i2]], -1), vid[j2, i2]
+
+    a, va = corner(0, 0)
+    b, vb = corner(1, 0)
+    c, vc = corner(1, 1)
+    d, vd = corner(0, 1)
+    t1 = np.stack([a, b, c], -2)
+    t2 = np.stack([a, c, d], -2)
+    v1 = np.stack([va, vb, vc], -1)
+    v2 = np.stack([va, vc, vd], -1)
+    elem_xy = np.stack([t1, t2], 2).reshape(-1, 3, 2)
+    elem_vid = np.stack([v1, v2], 2).reshape(-1, 3).astype(np.int32)
+    bc = np.zeros((ny, nx, 2, 3), np.int8)
+    bc[0, :, 0, 0] = bottom        # (a, b) of the lower triangle on y = 0
+    bc[ny - 1, :, 1, 1] = top      # (c, d) of the upper triangle on y = 1
+    e = elem_xy
+    det = (e[:, 1, 0] - e[:, 0, 0]) * (e[:, 2, 1] - e[:, 0, 1]) - (e[:, 2, 0] - e[:, 0, 0]) * (e[:, 1, 1] - e[:, 0, 1])
+    if not np.all(det > 0):
+        raise ValueError("jitter produced a non-positive element")
+    vert_xy = np.stack([X.reshape(-1), Y.reshape(-1)], -1)
+    return MeshData(nx, ny, np.ascontiguousarray(elem_xy), elem_vid, vert_xy, bc.reshape(-1, 3))
 
 
 def degree_map(n_elem: int, seed: int, p: int | None = None, probs=None) -> np.ndarray:
@@ -254,6 +304,7 @@ class Workload:
     prandtl: float = 0.72
     seed: int = 1234
     extra: dict = field(default_factory=dict)
+    domain: str = "periodic"   # or "channel": slip wall at y = 0, far field at y = 1
 
     @property
     def n_elem(self) -> int:
@@ -275,6 +326,10 @@ WORKLOADS = {
                             seed=33),
     # 262,144 jittered triangles, Euler p=3, Mach 1.5 oblique shock band
     "euler_p3_262k_shock": Workload("euler_p3_262k_shock", 256, 512, 0.2, 0, 3, None, "shock", 1.5, 0.0, seed=44),
+    # bounded domain: 8,192 jittered triangles between a slip wall (y = 0) and a far field (y = 1),
+    # Euler p=2, Mach 0.5 free stream along the wall + Gaussian density bump
+    "euler_channel_8k": Workload("euler_channel_8k", 64, 64, 0.2, 0, 2, None, "bump", 0.5, 0.0, seed=55,
+                                 domain="channel"),
 }
 
 
@@ -298,7 +353,10 @@ class Case:
 
 
 def make_case(wl: Workload) -> Case:
-    mesh = periodic_mesh(wl.nx, wl.ny, wl.jitter, wl.seed)
+    if wl.domain == "channel":
+        mesh = channel_mesh(wl.nx, wl.ny, wl.jitter, wl.seed)
+    else:
+        mesh = periodic_mesh(wl.nx, wl.ny, wl.jitter, wl.seed)
     ep = degree_map(mesh.n_elem, wl.seed + 1, p=wl.p, probs=wl.probs)
     fld = Field(wl.field, wl.mach, wl.aoa, wl.seed + 2, h=mesh.h, kvec=wl.extra.get("kvec"))
     return Case(wl, mesh, ep, fld)

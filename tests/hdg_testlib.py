@@ -10,7 +10,7 @@ from paper_1308_3995_gb300 import inputs as G
 
 def oracle_params(wl, cfl=0.0, sc=0.0):
     return O.Params(model=wl.model, mach=wl.mach, alpha=wl.alpha, reynolds=wl.reynolds, prandtl=wl.prandtl,
-                    cfl=cfl, sc_eps0=sc)
+                    cfl=cfl, sc_eps0=sc, aoa=wl.aoa)
 
 
 def lib_params(wl, cfl=0.0, precision=0, sc=0.0):

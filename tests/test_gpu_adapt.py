@@ -57,7 +57,7 @@ def test_indicators_against_oracle(ctx, name, nx, ny, kw):
     from paper_1308_3995_gb300 import hdg
     wl = G.small_variant(G.WORKLOADS[name], nx, ny, **kw)
     case = G.make_case(wl)
-    om = O.Mesh(case.mesh.elem_xy, case.mesh.elem_vid, case.elem_p, case.nfield)
+    om = O.Mesh(case.mesh.elem_xy, case.mesh.elem_vid, case.elem_p, case.nfield, case.mesh.elem_bc)
     U, Lam, _ = G.case_state(case, om.face_vid, om.face_p)
     mesh = hdg.Mesh(ctx, case.mesh.elem_xy, case.mesh.elem_vid, case.elem_p, case.nfield)
     sysm = hdg.System(ctx, mesh, lib_params(wl))

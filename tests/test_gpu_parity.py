@@ -24,7 +24,7 @@ def ctx():
 
 def build_case(wl):
     case = G.make_case(wl)
-    om = O.Mesh(case.mesh.elem_xy, case.mesh.elem_vid, case.elem_p, case.nfield)
+    om = O.Mesh(case.mesh.elem_xy, case.mesh.elem_vid, case.elem_p, case.nfield, case.mesh.elem_bc)
     U, Lam, dLam = G.case_state(case, om.face_vid, om.face_p)
     return case, om, U, Lam, dLam
 

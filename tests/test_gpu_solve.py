@@ -21,7 +21,7 @@ def ctx():
 def setup(ctx, wl, cfl, precision=0):
     from paper_1308_3995_gb300 import hdg
     case = G.make_case(wl)
-    om = O.Mesh(case.mesh.elem_xy, case.mesh.elem_vid, case.elem_p, case.nfield)
+    om = O.Mesh(case.mesh.elem_xy, case.mesh.elem_vid, case.elem_p, case.nfield, case.mesh.elem_bc)
     U, Lam, dLam = G.case_state(case, om.face_vid, om.face_p)
     mesh = hdg.Mesh(ctx, case.mesh.elem_xy, case.mesh.elem_vid, case.elem_p, case.nfield)
     sysm = hdg.System(ctx, mesh, lib_params(wl, cfl, precision))
