@@ -210,10 +210,10 @@ class Measured:
         self.wl, self.precision = wl, precision
         self.case = G.make_case(wl)
         c = self.case
-        self.mesh = hdg.Mesh(ctx, c.mesh.elem_xy, c.mesh.elem_vid, c.elem_p, c.nfield)
+        self.mesh = hdg.Mesh(ctx, c.mesh.elem_xy, c.mesh.elem_vid, c.elem_p, c.nfield, c.mesh.elem_bc)
         self.U, self.Lam, self.dLam = G.case_state(c, self.mesh.face_vid, self.mesh.face_p)
         self.prm = hdg.Params(model=wl.model, precision=precision, mach=wl.mach, alpha=wl.alpha,
-                              reynolds=wl.reynolds, prandtl=wl.prandtl, sc_eps0=sc_eps0)
+                              reynolds=wl.reynolds, prandtl=wl.prandtl, sc_eps0=sc_eps0, aoa=wl.aoa)
         self.sys = hdg.System(ctx, self.mesh, self.prm)
         self.Ut, self.Lt, self.dLt = (torch.from_numpy(a).to(dev) for a in (self.U, self.Lam, self.dLam))
         self.dUt = torch.empty(self.mesh.u_len, dtype=torch.float64, device=dev)

@@ -124,6 +124,9 @@ typedef struct {
    * (paper's values when needed: sc_eps0 = 0.2, sc_beta = 0). */
   double sc_eps0;
   double sc_beta;
+  /* Free-stream angle of attack [degrees]: the far-field state of boundary
+   * faces (Sec. 2.1) is rho = 1, |v| = mach at this angle, p = 1/gamma. */
+  double aoa;
 } hdg_params;
 
 /* Create a context on CUDA device `device` (makes it current on this thread). */
@@ -143,6 +146,20 @@ const char* hdg_last_error(const hdg_ctx* ctx);
  * exactly two distinct elements, or two elements share two faces. */
 hdg_status hdg_mesh_create(hdg_ctx* ctx, int32_t n_elem, int32_t nfield, const double* elem_xy,
                            const int32_t* elem_vid, const int8_t* elem_p, hdg_mesh** out);
+
+/* hdg_mesh_create for a bounded domain (Sec. 2.1, 3.2).  elem_bc (HOST, may be
+ * NULL = every face interior) [n_elem][3]: boundary kind of local face l of
+ * each element -- 0 interior, 1 slip wall, 2 far field (characteristic
+ * upwinding against the free stream of hdg_params.mach / aoa).  A boundary
+ * face carries no trace unknowns: the element gets the boundary operator
+ * <phi, f_c(w_b(w)) . n> and its Jacobian instead, elem_face is -1 there, and
+ * rows of K next to a boundary keep their five slots with the unused ones
+ * marked k_col = -1 (empty blocks, after the used columns).  Every untagged
+ * face must be shared by exactly two elements.  Euler only (nfield = 4; else
+ * HDG_ENOTSUP). */
+hdg_status hdg_mesh_create_bc(hdg_ctx* ctx, int32_t n_elem, int32_t nfield, const double* elem_xy,
+                              const int32_t* elem_vid, const int8_t* elem_p, const int8_t* elem_bc,
+                              hdg_mesh** out);
 hdg_status hdg_mesh_destroy(hdg_mesh* mesh);
 
 /* sizes[7] = {n_elem, n_face, u_len, lam_len, x_len, k_len, max_nt} */

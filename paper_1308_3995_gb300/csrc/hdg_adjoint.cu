@@ -47,7 +47,7 @@ __global__ void __launch_bounds__(32 * kRhsWarps) k_adjoint_rhs(AdjRhs a) {
     for (int l = 0; l < 3; ++l) {
       const int f = a.elem_face[3 * K + l];
       if (f == e) break;
-      toff += 4 * (a.face_p[f] + 1);
+      if (f >= 0) toff += 4 * (a.face_p[f] + 1);  // boundary faces carry no trace unknowns
     }
     const int64_t n = a.u_off[K + 1] - a.u_off[K];
     const double* xc = a.X + a.x_off[K] + (int64_t)(toff + lane) * n;  // column toff + lane of X_B

@@ -54,9 +54,11 @@ void free_all(std::vector<void*>& allocs) {
   allocs.clear();
 }
 
+int face_len(const hdg_mesh* M, int e) { return e < 0 ? 0 : 4 * (M->face_p[e] + 1); }
+
 int elem_nt(const hdg_mesh* M, int K) {
   int nt = 0;
-  for (int a = 0; a < 3; ++a) nt += 4 * (M->face_p[M->elem_face[3 * K + a]] + 1);
+  for (int a = 0; a < 3; ++a) nt += face_len(M, M->elem_face[3 * K + a]);
   return nt;
 }
 
@@ -124,15 +126,29 @@ const char* hdg_last_error(const hdg_ctx* ctx) { return ctx ? ctx->err.c_str() :
 
 hdg_status hdg_mesh_create(hdg_ctx* ctx, int32_t n_elem, int32_t nfield, const double* elem_xy,
                            const int32_t* elem_vid, const int8_t* elem_p, hdg_mesh** out) {
+  return hdg_mesh_create_bc(ctx, n_elem, nfield, elem_xy, elem_vid, elem_p, nullptr, out);
+}
+
+hdg_status hdg_mesh_create_bc(hdg_ctx* ctx, int32_t n_elem, int32_t nfield, const double* elem_xy,
+                              const int32_t* elem_vid, const int8_t* elem_p, const int8_t* elem_bc,
+                              hdg_mesh** out) {
   if (!ctx || !out) return HDG_EINVAL;
   *out = nullptr;
   if (n_elem < 1 || (nfield != 4 && nfield != 12) || !elem_xy || !elem_vid || !elem_p)
     return fail(ctx, HDG_EINVAL, "hdg_mesh_create: bad arguments");
+  bool any_bc = false;
+  for (int t = 0; elem_bc && t < 3 * n_elem; ++t) {
+    if (elem_bc[t] < 0 || elem_bc[t] > 2) return fail(ctx, HDG_EINVAL, "hdg_mesh_create_bc: boundary kind not in 0..2");
+    any_bc |= elem_bc[t] != 0;
+  }
+  if (any_bc && nfield != 4)
+    return fail(ctx, HDG_ENOTSUP, "hdg_mesh_create_bc: boundary faces are supported for Euler only");
   if (cudaSetDevice(ctx->device) != cudaSuccess) return fail(ctx, HDG_ECUDA, "cudaSetDevice failed");
   hdg_mesh* M = new hdg_mesh();
   M->ctx = ctx;
   M->n_elem = n_elem;
   M->nfield = nfield;
+  M->has_bc = any_bc;
   std::vector<double> xy(elem_xy, elem_xy + 6 * (size_t)n_elem);
   for (int K = 0; K < n_elem; ++K) {
     const double* c = &xy[6 * (size_t)K];
@@ -149,6 +165,7 @@ hdg_status hdg_mesh_create(hdg_ctx* ctx, int32_t n_elem, int32_t nfield, const d
   ents.reserve(3 * (size_t)n_elem);
   for (int K = 0; K < n_elem; ++K)
     for (int l = 0; l < 3; ++l) {
+      if (any_bc && elem_bc[3 * K + l]) continue;  // boundary face: no partner, no trace unknowns
       const int a = elem_vid[3 * K + l], b = elem_vid[3 * K + (l + 1) % 3];
       ents.push_back({std::min(a, b), std::max(a, b), K, l});
     }
@@ -163,8 +180,7 @@ hdg_status hdg_mesh_create(hdg_ctx* ctx, int32_t n_elem, int32_t nfield, const d
                     !(i + 2 < ents.size() && ents[i + 2].lo == ents[i].lo && ents[i + 2].hi == ents[i].hi);
     if (!ok) {
       delete M;
-      return fail(ctx, HDG_EINVAL, "hdg_mesh_create: a face is not shared by exactly two elements "
-                                   "(only closed/periodic meshes are supported)");
+      return fail(ctx, HDG_EINVAL, "hdg_mesh_create: an untagged face is not shared by exactly two elements");
     }
     const int f = M->n_face++;
     M->face_lo.push_back(ents[i].lo);
@@ -208,19 +224,20 @@ hdg_status hdg_mesh_create(hdg_ctx* ctx, int32_t n_elem, int32_t nfield, const d
       const int K = sd ? M->face_el1[f] : M->face_el0[f];
       for (int l = 0; l < 3; ++l) {
         const int e = M->elem_face[3 * (size_t)K + l];
-        if (e != f) cols[nc++] = e;
+        if (e != f && e >= 0) cols[nc++] = e;
       }
     }
-    std::sort(cols, cols + 5);
-    for (int b = 1; b < 5; ++b)
+    std::sort(cols, cols + nc);
+    for (int b = 1; b < nc; ++b)
       if (cols[b] == cols[b - 1]) {
         delete M;
         return fail(ctx, HDG_EINVAL, "hdg_mesh_create: two elements share two faces");
       }
+    for (int b = nc; b < 5; ++b) cols[b] = -1;  // unused slots next to boundary faces: empty blocks
     for (int b = 0; b < 5; ++b) {
       M->k_col[5 * (size_t)f + b] = cols[b];
       M->k_blkoff[5 * (size_t)f + b + 1] =
-          M->k_blkoff[5 * (size_t)f + b] + (int64_t)(4 * (M->face_p[f] + 1)) * (4 * (M->face_p[cols[b]] + 1));
+          M->k_blkoff[5 * (size_t)f + b] + (int64_t)(4 * (M->face_p[f] + 1)) * face_len(M, cols[b]);
     }
   }
   M->k_len = M->k_blkoff[5 * (size_t)M->n_face];
@@ -229,6 +246,10 @@ hdg_status hdg_mesh_create(hdg_ctx* ctx, int32_t n_elem, int32_t nfield, const d
     for (int a = 0; a < 3; ++a)
       for (int b = 0; b < 3; ++b) {
         const int ea = M->elem_face[3 * (size_t)K + a], eb = M->elem_face[3 * (size_t)K + b];
+        if (ea < 0 || eb < 0) {  // a boundary face: no block
+          kblk[9 * (size_t)K + 3 * a + b] = -1;
+          continue;
+        }
         int slot = 0;
         while (M->k_col[5 * (size_t)ea + slot] != eb) ++slot;
         kblk[9 * (size_t)K + 3 * a + b] = M->k_blkoff[5 * (size_t)ea + slot];
@@ -248,18 +269,26 @@ hdg_status hdg_mesh_create(hdg_ctx* ctx, int32_t n_elem, int32_t nfield, const d
   double* dxy;
   int *def, *dfp;
   uint8_t* dinfo;
+  uint8_t* dbc = nullptr;
+  std::vector<uint8_t> bcbits;
+  if (any_bc) {
+    bcbits.assign(n_elem, 0);
+    for (int K = 0; K < n_elem; ++K)
+      for (int l = 0; l < 3; ++l) bcbits[K] |= (uint8_t)((elem_bc[3 * K + l] & 3) << (2 * l));
+  }
   int64_t *duo, *dlo, *dxo, *dkb, *ddb;
   if ((st = upload(ctx, M->allocs, xy, &dxy)) || (st = upload(ctx, M->allocs, M->elem_face, &def)) ||
       (st = upload(ctx, M->allocs, info, &dinfo)) || (st = upload(ctx, M->allocs, M->face_p, &dfp)) ||
       (st = upload(ctx, M->allocs, M->u_off, &duo)) || (st = upload(ctx, M->allocs, M->lam_off, &dlo)) ||
       (st = upload(ctx, M->allocs, M->x_off, &dxo)) || (st = upload(ctx, M->allocs, kblk, &dkb)) ||
-      (st = upload(ctx, M->allocs, dblk, &ddb))) {
+      (st = upload(ctx, M->allocs, dblk, &ddb)) || (any_bc && (st = upload(ctx, M->allocs, bcbits, &dbc)))) {
     free_all(M->allocs);
     delete M;
     return st;
   }
   d.xy = dxy; d.elem_face = def; d.elem_info = dinfo; d.face_p = dfp;
   d.u_off = duo; d.lam_off = dlo; d.x_off = dxo; d.kblk = dkb; d.dblk_off = ddb;
+  d.elem_bc = dbc;
   for (int p = 1; p <= kMaxP; ++p) {
     M->bucket_n[p] = (int)bucket[p].size();
     if (M->bucket_n[p] && (st = upload(ctx, M->allocs, bucket[p], &M->d_bucket[p]))) {
@@ -323,6 +352,8 @@ void sys_sizes(const hdg_mesh* M, size_t* sz) {
 inline size_t round256(size_t b) { return (b + 255) & ~size_t(255); }
 
 hdg_status sys_validate(hdg_ctx* ctx, const hdg_mesh* M, const hdg_params* P, const char* who) {
+  if (M->has_bc && !std::isfinite(P->aoa))
+    return fail(ctx, HDG_EINVAL, std::string(who) + ": boundary faces need a finite aoa");
   const std::string w(who);
   if ((P->model == HDG_EULER) != (M->nfield == 4) || (P->model != HDG_EULER && P->model != HDG_NS_MIXED))
     return fail(ctx, HDG_EINVAL, w + ": model does not match the mesh's field count");
@@ -351,6 +382,7 @@ hdg_sys* sys_new(hdg_ctx* ctx, const hdg_mesh* M, const hdg_params* P) {
   S->ph.cfl = P->cfl;
   S->ph.sc_eps0 = P->sc_eps0 > 0.0 ? P->sc_eps0 : 0.0;
   S->ph.sc_beta = P->sc_beta;
+  far_field_state(*P, S->ph.winf);
   S->ph.model = P->model;
   S->ph.precision = P->precision;
   S->ph.persistent = 1;

@@ -1,6 +1,7 @@
 // Internal declarations shared by the host planner and the CUDA kernels.
 #pragma once
 
+#include <cmath>
 #include <cstdint>
 #include <string>
 #include <vector>
@@ -43,6 +44,7 @@ void build_tables(Tables& T);
 struct Phys {
   double gamma, alpha, prandtl, mu_inf, suth_s, cfl;
   double sc_eps0, sc_beta;  // shock capturing (Sec. 3.2); off unless sc_eps0 > 0
+  double winf[4];           // far-field conserved state (Sec. 2.1)
   int model, precision;
   int persistent;  // 1: grid = SMs x resident CTAs (loop over elements); 0: one CTA per element
   int adjoint;     // 1: adjoint local solves X~ = A^{-T} [C^T | F~] only (Sec. 4.2; Euler)
@@ -50,6 +52,16 @@ struct Phys {
   // k > 0 persistent grid of k CTAs per SM (capped by the occupancy)
   int grid[kMaxP + 1];
 };
+
+// far-field conserved state of Sec. 2.1: rho = 1, |v| = mach at angle aoa, p = 1/gamma
+inline void far_field_state(const hdg_params& P, double* w) {
+  const double a = P.aoa * 3.14159265358979323846 / 180.0;
+  const double u = P.mach * std::cos(a), v = P.mach * std::sin(a), p = 1.0 / P.gamma;
+  w[0] = 1.0;
+  w[1] = u;
+  w[2] = v;
+  w[3] = p / (P.gamma - 1.0) + 0.5 * (u * u + v * v);
+}
 
 inline void phys_default_grid(Phys& ph) {
   for (int p = 0; p <= kMaxP; ++p) ph.grid[p] = -1;
@@ -77,6 +89,8 @@ struct DevMesh {
   const int64_t* x_off;      // [n_elem+1]
   const int64_t* kblk;       // [n_elem][9]: offset in K of block (face a, face b), a,b local
   const int64_t* dblk_off;   // [n_face]: offset of a face's diagonal block in the half-1 scratch
+  const uint8_t* elem_bc;    // [n_elem] or null: bits 2l..2l+1 boundary kind of local face l
+                             // (0 interior, 1 slip wall, 2 far field); elem_face is -1 there
 };
 
 // Per-system output and work buffers handed to kernels by value.

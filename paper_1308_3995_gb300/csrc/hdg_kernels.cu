@@ -57,8 +57,9 @@ struct EulerLayout {
 
 inline int ldr_for(int ntmax) { return (ntmax + 1) | 1; }  // odd leading dimension
 // largest single-face trace size in a bucket of degree p: every face has p_e >= p
-inline int nkmax_for(int p, int ntmax) {
-  int nk = ntmax / 4 - 2 * (p + 1);
+inline int nkmax_for(int p, int ntmax, bool bounded = false) {
+  // on a mesh with boundary faces one face of the element may carry all of nt
+  int nk = bounded ? ntmax / 4 : ntmax / 4 - 2 * (p + 1);
   return nk > kMaxP + 1 ? kMaxP + 1 : nk;
 }
 
@@ -99,7 +100,7 @@ __global__ void __launch_bounds__(kCondThreads, 4) k_condense_euler(
   T* sW = sFhat + 3 * kPtSlots * 4;  // [3*6][16][5]
 
   __shared__ T g_det, g_Ji[2][2], g_n[3][2], g_len[3], g_mt;
-  __shared__ int g_e[3], g_pe[3], g_nk[3], g_toff[4], g_fl[3], g_side[3], g_old[3];
+  __shared__ int g_e[3], g_pe[3], g_nk[3], g_toff[4], g_fl[3], g_side[3], g_old[3], g_bc[3];
   // per trace index c < nt of the element: local face, field, mode
   __shared__ unsigned char g_cf[kMaxNt], g_cg[kMaxNt], g_cl[kMaxNt];
   __shared__ T s_pinv[64];
@@ -137,8 +138,9 @@ __global__ void __launch_bounds__(kCondThreads, 4) k_condense_euler(
       const int e = m.elem_face[3 * (size_t)K + a];
       const int info = m.elem_info[K];
       g_e[a] = e;
-      g_pe[a] = m.face_p[e];
-      g_nk[a] = g_pe[a] + 1;
+      g_bc[a] = m.elem_bc ? (m.elem_bc[K] >> (2 * a)) & 3 : 0;
+      g_pe[a] = e >= 0 ? m.face_p[e] : P;   // boundary face: the element's own degree, no traces
+      g_nk[a] = e >= 0 ? g_pe[a] + 1 : 0;
       g_fl[a] = (info >> a) & 1;
       g_side[a] = (info >> (3 + a)) & 1;
       if (tid == 0) {
@@ -191,6 +193,7 @@ __global__ void __launch_bounds__(kCondThreads, 4) k_condense_euler(
       g_cl[c] = (unsigned char)(cl - g * nk);
     }
     for (int a = 0; a < 3; ++a) {
+      if (g_e[a] < 0) continue;  // boundary face: no trace
       const double* lk = Lam + m.lam_off[g_e[a]];
       for (int t = tid; t < 4 * g_nk[a]; t += NT) sL[g_toff[a] + t] = A::from_d(lk[t]);
     }
@@ -328,7 +331,38 @@ __global__ void __launch_bounds__(kCondThreads, 4) k_condense_euler(
     for (int t = tid; t < 3 * kPtSlots; t += NT) {
       const int a = t / kPtSlots, g = t - a * kPtSlots;
       const int pe = g_pe[a], nk = pe + 1;
-      if (g < pe + 2) {
+      if (g < pe + 2 && g_bc[a]) {
+        // boundary operator of Sec. 3.2: <phi, f_c(w_b(w)) . n> and its Jacobian
+        // (A_n(w_b) d w_b / d w) on every field pair, kept in slot 0 of sW
+        const T* phe = tab + to.edge_phi[P][pe][a][g_fl[a]] + g * NP;
+        const T we = A::mul(tab[to.edge_w[pe] + g], g_len[a]);
+        T w[4], wb[4], dwb[4][4], fx[4], fy[4], Ax[16], Ay[16];
+#pragma unroll
+        for (int f = 0; f < 4; ++f) {
+          T acc = zero;
+#pragma unroll
+          for (int j = 0; j < NP; ++j) A::madd(acc, sU[f * NP + j], phe[j]);
+          w[f] = A::norm(acc);
+        }
+        T winf[4];
+#pragma unroll
+        for (int f = 0; f < 4; ++f) winf[f] = A::from_d(ph.winf[f]);
+        const T nx = g_n[a][0], ny = g_n[a][1];
+        boundary_state_jac(g_bc[a], w, nx, ny, winf, C, wb, dwb);
+        euler_flux_jac(wb, C, fx, fy, Ax, Ay);
+#pragma unroll
+        for (int f = 0; f < 4; ++f) sFhat[t * 4 + f] = A::mul(we, A::add(A::mul(nx, fx[f]), A::mul(ny, fy[f])));
+#pragma unroll
+        for (int f = 0; f < 4; ++f)
+#pragma unroll
+          for (int gg = 0; gg < 4; ++gg) {
+            T jb = zero;
+#pragma unroll
+            for (int h = 0; h < 4; ++h)
+              A::madd(jb, A::add(A::mul(nx, Ax[f * 4 + h]), A::mul(ny, Ay[f * 4 + h])), dwb[h][gg]);
+            sW[(t * 16 + f * 4 + gg) * 5] = A::mul(we, A::norm(jb));
+          }
+      } else if (g < pe + 2) {
         const T* phe = tab + to.edge_phi[P][pe][a][g_fl[a]] + g * NP;
         const T* ps = tab + to.edge_psi[pe] + g * nk;
         const T we = A::mul(tab[to.edge_w[pe] + g], g_len[a]);
@@ -413,13 +447,31 @@ __global__ void __launch_bounds__(kCondThreads, 4) k_condense_euler(
       sEh[t] = A::neg(acc);  // H
     }
     __syncthreads();
+    if (g_bc[0] | g_bc[1] | g_bc[2]) {
+      // boundary Jacobian, before the face-mass loop reuses the face scratch:
+      // A[(f,i),(g,j)] += sum over boundary faces, points q of phi_i phi_j (w_e A_n(w_b) dw_b/dw)_fg
+      for (int t = tid; t < 16 * NP * NP; t += NT) {
+        const int fg = t / (NP * NP), rem = t - fg * NP * NP, i = rem / NP, j = rem - i * NP;
+        T acc = zero;
+        for (int a = 0; a < 3; ++a) {
+          if (!g_bc[a]) continue;
+          const T* phe = tab + to.edge_phi[P][P][a][g_fl[a]];
+          for (int q = 0; q < P + 2; ++q)
+            A::madd(acc, A::mul(phe[q * NP + i], phe[q * NP + j]), sW[((a * kPtSlots + q) * 16 + fg) * 5]);
+        }
+        T* pa = &sA[((fg >> 2) * NP + i) * LDA + (fg & 3) * NP + j];
+        *pa = A::add(*pa, A::norm(acc));
+      }
+      __syncthreads();
+    }
     // face mass alpha <phi_i, phi_j>_dK on every field's diagonal block, plus the pseudo-time
     // mass and the frozen shock-capturing stiffness eps (grad phi_i, grad phi_j)_K
     T* sSt = scr;  // [NP][NP] eps * stiffness (the face scratch is dead here)
     for (int t = tid; t < NP * NP; t += NT) {
       const int i = t / NP, j = t - i * NP;
       T v = zero;
-      for (int a = 0; a < 3; ++a) A::madd(v, g_len[a], tab[to.face_mass[P][g_pe[a]][a] + t]);
+      for (int a = 0; a < 3; ++a)
+        if (!g_bc[a]) A::madd(v, g_len[a], tab[to.face_mass[P][g_pe[a]][a] + t]);
       v = A::mul(alpha, A::norm(v));
       if (i == j) v = A::add(v, g_mt);
       if (shock) {  // grad phi_i . grad phi_j = sum_rs G_rs d_r phi_i d_s phi_j, G = Ji Ji^T
@@ -551,6 +603,7 @@ __global__ void __launch_bounds__(kCondThreads, 4) k_condense_euler(
     // two-sided sums: side 0 parks its halves in K/E/res_lam, side 1 in the work space
     for (int a = 0; a < 3; ++a) {
       const int e = g_e[a], m4 = 4 * g_nk[a];
+      if (e < 0) continue;  // boundary face
       const int64_t lo = m.lam_off[e];
       double* dd = g_side[a] ? s.dhalf1 + m.dblk_off[e] : s.K + m.kblk[9 * (size_t)K + 4 * a];
       double* de = g_side[a] ? s.ehalf1 + lo : s.E + lo;
@@ -564,7 +617,7 @@ __global__ void __launch_bounds__(kCondThreads, 4) k_condense_euler(
     __threadfence();
     __syncthreads();
     if (tid < 3) {
-      g_old[tid] = atomicAdd(&s.face_cnt[g_e[tid]], 1);
+      g_old[tid] = g_e[tid] >= 0 ? atomicAdd(&s.face_cnt[g_e[tid]], 1) : 0;
       __threadfence();
     }
     __syncthreads();
@@ -611,6 +664,7 @@ __global__ void k_recover_f64(DevMesh m, const double* __restrict__ X, const dou
   double acc = 0.0;
   for (int a = 0; a < 3; ++a) {
     const int f = m.elem_face[3 * (size_t)K + a];
+    if (f < 0) continue;  // boundary face: no trace unknowns
     const int len = 4 * (m.face_p[f] + 1);
     const double* dl = dLam + m.lam_off[f];
     for (int t = 0; t < len; ++t, ++c) acc += xk[(size_t)c * n + r] * dl[t];
@@ -625,7 +679,7 @@ template <int P, class T>
 static bool launch_euler_bucket(const DevMesh& m, const DevSys& s, const Phys& ph, const T* tab, const TabOff& to,
                                 const double* U, const double* Lam, const int* elems, int n, int ntmax,
                                 cudaStream_t st, std::string* err) {
-  const int ldr = ldr_for(ntmax), nkmax = nkmax_for(P, ntmax);
+  const int ldr = ldr_for(ntmax), nkmax = nkmax_for(P, ntmax, m.elem_bc != nullptr);
   const EulerLayout<P> lay(ldr, nkmax);
   const size_t bytes = sizeof(T) * (size_t)lay.total;
   cudaError_t ce = cudaFuncSetAttribute(k_condense_euler<P, T>, cudaFuncAttributeMaxDynamicSharedMemorySize,

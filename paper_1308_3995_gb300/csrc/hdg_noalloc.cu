@@ -117,6 +117,7 @@ extern "C" hdg_status hdg_condense_noalloc(const hdg_mesh* mesh, const hdg_param
   ph.cfl = P->cfl;
   ph.sc_eps0 = P->sc_eps0 > 0.0 ? P->sc_eps0 : 0.0;
   ph.sc_beta = P->sc_beta;
+  far_field_state(*P, ph.winf);
   ph.model = P->model;
   ph.precision = P->precision;
   ph.persistent = 1;

@@ -20,6 +20,7 @@ struct hdg_ctx {
 struct hdg_mesh {
   hdg_ctx* ctx = nullptr;
   int n_elem = 0, n_face = 0, nfield = 4, max_nt = 0;
+  bool has_bc = false;
   int64_t u_len = 0, lam_len = 0, x_len = 0, k_len = 0, dh_len = 0;
   std::vector<int> face_lo, face_hi, face_el0, face_el1, face_p, elem_face, k_col;
   std::vector<int64_t> u_off, lam_off, x_off, k_blkoff;

@@ -190,4 +190,96 @@ __device__ __forceinline__ void visc_all(const T* w, const T (*q)[4], const NsCo
   }
 }
 
+// Boundary state of Sec. 2.1 and its derivative d w_b / d w (forward mode, four
+// directions), for kind 1 (slip wall: w_b = (rho, m - (m . n) n, E)) or 2 (far
+// field, characteristic upwinding: w_b = w + sum over negative eigenvalues of
+// r_j (l_j . (w_inf - w)), with r_j / l_j the right / left eigenvectors of
+// f_c'(w) . n -- r: (1, u - c n, H - c v_n), (1, u, v, |v|^2/2), (0, t, v_t),
+// (1, u + c n, H + c v_n), t = (-n_y, n_x); eigenvalues v_n - c, v_n, v_n,
+// v_n + c; the left eigenvectors in closed form; the selection is taken at the
+// current state and not differentiated).
+// Not inlined: its forward-mode elimination needs many registers, and only
+// boundary points call it, so it keeps its own frame instead of raising the
+// register pressure of the element kernel around it.
+template <class T>
+__device__ __noinline__ void boundary_state_jac(int kind, const T* w, T nx, T ny, const T* winf,
+                                                const EulerConst<T>& C, T* wb, T (*dwb)[4]) {
+  using A = Ar<T>;
+  using D = Dual<T, 4>;
+  D wd[4];
+#pragma unroll
+  for (int g = 0; g < 4; ++g) {
+    wd[g] = dconst<T, 4>(w[g]);
+    wd[g].d[g] = A::from_d(1.0);
+  }
+  D out[4];
+  if (kind == 1) {
+    const D mn = dadd(dscale(wd[1], nx), dscale(wd[2], ny));
+    out[0] = wd[0];
+    out[1] = dsub(wd[1], dscale(mn, nx));
+    out[2] = dsub(wd[2], dscale(mn, ny));
+    out[3] = wd[3];
+  } else {
+    const D ir = drcp(wd[0]);
+    const D u = dmul(wd[1], ir), v = dmul(wd[2], ir);
+    const D q2h = dscale(dadd(dmul(u, u), dmul(v, v)), C.half);
+    const D p = dscale(dsub(wd[3], dmul(wd[0], q2h)), C.g1);
+    const D c2 = dscale(dmul(p, ir), C.gam);
+    const D c = dsqrt(c2), ic = drcp(c);
+    const D H = dmul(dadd(wd[3], p), ir);
+    const D vn = dadd(dscale(u, nx), dscale(v, ny));
+    const D vt = dsub(dscale(v, nx), dscale(u, ny));
+    // left eigenvectors (rows of Q^{-1}) in closed form: b1 = (gamma-1)/c^2, b2 = b1 |v|^2/2
+    const D b1 = dscale(drcp(c2), C.g1), b2 = dmul(b1, q2h);
+    const T lam0 = A::sub(vn.v, c.v), lam1 = vn.v, lam3 = A::add(vn.v, c.v);
+    D dw[4];
+#pragma unroll
+    for (int f = 0; f < 4; ++f) dw[f] = dsub(dconst<T, 4>(winf[f]), wd[f]);   // w_inf - w
+#pragma unroll
+    for (int f = 0; f < 4; ++f) out[f] = wd[f];
+    const D bu = dmul(b1, u), bv = dmul(b1, v), vnc = dmul(vn, ic);
+    const D nxc = dscale(ic, nx), nyc = dscale(ic, ny);
+    if (A::to_d(lam0) < 0.0) {  // eigenvalue v_n - c: l = (b2 + v_n/c, -b1 u - n_x/c, -b1 v - n_y/c, b1) / 2
+      D y = dmul(dadd(b2, vnc), dw[0]);
+      y = dsub(y, dmul(dadd(bu, nxc), dw[1]));
+      y = dsub(y, dmul(dadd(bv, nyc), dw[2]));
+      y = dscale(dadd(y, dmul(b1, dw[3])), C.half);
+      const D cn = dscale(c, nx), cm = dscale(c, ny);
+      out[0] = dadd(out[0], y);
+      out[1] = dadd(out[1], dmul(dsub(u, cn), y));
+      out[2] = dadd(out[2], dmul(dsub(v, cm), y));
+      out[3] = dadd(out[3], dmul(dsub(H, dmul(c, vn)), y));
+    }
+    if (A::to_d(lam1) < 0.0) {  // eigenvalue v_n (twice): l2 = (1 - b2, b1 u, b1 v, -b1), l3 = (-v_t, -n_y, n_x, 0)
+      D y2 = dmul(dsub(dconst<T, 4>(C.one), b2), dw[0]);
+      y2 = dadd(y2, dmul(bu, dw[1]));
+      y2 = dadd(y2, dmul(bv, dw[2]));
+      y2 = dsub(y2, dmul(b1, dw[3]));
+      D y3 = dmul(vt, dw[0]);
+      y3 = dsub(dsub(dscale(dw[2], nx), dscale(dw[1], ny)), y3);
+      out[0] = dadd(out[0], y2);
+      out[1] = dadd(out[1], dsub(dmul(u, y2), dscale(y3, ny)));
+      out[2] = dadd(out[2], dadd(dmul(v, y2), dscale(y3, nx)));
+      out[3] = dadd(out[3], dadd(dmul(q2h, y2), dmul(vt, y3)));
+    }
+    if (A::to_d(lam3) < 0.0) {  // eigenvalue v_n + c: l = (b2 - v_n/c, -b1 u + n_x/c, -b1 v + n_y/c, b1) / 2
+      D y = dmul(dsub(b2, vnc), dw[0]);
+      y = dadd(y, dmul(dsub(nxc, bu), dw[1]));
+      y = dadd(y, dmul(dsub(nyc, bv), dw[2]));
+      y = dscale(dadd(y, dmul(b1, dw[3])), C.half);
+      const D cn = dscale(c, nx), cm = dscale(c, ny);
+      out[0] = dadd(out[0], y);
+      out[1] = dadd(out[1], dmul(dadd(u, cn), y));
+      out[2] = dadd(out[2], dmul(dadd(v, cm), y));
+      out[3] = dadd(out[3], dmul(dadd(H, dmul(c, vn)), y));
+    }
+  }
+#pragma unroll
+  for (int f = 0; f < 4; ++f) {
+    wb[f] = out[f].v;
+#pragma unroll
+    for (int g = 0; g < 4; ++g) dwb[f][g] = out[f].d[g];
+  }
+}
+
 }  // namespace hdg

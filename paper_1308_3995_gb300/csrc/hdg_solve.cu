@@ -142,6 +142,7 @@ __global__ void __launch_bounds__(32 * kFaceWarps) k_face_op(FaceDev f, const do
   if (mode != 3) {
     for (int b = 0; b < 5; ++b) {
       const int col = f.k_col[5 * e + b];
+      if (col < 0) break;  // unused slots (next to boundary faces) come last
       const int mb = 4 * (f.face_p[col] + 1), n = m * mb;
       // stored block: K (e, col) is m x mb; for K^T, block (col, e) is mb x m
       const double* blk = f.K + (TR ? f.k_tblk[5 * e + b] : f.k_blkoff[5 * e + b]);
@@ -329,6 +330,7 @@ hdg_status hdg_solver_create(hdg_sys* sys, int32_t restart, hdg_solver** out) {
   for (int e = 0; e < M->n_face; ++e)
     for (int b = 0; b < 5; ++b) {
       const int f = M->k_col[5 * e + b];
+      if (f < 0) continue;
       for (int t = 0; t < 5; ++t)
         if (M->k_col[5 * f + t] == e) tblk[5 * e + b] = M->k_blkoff[5 * f + t];
     }

@@ -34,7 +34,8 @@ EXPORTS = ["hdg_create", "hdg_destroy", "hdg_last_error", "hdg_mesh_create", "hd
            "hdg_step_host_async", "hdg_graph_create", "hdg_graph_launch", "hdg_solver_create",
            "hdg_solver_destroy", "hdg_trace_solve", "hdg_trace_matvec", "hdg_newton_update", "hdg_residual_norm",
            "hdg_sys_set_cfl", "hdg_cfl_law", "hdg_autotune", "hdg_trace_solve_ex", "hdg_adjoint_condense",
-           "hdg_adapt_indicators", "hdg_adapt_mark"]
+           "hdg_adapt_indicators", "hdg_adapt_mark",
+           "hdg_mesh_create_bc"]
 
 
 class HdgError(RuntimeError):
@@ -48,7 +49,7 @@ class hdg_params(ctypes.Structure):
                 ("prandtl", ctypes.c_double), ("reynolds", ctypes.c_double), ("mach", ctypes.c_double),
                 ("alpha", ctypes.c_double), ("cfl", ctypes.c_double), ("t_inf", ctypes.c_double),
                 ("refine_tol", ctypes.c_double), ("refine_max", ctypes.c_int32), ("reserved", ctypes.c_int32),
-                ("sc_eps0", ctypes.c_double), ("sc_beta", ctypes.c_double)]
+                ("sc_eps0", ctypes.c_double), ("sc_beta", ctypes.c_double), ("aoa", ctypes.c_double)]
 
 
 @dataclass
@@ -66,11 +67,12 @@ class Params:
     refine_max: int = 4
     sc_eps0: float = 0.0     # shock capturing (Sec. 3.2) off unless > 0 (paper's value 0.2)
     sc_beta: float = 0.0
+    aoa: float = 0.0         # free-stream angle of attack [degrees]: the far-field state
 
     def c(self) -> hdg_params:
         return hdg_params(self.model, self.precision, self.gamma, self.prandtl, self.reynolds, self.mach,
                           self.alpha, self.cfl, self.t_inf, self.refine_tol, self.refine_max, 0,
-                          self.sc_eps0, self.sc_beta)
+                          self.sc_eps0, self.sc_beta, self.aoa)
 
 
 _vp = ctypes.c_void_p
@@ -93,6 +95,9 @@ def lib(build: bool = True):
         L.hdg_last_error.restype = ctypes.c_char_p
         L.hdg_mesh_create.argtypes = [_vp, ctypes.c_int32, ctypes.c_int32, _dp, _i32p,
                                       ctypes.POINTER(ctypes.c_int8), ctypes.POINTER(_vp)]
+        L.hdg_mesh_create_bc.argtypes = [_vp, ctypes.c_int32, ctypes.c_int32, _dp, _i32p,
+                                         ctypes.POINTER(ctypes.c_int8), ctypes.POINTER(ctypes.c_int8),
+                                         ctypes.POINTER(_vp)]
         L.hdg_mesh_destroy.argtypes = [_vp]
         L.hdg_mesh_sizes.argtypes = [_vp, _i64p]
         L.hdg_mesh_layout.argtypes = [_vp, _i32p, _i32p, _i32p, _i32p, _i64p, _i64p, _i64p, _i32p, _i64p]
@@ -261,14 +266,16 @@ class Context:
 class Mesh:
     """hdg_mesh_create + hdg_mesh_sizes + hdg_mesh_layout (host arrays in, device plan out)."""
 
-    def __init__(self, ctx: Context, elem_xy, elem_vid, elem_p, nfield: int):
+    def __init__(self, ctx: Context, elem_xy, elem_vid, elem_p, nfield: int, elem_bc=None):
         xy = np.ascontiguousarray(elem_xy, dtype=np.float64).reshape(-1)
         vid = np.ascontiguousarray(elem_vid, dtype=np.int32).reshape(-1)
         p = np.ascontiguousarray(elem_p, dtype=np.int8).reshape(-1)
+        bc = None if elem_bc is None else np.ascontiguousarray(elem_bc, dtype=np.int8).reshape(-1)
         h = _vp()
-        _check(lib().hdg_mesh_create(ctx.h, int(p.size), int(nfield), xy.ctypes.data_as(_dp),
-                                     vid.ctypes.data_as(_i32p), p.ctypes.data_as(ctypes.POINTER(ctypes.c_int8)),
-                                     ctypes.byref(h)), ctx.h)
+        _check(lib().hdg_mesh_create_bc(ctx.h, int(p.size), int(nfield), xy.ctypes.data_as(_dp),
+                                        vid.ctypes.data_as(_i32p), p.ctypes.data_as(ctypes.POINTER(ctypes.c_int8)),
+                                        bc.ctypes.data_as(ctypes.POINTER(ctypes.c_int8)) if bc is not None else None,
+                                        ctypes.byref(h)), ctx.h)
         self.h, self.ctx, self.nfield = h, ctx, nfield
         s = np.zeros(7, np.int64)
         lib().hdg_mesh_sizes(h, s.ctypes.data_as(_i64p))

@@ -140,6 +140,46 @@ def channel_mesh(nx: int, ny: int, jitter: float, seed: int, bottom: int = BC_SL
     return MeshData(nx, ny, np.ascontiguousarray(elem_xy), elem_vid, vert_xy, bc.reshape(-1, 3))
 
 
+def box_mesh(nx: int, ny: int, jitter: float, seed: int, kind: int = BC_FAR_FIELD) -> MeshData:
+    """Unit square bounded on all four sides by boundary faces of one kind (far field by default).
+    Same cell split; interior vertices jittered in x and y, boundary vertices along their side only,
+    corners fixed."""
+    if nx < 2 or ny < 2:
+        raise ValueError("box grids need at least 2 cells per direction")
+    rng = np.random.default_rng(seed)
+    hx, hy = 1.0 / nx, 1.0 / ny
+    ii, jj = np.meshgrid(np.arange(nx + 1), np.arange(ny + 1), indexing="xy")  # [ny+1, nx+1]
+    jx = rng.uniform(-jitter * hx, jitter * hx, size=ii.shape) if jitter > 0 else np.zeros(ii.shape)
+    jy = rng.uniform(-jitter * hy, jitter * hy, size=ii.shape) if jitter > 0 else np.zeros(ii.shape)
+    jx[:, 0] = 0.0; jx[:, nx] = 0.0
+    jy[0, :] = 0.0; jy[ny, :] = 0.0
+    X = ii * hx + jx
+    Y = jj * hy + jy
+    vid = (jj * (nx + 1) + ii).astype(np.int64)
+    ic, jc = np.meshgrid(np.arange(nx), np.arange(ny), indexing="xy")
+
+    def corner(di, dj):
+        return np.stack([X[jc + dj, ic + di], Y[jc + dj, ic + di]], -1), vid[jc + dj, ic + di]
+
+    a, va = corner(0, 0)
+    b, vb = corner(1, 0)
+    c, vc = corner(1, 1)
+    d, vd = corner(0, 1)
+    elem_xy = np.stack([np.stack([a, b, c], -2), np.stack([a, c, d], -2)], 2).reshape(-1, 3, 2)
+    elem_vid = np.stack([np.stack([va, vb, vc], -1), np.stack([va, vc, vd], -1)], 2).reshape(-1, 3).astype(np.int32)
+    bc = np.zeros((ny, nx, 2, 3), np.int8)
+    bc[0, :, 0, 0] = kind          # (a, b) on y = 0
+    bc[:, nx - 1, 0, 1] = kind     # (b, c) on x = 1
+    bc[ny - 1, :, 1, 1] = kind     # (c, d) on y = 1
+    bc[:, 0, 1, 2] = kind          # (d, a) on x = 0
+    e = elem_xy
+    det = (e[:, 1, 0] - e[:, 0, 0]) * (e[:, 2, 1] - e[:, 0, 1]) - (e[:, 2, 0] - e[:, 0, 0]) * (e[:, 1, 1] - e[:, 0, 1])
+    if not np.all(det > 0):
+        raise ValueError("jitter produced a non-positive element")
+    vert_xy = np.stack([X.reshape(-1), Y.reshape(-1)], -1)
+    return MeshData(nx, ny, np.ascontiguousarray(elem_xy), elem_vid, vert_xy, bc.reshape(-1, 3))
+
+
 def degree_map(n_elem: int, seed: int, p: int | None = None, probs=None) -> np.ndarray:
     """Uniform degree p, or i.i.d. degrees 1..4 with the given probabilities."""
     if p is not None:
@@ -304,7 +344,7 @@ class Workload:
     prandtl: float = 0.72
     seed: int = 1234
     extra: dict = field(default_factory=dict)
-    domain: str = "periodic"   # or "channel": slip wall at y = 0, far field at y = 1
+    domain: str = "periodic"   # "channel": slip wall at y = 0, far field at y = 1; "box": far field all round
 
     @property
     def n_elem(self) -> int:
@@ -330,6 +370,9 @@ WORKLOADS = {
     # Euler p=2, Mach 0.5 free stream along the wall + Gaussian density bump
     "euler_channel_8k": Workload("euler_channel_8k", 64, 64, 0.2, 0, 2, None, "bump", 0.5, 0.0, seed=55,
                                  domain="channel"),
+    # far field on all four sides of the unit square: 8,192 jittered triangles, Euler p=2, Mach 0.5 at
+    # 10 degrees + Gaussian density bump, which the steady solve washes out to the free stream
+    "euler_box_8k": Workload("euler_box_8k", 64, 64, 0.2, 0, 2, None, "bump", 0.5, 10.0, seed=66, domain="box"),
 }
 
 
@@ -355,6 +398,8 @@ class Case:
 def make_case(wl: Workload) -> Case:
     if wl.domain == "channel":
         mesh = channel_mesh(wl.nx, wl.ny, wl.jitter, wl.seed)
+    elif wl.domain == "box":
+        mesh = box_mesh(wl.nx, wl.ny, wl.jitter, wl.seed)
     else:
         mesh = periodic_mesh(wl.nx, wl.ny, wl.jitter, wl.seed)
     ep = degree_map(mesh.n_elem, wl.seed + 1, p=wl.p, probs=wl.probs)

@@ -131,7 +131,7 @@ def prepare(ctx: hdg.Context, reqs: list, pin: bool = True):
     import torch
     for r in reqs:
         case = G.make_case(r.wl)
-        m = hdg.Mesh(ctx, case.mesh.elem_xy, case.mesh.elem_vid, case.elem_p, case.nfield)
+        m = hdg.Mesh(ctx, case.mesh.elem_xy, case.mesh.elem_vid, case.elem_p, case.nfield, case.mesh.elem_bc)
         U, Lam, dLam = G.case_state(case, m.face_vid, m.face_p)
         r.case, r.face_vid, r.face_p = case, m.face_vid.copy(), m.face_p.copy()
         r.n_elem = case.mesh.n_elem

@@ -16,7 +16,7 @@ def oracle_params(wl, cfl=0.0, sc=0.0):
 def lib_params(wl, cfl=0.0, precision=0, sc=0.0):
     from paper_1308_3995_gb300 import hdg
     return hdg.Params(model=wl.model, precision=precision, mach=wl.mach, alpha=wl.alpha, reynolds=wl.reynolds,
-                      prandtl=wl.prandtl, cfl=cfl, sc_eps0=sc)
+                      prandtl=wl.prandtl, cfl=cfl, sc_eps0=sc, aoa=wl.aoa)
 
 
 def rel_err(a, b, floor=1e-300):
@@ -62,12 +62,13 @@ def per_elem_vec_errors(m, a, b):
 
 # ----------------------------------------------------------------------------- element-wise parity
 def _blocks_split(om, K):
-    sz = [4 * (int(om.face_p[e]) + 1) for e in om.elem_face[K]]
+    sz = [4 * (int(om.face_p[e]) + 1) if e >= 0 else 0 for e in om.elem_face[K]]
     return np.concatenate([[0], np.cumsum(sz)]).astype(int)
 
 
 def gather_trace(om, K, Lam):
-    return np.concatenate([Lam[om.lam_off[e]:om.lam_off[e + 1]] for e in om.elem_face[K]])
+    parts = [Lam[om.lam_off[e]:om.lam_off[e + 1]] for e in om.elem_face[K] if e >= 0]
+    return np.concatenate(parts) if parts else np.zeros(0)
 
 
 class ParityChecker:
@@ -126,6 +127,8 @@ class ParityChecker:
                 if a == b:
                     continue
                 ea, eb = om.elem_face[K][a], om.elem_face[K][b]
+                if ea < 0 or eb < 0:   # boundary face: no trace block
+                    continue
                 slot = list(om.k_col[ea]).index(eb)
                 o0, o1 = om.k_blkoff[5 * ea + slot], om.k_blkoff[5 * ea + slot + 1]
                 worst = max(worst, rel_err(self.g["K"][o0:o1], e["S"][off[a]:off[a + 1], off[b]:off[b + 1]]))

@@ -59,7 +59,7 @@ def test_indicators_against_oracle(ctx, name, nx, ny, kw):
     case = G.make_case(wl)
     om = O.Mesh(case.mesh.elem_xy, case.mesh.elem_vid, case.elem_p, case.nfield, case.mesh.elem_bc)
     U, Lam, _ = G.case_state(case, om.face_vid, om.face_p)
-    mesh = hdg.Mesh(ctx, case.mesh.elem_xy, case.mesh.elem_vid, case.elem_p, case.nfield)
+    mesh = hdg.Mesh(ctx, case.mesh.elem_xy, case.mesh.elem_vid, case.elem_p, case.nfield, case.mesh.elem_bc)
     sysm = hdg.System(ctx, mesh, lib_params(wl))
     dev = torch.device("cuda:0")
     Ut, Lt = torch.from_numpy(U).to(dev), torch.from_numpy(Lam).to(dev)
@@ -88,7 +88,7 @@ def test_adaptation_pipeline_primal_adjoint_mark(ctx):
     from paper_1308_3995_gb300 import hdg
     wl = G.small_variant(G.WORKLOADS["euler_p3_262k_shock"], 24, 32)
     case = G.make_case(wl)
-    mesh = hdg.Mesh(ctx, case.mesh.elem_xy, case.mesh.elem_vid, case.elem_p, case.nfield)
+    mesh = hdg.Mesh(ctx, case.mesh.elem_xy, case.mesh.elem_vid, case.elem_p, case.nfield, case.mesh.elem_bc)
     U, Lam, _ = G.case_state(case, mesh.face_vid, mesh.face_p)
     cfl = 10.0
     primal = hdg.System(ctx, mesh, lib_params(wl, cfl))

@@ -31,7 +31,7 @@ def build_case(wl):
 
 def run_gpu(ctx, case, wl, U, Lam, dLam, cfl=0.0, repeat=1, precision=0, sc=0.0):
     from paper_1308_3995_gb300 import hdg
-    mesh = hdg.Mesh(ctx, case.mesh.elem_xy, case.mesh.elem_vid, case.elem_p, case.nfield)
+    mesh = hdg.Mesh(ctx, case.mesh.elem_xy, case.mesh.elem_vid, case.elem_p, case.nfield, case.mesh.elem_bc)
     sysm = hdg.System(ctx, mesh, lib_params(wl, cfl, precision, sc))
     dev = torch.device("cuda:0")
     Ut = torch.from_numpy(U).to(dev)
@@ -296,7 +296,7 @@ def test_step_host_matches_device_path(ctx):
     wl = G.small_variant(G.WORKLOADS["euler_p3_16k"], 6, 6)
     case, om, U, Lam, dLam = build_case(wl)
     _, _, (g,) = run_gpu(ctx, case, wl, U, Lam, dLam)
-    mesh = hdg.Mesh(ctx, case.mesh.elem_xy, case.mesh.elem_vid, case.elem_p, case.nfield)
+    mesh = hdg.Mesh(ctx, case.mesh.elem_xy, case.mesh.elem_vid, case.elem_p, case.nfield, case.mesh.elem_bc)
     sysm = hdg.System(ctx, mesh, lib_params(wl))
     Uh = torch.from_numpy(U).pin_memory()
     Lh = torch.from_numpy(Lam).pin_memory()
@@ -331,7 +331,7 @@ def test_graph_replay_and_concurrent_buckets_match_plain_path(ctx, name, kw):
     wl = G.small_variant(G.WORKLOADS[name], 7, 6, **kw)
     case, om, U, Lam, dLam = build_case(wl)
     _, _, (ref,) = run_gpu(ctx, case, wl, U, Lam, dLam)
-    mesh = hdg.Mesh(ctx, case.mesh.elem_xy, case.mesh.elem_vid, case.elem_p, case.nfield)
+    mesh = hdg.Mesh(ctx, case.mesh.elem_xy, case.mesh.elem_vid, case.elem_p, case.nfield, case.mesh.elem_bc)
     sysm = hdg.System(ctx, mesh, lib_params(wl))
     dev = torch.device("cuda:0")
     Ut, Lt, dLt = (torch.from_numpy(a).to(dev) for a in (U, Lam, dLam))
@@ -356,7 +356,7 @@ def test_autotuned_launch_shapes_keep_results_bitwise(ctx, name, kw, precision):
     from paper_1308_3995_gb300 import hdg
     wl = G.small_variant(G.WORKLOADS[name], 12, 14, **kw)
     case, om, U, Lam, dLam = build_case(wl)
-    mesh = hdg.Mesh(ctx, case.mesh.elem_xy, case.mesh.elem_vid, case.elem_p, case.nfield)
+    mesh = hdg.Mesh(ctx, case.mesh.elem_xy, case.mesh.elem_vid, case.elem_p, case.nfield, case.mesh.elem_bc)
     sysm = hdg.System(ctx, mesh, lib_params(wl, 0.0, precision))
     dev = torch.device("cuda:0")
     Ut, Lt = torch.from_numpy(U).to(dev), torch.from_numpy(Lam).to(dev)

@@ -23,7 +23,7 @@ def setup(ctx, wl, cfl, precision=0):
     case = G.make_case(wl)
     om = O.Mesh(case.mesh.elem_xy, case.mesh.elem_vid, case.elem_p, case.nfield, case.mesh.elem_bc)
     U, Lam, dLam = G.case_state(case, om.face_vid, om.face_p)
-    mesh = hdg.Mesh(ctx, case.mesh.elem_xy, case.mesh.elem_vid, case.elem_p, case.nfield)
+    mesh = hdg.Mesh(ctx, case.mesh.elem_xy, case.mesh.elem_vid, case.elem_p, case.nfield, case.mesh.elem_bc)
     sysm = hdg.System(ctx, mesh, lib_params(wl, cfl, precision))
     dev = torch.device("cuda:0")
     Ut, Lt = torch.from_numpy(U).to(dev), torch.from_numpy(Lam).to(dev)

@@ -838,3 +838,22 @@ def test_channel_condensed_then_recovered_equals_monolithic(cfl):
     tol = 1e-10 if cfl > 0 else 1e-6
     assert np.abs(dLc - dL).max() < tol * np.abs(dL).max()
     assert np.abs(dUc - dU).max() < tol * np.abs(dU).max()
+
+
+def test_box_free_stream_and_regular_pure_newton():
+    """Far field on every side (AoA 10 deg): the free stream is preserved, and the pure-Newton
+    monolithic system is well conditioned -- the condensed solve reproduces it to 1e-10."""
+    wl = G.small_variant(G.WORKLOADS["euler_box_8k"], 4, 3, p=2)
+    c = G.make_case(wl)
+    m = O.Mesh(c.mesh.elem_xy, c.mesh.elem_vid, c.elem_p, c.nfield, c.mesh.elem_bc)
+    P = O.Params(mach=wl.mach, alpha=wl.alpha, aoa=wl.aoa)
+    Uf, Lf = _uniform_state(m, G.conserved(*G.free_stream(wl.mach, wl.aoa)))
+    Ru, Rl = m.global_residual(P, Uf, Lf)
+    assert np.abs(Ru).max() < 1e-14 and np.abs(Rl).max() < 1e-14
+    U, L, _ = G.case_state(c, m.face_vid, m.face_p)
+    dU, dL = m.monolithic(P, U, L)
+    r = m.condense(P, U, L)
+    dLc = O.dense_solve(m.dense_K(r["K"]), r["E"])
+    dUc = m.recover(r["X"], dLc)
+    assert np.abs(dLc - dL).max() < 1e-10 * np.abs(dL).max()
+    assert np.abs(dUc - dU).max() < 1e-10 * np.abs(dU).max()

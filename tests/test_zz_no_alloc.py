@@ -26,7 +26,7 @@ def _compare_two_calls(wl):
     from paper_1308_3995_gb300 import hdg
     case = G.make_case(wl)
     ctx = hdg.Context(0)
-    mesh = hdg.Mesh(ctx, case.mesh.elem_xy, case.mesh.elem_vid, case.elem_p, case.nfield)
+    mesh = hdg.Mesh(ctx, case.mesh.elem_xy, case.mesh.elem_vid, case.elem_p, case.nfield, case.mesh.elem_bc)
     U, Lam, _ = G.case_state(case, mesh.face_vid, mesh.face_p)
     prm = hdg.Params(model=wl.model, mach=wl.mach, alpha=wl.alpha)
     dev = torch.device("cuda:0")
@@ -68,7 +68,7 @@ def test_noalloc_rejects_oversize_mesh():
     wl = G.small_variant(G.WORKLOADS["euler_p3_16k"], 96, 128, p=4)  # 36,864 faces at p_e = 4: ~130 MB
     case = G.make_case(wl)
     ctx = hdg.Context(0)
-    mesh = hdg.Mesh(ctx, case.mesh.elem_xy, case.mesh.elem_vid, case.elem_p, case.nfield)
+    mesh = hdg.Mesh(ctx, case.mesh.elem_xy, case.mesh.elem_vid, case.elem_p, case.nfield, case.mesh.elem_bc)
     prm = hdg.Params(model=0, mach=wl.mach, alpha=wl.alpha)
     dev = torch.device("cuda:0")
     one = torch.zeros(1, dtype=torch.float64, device=dev)
