@@ -380,6 +380,48 @@ def adjoint_section(ctx, wl, dev, flush, stream, cfl=10.0, rtol=1e-10, reps=3):
     return out
 
 
+def steady_section(ctx, dev, flush, stream, name="euler_box_8k", tol=1e-10, c0=1e6, c1=1e3, n0=4):
+    """A steady solve on a bounded domain (far field on all sides, Sec. 2.1/3.2): pseudo-transient
+    Newton with the CFL law of Eq. (cfl) (the paper's c0, c1, n0), GPU condensation, GMRES trace
+    solve, reconstruction and update each step, until ||N_h|| has dropped by tol."""
+    import torch
+
+    from paper_1308_3995_gb300 import hdg
+    from paper_1308_3995_gb300 import inputs as G
+    wl = G.WORKLOADS[name]
+    m = Measured(ctx, wl, hdg.HDG_FP64, dev, flush)
+    solver = hdg.Solver(m.sys, restart=50)
+    dL = torch.zeros(m.mesh.lam_len, dtype=torch.float64, device=dev)
+    U, L = m.Ut.clone(), m.Lt.clone()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    cfl, r_prev, r0, hist, its = 0.0, None, None, [], []
+    for n in range(1, 40):
+        m.sys.condense(U, L, stream)
+        r = m.sys.residual_norm(stream)
+        r0 = r0 or r
+        hist.append(r)
+        if r < tol * r0:
+            break
+        cfl = hdg.cfl_law(n, c0=c0, c1=c1, n0=n0, cfl_prev=cfl, res_prev=r_prev or r, res_cur=r)
+        m.sys.set_cfl(cfl)
+        m.sys.condense(U, L, stream)
+        dL.zero_()
+        it, _ = solver.solve(dL, rtol=1e-11, max_iter=5000, stream=stream)
+        its.append(it)
+        m.sys.recover(dL, m.dUt, stream)
+        m.sys.newton_update(U, L, m.dUt, dL, stream)
+        r_prev = r
+    torch.cuda.synchronize()
+    out = {"workload": f"{name}: {m.n_elem} triangles, Euler p={wl.p}, far field on all sides, Mach {wl.mach} "
+                       f"at {wl.aoa} deg + density bump", "cfl_law": {"c0": c0, "c1": c1, "n0": n0},
+           "time_to_solution_s": time.perf_counter() - t0, "newton_steps": len(its),
+           "gmres_iterations": its, "residual_history": hist, "converged": hist[-1] < tol * hist[0]}
+    solver.close()
+    m.close()
+    return out
+
+
 def serving_section(ctx, n_requests, seed, max_elems, rates=(0.7,), arena_gb=24):
     """Poisson stream through the continuous-batching loop (float-float, 8 slots)
     against the plain loop (binary64, one request at a time), at each load level
@@ -433,7 +475,8 @@ def run_ours(args, wl, ws, rank, local):
         if rank == 0:
             print(json.dumps({"metric": "Newton step with GPU trace solve; adjoint and adaptation",
                               "solve": solve_section(ctx, wl, dev, flush, stream),
-                              "adjoint": adjoint_section(ctx, wl, dev, flush, stream)}), flush=True)
+                              "adjoint": adjoint_section(ctx, wl, dev, flush, stream),
+                              "steady": steady_section(ctx, dev, flush, stream)}), flush=True)
         return 0
     if args.serving_only:
         line = {"metric": "serving: p50/p99 latency and elements/s, continuous batching (float-float) vs plain FP64",
@@ -527,6 +570,7 @@ def run_ours(args, wl, ws, rank, local):
         line["euler_p3_262k_shock"] = shock
         line["newton_step_with_trace_solve"] = solve_section(ctx, wl, dev, flush, stream)
         line["adjoint_and_adaptation"] = adjoint_section(ctx, wl, dev, flush, stream)
+        line["steady_solve_bounded_domain"] = steady_section(ctx, dev, flush, stream)
         if args.serving_requests > 0:
             line["serving"] = serving_section(ctx, args.serving_requests, 77, args.serving_max_elems)
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
