@@ -282,47 +282,50 @@ class Measured:
 
 def solve_section(ctx, wl, dev, flush, stream, cfl=10.0, rtol=1e-10, reps=3):
     """One pseudo-transient Newton step with the GPU trace solve (Sec. 3.3/3.4): condensation at
-    the given CFL, GMRES + block Jacobi on K dLambda = E, reconstruction, update; plus the
-    bandwidth of the trace matrix-vector product (HBM-bound: the K values stream once)."""
+    the given CFL, GMRES (block Jacobi, then multicolor block symmetric Gauss-Seidel) on
+    K dLambda = E, reconstruction, update; plus the bandwidth of the trace matrix-vector product
+    (the K values stream once)."""
     import torch
 
     from paper_1308_3995_gb300 import hdg
     m = Measured(ctx, wl, hdg.HDG_FP64, dev, flush)
     m.sys.set_cfl(cfl)
-    solver = hdg.Solver(m.sys, restart=30)
     x = torch.zeros(m.mesh.lam_len, dtype=torch.float64, device=dev)
     y = torch.empty_like(x)
-    res = []
-    for r in range(reps + 1):
-        U, L = m.Ut.clone(), m.Lt.clone()
-        flush.fill_(1.0)
-        torch.cuda.synchronize()
-        t0 = time.perf_counter()
-        m.sys.condense(U, L, stream)
-        x.zero_()
-        it, rel = solver.solve(x, rtol=rtol, max_iter=2000, stream=stream)
-        m.sys.recover(x, m.dUt, stream)
-        m.sys.newton_update(U, L, m.dUt, x, stream)
-        torch.cuda.synchronize()
-        if r > 0:
-            res.append((time.perf_counter() - t0, it, rel))
-    # matrix-vector product bandwidth (K values + x gathers + y), CUDA events on the stream
-    nmv = 20
-    k_bytes = 8 * m.mesh.k_len
-    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    solver.matvec(x, y, stream)
-    ev0.record(stream)
-    for _ in range(nmv):
-        solver.matvec(x, y, stream)
-    ev1.record(stream)
-    torch.cuda.synchronize()
-    mv_s = ev0.elapsed_time(ev1) * 1e-3 / nmv
-    out = {"workload": wl.name, "cfl": cfl, "rtol": rtol, "restart": 30,
-           "newton_step_ms": 1e3 * statistics.median(t for t, _, _ in res),
-           "gmres_iterations": res[-1][1], "rel_residual": res[-1][2],
-           "matvec": {"k_mb": k_bytes / 1e6, "ms": 1e3 * mv_s, "k_gbs": k_bytes / mv_s / 1e9,
-                      "frac_of_hbm": k_bytes / mv_s / 1e9 / HBM_PEAK_GBS}}
-    solver.close()
+    out = {"workload": wl.name, "cfl": cfl, "rtol": rtol, "restart": 30}
+    for precond, nm in ((0, "block_jacobi"), (1, "block_sgs")):
+        solver = hdg.Solver(m.sys, restart=30, precond=precond)
+        res = []
+        for r in range(reps + 1):
+            U, L = m.Ut.clone(), m.Lt.clone()
+            flush.fill_(1.0)
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            m.sys.condense(U, L, stream)
+            x.zero_()
+            it, rel = solver.solve(x, rtol=rtol, max_iter=3000, stream=stream)
+            m.sys.recover(x, m.dUt, stream)
+            m.sys.newton_update(U, L, m.dUt, x, stream)
+            torch.cuda.synchronize()
+            if r > 0:
+                res.append((time.perf_counter() - t0, it, rel))
+        out[nm] = {"newton_step_ms": 1e3 * statistics.median(t for t, _, _ in res),
+                   "gmres_iterations": res[-1][1], "rel_residual": res[-1][2]}
+        if precond == 0:
+            # matrix-vector product bandwidth (K values + x gathers + y), CUDA events on the stream
+            nmv = 20
+            k_bytes = 8 * m.mesh.k_len
+            ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            solver.matvec(x, y, stream)
+            ev0.record(stream)
+            for _ in range(nmv):
+                solver.matvec(x, y, stream)
+            ev1.record(stream)
+            torch.cuda.synchronize()
+            mv_s = ev0.elapsed_time(ev1) * 1e-3 / nmv
+            out["matvec"] = {"k_mb": k_bytes / 1e6, "ms": 1e3 * mv_s, "k_gbs": k_bytes / mv_s / 1e9,
+                             "frac_of_hbm": k_bytes / mv_s / 1e9 / HBM_PEAK_GBS}
+        solver.close()
     m.close()
     return out
 
@@ -390,7 +393,7 @@ def steady_section(ctx, dev, flush, stream, name="euler_box_8k", tol=1e-10, c0=1
     from paper_1308_3995_gb300 import inputs as G
     wl = G.WORKLOADS[name]
     m = Measured(ctx, wl, hdg.HDG_FP64, dev, flush)
-    solver = hdg.Solver(m.sys, restart=50)
+    solver = hdg.Solver(m.sys, restart=50, precond=0)
     dL = torch.zeros(m.mesh.lam_len, dtype=torch.float64, device=dev)
     U, L = m.Ut.clone(), m.Lt.clone()
     torch.cuda.synchronize()
@@ -415,6 +418,7 @@ def steady_section(ctx, dev, flush, stream, name="euler_box_8k", tol=1e-10, c0=1
     torch.cuda.synchronize()
     out = {"workload": f"{name}: {m.n_elem} triangles, Euler p={wl.p}, far field on all sides, Mach {wl.mach} "
                        f"at {wl.aoa} deg + density bump", "cfl_law": {"c0": c0, "c1": c1, "n0": n0},
+           "preconditioner": "block Jacobi",
            "time_to_solution_s": time.perf_counter() - t0, "newton_steps": len(its),
            "gmres_iterations": its, "residual_history": hist, "converged": hist[-1] < tol * hist[0]}
     solver.close()

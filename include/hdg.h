@@ -319,6 +319,15 @@ hdg_status hdg_solver_destroy(hdg_solver* solver);
 hdg_status hdg_trace_solve(hdg_solver* solver, double* dLam, double rtol, int32_t max_iter, int32_t* iters,
                            double* rel_res, void* stream);
 
+/* Preconditioner of the trace solve: 0 block Jacobi (default), 1 multicolor
+ * block symmetric Gauss-Seidel -- faces colored so that no two faces of one
+ * element share a color (at most 5 colors on triangles), then one forward and
+ * one backward sweep over the colors, each color's block rows updated in
+ * parallel with the diagonal inverses of block Jacobi.  About three times the
+ * work of a block-Jacobi application per iteration, far fewer iterations at
+ * large CFL.  Applies to both K and K^T. */
+hdg_status hdg_solver_set_preconditioner(hdg_solver* solver, int32_t kind);
+
 /* Like hdg_trace_solve, with a right-hand side other than the system's E
  * (DEVICE rhs [lam_len]; NULL: E) and, when transpose != 0, the transposed
  * system K^T x = rhs (block Jacobi then uses the transposed diagonal blocks):

@@ -113,7 +113,11 @@ __global__ void __launch_bounds__(32 * kFaceWarps) k_bj_invert(FaceDev f) {
   }
 }
 
-// mode: 0 y = Dinv K x, 1 y = Dinv (b - K x), 2 y = K x, 3 y = Dinv b.
+// mode: 0 y = Dinv K x, 1 y = Dinv (b - K x), 2 y = K x, 3 y = Dinv b, 4 y = b - K x.
+// faces (may be null): the list of faces to process (one warp each), else all;
+// skip_diag: leave the diagonal block out of K x (a Gauss-Seidel sweep over
+// one color, in place: x and y may be the same vector, as no two faces of a
+// color are coupled).
 // Each block of the face row is staged through shared memory with coalesced
 // loads (the warp reads the m x mb row-major block as one contiguous run; rows
 // padded to mb + 1 against bank conflicts).  The products then use every lane
@@ -124,14 +128,16 @@ __global__ void __launch_bounds__(32 * kFaceWarps) k_bj_invert(FaceDev f) {
 // would cost time directly.
 // TR: the same with K^T (block (k_col[5e+b], e) transposed) and Dinv^T.
 template <bool TR>
-__global__ void __launch_bounds__(32 * kFaceWarps) k_face_op(FaceDev f, const double* __restrict__ x,
-                                                               const double* __restrict__ bvec, double* __restrict__ y,
-                                                               int mode) {
+__global__ void __launch_bounds__(32 * kFaceWarps) k_face_op(FaceDev f, const double* x,
+                                                               const double* __restrict__ bvec, double* y,
+                                                               int mode, const int* __restrict__ faces, int nfaces,
+                                                               int skip_diag) {
   __shared__ double s_blk[kFaceWarps][kMaxM * (kMaxM + 1)];
   __shared__ double s_t[kFaceWarps][kMaxM];
   const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int e = blockIdx.x * kFaceWarps + w;
-  if (e >= f.n_face) return;
+  const int ei = blockIdx.x * kFaceWarps + w;
+  if (ei >= (faces ? nfaces : f.n_face)) return;
+  const int e = faces ? faces[ei] : ei;
   const int m = 4 * (f.face_p[e] + 1);
   const int nseg = (m <= 8) ? 4 : ((m <= 16) ? 2 : 1);
   const int r = lane % m, sg = lane / m;
@@ -143,6 +149,7 @@ __global__ void __launch_bounds__(32 * kFaceWarps) k_face_op(FaceDev f, const do
     for (int b = 0; b < 5; ++b) {
       const int col = f.k_col[5 * e + b];
       if (col < 0) break;  // unused slots (next to boundary faces) come last
+      if (skip_diag && col == e) continue;
       const int mb = 4 * (f.face_p[col] + 1), n = m * mb;
       // stored block: K (e, col) is m x mb; for K^T, block (col, e) is mb x m
       const double* blk = f.K + (TR ? f.k_tblk[5 * e + b] : f.k_blkoff[5 * e + b]);
@@ -160,10 +167,10 @@ __global__ void __launch_bounds__(32 * kFaceWarps) k_face_op(FaceDev f, const do
       if (act) {
         const double* xc = x + f.lam_off[col];
         if (TR) {
-          for (int c = sg; c < mb; c += nseg) t = fma(sb[c * ld + r], __ldg(xc + c), t);
+          for (int c = sg; c < mb; c += nseg) t = fma(sb[c * ld + r], xc[c], t);
         } else {
           const double* row = sb + r * ld;
-          for (int c = sg; c < mb; c += nseg) t = fma(row[c], __ldg(xc + c), t);
+          for (int c = sg; c < mb; c += nseg) t = fma(row[c], xc[c], t);
         }
       }
       __syncwarp();
@@ -172,12 +179,12 @@ __global__ void __launch_bounds__(32 * kFaceWarps) k_face_op(FaceDev f, const do
   // the nseg partial sums of row r sit in lanes r, r + m, ...
   for (int o = m * (nseg >> 1); o >= m; o >>= 1) t += __shfl_down_sync(0xffffffffu, t, o);
   if (lane < m) {
-    if (mode == 1) t = bvec[lo + lane] - t;
+    if (mode == 1 || mode == 4) t = bvec[lo + lane] - t;
     if (mode == 3) t = bvec[lo + lane];
     s_t[w][lane] = t;
   }
   __syncwarp();
-  if (mode == 2) {
+  if (mode == 2 || mode == 4) {
     if (lane < m) y[lo + lane] = t;
     return;
   }
@@ -285,7 +292,11 @@ struct hdg_solver {
   double* h = nullptr;        // [2 (restart + 1) + 2] device results of k_reduce
   double* coef = nullptr;     // [restart + 1] coefficients from the host
   double* zero = nullptr;     // [n] zeros
+  double* tmp = nullptr;      // [n] work vector of the Gauss-Seidel preconditioner
   double* hpin = nullptr;     // pinned host mirror of h / coef
+  int precond = 0;            // 0 block Jacobi, 1 multicolor block symmetric Gauss-Seidel
+  int* colors = nullptr;      // faces grouped by color
+  std::vector<int> color_off; // [n_colors + 1]
   std::vector<void*> allocs;
 };
 
@@ -296,10 +307,49 @@ hdg_status ck(hdg_ctx* ctx, cudaError_t e, const char* what) {
   return HDG_OK;
 }
 
-void face_op(hdg_solver* S, bool tr, const double* x, const double* b, double* y, int mode, cudaStream_t st) {
-  const int fb = (S->f.n_face + kFaceWarps - 1) / kFaceWarps;
-  if (tr) k_face_op<true><<<fb, 32 * kFaceWarps, 0, st>>>(S->f, x, b, y, mode);
-  else k_face_op<false><<<fb, 32 * kFaceWarps, 0, st>>>(S->f, x, b, y, mode);
+void face_op(hdg_solver* S, bool tr, const double* x, const double* b, double* y, int mode, cudaStream_t st,
+             const int* faces = nullptr, int nfaces = 0, int skip_diag = 0) {
+  const int nf = faces ? nfaces : S->f.n_face;
+  if (nf == 0) return;
+  const int fb = (nf + kFaceWarps - 1) / kFaceWarps;
+  if (tr) k_face_op<true><<<fb, 32 * kFaceWarps, 0, st>>>(S->f, x, b, y, mode, faces, nfaces, skip_diag);
+  else k_face_op<false><<<fb, 32 * kFaceWarps, 0, st>>>(S->f, x, b, y, mode, faces, nfaces, skip_diag);
+}
+
+// z = M^{-1} r for the multicolor block symmetric Gauss-Seidel preconditioner:
+// from z = 0, a forward sweep over the colors, then a backward one; each color
+// is one launch (its faces are mutually uncoupled, so the sweep is exact Gauss-Seidel).
+void sgs_apply(hdg_solver* S, bool tr, const double* r, double* z, cudaStream_t st) {
+  cudaMemsetAsync(z, 0, sizeof(double) * S->n, st);
+  const int nc = (int)S->color_off.size() - 1;
+  for (int pass = 0; pass < 2; ++pass)
+    for (int k = 0; k < nc; ++k) {
+      const int c = pass == 0 ? k : nc - 1 - k;
+      const int o0 = S->color_off[c], o1 = S->color_off[c + 1];
+      face_op(S, tr, z, r, z, 1, st, S->colors + o0, o1 - o0, 1);
+    }
+}
+
+// the preconditioned operator and residual for either preconditioner
+void prec_op(hdg_solver* S, bool tr, const double* v, double* w, cudaStream_t st) {  // w = M^{-1} K v
+  if (S->precond == 0) {
+    face_op(S, tr, v, nullptr, w, 0, st);
+  } else {
+    face_op(S, tr, v, nullptr, S->tmp, 2, st);
+    sgs_apply(S, tr, S->tmp, w, st);
+  }
+}
+void prec_res(hdg_solver* S, bool tr, const double* x, const double* b, double* w, cudaStream_t st) {
+  if (S->precond == 0) {  // w = M^{-1} (b - K x)
+    face_op(S, tr, x, b, w, 1, st);
+  } else {
+    face_op(S, tr, x, b, S->tmp, 4, st);
+    sgs_apply(S, tr, S->tmp, w, st);
+  }
+}
+void prec_rhs(hdg_solver* S, bool tr, const double* b, double* w, cudaStream_t st) {  // w = M^{-1} b
+  if (S->precond == 0) face_op(S, tr, S->zero, b, w, 3, st);
+  else sgs_apply(S, tr, b, w, st);
 }
 
 // out[0..nvec) = V_j . w for j < nvec (device), enqueued on st
@@ -346,14 +396,36 @@ hdg_status hdg_solver_create(hdg_sys* sys, int32_t restart, hdg_solver** out) {
     S->allocs.push_back(*p);
     return true;
   };
-  void *kc, *kb, *kt, *dof, *dinv, *bad, *V, *part, *h, *coef, *zero;
+  void *kc, *kb, *kt, *dof, *dinv, *bad, *V, *part, *h, *coef, *zero, *tmpv, *cols;
+  // greedy coloring: faces of one element (the nonzero blocks of a K row) get different colors
+  std::vector<int> color(M->n_face, -1);
+  int ncol = 0;
+  for (int e = 0; e < M->n_face; ++e) {
+    unsigned used = 0;
+    for (int b = 0; b < 5; ++b) {
+      const int f = M->k_col[5 * e + b];
+      if (f >= 0 && f != e && color[f] >= 0) used |= 1u << color[f];
+    }
+    int c = 0;
+    while (used & (1u << c)) ++c;
+    color[e] = c;
+    ncol = std::max(ncol, c + 1);
+  }
+  std::vector<int> by_color;
+  S->color_off.assign(1, 0);
+  for (int c = 0; c < ncol; ++c) {
+    for (int e = 0; e < M->n_face; ++e)
+      if (color[e] == c) by_color.push_back(e);
+    S->color_off.push_back((int)by_color.size());
+  }
   const size_t nr = (size_t)restart + 1;
   bool ok = alloc(sizeof(int) * M->k_col.size(), &kc) && alloc(sizeof(int64_t) * M->k_blkoff.size(), &kb) &&
             alloc(sizeof(int64_t) * tblk.size(), &kt) &&
             alloc(sizeof(int64_t) * dinv_off.size(), &dof) && alloc(sizeof(double) * tot, &dinv) &&
             alloc(sizeof(int), &bad) && alloc(sizeof(double) * nr * S->n, &V) &&
             alloc(sizeof(double) * nr * S->dot_blocks, &part) && alloc(sizeof(double) * (2 * nr + 2), &h) &&
-            alloc(sizeof(double) * nr, &coef) && alloc(sizeof(double) * S->n, &zero);
+            alloc(sizeof(double) * nr, &coef) && alloc(sizeof(double) * S->n, &zero) &&
+            alloc(sizeof(double) * S->n, &tmpv) && alloc(sizeof(int) * std::max<size_t>(1, by_color.size()), &cols);
   if (!ok || cudaMallocHost((void**)&S->hpin, sizeof(double) * (2 * nr + 2)) != cudaSuccess) {
     for (void* p : S->allocs) cudaFree(p);
     delete S;
@@ -365,6 +437,8 @@ hdg_status hdg_solver_create(hdg_sys* sys, int32_t restart, hdg_solver** out) {
   if (st == HDG_OK) st = ck(ctx, cudaMemcpy(dof, dinv_off.data(), sizeof(int64_t) * dinv_off.size(), cudaMemcpyHostToDevice), "cudaMemcpy");
   if (st == HDG_OK) st = ck(ctx, cudaMemcpy(kt, tblk.data(), sizeof(int64_t) * tblk.size(), cudaMemcpyHostToDevice), "cudaMemcpy");
   if (st == HDG_OK) st = ck(ctx, cudaMemset(zero, 0, sizeof(double) * S->n), "cudaMemset");
+  if (st == HDG_OK && !by_color.empty())
+    st = ck(ctx, cudaMemcpy(cols, by_color.data(), sizeof(int) * by_color.size(), cudaMemcpyHostToDevice), "cudaMemcpy");
   if (st != HDG_OK) {
     for (void* p : S->allocs) cudaFree(p);
     cudaFreeHost(S->hpin);
@@ -386,6 +460,8 @@ hdg_status hdg_solver_create(hdg_sys* sys, int32_t restart, hdg_solver** out) {
   S->h = (double*)h;
   S->coef = (double*)coef;
   S->zero = (double*)zero;
+  S->tmp = (double*)tmpv;
+  S->colors = (int*)cols;
   *out = S;
   return HDG_OK;
 }
@@ -396,6 +472,12 @@ hdg_status hdg_solver_destroy(hdg_solver* S) {
   for (void* p : S->allocs) cudaFree(p);
   if (S->hpin) cudaFreeHost(S->hpin);
   delete S;
+  return HDG_OK;
+}
+
+hdg_status hdg_solver_set_preconditioner(hdg_solver* S, int32_t kind) {
+  if (!S || kind < 0 || kind > 1) return HDG_EINVAL;
+  S->precond = kind;
   return HDG_OK;
 }
 
@@ -428,7 +510,7 @@ hdg_status hdg_trace_solve_ex(hdg_solver* S, const double* rhs, int32_t transpos
   k_bj_invert<<<fb, 32 * kFaceWarps, 0, st>>>(S->f);
   // ||M^-1 E||
   const double* E = rhs ? rhs : S->sys->ds.E;
-  face_op(S, tr, S->zero, E, S->V, 3, st);
+  prec_rhs(S, tr, E, S->V, st);
   multidot(S, S->V, 1, S->V, n, S->h, st);
   int bad = 0;
   if ((rs = ck(ctx, cudaMemcpyAsync(S->hpin, S->h, sizeof(double), cudaMemcpyDeviceToHost, st), "cudaMemcpyAsync")) != HDG_OK) return rs;
@@ -446,7 +528,7 @@ hdg_status hdg_trace_solve_ex(hdg_solver* S, const double* rhs, int32_t transpos
   double rel = 1.0;
   while (true) {
     // r0 = M^-1 (E - K x), beta = ||r0||
-    face_op(S, tr, x, E, S->V, 1, st);
+    prec_res(S, tr, x, E, S->V, st);
     multidot(S, S->V, 1, S->V, n, S->h, st);
     if ((rs = ck(ctx, cudaMemcpyAsync(S->hpin, S->h, sizeof(double), cudaMemcpyDeviceToHost, st), "cudaMemcpyAsync")) != HDG_OK) return rs;
     if ((rs = ck(ctx, cudaStreamSynchronize(st), "cudaStreamSynchronize")) != HDG_OK) return rs;
@@ -460,7 +542,7 @@ hdg_status hdg_trace_solve_ex(hdg_solver* S, const double* rhs, int32_t transpos
     for (int j = 0; j < R && it < max_iter; ++j) {
       double* vj = S->V + (int64_t)j * n;
       double* w = S->V + (int64_t)(j + 1) * n;
-      face_op(S, tr, vj, nullptr, w, 0, st);
+      prec_op(S, tr, vj, w, st);
       // classical Gram-Schmidt, twice
       multidot(S, S->V, j + 1, w, n, S->h, st);
       k_multiaxpy<<<vb, 256, 0, st>>>(S->V, n, j + 1, S->h, -1.0, w, n);

@@ -35,7 +35,7 @@ EXPORTS = ["hdg_create", "hdg_destroy", "hdg_last_error", "hdg_mesh_create", "hd
            "hdg_solver_destroy", "hdg_trace_solve", "hdg_trace_matvec", "hdg_newton_update", "hdg_residual_norm",
            "hdg_sys_set_cfl", "hdg_cfl_law", "hdg_autotune", "hdg_trace_solve_ex", "hdg_adjoint_condense",
            "hdg_adapt_indicators", "hdg_adapt_mark",
-           "hdg_mesh_create_bc"]
+           "hdg_mesh_create_bc", "hdg_solver_set_preconditioner"]
 
 
 class HdgError(RuntimeError):
@@ -125,6 +125,7 @@ def lib(build: bool = True):
         L.hdg_trace_solve.argtypes = [_vp, _vp, ctypes.c_double, ctypes.c_int32, ctypes.POINTER(ctypes.c_int32),
                                       ctypes.POINTER(ctypes.c_double), _vp]
         L.hdg_trace_matvec.argtypes = [_vp, _vp, _vp, ctypes.c_int32, _vp]
+        L.hdg_solver_set_preconditioner.argtypes = [_vp, ctypes.c_int32]
         L.hdg_trace_solve_ex.argtypes = [_vp, _vp, ctypes.c_int32, _vp, ctypes.c_double, ctypes.c_int32,
                                          ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(ctypes.c_double), _vp]
         L.hdg_adjoint_condense.argtypes = [_vp, _vp, _vp, _vp, _vp, _vp]
@@ -180,10 +181,12 @@ def adapt_mark(ctx: "Context", eta2, sensor, code, theta=0.05, eps_s=1e-6, strea
 class Solver:
     """hdg_solver_create / hdg_trace_solve / hdg_trace_matvec: GMRES on the trace system of a System."""
 
-    def __init__(self, system: "System", restart: int = 30):
+    def __init__(self, system: "System", restart: int = 30, precond: int = 0):
+        """precond: 0 block Jacobi, 1 multicolor block symmetric Gauss-Seidel."""
         h = _vp()
         _check(lib().hdg_solver_create(system.h, int(restart), ctypes.byref(h)), system.ctx.h)
         self.h, self.sys = h, system
+        _check(lib().hdg_solver_set_preconditioner(h, int(precond)), system.ctx.h)
 
     def solve(self, dLam, rtol=1e-12, max_iter=500, stream=None, check=True, rhs=None, transpose=False):
         """Solve K dLam = E (or K^T dLam = rhs) in place (dLam holds the initial guess);

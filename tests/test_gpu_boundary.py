@@ -116,8 +116,8 @@ def test_channel_newton_steps_match_oracle_monolithic(ctx):
     solver.close(); sysm.close(); mesh.close()
 
 
-@pytest.mark.parametrize("c0,c1,n0", [(1e6, 1e3, 4), (10.0, 10.0, 3)])
-def test_box_steady_solve_converges(ctx, c0, c1, n0):
+@pytest.mark.parametrize("c0,c1,n0,precond", [(1e6, 1e3, 4, 0), (10.0, 10.0, 3, 0)])
+def test_box_steady_solve_converges(ctx, c0, c1, n0, precond):
     """A steady Newton solve on the GPU: 8,192-element box with far field on all sides (Euler p = 2,
     Mach 0.5 at 10 degrees, density bump): pseudo time with the CFL law of Eq. (cfl) (the paper's
     c0 = 1e6, c1 = 1e3, n0 = 4, and a gentler ramp), GMRES to 1e-11 each step, until the residual has
@@ -127,7 +127,7 @@ def test_box_steady_solve_converges(ctx, c0, c1, n0):
     case, om, U, Lam, dLam, mesh, sysm = _setup(ctx, wl, 1.0)
     dev = torch.device("cuda:0")
     Ut, Lt = torch.from_numpy(U).to(dev), torch.from_numpy(Lam).to(dev)
-    solver = hdg.Solver(sysm, restart=50)
+    solver = hdg.Solver(sysm, restart=50, precond=precond)
     dL = torch.zeros(mesh.lam_len, dtype=torch.float64, device=dev)
     dU = torch.zeros(mesh.u_len, dtype=torch.float64, device=dev)
     cfl, r_prev, r0 = 0.0, None, None

@@ -30,22 +30,24 @@ def setup(ctx, wl, cfl, precision=0):
     return case, om, U, Lam, mesh, sysm, Ut, Lt
 
 
+@pytest.mark.parametrize("precond", [0, 1])
 @pytest.mark.parametrize("name,nx,ny,kw", [("euler_p3_16k", 5, 6, {}), ("ns_mixp_65k", 4, 5, {}),
                                            ("ns_mixp_65k", 5, 5, {"model": 0})])
-def test_trace_solve_matches_dense_oracle_solve(ctx, name, nx, ny, kw):
+def test_trace_solve_matches_dense_oracle_solve(ctx, name, nx, ny, kw, precond):
     """GMRES + block Jacobi on the GPU's K, E against the dense LU solve of the oracle's K, E."""
     from paper_1308_3995_gb300 import hdg
     wl = G.small_variant(G.WORKLOADS[name], nx, ny, **kw)
     cfl = 10.0
     case, om, U, Lam, mesh, sysm, Ut, Lt = setup(ctx, wl, cfl)
     sysm.condense(Ut, Lt)
-    solver = hdg.Solver(sysm, restart=30)
+    solver = hdg.Solver(sysm, restart=30, precond=precond)
     x = torch.zeros(mesh.lam_len, dtype=torch.float64, device="cuda:0")
     it, rel = solver.solve(x, rtol=1e-13, max_iter=400)
     r = om.condense(oracle_params(wl, cfl), U, Lam)
     ref = O.dense_solve(om.dense_K(r["K"]), r["E"])
     err = rel_err(x.cpu().numpy(), ref)
-    print(wl.name, "iterations", it, "rel. residual", f"{rel:.1e}", "error vs dense oracle", f"{err:.1e}")
+    print(wl.name, ["block Jacobi", "block SGS"][precond], "iterations", it, "rel. residual", f"{rel:.1e}",
+          "error vs dense oracle", f"{err:.1e}")
     assert rel <= 1e-13 and err < 1e-10
     # the matrix-vector product against the dense oracle matrix
     v = torch.from_numpy(np.random.default_rng(3).standard_normal(mesh.lam_len)).to("cuda:0")
@@ -154,7 +156,8 @@ def test_trace_solve_reports_timeout_and_singular_blocks(ctx):
                                                      ("euler_p3_16k", 3, 3, {}, 0),
                                                      ("ns_mixp_65k", 3, 4, {"model": 0}, 0),
                                                      ("euler_p3_16k", 3, 3, {}, 1)])
-def test_hybridized_adjoint_matches_transposed_monolithic_solve(ctx, name, nx, ny, kw, precision):
+@pytest.mark.parametrize("precond", [0, 1])
+def test_hybridized_adjoint_matches_transposed_monolithic_solve(ctx, name, nx, ny, kw, precision, precond):
     """Sec. 4.2: the adjoint of the Newton matrix (pseudo-time mass included, CFL 10) with right-hand
     side [F~; 0]: GPU adjoint local solves, E~ = -X_B^T F~, GMRES on K^T, reconstruction -- against
     the dense solve of the transposed monolithic Jacobian of the oracle (complex step)."""
@@ -167,7 +170,7 @@ def test_hybridized_adjoint_matches_transposed_monolithic_solve(ctx, name, nx, n
     Ftt = torch.from_numpy(Ft).to("cuda:0")
     primal.condense(Ut, Lt)
     adj.adjoint_condense(primal, Ut, Lt, Ftt)
-    solver = hdg.Solver(primal, restart=40)
+    solver = hdg.Solver(primal, restart=40, precond=precond)
     lt = torch.zeros(mesh.lam_len, dtype=torch.float64, device="cuda:0")
     ut = torch.zeros(mesh.u_len, dtype=torch.float64, device="cuda:0")
     it, rel = solver.solve(lt, rtol=1e-14, max_iter=1000, rhs=adj.views()["E"], transpose=True)
