@@ -127,7 +127,7 @@ __global__ void __launch_bounds__(32 * kFaceWarps) k_bj_invert(FaceDev f) {
 // not HBM, bounds a binary64 product of 0.25 flop per byte, so idle lanes
 // would cost time directly.
 // TR: the same with K^T (block (k_col[5e+b], e) transposed) and Dinv^T.
-template <bool TR>
+template <bool TR, bool INPLACE>
 __global__ void __launch_bounds__(32 * kFaceWarps) k_face_op(FaceDev f, const double* x,
                                                                const double* __restrict__ bvec, double* y,
                                                                int mode, const int* __restrict__ faces, int nfaces,
@@ -166,11 +166,12 @@ __global__ void __launch_bounds__(32 * kFaceWarps) k_face_op(FaceDev f, const do
       __syncwarp();
       if (act) {
         const double* xc = x + f.lam_off[col];
+        // in place (a Gauss-Seidel sweep) x is written by this launch: no read-only cache path
         if (TR) {
-          for (int c = sg; c < mb; c += nseg) t = fma(sb[c * ld + r], xc[c], t);
+          for (int c = sg; c < mb; c += nseg) t = fma(sb[c * ld + r], INPLACE ? xc[c] : __ldg(xc + c), t);
         } else {
           const double* row = sb + r * ld;
-          for (int c = sg; c < mb; c += nseg) t = fma(row[c], xc[c], t);
+          for (int c = sg; c < mb; c += nseg) t = fma(row[c], INPLACE ? xc[c] : __ldg(xc + c), t);
         }
       }
       __syncwarp();
@@ -312,8 +313,14 @@ void face_op(hdg_solver* S, bool tr, const double* x, const double* b, double* y
   const int nf = faces ? nfaces : S->f.n_face;
   if (nf == 0) return;
   const int fb = (nf + kFaceWarps - 1) / kFaceWarps;
-  if (tr) k_face_op<true><<<fb, 32 * kFaceWarps, 0, st>>>(S->f, x, b, y, mode, faces, nfaces, skip_diag);
-  else k_face_op<false><<<fb, 32 * kFaceWarps, 0, st>>>(S->f, x, b, y, mode, faces, nfaces, skip_diag);
+  const bool inplace = x == y;
+  if (tr) {
+    if (inplace) k_face_op<true, true><<<fb, 32 * kFaceWarps, 0, st>>>(S->f, x, b, y, mode, faces, nfaces, skip_diag);
+    else k_face_op<true, false><<<fb, 32 * kFaceWarps, 0, st>>>(S->f, x, b, y, mode, faces, nfaces, skip_diag);
+  } else {
+    if (inplace) k_face_op<false, true><<<fb, 32 * kFaceWarps, 0, st>>>(S->f, x, b, y, mode, faces, nfaces, skip_diag);
+    else k_face_op<false, false><<<fb, 32 * kFaceWarps, 0, st>>>(S->f, x, b, y, mode, faces, nfaces, skip_diag);
+  }
 }
 
 // z = M^{-1} r for the multicolor block symmetric Gauss-Seidel preconditioner:
