@@ -369,3 +369,72 @@ def dense_solve(A, b):
     if lib().orc_dense_solve(A.shape[0], _d(A), _d(x)) != 0:
         raise RuntimeError("singular")
     return x
+
+
+# ----------------------------------------------------------------------------- block ILU(0)
+# The paper preconditions GMRES on the trace system with incomplete LU (Sec. 3.4, the
+# paragraph after Eq. hybridsystem).  The oracle below is the textbook block ILU(0): the
+# IKJ form of Gaussian elimination with blocks as entries, fill kept only where the block
+# pattern of the matrix has a block (Saad, Iterative Methods for Sparse Linear Systems,
+# 2nd ed., Sec. 10.3), in a caller-given elimination order of the block rows.
+def trace_pattern(mesh) -> set:
+    """Block pattern of the trace matrix: the pairs (face, face) that share an element."""
+    P = set()
+    for f in range(mesh.n_face):
+        for b in range(5):
+            c = int(mesh.k_col[f, b])
+            if c >= 0:
+                P.add((f, c))
+    return P
+
+
+def block_ilu0(A, offs, pattern, order):
+    """Block ILU(0) of the dense block matrix ``A`` (block row/column b spans
+    ``offs[b]:offs[b+1]``) eliminated in the block order ``order``.
+
+    Returns ``(L, U, perm)``: with ``perm`` the scalar permutation that lists the
+    blocks in ``order``, ``L`` (identity diagonal blocks, blocks only below) and
+    ``U`` (blocks on and above the diagonal) factor ``A[perm][:, perm]``
+    incompletely: (L U)_ij = A_ij on every block (i, j) of ``pattern``."""
+    A = _f64(A)
+    nb = len(offs) - 1
+    pos = {b: i for i, b in enumerate(order)}
+    size = [int(offs[b + 1] - offs[b]) for b in order]
+    po = np.concatenate([[0], np.cumsum(size)]).astype(np.int64)
+    perm = np.concatenate([np.arange(offs[b], offs[b + 1]) for b in order]).astype(np.int64)
+    W = A[np.ix_(perm, perm)].copy()
+    row = [[] for _ in range(nb)]              # pattern of each permuted block row
+    for (i, j) in pattern:
+        row[pos[i]].append(pos[j])
+    rows = [set(r) for r in row]
+
+    def B(i, j):
+        return (slice(po[i], po[i + 1]), slice(po[j], po[j + 1]))
+
+    for i in range(1, nb):
+        for k in sorted(c for c in rows[i] if c < i):
+            W[B(i, k)] = W[B(i, k)] @ np.linalg.inv(W[B(k, k)])
+            for j in sorted(c for c in rows[i] if c > k):
+                if j in rows[k]:
+                    W[B(i, j)] -= W[B(i, k)] @ W[B(k, j)]
+    L = np.eye(len(perm))
+    U = np.zeros_like(W)
+    for i in range(nb):
+        for j in rows[i]:
+            if j < i:
+                L[B(i, j)] = W[B(i, j)]
+            else:
+                U[B(i, j)] = W[B(i, j)]
+    return L, U, perm
+
+
+def block_ilu0_apply(L, U, perm, r, transpose=False):
+    """z = M^{-1} r (or M^{-T} r) for the preconditioner M = P^T L U P of ``block_ilu0``."""
+    rp = _f64(r)[perm]
+    if transpose:
+        zp = np.linalg.solve(L.T, np.linalg.solve(U.T, rp))
+    else:
+        zp = np.linalg.solve(U, np.linalg.solve(L, rp))
+    z = np.empty_like(zp)
+    z[perm] = zp
+    return z

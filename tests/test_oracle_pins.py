@@ -857,3 +857,110 @@ def test_box_free_stream_and_regular_pure_newton():
     dUc = m.recover(r["X"], dLc)
     assert np.abs(dLc - dL).max() < 1e-10 * np.abs(dL).max()
     assert np.abs(dUc - dU).max() < 1e-10 * np.abs(dU).max()
+
+
+# ----------------------------------------------------------------------------- block ILU(0)
+def _face_graph_matrix(name, nx, ny, seed, **kw):
+    """A random matrix on the trace pattern of a small mesh (diagonal blocks shifted so the
+    incomplete factorization has nonsingular pivots), with its block offsets and pattern."""
+    _, _, m, _ = _case(name, nx, ny, **kw)
+    offs = np.asarray(m.lam_off[:m.n_face + 1], dtype=np.int64)
+    P = O.trace_pattern(m)
+    rng = np.random.default_rng(seed)
+    A = np.zeros((m.lam_len, m.lam_len))
+    for (i, j) in P:
+        blk = rng.standard_normal((offs[i + 1] - offs[i], offs[j + 1] - offs[j]))
+        if i == j:
+            blk += 8.0 * np.eye(blk.shape[0])
+        A[offs[i]:offs[i + 1], offs[j]:offs[j + 1]] = blk
+    return m, offs, P, A
+
+
+def _greedy_colors(m):
+    color = -np.ones(m.n_face, dtype=np.int64)
+    for e in range(m.n_face):
+        used = {int(color[c]) for c in m.k_col[e] if c >= 0 and c != e and color[c] >= 0}
+        k = 0
+        while k in used:
+            k += 1
+        color[e] = k
+    return color
+
+
+@pytest.mark.parametrize("name,nx,ny,kw", [("euler_p1_256", 3, 4, {}), ("ns_mixp_65k", 3, 3, {"model": 0}),
+                                           ("euler_channel_8k", 3, 3, {"p": 1})])
+def test_block_ilu0_reproduces_matrix_on_its_pattern(name, nx, ny, kw):
+    """The defining property of ILU(0): L U equals A on every block of A's pattern (and only
+    there: the trace graph has cycles, so the dropped fill is nonzero); L is unit block lower,
+    U block upper, in the elimination order (Sec. 3.4 preconditioner; Saad Sec. 10.3)."""
+    m, offs, P, A = _face_graph_matrix(name, nx, ny, 11, **kw)
+    order = np.random.default_rng(12).permutation(m.n_face)
+    L, U, perm = O.block_ilu0(A, offs, P, order)
+    Ap, M = A[np.ix_(perm, perm)], L @ U
+    assert np.allclose(np.diag(L), 1.0) and np.abs(np.triu(L, 1)).max() == 0.0
+    pos = {int(b): i for i, b in enumerate(order)}
+    po = np.concatenate([[0], np.cumsum([offs[b + 1] - offs[b] for b in order])])
+    dropped = 0.0
+    for i in range(m.n_face):
+        for j in range(m.n_face):
+            sl = (slice(po[i], po[i + 1]), slice(po[j], po[j + 1]))
+            if (int(order[i]), int(order[j])) in P:
+                assert np.abs(M[sl] - Ap[sl]).max() <= 1e-12 * np.abs(Ap[sl]).max()
+            else:
+                dropped = max(dropped, np.abs(M[sl]).max())
+                assert np.abs(L[sl]).max() == 0.0 and np.abs(U[sl]).max() == 0.0
+            if j < i:
+                assert np.abs(U[sl]).max() == 0.0
+    assert dropped > 1e-3
+
+
+def test_block_ilu0_is_exact_without_fill():
+    """A block-tridiagonal matrix in its natural order has no fill: ILU(0) is the exact block
+    LU, and M^{-1} r is A^{-1} r (mixed block sizes 4..20 as on a p-mixed trace)."""
+    rng = np.random.default_rng(4)
+    sizes = [4, 8, 12, 16, 20, 8, 4]
+    offs = np.concatenate([[0], np.cumsum(sizes)])
+    P = {(i, j) for i in range(len(sizes)) for j in range(len(sizes)) if abs(i - j) <= 1}
+    A = np.zeros((offs[-1], offs[-1]))
+    for (i, j) in P:
+        A[offs[i]:offs[i + 1], offs[j]:offs[j + 1]] = rng.standard_normal((sizes[i], sizes[j])) + \
+            (6.0 * np.eye(sizes[i]) if i == j else 0.0)
+    L, U, perm = O.block_ilu0(A, offs, P, list(range(len(sizes))))
+    r = rng.standard_normal(offs[-1])
+    assert np.abs(O.block_ilu0_apply(L, U, perm, r) - np.linalg.solve(A, r)).max() < 1e-12
+    assert np.abs(O.block_ilu0_apply(L, U, perm, r, transpose=True) - np.linalg.solve(A.T, r)).max() < 1e-12
+
+
+def test_block_ilu0_of_transpose_is_transposed_preconditioner():
+    """ILU(0) on a symmetric pattern is unique given the order, so the incomplete factors of
+    A^T are the transposed ones (up to block-diagonal scaling): M(A^T) = M(A)^T.  The adjoint
+    solve (Sec. 4.2) applies M^{-T} from the factors of K."""
+    m, offs, P, A = _face_graph_matrix("euler_p1_256", 3, 4, 21)
+    order = np.random.default_rng(22).permutation(m.n_face)
+    L, U, perm = O.block_ilu0(A, offs, P, order)
+    Lt, Ut, permt = O.block_ilu0(A.T, offs, {(j, i) for (i, j) in P}, order)
+    r = np.random.default_rng(23).standard_normal(m.lam_len)
+    a = O.block_ilu0_apply(L, U, perm, r, transpose=True)
+    b = O.block_ilu0_apply(Lt, Ut, permt, r)
+    assert np.abs(a - b).max() < 1e-12 * np.abs(b).max()
+
+
+def test_block_ilu0_depends_only_on_the_color_sequence():
+    """Faces of one color share no element, so their trace blocks are uncoupled: any
+    elimination order that lists the colors in the same sequence gives the same incomplete
+    factorization (to rounding).  This is what lets a color be factored in parallel."""
+    m, offs, P, A = _face_graph_matrix("ns_mixp_65k", 3, 4, 31, model=0)
+    color = _greedy_colors(m)
+    assert all(color[i] != color[j] for (i, j) in P if i != j)
+    rng = np.random.default_rng(32)
+    orders = []
+    for _ in range(2):
+        key = color * m.n_face + rng.permutation(m.n_face)
+        orders.append(np.argsort(key, kind="stable"))
+    r = rng.standard_normal(m.lam_len)
+    z = [O.block_ilu0_apply(*O.block_ilu0(A, offs, P, o), r) for o in orders]
+    assert np.abs(z[0] - z[1]).max() < 1e-12 * np.abs(z[0]).max()
+    # a different color sequence is a different preconditioner
+    key = (color.max() - color) * m.n_face + np.arange(m.n_face)
+    z2 = O.block_ilu0_apply(*O.block_ilu0(A, offs, P, np.argsort(key, kind="stable")), r)
+    assert np.abs(z2 - z[0]).max() > 1e-6 * np.abs(z[0]).max()
