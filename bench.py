@@ -282,9 +282,10 @@ class Measured:
 
 def solve_section(ctx, wl, dev, flush, stream, cfl=10.0, rtol=1e-10, reps=3):
     """One pseudo-transient Newton step with the GPU trace solve (Sec. 3.3/3.4): condensation at
-    the given CFL, GMRES (block Jacobi, then multicolor block symmetric Gauss-Seidel) on
-    K dLambda = E, reconstruction, update; plus the bandwidth of the trace matrix-vector product
-    (the K values stream once)."""
+    the given CFL, GMRES (block Jacobi, multicolor block symmetric Gauss-Seidel, then block
+    ILU(0) in the multicolor order) on K dLambda = E, reconstruction, update; plus the bandwidth
+    of the trace matrix-vector product (the K values stream once) and the ILU(0) factorization
+    and application times."""
     import torch
 
     from paper_1308_3995_gb300 import hdg
@@ -293,7 +294,7 @@ def solve_section(ctx, wl, dev, flush, stream, cfl=10.0, rtol=1e-10, reps=3):
     x = torch.zeros(m.mesh.lam_len, dtype=torch.float64, device=dev)
     y = torch.empty_like(x)
     out = {"workload": wl.name, "cfl": cfl, "rtol": rtol, "restart": 30}
-    for precond, nm in ((0, "block_jacobi"), (1, "block_sgs")):
+    for precond, nm in ((0, "block_jacobi"), (1, "block_sgs"), (2, "block_ilu0")):
         solver = hdg.Solver(m.sys, restart=30, precond=precond)
         res = []
         for r in range(reps + 1):
@@ -325,6 +326,19 @@ def solve_section(ctx, wl, dev, flush, stream, cfl=10.0, rtol=1e-10, reps=3):
             mv_s = ev0.elapsed_time(ev1) * 1e-3 / nmv
             out["matvec"] = {"k_mb": k_bytes / 1e6, "ms": 1e3 * mv_s, "k_gbs": k_bytes / mv_s / 1e9,
                              "frac_of_hbm": k_bytes / mv_s / 1e9 / HBM_PEAK_GBS}
+        if precond == 2:
+            # factorization (copy of K + one launch per color) and one application M^{-1} r
+            ev0, ev1, ev2 = (torch.cuda.Event(enable_timing=True) for _ in range(3))
+            ev0.record(stream)
+            solver.setup(stream)
+            ev1.record(stream)
+            for _ in range(10):
+                solver.precond_apply(x, y, stream)
+            ev2.record(stream)
+            torch.cuda.synchronize()
+            out[nm]["factor_ms"] = ev0.elapsed_time(ev1)
+            out[nm]["apply_ms"] = ev1.elapsed_time(ev2) / 10
+            out[nm]["colors"] = solver.colors()[1]
         solver.close()
     m.close()
     return out
@@ -393,35 +407,36 @@ def steady_section(ctx, dev, flush, stream, name="euler_box_8k", tol=1e-10, c0=1
     from paper_1308_3995_gb300 import inputs as G
     wl = G.WORKLOADS[name]
     m = Measured(ctx, wl, hdg.HDG_FP64, dev, flush)
-    solver = hdg.Solver(m.sys, restart=50, precond=0)
     dL = torch.zeros(m.mesh.lam_len, dtype=torch.float64, device=dev)
-    U, L = m.Ut.clone(), m.Lt.clone()
-    torch.cuda.synchronize()
-    t0 = time.perf_counter()
-    cfl, r_prev, r0, hist, its = 0.0, None, None, [], []
-    for n in range(1, 40):
-        m.sys.condense(U, L, stream)
-        r = m.sys.residual_norm(stream)
-        r0 = r0 or r
-        hist.append(r)
-        if r < tol * r0:
-            break
-        cfl = hdg.cfl_law(n, c0=c0, c1=c1, n0=n0, cfl_prev=cfl, res_prev=r_prev or r, res_cur=r)
-        m.sys.set_cfl(cfl)
-        m.sys.condense(U, L, stream)
-        dL.zero_()
-        it, _ = solver.solve(dL, rtol=1e-11, max_iter=5000, stream=stream)
-        its.append(it)
-        m.sys.recover(dL, m.dUt, stream)
-        m.sys.newton_update(U, L, m.dUt, dL, stream)
-        r_prev = r
-    torch.cuda.synchronize()
     out = {"workload": f"{name}: {m.n_elem} triangles, Euler p={wl.p}, far field on all sides, Mach {wl.mach} "
-                       f"at {wl.aoa} deg + density bump", "cfl_law": {"c0": c0, "c1": c1, "n0": n0},
-           "preconditioner": "block Jacobi",
-           "time_to_solution_s": time.perf_counter() - t0, "newton_steps": len(its),
-           "gmres_iterations": its, "residual_history": hist, "converged": hist[-1] < tol * hist[0]}
-    solver.close()
+                       f"at {wl.aoa} deg + density bump", "cfl_law": {"c0": c0, "c1": c1, "n0": n0}}
+    for precond, nm in ((0, "block_jacobi"), (2, "block_ilu0")):
+        solver = hdg.Solver(m.sys, restart=50, precond=precond)
+        U, L = m.Ut.clone(), m.Lt.clone()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        cfl, r_prev, r0, hist, its = 0.0, None, None, [], []
+        for n in range(1, 40):
+            m.sys.condense(U, L, stream)
+            r = m.sys.residual_norm(stream)
+            r0 = r0 or r
+            hist.append(r)
+            if r < tol * r0:
+                break
+            cfl = hdg.cfl_law(n, c0=c0, c1=c1, n0=n0, cfl_prev=cfl, res_prev=r_prev or r, res_cur=r)
+            m.sys.set_cfl(cfl)
+            m.sys.condense(U, L, stream)
+            dL.zero_()
+            it, _ = solver.solve(dL, rtol=1e-11, max_iter=5000, stream=stream)
+            its.append(it)
+            m.sys.recover(dL, m.dUt, stream)
+            m.sys.newton_update(U, L, m.dUt, dL, stream)
+            r_prev = r
+        torch.cuda.synchronize()
+        out[nm] = {"time_to_solution_s": time.perf_counter() - t0, "newton_steps": len(its),
+                   "gmres_iterations": its, "residual_history": hist, "converged": hist[-1] < tol * hist[0]}
+        solver.close()
+        m.sys.set_cfl(0.0)
     m.close()
     return out
 

@@ -294,9 +294,10 @@ int32_t hdg_sys_launches(const hdg_sys* sys);
 /* ---- Global trace solve and pseudo-transient Newton update (Sec. 3.3, 3.4) ----
  * The paper solves K dLambda = E (Eq. hybridsystem) with preconditioned GMRES
  * (an ILU(n) preconditioner through PETSc).  This library solves it on the GPU
- * with restarted GMRES, left-preconditioned by block Jacobi: M = the diagonal
- * face blocks of K, inverted once per solve (Gauss-Jordan with partial
- * pivoting, binary64).  Arnoldi uses classical Gram-Schmidt with one
+ * with restarted GMRES, left-preconditioned by block Jacobi (default: M = the
+ * diagonal face blocks of K, inverted once per solve by Gauss-Jordan with
+ * partial pivoting), multicolor block SGS or block ILU(0) (see
+ * hdg_solver_set_preconditioner).  Arnoldi uses classical Gram-Schmidt with one
  * re-orthogonalisation pass; the Hessenberg least-squares problem (Givens
  * rotations) is solved on the host.  Everything is binary64. */
 typedef struct hdg_solver hdg_solver;
@@ -315,18 +316,43 @@ hdg_status hdg_solver_destroy(hdg_solver* solver);
  * residual estimate per iteration) and returns the iteration count and the
  * final preconditioned relative residual in *iters / *rel_res (either may be
  * NULL).  Returns HDG_OK when converged, HDG_ETIMEOUT when max_iter was
- * reached first, HDG_ESINGULAR when a diagonal block of K is singular. */
+ * reached first, HDG_ESINGULAR when a pivot block of the preconditioner (a
+ * diagonal block of K; for ILU(0), a modified one) is singular. */
 hdg_status hdg_trace_solve(hdg_solver* solver, double* dLam, double rtol, int32_t max_iter, int32_t* iters,
                            double* rel_res, void* stream);
 
 /* Preconditioner of the trace solve: 0 block Jacobi (default), 1 multicolor
- * block symmetric Gauss-Seidel -- faces colored so that no two faces of one
- * element share a color (at most 5 colors on triangles), then one forward and
- * one backward sweep over the colors, each color's block rows updated in
- * parallel with the diagonal inverses of block Jacobi.  About three times the
- * work of a block-Jacobi application per iteration, far fewer iterations at
- * large CFL.  Applies to both K and K^T. */
+ * block symmetric Gauss-Seidel -- faces colored greedily so that no two faces
+ * of one element share a color, then one forward and one backward sweep over
+ * the colors, each color's block rows updated in parallel with the diagonal
+ * inverses of block Jacobi (about three times the work of a block-Jacobi
+ * application) -- or 2 block ILU(0), the paper's incomplete LU with no fill
+ * level (Sec. 3.4), eliminated in the same multicolor order: rows of one color
+ * are factored in parallel, L_ek = F_ek U_kk^{-1} for the faces k of earlier
+ * colors, F_ej -= L_ek F_kj inside K's block pattern; M = L U is applied by a
+ * forward and a backward sweep over the colors (about twice the work of a
+ * block-Jacobi application).  Kind 2 allocates a copy of K's values, the pivot
+ * inverses and one vector here (HDG_ENOMEM if that fails).  All kinds apply to
+ * both K and K^T (M^{-T} from the same factors).  Returns HDG_EINVAL for any
+ * other kind. */
 hdg_status hdg_solver_set_preconditioner(hdg_solver* solver, int32_t kind);
+
+/* Factor the preconditioner of the solver's kind for the system's current K
+ * (enqueued on `stream`, then `stream` is synchronised).  hdg_trace_solve*
+ * does this itself at every call; it is needed before
+ * hdg_solver_precond_apply.  HDG_ESINGULAR if a pivot block is singular. */
+hdg_status hdg_solver_setup(hdg_solver* solver, void* stream);
+
+/* z = M^{-1} r, or M^{-T} r when transpose != 0, with the preconditioner of the
+ * last hdg_solver_setup or solve (DEVICE vectors [lam_len], r != z; enqueued on
+ * `stream`).  HDG_EINVAL if no factorization of the current kind exists. */
+hdg_status hdg_solver_precond_apply(hdg_solver* solver, const double* r, double* z, int32_t transpose,
+                                    void* stream);
+
+/* The multicolor order: face_color[n_face] (HOST, may be NULL) receives each
+ * face's color (0-based; no two faces of one element share one), *n_colors
+ * (may be NULL) the number of colors. */
+hdg_status hdg_solver_colors(const hdg_solver* solver, int32_t* face_color, int32_t* n_colors);
 
 /* Like hdg_trace_solve, with a right-hand side other than the system's E
  * (DEVICE rhs [lam_len]; NULL: E) and, when transpose != 0, the transposed

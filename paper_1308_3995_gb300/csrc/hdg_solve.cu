@@ -2,14 +2,22 @@
 // pseudo-transient Newton update (Sec. 3.3) on the GPU.
 //
 // The paper uses ILU(n)-preconditioned GMRES from PETSc on the CPU.  Here:
-// restarted GMRES, left-preconditioned by block Jacobi (the inverses of K's
-// diagonal face blocks), binary64 throughout.  Kernels:
+// restarted GMRES, left-preconditioned, binary64 throughout, with one of
+//   0 block Jacobi (the inverses of K's diagonal face blocks),
+//   1 multicolor block symmetric Gauss-Seidel,
+//   2 block ILU(0) in the multicolor order of the faces (faces of one color
+//     share no element, so their rows are uncoupled: each color is factored,
+//     and swept in the triangular solves, by one launch).
+// Kernels:
 //   k_bj_invert   one warp per face: Gauss-Jordan with partial pivoting of the
 //                 face's diagonal block (m = 4 (p_e + 1) <= 20 rows);
+//   k_ilu_row     one warp per face of one color: the face's block row of the
+//                 incomplete factors, then the inverse of its pivot block;
 //   k_face_op     one warp per face: t = (K x)_e (each block staged through
 //                 shared memory with coalesced loads, one lane per row, the
-//                 five blocks of the face row in column order), then, by
-//                 mode, y_e = t, Dinv_e t, Dinv_e (b_e - t) or Dinv_e b_e;
+//                 five blocks of the face row in column order; optionally only
+//                 the blocks of earlier or of later colors), then, by mode,
+//                 y_e = t, Dinv_e t, Dinv_e (b_e - t), Dinv_e b_e or b_e - t;
 //   k_multidot    partial dot products of one vector with up to 8 others per
 //                 block row of the grid, reduced in a fixed order by k_reduce
 //                 (bitwise reproducible);
@@ -47,29 +55,20 @@ struct FaceDev {
   const int64_t* k_blkoff;  // [5 n_face + 1]
   const int64_t* dinv_off;  // [n_face]
   const int64_t* k_tblk;    // [5 n_face]: offset of block (k_col[5e+b], e), for products with K^T
-  const double* K;
+  const int* fcolor;        // [n_face] color of each face in the multicolor order
+  const double* K;          // the matrix (K, or the incomplete factors of the ILU preconditioner)
   double* dinv;
   int* bad;                 // set to 1 if a diagonal block is singular
 };
 
 // ---------------------------------------------------------------- block Jacobi
-__global__ void __launch_bounds__(32 * kFaceWarps) k_bj_invert(FaceDev f) {
-  __shared__ double s_aug[kFaceWarps][kMaxM][2 * kMaxM + 1];
-  const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int e = blockIdx.x * kFaceWarps + w;
-  if (e >= f.n_face) return;
-  const int m = 4 * (f.face_p[e] + 1), m2 = 2 * m;
-  int b = 0;
-  while (b < 4 && f.k_col[5 * e + b] != e) ++b;
-  const double* D = f.K + f.k_blkoff[5 * e + b];
-  double(*a)[2 * kMaxM + 1] = s_aug[w];
-  for (int t = lane; t < m * m2; t += 32) {
-    const int r = t / m2, c = t - r * m2;
-    a[r][c] = (c < m) ? D[r * m + c] : (c - m == r ? 1.0 : 0.0);
-  }
-  __syncwarp();
+// Gauss-Jordan inversion with partial pivoting (largest |a_rk|, first on ties)
+// of the m x m block in the left half of a (the identity in the right half);
+// the inverse is left in columns m .. 2m-1.  One warp, m <= 32; false if the
+// block is singular (the result is then warp-uniform).
+__device__ bool warp_gj_invert(double (*a)[2 * kMaxM + 1], int m, int lane) {
+  const int m2 = 2 * m;
   for (int k = 0; k < m; ++k) {
-    // pivot: largest |a_rk|, r >= k, first on ties (lanes over rows; m <= 32)
     double best = (lane >= k && lane < m) ? fabs(a[lane][k]) : -1.0;
     int bi = lane;
 #pragma unroll
@@ -80,10 +79,7 @@ __global__ void __launch_bounds__(32 * kFaceWarps) k_bj_invert(FaceDev f) {
     }
     best = __shfl_sync(0xffffffffu, best, 0);
     bi = __shfl_sync(0xffffffffu, bi, 0);
-    if (!(best > 0.0)) {
-      if (lane == 0) *f.bad = 1;
-      return;  // the whole warp leaves together (best and bi are warp-uniform)
-    }
+    if (!(best > 0.0)) return false;
     for (int c = lane; c < m2; c += 32) {
       const double t = a[k][c];
       a[k][c] = a[bi][c];
@@ -106,18 +102,136 @@ __global__ void __launch_bounds__(32 * kFaceWarps) k_bj_invert(FaceDev f) {
     }
     __syncwarp();
   }
-  double* out = f.dinv + f.dinv_off[e];
+  return true;
+}
+
+__device__ void load_aug(double (*a)[2 * kMaxM + 1], const double* D, int m, int lane) {
+  const int m2 = 2 * m;
+  for (int t = lane; t < m * m2; t += 32) {
+    const int r = t / m2, c = t - r * m2;
+    a[r][c] = (c < m) ? D[r * m + c] : (c - m == r ? 1.0 : 0.0);
+  }
+  __syncwarp();
+}
+
+__device__ void store_inverse(double (*a)[2 * kMaxM + 1], double* out, int m, int lane) {
   for (int t = lane; t < m * m; t += 32) {
     const int r = t / m, c = t - r * m;
     out[t] = a[r][m + c];
   }
 }
 
+__global__ void __launch_bounds__(32 * kFaceWarps) k_bj_invert(FaceDev f) {
+  __shared__ double s_aug[kFaceWarps][kMaxM][2 * kMaxM + 1];
+  const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int e = blockIdx.x * kFaceWarps + w;
+  if (e >= f.n_face) return;
+  const int m = 4 * (f.face_p[e] + 1);
+  int b = 0;
+  while (b < 4 && f.k_col[5 * e + b] != e) ++b;
+  double(*a)[2 * kMaxM + 1] = s_aug[w];
+  load_aug(a, f.K + f.k_blkoff[5 * e + b], m, lane);
+  if (!warp_gj_invert(a, m, lane)) {
+    if (lane == 0) *f.bad = 1;
+    return;  // the whole warp leaves together
+  }
+  store_inverse(a, f.dinv + f.dinv_off[e], m, lane);
+}
+
+// ---------------------------------------------------------------- block ILU(0)
+// One block row of the incomplete factorization per warp, for the faces of one
+// color (rows of earlier colors are final; rows of one color share no block).
+// F holds K's values before the first color.  For the faces k of earlier
+// colors in row e, in ascending color: L_ek = F_ek U_kk^{-1}, then
+// F_ej -= L_ek F_kj for every block (e, j) whose (k, j) is in the pattern and
+// whose j comes after k (fill outside the pattern is dropped).  Last, the
+// inverse of the modified pivot block F_ee goes to dinv.  Same-color faces k
+// update disjoint blocks of row e, so the order among them does not matter.
+__global__ void __launch_bounds__(32 * kFaceWarps) k_ilu_row(FaceDev f, double* F, const int* __restrict__ faces,
+                                                             int nfaces) {
+  __shared__ double s_aug[kFaceWarps][kMaxM][2 * kMaxM + 1];
+  __shared__ double s_l[kFaceWarps][kMaxM * kMaxM];
+  const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int ei = blockIdx.x * kFaceWarps + w;
+  if (ei >= nfaces) return;
+  const int e = faces[ei];
+  const int m = 4 * (f.face_p[e] + 1);
+  const int ce = f.fcolor[e];
+  int lk[4], lb[4], nl = 0, bd = 0;
+  for (int b = 0; b < 5; ++b) {
+    const int c = f.k_col[5 * e + b];
+    if (c < 0) break;
+    if (c == e) {
+      bd = b;
+      continue;
+    }
+    const int cc = f.fcolor[c];
+    if (cc < ce && nl < 4) {  // insertion by ascending color
+      int t = nl++;
+      while (t > 0 && f.fcolor[lk[t - 1]] > cc) {
+        lk[t] = lk[t - 1];
+        lb[t] = lb[t - 1];
+        --t;
+      }
+      lk[t] = c;
+      lb[t] = b;
+    }
+  }
+  double* su = &s_aug[w][0][0];       // U_kk^{-1} (mk x mk)
+  double* sf = su + kMaxM * kMaxM;    // F_ek, then F_kj
+  double* sl = s_l[w];                // L_ek (m x mk)
+  for (int t = 0; t < nl; ++t) {
+    const int k = lk[t], mk = 4 * (f.face_p[k] + 1), ck = f.fcolor[k];
+    double* Fek = F + f.k_blkoff[5 * e + lb[t]];
+    const double* Uk = f.dinv + f.dinv_off[k];
+    for (int i = lane; i < mk * mk; i += 32) su[i] = Uk[i];
+    for (int i = lane; i < m * mk; i += 32) sf[i] = Fek[i];
+    __syncwarp();
+    for (int i = lane; i < m * mk; i += 32) {
+      const int r = i / mk, c = i - r * mk;
+      double s = 0.0;
+      for (int q = 0; q < mk; ++q) s = fma(sf[r * mk + q], su[q * mk + c], s);
+      sl[i] = s;
+      Fek[i] = s;
+    }
+    __syncwarp();
+    for (int b = 0; b < 5; ++b) {
+      const int j = f.k_col[5 * e + b];
+      if (j < 0) break;
+      if (f.fcolor[j] <= ck) continue;  // k itself and faces before it
+      int tk = 0;                        // slot of j in row k
+      while (tk < 5 && f.k_col[5 * k + tk] != j) ++tk;
+      if (tk == 5) continue;             // (k, j) outside the pattern
+      const int mj = 4 * (f.face_p[j] + 1);
+      const double* Fkj = F + f.k_blkoff[5 * k + tk];
+      double* Fej = F + f.k_blkoff[5 * e + b];
+      for (int i = lane; i < mk * mj; i += 32) sf[i] = Fkj[i];
+      __syncwarp();
+      for (int i = lane; i < m * mj; i += 32) {
+        const int r = i / mj, c = i - r * mj;
+        double s = Fej[i];
+        for (int q = 0; q < mk; ++q) s = fma(-sl[r * mk + q], sf[q * mj + c], s);
+        Fej[i] = s;
+      }
+      __syncwarp();
+    }
+  }
+  double(*a)[2 * kMaxM + 1] = s_aug[w];
+  load_aug(a, F + f.k_blkoff[5 * e + bd], m, lane);
+  if (!warp_gj_invert(a, m, lane)) {
+    if (lane == 0) *f.bad = 1;
+    return;
+  }
+  store_inverse(a, f.dinv + f.dinv_off[e], m, lane);
+}
+
 // mode: 0 y = Dinv K x, 1 y = Dinv (b - K x), 2 y = K x, 3 y = Dinv b, 4 y = b - K x.
 // faces (may be null): the list of faces to process (one warp each), else all;
 // skip_diag: leave the diagonal block out of K x (a Gauss-Seidel sweep over
 // one color, in place: x and y may be the same vector, as no two faces of a
-// color are coupled).
+// color are coupled); tri: 1 only the blocks of faces of earlier colors, 2
+// only those of later colors (the triangular solves of the ILU
+// preconditioner, in place over one color as well).
 // Each block of the face row is staged through shared memory with coalesced
 // loads (the warp reads the m x mb row-major block as one contiguous run; rows
 // padded to mb + 1 against bank conflicts).  The products then use every lane
@@ -131,7 +245,7 @@ template <bool TR, bool INPLACE>
 __global__ void __launch_bounds__(32 * kFaceWarps) k_face_op(FaceDev f, const double* x,
                                                                const double* __restrict__ bvec, double* y,
                                                                int mode, const int* __restrict__ faces, int nfaces,
-                                                               int skip_diag) {
+                                                               int skip_diag, int tri) {
   __shared__ double s_blk[kFaceWarps][kMaxM * (kMaxM + 1)];
   __shared__ double s_t[kFaceWarps][kMaxM];
   const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -143,6 +257,7 @@ __global__ void __launch_bounds__(32 * kFaceWarps) k_face_op(FaceDev f, const do
   const int r = lane % m, sg = lane / m;
   const bool act = sg < nseg;
   const int64_t lo = f.lam_off[e];
+  const int ce = tri ? f.fcolor[e] : 0;
   double* sb = s_blk[w];
   double t = 0.0;
   if (mode != 3) {
@@ -150,6 +265,10 @@ __global__ void __launch_bounds__(32 * kFaceWarps) k_face_op(FaceDev f, const do
       const int col = f.k_col[5 * e + b];
       if (col < 0) break;  // unused slots (next to boundary faces) come last
       if (skip_diag && col == e) continue;
+      if (tri) {
+        const int cc = f.fcolor[col];
+        if (tri == 1 ? cc >= ce : cc <= ce) continue;
+      }
       const int mb = 4 * (f.face_p[col] + 1), n = m * mb;
       // stored block: K (e, col) is m x mb; for K^T, block (col, e) is mb x m
       const double* blk = f.K + (TR ? f.k_tblk[5 * e + b] : f.k_blkoff[5 * e + b]);
@@ -293,11 +412,18 @@ struct hdg_solver {
   double* h = nullptr;        // [2 (restart + 1) + 2] device results of k_reduce
   double* coef = nullptr;     // [restart + 1] coefficients from the host
   double* zero = nullptr;     // [n] zeros
-  double* tmp = nullptr;      // [n] work vector of the Gauss-Seidel preconditioner
+  double* tmp = nullptr;      // [n] work vector of the Gauss-Seidel and ILU preconditioners
+  double* tmp2 = nullptr;     // [n] second work vector of the ILU preconditioner
   double* hpin = nullptr;     // pinned host mirror of h / coef
-  int precond = 0;            // 0 block Jacobi, 1 multicolor block symmetric Gauss-Seidel
+  int precond = 0;            // 0 block Jacobi, 1 multicolor block SGS, 2 block ILU(0)
+  bool factored = false;      // a setup has been enqueued for the current kind
   int* colors = nullptr;      // faces grouped by color
   std::vector<int> color_off; // [n_colors + 1]
+  std::vector<int> fcolor;    // host copy of the face colors
+  FaceDev fi{};               // the ILU factors: values F (K's layout) and pivot inverses
+  double* F = nullptr;
+  int64_t k_vals = 0;         // doubles in K
+  int64_t dinv_len = 0;       // doubles in the pivot inverses
   std::vector<void*> allocs;
 };
 
@@ -308,18 +434,18 @@ hdg_status ck(hdg_ctx* ctx, cudaError_t e, const char* what) {
   return HDG_OK;
 }
 
-void face_op(hdg_solver* S, bool tr, const double* x, const double* b, double* y, int mode, cudaStream_t st,
-             const int* faces = nullptr, int nfaces = 0, int skip_diag = 0) {
-  const int nf = faces ? nfaces : S->f.n_face;
+void face_op(const FaceDev& fd, bool tr, const double* x, const double* b, double* y, int mode, cudaStream_t st,
+             const int* faces = nullptr, int nfaces = 0, int skip_diag = 0, int tri = 0) {
+  const int nf = faces ? nfaces : fd.n_face;
   if (nf == 0) return;
   const int fb = (nf + kFaceWarps - 1) / kFaceWarps;
   const bool inplace = x == y;
   if (tr) {
-    if (inplace) k_face_op<true, true><<<fb, 32 * kFaceWarps, 0, st>>>(S->f, x, b, y, mode, faces, nfaces, skip_diag);
-    else k_face_op<true, false><<<fb, 32 * kFaceWarps, 0, st>>>(S->f, x, b, y, mode, faces, nfaces, skip_diag);
+    if (inplace) k_face_op<true, true><<<fb, 32 * kFaceWarps, 0, st>>>(fd, x, b, y, mode, faces, nfaces, skip_diag, tri);
+    else k_face_op<true, false><<<fb, 32 * kFaceWarps, 0, st>>>(fd, x, b, y, mode, faces, nfaces, skip_diag, tri);
   } else {
-    if (inplace) k_face_op<false, true><<<fb, 32 * kFaceWarps, 0, st>>>(S->f, x, b, y, mode, faces, nfaces, skip_diag);
-    else k_face_op<false, false><<<fb, 32 * kFaceWarps, 0, st>>>(S->f, x, b, y, mode, faces, nfaces, skip_diag);
+    if (inplace) k_face_op<false, true><<<fb, 32 * kFaceWarps, 0, st>>>(fd, x, b, y, mode, faces, nfaces, skip_diag, tri);
+    else k_face_op<false, false><<<fb, 32 * kFaceWarps, 0, st>>>(fd, x, b, y, mode, faces, nfaces, skip_diag, tri);
   }
 }
 
@@ -333,30 +459,73 @@ void sgs_apply(hdg_solver* S, bool tr, const double* r, double* z, cudaStream_t 
     for (int k = 0; k < nc; ++k) {
       const int c = pass == 0 ? k : nc - 1 - k;
       const int o0 = S->color_off[c], o1 = S->color_off[c + 1];
-      face_op(S, tr, z, r, z, 1, st, S->colors + o0, o1 - o0, 1);
+      face_op(S->f, tr, z, r, z, 1, st, S->colors + o0, o1 - o0, 1);
     }
 }
 
-// the preconditioned operator and residual for either preconditioner
-void prec_op(hdg_solver* S, bool tr, const double* v, double* w, cudaStream_t st) {  // w = M^{-1} K v
+// z = (L U)^{-1} r, or (L U)^{-T} r, with the block ILU(0) factors: a forward
+// sweep over the colors into tmp2 (L y = r: y_e = r_e - sum of L_ek y_k over
+// earlier colors; transposed, U^T y = r), then a backward one into z
+// (U z = y: z_e = U_ee^{-1} (y_e - sum of U_ej z_j over later colors;
+// transposed, L^T z = y).  r and z must not be tmp2.
+void ilu_apply(hdg_solver* S, bool tr, const double* r, double* z, cudaStream_t st) {
+  const int nc = (int)S->color_off.size() - 1;
+  for (int c = 0; c < nc; ++c) {
+    const int o0 = S->color_off[c], o1 = S->color_off[c + 1];
+    face_op(S->fi, tr, S->tmp2, r, S->tmp2, tr ? 1 : 4, st, S->colors + o0, o1 - o0, 0, 1);
+  }
+  for (int c = nc - 1; c >= 0; --c) {
+    const int o0 = S->color_off[c], o1 = S->color_off[c + 1];
+    face_op(S->fi, tr, z, S->tmp2, z, tr ? 4 : 1, st, S->colors + o0, o1 - o0, 0, 2);
+  }
+}
+
+// w = M^{-1} b for the solver's preconditioner
+void prec_rhs(hdg_solver* S, bool tr, const double* b, double* w, cudaStream_t st) {
+  if (S->precond == 0) face_op(S->f, tr, S->zero, b, w, 3, st);
+  else if (S->precond == 1) sgs_apply(S, tr, b, w, st);
+  else ilu_apply(S, tr, b, w, st);
+}
+// w = M^{-1} K v (block Jacobi: one fused launch)
+void prec_op(hdg_solver* S, bool tr, const double* v, double* w, cudaStream_t st) {
   if (S->precond == 0) {
-    face_op(S, tr, v, nullptr, w, 0, st);
+    face_op(S->f, tr, v, nullptr, w, 0, st);
   } else {
-    face_op(S, tr, v, nullptr, S->tmp, 2, st);
-    sgs_apply(S, tr, S->tmp, w, st);
+    face_op(S->f, tr, v, nullptr, S->tmp, 2, st);
+    prec_rhs(S, tr, S->tmp, w, st);
   }
 }
+// w = M^{-1} (b - K x)
 void prec_res(hdg_solver* S, bool tr, const double* x, const double* b, double* w, cudaStream_t st) {
-  if (S->precond == 0) {  // w = M^{-1} (b - K x)
-    face_op(S, tr, x, b, w, 1, st);
+  if (S->precond == 0) {
+    face_op(S->f, tr, x, b, w, 1, st);
   } else {
-    face_op(S, tr, x, b, S->tmp, 4, st);
-    sgs_apply(S, tr, S->tmp, w, st);
+    face_op(S->f, tr, x, b, S->tmp, 4, st);
+    prec_rhs(S, tr, S->tmp, w, st);
   }
 }
-void prec_rhs(hdg_solver* S, bool tr, const double* b, double* w, cudaStream_t st) {  // w = M^{-1} b
-  if (S->precond == 0) face_op(S, tr, S->zero, b, w, 3, st);
-  else sgs_apply(S, tr, b, w, st);
+
+// enqueue the factorization of the preconditioner for the current K; a
+// singular pivot block sets f.bad (cleared first)
+hdg_status setup_enqueue(hdg_solver* S, cudaStream_t st) {
+  hdg_ctx* ctx = S->sys->ctx;
+  hdg_status rs;
+  if ((rs = ck(ctx, cudaMemsetAsync(S->f.bad, 0, sizeof(int), st), "cudaMemsetAsync")) != HDG_OK) return rs;
+  if (S->precond == 2) {
+    if ((rs = ck(ctx, cudaMemcpyAsync(S->F, S->f.K, sizeof(double) * S->k_vals, cudaMemcpyDeviceToDevice, st),
+                 "cudaMemcpyAsync")) != HDG_OK)
+      return rs;
+    const int nc = (int)S->color_off.size() - 1;
+    for (int c = 0; c < nc; ++c) {
+      const int o0 = S->color_off[c], n = S->color_off[c + 1] - o0;
+      if (n > 0) k_ilu_row<<<(n + kFaceWarps - 1) / kFaceWarps, 32 * kFaceWarps, 0, st>>>(S->fi, S->F, S->colors + o0, n);
+    }
+  } else {
+    k_bj_invert<<<(S->f.n_face + kFaceWarps - 1) / kFaceWarps, 32 * kFaceWarps, 0, st>>>(S->f);
+  }
+  if ((rs = ck(ctx, cudaGetLastError(), "preconditioner setup")) != HDG_OK) return rs;
+  S->factored = true;
+  return HDG_OK;
 }
 
 // out[0..nvec) = V_j . w for j < nvec (device), enqueued on st
@@ -403,7 +572,7 @@ hdg_status hdg_solver_create(hdg_sys* sys, int32_t restart, hdg_solver** out) {
     S->allocs.push_back(*p);
     return true;
   };
-  void *kc, *kb, *kt, *dof, *dinv, *bad, *V, *part, *h, *coef, *zero, *tmpv, *cols;
+  void *kc, *kb, *kt, *dof, *dinv, *bad, *V, *part, *h, *coef, *zero, *tmpv, *cols, *fcol;
   // greedy coloring: faces of one element (the nonzero blocks of a K row) get different colors
   std::vector<int> color(M->n_face, -1);
   int ncol = 0;
@@ -432,7 +601,8 @@ hdg_status hdg_solver_create(hdg_sys* sys, int32_t restart, hdg_solver** out) {
             alloc(sizeof(int), &bad) && alloc(sizeof(double) * nr * S->n, &V) &&
             alloc(sizeof(double) * nr * S->dot_blocks, &part) && alloc(sizeof(double) * (2 * nr + 2), &h) &&
             alloc(sizeof(double) * nr, &coef) && alloc(sizeof(double) * S->n, &zero) &&
-            alloc(sizeof(double) * S->n, &tmpv) && alloc(sizeof(int) * std::max<size_t>(1, by_color.size()), &cols);
+            alloc(sizeof(double) * S->n, &tmpv) && alloc(sizeof(int) * std::max<size_t>(1, by_color.size()), &cols) &&
+            alloc(sizeof(int) * std::max<size_t>(1, color.size()), &fcol);
   if (!ok || cudaMallocHost((void**)&S->hpin, sizeof(double) * (2 * nr + 2)) != cudaSuccess) {
     for (void* p : S->allocs) cudaFree(p);
     delete S;
@@ -446,6 +616,8 @@ hdg_status hdg_solver_create(hdg_sys* sys, int32_t restart, hdg_solver** out) {
   if (st == HDG_OK) st = ck(ctx, cudaMemset(zero, 0, sizeof(double) * S->n), "cudaMemset");
   if (st == HDG_OK && !by_color.empty())
     st = ck(ctx, cudaMemcpy(cols, by_color.data(), sizeof(int) * by_color.size(), cudaMemcpyHostToDevice), "cudaMemcpy");
+  if (st == HDG_OK && !color.empty())
+    st = ck(ctx, cudaMemcpy(fcol, color.data(), sizeof(int) * color.size(), cudaMemcpyHostToDevice), "cudaMemcpy");
   if (st != HDG_OK) {
     for (void* p : S->allocs) cudaFree(p);
     cudaFreeHost(S->hpin);
@@ -459,6 +631,7 @@ hdg_status hdg_solver_create(hdg_sys* sys, int32_t restart, hdg_solver** out) {
   S->f.k_blkoff = (const int64_t*)kb;
   S->f.dinv_off = (const int64_t*)dof;
   S->f.k_tblk = (const int64_t*)kt;
+  S->f.fcolor = (const int*)fcol;
   S->f.K = sys->ds.K;
   S->f.dinv = (double*)dinv;
   S->f.bad = (int*)bad;
@@ -469,6 +642,9 @@ hdg_status hdg_solver_create(hdg_sys* sys, int32_t restart, hdg_solver** out) {
   S->zero = (double*)zero;
   S->tmp = (double*)tmpv;
   S->colors = (int*)cols;
+  S->fcolor = color;
+  S->k_vals = M->k_blkoff.empty() ? 0 : M->k_blkoff.back();
+  S->dinv_len = tot;
   *out = S;
   return HDG_OK;
 }
@@ -483,14 +659,70 @@ hdg_status hdg_solver_destroy(hdg_solver* S) {
 }
 
 hdg_status hdg_solver_set_preconditioner(hdg_solver* S, int32_t kind) {
-  if (!S || kind < 0 || kind > 1) return HDG_EINVAL;
+  if (!S || kind < 0 || kind > 2) return HDG_EINVAL;
+  if (kind == 2 && !S->F) {  // the incomplete factors: a copy of K's values, pivot inverses, a work vector
+    hdg_ctx* ctx = S->sys->ctx;
+    if (cudaSetDevice(ctx->device) != cudaSuccess) return fail(ctx, HDG_ECUDA, "cudaSetDevice failed");
+    void *F = nullptr, *di = nullptr, *t2 = nullptr;
+    if (cudaMalloc(&F, sizeof(double) * std::max<int64_t>(S->k_vals, 2)) != cudaSuccess) F = nullptr;
+    if (F && cudaMalloc(&di, sizeof(double) * std::max<int64_t>(S->dinv_len, 2)) != cudaSuccess) di = nullptr;
+    if (di && cudaMalloc(&t2, sizeof(double) * std::max<int64_t>(S->n, 2)) != cudaSuccess) t2 = nullptr;
+    if (!t2) {
+      if (F) cudaFree(F);
+      if (di) cudaFree(di);
+      return fail(ctx, HDG_ENOMEM, "hdg_solver_set_preconditioner: device allocation of the ILU factors failed");
+    }
+    S->allocs.push_back(F);
+    S->allocs.push_back(di);
+    S->allocs.push_back(t2);
+    S->F = (double*)F;
+    S->tmp2 = (double*)t2;
+    S->fi = S->f;
+    S->fi.K = S->F;
+    S->fi.dinv = (double*)di;
+  }
+  if (kind != S->precond) S->factored = false;
   S->precond = kind;
+  return HDG_OK;
+}
+
+hdg_status hdg_solver_setup(hdg_solver* S, void* stream) {
+  if (!S) return HDG_EINVAL;
+  hdg_ctx* ctx = S->sys->ctx;
+  cudaStream_t st = (cudaStream_t)stream;
+  hdg_status rs;
+  if ((rs = setup_enqueue(S, st)) != HDG_OK) return rs;
+  if ((rs = ck(ctx, cudaMemcpyAsync(S->hpin, S->f.bad, sizeof(int), cudaMemcpyDeviceToHost, st), "cudaMemcpyAsync")) != HDG_OK)
+    return rs;
+  if ((rs = ck(ctx, cudaStreamSynchronize(st), "cudaStreamSynchronize")) != HDG_OK) return rs;
+  int bad = 0;
+  std::memcpy(&bad, S->hpin, sizeof(int));
+  if (bad) {
+    S->factored = false;
+    return fail(ctx, HDG_ESINGULAR, "hdg_solver_setup: a pivot block of the preconditioner is singular");
+  }
+  return HDG_OK;
+}
+
+hdg_status hdg_solver_precond_apply(hdg_solver* S, const double* r, double* z, int32_t transpose, void* stream) {
+  if (!S || !r || !z || r == z) return HDG_EINVAL;
+  hdg_ctx* ctx = S->sys->ctx;
+  if (!S->factored) return fail(ctx, HDG_EINVAL, "hdg_solver_precond_apply: no preconditioner set up for this kind");
+  if (r == S->tmp2 || z == S->tmp2) return HDG_EINVAL;
+  prec_rhs(S, transpose != 0, r, z, (cudaStream_t)stream);
+  return ck(ctx, cudaGetLastError(), "preconditioner apply");
+}
+
+hdg_status hdg_solver_colors(const hdg_solver* S, int32_t* face_color, int32_t* n_colors) {
+  if (!S) return HDG_EINVAL;
+  if (face_color) std::memcpy(face_color, S->fcolor.data(), sizeof(int32_t) * S->fcolor.size());
+  if (n_colors) *n_colors = (int32_t)S->color_off.size() - 1;
   return HDG_OK;
 }
 
 hdg_status hdg_trace_matvec(hdg_solver* S, const double* x, double* y, int32_t transpose, void* stream) {
   if (!S || !x || !y) return HDG_EINVAL;
-  face_op(S, transpose != 0, x, nullptr, y, 2, (cudaStream_t)stream);
+  face_op(S->f, transpose != 0, x, nullptr, y, 2, (cudaStream_t)stream);
   return ck(S->sys->ctx, cudaGetLastError(), "k_face_op");
 }
 
@@ -507,14 +739,12 @@ hdg_status hdg_trace_solve_ex(hdg_solver* S, const double* rhs, int32_t transpos
   cudaStream_t st = (cudaStream_t)stream;
   const int64_t n = S->n;
   const int R = S->restart;
-  const int fb = (S->f.n_face + kFaceWarps - 1) / kFaceWarps;
   const int vb = grid_for(n, 256, 8 * S->sms);
   hdg_status rs;
   if (iters_out) *iters_out = 0;
   if (rel_out) *rel_out = 0.0;
-  // block-Jacobi factors of the current K
-  if ((rs = ck(ctx, cudaMemsetAsync(S->f.bad, 0, sizeof(int), st), "cudaMemsetAsync")) != HDG_OK) return rs;
-  k_bj_invert<<<fb, 32 * kFaceWarps, 0, st>>>(S->f);
+  // the preconditioner's factors of the current K
+  if ((rs = setup_enqueue(S, st)) != HDG_OK) return rs;
   // ||M^-1 E||
   const double* E = rhs ? rhs : S->sys->ds.E;
   prec_rhs(S, tr, E, S->V, st);
@@ -524,7 +754,10 @@ hdg_status hdg_trace_solve_ex(hdg_solver* S, const double* rhs, int32_t transpos
   if ((rs = ck(ctx, cudaMemcpyAsync(&S->hpin[1], S->f.bad, sizeof(int), cudaMemcpyDeviceToHost, st), "cudaMemcpyAsync")) != HDG_OK) return rs;
   if ((rs = ck(ctx, cudaStreamSynchronize(st), "cudaStreamSynchronize")) != HDG_OK) return rs;
   std::memcpy(&bad, &S->hpin[1], sizeof(int));
-  if (bad) return fail(ctx, HDG_ESINGULAR, "hdg_trace_solve: a diagonal block of K is singular");
+  if (bad) {
+    S->factored = false;
+    return fail(ctx, HDG_ESINGULAR, "hdg_trace_solve: a pivot block of the preconditioner is singular");
+  }
   const double bnorm = std::sqrt(S->hpin[0]);
   if (!(bnorm > 0.0)) {  // E = 0: the solution is 0
     if ((rs = ck(ctx, cudaMemsetAsync(x, 0, sizeof(double) * n, st), "cudaMemsetAsync")) != HDG_OK) return rs;

@@ -35,7 +35,8 @@ EXPORTS = ["hdg_create", "hdg_destroy", "hdg_last_error", "hdg_mesh_create", "hd
            "hdg_solver_destroy", "hdg_trace_solve", "hdg_trace_matvec", "hdg_newton_update", "hdg_residual_norm",
            "hdg_sys_set_cfl", "hdg_cfl_law", "hdg_autotune", "hdg_trace_solve_ex", "hdg_adjoint_condense",
            "hdg_adapt_indicators", "hdg_adapt_mark",
-           "hdg_mesh_create_bc", "hdg_solver_set_preconditioner"]
+           "hdg_mesh_create_bc", "hdg_solver_set_preconditioner", "hdg_solver_setup", "hdg_solver_precond_apply",
+           "hdg_solver_colors"]
 
 
 class HdgError(RuntimeError):
@@ -126,6 +127,9 @@ def lib(build: bool = True):
                                       ctypes.POINTER(ctypes.c_double), _vp]
         L.hdg_trace_matvec.argtypes = [_vp, _vp, _vp, ctypes.c_int32, _vp]
         L.hdg_solver_set_preconditioner.argtypes = [_vp, ctypes.c_int32]
+        L.hdg_solver_setup.argtypes = [_vp, _vp]
+        L.hdg_solver_precond_apply.argtypes = [_vp, _vp, _vp, ctypes.c_int32, _vp]
+        L.hdg_solver_colors.argtypes = [_vp, ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(ctypes.c_int32)]
         L.hdg_trace_solve_ex.argtypes = [_vp, _vp, ctypes.c_int32, _vp, ctypes.c_double, ctypes.c_int32,
                                          ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(ctypes.c_double), _vp]
         L.hdg_adjoint_condense.argtypes = [_vp, _vp, _vp, _vp, _vp, _vp]
@@ -181,8 +185,11 @@ def adapt_mark(ctx: "Context", eta2, sensor, code, theta=0.05, eps_s=1e-6, strea
 class Solver:
     """hdg_solver_create / hdg_trace_solve / hdg_trace_matvec: GMRES on the trace system of a System."""
 
+    BLOCK_JACOBI, BLOCK_SGS, BLOCK_ILU0 = 0, 1, 2
+
     def __init__(self, system: "System", restart: int = 30, precond: int = 0):
-        """precond: 0 block Jacobi, 1 multicolor block symmetric Gauss-Seidel."""
+        """precond: 0 block Jacobi, 1 multicolor block symmetric Gauss-Seidel, 2 block ILU(0)
+        in the multicolor order."""
         h = _vp()
         _check(lib().hdg_solver_create(system.h, int(restart), ctypes.byref(h)), system.ctx.h)
         self.h, self.sys = h, system
@@ -202,6 +209,27 @@ class Solver:
     def matvec(self, x, y, stream=None, transpose=False):
         _check(lib().hdg_trace_matvec(self.h, _ptr(x), _ptr(y), int(bool(transpose)), _stream(stream)),
                self.sys.ctx.h)
+
+    def set_preconditioner(self, kind: int):
+        _check(lib().hdg_solver_set_preconditioner(self.h, int(kind)), self.sys.ctx.h)
+
+    def setup(self, stream=None):
+        """Factor the preconditioner for the system's current K (synchronises the stream)."""
+        _check(lib().hdg_solver_setup(self.h, _stream(stream)), self.sys.ctx.h)
+
+    def precond_apply(self, r, z, stream=None, transpose=False):
+        """z = M^{-1} r (or M^{-T} r) with the factors of the last setup or solve."""
+        _check(lib().hdg_solver_precond_apply(self.h, _ptr(r), _ptr(z), int(bool(transpose)), _stream(stream)),
+               self.sys.ctx.h)
+
+    def colors(self):
+        """(face -> color array, number of colors) of the multicolor order."""
+        n = ctypes.c_int32()
+        lib().hdg_solver_colors(self.h, None, ctypes.byref(n))
+        out = np.empty(self.sys.mesh.n_face, dtype=np.int32)
+        _check(lib().hdg_solver_colors(self.h, out.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)), ctypes.byref(n)),
+               self.sys.ctx.h)
+        return out, int(n.value)
 
     def close(self):
         if getattr(self, "h", None):
