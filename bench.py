@@ -441,10 +441,12 @@ def steady_section(ctx, dev, flush, stream, name="euler_box_8k", tol=1e-10, c0=1
     return out
 
 
-def serving_section(ctx, n_requests, seed, max_elems, rates=(0.7,), arena_gb=24):
+def serving_section(ctx, n_requests, seed, max_elems, rates=(0.7,), arena_gb=24, solve=False):
     """Poisson stream through the continuous-batching loop (float-float, 8 slots)
     against the plain loop (binary64, one request at a time), at each load level
-    (fraction of the batched loop's saturated throughput)."""
+    (fraction of the batched loop's saturated throughput).  solve: each request is
+    a whole Newton step with the GPU trace solve to 1e-10 (CFL 10, block ILU(0)),
+    else condensation + reconstruction with a seeded trace update."""
     import torch
 
     from paper_1308_3995_gb300 import hdg
@@ -452,8 +454,8 @@ def serving_section(ctx, n_requests, seed, max_elems, rates=(0.7,), arena_gb=24)
     wls = SV.request_workloads(n_requests, seed=seed, min_elems=1000, max_elems=max_elems)
     reqs = SV.prepare(ctx, [SV.Request(i, 0.0, w) for i, w in enumerate(wls)])
     arena = int(arena_gb) << 30
-    mixed = SV.Server(ctx, arena, slots=8, precision=hdg.HDG_FLOAT2)
-    plain = SV.Server(ctx, arena, slots=1, precision=hdg.HDG_FP64)
+    mixed = SV.Server(ctx, arena, slots=8, precision=hdg.HDG_FLOAT2, solve=solve)
+    plain = SV.Server(ctx, arena, slots=1, precision=hdg.HDG_FP64, solve=solve)
     sat = mixed.run(reqs, "saturated")                       # everything at t = 0
     mean_el = sat.elements / sat.n
     levels = {}
@@ -468,7 +470,12 @@ def serving_section(ctx, n_requests, seed, max_elems, rates=(0.7,), arena_gb=24)
     del mixed, plain
     torch.cuda.empty_cache()
     out = {"requests": len(reqs), "sizes": f"1000..{max_elems} elements log-uniform, Euler/NS 50/50, p 1..4",
+           "request": ("Newton step: condensation at CFL 10, GMRES(30) + block ILU(0) trace solve to 1e-10 "
+                       "relative residual, reconstruction; dU and dLambda back to the host") if solve else
+                      "condensation + reconstruction with a seeded trace update; dU back to the host",
            "saturated_elements_per_s": sat.throughput, "elements_total": sat.elements}
+    if solve:
+        out["saturated_gmres_iterations_median"] = sat.as_dict().get("gmres_iterations_median")
     if len(levels) == 1:
         out.update(next(iter(levels.values())))
     else:
@@ -500,7 +507,10 @@ def run_ours(args, wl, ws, rank, local):
     if args.serving_only:
         line = {"metric": "serving: p50/p99 latency and elements/s, continuous batching (float-float) vs plain FP64",
                 "serving": serving_section(ctx, args.serving_requests, 77, args.serving_max_elems,
-                                           tuple(float(v) for v in args.serving_rates.split(",")), args.serving_arena_gb)}
+                                           tuple(float(v) for v in args.serving_rates.split(",")), args.serving_arena_gb),
+                "serving_with_trace_solve": serving_section(ctx, args.serving_requests, 77, args.serving_max_elems,
+                                                            tuple(float(v) for v in args.serving_rates.split(",")),
+                                                            args.serving_arena_gb, solve=True)}
         if rank == 0:
             print(json.dumps(line), flush=True)
         return 0
@@ -592,6 +602,8 @@ def run_ours(args, wl, ws, rank, local):
         line["steady_solve_bounded_domain"] = steady_section(ctx, dev, flush, stream)
         if args.serving_requests > 0:
             line["serving"] = serving_section(ctx, args.serving_requests, 77, args.serving_max_elems)
+            line["serving_with_trace_solve"] = serving_section(ctx, args.serving_requests, 77, args.serving_max_elems,
+                                                               solve=True)
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
         # the oracle on the host's cores (std::thread over elements): ~20 s of CPU work
         nth = host_threads()

@@ -309,6 +309,21 @@ typedef struct hdg_solver hdg_solver;
 hdg_status hdg_solver_create(hdg_sys* sys, int32_t restart, hdg_solver** out);
 hdg_status hdg_solver_destroy(hdg_solver* solver);
 
+/* The same solver with every device buffer in the caller's DEVICE workspace
+ * (256-byte aligned, at least hdg_solver_workspace_bytes(mesh, restart,
+ * precond) bytes, owned by the caller and untouched after
+ * hdg_solver_destroy), preconditioner kind `precond` (0, 1, 2 as for
+ * hdg_solver_set_preconditioner; switching to ILU(0) later needs a workspace
+ * planned with precond = 2).  Creating and destroying it allocates and frees
+ * no device memory, so neither synchronises the device.  HDG_EINVAL for a
+ * short or misaligned workspace. */
+hdg_status hdg_solver_create_ws(hdg_sys* sys, int32_t restart, int32_t precond, void* workspace, int64_t bytes,
+                                hdg_solver** out);
+
+/* Bytes of device workspace hdg_solver_create_ws needs for a system on `mesh`
+ * (-1 for invalid arguments). */
+int64_t hdg_solver_workspace_bytes(const hdg_mesh* mesh, int32_t restart, int32_t precond);
+
 /* Solve K dLam = E for the DEVICE vector dLam [lam_len] (its input value is
  * the initial guess; pass zeros for none), on `stream`.  Stops when the
  * preconditioned residual ||M^-1 (E - K dLam)||_2 <= rtol ||M^-1 E||_2 or after
@@ -360,6 +375,17 @@ hdg_status hdg_solver_colors(const hdg_solver* solver, int32_t* face_color, int3
  * the hybridized adjoint system of Sec. 4.2. */
 hdg_status hdg_trace_solve_ex(hdg_solver* solver, const double* rhs, int32_t transpose, double* dLam, double rtol,
                               int32_t max_iter, int32_t* iters, double* rel_res, void* stream);
+
+/* One pseudo-transient Newton step of Sec. 3.3 from HOST buffers, blocking:
+ * copy U [u_len] and Lam [lam_len] to the system's device staging, condense
+ * (hdg_condense), solve K dLam = E with `solver` (built on this system) to
+ * `rtol` as hdg_trace_solve, reconstruct dU = X_F - X_B dLam (hdg_recover),
+ * copy dU [u_len] and dLam [lam_len] back, synchronise `stream`.  Statuses as
+ * the calls it makes (HDG_ETIMEOUT when the solve stops at max_iter: dU and
+ * dLam are then not written). */
+hdg_status hdg_solve_step_host(hdg_sys* sys, hdg_solver* solver, const double* U, const double* Lam, double* dU,
+                               double* dLam, double rtol, int32_t max_iter, int32_t* iters, double* rel_res,
+                               void* stream);
 
 /* y = K x, or y = K^T x when transpose != 0, for DEVICE vectors x, y
  * [lam_len] (K of the last hdg_condense). */

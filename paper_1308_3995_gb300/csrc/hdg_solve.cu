@@ -422,6 +422,8 @@ struct hdg_solver {
   std::vector<int> fcolor;    // host copy of the face colors
   FaceDev fi{};               // the ILU factors: values F (K's layout) and pivot inverses
   double* F = nullptr;
+  bool external_ws = false;   // device buffers carved from the caller's workspace
+  bool hpin_pageable = false; // host mirror from new[] (caller's workspace) or pinned
   int64_t k_vals = 0;         // doubles in K
   int64_t dinv_len = 0;       // doubles in the pivot inverses
   std::vector<void*> allocs;
@@ -537,21 +539,75 @@ void multidot(hdg_solver* S, const double* V, int nvec, const double* w, int64_t
 
 }  // namespace
 
-extern "C" {
+namespace {
 
-hdg_status hdg_solver_create(hdg_sys* sys, int32_t restart, hdg_solver** out) {
+// Byte offsets of the solver's device buffers in one workspace (256-byte aligned).
+struct SolverPlan {
+  int64_t n = 0, dinv_len = 0, k_vals = 0;
+  int dot_blocks = 0;
+  size_t kc, kb, kt, dof, dinv, bad, V, part, h, coef, zero, tmp, cols, fcol, F, dinv2, tmp2, total;
+};
+
+SolverPlan plan_solver(const hdg_mesh* M, int restart, bool ilu, int sms) {
+  SolverPlan p{};
+  size_t o = 0;
+  auto take = [&o](size_t bytes) {
+    const size_t at = o;
+    o += (std::max<size_t>(bytes, 16) + 255) / 256 * 256;
+    return at;
+  };
+  const size_t nf = (size_t)M->n_face, nr = (size_t)restart + 1;
+  p.n = M->lam_len;
+  for (int e = 0; e < M->n_face; ++e) p.dinv_len += (int64_t)(4 * (M->face_p[e] + 1)) * (4 * (M->face_p[e] + 1));
+  p.k_vals = M->k_blkoff.empty() ? 0 : M->k_blkoff.back();
+  p.dot_blocks = std::max(1, std::min<int>(2 * std::max(sms, 1), (int)((p.n + kDotThreads - 1) / kDotThreads)));
+  p.kc = take(sizeof(int) * 5 * nf);
+  p.kb = take(sizeof(int64_t) * M->k_blkoff.size());
+  p.kt = take(sizeof(int64_t) * 5 * nf);
+  p.dof = take(sizeof(int64_t) * nf);
+  p.dinv = take(sizeof(double) * p.dinv_len);
+  p.bad = take(sizeof(int));
+  p.V = take(sizeof(double) * nr * p.n);
+  p.part = take(sizeof(double) * nr * p.dot_blocks);
+  p.h = take(sizeof(double) * (2 * nr + 2));
+  p.coef = take(sizeof(double) * nr);
+  p.zero = take(sizeof(double) * p.n);
+  p.tmp = take(sizeof(double) * p.n);
+  p.cols = take(sizeof(int) * nf);
+  p.fcol = take(sizeof(int) * nf);
+  p.F = p.dinv2 = p.tmp2 = 0;
+  if (ilu) {
+    p.F = take(sizeof(double) * p.k_vals);
+    p.dinv2 = take(sizeof(double) * p.dinv_len);
+    p.tmp2 = take(sizeof(double) * p.n);
+  }
+  p.total = o;
+  return p;
+}
+
+}  // namespace
+
+extern "C" hdg_status hdg_solver_destroy(hdg_solver* S);
+
+namespace {
+
+// Plan, place (one cudaMalloc, or the caller's workspace) and fill the solver's state.
+hdg_status solver_build(hdg_sys* sys, int32_t restart, int32_t precond, void* ws, int64_t ws_bytes,
+                        hdg_solver** out) {
   if (!sys || !out) return HDG_EINVAL;
   *out = nullptr;
   hdg_ctx* ctx = sys->ctx;
   if (restart < 1 || restart > kMaxRestart) return fail(ctx, HDG_EINVAL, "hdg_solver_create: restart must be in 1..64");
+  if (precond < 0 || precond > 2) return fail(ctx, HDG_EINVAL, "hdg_solver_create: preconditioner kind must be 0, 1 or 2");
   const hdg_mesh* M = sys->mesh;
   if (cudaSetDevice(ctx->device) != cudaSuccess) return fail(ctx, HDG_ECUDA, "cudaSetDevice failed");
-  hdg_solver* S = new hdg_solver();
-  S->sys = sys;
-  S->restart = restart;
-  S->n = M->lam_len;
-  cudaDeviceGetAttribute(&S->sms, cudaDevAttrMultiProcessorCount, ctx->device);
-  S->dot_blocks = std::max(1, std::min<int>(2 * S->sms, (int)((S->n + kDotThreads - 1) / kDotThreads)));
+  int sms = 0;
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, ctx->device);
+  const SolverPlan P = plan_solver(M, restart, precond == 2, sms);
+  if (ws && ((uintptr_t)ws % 256 != 0 || ws_bytes < (int64_t)P.total))
+    return fail(ctx, HDG_EINVAL,
+                "hdg_solver_create_ws: workspace smaller than hdg_solver_workspace_bytes or not 256-byte aligned");
+  // tables: block of (col, e) for products with K^T, pivot-inverse offsets, the multicolor order
   std::vector<int64_t> tblk(5 * (size_t)M->n_face, -1);
   for (int e = 0; e < M->n_face; ++e)
     for (int b = 0; b < 5; ++b) {
@@ -567,12 +623,6 @@ hdg_status hdg_solver_create(hdg_sys* sys, int32_t restart, hdg_solver** out) {
     dinv_off[e] = tot;
     tot += (int64_t)m * m;
   }
-  auto alloc = [&](size_t bytes, void** p) -> bool {
-    if (cudaMalloc(p, std::max<size_t>(bytes, 16)) != cudaSuccess) return false;
-    S->allocs.push_back(*p);
-    return true;
-  };
-  void *kc, *kb, *kt, *dof, *dinv, *bad, *V, *part, *h, *coef, *zero, *tmpv, *cols, *fcol;
   // greedy coloring: faces of one element (the nonzero blocks of a K row) get different colors
   std::vector<int> color(M->n_face, -1);
   int ncol = 0;
@@ -587,73 +637,118 @@ hdg_status hdg_solver_create(hdg_sys* sys, int32_t restart, hdg_solver** out) {
     color[e] = c;
     ncol = std::max(ncol, c + 1);
   }
-  std::vector<int> by_color;
+  hdg_solver* S = new hdg_solver();
+  S->sys = sys;
+  S->restart = restart;
+  S->n = P.n;
+  S->sms = sms;
+  S->dot_blocks = P.dot_blocks;
   S->color_off.assign(1, 0);
+  std::vector<int> by_color;
   for (int c = 0; c < ncol; ++c) {
     for (int e = 0; e < M->n_face; ++e)
       if (color[e] == c) by_color.push_back(e);
     S->color_off.push_back((int)by_color.size());
   }
-  const size_t nr = (size_t)restart + 1;
-  bool ok = alloc(sizeof(int) * M->k_col.size(), &kc) && alloc(sizeof(int64_t) * M->k_blkoff.size(), &kb) &&
-            alloc(sizeof(int64_t) * tblk.size(), &kt) &&
-            alloc(sizeof(int64_t) * dinv_off.size(), &dof) && alloc(sizeof(double) * tot, &dinv) &&
-            alloc(sizeof(int), &bad) && alloc(sizeof(double) * nr * S->n, &V) &&
-            alloc(sizeof(double) * nr * S->dot_blocks, &part) && alloc(sizeof(double) * (2 * nr + 2), &h) &&
-            alloc(sizeof(double) * nr, &coef) && alloc(sizeof(double) * S->n, &zero) &&
-            alloc(sizeof(double) * S->n, &tmpv) && alloc(sizeof(int) * std::max<size_t>(1, by_color.size()), &cols) &&
-            alloc(sizeof(int) * std::max<size_t>(1, color.size()), &fcol);
-  if (!ok || cudaMallocHost((void**)&S->hpin, sizeof(double) * (2 * nr + 2)) != cudaSuccess) {
-    for (void* p : S->allocs) cudaFree(p);
-    delete S;
-    return fail(ctx, HDG_ENOMEM, "hdg_solver_create: device allocation failed");
+  char* base = (char*)ws;
+  if (!base) {
+    void* p = nullptr;
+    if (cudaMalloc(&p, P.total) != cudaSuccess) {
+      delete S;
+      return fail(ctx, HDG_ENOMEM, "hdg_solver_create: device allocation failed");
+    }
+    S->allocs.push_back(p);
+    base = (char*)p;
+  } else {
+    S->external_ws = true;
   }
+  const size_t nr = (size_t)restart + 1;
+  if (S->external_ws) {  // no pinned allocation (its release may synchronise the device)
+    S->hpin = new double[2 * nr + 2];
+    S->hpin_pageable = true;
+  } else if (cudaMallocHost((void**)&S->hpin, sizeof(double) * (2 * nr + 2)) != cudaSuccess) {
+    S->hpin = nullptr;
+    hdg_solver_destroy(S);
+    return fail(ctx, HDG_ENOMEM, "hdg_solver_create: pinned host allocation failed");
+  }
+  int *kc = (int*)(base + P.kc), *cols = (int*)(base + P.cols), *fcol = (int*)(base + P.fcol);
+  int64_t *kb = (int64_t*)(base + P.kb), *kt = (int64_t*)(base + P.kt), *dof = (int64_t*)(base + P.dof);
   hdg_status st = HDG_OK;
   if (st == HDG_OK) st = ck(ctx, cudaMemcpy(kc, M->k_col.data(), sizeof(int) * M->k_col.size(), cudaMemcpyHostToDevice), "cudaMemcpy");
   if (st == HDG_OK) st = ck(ctx, cudaMemcpy(kb, M->k_blkoff.data(), sizeof(int64_t) * M->k_blkoff.size(), cudaMemcpyHostToDevice), "cudaMemcpy");
   if (st == HDG_OK) st = ck(ctx, cudaMemcpy(dof, dinv_off.data(), sizeof(int64_t) * dinv_off.size(), cudaMemcpyHostToDevice), "cudaMemcpy");
   if (st == HDG_OK) st = ck(ctx, cudaMemcpy(kt, tblk.data(), sizeof(int64_t) * tblk.size(), cudaMemcpyHostToDevice), "cudaMemcpy");
-  if (st == HDG_OK) st = ck(ctx, cudaMemset(zero, 0, sizeof(double) * S->n), "cudaMemset");
+  if (st == HDG_OK) st = ck(ctx, cudaMemset(base + P.zero, 0, sizeof(double) * S->n), "cudaMemset");
   if (st == HDG_OK && !by_color.empty())
     st = ck(ctx, cudaMemcpy(cols, by_color.data(), sizeof(int) * by_color.size(), cudaMemcpyHostToDevice), "cudaMemcpy");
   if (st == HDG_OK && !color.empty())
     st = ck(ctx, cudaMemcpy(fcol, color.data(), sizeof(int) * color.size(), cudaMemcpyHostToDevice), "cudaMemcpy");
   if (st != HDG_OK) {
-    for (void* p : S->allocs) cudaFree(p);
-    cudaFreeHost(S->hpin);
-    delete S;
+    hdg_solver_destroy(S);
     return st;
   }
   S->f.n_face = M->n_face;
   S->f.face_p = M->dm.face_p;
   S->f.lam_off = M->dm.lam_off;
-  S->f.k_col = (const int*)kc;
-  S->f.k_blkoff = (const int64_t*)kb;
-  S->f.dinv_off = (const int64_t*)dof;
-  S->f.k_tblk = (const int64_t*)kt;
-  S->f.fcolor = (const int*)fcol;
+  S->f.k_col = kc;
+  S->f.k_blkoff = kb;
+  S->f.dinv_off = dof;
+  S->f.k_tblk = kt;
+  S->f.fcolor = fcol;
   S->f.K = sys->ds.K;
-  S->f.dinv = (double*)dinv;
-  S->f.bad = (int*)bad;
-  S->V = (double*)V;
-  S->partial = (double*)part;
-  S->h = (double*)h;
-  S->coef = (double*)coef;
-  S->zero = (double*)zero;
-  S->tmp = (double*)tmpv;
-  S->colors = (int*)cols;
+  S->f.dinv = (double*)(base + P.dinv);
+  S->f.bad = (int*)(base + P.bad);
+  S->V = (double*)(base + P.V);
+  S->partial = (double*)(base + P.part);
+  S->h = (double*)(base + P.h);
+  S->coef = (double*)(base + P.coef);
+  S->zero = (double*)(base + P.zero);
+  S->tmp = (double*)(base + P.tmp);
+  S->colors = cols;
   S->fcolor = color;
-  S->k_vals = M->k_blkoff.empty() ? 0 : M->k_blkoff.back();
+  S->k_vals = P.k_vals;
   S->dinv_len = tot;
+  if (precond == 2) {
+    S->F = (double*)(base + P.F);
+    S->tmp2 = (double*)(base + P.tmp2);
+    S->fi = S->f;
+    S->fi.K = S->F;
+    S->fi.dinv = (double*)(base + P.dinv2);
+  }
+  S->precond = precond;
   *out = S;
   return HDG_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+hdg_status hdg_solver_create(hdg_sys* sys, int32_t restart, hdg_solver** out) {
+  return solver_build(sys, restart, 0, nullptr, 0, out);
+}
+
+hdg_status hdg_solver_create_ws(hdg_sys* sys, int32_t restart, int32_t precond, void* workspace, int64_t bytes,
+                                hdg_solver** out) {
+  if (!workspace) return HDG_EINVAL;
+  return solver_build(sys, restart, precond, workspace, bytes, out);
+}
+
+int64_t hdg_solver_workspace_bytes(const hdg_mesh* mesh, int32_t restart, int32_t precond) {
+  if (!mesh || restart < 1 || restart > kMaxRestart || precond < 0 || precond > 2) return -1;
+  int sms = 0;
+  if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, mesh->ctx->device) != cudaSuccess) return -1;
+  return (int64_t)plan_solver(mesh, restart, precond == 2, sms).total;
 }
 
 hdg_status hdg_solver_destroy(hdg_solver* S) {
   if (!S) return HDG_EINVAL;
   cudaSetDevice(S->sys->ctx->device);
   for (void* p : S->allocs) cudaFree(p);
-  if (S->hpin) cudaFreeHost(S->hpin);
+  if (S->hpin) {
+    if (S->hpin_pageable) delete[] S->hpin;
+    else cudaFreeHost(S->hpin);
+  }
   delete S;
   return HDG_OK;
 }
@@ -662,6 +757,8 @@ hdg_status hdg_solver_set_preconditioner(hdg_solver* S, int32_t kind) {
   if (!S || kind < 0 || kind > 2) return HDG_EINVAL;
   if (kind == 2 && !S->F) {  // the incomplete factors: a copy of K's values, pivot inverses, a work vector
     hdg_ctx* ctx = S->sys->ctx;
+    if (S->external_ws)
+      return fail(ctx, HDG_ENOMEM, "hdg_solver_set_preconditioner: the caller's workspace was planned without ILU(0)");
     if (cudaSetDevice(ctx->device) != cudaSuccess) return fail(ctx, HDG_ECUDA, "cudaSetDevice failed");
     void *F = nullptr, *di = nullptr, *t2 = nullptr;
     if (cudaMalloc(&F, sizeof(double) * std::max<int64_t>(S->k_vals, 2)) != cudaSuccess) F = nullptr;
@@ -833,6 +930,33 @@ hdg_status hdg_trace_solve_ex(hdg_solver* S, const double* rhs, int32_t transpos
   if (iters_out) *iters_out = it;
   if (rel_out) *rel_out = rel;
   return (rel > rtol) ? fail(ctx, HDG_ETIMEOUT, "hdg_trace_solve: max_iter reached before rtol") : HDG_OK;
+}
+
+hdg_status hdg_solve_step_host(hdg_sys* sys, hdg_solver* S, const double* U, const double* Lam, double* dU,
+                               double* dLam, double rtol, int32_t max_iter, int32_t* iters, double* rel_res,
+                               void* stream) {
+  if (!sys || !S) return HDG_EINVAL;
+  hdg_ctx* ctx = sys->ctx;
+  if (S->sys != sys) return fail(ctx, HDG_EINVAL, "hdg_solve_step_host: the solver belongs to another system");
+  if (!U || !Lam || !dU || !dLam) return fail(ctx, HDG_EINVAL, "hdg_solve_step_host: null argument");
+  const hdg_mesh* M = sys->mesh;
+  cudaStream_t st = (cudaStream_t)stream;
+  const size_t d = sizeof(double);
+  hdg_status rs;
+  if ((rs = ck(ctx, cudaMemcpyAsync(sys->d_U, U, d * M->u_len, cudaMemcpyHostToDevice, st), "cudaMemcpyAsync")) != HDG_OK)
+    return rs;
+  if ((rs = ck(ctx, cudaMemcpyAsync(sys->d_Lam, Lam, d * M->lam_len, cudaMemcpyHostToDevice, st), "cudaMemcpyAsync")) != HDG_OK)
+    return rs;
+  if ((rs = hdg_condense(sys, sys->d_U, sys->d_Lam, stream)) != HDG_OK) return rs;
+  if ((rs = ck(ctx, cudaMemsetAsync(sys->d_dLam, 0, d * M->lam_len, st), "cudaMemsetAsync")) != HDG_OK) return rs;
+  if ((rs = hdg_trace_solve_ex(S, nullptr, 0, sys->d_dLam, rtol, max_iter, iters, rel_res, stream)) != HDG_OK)
+    return rs;
+  if ((rs = hdg_recover(sys, sys->d_dLam, sys->d_dU, stream)) != HDG_OK) return rs;
+  if ((rs = ck(ctx, cudaMemcpyAsync(dU, sys->d_dU, d * M->u_len, cudaMemcpyDeviceToHost, st), "cudaMemcpyAsync")) != HDG_OK)
+    return rs;
+  if ((rs = ck(ctx, cudaMemcpyAsync(dLam, sys->d_dLam, d * M->lam_len, cudaMemcpyDeviceToHost, st), "cudaMemcpyAsync")) != HDG_OK)
+    return rs;
+  return ck(ctx, cudaStreamSynchronize(st), "cudaStreamSynchronize");
 }
 
 hdg_status hdg_newton_update(hdg_sys* sys, double* U, double* Lam, const double* dU, const double* dLam,

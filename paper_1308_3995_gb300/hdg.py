@@ -36,7 +36,7 @@ EXPORTS = ["hdg_create", "hdg_destroy", "hdg_last_error", "hdg_mesh_create", "hd
            "hdg_sys_set_cfl", "hdg_cfl_law", "hdg_autotune", "hdg_trace_solve_ex", "hdg_adjoint_condense",
            "hdg_adapt_indicators", "hdg_adapt_mark",
            "hdg_mesh_create_bc", "hdg_solver_set_preconditioner", "hdg_solver_setup", "hdg_solver_precond_apply",
-           "hdg_solver_colors"]
+           "hdg_solver_colors", "hdg_solver_create_ws", "hdg_solver_workspace_bytes", "hdg_solve_step_host"]
 
 
 class HdgError(RuntimeError):
@@ -130,6 +130,12 @@ def lib(build: bool = True):
         L.hdg_solver_setup.argtypes = [_vp, _vp]
         L.hdg_solver_precond_apply.argtypes = [_vp, _vp, _vp, ctypes.c_int32, _vp]
         L.hdg_solver_colors.argtypes = [_vp, ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(ctypes.c_int32)]
+        L.hdg_solver_create_ws.argtypes = [_vp, ctypes.c_int32, ctypes.c_int32, _vp, ctypes.c_int64,
+                                           ctypes.POINTER(_vp)]
+        L.hdg_solver_workspace_bytes.argtypes = [_vp, ctypes.c_int32, ctypes.c_int32]
+        L.hdg_solver_workspace_bytes.restype = ctypes.c_int64
+        L.hdg_solve_step_host.argtypes = [_vp, _vp, _vp, _vp, _vp, _vp, ctypes.c_double, ctypes.c_int32,
+                                          ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(ctypes.c_double), _vp]
         L.hdg_trace_solve_ex.argtypes = [_vp, _vp, ctypes.c_int32, _vp, ctypes.c_double, ctypes.c_int32,
                                          ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(ctypes.c_double), _vp]
         L.hdg_adjoint_condense.argtypes = [_vp, _vp, _vp, _vp, _vp, _vp]
@@ -187,13 +193,38 @@ class Solver:
 
     BLOCK_JACOBI, BLOCK_SGS, BLOCK_ILU0 = 0, 1, 2
 
-    def __init__(self, system: "System", restart: int = 30, precond: int = 0):
+    def __init__(self, system: "System", restart: int = 30, precond: int = 0, workspace=None):
         """precond: 0 block Jacobi, 1 multicolor block symmetric Gauss-Seidel, 2 block ILU(0)
-        in the multicolor order."""
+        in the multicolor order.  workspace: optional (device pointer, bytes) holding every
+        device buffer (hdg_solver_create_ws; size from ``workspace_bytes``)."""
         h = _vp()
-        _check(lib().hdg_solver_create(system.h, int(restart), ctypes.byref(h)), system.ctx.h)
-        self.h, self.sys = h, system
-        _check(lib().hdg_solver_set_preconditioner(h, int(precond)), system.ctx.h)
+        if workspace is None:
+            _check(lib().hdg_solver_create(system.h, int(restart), ctypes.byref(h)), system.ctx.h)
+            self.h, self.sys = h, system
+            _check(lib().hdg_solver_set_preconditioner(h, int(precond)), system.ctx.h)
+        else:
+            ptr, nbytes = workspace
+            _check(lib().hdg_solver_create_ws(system.h, int(restart), int(precond), ctypes.c_void_p(int(ptr)),
+                                              int(nbytes), ctypes.byref(h)), system.ctx.h)
+            self.h, self.sys = h, system
+
+    @staticmethod
+    def workspace_bytes(mesh: "Mesh", restart: int = 30, precond: int = 0) -> int:
+        n = int(lib().hdg_solver_workspace_bytes(mesh.h, int(restart), int(precond)))
+        if n < 0:
+            raise HdgError(HDG_EINVAL, "hdg_solver_workspace_bytes: invalid arguments")
+        return n
+
+    def step_host(self, U, Lam, dU, dLam, rtol=1e-10, max_iter=3000, stream=None):
+        """hdg_solve_step_host: one Newton step from pinned host tensors (blocking);
+        returns (iterations, rel. residual)."""
+        def hp(a):
+            return a.data_ptr() if hasattr(a, "data_ptr") else a.ctypes.data
+        it, rel = ctypes.c_int32(), ctypes.c_double()
+        _check(lib().hdg_solve_step_host(self.sys.h, self.h, hp(U), hp(Lam), hp(dU), hp(dLam), float(rtol),
+                                         int(max_iter), ctypes.byref(it), ctypes.byref(rel), _stream(stream)),
+               self.sys.ctx.h)
+        return int(it.value), float(rel.value)
 
     def solve(self, dLam, rtol=1e-12, max_iter=500, stream=None, check=True, rhs=None, transpose=False):
         """Solve K dLam = E (or K^T dLam = rhs) in place (dLam holds the initial guess);

@@ -12,6 +12,16 @@ CUDA event; the request then releases its slot and its arena range at once.
 Nothing here allocates or frees device memory while requests are in flight
 (the arena is one tensor allocated at start-up; systems are carved from it).
 
+With ``solve=True`` a request is a whole pseudo-transient Newton step of
+Sec. 3.3 instead: condensation at a finite CFL, the GPU trace solve of
+K dLambda = E to a relative residual of 1e-10 (GMRES, block ILU(0) by
+default), reconstruction, and dU, dLambda copied back
+(``hdg_solve_step_host``).  The trace solve reads one residual estimate per
+GMRES iteration, so the call blocks its host thread: each stream slot then has
+a worker thread that runs its requests' steps (the library releases the
+interpreter lock during the call); the system and the solver both live in
+the request's arena range.
+
 The plain baseline is the same loop with one slot and binary64 arithmetic
 (requests served one at a time, in arrival order).
 
@@ -22,6 +32,8 @@ from __future__ import annotations
 
 import bisect
 import math
+import queue
+import threading
 import time
 from dataclasses import dataclass, field
 
@@ -93,6 +105,8 @@ class Request:
     # results
     dU: object = None
     dU_host: object = None
+    dLam_host: object = None   # trace update computed by the solve (solve mode)
+    iters: int = 0             # GMRES iterations of the solve (solve mode)
     mesh: object = None
     admitted_s: float = math.nan
     done_s: float = math.nan
@@ -136,10 +150,11 @@ def prepare(ctx: hdg.Context, reqs: list, pin: bool = True):
         r.case, r.face_vid, r.face_p = case, m.face_vid.copy(), m.face_p.copy()
         r.n_elem = case.mesh.n_elem
         m.close()
-        t = (torch.from_numpy(U), torch.from_numpy(Lam), torch.from_numpy(dLam), torch.empty(U.size, dtype=torch.float64))
+        t = (torch.from_numpy(U), torch.from_numpy(Lam), torch.from_numpy(dLam), torch.empty(U.size, dtype=torch.float64),
+             torch.empty(Lam.size, dtype=torch.float64))
         if pin:
             t = tuple(x.pin_memory() for x in t)
-        r.U, r.Lam, r.dLam, r.dU_host = t
+        r.U, r.Lam, r.dLam, r.dU_host, r.dLam_host = t
     return reqs
 
 
@@ -151,6 +166,7 @@ class Report:
     elements: int
     makespan_s: float
     latencies_s: list = field(default_factory=list)
+    gmres_iterations: list = field(default_factory=list)
 
     @property
     def throughput(self) -> float:
@@ -164,16 +180,24 @@ class Report:
         return lat[k]
 
     def as_dict(self) -> dict:
-        return {"mode": self.mode, "requests": self.n, "elements": self.elements,
-                "makespan_s": self.makespan_s, "elements_per_s": self.throughput,
-                "p50_ms": 1e3 * self.pct(50), "p99_ms": 1e3 * self.pct(99),
-                "mean_ms": 1e3 * float(np.mean(self.latencies_s)) if self.latencies_s else math.nan}
+        d = {"mode": self.mode, "requests": self.n, "elements": self.elements,
+             "makespan_s": self.makespan_s, "elements_per_s": self.throughput,
+             "p50_ms": 1e3 * self.pct(50), "p99_ms": 1e3 * self.pct(99),
+             "mean_ms": 1e3 * float(np.mean(self.latencies_s)) if self.latencies_s else math.nan}
+        if self.gmres_iterations:
+            d["gmres_iterations_median"] = float(np.median(self.gmres_iterations))
+            d["gmres_iterations_max"] = int(max(self.gmres_iterations))
+        return d
 
 
 class Server:
-    def __init__(self, ctx: hdg.Context, arena_bytes: int, slots: int, precision: int, keep_outputs: bool = False):
+    def __init__(self, ctx: hdg.Context, arena_bytes: int, slots: int, precision: int, keep_outputs: bool = False,
+                 solve: bool = False, precond: int = 2, rtol: float = 1e-10, cfl: float = 10.0,
+                 restart: int = 30, max_iter: int = 5000):
         import torch
         self.ctx, self.slots, self.precision, self.keep = ctx, int(slots), int(precision), keep_outputs
+        self.solve, self.precond, self.rtol, self.cfl = bool(solve), int(precond), float(rtol), float(cfl)
+        self.restart, self.max_iter = int(restart), int(max_iter)
         self.dev = torch.device(f"cuda:{ctx.device}")
         self.buf = torch.empty(int(arena_bytes), dtype=torch.uint8, device=self.dev)
         self.arena = Arena(int(arena_bytes))
@@ -181,7 +205,31 @@ class Server:
 
     def _params(self, wl):
         return hdg.Params(model=wl.model, precision=self.precision, mach=wl.mach, alpha=wl.alpha,
-                          reynolds=wl.reynolds, prandtl=wl.prandtl)
+                          reynolds=wl.reynolds, prandtl=wl.prandtl, cfl=self.cfl if self.solve else 0.0)
+
+    def _worker(self, slot: int, jobs: "queue.Queue", done: "queue.Queue", t0_box: list):
+        """Runs the Newton steps of the requests given to one stream slot (solve mode)."""
+        import torch
+        torch.cuda.set_device(self.dev)
+        st = self.streams[slot]
+        while True:
+            job = jobs.get()
+            if job is None:
+                return
+            r, off, n_sys, n_sol, prm = job
+            try:
+                base = self.buf.data_ptr() + off
+                sysm = hdg.System(self.ctx, r.mesh, prm, workspace=(base, n_sys))
+                sol = hdg.Solver(sysm, self.restart, self.precond, workspace=(base + n_sys, n_sol))
+                r.iters, _ = sol.step_host(r.U, r.Lam, r.dU_host, r.dLam_host, self.rtol, self.max_iter, st)
+                r.done_s = time.perf_counter() - t0_box[0]
+                if self.keep:
+                    r.dU = r.dU_host.numpy().copy()
+                sol.close()          # arena-backed: frees no device memory
+                sysm.close()
+                done.put((r, slot, off, None))
+            except Exception as exc:  # noqa: BLE001 - handed to the main loop
+                done.put((r, slot, off, exc))
 
     def run(self, reqs: list, mode: str = "") -> Report:
         import torch
@@ -189,61 +237,96 @@ class Server:
         free_slots = list(range(self.slots))
         waiting, active, meshes = [], [], []
         nxt = 0
+        done_q, workers, jobs = queue.Queue(), [], []
+        t0_box = [0.0]
+        if self.solve:
+            for k in range(self.slots):
+                jobs.append(queue.Queue())
+                th = threading.Thread(target=self._worker, args=(k, jobs[k], done_q, t0_box), daemon=True)
+                th.start()
+                workers.append(th)
+        n_active = 0
         torch.cuda.synchronize(self.dev)
         t0 = time.perf_counter()
-        while nxt < len(order) or waiting or active:
-            now = time.perf_counter() - t0
-            while nxt < len(order) and order[nxt].arrival_s <= now:
-                waiting.append(order[nxt])
-                nxt += 1
-            # admit in arrival order while a slot and arena room are available; the head
-            # request's mesh is planned once and kept until it is admitted
-            while waiting and free_slots:
-                r = waiting[0]
-                wl = r.wl
-                if r.mesh is None:
-                    r.mesh = hdg.Mesh(self.ctx, r.case.mesh.elem_xy, r.case.mesh.elem_vid, r.case.elem_p,
-                                      r.case.nfield)
-                    meshes.append(r.mesh)
-                mesh = r.mesh
-                prm = self._params(wl)
-                need = mesh.workspace_bytes(prm)
-                if need > self.arena.capacity:
-                    raise hdg.HdgError(hdg.HDG_ENOMEM, f"request {r.rid} needs {need} bytes, arena holds "
-                                                       f"{self.arena.capacity}")
-                off = self.arena.alloc(need)
-                if off is None:
-                    break
-                waiting.pop(0)
-                slot = free_slots.pop(0)
-                sysm = hdg.System(self.ctx, mesh, prm, workspace=(self.buf.data_ptr() + off, need))
-                dU = r.dU_host
-                st = self.streams[slot]
-                sysm.step_host_async(r.U, r.Lam, r.dLam, dU, st)
-                ev = torch.cuda.Event()
-                ev.record(st)
-                r.admitted_s = time.perf_counter() - t0
-                active.append((r, slot, off, sysm, dU, ev))
-            # completions
-            still = []
-            for item in active:
-                r, slot, off, sysm, dU, ev = item
-                if ev.query():
-                    r.done_s = time.perf_counter() - t0
-                    if self.keep:
-                        r.dU = dU.numpy().copy()
-                    sysm.close()                 # frees nothing on the device (arena-backed)
-                    self.arena.free(off)
-                    free_slots.append(slot)
+        t0_box[0] = t0
+        try:
+            while nxt < len(order) or waiting or n_active:
+                now = time.perf_counter() - t0
+                while nxt < len(order) and order[nxt].arrival_s <= now:
+                    waiting.append(order[nxt])
+                    nxt += 1
+                # admit in arrival order while a slot and arena room are available; the head
+                # request's mesh is planned once and kept until it is admitted
+                while waiting and free_slots:
+                    r = waiting[0]
+                    wl = r.wl
+                    if r.mesh is None:
+                        r.mesh = hdg.Mesh(self.ctx, r.case.mesh.elem_xy, r.case.mesh.elem_vid, r.case.elem_p,
+                                          r.case.nfield)
+                        meshes.append(r.mesh)
+                    mesh = r.mesh
+                    prm = self._params(wl)
+                    n_sys = Arena._round(mesh.workspace_bytes(prm))
+                    n_sol = hdg.Solver.workspace_bytes(mesh, self.restart, self.precond) if self.solve else 0
+                    need = n_sys + n_sol
+                    if need > self.arena.capacity:
+                        raise hdg.HdgError(hdg.HDG_ENOMEM, f"request {r.rid} needs {need} bytes, arena holds "
+                                                           f"{self.arena.capacity}")
+                    off = self.arena.alloc(need)
+                    if off is None:
+                        break
+                    waiting.pop(0)
+                    slot = free_slots.pop(0)
+                    r.admitted_s = time.perf_counter() - t0
+                    n_active += 1
+                    if self.solve:
+                        jobs[slot].put((r, off, n_sys, n_sol, prm))
+                        continue
+                    sysm = hdg.System(self.ctx, mesh, prm, workspace=(self.buf.data_ptr() + off, n_sys))
+                    dU = r.dU_host
+                    st = self.streams[slot]
+                    sysm.step_host_async(r.U, r.Lam, r.dLam, dU, st)
+                    ev = torch.cuda.Event()
+                    ev.record(st)
+                    active.append((r, slot, off, sysm, dU, ev))
+                # completions
+                if self.solve:
+                    while True:
+                        try:
+                            r, slot, off, exc = done_q.get_nowait()
+                        except queue.Empty:
+                            break
+                        if exc is not None:
+                            raise exc
+                        self.arena.free(off)
+                        free_slots.append(slot)
+                        n_active -= 1
                 else:
-                    still.append(item)
-            active = still
-            if not active and not waiting and nxt < len(order):
-                wait = order[nxt].arrival_s - (time.perf_counter() - t0)
-                if wait > 0:
-                    time.sleep(min(wait, 0.01))
-            elif active:
-                time.sleep(2e-5)
+                    still = []
+                    for item in active:
+                        r, slot, off, sysm, dU, ev = item
+                        if ev.query():
+                            r.done_s = time.perf_counter() - t0
+                            if self.keep:
+                                r.dU = dU.numpy().copy()
+                            sysm.close()                 # frees nothing on the device (arena-backed)
+                            self.arena.free(off)
+                            free_slots.append(slot)
+                            n_active -= 1
+                        else:
+                            still.append(item)
+                    active = still
+                if not n_active and not waiting and nxt < len(order):
+                    wait = order[nxt].arrival_s - (time.perf_counter() - t0)
+                    if wait > 0:
+                        time.sleep(min(wait, 0.01))
+                elif n_active:
+                    time.sleep(2e-5)
+        finally:
+            for q in jobs:
+                q.put(None)
+            for th in workers:
+                th.join(timeout=60)
         makespan = max(r.done_s for r in order) - min(r.arrival_s for r in order)
         torch.cuda.synchronize(self.dev)
         for m in meshes:
@@ -251,5 +334,6 @@ class Server:
         for r in order:
             r.mesh = None
         rep = Report(mode, len(order), sum(r.n_elem for r in order), makespan,
-                     [r.done_s - r.arrival_s for r in order])
+                     [r.done_s - r.arrival_s for r in order],
+                     [r.iters for r in order] if self.solve else [])
         return rep

@@ -116,3 +116,36 @@ def test_admission_waits_for_arena_room_and_rejects_oversize():
     with pytest.raises(hdg.HdgError) as ei:
         tiny.run(reqs[:1], "tiny")
     assert ei.value.status == hdg.HDG_ENOMEM
+
+
+@pytest.mark.gpu
+def test_solve_mode_requests_match_the_oracle_newton_step():
+    """Requests as whole Newton steps (condensation at CFL 10, GPU trace solve to 1e-10 with
+    block ILU(0), reconstruction): each result is bitwise the same alone and in the mix, and the
+    smallest ones agree with the oracle's dense solve of its own K, E and its reconstruction."""
+    import oracle as O
+    from hdg_testlib import oracle_params
+    from paper_1308_3995_gb300 import hdg
+    ctx = hdg.Context(0)
+    wls = SV.request_workloads(6, seed=21, min_elems=60, max_elems=400)
+    reqs = SV.prepare(ctx, [SV.Request(i, 0.002 * i, w) for i, w in enumerate(wls)])
+    mixed = SV.Server(ctx, arena_bytes=2 << 30, slots=3, precision=hdg.HDG_FLOAT2, keep_outputs=True, solve=True)
+    rep = mixed.run(reqs, "mixed-solve")
+    assert rep.n == 6 and len(rep.gmres_iterations) == 6 and min(rep.gmres_iterations) > 0
+    assert mixed.arena.bytes_used == 0
+    in_mix = {r.rid: (r.dU.copy(), r.dLam_host.numpy().copy()) for r in reqs}
+    alone = SV.Server(ctx, arena_bytes=2 << 30, slots=1, precision=hdg.HDG_FLOAT2, keep_outputs=True, solve=True)
+    for r in reqs:
+        r.arrival_s = 0.0
+        alone.run([r], "alone")
+        assert np.array_equal(r.dU, in_mix[r.rid][0]) and np.array_equal(r.dLam_host.numpy(), in_mix[r.rid][1])
+    for r in sorted(reqs, key=lambda q: q.n_elem)[:2]:
+        c = r.case
+        om = O.Mesh(c.mesh.elem_xy, c.mesh.elem_vid, c.elem_p, c.nfield, c.mesh.elem_bc)
+        res = om.condense(oracle_params(r.wl, cfl=10.0), r.U.numpy(), r.Lam.numpy())
+        dL = O.dense_solve(om.dense_K(res["K"]), res["E"])
+        dU = om.recover(res["X"], dL)
+        eL = np.linalg.norm(in_mix[r.rid][1] - dL) / np.linalg.norm(dL)
+        eU = np.linalg.norm(in_mix[r.rid][0] - dU) / np.linalg.norm(dU)
+        print(r.wl.name, r.n_elem, "elements, iterations", r.iters, f"dLambda {eL:.1e} dU {eU:.1e}")
+        assert eL < 1e-7 and eU < 1e-7
