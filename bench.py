@@ -244,6 +244,7 @@ class Measured:
         self.step_ms = [e[0].elapsed_time(e[2]) for e in ev]
         self.cond_ms = [e[0].elapsed_time(e[1]) for e in ev]
         self.rec_ms = [e[1].elapsed_time(e[2]) for e in ev]
+        self.bucket_ms = self.sys.bucket_times()     # per-degree times inside the last mixed launch
         self.status_bad = int((self.sys.views()["status"] != 0).sum())
         return self
 
@@ -264,16 +265,24 @@ class Measured:
     def summary(self):
         tot = sum(self.step_ms)
         lat = sorted(self.step_ms)
-        p99 = lat[min(len(lat) - 1, int(math.ceil(0.99 * len(lat))) - 1)]
+
+        def pct(q):
+            return lat[min(len(lat) - 1, max(0, int(math.ceil(q / 100.0 * len(lat))) - 1))]
+        p99 = pct(99)
         fl, by = self.algorithmic()
         cond_s = statistics.mean(self.cond_ms) * 1e-3
         return {"elements_per_s": self.n_elem * len(self.step_ms) / (tot * 1e-3), "ms_per_step": tot / len(lat),
-                "p50_step_ms": lat[len(lat) // 2], "p99_step_ms": p99, "condense_ms": 1e3 * cond_s,
+                "p50_step_ms": lat[len(lat) // 2], "p10_step_ms": pct(10), "p90_step_ms": pct(90),
+                "p99_step_ms": p99, "condense_ms": 1e3 * cond_s,
                 "recover_ms": statistics.mean(self.rec_ms), "elem_status_nonzero": self.status_bad,
                 "fp64_equiv_tflops": fl / cond_s / 1e12, "algorithmic_gflop_per_launch": fl / 1e9,
                 "algorithmic_mb_per_launch": by / 1e6,
                 "launch_shapes": {str(p): ("one CTA per element" if v == 0 else f"persistent, {v} CTAs/SM")
-                                  for p, v in self.shapes.items()}}
+                                  for p, v in self.shapes.items()},
+                **({"buckets_in_last_step": {
+                    str(p): {"elements": int((self.mesh.elem_p == p).sum()), "ms": ms,
+                             "elements_per_s": int((self.mesh.elem_p == p).sum()) / (ms * 1e-3)}
+                    for p, ms in self.bucket_ms.items()}} if self.bucket_ms else {})}
 
     def close(self):
         self.sys.close()
@@ -554,8 +563,8 @@ def run_ours(args, wl, ws, rank, local):
             "peak_note": "FP64 1.25 TFLOP/s nominal (recipe); 1.255 measured by an FMA-chain microbenchmark"}
     extra = {"precision": "fp64" if args.precision == 0 else "float-float", "sc_eps0": args.sc_eps0,
              "launch_shapes": summ["launch_shapes"]}
-    extra.update({k: summ[k] for k in ("p50_step_ms", "p99_step_ms", "condense_ms", "recover_ms",
-                                       "elem_status_nonzero")})
+    extra.update({k: summ[k] for k in ("p50_step_ms", "p10_step_ms", "p90_step_ms", "p99_step_ms", "condense_ms",
+                                       "recover_ms", "elem_status_nonzero")})
     line = {"metric": METRIC, "value": value, "unit": "elements/s", "n_gpus": ws, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64" if args.precision == 0 else "f32x2",

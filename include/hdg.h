@@ -291,6 +291,14 @@ hdg_status hdg_adapt_mark(hdg_ctx* ctx, int32_t n, const double* eta2, const dou
 /* Number of kernel launches the last hdg_condense + hdg_recover enqueued. */
 int32_t hdg_sys_launches(const hdg_sys* sys);
 
+/* Per-degree time of the last hdg_condense on a mesh with more than one degree
+ * bucket (the buckets run concurrently on forked streams): ms[p], p = 1..4,
+ * the milliseconds between the start and the end of bucket p's launches on
+ * its stream (CUDA events; waits for them), -1 for an empty bucket; ms[0] is
+ * -1.  All -1 after a single-bucket hdg_condense or one captured into a graph.
+ * HOST array ms[5]. */
+hdg_status hdg_sys_bucket_times(const hdg_sys* sys, float* ms);
+
 /* ---- Global trace solve and pseudo-transient Newton update (Sec. 3.3, 3.4) ----
  * The paper solves K dLambda = E (Eq. hybridsystem) with preconditioned GMRES
  * (an ILU(n) preconditioner through PETSc).  This library solves it on the GPU

@@ -196,7 +196,8 @@ class Params:
 
 
 def boundary_state(kind, w, n, params) -> np.ndarray:
-    """Boundary state w_b(w) of Sec. 2.1: kind 1 slip wall, 2 far field (characteristic), normal n."""
+    """Boundary state w_b(w) of Sec. 2.1/2.2: kind 1 slip wall, 2 far field (characteristic), 3 no-slip
+    wall (rho, 0, 0, E); normal n."""
     wb = np.zeros(4)
     P = params.c()
     lib().orc_boundary_state(int(kind), _d(_f64(w)), float(n[0]), float(n[1]), ctypes.byref(P), _d(wb))

@@ -12,8 +12,9 @@
 //     flux, temperature, Newtonian stress and Sutherland viscosity (Sec. 2.2);
 //   * the HDG residual N_h of Eq. (hdg_ls1)-(hdg_cont) with the combined
 //     Lax-Friedrichs/LDG-type numerical flux of Sec. 3.2 (source s = 0), the
-//     Euler boundary operator of Sec. 3.2 on tagged boundary faces (slip wall
-//     and characteristic far field, boundary states of Sec. 2.1), optionally with the
+//     boundary operator of Sec. 3.2 on tagged boundary faces (Euler: slip wall
+//     and characteristic far field; Navier-Stokes: no-slip adiabatic wall;
+//     boundary states and wall viscous flux of Sec. 2.1/2.2), optionally with the
 //     shock-capturing volume term of Sec. 3.2 (artificial viscosity eps_K from
 //     the L1 norm of the strong convective residual, effective size h_K / p_K);
 //   * the Newton matrix N'_h (Eq. linearsystem) as the exact complex-step
@@ -420,6 +421,10 @@ static double re(double x) { return x; }
 static double re(const cplx& x) { return x.real(); }
 template <class T>
 static void boundary_state(int kind, const T* w, double nx, double ny, const orc_params& P, T* wb) {
+  if (kind == 3) {  // no-slip wall (Sec. 2.2): w_b = (rho, 0, 0, E)
+    wb[0] = w[0]; wb[1] = 0.0; wb[2] = 0.0; wb[3] = w[3];
+    return;
+  }
   if (kind == 1) {
     T mn = w[1] * nx + w[2] * ny;
     wb[0] = w[0]; wb[1] = w[1] - mn * nx; wb[2] = w[2] - mn * ny; wb[3] = w[3];
@@ -536,22 +541,44 @@ static void element_residual(const OMesh& M, const orc_params& P, int K, const G
   int loff = 0;
   for (int lf = 0; lf < 3; ++lf) {
     int e = M.elem_face[K * 3 + lf];
-    if (e < 0) {  // boundary operator of Sec. 3.2 (Euler): <phi, f_c(w_b(w)) . n>, no lambda
+    if (e < 0) {  // boundary operator of Sec. 3.2: <tau.n, w_b> + <phi, (f_c(w_b) - f_v(w_b, q_b)).n>, no lambda
       const EdgeTab& Eb = g_edge[p][p];
       const int fl = elem_flip(M, K, lf);
       const double nx = g.nrm[lf][0], ny = g.nrm[lf][1];
       for (int gq = 0; gq < Eb.ne; ++gq) {
         const double we = Eb.w[gq] * g.len[lf];
         const double* phi = &Eb.phi[lf][fl][gq * np];
-        T w[4], wb[4], fc[2][4];
+        T w[4], wb[4], fc[2][4], fv[2][4];
         for (int f = 0; f < 4; ++f) {
           w[f] = 0.0;
           for (int j = 0; j < np; ++j) w[f] += U[woff + f * np + j] * phi[j];
         }
         boundary_state(M.bc[K * 3 + lf], w, nx, ny, P, wb);
         euler_flux(wb, P.gamma, fc);
+        for (int k = 0; k < 2; ++k) for (int f = 0; f < 4; ++f) fv[k][f] = 0.0;
+        if (ns) {
+          // no-slip adiabatic wall: q_b = q_h (the interior gradient), and the
+          // wall's viscous flux is (0, tau, 0): the energy row (tau.v_b + k grad T)
+          // vanishes as v_b = 0 and grad T . n = 0
+          T qv[2][4];
+          for (int k = 0; k < 2; ++k)
+            for (int f = 0; f < 4; ++f) {
+              qv[k][f] = 0.0;
+              for (int j = 0; j < np; ++j) qv[k][f] += U[(k * 4 + f) * np + j] * phi[j];
+            }
+          ns_viscous_flux(wb, qv, P, fv);
+          fv[0][3] = 0.0;
+          fv[1][3] = 0.0;
+          // -<tau.n, w_b>_dK in the q equations
+          for (int k = 0; k < 2; ++k) {
+            const double nk_ = (k == 0) ? nx : ny;
+            for (int f = 0; f < 4; ++f)
+              for (int j = 0; j < np; ++j) Nu[(k * 4 + f) * np + j] -= we * phi[j] * nk_ * wb[f];
+          }
+        }
         for (int f = 0; f < 4; ++f)
-          for (int j = 0; j < np; ++j) Nu[woff + f * np + j] += we * phi[j] * (nx * fc[0][f] + ny * fc[1][f]);
+          for (int j = 0; j < np; ++j)
+            Nu[woff + f * np + j] += we * phi[j] * (nx * (fc[0][f] - fv[0][f]) + ny * (fc[1][f] - fv[1][f]));
       }
       continue;
     }
@@ -799,7 +826,8 @@ void orc_ns_viscous_flux(const double* w, const double* q, const orc_params* P, 
 // Build the mesh.  Returns 0 ok, 2 bad input (non-positive det J, p out of
 // range, a face not shared by exactly two elements, two elements sharing two faces).
 // elem_bc (may be null: every face interior) [n_elem][3]: 0 interior, 1 slip
-// wall, 2 far field; boundary faces carry no trace unknowns (Euler only).
+// wall, 2 far field (Euler), 3 no-slip adiabatic wall (Navier-Stokes);
+// boundary faces carry no trace unknowns.
 int orc_mesh_create(int n_elem, int nfield, const double* elem_xy, const int32_t* elem_vid,
                     const int8_t* elem_p, const int8_t* elem_bc, void** out) {
   ensure_tables();
@@ -812,7 +840,9 @@ int orc_mesh_create(int n_elem, int nfield, const double* elem_xy, const int32_t
   M->bc.assign(3 * n_elem, 0);
   for (int t = 0; elem_bc && t < 3 * n_elem; ++t) {
     M->bc[t] = elem_bc[t];
-    if (M->bc[t] < 0 || M->bc[t] > 2 || (M->bc[t] != 0 && nfield != 4)) { delete M; return 2; }
+    const int b = M->bc[t];
+    const bool ok = b == 0 || (nfield == 4 && (b == 1 || b == 2)) || (nfield == 12 && b == 3);
+    if (!ok) { delete M; return 2; }
   }
   for (int K = 0; K < n_elem; ++K) {
     M->p[K] = elem_p[K];

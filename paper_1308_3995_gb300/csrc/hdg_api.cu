@@ -401,6 +401,8 @@ hdg_status ensure_streams(hdg_sys* S) {
   for (int p = 1; p <= kMaxP; ++p) {
     HDG_CK(S->ctx, cudaStreamCreateWithFlags(&S->bstream[p], cudaStreamNonBlocking));
     HDG_CK(S->ctx, cudaEventCreateWithFlags(&S->bevent[p], cudaEventDisableTiming));
+    HDG_CK(S->ctx, cudaEventCreate(&S->tbeg[p]));
+    HDG_CK(S->ctx, cudaEventCreate(&S->tend[p]));
   }
   HDG_CK(S->ctx, cudaEventCreateWithFlags(&S->fork, cudaEventDisableTiming));
   S->have_streams = true;
@@ -486,6 +488,8 @@ hdg_status hdg_sys_destroy(hdg_sys* S) {
     for (int p = 1; p <= kMaxP; ++p) {
       cudaStreamDestroy(S->bstream[p]);
       cudaEventDestroy(S->bevent[p]);
+      cudaEventDestroy(S->tbeg[p]);
+      cudaEventDestroy(S->tend[p]);
     }
     cudaEventDestroy(S->fork);
   }
@@ -512,10 +516,17 @@ hdg_status hdg_condense(hdg_sys* S, const double* U, const double* Lam, void* st
     hdg_status rs = ensure_streams(S);
     if (rs != HDG_OK) return rs;
     HDG_CK(ctx, cudaEventRecord(S->fork, st));
+    // per-bucket timing events, except inside a graph capture
+    cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+    HDG_CK(ctx, cudaStreamIsCapturing(st, &cap));
+    S->timed = cap == cudaStreamCaptureStatusNone;
     void* bs[kMaxP + 1] = {};
     for (int p = 1; p <= kMaxP; ++p) {
       bs[p] = S->bstream[p];
-      if (M->bucket_n[p]) HDG_CK(ctx, cudaStreamWaitEvent(S->bstream[p], S->fork, 0));
+      if (M->bucket_n[p]) {
+        HDG_CK(ctx, cudaStreamWaitEvent(S->bstream[p], S->fork, 0));
+        if (S->timed) HDG_CK(ctx, cudaEventRecord(S->tbeg[p], S->bstream[p]));
+      }
     }
     Phys ph = S->ph;
     ph.persistent = 0;
@@ -524,15 +535,31 @@ hdg_status hdg_condense(hdg_sys* S, const double* U, const double* Lam, void* st
     if (n >= 0)
       for (int p = 1; p <= kMaxP; ++p)
         if (M->bucket_n[p]) {
+          if (S->timed) HDG_CK(ctx, cudaEventRecord(S->tend[p], S->bstream[p]));
           HDG_CK(ctx, cudaEventRecord(S->bevent[p], S->bstream[p]));
           HDG_CK(ctx, cudaStreamWaitEvent(st, S->bevent[p], 0));
         }
   } else {
+    S->timed = false;
     n = launch_condense(M->dm, S->ds, S->ph, ctx->d_tab, ctx->d_tab_ff, ctx->tab.off, U, Lam, M->d_bucket,
                         M->bucket_n, M->bucket_ntmax, stream, &err);
   }
   if (n < 0) return fail(ctx, HDG_ECUDA, "hdg_condense: " + err);
   S->launches = n;
+  return HDG_OK;
+}
+
+hdg_status hdg_sys_bucket_times(const hdg_sys* S, float* ms) {
+  if (!S || !ms) return HDG_EINVAL;
+  for (int p = 0; p <= kMaxP; ++p) ms[p] = -1.0f;
+  if (!S->timed) return HDG_OK;
+  const hdg_mesh* M = S->mesh;
+  for (int p = 1; p <= kMaxP; ++p) {
+    if (!M->bucket_n[p]) continue;
+    if (cudaEventSynchronize(S->tend[p]) != cudaSuccess ||
+        cudaEventElapsedTime(&ms[p], S->tbeg[p], S->tend[p]) != cudaSuccess)
+      return fail(S->ctx, HDG_ECUDA, "hdg_sys_bucket_times: event query failed");
+  }
   return HDG_OK;
 }
 

@@ -45,6 +45,9 @@ struct hdg_sys {
   // degree buckets launched concurrently: one stream and one event per degree, a fork event
   cudaStream_t bstream[hdg::kMaxP + 1] = {};
   cudaEvent_t bevent[hdg::kMaxP + 1] = {};
+  cudaEvent_t tbeg[hdg::kMaxP + 1] = {};  // timing events around each bucket's launches
+  cudaEvent_t tend[hdg::kMaxP + 1] = {};
+  bool timed = false;                      // the last hdg_condense recorded them
   cudaEvent_t fork = nullptr;
   bool have_streams = false;
   // captured step (hdg_graph_create)

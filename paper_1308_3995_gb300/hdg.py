@@ -36,7 +36,8 @@ EXPORTS = ["hdg_create", "hdg_destroy", "hdg_last_error", "hdg_mesh_create", "hd
            "hdg_sys_set_cfl", "hdg_cfl_law", "hdg_autotune", "hdg_trace_solve_ex", "hdg_adjoint_condense",
            "hdg_adapt_indicators", "hdg_adapt_mark",
            "hdg_mesh_create_bc", "hdg_solver_set_preconditioner", "hdg_solver_setup", "hdg_solver_precond_apply",
-           "hdg_solver_colors", "hdg_solver_create_ws", "hdg_solver_workspace_bytes", "hdg_solve_step_host"]
+           "hdg_solver_colors", "hdg_solver_create_ws", "hdg_solver_workspace_bytes", "hdg_solve_step_host",
+           "hdg_sys_bucket_times"]
 
 
 class HdgError(RuntimeError):
@@ -130,6 +131,7 @@ def lib(build: bool = True):
         L.hdg_solver_setup.argtypes = [_vp, _vp]
         L.hdg_solver_precond_apply.argtypes = [_vp, _vp, _vp, ctypes.c_int32, _vp]
         L.hdg_solver_colors.argtypes = [_vp, ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(ctypes.c_int32)]
+        L.hdg_sys_bucket_times.argtypes = [_vp, ctypes.POINTER(ctypes.c_float)]
         L.hdg_solver_create_ws.argtypes = [_vp, ctypes.c_int32, ctypes.c_int32, _vp, ctypes.c_int64,
                                            ctypes.POINTER(_vp)]
         L.hdg_solver_workspace_bytes.argtypes = [_vp, ctypes.c_int32, ctypes.c_int32]
@@ -428,6 +430,12 @@ class System:
     @property
     def launches(self) -> int:
         return int(lib().hdg_sys_launches(self.h))
+
+    def bucket_times(self) -> dict:
+        """hdg_sys_bucket_times: {p: ms} of each degree bucket in the last multi-bucket condensation."""
+        ms = (ctypes.c_float * 5)()
+        _check(lib().hdg_sys_bucket_times(self.h, ms), self.ctx.h)
+        return {p: float(ms[p]) for p in range(1, 5) if ms[p] >= 0.0}
 
     def newton_update(self, U, Lam, dU, dLam, stream=None):
         """hdg_newton_update: U += dU, Lam += dLam on device tensors."""

@@ -91,7 +91,7 @@ def periodic_mesh(nx: int, ny: int, jitter: float, seed: int) -> MeshData:
     return MeshData(nx, ny, np.ascontiguousarray(elem_xy), elem_vid, vert_xy)
 
 
-BC_SLIP_WALL, BC_FAR_FIELD = 1, 2
+BC_SLIP_WALL, BC_FAR_FIELD, BC_NO_SLIP_WALL = 1, 2, 3
 
 
 def channel_mesh(nx: int, ny: int, jitter: float, seed: int, bottom: int = BC_SLIP_WALL,
@@ -344,7 +344,9 @@ class Workload:
     prandtl: float = 0.72
     seed: int = 1234
     extra: dict = field(default_factory=dict)
-    domain: str = "periodic"   # "channel": slip wall at y = 0, far field at y = 1; "box": far field all round
+    # "channel": slip wall at y = 0, far field at y = 1; "box": far field all round;
+    # "wall_channel": no-slip adiabatic walls at y = 0 and y = 1 (Navier-Stokes)
+    domain: str = "periodic"
 
     @property
     def n_elem(self) -> int:
@@ -373,6 +375,10 @@ WORKLOADS = {
     # far field on all four sides of the unit square: 8,192 jittered triangles, Euler p=2, Mach 0.5 at
     # 10 degrees + Gaussian density bump, which the steady solve washes out to the free stream
     "euler_box_8k": Workload("euler_box_8k", 64, 64, 0.2, 0, 2, None, "bump", 0.5, 10.0, seed=66, domain="box"),
+    # Navier-Stokes between two no-slip adiabatic walls (y = 0, y = 1), periodic in x: 8,192 jittered
+    # triangles, p in {1,2,3,4} at 40/30/20/10 %, Mach 0.5, Re 5000, Fourier modes on the free stream
+    "ns_wall_channel_8k": Workload("ns_wall_channel_8k", 64, 64, 0.2, 1, None, (0.4, 0.3, 0.2, 0.1), "fourier",
+                                   0.5, 0.0, seed=77, domain="wall_channel"),
 }
 
 
@@ -398,6 +404,8 @@ class Case:
 def make_case(wl: Workload) -> Case:
     if wl.domain == "channel":
         mesh = channel_mesh(wl.nx, wl.ny, wl.jitter, wl.seed)
+    elif wl.domain == "wall_channel":
+        mesh = channel_mesh(wl.nx, wl.ny, wl.jitter, wl.seed, bottom=BC_NO_SLIP_WALL, top=BC_NO_SLIP_WALL)
     elif wl.domain == "box":
         mesh = box_mesh(wl.nx, wl.ny, wl.jitter, wl.seed)
     else:

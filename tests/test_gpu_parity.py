@@ -375,3 +375,23 @@ def test_autotuned_launch_shapes_keep_results_bitwise(ctx, name, kw, precision):
     print(wl.name, ["fp64", "float2"][precision], "shapes", shapes)
     sysm.close()
     mesh.close()
+
+
+def test_bucket_times_of_a_mixed_degree_launch(ctx):
+    """Per-degree device times of a condensation whose degree buckets run concurrently: one positive
+    time per present degree, none for a single-degree mesh."""
+    from paper_1308_3995_gb300 import hdg
+    dev = torch.device("cuda:0")
+    for name, kw, want in (("ns_mixp_65k", {}, None), ("euler_p3_16k", {}, set())):
+        wl = G.small_variant(G.WORKLOADS[name], 12, 14, **kw)
+        case, om, U, Lam, dLam = build_case(wl)
+        mesh = hdg.Mesh(ctx, case.mesh.elem_xy, case.mesh.elem_vid, case.elem_p, case.nfield, case.mesh.elem_bc)
+        sysm = hdg.System(ctx, mesh, lib_params(wl, 0.0, 0))
+        sysm.condense(torch.from_numpy(U).to(dev), torch.from_numpy(Lam).to(dev))
+        t = sysm.bucket_times()
+        present = set(int(p) for p in np.unique(case.elem_p))
+        expect = present if want is None else want
+        assert set(t) == expect and all(v > 0.0 for v in t.values()), (name, t)
+        print(name, t)
+        sysm.close()
+        mesh.close()

@@ -964,3 +964,119 @@ def test_block_ilu0_depends_only_on_the_color_sequence():
     key = (color.max() - color) * m.n_face + np.arange(m.n_face)
     z2 = O.block_ilu0_apply(*O.block_ilu0(A, offs, P, np.argsort(key, kind="stable")), r)
     assert np.abs(z2 - z[0]).max() > 1e-6 * np.abs(z[0]).max()
+
+
+# ----------------------------------------------------------------------------- Navier-Stokes walls
+def _wall_case(nx, ny, **kw):
+    wl = G.small_variant(G.WORKLOADS["ns_wall_channel_8k"], nx, ny, **kw)
+    c = G.make_case(wl)
+    m = O.Mesh(c.mesh.elem_xy, c.mesh.elem_vid, c.elem_p, c.nfield, c.mesh.elem_bc)
+    P = O.Params(model=1, mach=wl.mach, alpha=wl.alpha, reynolds=wl.reynolds, prandtl=wl.prandtl)
+    return wl, c, m, P
+
+
+def test_no_slip_wall_state():
+    """Sec. 2.2: the no-slip wall's boundary function keeps density and total energy and zeroes
+    the momentum, w_b = (rho, 0, 0, E), whatever the normal."""
+    w = _cons(1.1, 0.4, -0.3, 0.8)
+    for n in ((0.0, -1.0), (0.6, 0.8)):
+        wb = O.boundary_state(3, w, n, O.Params(model=1))
+        assert np.array_equal(wb, [w[0], 0.0, 0.0, w[3]])
+
+
+@pytest.mark.parametrize("p", [1, 3])
+def test_ns_wall_channel_rest_state(p):
+    """A fluid at rest (uniform rho and p, v = 0, q = 0) between no-slip adiabatic walls is a steady
+    state: the wall flux is (0, p n, 0), as on interior faces, so every residual row vanishes."""
+    wl, c, m, P = _wall_case(4, 3, p=p, probs=None)
+    U, L = _uniform_state(m, _cons(1.2, 0.0, 0.0, 0.9))
+    Ru, Rl = m.global_residual(P, U, L)
+    assert np.abs(Ru).max() < 1e-13 and np.abs(Rl).max() < 1e-13     # rounding of O(1) flux sums
+    nb = int((c.mesh.elem_bc > 0).sum())
+    assert nb == 2 * wl.nx and m.n_face == (3 * m.n_elem - nb) // 2
+
+
+def test_ns_wall_q_equation_is_consistent():
+    """On a wall element, q = grad w solves the gradient equations exactly for a linear state with
+    zero velocity (then w_b = w on the wall): (tau, q) + (div tau, w) - <tau.n, lambda or w_b> = 0.
+    This fixes the sign of the wall's <tau.n, w_b> term to that of the interior faces' (the printed
+    boundary operator carries the opposite sign, which would leave -2 <tau.n, w_b> here)."""
+    wl, c, m, P = _wall_case(4, 3, p=2, probs=None)
+    bel = [K for K in range(m.n_elem) if c.mesh.elem_bc[K].any()]
+    for K in (bel[0], bel[-1]):
+        U, gw, _, _ = _linear_density_state(m, K, 1.1, [0.3, -0.4], 0.0, 0.0, 0.8)
+        xy = m.elem_xy[K].reshape(3, 2)
+        vid = c.mesh.elem_vid[K]
+
+        def wfun(x):
+            rho = 1.1 + (x - xy[0]) @ np.array([0.3, -0.4])
+            return np.array([rho, 0.0, 0.0, 0.8 / (GAMMA - 1)])
+
+        L = np.zeros(m.lam_len)
+        for lf in range(3):
+            e = m.elem_face[K][lf]
+            if e < 0:
+                continue
+            a, b = lf, (lf + 1) % 3
+            lo, hi = (a, b) if vid[a] < vid[b] else (b, a)
+            wl0, wh = wfun(xy[lo]), wfun(xy[hi])
+            nk = m.face_p[e] + 1
+            for f in range(4):
+                L[m.lam_off[e] + f * nk] = 0.5 * (wl0[f] + wh[f])             # mode 0: mean
+                L[m.lam_off[e] + f * nk + 1] = (wh[f] - wl0[f]) / (2 * math.sqrt(3))  # mode 1
+        Nu, _ = m.element_residual(P, K, U, L)
+        nq = 8 * O.n_basis(int(m.elem_p[K]))
+        assert np.abs(Nu[:nq]).max() < 1e-13
+
+
+def test_ns_wall_conserves_mass_and_energy():
+    """The wall's mass and energy fluxes vanish (v_b = 0; adiabatic: grad T.n = 0), so for any state
+    the element residuals tested with 1 sum to the trace residuals' mean modes in those fields,
+    while the momentum balance picks up the wall force."""
+    wl, c, m, P = _wall_case(4, 3)
+    U, L, _ = G.case_state(c, m.face_vid, m.face_p)
+    Ru, Rl = m.global_residual(P, U, L)
+    tot_el, tot_tr = np.zeros(4), np.zeros(4)
+    for K in range(m.n_elem):
+        nb = O.n_basis(int(m.elem_p[K]))
+        rw = Ru[m.u_off[K] + 8 * nb:m.u_off[K] + 12 * nb].reshape(4, nb)
+        tot_el += rw[:, 0] / math.sqrt(2)                 # test function 1 = phi_0 / sqrt(2)
+    for e in range(m.n_face):
+        nk = m.face_p[e] + 1
+        tot_tr += Rl[m.lam_off[e]:m.lam_off[e] + 4 * nk].reshape(4, nk)[:, 0]
+    scale = np.abs(Rl).max()
+    for f in (0, 3):
+        assert abs(tot_el[f] - tot_tr[f]) < 1e-12 * scale
+    assert abs(tot_el[2] - tot_tr[2]) > 1e-6 * scale        # wall normal force (walls along x)
+
+
+def test_ns_wall_jacobian_vs_central_differences():
+    """Complex-step Newton blocks of wall elements agree with central finite differences."""
+    wl, c, m, P = _wall_case(4, 3, p=2, probs=None)
+    U, L, _ = G.case_state(c, m.face_vid, m.face_p)
+    bel = [K for K in range(m.n_elem) if c.mesh.elem_bc[K].any()]
+    rng = np.random.default_rng(5)
+    for K in (bel[0], bel[-1]):
+        A, B, C, D, F, H = m.element_blocks(P, K, U, L)
+        n = A.shape[0]
+        for col in rng.choice(n, 6, replace=False):
+            h = 1e-6
+            Up, Um = U.copy(), U.copy()
+            Up[m.u_off[K] + col] += h; Um[m.u_off[K] + col] -= h
+            du = (m.element_residual(P, K, Up, L)[0] - m.element_residual(P, K, Um, L)[0]) / (2 * h)
+            assert np.abs(du - A[:, col]).max() < 1e-7 * max(1.0, np.abs(A).max())
+
+
+def test_ns_wall_channel_condensed_then_recovered_equals_monolithic():
+    """Sec. 3.4 with no-slip walls: the condensed solve plus reconstruction equals the monolithic
+    Newton step at CFL 10 (mixed degrees)."""
+    wl, c, m, P = _wall_case(3, 3)
+    P.cfl = 10.0
+    U, L, _ = G.case_state(c, m.face_vid, m.face_p)
+    dU, dL = m.monolithic(P, U, L)
+    r = m.condense(P, U, L)
+    assert r["status"].max() == 0
+    dLc = O.dense_solve(m.dense_K(r["K"]), r["E"])
+    dUc = m.recover(r["X"], dLc)
+    assert np.abs(dLc - dL).max() < 1e-10 * np.abs(dL).max()
+    assert np.abs(dUc - dU).max() < 1e-10 * np.abs(dU).max()
