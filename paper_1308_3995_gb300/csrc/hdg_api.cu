@@ -138,11 +138,14 @@ hdg_status hdg_mesh_create_bc(hdg_ctx* ctx, int32_t n_elem, int32_t nfield, cons
     return fail(ctx, HDG_EINVAL, "hdg_mesh_create: bad arguments");
   bool any_bc = false;
   for (int t = 0; elem_bc && t < 3 * n_elem; ++t) {
-    if (elem_bc[t] < 0 || elem_bc[t] > 2) return fail(ctx, HDG_EINVAL, "hdg_mesh_create_bc: boundary kind not in 0..2");
-    any_bc |= elem_bc[t] != 0;
+    const int b = elem_bc[t];
+    if (b < 0 || b > 3) return fail(ctx, HDG_EINVAL, "hdg_mesh_create_bc: boundary kind not in 0..3");
+    if (b == 3 && nfield == 4)
+      return fail(ctx, HDG_EINVAL, "hdg_mesh_create_bc: the no-slip wall (kind 3) is a Navier-Stokes boundary");
+    if ((b == 1 || b == 2) && nfield == 12)
+      return fail(ctx, HDG_ENOTSUP, "hdg_mesh_create_bc: Navier-Stokes boundaries are no-slip adiabatic walls (kind 3)");
+    any_bc |= b != 0;
   }
-  if (any_bc && nfield != 4)
-    return fail(ctx, HDG_ENOTSUP, "hdg_mesh_create_bc: boundary faces are supported for Euler only");
   if (cudaSetDevice(ctx->device) != cudaSuccess) return fail(ctx, HDG_ECUDA, "cudaSetDevice failed");
   hdg_mesh* M = new hdg_mesh();
   M->ctx = ctx;

@@ -18,6 +18,12 @@
 //     C_w = alpha <psi_l, phi_j> delta_fg come from reference tables;
 //   * A_wq and C_q are produced one (direction k', field g) block column at a
 //     time and consumed at once, so they are never stored whole.
+// No-slip adiabatic walls (Sec. 2.2, boundary operator of Sec. 3.2): a wall
+// face has no trace unknowns; its flux is (f_c(w_b) - f_v(w_b, q)) . n with
+// w_b = (rho, 0, 0, E) and the energy row of f_v zero, and the gradient
+// equations see -<tau.n, w_b>, so A_qw of the fields rho and E gains
+// -n_k |e| <phi_i, phi_j>_e (D_k^wall below) and A_ww gains the wall flux's
+// Jacobian in its columns rho and E.
 #pragma once
 
 #include <cuda_runtime.h>
@@ -102,7 +108,7 @@ __global__ void __launch_bounds__(kNsThreads) k_condense_ns(DevMesh m, DevSys s,
   T* sCc = smem + lay.oCc;   // C_q block column [nt][n_p]
 
   __shared__ T g_det, g_ic, g_Ji[2][2], g_n[3][2], g_len[3], g_mt;
-  __shared__ int g_e[3], g_pe[3], g_nk[3], g_toff[4], g_fl[3], g_side[3], g_old[3];
+  __shared__ int g_e[3], g_pe[3], g_nk[3], g_toff[4], g_fl[3], g_side[3], g_old[3], g_wall;
   __shared__ unsigned char g_cf[kMaxNt], g_cg[kMaxNt], g_cl[kMaxNt];
   __shared__ T s_pinv[64];
   __shared__ int s_bad;
@@ -146,8 +152,8 @@ __global__ void __launch_bounds__(kNsThreads) k_condense_ns(DevMesh m, DevSys s,
       const int e = m.elem_face[3 * (size_t)K + a];
       const int info = m.elem_info[K];
       g_e[a] = e;
-      g_pe[a] = m.face_p[e];
-      g_nk[a] = g_pe[a] + 1;
+      g_pe[a] = e >= 0 ? m.face_p[e] : P;  // a wall face: the element's own edge rule,
+      g_nk[a] = e >= 0 ? g_pe[a] + 1 : 0;   // and no trace unknowns
       g_fl[a] = (info >> a) & 1;
       g_side[a] = (info >> (3 + a)) & 1;
       if (tid == 0) {
@@ -188,6 +194,7 @@ __global__ void __launch_bounds__(kNsThreads) k_condense_ns(DevMesh m, DevSys s,
       g_toff[1] = 4 * g_nk[0];
       g_toff[2] = 4 * (g_nk[0] + g_nk[1]);
       g_toff[3] = 4 * (g_nk[0] + g_nk[1] + g_nk[2]);
+      g_wall = (g_e[0] < 0) || (g_e[1] < 0) || (g_e[2] < 0);
     }
     {
       const double* uk = U + m.u_off[K];
@@ -209,6 +216,7 @@ __global__ void __launch_bounds__(kNsThreads) k_condense_ns(DevMesh m, DevSys s,
       g_cl[c] = (unsigned char)(cl - g * nk);
     }
     for (int a = 0; a < 3; ++a) {
+      if (g_e[a] < 0) continue;  // wall face
       const double* lk = Lam + m.lam_off[g_e[a]];
       for (int t = tid; t < 4 * g_nk[a]; t += NT) sL[g_toff[a] + t] = A::from_d(lk[t]);
     }
@@ -272,6 +280,38 @@ __global__ void __launch_bounds__(kNsThreads) k_condense_ns(DevMesh m, DevSys s,
           acc = A::norm(acc);
           if (f < 4) qv[0][f] = acc; else if (f < 8) qv[1][f - 4] = acc; else w[f - 8] = acc;
         }
+        const T nx = g_n[a][0], ny = g_n[a][1];
+        if (g_e[a] < 0) {
+          // no-slip adiabatic wall: w_b = (rho, 0, 0, E), f_v(w_b, q) with its energy row zero
+          const T wb[4] = {w[0], zero, zero, w[3]};
+          euler_flux_jac(wb, C, fx, fy, Ax, Ay);
+          visc_all(wb, qv, V, fv, dw, dq);
+#pragma unroll
+          for (int k = 0; k < 2; ++k) {
+            fv[k][3] = zero;
+#pragma unroll
+            for (int g2 = 0; g2 < 4; ++g2) dw[k][3][g2] = zero;
+#pragma unroll
+            for (int kg = 0; kg < 8; ++kg) dq[k][3][kg] = zero;
+          }
+#pragma unroll
+          for (int f = 0; f < 4; ++f)
+            sFhat[t * 4 + f] = A::mul(we, A::add(A::mul(nx, A::sub(fx[f], fv[0][f])), A::mul(ny, A::sub(fy[f], fv[1][f]))));
+          // d f_hat / d w = (d f / d w_b) diag(1, 0, 0, 1): columns rho and E (slot of d f_hat / d lambda)
+#pragma unroll
+          for (int f = 0; f < 4; ++f)
+#pragma unroll
+            for (int g2 = 0; g2 < 4; ++g2) {
+              const T an = A::add(A::mul(nx, A::sub(Ax[f * 4 + g2], dw[0][f][g2])), A::mul(ny, A::sub(Ay[f * 4 + g2], dw[1][f][g2])));
+              sAl[t * 16 + f * 4 + g2] = (g2 == 0 || g2 == 3) ? A::mul(we, an) : zero;
+            }
+#pragma unroll
+          for (int f = 1; f < 4; ++f)
+#pragma unroll
+            for (int kg = 0; kg < 8; ++kg)
+              sAq[t * 24 + (f - 1) * 8 + kg] = A::neg(A::mul(we, A::add(A::mul(nx, dq[0][f][kg]), A::mul(ny, dq[1][f][kg]))));
+          continue;
+        }
 #pragma unroll
         for (int f = 0; f < 4; ++f) {
           T al = zero;
@@ -280,7 +320,6 @@ __global__ void __launch_bounds__(kNsThreads) k_condense_ns(DevMesh m, DevSys s,
         }
         euler_flux_jac(lam, C, fx, fy, Ax, Ay);
         visc_all(lam, qv, V, fv, dw, dq);  // f_v(lambda, q_K) and its derivatives
-        const T nx = g_n[a][0], ny = g_n[a][1];
 #pragma unroll
         for (int f = 0; f < 4; ++f)
           sFhat[t * 4 + f] = A::mul(we, A::sub(A::add(A::mul(nx, A::sub(fx[f], fv[0][f])), A::mul(ny, A::sub(fy[f], fv[1][f]))),
@@ -344,9 +383,18 @@ __global__ void __launch_bounds__(kNsThreads) k_condense_ns(DevMesh m, DevSys s,
       A::madd(acc, g_det, sU[t]);
       for (int j = 0; j < NP; ++j) A::madd(acc, sDk[k * NP * NP + i * NP + j], sU[(8 + f) * NP + j]);
       for (int a = 0; a < 3; ++a) {
+        const T sc = A::mul(g_n[a][k], g_len[a]);
+        if (g_e[a] < 0) {  // wall: -n_k <phi_i, w_b,f>_e, w_b = (rho, 0, 0, E)
+          if (f == 0 || f == 3) {
+            const T* fm = tab + to.face_mass[P][P][a];
+            T s2 = zero;
+            for (int j = 0; j < NP; ++j) A::madd(s2, fm[i * NP + j], sU[(8 + f) * NP + j]);
+            A::msub(acc, sc, A::norm(s2));
+          }
+          continue;
+        }
         const int nk = g_nk[a];
         const T* me = tab + to.edge_cross[P][g_pe[a]][a][g_fl[a]];
-        const T sc = A::mul(g_n[a][k], g_len[a]);
         T s2 = zero;
         for (int l = 0; l < nk; ++l) A::madd(s2, me[l * NP + i], sL[g_toff[a] + f * nk + l]);
         A::msub(acc, sc, A::norm(s2));
@@ -450,16 +498,49 @@ __global__ void __launch_bounds__(kNsThreads) k_condense_ns(DevMesh m, DevSys s,
       __syncthreads();
     }
     // face mass alpha <phi_i, phi_j>_dK and the pseudo-time mass on the diagonal blocks; F_w
+    T* sDw = sW;  // D_k^wall = D_k - sum over wall faces n_k |e| <phi_i, phi_j>_e (sW is dead here)
     for (int t = tid; t < NP * NP; t += NT) {
       const int i = t / NP, j = t - i * NP;
       T v = zero;
-      for (int a = 0; a < 3; ++a) A::madd(v, g_len[a], tab[to.face_mass[P][g_pe[a]][a] + t]);
+      for (int a = 0; a < 3; ++a)
+        if (g_e[a] >= 0) A::madd(v, g_len[a], tab[to.face_mass[P][g_pe[a]][a] + t]);  // no alpha on walls
       v = A::mul(alpha, A::norm(v));
       if (i == j) v = A::add(v, g_mt);
 #pragma unroll
       for (int f = 0; f < 4; ++f) {
         T* p = &sA[(f * NP + i) * LDA + f * NP + j];
         *p = A::add(*p, v);
+      }
+      if (g_wall) {
+        // wall flux Jacobian <phi_i, (d f_hat_b / d w)_fg phi_j>_e in the columns g = rho, E
+        T wv[4][2], b0 = zero, b1 = zero;
+#pragma unroll
+        for (int f = 0; f < 4; ++f) wv[f][0] = wv[f][1] = zero;
+        for (int a = 0; a < 3; ++a) {
+          if (g_e[a] >= 0) continue;
+          const T* phe = tab + to.edge_phi[P][P][a][g_fl[a]];
+          for (int q = 0; q < P + 2; ++q) {
+            const T pp = A::mul(phe[q * NP + i], phe[q * NP + j]);
+            const T* al = sAl + (a * kNsPt + q) * 16;
+#pragma unroll
+            for (int f = 0; f < 4; ++f) {
+              A::madd(wv[f][0], pp, al[f * 4]);
+              A::madd(wv[f][1], pp, al[f * 4 + 3]);
+            }
+          }
+          const T fmv = A::mul(g_len[a], tab[to.face_mass[P][P][a] + t]);
+          A::madd(b0, g_n[a][0], fmv);
+          A::madd(b1, g_n[a][1], fmv);
+        }
+#pragma unroll
+        for (int f = 0; f < 4; ++f) {
+          T* p0 = &sA[(f * NP + i) * LDA + j];
+          T* p3 = &sA[(f * NP + i) * LDA + 3 * NP + j];
+          *p0 = A::norm(A::add(*p0, A::norm(wv[f][0])));
+          *p3 = A::norm(A::add(*p3, A::norm(wv[f][1])));
+        }
+        sDw[t] = A::norm(A::sub(sDk[t], A::norm(b0)));
+        sDw[NP * NP + t] = A::norm(A::sub(sDk[NP * NP + t], A::norm(b1)));
       }
     }
     for (int t = tid; t < NW4; t += NT) sR[t * ldr + nt] = A::neg(sNu[8 * NP + t]);
@@ -515,7 +596,8 @@ __global__ void __launch_bounds__(kNsThreads) k_condense_ns(DevMesh m, DevSys s,
         sBc[t] = A::norm(acc);
       }
       __syncthreads();
-      const T* Dk = sDk + kd * NP * NP;
+      // A_qw block of field gq: D_k, or D_k^wall for rho and E on a wall element
+      const T* Dk = ((g_wall && (gq == 0 || gq == 3)) ? sDw : sDk) + kd * NP * NP;
       // (i) A'[(f,i),(g,j)] -= 1/det sum_i' A_wq[(f,i),i'] D_k'[i'][j]
       for (int t = r0 * NP + tid; t < NW4 * NP; t += NT) {
         const int r = t / NP, jj = t - r * NP;
@@ -619,7 +701,8 @@ __global__ void __launch_bounds__(kNsThreads) k_condense_ns(DevMesh m, DevSys s,
           const T* me = tab + to.edge_cross[P][g_pe[a]][a][g_fl[a]];
           acc = A::neg(A::mul(A::mul(g_n[a][k], g_len[a]), me[l * NP + i]));   // B_q
         }
-        for (int j = 0; j < NP; ++j) A::msub(acc, sDk[k * NP * NP + i * NP + j], sR[(f * NP + j) * ldr + c]);
+        const T* Dq = ((g_wall && (f == 0 || f == 3)) ? sDw : sDk) + k * NP * NP;
+        for (int j = 0; j < NP; ++j) A::msub(acc, Dq[i * NP + j], sR[(f * NP + j) * ldr + c]);
         const T v = A::mul(A::norm(acc), ic);
         xk[(size_t)c * N + r] = A::to_d(v);
         bad |= A::bad(v);
@@ -647,6 +730,7 @@ __global__ void __launch_bounds__(kNsThreads) k_condense_ns(DevMesh m, DevSys s,
     // two-sided sums: side 0 parks its halves in K/E/res_lam, side 1 in the work space
     for (int a = 0; a < 3; ++a) {
       const int e = g_e[a], m4 = 4 * g_nk[a], o = g_toff[a];
+      if (e < 0) continue;  // wall face: nothing to assemble
       const int64_t lo = m.lam_off[e];
       double* dd = g_side[a] ? s.dhalf1 + m.dblk_off[e] : s.K + m.kblk[9 * (size_t)K + 4 * a];
       double* de = g_side[a] ? s.ehalf1 + lo : s.E + lo;
@@ -663,7 +747,7 @@ __global__ void __launch_bounds__(kNsThreads) k_condense_ns(DevMesh m, DevSys s,
     __threadfence();
     __syncthreads();
     if (tid < 3) {
-      g_old[tid] = atomicAdd(&s.face_cnt[g_e[tid]], 1);
+      g_old[tid] = g_e[tid] >= 0 ? atomicAdd(&s.face_cnt[g_e[tid]], 1) : 0;
       __threadfence();
     }
     __syncthreads();

@@ -192,10 +192,78 @@ def test_channel_adjoint_matches_transposed_monolithic(ctx):
     solver.close(); adj.close(); primal.close(); mesh.close()
 
 
-def test_navier_stokes_meshes_with_boundaries_rejected(ctx):
+def test_boundary_kinds_checked_against_the_model(ctx):
+    """Navier-Stokes meshes take no-slip walls only (slip wall / far field: HDG_ENOTSUP); the no-slip
+    wall is not an Euler boundary (HDG_EINVAL)."""
     from paper_1308_3995_gb300 import hdg
     wl = G.small_variant(G.WORKLOADS["euler_channel_8k"], 4, 3, model=1)
     case = G.make_case(wl)
     with pytest.raises(hdg.HdgError) as ei:
         hdg.Mesh(ctx, case.mesh.elem_xy, case.mesh.elem_vid, case.elem_p, case.nfield, case.mesh.elem_bc)
     assert ei.value.status == hdg.HDG_ENOTSUP
+    wl = G.small_variant(G.WORKLOADS["ns_wall_channel_8k"], 4, 3, model=0, p=2, probs=None)
+    case = G.make_case(wl)
+    with pytest.raises(hdg.HdgError) as ei:
+        hdg.Mesh(ctx, case.mesh.elem_xy, case.mesh.elem_vid, case.elem_p, case.nfield, case.mesh.elem_bc)
+    assert ei.value.status == hdg.HDG_EINVAL
+
+
+# ----------------------------------------------------------------------------- Navier-Stokes walls
+@pytest.mark.parametrize("precision", [0, 1])
+@pytest.mark.parametrize("p,cfl,sc", [(1, 0.0, 0.0), (2, 10.0, 0.0), (3, 0.0, 0.0), (4, 0.0, 0.0),
+                                      (None, 0.0, 0.0), (None, 10.0, 0.0), (2, 0.0, 0.2)])
+def test_ns_wall_channel_parity(ctx, precision, p, cfl, sc):
+    """Navier-Stokes between no-slip adiabatic walls (Sec. 2.2, 3.2), every element and face against
+    the oracle: wall flux, its Jacobian in the rho and E columns, the wall term of the gradient
+    equations inside the in-element q elimination."""
+    kw = {"p": p, "probs": None} if p else {}
+    wl = G.small_variant(G.WORKLOADS["ns_wall_channel_8k"], 5, 4, **kw)
+    case, om, U, Lam, dLam, mesh, sysm = _setup(ctx, wl, cfl, precision, sc)
+    for name in ("face_vid", "face_el", "face_p", "elem_face", "u_off", "lam_off", "x_off", "k_col", "k_blkoff"):
+        assert np.array_equal(np.asarray(getattr(mesh, name)).ravel(), np.asarray(getattr(om, name)).ravel()), name
+    g = _run(sysm, mesh, U, Lam, dLam)
+    assert np.all(g["status"] == 0)
+    chk = ParityChecker(om, oracle_params(wl, cfl, sc), U, Lam, dLam, g)
+    errs = chk.run(range(om.n_elem), range(om.n_face))
+    print(wl.name, p, cfl, sc, ["fp64", "float2"][precision], {k: f"{v:.1e}" for k, v in errs.items()})
+    for k, v in errs.items():
+        assert v < [TOL, TOL_MIXED][precision], (k, v)
+    sysm.close(); mesh.close()
+
+
+def test_ns_wall_channel_rest_state_residual_vanishes(ctx):
+    """Fluid at rest between no-slip adiabatic walls: every residual row is zero on the GPU too."""
+    wl = G.small_variant(G.WORKLOADS["ns_wall_channel_8k"], 8, 6, p=3, probs=None)
+    case, om, U, Lam, dLam, mesh, sysm = _setup(ctx, wl)
+    w0 = G.conserved(1.2, 0.0, 0.0, 0.9 * 0.4)
+    nb = 10
+    U = np.zeros(mesh.u_len); L = np.zeros(mesh.lam_len)
+    for f in range(4):
+        U.reshape(-1, 12 * nb)[:, 8 * nb + f * nb] = w0[f] / np.sqrt(2)
+        L.reshape(-1, 16)[:, f * 4] = w0[f]
+    g = _run(sysm, mesh, U, L, dLam)
+    assert np.abs(g["res_u"]).max() < 1e-13 and np.abs(g["res_lam"]).max() < 1e-13
+    sysm.close(); mesh.close()
+
+
+def test_ns_wall_channel_newton_step_matches_oracle_monolithic(ctx):
+    """One pseudo-transient Newton step (CFL 10) with walls: GPU condensation, GMRES + block ILU(0)
+    trace solve, reconstruction -- against the oracle's monolithic step (complex-step Jacobian of the
+    global residual, dense solve)."""
+    from paper_1308_3995_gb300 import hdg
+    wl = G.small_variant(G.WORKLOADS["ns_wall_channel_8k"], 3, 3)
+    case, om, U, Lam, dLam, mesh, sysm = _setup(ctx, wl, 10.0)
+    dev = torch.device("cuda:0")
+    Ut, Lt = torch.from_numpy(U).to(dev), torch.from_numpy(Lam).to(dev)
+    sysm.condense(Ut, Lt)
+    solver = hdg.Solver(sysm, restart=40, precond=2)
+    x = torch.zeros(mesh.lam_len, dtype=torch.float64, device=dev)
+    it, rel = solver.solve(x, rtol=1e-13, max_iter=2000)
+    dUt = torch.empty(mesh.u_len, dtype=torch.float64, device=dev)
+    sysm.recover(x, dUt)
+    torch.cuda.synchronize()
+    dU, dL = om.monolithic(oracle_params(wl, 10.0), U, Lam)
+    eU, eL = rel_err(dUt.cpu().numpy(), dU), rel_err(x.cpu().numpy(), dL)
+    print(wl.name, "iterations", it, f"dU {eU:.1e} dLambda {eL:.1e}")
+    assert eU < 1e-9 and eL < 1e-9
+    solver.close(); sysm.close(); mesh.close()
