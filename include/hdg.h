@@ -401,7 +401,7 @@ hdg_status hdg_solve_step_host(hdg_sys* sys, hdg_solver* solver, const double* U
  * [lam_len] (K of the last hdg_condense). */
 hdg_status hdg_trace_matvec(hdg_solver* solver, const double* x, double* y, int32_t transpose, void* stream);
 
-/* Hybridized adjoint (Sec. 4.2, Euler in this build).  The adjoint system is
+/* Hybridized adjoint (Sec. 4.2; Euler and Navier-Stokes).  The adjoint system is
  * the transpose of the Newton matrix of `primal` (same mesh and parameters,
  * pseudo-time mass included), right-hand side [F~; 0] (F~ = J'(U) for a target
  * functional J of the interior unknowns; the trace part is zero in the
@@ -412,7 +412,9 @@ hdg_status hdg_trace_matvec(hdg_solver* solver, const double* x, double* y, int3
  * Then solve K^T Lambda~ = E~ with hdg_trace_solve_ex(solver of primal,
  * E~ of adj, transpose = 1, ...) and reconstruct U~ = X~_F - X~_C Lambda~ with
  * hdg_recover(adj, Lambda~, U~).  adj must be a separate system on the same
- * mesh with the same parameters (HDG_EINVAL otherwise; HDG_ENOTSUP for NS). */
+ * mesh with the same parameters (HDG_EINVAL otherwise).  For Navier-Stokes
+ * F~ covers all of [Q; W] (a functional of the gradient, e.g. a wall shear,
+ * has a q part). */
 hdg_status hdg_adjoint_condense(hdg_sys* adj, const hdg_sys* primal, const double* U, const double* Lam,
                                 const double* Ftilde, void* stream);
 

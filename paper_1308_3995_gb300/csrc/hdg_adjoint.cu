@@ -75,7 +75,6 @@ hdg_status hdg_adjoint_condense(hdg_sys* adj, const hdg_sys* primal, const doubl
   if (!U || !Lam || !Ftilde) return fail(ctx, HDG_EINVAL, "hdg_adjoint_condense: null input");
   const hdg_mesh* M = adj->mesh;
   if (primal->mesh != M) return fail(ctx, HDG_EINVAL, "hdg_adjoint_condense: systems on different meshes");
-  if (M->nfield != 4) return fail(ctx, HDG_ENOTSUP, "hdg_adjoint_condense: Euler only in this build");
   if (primal->ph.precision != adj->ph.precision || primal->ph.cfl != adj->ph.cfl ||
       primal->ph.sc_eps0 != adj->ph.sc_eps0)
     return fail(ctx, HDG_EINVAL, "hdg_adjoint_condense: primal and adjoint systems have different parameters");

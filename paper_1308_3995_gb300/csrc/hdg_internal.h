@@ -47,7 +47,7 @@ struct Phys {
   double winf[4];           // far-field conserved state (Sec. 2.1)
   int model, precision;
   int persistent;  // 1: grid = SMs x resident CTAs (loop over elements); 0: one CTA per element
-  int adjoint;     // 1: adjoint local solves X~ = A^{-T} [C^T | F~] only (Sec. 4.2; Euler)
+  int adjoint;     // 1: adjoint local solves X~ = A^{-T} [C^T | F~] only (Sec. 4.2)
   // launch shape per degree (autotuned): -1 default (by `persistent`), 0 one CTA per element,
   // k > 0 persistent grid of k CTAs per SM (capped by the occupancy)
   int grid[kMaxP + 1];

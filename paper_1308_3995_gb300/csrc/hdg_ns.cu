@@ -9,6 +9,11 @@ bool launch_ns_ff(int p, const DevMesh& m, const DevSys& s, const Phys& ph, cons
 
 int ns_occupancy_ff(int p, int ntmax);
 
+// adjoint-mode instantiations (Sec. 4.2), in translation units of their own
+bool launch_ns_adjoint(int p, const DevMesh& m, const DevSys& s, const Phys& ph, const double* tab,
+                       const void* tab_ff, const TabOff& to, const double* U, const double* Lam, const int* elems,
+                       int n, int ntmax, cudaStream_t st, std::string* err);
+
 int ns_occupancy(const Phys& ph, int p, int ntmax) {
   return ph.precision == HDG_FP64 ? ns_occ_p<double>(p, ntmax) : ns_occupancy_ff(p, ntmax);
 }
@@ -22,7 +27,9 @@ int launch_condense_ns(const DevMesh& m, const DevSys& s, const Phys& ph, const 
     if (bucket_n[p] == 0) continue;
     cudaStream_t st = (cudaStream_t)(bucket_streams ? bucket_streams[p] : stream);
     bool ok;
-    if (ph.precision == HDG_FP64)
+    if (ph.adjoint)
+      ok = launch_ns_adjoint(p, m, s, ph, tab, tab_ff, to, U, Lam, bucket[p], bucket_n[p], bucket_ntmax[p], st, err);
+    else if (ph.precision == HDG_FP64)
       ok = launch_ns_p<double>(p, m, s, ph, tab, to, U, Lam, bucket[p], bucket_n[p], bucket_ntmax[p], st, err);
     else
       ok = launch_ns_ff(p, m, s, ph, tab_ff, to, U, Lam, bucket[p], bucket_n[p], bucket_ntmax[p], st, err);

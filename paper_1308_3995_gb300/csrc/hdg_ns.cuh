@@ -18,6 +18,10 @@
 //     C_w = alpha <psi_l, phi_j> delta_fg come from reference tables;
 //   * A_wq and C_q are produced one (direction k', field g) block column at a
 //     time and consumed at once, so they are never stored whole.
+// Adjoint mode (Sec. 4.2, ph.adjoint): X~ = A^{-T} [C^T | F~] by the same
+// elimination transposed: A'^T X~_w = G_w - A_qw^T G_q / det (G = [C^T | F~],
+// A' the Schur matrix above), then X~_q = (G_q - A_wq^T X~_w) / det with the
+// block columns of A_wq and C_q produced a second time after the LU.
 // No-slip adiabatic walls (Sec. 2.2, boundary operator of Sec. 3.2): a wall
 // face has no trace unknowns; its flux is (f_c(w_b) - f_v(w_b, q)) . n with
 // w_b = (rho, 0, 0, E) and the energy row of f_v zero, and the gradient
@@ -70,8 +74,8 @@ struct NsLayout {
   }
 };
 
-template <int P, class T>
-__global__ void __launch_bounds__(kNsThreads) k_condense_ns(DevMesh m, DevSys s, Phys ph, const T* __restrict__ tab,
+template <int P, class T, bool ADJ>
+__global__ void __launch_bounds__(kNsThreads, 1) k_condense_ns(DevMesh m, DevSys s, Phys ph, const T* __restrict__ tab,
                                                              TabOff to, const double* __restrict__ U,
                                                              const double* __restrict__ Lam,
                                                              const int* __restrict__ elems, int n_elems, int ntmax) {
@@ -441,14 +445,20 @@ __global__ void __launch_bounds__(kNsThreads) k_condense_ns(DevMesh m, DevSys s,
       a0[2 * NP] = A::neg(sDk[NP * NP + t]);
       a0[3 * NP] = zero;
     }
-    // B_w: rows (f,i) over warps, trace columns over lanes
+    // B_w: rows (f,i) over warps, trace columns over lanes; in adjoint mode C_w^T instead,
+    // C_w^T[(f,i), (a,g,l)] = alpha |e_a| <psi_l, phi_i> delta_fg
+    constexpr bool adjoint = ADJ;  // a separate instantiation: the primal kernel carries none of it
     for (int r = ty; r < NW4; r += NW) {
       const int f = r / NP, i = r - f * NP;
       for (int c = tx; c < nt; c += 32) {
         const int a = g_cf[c], g = g_cg[c], l = g_cl[c], nk = g_nk[a];
-        const T* phe = tab + to.edge_phi[P][g_pe[a]][a][g_fl[a]];
         T acc = zero;
-        for (int q = 0; q < nk + 1; ++q) A::madd(acc, phe[q * NP + i], sW[((a * kNsPt + q) * 16 + f * 4 + g) * 5 + l]);
+        if (adjoint) {
+          if (g == f) acc = A::mul(A::mul(alpha, g_len[a]), tab[to.edge_cross[P][g_pe[a]][a][g_fl[a]] + l * NP + i]);
+        } else {
+          const T* phe = tab + to.edge_phi[P][g_pe[a]][a][g_fl[a]];
+          for (int q = 0; q < nk + 1; ++q) A::madd(acc, phe[q * NP + i], sW[((a * kNsPt + q) * 16 + f * 4 + g) * 5 + l]);
+        }
         sR[r * ldr + c] = A::norm(acc);
       }
     }
@@ -543,7 +553,8 @@ __global__ void __launch_bounds__(kNsThreads) k_condense_ns(DevMesh m, DevSys s,
         sDw[NP * NP + t] = A::norm(A::sub(sDk[NP * NP + t], A::norm(b1)));
       }
     }
-    for (int t = tid; t < NW4; t += NT) sR[t * ldr + nt] = A::neg(sNu[8 * NP + t]);
+    for (int t = tid; t < NW4; t += NT)  // F_w, or the adjoint right-hand side F~_w
+      sR[t * ldr + nt] = adjoint ? A::from_d(s.ftilde[m.u_off[K] + 8 * NP + t]) : A::neg(sNu[8 * NP + t]);
     __syncthreads();
 
     // ---------------- q elimination, one (k', g) block column at a time ----------------
@@ -554,140 +565,195 @@ __global__ void __launch_bounds__(kNsThreads) k_condense_ns(DevMesh m, DevSys s,
     // mode l -> column toff[a] + g nk_a + l) instead of being filtered.
     const T ic = g_ic;
     const int nq4 = nt / 4;  // trace columns per field
-    for (int kk = 0; kk < 8; ++kk) {
-      const int kd = kk >> 2, gq = kk & 3;
-      // Z'_f[i][q] = sum_r dphi_i/dxi_r Ahat^wq_r,f,kk (rows f = 1..3)
-      for (int t = tid; t < 3 * NP * NQ; t += NT) {
-        const int f1 = t / (NP * NQ), rem = t - f1 * NP * NQ, i = rem / NQ, q = rem - i * NQ;
-        sZ[t] = A::add(A::mul(vgx[q * NP + i], sAwq[(f1 * 8 + kk) * NQ + q]),
-                       A::mul(vge[q * NP + i], sAwq[(24 + f1 * 8 + kk) * NQ + q]));
-      }
-      // C_q block column: rows (a, f, l), C_q = <psi_l, (-n.df_v/dq)_f,kk phi_j>_e
-      for (int t = tid; t < nt * NP; t += NT) {
-        const int r = t / NP, jj = t - r * NP;
-        const int a = g_cf[r], f = g_cg[r], l = g_cl[r], nk = g_nk[a];
-        T acc = zero;
-        if (f > 0) {
-          const T* phe = tab + to.edge_phi[P][g_pe[a]][a][g_fl[a]];
-          const T* ps = tab + to.edge_psi[g_pe[a]];
-          for (int q = 0; q < nk + 1; ++q)
-            A::madd(acc, A::mul(ps[q * nk + l], sAq[(a * kNsPt + q) * 24 + (f - 1) * 8 + kk]), phe[q * NP + jj]);
+    // Pass 0: the q elimination of the primal (or the transposed one of the adjoint mode), the
+    // LU and X_w.  Pass 1 (adjoint mode only): X~_q = (G_q - A_wq^T X~_w) / det.  Each pass
+    // produces the A_wq block column kk = (k', g) into sBc [4 n_p][n_p] and the C_q block column
+    // into sCc [nt][n_p] from the resident point data (sZ is free again after the LU).
+    int bad = 0;
+    for (int pass = 0; pass < 2; ++pass) {
+      if (pass == 1 && !adjoint) break;
+      for (int kk = 0; kk < 8; ++kk) {
+        const int kd = kk >> 2, gq = kk & 3;
+        const int r0 = (shock && gq == 0) ? 0 : NP;  // first row of A_wq that can be nonzero
+        // Z'_f[i][q] = sum_r dphi_i/dxi_r Ahat^wq_r,f,kk (rows f = 1..3)
+        for (int t = tid; t < 3 * NP * NQ; t += NT) {
+          const int f1 = t / (NP * NQ), rem = t - f1 * NP * NQ, i = rem / NQ, q = rem - i * NQ;
+          sZ[t] = A::add(A::mul(vgx[q * NP + i], sAwq[(f1 * 8 + kk) * NQ + q]),
+                         A::mul(vge[q * NP + i], sAwq[(24 + f1 * 8 + kk) * NQ + q]));
         }
-        sCc[t] = A::norm(acc);
-      }
-      __syncthreads();
-      // A_wq block column: volume (Z' phi^T) + face <phi_i, (-n.df_v/dq) phi_j>_dK; rows of field 0
-      // are zero (plus eps D_k on field gq under shock capturing)
-      const int r0 = (shock && gq == 0) ? 0 : NP;  // first row that can be nonzero
-      for (int t = tid; t < NW4 * NP; t += NT) {
-        const int r = t / NP, jj = t - r * NP, f = r / NP, i = r - f * NP;
-        T acc0 = zero, acc1 = zero;
-        if (f > 0) {
-          const T* z = sZ + ((f - 1) * NP + i) * NQ;
-          for (int q = 0; q < NQ; ++q) A::madd(acc0, z[q], vphi[q * NP + jj]);
-          for (int a = 0; a < 3; ++a) {
-            const T* phe = tab + to.edge_phi[P][g_pe[a]][a][g_fl[a]];
-            for (int q = 0; q < g_pe[a] + 2; ++q)
-              A::madd(acc1, A::mul(phe[q * NP + i], sAq[(a * kNsPt + q) * 24 + (f - 1) * 8 + kk]), phe[q * NP + jj]);
-          }
-        }
-        T acc = A::add(A::norm(acc0), A::norm(acc1));
-        if (shock && f == gq) A::madd(acc, eps, sDk[kd * NP * NP + i * NP + jj]);  // frozen shock capturing
-        sBc[t] = A::norm(acc);
-      }
-      __syncthreads();
-      // A_qw block of field gq: D_k, or D_k^wall for rho and E on a wall element
-      const T* Dk = ((g_wall && (gq == 0 || gq == 3)) ? sDw : sDk) + kd * NP * NP;
-      // (i) A'[(f,i),(g,j)] -= 1/det sum_i' A_wq[(f,i),i'] D_k'[i'][j]
-      for (int t = r0 * NP + tid; t < NW4 * NP; t += NT) {
-        const int r = t / NP, jj = t - r * NP;
-        T acc = zero;
-        for (int i2 = 0; i2 < NP; ++i2) A::madd(acc, sBc[r * NP + i2], Dk[i2 * NP + jj]);
-        T* p = &sA[r * LDA + gq * NP + jj];
-        A::msub(*p, ic, A::norm(acc));
-        *p = A::norm(*p);
-      }
-      // (ii)+(iii) R'_w -= 1/det A_wq R_q on the columns of field g and the F column,
-      // B_q = -n_k' |e_a| <phi_i', psi_l>
-      {
-        const int ncol = nq4 + 1;
-        for (int t = tid; t < (NW4 - r0) * ncol; t += NT) {
-          const int r = r0 + t / ncol, cc = t - (t / ncol) * ncol;
+        // C_q block column: rows (a, f, l), C_q = <psi_l, (-n.df_v/dq)_f,kk phi_j>_e
+        for (int t = tid; t < nt * NP; t += NT) {
+          const int r = t / NP, jj = t - r * NP;
+          const int a = g_cf[r], f = g_cg[r], l = g_cl[r], nk = g_nk[a];
           T acc = zero;
-          int c;
-          if (cc == nq4) {
-            c = nt;
-            for (int i2 = 0; i2 < NP; ++i2) A::msub(acc, sBc[r * NP + i2], sNu[kk * NP + i2]);  // F_q = -N_q
-          } else {
-            const int a = (cc < g_nk[0]) ? 0 : (cc < g_nk[0] + g_nk[1] ? 1 : 2);
-            const int l = cc - (a > 0 ? g_nk[0] : 0) - (a > 1 ? g_nk[1] : 0);
-            c = g_toff[a] + gq * g_nk[a] + l;
-            const T* me = tab + to.edge_cross[P][g_pe[a]][a][g_fl[a]];
-            T s2 = zero;
-            for (int i2 = 0; i2 < NP; ++i2) A::madd(s2, sBc[r * NP + i2], me[l * NP + i2]);
-            acc = A::neg(A::mul(A::mul(g_n[a][kd], g_len[a]), A::norm(s2)));   // A_wq B_q
+          if (f > 0) {
+            const T* phe = tab + to.edge_phi[P][g_pe[a]][a][g_fl[a]];
+            const T* ps = tab + to.edge_psi[g_pe[a]];
+            for (int q = 0; q < nk + 1; ++q)
+              A::madd(acc, A::mul(ps[q * nk + l], sAq[(a * kNsPt + q) * 24 + (f - 1) * 8 + kk]), phe[q * NP + jj]);
           }
-          T* p = &sR[r * ldr + c];
+          sCc[t] = A::norm(acc);
+        }
+        __syncthreads();
+        // A_wq block column: volume (Z' phi^T) + face <phi_i, (-n.df_v/dq) phi_j>_dK; rows of field 0
+        // are zero (plus eps D_k on field gq under shock capturing)
+        for (int t = tid; t < NW4 * NP; t += NT) {
+          const int r = t / NP, jj = t - r * NP, f = r / NP, i = r - f * NP;
+          T acc0 = zero, acc1 = zero;
+          if (f > 0) {
+            const T* z = sZ + ((f - 1) * NP + i) * NQ;
+            for (int q = 0; q < NQ; ++q) A::madd(acc0, z[q], vphi[q * NP + jj]);
+            for (int a = 0; a < 3; ++a) {
+              const T* phe = tab + to.edge_phi[P][g_pe[a]][a][g_fl[a]];
+              for (int q = 0; q < g_pe[a] + 2; ++q)
+                A::madd(acc1, A::mul(phe[q * NP + i], sAq[(a * kNsPt + q) * 24 + (f - 1) * 8 + kk]), phe[q * NP + jj]);
+            }
+          }
+          T acc = A::add(A::norm(acc0), A::norm(acc1));
+          if (shock && f == gq) A::madd(acc, eps, sDk[kd * NP * NP + i * NP + jj]);  // frozen shock capturing
+          sBc[t] = A::norm(acc);
+        }
+        __syncthreads();
+        if (pass == 1) {
+          double* xk = s.X + m.x_off[K];
+          const double* ftq = s.ftilde + m.u_off[K] + kk * NP;
+          for (int t = tid; t < NP * nr1; t += NT) {
+            const int c = t / NP, i = t - c * NP;
+            T acc = (c < nt) ? sCc[c * NP + i] : A::from_d(ftq[i]);
+            for (int r = 0; r < NW4; ++r) A::msub(acc, sBc[r * NP + i], sR[r * ldr + c]);
+            const T v = A::mul(A::norm(acc), ic);
+            xk[(size_t)c * N + kk * NP + i] = A::to_d(v);
+            bad |= A::bad(v);
+          }
+          __syncthreads();
+          continue;
+        }
+        // A_qw block of field gq: D_k, or D_k^wall for rho and E on a wall element
+        const T* Dk = ((g_wall && (gq == 0 || gq == 3)) ? sDw : sDk) + kd * NP * NP;
+        // (i) A'[(f,i),(g,j)] -= 1/det sum_i' A_wq[(f,i),i'] D_k'[i'][j]
+        for (int t = r0 * NP + tid; t < NW4 * NP; t += NT) {
+          const int r = t / NP, jj = t - r * NP;
+          T acc = zero;
+          for (int i2 = 0; i2 < NP; ++i2) A::madd(acc, sBc[r * NP + i2], Dk[i2 * NP + jj]);
+          T* p = &sA[r * LDA + gq * NP + jj];
           A::msub(*p, ic, A::norm(acc));
           *p = A::norm(*p);
         }
-      }
-      // (iv) C' -= 1/det C_q A_qw
-      for (int t = tid; t < nt * NP; t += NT) {
-        const int r = t / NP, cc = t - r * NP;
-        if (g_cg[r] == 0) continue;  // C_q row of field 0 is zero
-        T acc = zero;
-        for (int i2 = 0; i2 < NP; ++i2) A::madd(acc, sCc[r * NP + i2], Dk[i2 * NP + cc]);
-        T* p = &sCp[r * ldc + gq * NP + cc];
-        A::msub(*p, ic, A::norm(acc));
-        *p = A::norm(*p);
-      }
-      // (v)+(vi) S0 -= 1/det C_q B_q on the columns of field g, E0 -= 1/det C_q F_q
-      {
-        const int ncol = nq4 + 1;
-        for (int t = tid; t < nt * ncol; t += NT) {
-          const int r = t / ncol, cc = t - r * ncol;
-          if (g_cg[r] == 0) continue;  // C_q row of field 0 is zero
-          T acc = zero;
-          if (cc == nq4) {
-            for (int i2 = 0; i2 < NP; ++i2) A::msub(acc, sCc[r * NP + i2], sNu[kk * NP + i2]);
-            T* p = &sE[r];
-            A::msub(*p, ic, A::norm(acc));
-            *p = A::norm(*p);
-          } else {
-            const int a = (cc < g_nk[0]) ? 0 : (cc < g_nk[0] + g_nk[1] ? 1 : 2);
-            const int l = cc - (a > 0 ? g_nk[0] : 0) - (a > 1 ? g_nk[1] : 0);
-            const int c = g_toff[a] + gq * g_nk[a] + l;
-            const T* me = tab + to.edge_cross[P][g_pe[a]][a][g_fl[a]];
-            T s2 = zero;
-            for (int i2 = 0; i2 < NP; ++i2) A::madd(s2, sCc[r * NP + i2], me[l * NP + i2]);
-            acc = A::neg(A::mul(A::mul(g_n[a][kd], g_len[a]), A::norm(s2)));   // C_q B_q
-            T* p = &sS[r * lds + c];
+        if (adjoint) {
+          // transposed system: G'_w = G_w - A_qw^T G_q / det on the rows of field g, with
+          // G_q = [C_q^T | F~_q] of this block: A_qw^T G_q = D_k'^T [C_q^T | F~_q]
+          const double* ftq = s.ftilde + m.u_off[K] + kk * NP;
+          for (int t = tid; t < NP * nr1; t += NT) {
+            const int i = t / nr1, c = t - i * nr1;
+            T acc = zero;
+            for (int i2 = 0; i2 < NP; ++i2)
+              A::madd(acc, Dk[i2 * NP + i], (c < nt) ? sCc[c * NP + i2] : A::from_d(ftq[i2]));
+            T* p = &sR[(gq * NP + i) * ldr + c];
             A::msub(*p, ic, A::norm(acc));
             *p = A::norm(*p);
           }
+        } else {
+          // (ii)+(iii) R'_w -= 1/det A_wq R_q on the columns of field g and the F column,
+          // B_q = -n_k' |e_a| <phi_i', psi_l>
+          {
+            const int ncol = nq4 + 1;
+            for (int t = tid; t < (NW4 - r0) * ncol; t += NT) {
+              const int r = r0 + t / ncol, cc = t - (t / ncol) * ncol;
+              T acc = zero;
+              int c;
+              if (cc == nq4) {
+                c = nt;
+                for (int i2 = 0; i2 < NP; ++i2) A::msub(acc, sBc[r * NP + i2], sNu[kk * NP + i2]);  // F_q = -N_q
+              } else {
+                const int a = (cc < g_nk[0]) ? 0 : (cc < g_nk[0] + g_nk[1] ? 1 : 2);
+                const int l = cc - (a > 0 ? g_nk[0] : 0) - (a > 1 ? g_nk[1] : 0);
+                c = g_toff[a] + gq * g_nk[a] + l;
+                const T* me = tab + to.edge_cross[P][g_pe[a]][a][g_fl[a]];
+                T s2 = zero;
+                for (int i2 = 0; i2 < NP; ++i2) A::madd(s2, sBc[r * NP + i2], me[l * NP + i2]);
+                acc = A::neg(A::mul(A::mul(g_n[a][kd], g_len[a]), A::norm(s2)));   // A_wq B_q
+              }
+              T* p = &sR[r * ldr + c];
+              A::msub(*p, ic, A::norm(acc));
+              *p = A::norm(*p);
+            }
+          }
+          // (iv) C' -= 1/det C_q A_qw
+          for (int t = tid; t < nt * NP; t += NT) {
+            const int r = t / NP, cc = t - r * NP;
+            if (g_cg[r] == 0) continue;  // C_q row of field 0 is zero
+            T acc = zero;
+            for (int i2 = 0; i2 < NP; ++i2) A::madd(acc, sCc[r * NP + i2], Dk[i2 * NP + cc]);
+            T* p = &sCp[r * ldc + gq * NP + cc];
+            A::msub(*p, ic, A::norm(acc));
+            *p = A::norm(*p);
+          }
+          // (v)+(vi) S0 -= 1/det C_q B_q on the columns of field g, E0 -= 1/det C_q F_q
+          {
+            const int ncol = nq4 + 1;
+            for (int t = tid; t < nt * ncol; t += NT) {
+              const int r = t / ncol, cc = t - r * ncol;
+              if (g_cg[r] == 0) continue;  // C_q row of field 0 is zero
+              T acc = zero;
+              if (cc == nq4) {
+                for (int i2 = 0; i2 < NP; ++i2) A::msub(acc, sCc[r * NP + i2], sNu[kk * NP + i2]);
+                T* p = &sE[r];
+                A::msub(*p, ic, A::norm(acc));
+                *p = A::norm(*p);
+              } else {
+                const int a = (cc < g_nk[0]) ? 0 : (cc < g_nk[0] + g_nk[1] ? 1 : 2);
+                const int l = cc - (a > 0 ? g_nk[0] : 0) - (a > 1 ? g_nk[1] : 0);
+                const int c = g_toff[a] + gq * g_nk[a] + l;
+                const T* me = tab + to.edge_cross[P][g_pe[a]][a][g_fl[a]];
+                T s2 = zero;
+                for (int i2 = 0; i2 < NP; ++i2) A::madd(s2, sCc[r * NP + i2], me[l * NP + i2]);
+                acc = A::neg(A::mul(A::mul(g_n[a][kd], g_len[a]), A::norm(s2)));   // C_q B_q
+                T* p = &sS[r * lds + c];
+                A::msub(*p, ic, A::norm(acc));
+                *p = A::norm(*p);
+              }
+            }
+          }
         }
+        __syncthreads();
+      }
+      if (pass == 1) break;
+      if (adjoint) {  // the adjoint solves with the transposed Schur matrix A'^T (Sec. 4.2)
+        for (int t = tid; t < NW4 * NW4; t += NT) {
+          const int i = t / NW4, j = t - i * NW4;
+          if (i < j) {
+            const T v = sA[i * LDA + j];
+            sA[i * LDA + j] = sA[j * LDA + i];
+            sA[j * LDA + i] = v;
+          }
+        }
+        __syncthreads();
+      }
+
+      // ---------------- a4/a5: LU with partial pivoting on [A' | R'_w] ----------------
+      lu_solve<T, NW4, NT>(sA, LDA, sR, ldr, nr1, reinterpret_cast<int*>(sZ), s_pinv, &s_bad, tid);  // sZ is dead here
+      // X_w (renormalised in place) and the interior residual
+      {
+        double* xk = s.X + m.x_off[K];
+        for (int t = tid; t < NW4 * nr1; t += NT) {
+          const int c = t / NW4, r = t - c * NW4;
+          const T v = A::norm(sR[r * ldr + c]);
+          sR[r * ldr + c] = v;
+          xk[(size_t)c * N + 8 * NP + r] = A::to_d(v);
+          bad |= A::bad(v);
+        }
+        double* ru = s.res_u + m.u_off[K];
+        for (int t = tid; t < N; t += NT) ru[t] = A::to_d(sNu[t]);
       }
       __syncthreads();
     }
-
-    // ---------------- a4/a5: LU with partial pivoting on [A' | R'_w] ----------------
-    lu_solve<T, NW4, NT>(sA, LDA, sR, ldr, nr1, reinterpret_cast<int*>(sZ), s_pinv, &s_bad, tid);  // sZ is dead here
-    int bad = 0;
-    // X_w (renormalised in place) and the interior residual
-    {
-      double* xk = s.X + m.x_off[K];
-      for (int t = tid; t < NW4 * nr1; t += NT) {
-        const int c = t / NW4, r = t - c * NW4;
-        const T v = A::norm(sR[r * ldr + c]);
-        sR[r * ldr + c] = v;
-        xk[(size_t)c * N + 8 * NP + r] = A::to_d(v);
-        bad |= A::bad(v);
-      }
-      double* ru = s.res_u + m.u_off[K];
-      for (int t = tid; t < N; t += NT) ru[t] = A::to_d(sNu[t]);
+    if (adjoint) {  // the adjoint needs only the local solves
+      if (bad) atomicOr(&s_bad, 2);
+      __syncthreads();
+      if (tid == 0) s.status[K] = (s_bad & 1) ? 1 : ((s_bad & 2) ? 2 : 0);
+      __syncthreads();
+      continue;
     }
-    __syncthreads();
     // X_q = (R_q - A_qw X_w) / det
     {
       double* xk = s.X + m.x_off[K];
@@ -778,21 +844,21 @@ __global__ void __launch_bounds__(kNsThreads) k_condense_ns(DevMesh m, DevSys s,
   }
 }
 
-template <int P, class T>
+template <int P, class T, bool ADJ>
 inline bool launch_ns_bucket(const DevMesh& m, const DevSys& s, const Phys& ph, const T* tab, const TabOff& to,
                              const double* U, const double* Lam, const int* elems, int n, int ntmax, cudaStream_t st,
                              std::string* err) {
   const NsLayout<P> lay(ntmax);
   const size_t bytes = sizeof(T) * (size_t)lay.total;
-  cudaError_t ce = cudaFuncSetAttribute(k_condense_ns<P, T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+  cudaError_t ce = cudaFuncSetAttribute(k_condense_ns<P, T, ADJ>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
   if (ce != cudaSuccess) { *err = std::string("NS kernel shared memory: ") + cudaGetErrorString(ce); return false; }
   int dev = 0, sms = 0, per_sm = 0;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_condense_ns<P, T>, kNsThreads, bytes);
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_condense_ns<P, T, ADJ>, kNsThreads, bytes);
   if (per_sm < 1) { *err = "NS condensation kernel does not fit on an SM"; return false; }
   const long grid = condense_grid(ph, P, sms, per_sm, n);
-  k_condense_ns<P, T><<<(int)grid, kNsThreads, bytes, st>>>(m, s, ph, tab, to, U, Lam, elems, n, ntmax);
+  k_condense_ns<P, T, ADJ><<<(int)grid, kNsThreads, bytes, st>>>(m, s, ph, tab, to, U, Lam, elems, n, ntmax);
   ce = cudaGetLastError();
   if (ce != cudaSuccess) { *err = cudaGetErrorString(ce); return false; }
   return true;
@@ -802,10 +868,10 @@ template <int P, class T>
 inline int ns_occ(int ntmax) {
   const NsLayout<P> lay(ntmax);
   const size_t bytes = sizeof(T) * (size_t)lay.total;
-  if (cudaFuncSetAttribute(k_condense_ns<P, T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes) != cudaSuccess)
+  if (cudaFuncSetAttribute(k_condense_ns<P, T, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes) != cudaSuccess)
     return 0;
   int per_sm = 0;
-  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_condense_ns<P, T>, kNsThreads, bytes);
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_condense_ns<P, T, false>, kNsThreads, bytes);
   return per_sm;
 }
 
@@ -820,15 +886,15 @@ inline int ns_occ_p(int p, int ntmax) {
   return 0;
 }
 
-template <class T>
+template <class T, bool ADJ = false>
 inline bool launch_ns_p(int p, const DevMesh& m, const DevSys& s, const Phys& ph, const T* tab, const TabOff& to,
                         const double* U, const double* Lam, const int* elems, int n, int ntmax, cudaStream_t st,
                         std::string* err) {
   switch (p) {
-    case 1: return launch_ns_bucket<1, T>(m, s, ph, tab, to, U, Lam, elems, n, ntmax, st, err);
-    case 2: return launch_ns_bucket<2, T>(m, s, ph, tab, to, U, Lam, elems, n, ntmax, st, err);
-    case 3: return launch_ns_bucket<3, T>(m, s, ph, tab, to, U, Lam, elems, n, ntmax, st, err);
-    case 4: return launch_ns_bucket<4, T>(m, s, ph, tab, to, U, Lam, elems, n, ntmax, st, err);
+    case 1: return launch_ns_bucket<1, T, ADJ>(m, s, ph, tab, to, U, Lam, elems, n, ntmax, st, err);
+    case 2: return launch_ns_bucket<2, T, ADJ>(m, s, ph, tab, to, U, Lam, elems, n, ntmax, st, err);
+    case 3: return launch_ns_bucket<3, T, ADJ>(m, s, ph, tab, to, U, Lam, elems, n, ntmax, st, err);
+    case 4: return launch_ns_bucket<4, T, ADJ>(m, s, ph, tab, to, U, Lam, elems, n, ntmax, st, err);
   }
   *err = "degree out of range";
   return false;

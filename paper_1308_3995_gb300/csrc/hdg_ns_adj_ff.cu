@@ -1,0 +1,12 @@
+// Navier-Stokes element kernel, adjoint mode: float-float instantiations.
+#include "hdg_ns.cuh"
+
+namespace hdg {
+
+bool launch_ns_adjoint_ff(int p, const DevMesh& m, const DevSys& s, const Phys& ph, const void* tab,
+                          const TabOff& to, const double* U, const double* Lam, const int* elems, int n, int ntmax,
+                          cudaStream_t st, std::string* err) {
+  return launch_ns_p<ff, true>(p, m, s, ph, (const ff*)tab, to, U, Lam, elems, n, ntmax, st, err);
+}
+
+}  // namespace hdg
