@@ -58,6 +58,7 @@ def lib():
                                   _c_double_p, _c_double_p]
         L.orc_legendre01.argtypes = [ctypes.c_int, ctypes.c_int, _c_double_p, _c_double_p]
         L.orc_euler_flux.argtypes = [_c_double_p, ctypes.c_double, _c_double_p]
+        L.orc_mesh_set_source.argtypes = [ctypes.c_void_p, _c_double_p]
         L.orc_euler_flux.restype = None
         L.orc_ns_viscous_flux.argtypes = [_c_double_p, _c_double_p, ctypes.POINTER(OrcParams), _c_double_p]
         L.orc_ns_viscous_flux.restype = None
@@ -348,6 +349,15 @@ class Mesh:
         if st == 2:
             raise ValueError("mesh too large for the dense Jacobian")
         return J
+
+    def set_source(self, S=None):
+        """Source s of Eq. (hdg_ls3) as the coefficients of its L2 projection in U's layout
+        (w part); None: s = 0."""
+        if S is None:
+            lib().orc_mesh_set_source(self._h, None)
+        else:
+            self._src = _f64(S).copy()
+            lib().orc_mesh_set_source(self._h, _d(self._src))
 
     def dense_K(self, Kv):
         """Expand the block-sparse trace matrix into a dense lam_len x lam_len array."""

@@ -318,6 +318,7 @@ struct OMesh {
   std::vector<int64_t> u_off, lam_off, x_off, k_blkoff;
   std::vector<int> k_col;        // [nf][5]
   int64_t u_len = 0, lam_len = 0, x_len = 0, k_len = 0;
+  std::vector<double> src;       // [u_len] source s_h in U's layout (w part), empty: s = 0
 };
 
 struct Geom {
@@ -537,6 +538,9 @@ static void element_residual(const OMesh& M, const orc_params& P, int K, const G
             Nu[(k * 4 + f) * np + i] += wq * (phi[i] * qv[k][f] + gk * w[f]);
           }
   }
+  // source: -(phi_i, s_h)_K = -det J S_i for the orthonormal basis (Eq. hdg_ls3)
+  if (!M.src.empty())
+    for (int r = woff; r < n; ++r) Nu[r] -= g.detJ * M.src[M.u_off[K] + r];
   // face terms
   int loff = 0;
   for (int lf = 0; lf < 3; ++lf) {
@@ -918,6 +922,14 @@ int orc_mesh_create(int n_elem, int nfield, const double* elem_xy, const int32_t
   return 0;
 }
 void orc_mesh_destroy(void* h) { delete (OMesh*)h; }
+
+// Source term s of Eq. (hdg_ls3), given as the coefficients of its L2
+// projection in U's layout [u_len] (only the w part is read); NULL: s = 0.
+void orc_mesh_set_source(void* h, const double* S) {
+  OMesh* M = (OMesh*)h;
+  if (S) M->src.assign(S, S + M->u_len);
+  else M->src.clear();
+}
 
 // sizes: [n_face, u_len, lam_len, x_len, k_len]
 void orc_mesh_sizes(void* h, int64_t* out) {

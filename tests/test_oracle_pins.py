@@ -1080,3 +1080,50 @@ def test_ns_wall_channel_condensed_then_recovered_equals_monolithic():
     dUc = m.recover(r["X"], dLc)
     assert np.abs(dLc - dL).max() < 1e-10 * np.abs(dL).max()
     assert np.abs(dUc - dU).max() < 1e-10 * np.abs(dU).max()
+
+
+# ----------------------------------------------------------------------------- source term
+@pytest.mark.parametrize("model", [0, 1])
+def test_source_term_enters_as_minus_mass_times_coefficients(model):
+    """Eq. (hdg_ls3): the source adds -(phi_i, s_h)_K = -det J S_i to the w rows only (orthonormal
+    basis), nothing to the gradient or trace rows, and leaves the Newton matrix unchanged."""
+    wl, c, m, P = _case("ns_mixp_65k", 3, 4, model=model)
+    U, L, _ = G.case_state(c, m.face_vid, m.face_p)
+    S = np.random.default_rng(8).standard_normal(m.u_len)
+    K = 5
+    n0, l0 = m.element_residual(P, K, U, L)
+    A0 = m.element_blocks(P, K, U, L)[0]
+    m.set_source(S)
+    n1, l1 = m.element_residual(P, K, U, L)
+    A1 = m.element_blocks(P, K, U, L)[0]
+    m.set_source(None)
+    xy = m.elem_xy[K].reshape(3, 2)
+    det = float(np.linalg.det(np.stack([xy[1] - xy[0], xy[2] - xy[0]], 1)))
+    nb = O.n_basis(int(m.elem_p[K]))
+    woff = 8 * nb if model == 1 else 0
+    ref = np.zeros_like(n0)
+    ref[woff:] = -det * S[m.u_off[K] + woff:m.u_off[K + 1]]
+    assert np.abs((n1 - n0) - ref).max() < 1e-13 * max(1.0, np.abs(n0).max())
+    assert np.array_equal(l0, l1) and np.array_equal(A0, A1)
+
+
+def test_manufactured_solution_residual_is_high_order():
+    """With the source of a smooth manufactured field, the residual of its L2 projection (exact
+    traces) drops from O(h^2) -- the element integral of an O(1) flux divergence -- to O(h^(p+2)):
+    the source cancels the divergence with the sign and scale of the discrete steady equations
+    (a wrong sign or a missing det J would leave O(h^2) or O(1))."""
+    import mms
+    res, res0 = [], []
+    for n in (4, 8):
+        wl = G.small_variant(G.WORKLOADS["euler_p3_16k"], n, 2 * n, jitter=0.0, p=2)
+        c = G.make_case(wl)
+        m = O.Mesh(c.mesh.elem_xy, c.mesh.elem_vid, c.elem_p, c.nfield)
+        P = O.Params(mach=0.6, alpha=1.6)
+        U = mms.project(m, mms.conserved)
+        L = mms.project_traces(m, c.mesh.elem_vid)
+        res0.append(np.abs(m.global_residual(P, U, L)[0]).max())
+        m.set_source(mms.project(m, mms.source))
+        res.append(np.abs(m.global_residual(P, U, L)[0]).max())
+        m.set_source(None)
+    assert res0[0] / res0[1] < 2 ** 2.5, res0
+    assert res[0] / res[1] > 2 ** 3.5 and res[1] < 0.05 * res0[1], res
