@@ -418,6 +418,14 @@ hdg_status hdg_trace_matvec(hdg_solver* solver, const double* x, double* y, int3
 hdg_status hdg_adjoint_condense(hdg_sys* adj, const hdg_sys* primal, const double* U, const double* Lam,
                                 const double* Ftilde, void* stream);
 
+/* Source term s of Eq. (hdg_ls3): the residual's w rows get -(phi_i, s_h)_K =
+ * -det J_K S_K,i (orthonormal basis), s_h the L2 projection of s with
+ * coefficients S (DEVICE [u_len], U's layout; only the w part is read, the
+ * caller keeps it alive and unchanged while it is set).  s does not depend on
+ * the state, so the Newton matrix is unchanged.  NULL removes it.  Used for
+ * manufactured solutions.  HDG_EINVAL once a graph has been captured. */
+hdg_status hdg_sys_set_source(hdg_sys* sys, const double* S);
+
 /* Newton update on DEVICE vectors: U += dU [u_len], Lam += dLam [lam_len]. */
 hdg_status hdg_newton_update(hdg_sys* sys, double* U, double* Lam, const double* dU, const double* dLam,
                              void* stream);

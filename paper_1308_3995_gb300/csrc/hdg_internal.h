@@ -108,6 +108,7 @@ struct DevSys {
   double* rhalf1;            // [lam_len]
   int32_t* face_cnt;         // [n_face], zero between calls
   const double* ftilde;      // [u_len] adjoint right-hand side (adjoint mode only)
+  const double* src;         // [u_len] source coefficients in U's layout (w part), or null
 };
 
 // Read-only view of a mesh plan and its context, for translation units other

@@ -426,7 +426,7 @@ __global__ void __launch_bounds__(kCondThreads, 4) k_condense_euler(
       const int a = t / (5 * NP), rem = t - a * 5 * NP, k = rem / NP;
       if (k < g_nk[a]) sMe[t] = A::mul(A::mul(alpha, g_len[a]), tab[to.edge_cross[P][g_pe[a]][a][g_fl[a]] + rem]);
     }
-    // face parts of the residuals
+    // face parts of the residuals, and the source term -(phi_i, s_h)_K = -det J S_i (Eq. hdg_ls3)
     for (int t = tid; t < N; t += NT) {
       const int f = t / NP, i = t - f * NP;
       T acc = sNu[t];
@@ -434,6 +434,7 @@ __global__ void __launch_bounds__(kCondThreads, 4) k_condense_euler(
         const T* phe = tab + to.edge_phi[P][g_pe[a]][a][g_fl[a]];
         for (int q = 0; q < g_pe[a] + 2; ++q) A::madd(acc, phe[q * NP + i], sFhat[(a * kPtSlots + q) * 4 + f]);
       }
+      if (s.src) A::msub(acc, g_det, A::from_d(s.src[m.u_off[K] + t]));
       sNu[t] = A::norm(acc);
     }
     for (int t = tid; t < nt; t += NT) {

@@ -424,6 +424,7 @@ __global__ void __launch_bounds__(kNsThreads, 1) k_condense_ns(DevMesh m, DevSys
           for (int j = 0; j < NP; ++j) A::madd(v, sDk[k * NP * NP + i * NP + j], sU[(k * 4 + f) * NP + j]);
         A::madd(acc, eps, A::norm(v));
       }
+      if (s.src) A::msub(acc, g_det, A::from_d(s.src[m.u_off[K] + 8 * NP + t]));  // -(phi_i, s_h)_K
       sNu[8 * NP + t] = A::norm(acc);
     }
     for (int t = tid; t < nt; t += NT) {

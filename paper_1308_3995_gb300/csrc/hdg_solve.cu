@@ -1003,6 +1003,13 @@ hdg_status hdg_sys_set_cfl(hdg_sys* sys, double cfl) {
   return HDG_OK;
 }
 
+hdg_status hdg_sys_set_source(hdg_sys* sys, const double* S) {
+  if (!sys) return HDG_EINVAL;
+  if (sys->gexec) return fail(sys->ctx, HDG_EINVAL, "hdg_sys_set_source: a captured graph holds the parameters");
+  sys->ds.src = S;
+  return HDG_OK;
+}
+
 double hdg_cfl_law(int32_t n, double c0, double c1, int32_t n0, double cfl_prev, double res_prev, double res_cur) {
   if (n < 0 || n0 < 1) return -1.0;
   if (n <= n0) {

@@ -37,7 +37,7 @@ EXPORTS = ["hdg_create", "hdg_destroy", "hdg_last_error", "hdg_mesh_create", "hd
            "hdg_adapt_indicators", "hdg_adapt_mark",
            "hdg_mesh_create_bc", "hdg_solver_set_preconditioner", "hdg_solver_setup", "hdg_solver_precond_apply",
            "hdg_solver_colors", "hdg_solver_create_ws", "hdg_solver_workspace_bytes", "hdg_solve_step_host",
-           "hdg_sys_bucket_times"]
+           "hdg_sys_bucket_times", "hdg_sys_set_source"]
 
 
 class HdgError(RuntimeError):
@@ -132,6 +132,7 @@ def lib(build: bool = True):
         L.hdg_solver_precond_apply.argtypes = [_vp, _vp, _vp, ctypes.c_int32, _vp]
         L.hdg_solver_colors.argtypes = [_vp, ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(ctypes.c_int32)]
         L.hdg_sys_bucket_times.argtypes = [_vp, ctypes.POINTER(ctypes.c_float)]
+        L.hdg_sys_set_source.argtypes = [_vp, _vp]
         L.hdg_solver_create_ws.argtypes = [_vp, ctypes.c_int32, ctypes.c_int32, _vp, ctypes.c_int64,
                                            ctypes.POINTER(_vp)]
         L.hdg_solver_workspace_bytes.argtypes = [_vp, ctypes.c_int32, ctypes.c_int32]
@@ -430,6 +431,12 @@ class System:
     @property
     def launches(self) -> int:
         return int(lib().hdg_sys_launches(self.h))
+
+    def set_source(self, S=None):
+        """hdg_sys_set_source: source coefficients (device tensor in U's layout, kept alive
+        by this object) or None."""
+        self._src = S
+        _check(lib().hdg_sys_set_source(self.h, _ptr(S) if S is not None else None), self.ctx.h)
 
     def bucket_times(self) -> dict:
         """hdg_sys_bucket_times: {p: ms} of each degree bucket in the last multi-bucket condensation."""
