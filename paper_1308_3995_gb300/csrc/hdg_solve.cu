@@ -18,14 +18,18 @@
 //                 five blocks of the face row in column order; optionally only
 //                 the blocks of earlier or of later colors), then, by mode,
 //                 y_e = t, Dinv_e t, Dinv_e (b_e - t), Dinv_e b_e or b_e - t;
-//   k_multidot    partial dot products of one vector with up to 8 others per
-//                 block row of the grid, reduced in a fixed order by k_reduce
+//   k_dots_slab   dot products of one vector with the Krylov vectors, one
+//                 contiguous slab of rows per block, vectors over its warps;
+//                 k_reduce sums the per-block partials in a fixed order
 //                 (bitwise reproducible);
-//   k_multiaxpy   w -= V c (c on the device), one thread per entry.
+//   k_axpy_v      w -= V c (c on the device), fused with ||w||^2 for the
+//                 second Gram-Schmidt pass (reduced by the last block to
+//                 finish, in a fixed order);
+//   k_multiaxpy   x += V y at the end of a restart cycle.
 // The Arnoldi process uses classical Gram-Schmidt with one
-// re-orthogonalisation pass; the small Hessenberg least-squares problem
-// (Givens rotations) is solved on the host, one residual estimate read back
-// per iteration.
+// re-orthogonalisation pass; the small Hessenberg
+// least-squares problem (Givens rotations) is solved on the host, one residual
+// estimate read back per iteration.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -45,7 +49,7 @@ constexpr int kMaxRestart = 64;
 constexpr int kFaceWarps = 4;          // faces per CTA in the per-face kernels
 constexpr int kMaxM = 4 * (kMaxP + 1);  // largest face block (20)
 constexpr int kDotThreads = 256;
-constexpr int kDotChunk = 8;           // vectors per k_multidot block row
+constexpr int kDotChunk = 8;           // vectors per k_dots block row
 
 struct FaceDev {
   int n_face;
@@ -380,6 +384,148 @@ __global__ void k_scale(double* __restrict__ v, double s, int64_t n) {
     v[i] *= s;
 }
 
+// ---------------------------------------------------------------- Krylov kernels
+// Vectors of the trace space have an even length (4 (p_e + 1) per face) and
+// start 32-byte aligned, so they are read as double2.  The norm fused into
+// the second Gram-Schmidt update is reduced in one launch: warp shuffles, the
+// warps of a block in order, one partial per block, and the last block to
+// finish (a ticket taken after a fence) sums the partials in a fixed order and
+// resets the ticket -- bitwise reproducible.
+
+// out[j] = sum over blocks of part[j][b], j < nout (called by the last block only):
+// every thread takes a strided share of the partials, then a fixed-order tree
+__device__ void finish_reduction(const double* part, int nout, int nblk, double* out, unsigned* ticket) {
+  __shared__ double s_fin[kDotThreads];
+  for (int j = 0; j < nout; ++j) {
+    double v = 0.0;
+    for (int b = threadIdx.x; b < nblk; b += blockDim.x) v += __ldcg(part + (int64_t)j * nblk + b);
+    s_fin[threadIdx.x] = v;
+    __syncthreads();
+    for (int st = blockDim.x / 2; st > 0; st >>= 1) {
+      if (threadIdx.x < st) s_fin[threadIdx.x] += s_fin[threadIdx.x + st];
+      __syncthreads();
+    }
+    if (threadIdx.x == 0) out[j] = s_fin[0];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) *ticket = 0u;
+}
+
+// block-wide sum of acc[0..nj) into part[j0 + j][blockIdx] (blockIdx flattened over x), then
+// the last block finishes every output; returns nothing useful to the caller
+template <int NA>
+__device__ void block_partials(const double (&acc)[NA], int nj, int j0, double* part, int nout, int nblk,
+                               double* out, unsigned* ticket) {
+  __shared__ double s_red[NA][kDotThreads / 32];
+  __shared__ bool s_last;
+  const int lane = threadIdx.x & 31, wp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+#pragma unroll
+  for (int j = 0; j < NA; ++j) {
+    double v = acc[j];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+    if (lane == 0) s_red[j][wp] = v;
+  }
+  __syncthreads();
+  if (threadIdx.x < nj) {
+    double v = 0.0;
+    for (int k = 0; k < nw; ++k) v += s_red[threadIdx.x][k];
+    part[(int64_t)(j0 + threadIdx.x) * gridDim.x + blockIdx.x] = v;
+  }
+  __threadfence();
+  __syncthreads();
+  if (threadIdx.x == 0) s_last = atomicAdd(ticket, 1u) == gridDim.x * gridDim.y - 1;
+  __syncthreads();
+  if (s_last) {
+    __threadfence();
+    finish_reduction(part, nout, nblk, out, ticket);
+  }
+}
+
+// part[j][block] = V_j . w over the block's slab of rows, j < nvec: each block
+// owns a contiguous slab (its slice of w stays in L1 while its warps stream
+// their vectors: warp k takes vectors k, k + 8, ..., four at a time, two
+// double2 rows per lane in flight for each); k_reduce sums the partials.
+__global__ void __launch_bounds__(kDotThreads) k_dots_slab(const double* __restrict__ V, int64_t ldv, int nvec,
+                                                           const double* __restrict__ w, int64_t n,
+                                                           double* __restrict__ part) {
+  constexpr int NW = kDotThreads / 32, VPW = 4;  // warps per block, vectors per warp per sweep
+  const int lane = threadIdx.x & 31, wp = threadIdx.x >> 5;
+  const int64_t n2 = n >> 1;
+  const int64_t per = (n2 + gridDim.x - 1) / gridDim.x;
+  const int64_t b0 = min(n2, (int64_t)blockIdx.x * per), b1 = min(n2, b0 + per);
+  const double2* w2 = reinterpret_cast<const double2*>(w);
+  for (int jb = wp; jb < nvec; jb += NW * VPW) {
+    const double2* v2[VPW];
+    double acc[VPW];
+#pragma unroll
+    for (int k = 0; k < VPW; ++k) {
+      const int j = min(jb + k * NW, nvec - 1);
+      v2[k] = reinterpret_cast<const double2*>(V + (int64_t)j * ldv);
+      acc[k] = 0.0;
+    }
+    for (int64_t i = b0 + lane; i < b1; i += 64) {
+      const bool two = i + 32 < b1;
+      const double2 wa = __ldg(w2 + i);
+      const double2 wb = two ? __ldg(w2 + i + 32) : make_double2(0.0, 0.0);
+#pragma unroll
+      for (int k = 0; k < VPW; ++k) {
+        const double2 a = __ldg(v2[k] + i);
+        const double2 b = two ? __ldg(v2[k] + i + 32) : make_double2(0.0, 0.0);
+        acc[k] = fma(a.x, wa.x, acc[k]);
+        acc[k] = fma(a.y, wa.y, acc[k]);
+        acc[k] = fma(b.x, wb.x, acc[k]);
+        acc[k] = fma(b.y, wb.y, acc[k]);
+      }
+    }
+#pragma unroll
+    for (int k = 0; k < VPW; ++k) {
+      double v = acc[k];
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+      const int j = jb + k * NW;
+      if (lane == 0 && j < nvec) {
+        if (blockIdx.x == 0 && (n & 1)) v = fma(V[(int64_t)j * ldv + n - 1], w[n - 1], v);  // odd tail
+        part[(int64_t)j * gridDim.x + blockIdx.x] = v;
+      }
+    }
+  }
+}
+
+// w -= V c (j < nvec, c on the device); with NORM, out[0] = ||w||^2 of the updated w
+template <bool NORM>
+__global__ void __launch_bounds__(kDotThreads) k_axpy_v(const double* __restrict__ V, int64_t ldv, int nvec,
+                                                        const double* __restrict__ c, double* __restrict__ w,
+                                                        int64_t n, double* __restrict__ part,
+                                                        double* __restrict__ out, unsigned* ticket) {
+  __shared__ double s_c[kMaxRestart + 1];
+  for (int j = threadIdx.x; j < nvec; j += blockDim.x) s_c[j] = c[j];
+  __syncthreads();
+  double acc[1] = {0.0};
+  const int64_t n2 = n >> 1;
+  double2* w2 = reinterpret_cast<double2*>(w);
+  for (int64_t i = blockIdx.x * (int64_t)kDotThreads + threadIdx.x; i < n2; i += (int64_t)gridDim.x * kDotThreads) {
+    double2 a = w2[i];
+    for (int j = 0; j < nvec; ++j) {
+      const double2 v = __ldg(reinterpret_cast<const double2*>(V + (int64_t)j * ldv) + i);
+      a.x = fma(-s_c[j], v.x, a.x);
+      a.y = fma(-s_c[j], v.y, a.y);
+    }
+    w2[i] = a;
+    if (NORM) {
+      acc[0] = fma(a.x, a.x, acc[0]);
+      acc[0] = fma(a.y, a.y, acc[0]);
+    }
+  }
+  if ((n & 1) && blockIdx.x == 0 && threadIdx.x == 0) {
+    double a = w[n - 1];
+    for (int j = 0; j < nvec; ++j) a = fma(-s_c[j], V[(int64_t)j * ldv + n - 1], a);
+    w[n - 1] = a;
+    if (NORM) acc[0] = fma(a, a, acc[0]);
+  }
+  if (NORM) block_partials<1>(acc, 1, 0, part, 1, gridDim.x, out, ticket);
+}
+
 __global__ void k_axpy2(double* __restrict__ U, const double* __restrict__ dU, int64_t nu, double* __restrict__ L,
                         const double* __restrict__ dL, int64_t nl) {
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < nu + nl; i += (int64_t)gridDim.x * blockDim.x) {
@@ -409,7 +555,8 @@ struct hdg_solver {
   FaceDev f{};
   double* V = nullptr;        // [restart + 1][n]
   double* partial = nullptr;  // [restart + 1][dot_blocks]
-  double* h = nullptr;        // [2 (restart + 1) + 2] device results of k_reduce
+  unsigned* ticket = nullptr; // last-block ticket of the fused reductions (zero between launches)
+  double* h = nullptr;        // [2 (restart + 1) + 2] device results of the reductions
   double* coef = nullptr;     // [restart + 1] coefficients from the host
   double* zero = nullptr;     // [n] zeros
   double* tmp = nullptr;      // [n] work vector of the Gauss-Seidel and ILU preconditioners
@@ -530,11 +677,16 @@ hdg_status setup_enqueue(hdg_solver* S, cudaStream_t st) {
   return HDG_OK;
 }
 
-// out[0..nvec) = V_j . w for j < nvec (device), enqueued on st
+// out[0..nvec) = V_j . w for j < nvec (device), one launch, enqueued on st
 void multidot(hdg_solver* S, const double* V, int nvec, const double* w, int64_t n, double* out, cudaStream_t st) {
-  dim3 g(S->dot_blocks, (nvec + kDotChunk - 1) / kDotChunk);
-  k_multidot<<<g, kDotThreads, 0, st>>>(V, S->n, nvec, w, n, S->partial);
+  k_dots_slab<<<S->dot_blocks, kDotThreads, 0, st>>>(V, S->n, nvec, w, n, S->partial);
   k_reduce<<<nvec, kDotThreads, 0, st>>>(S->partial, S->dot_blocks, out);
+}
+// w -= V c (nvec columns); with norm2 != null also norm2[0] = ||w||^2 afterwards
+void axpy_v(hdg_solver* S, const double* V, int nvec, const double* c, double* w, int64_t n, double* norm2,
+            cudaStream_t st) {
+  if (norm2) k_axpy_v<true><<<S->dot_blocks, kDotThreads, 0, st>>>(V, S->n, nvec, c, w, n, S->partial, norm2, S->ticket);
+  else k_axpy_v<false><<<S->dot_blocks, kDotThreads, 0, st>>>(V, S->n, nvec, c, w, n, S->partial, nullptr, S->ticket);
 }
 
 }  // namespace
@@ -545,7 +697,7 @@ namespace {
 struct SolverPlan {
   int64_t n = 0, dinv_len = 0, k_vals = 0;
   int dot_blocks = 0;
-  size_t kc, kb, kt, dof, dinv, bad, V, part, h, coef, zero, tmp, cols, fcol, F, dinv2, tmp2, total;
+  size_t kc, kb, kt, dof, dinv, bad, ticket, V, part, h, coef, zero, tmp, cols, fcol, F, dinv2, tmp2, total;
 };
 
 SolverPlan plan_solver(const hdg_mesh* M, int restart, bool ilu, int sms) {
@@ -560,13 +712,14 @@ SolverPlan plan_solver(const hdg_mesh* M, int restart, bool ilu, int sms) {
   p.n = M->lam_len;
   for (int e = 0; e < M->n_face; ++e) p.dinv_len += (int64_t)(4 * (M->face_p[e] + 1)) * (4 * (M->face_p[e] + 1));
   p.k_vals = M->k_blkoff.empty() ? 0 : M->k_blkoff.back();
-  p.dot_blocks = std::max(1, std::min<int>(2 * std::max(sms, 1), (int)((p.n + kDotThreads - 1) / kDotThreads)));
+  p.dot_blocks = std::max(1, std::min<int>(2 * std::max(sms, 1), (int)((p.n / 2 + kDotThreads - 1) / kDotThreads)));
   p.kc = take(sizeof(int) * 5 * nf);
   p.kb = take(sizeof(int64_t) * M->k_blkoff.size());
   p.kt = take(sizeof(int64_t) * 5 * nf);
   p.dof = take(sizeof(int64_t) * nf);
   p.dinv = take(sizeof(double) * p.dinv_len);
   p.bad = take(sizeof(int));
+  p.ticket = take(sizeof(unsigned));
   p.V = take(sizeof(double) * nr * p.n);
   p.part = take(sizeof(double) * nr * p.dot_blocks);
   p.h = take(sizeof(double) * (2 * nr + 2));
@@ -679,6 +832,7 @@ hdg_status solver_build(hdg_sys* sys, int32_t restart, int32_t precond, void* ws
   if (st == HDG_OK) st = ck(ctx, cudaMemcpy(dof, dinv_off.data(), sizeof(int64_t) * dinv_off.size(), cudaMemcpyHostToDevice), "cudaMemcpy");
   if (st == HDG_OK) st = ck(ctx, cudaMemcpy(kt, tblk.data(), sizeof(int64_t) * tblk.size(), cudaMemcpyHostToDevice), "cudaMemcpy");
   if (st == HDG_OK) st = ck(ctx, cudaMemset(base + P.zero, 0, sizeof(double) * S->n), "cudaMemset");
+  if (st == HDG_OK) st = ck(ctx, cudaMemset(base + P.ticket, 0, sizeof(unsigned)), "cudaMemset");
   if (st == HDG_OK && !by_color.empty())
     st = ck(ctx, cudaMemcpy(cols, by_color.data(), sizeof(int) * by_color.size(), cudaMemcpyHostToDevice), "cudaMemcpy");
   if (st == HDG_OK && !color.empty())
@@ -700,6 +854,7 @@ hdg_status solver_build(hdg_sys* sys, int32_t restart, int32_t precond, void* ws
   S->f.bad = (int*)(base + P.bad);
   S->V = (double*)(base + P.V);
   S->partial = (double*)(base + P.part);
+  S->ticket = (unsigned*)(base + P.ticket);
   S->h = (double*)(base + P.h);
   S->coef = (double*)(base + P.coef);
   S->zero = (double*)(base + P.zero);
@@ -880,12 +1035,14 @@ hdg_status hdg_trace_solve_ex(hdg_solver* S, const double* rhs, int32_t transpos
       double* vj = S->V + (int64_t)j * n;
       double* w = S->V + (int64_t)(j + 1) * n;
       prec_op(S, tr, vj, w, st);
-      // classical Gram-Schmidt, twice
+      // classical Gram-Schmidt, twice (the second pass fused with ||w||^2); a
+      // reorthogonalise-when-needed test (Daniel et al., ||w'||^2 < ||w||^2 / 2)
+      // fires in almost every iteration of these trace systems, so both passes
+      // always run and one read-back per iteration suffices
       multidot(S, S->V, j + 1, w, n, S->h, st);
-      k_multiaxpy<<<vb, 256, 0, st>>>(S->V, n, j + 1, S->h, -1.0, w, n);
+      axpy_v(S, S->V, j + 1, S->h, w, n, nullptr, st);
       multidot(S, S->V, j + 1, w, n, S->h + (R + 1), st);
-      k_multiaxpy<<<vb, 256, 0, st>>>(S->V, n, j + 1, S->h + (R + 1), -1.0, w, n);
-      multidot(S, w, 1, w, n, S->h + 2 * (R + 1), st);
+      axpy_v(S, S->V, j + 1, S->h + (R + 1), w, n, S->h + 2 * (R + 1), st);
       if ((rs = ck(ctx, cudaMemcpyAsync(S->hpin, S->h, sizeof(double) * (2 * (R + 1) + 1), cudaMemcpyDeviceToHost, st),
                    "cudaMemcpyAsync")) != HDG_OK)
         return rs;
