@@ -303,7 +303,7 @@ def solve_section(ctx, wl, dev, flush, stream, cfl=10.0, rtol=1e-10, reps=3):
     x = torch.zeros(m.mesh.lam_len, dtype=torch.float64, device=dev)
     y = torch.empty_like(x)
     out = {"workload": wl.name, "cfl": cfl, "rtol": rtol, "restart": 30}
-    for precond, nm in ((0, "block_jacobi"), (1, "block_sgs"), (2, "block_ilu0")):
+    for precond, nm in ((0, "block_jacobi"), (1, "block_sgs"), (2, "block_ilu0"), (3, "block_ilu0_f32")):
         solver = hdg.Solver(m.sys, restart=30, precond=precond)
         res = []
         for r in range(reps + 1):
@@ -335,7 +335,7 @@ def solve_section(ctx, wl, dev, flush, stream, cfl=10.0, rtol=1e-10, reps=3):
             mv_s = ev0.elapsed_time(ev1) * 1e-3 / nmv
             out["matvec"] = {"k_mb": k_bytes / 1e6, "ms": 1e3 * mv_s, "k_gbs": k_bytes / mv_s / 1e9,
                              "frac_of_hbm": k_bytes / mv_s / 1e9 / HBM_PEAK_GBS}
-        if precond == 2:
+        if precond >= 2:
             # factorization (copy of K + one launch per color) and one application M^{-1} r
             ev0, ev1, ev2 = (torch.cuda.Event(enable_timing=True) for _ in range(3))
             ev0.record(stream)
@@ -419,7 +419,7 @@ def steady_section(ctx, dev, flush, stream, name="euler_box_8k", tol=1e-10, c0=1
     dL = torch.zeros(m.mesh.lam_len, dtype=torch.float64, device=dev)
     out = {"workload": f"{name}: {m.n_elem} triangles, Euler p={wl.p}, far field on all sides, Mach {wl.mach} "
                        f"at {wl.aoa} deg + density bump", "cfl_law": {"c0": c0, "c1": c1, "n0": n0}}
-    for precond, nm in ((0, "block_jacobi"), (2, "block_ilu0")):
+    for precond, nm in ((0, "block_jacobi"), (2, "block_ilu0"), (3, "block_ilu0_f32")):
         solver = hdg.Solver(m.sys, restart=50, precond=precond)
         U, L = m.Ut.clone(), m.Lt.clone()
         torch.cuda.synchronize()

@@ -322,9 +322,9 @@ hdg_status hdg_solver_destroy(hdg_solver* solver);
 /* The same solver with every device buffer in the caller's DEVICE workspace
  * (256-byte aligned, at least hdg_solver_workspace_bytes(mesh, restart,
  * precond) bytes, owned by the caller and untouched after
- * hdg_solver_destroy), preconditioner kind `precond` (0, 1, 2 as for
- * hdg_solver_set_preconditioner; switching to ILU(0) later needs a workspace
- * planned with precond = 2).  Creating and destroying it allocates and frees
+ * hdg_solver_destroy), preconditioner kind `precond` (0..3 as for
+ * hdg_solver_set_preconditioner; switching to an ILU(0) kind later needs a
+ * workspace planned with that kind).  Creating and destroying it allocates and frees
  * no device memory, so neither synchronises the device.  HDG_EINVAL for a
  * short or misaligned workspace. */
 hdg_status hdg_solver_create_ws(hdg_sys* sys, int32_t restart, int32_t precond, void* workspace, int64_t bytes,
@@ -356,10 +356,14 @@ hdg_status hdg_trace_solve(hdg_solver* solver, double* dLam, double rtol, int32_
  * are factored in parallel, L_ek = F_ek U_kk^{-1} for the faces k of earlier
  * colors, F_ej -= L_ek F_kj inside K's block pattern; M = L U is applied by a
  * forward and a backward sweep over the colors (about twice the work of a
- * block-Jacobi application).  Kind 2 allocates a copy of K's values, the pivot
- * inverses and one vector here (HDG_ENOMEM if that fails).  All kinds apply to
- * both K and K^T (M^{-T} from the same factors).  Returns HDG_EINVAL for any
- * other kind. */
+ * block-Jacobi application), or 3 the same block ILU(0) with binary32
+ * factors (a mixed-precision preconditioner: the factorization runs on the
+ * binary32 pipe from a binary32 copy of K, the sweeps stream half the bytes
+ * and form their products in binary64, so M = L U stays one fixed linear
+ * operator and the binary64 GMRES loses no accuracy).  Kinds 2 and 3
+ * allocate a copy of K's values, the pivot inverses and one vector here
+ * (HDG_ENOMEM if that fails).  All kinds apply to both K and K^T (M^{-T} from
+ * the same factors).  Returns HDG_EINVAL for any other kind. */
 hdg_status hdg_solver_set_preconditioner(hdg_solver* solver, int32_t kind);
 
 /* Factor the preconditioner of the solver's kind for the system's current K

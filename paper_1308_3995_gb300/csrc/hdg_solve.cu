@@ -51,7 +51,10 @@ constexpr int kMaxM = 4 * (kMaxP + 1);  // largest face block (20)
 constexpr int kDotThreads = 256;
 constexpr int kDotChunk = 8;           // vectors per k_dots block row
 
-struct FaceDev {
+// MT: value type of the stored matrix and pivot inverses (binary64, or binary32
+// for the mixed-precision ILU(0) factors; products always run in binary64)
+template <class MT>
+struct FaceDevT {
   int n_face;
   const int* face_p;
   const int64_t* lam_off;
@@ -60,46 +63,48 @@ struct FaceDev {
   const int64_t* dinv_off;  // [n_face]
   const int64_t* k_tblk;    // [5 n_face]: offset of block (k_col[5e+b], e), for products with K^T
   const int* fcolor;        // [n_face] color of each face in the multicolor order
-  const double* K;          // the matrix (K, or the incomplete factors of the ILU preconditioner)
-  double* dinv;
+  const MT* K;              // the matrix (K, or the incomplete factors of the ILU preconditioner)
+  MT* dinv;
   int* bad;                 // set to 1 if a diagonal block is singular
 };
+using FaceDev = FaceDevT<double>;
 
 // ---------------------------------------------------------------- block Jacobi
 // Gauss-Jordan inversion with partial pivoting (largest |a_rk|, first on ties)
 // of the m x m block in the left half of a (the identity in the right half);
 // the inverse is left in columns m .. 2m-1.  One warp, m <= 32; false if the
 // block is singular (the result is then warp-uniform).
-__device__ bool warp_gj_invert(double (*a)[2 * kMaxM + 1], int m, int lane) {
+template <class VT>
+__device__ bool warp_gj_invert(VT (*a)[2 * kMaxM + 1], int m, int lane) {
   const int m2 = 2 * m;
   for (int k = 0; k < m; ++k) {
-    double best = (lane >= k && lane < m) ? fabs(a[lane][k]) : -1.0;
+    VT best = (lane >= k && lane < m) ? (VT)fabs(a[lane][k]) : (VT)-1.0;
     int bi = lane;
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {
-      const double ob = __shfl_down_sync(0xffffffffu, best, o);
+      const VT ob = __shfl_down_sync(0xffffffffu, best, o);
       const int oi = __shfl_down_sync(0xffffffffu, bi, o);
       if (ob > best || (ob == best && oi < bi)) { best = ob; bi = oi; }
     }
     best = __shfl_sync(0xffffffffu, best, 0);
     bi = __shfl_sync(0xffffffffu, bi, 0);
-    if (!(best > 0.0)) return false;
+    if (!(best > (VT)0)) return false;
     for (int c = lane; c < m2; c += 32) {
-      const double t = a[k][c];
+      const VT t = a[k][c];
       a[k][c] = a[bi][c];
       a[bi][c] = t;
     }
     __syncwarp();
-    const double pinv = 1.0 / a[k][k];
+    const VT pinv = (VT)1 / a[k][k];
     __syncwarp();
     for (int c = lane; c < m2; c += 32) a[k][c] *= pinv;
     __syncwarp();
-    double fr[kMaxM];
+    VT fr[kMaxM];
 #pragma unroll
-    for (int r = 0; r < kMaxM; ++r) fr[r] = (r < m) ? a[r][k] : 0.0;
+    for (int r = 0; r < kMaxM; ++r) fr[r] = (r < m) ? a[r][k] : (VT)0;
     __syncwarp();
     for (int c = lane; c < m2; c += 32) {
-      const double akc = a[k][c];
+      const VT akc = a[k][c];
 #pragma unroll
       for (int r = 0; r < kMaxM; ++r)
         if (r < m && r != k) a[r][c] = fma(-fr[r], akc, a[r][c]);
@@ -109,16 +114,18 @@ __device__ bool warp_gj_invert(double (*a)[2 * kMaxM + 1], int m, int lane) {
   return true;
 }
 
-__device__ void load_aug(double (*a)[2 * kMaxM + 1], const double* D, int m, int lane) {
+template <class VT>
+__device__ void load_aug(VT (*a)[2 * kMaxM + 1], const VT* D, int m, int lane) {
   const int m2 = 2 * m;
   for (int t = lane; t < m * m2; t += 32) {
     const int r = t / m2, c = t - r * m2;
-    a[r][c] = (c < m) ? D[r * m + c] : (c - m == r ? 1.0 : 0.0);
+    a[r][c] = (c < m) ? D[r * m + c] : (c - m == r ? (VT)1 : (VT)0);
   }
   __syncwarp();
 }
 
-__device__ void store_inverse(double (*a)[2 * kMaxM + 1], double* out, int m, int lane) {
+template <class VT>
+__device__ void store_inverse(VT (*a)[2 * kMaxM + 1], VT* out, int m, int lane) {
   for (int t = lane; t < m * m; t += 32) {
     const int r = t / m, c = t - r * m;
     out[t] = a[r][m + c];
@@ -151,10 +158,11 @@ __global__ void __launch_bounds__(32 * kFaceWarps) k_bj_invert(FaceDev f) {
 // whose j comes after k (fill outside the pattern is dropped).  Last, the
 // inverse of the modified pivot block F_ee goes to dinv.  Same-color faces k
 // update disjoint blocks of row e, so the order among them does not matter.
-__global__ void __launch_bounds__(32 * kFaceWarps) k_ilu_row(FaceDev f, double* F, const int* __restrict__ faces,
+template <class VT>
+__global__ void __launch_bounds__(32 * kFaceWarps) k_ilu_row(FaceDevT<VT> f, VT* F, const int* __restrict__ faces,
                                                              int nfaces) {
-  __shared__ double s_aug[kFaceWarps][kMaxM][2 * kMaxM + 1];
-  __shared__ double s_l[kFaceWarps][kMaxM * kMaxM];
+  __shared__ VT s_aug[kFaceWarps][kMaxM][2 * kMaxM + 1];
+  __shared__ VT s_l[kFaceWarps][kMaxM * kMaxM];
   const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int ei = blockIdx.x * kFaceWarps + w;
   if (ei >= nfaces) return;
@@ -181,19 +189,19 @@ __global__ void __launch_bounds__(32 * kFaceWarps) k_ilu_row(FaceDev f, double* 
       lb[t] = b;
     }
   }
-  double* su = &s_aug[w][0][0];       // U_kk^{-1} (mk x mk)
-  double* sf = su + kMaxM * kMaxM;    // F_ek, then F_kj
-  double* sl = s_l[w];                // L_ek (m x mk)
+  VT* su = &s_aug[w][0][0];           // U_kk^{-1} (mk x mk)
+  VT* sf = su + kMaxM * kMaxM;        // F_ek, then F_kj
+  VT* sl = s_l[w];                    // L_ek (m x mk)
   for (int t = 0; t < nl; ++t) {
     const int k = lk[t], mk = 4 * (f.face_p[k] + 1), ck = f.fcolor[k];
-    double* Fek = F + f.k_blkoff[5 * e + lb[t]];
-    const double* Uk = f.dinv + f.dinv_off[k];
+    VT* Fek = F + f.k_blkoff[5 * e + lb[t]];
+    const VT* Uk = f.dinv + f.dinv_off[k];
     for (int i = lane; i < mk * mk; i += 32) su[i] = Uk[i];
     for (int i = lane; i < m * mk; i += 32) sf[i] = Fek[i];
     __syncwarp();
     for (int i = lane; i < m * mk; i += 32) {
       const int r = i / mk, c = i - r * mk;
-      double s = 0.0;
+      VT s = 0;
       for (int q = 0; q < mk; ++q) s = fma(sf[r * mk + q], su[q * mk + c], s);
       sl[i] = s;
       Fek[i] = s;
@@ -207,26 +215,32 @@ __global__ void __launch_bounds__(32 * kFaceWarps) k_ilu_row(FaceDev f, double* 
       while (tk < 5 && f.k_col[5 * k + tk] != j) ++tk;
       if (tk == 5) continue;             // (k, j) outside the pattern
       const int mj = 4 * (f.face_p[j] + 1);
-      const double* Fkj = F + f.k_blkoff[5 * k + tk];
-      double* Fej = F + f.k_blkoff[5 * e + b];
+      const VT* Fkj = F + f.k_blkoff[5 * k + tk];
+      VT* Fej = F + f.k_blkoff[5 * e + b];
       for (int i = lane; i < mk * mj; i += 32) sf[i] = Fkj[i];
       __syncwarp();
       for (int i = lane; i < m * mj; i += 32) {
         const int r = i / mj, c = i - r * mj;
-        double s = Fej[i];
+        VT s = Fej[i];
         for (int q = 0; q < mk; ++q) s = fma(-sl[r * mk + q], sf[q * mj + c], s);
         Fej[i] = s;
       }
       __syncwarp();
     }
   }
-  double(*a)[2 * kMaxM + 1] = s_aug[w];
-  load_aug(a, F + f.k_blkoff[5 * e + bd], m, lane);
+  VT(*a)[2 * kMaxM + 1] = s_aug[w];
+  load_aug(a, (const VT*)(F + f.k_blkoff[5 * e + bd]), m, lane);
   if (!warp_gj_invert(a, m, lane)) {
     if (lane == 0) *f.bad = 1;
     return;
   }
   store_inverse(a, f.dinv + f.dinv_off[e], m, lane);
+}
+
+// binary64 -> binary32 copy of K's values (the mixed-precision ILU(0) starts from it)
+__global__ void k_to_float(const double* __restrict__ a, float* __restrict__ b, int64_t n) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    b[i] = __double2float_rn(a[i]);
 }
 
 // mode: 0 y = Dinv K x, 1 y = Dinv (b - K x), 2 y = K x, 3 y = Dinv b, 4 y = b - K x.
@@ -245,8 +259,8 @@ __global__ void __launch_bounds__(32 * kFaceWarps) k_ilu_row(FaceDev f, double* 
 // not HBM, bounds a binary64 product of 0.25 flop per byte, so idle lanes
 // would cost time directly.
 // TR: the same with K^T (block (k_col[5e+b], e) transposed) and Dinv^T.
-template <bool TR, bool INPLACE>
-__global__ void __launch_bounds__(32 * kFaceWarps) k_face_op(FaceDev f, const double* x,
+template <bool TR, bool INPLACE, class MT>
+__global__ void __launch_bounds__(32 * kFaceWarps) k_face_op(FaceDevT<MT> f, const double* x,
                                                                const double* __restrict__ bvec, double* y,
                                                                int mode, const int* __restrict__ faces, int nfaces,
                                                                int skip_diag, int tri) {
@@ -265,30 +279,43 @@ __global__ void __launch_bounds__(32 * kFaceWarps) k_face_op(FaceDev f, const do
   double* sb = s_blk[w];
   double t = 0.0;
   if (mode != 3) {
-    for (int b = 0; b < 5; ++b) {
-      const int col = f.k_col[5 * e + b];
-      if (col < 0) break;  // unused slots (next to boundary faces) come last
-      if (skip_diag && col == e) continue;
-      if (tri) {
+    // metadata of the five slots fetched in parallel, lane b for slot b (one round of
+    // dependent loads instead of one per slot): column, its size, block and x offsets
+    int mcol = -1, mmb = 0;
+    long long moff = 0, mxo = 0;
+    if (lane < 5) {
+      const int col = f.k_col[5 * e + lane];
+      bool ok = col >= 0 && !(skip_diag && col == e);  // unused slots (next to boundary faces) are -1
+      if (ok && tri) {
         const int cc = f.fcolor[col];
-        if (tri == 1 ? cc >= ce : cc <= ce) continue;
+        ok = (tri == 1) ? cc < ce : cc > ce;
       }
-      const int mb = 4 * (f.face_p[col] + 1), n = m * mb;
+      if (ok) {
+        mcol = col;
+        mmb = 4 * (f.face_p[col] + 1);
+        moff = TR ? f.k_tblk[5 * e + lane] : f.k_blkoff[5 * e + lane];
+        mxo = f.lam_off[col];
+      }
+    }
+    for (int b = 0; b < 5; ++b) {
+      const int col = __shfl_sync(0xffffffffu, mcol, b);
+      if (col < 0) continue;
+      const int mb = __shfl_sync(0xffffffffu, mmb, b), n = m * mb;
       // stored block: K (e, col) is m x mb; for K^T, block (col, e) is mb x m
-      const double* blk = f.K + (TR ? f.k_tblk[5 * e + b] : f.k_blkoff[5 * e + b]);
+      const MT* blk = f.K + __shfl_sync(0xffffffffu, moff, b);
+      const double* xc = x + __shfl_sync(0xffffffffu, mxo, b);
       const int rl = TR ? m : mb, ld = rl + 1;  // stored row length and padded stride
       // (row, column) of entry lane + 32 k, stepped without division
       const int q = 32 / rl, qr = 32 - q * rl;
       int rr = lane / rl, cc = lane - rr * rl;
       for (int idx = lane; idx < n; idx += 32) {
-        sb[rr * ld + cc] = __ldcs(blk + idx);  // streamed: each value is used once per product
+        sb[rr * ld + cc] = (double)__ldcs(blk + idx);  // streamed: each value is used once per product
         rr += q;
         cc += qr;
         if (cc >= rl) { cc -= rl; ++rr; }
       }
       __syncwarp();
       if (act) {
-        const double* xc = x + f.lam_off[col];
         // in place (a Gauss-Seidel sweep) x is written by this launch: no read-only cache path
         if (TR) {
           for (int c = sg; c < mb; c += nseg) t = fma(sb[c * ld + r], INPLACE ? xc[c] : __ldg(xc + c), t);
@@ -314,8 +341,8 @@ __global__ void __launch_bounds__(32 * kFaceWarps) k_face_op(FaceDev f, const do
   }
   double v = 0.0;
   if (act) {
-    const double* di = f.dinv + f.dinv_off[e];
-    for (int c = sg; c < m; c += nseg) v = fma(TR ? di[c * m + r] : di[r * m + c], s_t[w][c], v);
+    const MT* di = f.dinv + f.dinv_off[e];
+    for (int c = sg; c < m; c += nseg) v = fma((double)(TR ? di[c * m + r] : di[r * m + c]), s_t[w][c], v);
   }
   for (int o = m * (nseg >> 1); o >= m; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
   if (lane < m) y[lo + lane] = v;
@@ -562,13 +589,15 @@ struct hdg_solver {
   double* tmp = nullptr;      // [n] work vector of the Gauss-Seidel and ILU preconditioners
   double* tmp2 = nullptr;     // [n] second work vector of the ILU preconditioner
   double* hpin = nullptr;     // pinned host mirror of h / coef
-  int precond = 0;            // 0 block Jacobi, 1 multicolor block SGS, 2 block ILU(0)
+  int precond = 0;            // 0 block Jacobi, 1 multicolor block SGS, 2 block ILU(0), 3 ILU(0) in binary32
   bool factored = false;      // a setup has been enqueued for the current kind
   int* colors = nullptr;      // faces grouped by color
   std::vector<int> color_off; // [n_colors + 1]
   std::vector<int> fcolor;    // host copy of the face colors
   FaceDev fi{};               // the ILU factors: values F (K's layout) and pivot inverses
   double* F = nullptr;
+  FaceDevT<float> fi32{};     // the same in binary32 (mixed-precision ILU(0), kind 3)
+  float* F32 = nullptr;
   bool external_ws = false;   // device buffers carved from the caller's workspace
   bool hpin_pageable = false; // host mirror from new[] (caller's workspace) or pinned
   int64_t k_vals = 0;         // doubles in K
@@ -583,18 +612,19 @@ hdg_status ck(hdg_ctx* ctx, cudaError_t e, const char* what) {
   return HDG_OK;
 }
 
-void face_op(const FaceDev& fd, bool tr, const double* x, const double* b, double* y, int mode, cudaStream_t st,
+template <class MT>
+void face_op(const FaceDevT<MT>& fd, bool tr, const double* x, const double* b, double* y, int mode, cudaStream_t st,
              const int* faces = nullptr, int nfaces = 0, int skip_diag = 0, int tri = 0) {
   const int nf = faces ? nfaces : fd.n_face;
   if (nf == 0) return;
   const int fb = (nf + kFaceWarps - 1) / kFaceWarps;
   const bool inplace = x == y;
   if (tr) {
-    if (inplace) k_face_op<true, true><<<fb, 32 * kFaceWarps, 0, st>>>(fd, x, b, y, mode, faces, nfaces, skip_diag, tri);
-    else k_face_op<true, false><<<fb, 32 * kFaceWarps, 0, st>>>(fd, x, b, y, mode, faces, nfaces, skip_diag, tri);
+    if (inplace) k_face_op<true, true, MT><<<fb, 32 * kFaceWarps, 0, st>>>(fd, x, b, y, mode, faces, nfaces, skip_diag, tri);
+    else k_face_op<true, false, MT><<<fb, 32 * kFaceWarps, 0, st>>>(fd, x, b, y, mode, faces, nfaces, skip_diag, tri);
   } else {
-    if (inplace) k_face_op<false, true><<<fb, 32 * kFaceWarps, 0, st>>>(fd, x, b, y, mode, faces, nfaces, skip_diag, tri);
-    else k_face_op<false, false><<<fb, 32 * kFaceWarps, 0, st>>>(fd, x, b, y, mode, faces, nfaces, skip_diag, tri);
+    if (inplace) k_face_op<false, true, MT><<<fb, 32 * kFaceWarps, 0, st>>>(fd, x, b, y, mode, faces, nfaces, skip_diag, tri);
+    else k_face_op<false, false, MT><<<fb, 32 * kFaceWarps, 0, st>>>(fd, x, b, y, mode, faces, nfaces, skip_diag, tri);
   }
 }
 
@@ -617,16 +647,21 @@ void sgs_apply(hdg_solver* S, bool tr, const double* r, double* z, cudaStream_t 
 // earlier colors; transposed, U^T y = r), then a backward one into z
 // (U z = y: z_e = U_ee^{-1} (y_e - sum of U_ej z_j over later colors;
 // transposed, L^T z = y).  r and z must not be tmp2.
-void ilu_apply(hdg_solver* S, bool tr, const double* r, double* z, cudaStream_t st) {
+template <class MT>
+void ilu_sweeps(hdg_solver* S, const FaceDevT<MT>& fi, bool tr, const double* r, double* z, cudaStream_t st) {
   const int nc = (int)S->color_off.size() - 1;
   for (int c = 0; c < nc; ++c) {
     const int o0 = S->color_off[c], o1 = S->color_off[c + 1];
-    face_op(S->fi, tr, S->tmp2, r, S->tmp2, tr ? 1 : 4, st, S->colors + o0, o1 - o0, 0, 1);
+    face_op(fi, tr, S->tmp2, r, S->tmp2, tr ? 1 : 4, st, S->colors + o0, o1 - o0, 0, 1);
   }
   for (int c = nc - 1; c >= 0; --c) {
     const int o0 = S->color_off[c], o1 = S->color_off[c + 1];
-    face_op(S->fi, tr, z, S->tmp2, z, tr ? 4 : 1, st, S->colors + o0, o1 - o0, 0, 2);
+    face_op(fi, tr, z, S->tmp2, z, tr ? 4 : 1, st, S->colors + o0, o1 - o0, 0, 2);
   }
+}
+void ilu_apply(hdg_solver* S, bool tr, const double* r, double* z, cudaStream_t st) {
+  if (S->precond == 3) ilu_sweeps(S, S->fi32, tr, r, z, st);  // binary32 factors, binary64 products
+  else ilu_sweeps(S, S->fi, tr, r, z, st);
 }
 
 // w = M^{-1} b for the solver's preconditioner
@@ -654,20 +689,43 @@ void prec_res(hdg_solver* S, bool tr, const double* x, const double* b, double* 
   }
 }
 
+// the binary32 factor view: K's layout and tables, values and pivot inverses in binary32
+void set_fi32(hdg_solver* S, float* dinv32) {
+  const FaceDev& f = S->f;
+  S->fi32.n_face = f.n_face;
+  S->fi32.face_p = f.face_p;
+  S->fi32.lam_off = f.lam_off;
+  S->fi32.k_col = f.k_col;
+  S->fi32.k_blkoff = f.k_blkoff;
+  S->fi32.dinv_off = f.dinv_off;
+  S->fi32.k_tblk = f.k_tblk;
+  S->fi32.fcolor = f.fcolor;
+  S->fi32.K = S->F32;
+  S->fi32.dinv = dinv32;
+  S->fi32.bad = f.bad;
+}
+
 // enqueue the factorization of the preconditioner for the current K; a
 // singular pivot block sets f.bad (cleared first)
 hdg_status setup_enqueue(hdg_solver* S, cudaStream_t st) {
   hdg_ctx* ctx = S->sys->ctx;
   hdg_status rs;
   if ((rs = ck(ctx, cudaMemsetAsync(S->f.bad, 0, sizeof(int), st), "cudaMemsetAsync")) != HDG_OK) return rs;
-  if (S->precond == 2) {
-    if ((rs = ck(ctx, cudaMemcpyAsync(S->F, S->f.K, sizeof(double) * S->k_vals, cudaMemcpyDeviceToDevice, st),
-                 "cudaMemcpyAsync")) != HDG_OK)
+  if (S->precond == 2 || S->precond == 3) {
+    const bool f32 = S->precond == 3;
+    if (f32) {
+      k_to_float<<<grid_for(S->k_vals, 256, 8 * S->sms), 256, 0, st>>>(S->f.K, S->F32, S->k_vals);
+    } else if ((rs = ck(ctx, cudaMemcpyAsync(S->F, S->f.K, sizeof(double) * S->k_vals, cudaMemcpyDeviceToDevice, st),
+                        "cudaMemcpyAsync")) != HDG_OK) {
       return rs;
+    }
     const int nc = (int)S->color_off.size() - 1;
     for (int c = 0; c < nc; ++c) {
       const int o0 = S->color_off[c], n = S->color_off[c + 1] - o0;
-      if (n > 0) k_ilu_row<<<(n + kFaceWarps - 1) / kFaceWarps, 32 * kFaceWarps, 0, st>>>(S->fi, S->F, S->colors + o0, n);
+      if (n == 0) continue;
+      const int nb = (n + kFaceWarps - 1) / kFaceWarps;
+      if (f32) k_ilu_row<float><<<nb, 32 * kFaceWarps, 0, st>>>(S->fi32, S->F32, S->colors + o0, n);
+      else k_ilu_row<double><<<nb, 32 * kFaceWarps, 0, st>>>(S->fi, S->F, S->colors + o0, n);
     }
   } else {
     k_bj_invert<<<(S->f.n_face + kFaceWarps - 1) / kFaceWarps, 32 * kFaceWarps, 0, st>>>(S->f);
@@ -700,7 +758,7 @@ struct SolverPlan {
   size_t kc, kb, kt, dof, dinv, bad, ticket, V, part, h, coef, zero, tmp, cols, fcol, F, dinv2, tmp2, total;
 };
 
-SolverPlan plan_solver(const hdg_mesh* M, int restart, bool ilu, int sms) {
+SolverPlan plan_solver(const hdg_mesh* M, int restart, int precond, int sms) {
   SolverPlan p{};
   size_t o = 0;
   auto take = [&o](size_t bytes) {
@@ -729,9 +787,10 @@ SolverPlan plan_solver(const hdg_mesh* M, int restart, bool ilu, int sms) {
   p.cols = take(sizeof(int) * nf);
   p.fcol = take(sizeof(int) * nf);
   p.F = p.dinv2 = p.tmp2 = 0;
-  if (ilu) {
-    p.F = take(sizeof(double) * p.k_vals);
-    p.dinv2 = take(sizeof(double) * p.dinv_len);
+  if (precond == 2 || precond == 3) {  // the incomplete factors, in binary64 or binary32
+    const size_t vs = precond == 2 ? sizeof(double) : sizeof(float);
+    p.F = take(vs * p.k_vals);
+    p.dinv2 = take(vs * p.dinv_len);
     p.tmp2 = take(sizeof(double) * p.n);
   }
   p.total = o;
@@ -751,12 +810,12 @@ hdg_status solver_build(hdg_sys* sys, int32_t restart, int32_t precond, void* ws
   *out = nullptr;
   hdg_ctx* ctx = sys->ctx;
   if (restart < 1 || restart > kMaxRestart) return fail(ctx, HDG_EINVAL, "hdg_solver_create: restart must be in 1..64");
-  if (precond < 0 || precond > 2) return fail(ctx, HDG_EINVAL, "hdg_solver_create: preconditioner kind must be 0, 1 or 2");
+  if (precond < 0 || precond > 3) return fail(ctx, HDG_EINVAL, "hdg_solver_create: preconditioner kind must be 0..3");
   const hdg_mesh* M = sys->mesh;
   if (cudaSetDevice(ctx->device) != cudaSuccess) return fail(ctx, HDG_ECUDA, "cudaSetDevice failed");
   int sms = 0;
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, ctx->device);
-  const SolverPlan P = plan_solver(M, restart, precond == 2, sms);
+  const SolverPlan P = plan_solver(M, restart, precond, sms);
   if (ws && ((uintptr_t)ws % 256 != 0 || ws_bytes < (int64_t)P.total))
     return fail(ctx, HDG_EINVAL,
                 "hdg_solver_create_ws: workspace smaller than hdg_solver_workspace_bytes or not 256-byte aligned");
@@ -869,6 +928,10 @@ hdg_status solver_build(hdg_sys* sys, int32_t restart, int32_t precond, void* ws
     S->fi = S->f;
     S->fi.K = S->F;
     S->fi.dinv = (double*)(base + P.dinv2);
+  } else if (precond == 3) {
+    S->F32 = (float*)(base + P.F);
+    S->tmp2 = (double*)(base + P.tmp2);
+    set_fi32(S, (float*)(base + P.dinv2));
   }
   S->precond = precond;
   *out = S;
@@ -890,10 +953,10 @@ hdg_status hdg_solver_create_ws(hdg_sys* sys, int32_t restart, int32_t precond, 
 }
 
 int64_t hdg_solver_workspace_bytes(const hdg_mesh* mesh, int32_t restart, int32_t precond) {
-  if (!mesh || restart < 1 || restart > kMaxRestart || precond < 0 || precond > 2) return -1;
+  if (!mesh || restart < 1 || restart > kMaxRestart || precond < 0 || precond > 3) return -1;
   int sms = 0;
   if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, mesh->ctx->device) != cudaSuccess) return -1;
-  return (int64_t)plan_solver(mesh, restart, precond == 2, sms).total;
+  return (int64_t)plan_solver(mesh, restart, precond, sms).total;
 }
 
 hdg_status hdg_solver_destroy(hdg_solver* S) {
@@ -909,29 +972,38 @@ hdg_status hdg_solver_destroy(hdg_solver* S) {
 }
 
 hdg_status hdg_solver_set_preconditioner(hdg_solver* S, int32_t kind) {
-  if (!S || kind < 0 || kind > 2) return HDG_EINVAL;
-  if (kind == 2 && !S->F) {  // the incomplete factors: a copy of K's values, pivot inverses, a work vector
+  if (!S || kind < 0 || kind > 3) return HDG_EINVAL;
+  const bool need64 = kind == 2 && !S->F, need32 = kind == 3 && !S->F32;
+  if (need64 || need32) {  // the incomplete factors: a copy of K's values, pivot inverses, a work vector
     hdg_ctx* ctx = S->sys->ctx;
     if (S->external_ws)
-      return fail(ctx, HDG_ENOMEM, "hdg_solver_set_preconditioner: the caller's workspace was planned without ILU(0)");
+      return fail(ctx, HDG_ENOMEM, "hdg_solver_set_preconditioner: the caller's workspace was planned without these factors");
     if (cudaSetDevice(ctx->device) != cudaSuccess) return fail(ctx, HDG_ECUDA, "cudaSetDevice failed");
+    const size_t vs = need64 ? sizeof(double) : sizeof(float);
     void *F = nullptr, *di = nullptr, *t2 = nullptr;
-    if (cudaMalloc(&F, sizeof(double) * std::max<int64_t>(S->k_vals, 2)) != cudaSuccess) F = nullptr;
-    if (F && cudaMalloc(&di, sizeof(double) * std::max<int64_t>(S->dinv_len, 2)) != cudaSuccess) di = nullptr;
-    if (di && cudaMalloc(&t2, sizeof(double) * std::max<int64_t>(S->n, 2)) != cudaSuccess) t2 = nullptr;
-    if (!t2) {
+    if (cudaMalloc(&F, vs * std::max<int64_t>(S->k_vals, 2)) != cudaSuccess) F = nullptr;
+    if (F && cudaMalloc(&di, vs * std::max<int64_t>(S->dinv_len, 2)) != cudaSuccess) di = nullptr;
+    if (di && !S->tmp2 && cudaMalloc(&t2, sizeof(double) * std::max<int64_t>(S->n, 2)) != cudaSuccess) t2 = nullptr;
+    if (!di || (!S->tmp2 && !t2)) {
       if (F) cudaFree(F);
       if (di) cudaFree(di);
       return fail(ctx, HDG_ENOMEM, "hdg_solver_set_preconditioner: device allocation of the ILU factors failed");
     }
     S->allocs.push_back(F);
     S->allocs.push_back(di);
-    S->allocs.push_back(t2);
-    S->F = (double*)F;
-    S->tmp2 = (double*)t2;
-    S->fi = S->f;
-    S->fi.K = S->F;
-    S->fi.dinv = (double*)di;
+    if (t2) {
+      S->allocs.push_back(t2);
+      S->tmp2 = (double*)t2;
+    }
+    if (need64) {
+      S->F = (double*)F;
+      S->fi = S->f;
+      S->fi.K = S->F;
+      S->fi.dinv = (double*)di;
+    } else {
+      S->F32 = (float*)F;
+      set_fi32(S, (float*)di);
+    }
   }
   if (kind != S->precond) S->factored = false;
   S->precond = kind;

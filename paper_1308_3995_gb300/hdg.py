@@ -194,11 +194,11 @@ def adapt_mark(ctx: "Context", eta2, sensor, code, theta=0.05, eps_s=1e-6, strea
 class Solver:
     """hdg_solver_create / hdg_trace_solve / hdg_trace_matvec: GMRES on the trace system of a System."""
 
-    BLOCK_JACOBI, BLOCK_SGS, BLOCK_ILU0 = 0, 1, 2
+    BLOCK_JACOBI, BLOCK_SGS, BLOCK_ILU0, BLOCK_ILU0_F32 = 0, 1, 2, 3
 
     def __init__(self, system: "System", restart: int = 30, precond: int = 0, workspace=None):
         """precond: 0 block Jacobi, 1 multicolor block symmetric Gauss-Seidel, 2 block ILU(0)
-        in the multicolor order.  workspace: optional (device pointer, bytes) holding every
+        in the multicolor order, 3 the same with binary32 factors.  workspace: optional (device pointer, bytes) holding every
         device buffer (hdg_solver_create_ws; size from ``workspace_bytes``)."""
         h = _vp()
         if workspace is None:

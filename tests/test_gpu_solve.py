@@ -30,10 +30,10 @@ def setup(ctx, wl, cfl, precision=0):
     return case, om, U, Lam, mesh, sysm, Ut, Lt
 
 
-PRECOND_NAMES = ["block Jacobi", "block SGS", "block ILU(0)"]
+PRECOND_NAMES = ["block Jacobi", "block SGS", "block ILU(0)", "block ILU(0) binary32"]
 
 
-@pytest.mark.parametrize("precond", [0, 1, 2])
+@pytest.mark.parametrize("precond", [0, 1, 2, 3])
 @pytest.mark.parametrize("name,nx,ny,kw", [("euler_p3_16k", 5, 6, {}), ("ns_mixp_65k", 4, 5, {}),
                                            ("ns_mixp_65k", 5, 5, {"model": 0})])
 def test_trace_solve_matches_dense_oracle_solve(ctx, name, nx, ny, kw, precond):
@@ -61,7 +61,7 @@ def test_trace_solve_matches_dense_oracle_solve(ctx, name, nx, ny, kw, precond):
     solver.close(); sysm.close(); mesh.close()
 
 
-@pytest.mark.parametrize("precond", [0, 2])
+@pytest.mark.parametrize("precond", [0, 2, 3])
 def test_trace_solve_full_size_true_residual(ctx, precond):
     """16,384-element p = 3 workload at CFL 10: the true residual ||E - K dLambda|| (matrix-vector
     product checked row by row against the host copy of K) is small after the solve."""
@@ -164,7 +164,7 @@ def test_trace_solve_reports_timeout_and_singular_blocks(ctx):
                                                      ("ns_mixp_65k", 3, 3, {}, 1),
                                                      ("ns_wall_channel_8k", 3, 3, {}, 0),
                                                      ("ns_mixp_65k", 3, 3, {"p": 4, "probs": None}, 0)])
-@pytest.mark.parametrize("precond", [0, 1, 2])
+@pytest.mark.parametrize("precond", [0, 1, 2, 3])
 def test_hybridized_adjoint_matches_transposed_monolithic_solve(ctx, name, nx, ny, kw, precision, precond):
     """Sec. 4.2: the adjoint of the Newton matrix (pseudo-time mass included, CFL 10) with right-hand
     side [F~; 0]: GPU adjoint local solves, E~ = -X_B^T F~, GMRES on K^T, reconstruction -- against
@@ -229,6 +229,8 @@ def test_block_ilu0_preconditioner_matches_oracle(ctx, name, nx, ny, kw, cfl):
     sysm.condense(Ut, Lt)
     solver = hdg.Solver(sysm, restart=10, precond=2)
     solver.setup()
+    solver32 = hdg.Solver(sysm, restart=10, precond=3)
+    solver32.setup()
     color, nc = solver.colors()
     P = O.trace_pattern(om)
     assert nc <= 8 and all(color[i] != color[j] for (i, j) in P if i != j)
@@ -244,6 +246,10 @@ def test_block_ilu0_preconditioner_matches_oracle(ctx, name, nx, ny, kw, cfl):
         torch.cuda.synchronize()
         ref = O.block_ilu0_apply(L, Uf, perm, r, transpose=transpose)
         err = np.abs(z.cpu().numpy() - ref).max() / np.abs(ref).max()
-        print(wl.name, "colors", nc, "transpose" if transpose else "", f"{err:.1e}")
-        assert err < 1e-11
-    solver.close(); sysm.close(); mesh.close()
+        # binary32 factors: the same incomplete factorization to binary32 rounding
+        solver32.precond_apply(torch.from_numpy(r).to("cuda:0"), z, transpose=transpose)
+        torch.cuda.synchronize()
+        err32 = np.abs(z.cpu().numpy() - ref).max() / np.abs(ref).max()
+        print(wl.name, "colors", nc, "transpose" if transpose else "", f"{err:.1e}", f"binary32 factors {err32:.1e}")
+        assert err < 1e-11 and err32 < 1e-4
+    solver32.close(); solver.close(); sysm.close(); mesh.close()
