@@ -36,7 +36,7 @@ L2_FLUSH_BYTES = 256 << 20  # > 129 MB L2
 HBM_PEAK_GBS = 6674.8       # measured copy bandwidth of the GB300s (MEASURED_PEAKS.json)
 # dram__bytes_read.sum + dram__bytes_write.sum per condensation launch from ncu
 # (profiles/), scaled to the full workload by elements; only for unchanged kernels
-TRAFFIC_PER_LAUNCH = {("euler_p3_16k", 0): 11974656 + 522418176}
+TRAFFIC_PER_LAUNCH = {("euler_p3_16k", 0): 12611072 + 522575360}
 
 
 def dense_condensation_flops(n: int, nt: int) -> float:
