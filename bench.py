@@ -167,6 +167,54 @@ def time_oracle_sample(wl, target_s: float = 12.0, max_elems: int | None = None)
     return om, P, U, Lam, dLam, n
 
 
+def oracle_accuracy(m, sample: int = 0, per_field: bool = False) -> dict:
+    """Part of the CPU-baseline leg: the GPU results of a measured step (its last
+    condensation and reconstruction) against the oracle on the same inputs.
+    Whole mesh (sample = 0): max over elements of the relative error of the local
+    solves X_B, max over blocks of the assembled trace matrix K, and the global
+    relative errors of E and of the reconstruction dU.  sample > 0: X_B on
+    elements [0, sample) only (also per field with per_field)."""
+    import numpy as np
+
+    import oracle as O
+    c, wl = m.case, m.wl
+    om = O.Mesh(c.mesh.elem_xy, c.mesh.elem_vid, c.elem_p, c.nfield, c.mesh.elem_bc)
+    P = O.Params(model=wl.model, mach=wl.mach, alpha=wl.alpha, reynolds=wl.reynolds, prandtl=wl.prandtl,
+                 sc_eps0=m.prm.sc_eps0, aoa=wl.aoa)
+    r = om.condense(P, m.U, m.Lam, 0, sample, threads=host_threads())
+    v = {k: t.cpu().numpy() for k, t in m.sys.views().items()}
+    n_el = sample or om.n_elem
+    xo, uo = np.asarray(om.x_off), np.asarray(om.u_off)
+    nf = 12 if c.nfield == 12 else 4
+    worst, fworst = 0.0, np.zeros(nf)
+    for K in range(n_el):
+        n = int(uo[K + 1] - uo[K])
+        nc = int(xo[K + 1] - xo[K]) // n
+        g = v["X"][xo[K]:xo[K + 1]].reshape(nc, n)[:nc - 1]      # columns of X_B (library: column-major)
+        o = r["X"][xo[K]:xo[K + 1]].reshape(n, nc).T[:nc - 1]    # (oracle: row-major n x (nt + 1))
+        worst = max(worst, float(np.linalg.norm(g - o) / np.linalg.norm(o)))
+        if per_field:
+            nb = n // nf
+            for f in range(nf):
+                gf, of = g[:, f * nb:(f + 1) * nb], o[:, f * nb:(f + 1) * nb]
+                fworst[f] = max(fworst[f], float(np.linalg.norm(gf - of) / max(np.linalg.norm(of), 1e-300)))
+    out = {"elements_checked": n_el, "X_B_max_rel": worst}
+    if per_field:
+        names = (["q_x " + t for t in ("rho", "rho u", "rho v", "E")] + ["q_y " + t for t in ("rho", "rho u", "rho v", "E")]
+                 if nf == 12 else [])
+        names += ["rho", "rho u", "rho v", "E"]
+        out["X_B_max_rel_per_field"] = dict(zip(names, (float(x) for x in fworst)))
+    if not sample:
+        kb = np.asarray(om.k_blkoff)
+        d2 = np.add.reduceat((v["K"] - r["K"]) ** 2, kb[:-1][np.diff(kb) > 0])
+        k2 = np.add.reduceat(r["K"] ** 2, kb[:-1][np.diff(kb) > 0])
+        out["K_block_max_rel"] = float(np.sqrt((d2 / k2).max()))
+        out["E_rel"] = float(np.linalg.norm(v["E"] - r["E"]) / np.linalg.norm(r["E"]))
+        du = om.recover(r["X"], m.dLam)
+        out["dU_rel"] = float(np.linalg.norm(m.dUt.cpu().numpy() - du) / np.linalg.norm(du))
+    return out
+
+
 def run_reference(args, wl, rank):
     if rank != 0:
         return 0
@@ -565,6 +613,10 @@ def run_ours(args, wl, ws, rank, local):
              "launch_shapes": summ["launch_shapes"]}
     extra.update({k: summ[k] for k in ("p50_step_ms", "p10_step_ms", "p90_step_ms", "p99_step_ms", "condense_ms",
                                        "recover_ms", "elem_status_nonzero")})
+    check = rank == 0 and ws == 1 and not args.no_cpu_baseline   # the CPU-baseline leg checks every result
+    acc = {}
+    if check:
+        acc[f"{wl.name}_{'fp64' if args.precision == 0 else 'float2'}"] = oracle_accuracy(main_m)
     line = {"metric": METRIC, "value": value, "unit": "elements/s", "n_gpus": ws, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64" if args.precision == 0 else "f32x2",
@@ -579,6 +631,8 @@ def run_ours(args, wl, ws, rank, local):
         # the same workload in float-float arithmetic (mixed-precision path, parity <= 1e-12 vs the oracle)
         mm = Measured(ctx, wl, hdg.HDG_FLOAT2, dev, flush).run(max(5, args.steps // 2), 3, stream)
         line["mixed_float2"] = {**mm.summary(), "dtype": "f32x2 (binary32 pairs, ~48-bit significand)"}
+        if check:
+            acc[f"{wl.name}_float2"] = oracle_accuracy(mm)
         mm.close()
         # condensed elements/s per p at equal element counts (Euler, 16,384 triangles)
         per_p = {}
@@ -588,6 +642,8 @@ def run_ours(args, wl, ws, rank, local):
             for prec, nm in ((hdg.HDG_FP64, "fp64"), (hdg.HDG_FLOAT2, "float2")):
                 mp = Measured(ctx, wp, prec, dev, flush).run(5, 2, stream)
                 row[nm] = mp.summary()["elements_per_s"]
+                if check:
+                    acc[f"{wp.name}_{nm}"] = oracle_accuracy(mp)
                 mp.close()
             per_p[str(p)] = row
         line["elements_per_s_per_p"] = per_p
@@ -596,6 +652,8 @@ def run_ours(args, wl, ws, rank, local):
         for prec, nm in ((hdg.HDG_FP64, "fp64"), (hdg.HDG_FLOAT2, "float2")):
             mn = Measured(ctx, G.WORKLOADS["ns_mixp_65k"], prec, dev, flush).run(3, 1, stream)
             ns[nm] = mn.summary()
+            if check:
+                acc[f"ns_mixp_65k_{nm}"] = oracle_accuracy(mn, sample=2048, per_field=True)
             mn.close()
         line["ns_mixp_65k"] = ns
         # 262,144-triangle Euler p = 3, Mach 1.5 shock band, shock capturing off / on (eps_0 = 0.2)
@@ -604,6 +662,9 @@ def run_ours(args, wl, ws, rank, local):
             for prec, nm in ((hdg.HDG_FP64, "fp64"), (hdg.HDG_FLOAT2, "float2")):
                 ms = Measured(ctx, G.WORKLOADS["euler_p3_262k_shock"], prec, dev, flush, sc).run(3, 1, stream)
                 shock[f"{nm}_sc{'_on' if sc else '_off'}"] = ms.summary()
+                if check:
+                    acc[f"euler_p3_262k_shock_{nm}_sc{'_on' if sc else '_off'}"] = oracle_accuracy(ms, sample=4096,
+                                                                                                   per_field=True)
                 ms.close()
         line["euler_p3_262k_shock"] = shock
         line["newton_step_with_trace_solve"] = solve_section(ctx, wl, dev, flush, stream)
@@ -627,7 +688,12 @@ def run_ours(args, wl, ws, rank, local):
         line["cpu_baseline"] = {"value": n / dt, "unit": "elements/s", "cores": nth, "kind": "oracle",
                                 "sample": f"elements 0..{n - 1} of {om.n_elem} (condensation + assembly), "
                                           f"{nth} host threads, {dt:.1f} s",
-                                "single_thread_value": n1 / dt1}
+                                "single_thread_value": n1 / dt1,
+                                "accuracy_of_gpu_results": {
+                                    "bar": "1e-12 relative (binary64), 1e-10 (float-float) on X_B per element and "
+                                           "K per block; E = H - C X_F and dU are residual-type (they cancel), "
+                                           "reported as global relative errors",
+                                    **acc}}
     if rank == 0:
         print(json.dumps(line), flush=True)
     if ws > 1:
