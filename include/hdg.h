@@ -83,7 +83,7 @@ typedef enum {
   HDG_ECUDA = 3,      /* a CUDA runtime call failed */
   HDG_ESINGULAR = 4,  /* some element's local block had a zero pivot (see elem_status) */
   HDG_ETIMEOUT = 5,   /* a bounded device wait ran out */
-  HDG_ENOTSUP = 6     /* combination not supported by this build */
+  HDG_ENOTSUP = 6     /* combination not supported by this library */
 } hdg_status;
 
 typedef enum { HDG_EULER = 0, HDG_NS_MIXED = 1 } hdg_model;

@@ -27,7 +27,7 @@
 //     (dQ, dW) from dLambda by Eq. (ls);
 //   * for tiny meshes, the monolithic linearised system solved densely.
 //
-// Readings of points the paper leaves open are listed in the design doc and fixed
+// Readings of points the paper leaves open are fixed
 // here: orthonormal Dubiner basis in the order (k=0..p, j=0..k, i=k-j);
 // collapsed Gauss volume rule with (p+2)x(p+2) points; (p_e+2)-point
 // Gauss-Legendre edge rule; orthonormal Legendre trace basis with the edge

@@ -361,7 +361,7 @@ hdg_status sys_validate(hdg_ctx* ctx, const hdg_mesh* M, const hdg_params* P, co
   if ((P->model == HDG_EULER) != (M->nfield == 4) || (P->model != HDG_EULER && P->model != HDG_NS_MIXED))
     return fail(ctx, HDG_EINVAL, w + ": model does not match the mesh's field count");
   if (P->precision != HDG_FP64 && P->precision != HDG_FLOAT2)
-    return fail(ctx, HDG_ENOTSUP, w + ": precision not supported by this build");
+    return fail(ctx, HDG_ENOTSUP, w + ": precision not supported by this library");
   if (P->model == HDG_NS_MIXED && !(P->reynolds > 0.0 && P->prandtl > 0.0 && P->t_inf > 0.0))
     return fail(ctx, HDG_EINVAL, w + ": Navier-Stokes needs reynolds, prandtl, t_inf > 0");
   if (!(P->gamma > 1.0) || !(P->alpha > 0.0) || !(P->mach > 0.0))
