@@ -74,8 +74,14 @@ struct NsLayout {
   }
 };
 
+// Two CTAs per SM for p <= 2 (registers capped at 128, a few hundred bytes of
+// spills in the pointwise Jacobians): at one CTA of 8 warps per SM those
+// buckets stall on block barriers with the binary64 pipe 40-55 % busy; the
+// second CTA hides them (Navier-Stokes p mix: 101.7 -> 86.0 ms per step in
+// binary64, 76.3 -> 70.5 ms in float-float).  For p >= 3 shared memory allows
+// one CTA per SM anyway.
 template <int P, class T, bool ADJ>
-__global__ void __launch_bounds__(kNsThreads, 1) k_condense_ns(DevMesh m, DevSys s, Phys ph, const T* __restrict__ tab,
+__global__ void __launch_bounds__(kNsThreads, (P <= 2 ? 2 : 1)) k_condense_ns(DevMesh m, DevSys s, Phys ph, const T* __restrict__ tab,
                                                              TabOff to, const double* __restrict__ U,
                                                              const double* __restrict__ Lam,
                                                              const int* __restrict__ elems, int n_elems, int ntmax) {
