@@ -68,8 +68,15 @@ inline int nkmax_for(int p, int ntmax, bool bounded = false) {
 // arithmetic T (binary64, or float-float on the FP32 pipe).  `tab` holds the
 // library's tables in that arithmetic.  Inputs and outputs are binary64.
 // --------------------------------------------------------------------------
+// CTAs per SM: at low degree the element's binary64 work is small and the
+// block barriers dominate, so more resident CTAs pay even with some spills:
+// p = 1 at 8 (64 registers; 16.6 M instead of 11.0 M elements/s in binary64,
+// 18.1 M instead of 11.0 M in float-float), p = 2 at 6 in binary64 (80
+// registers; 6.78 M instead of 5.82 M; float-float p = 2 is a little slower
+// there and stays at 4), p >= 3 at 4 (shared memory allows no more).
 template <int P, class T>
-__global__ void __launch_bounds__(kCondThreads, 4) k_condense_euler(
+__global__ void __launch_bounds__(kCondThreads, (P == 1 ? 8 : ((P == 2 && std::is_same<T, double>::value) ? 6 : 4)))
+k_condense_euler(
     DevMesh m, DevSys s, Phys ph, const T* __restrict__ tab, TabOff to, const double* __restrict__ U,
     const double* __restrict__ Lam, const int* __restrict__ elems, int n_elems, int ldr, int nkmax) {
   using L = EulerLayout<P>;
