@@ -9,8 +9,11 @@ copies, condensation, reconstruction, device->host copy of dU -- is enqueued
 on its own stream with ``hdg_step_host_async``, so requests that arrive while
 others are on the GPU overlap with them.  A completion is observed through a
 CUDA event; the request then releases its slot and its arena range at once.
-Nothing here allocates or frees device memory while requests are in flight
-(the arena is one tensor allocated at start-up; systems are carved from it).
+Systems and solvers are carved from one arena tensor allocated at start-up;
+while requests are in flight the only device allocations are the small mesh
+plans made at admission (``hdg_mesh_create``: topology, offsets, degree
+buckets), and nothing is freed until the run ends, so no call made here
+synchronises the device.
 
 With ``solve=True`` a request is a whole pseudo-transient Newton step of
 Sec. 3.3 instead: condensation at a finite CFL, the GPU trace solve of
