@@ -253,3 +253,59 @@ def test_block_ilu0_preconditioner_matches_oracle(ctx, name, nx, ny, kw, cfl):
         print(wl.name, "colors", nc, "transpose" if transpose else "", f"{err:.1e}", f"binary32 factors {err32:.1e}")
         assert err < 1e-11 and err32 < 1e-4
     solver32.close(); solver.close(); sysm.close(); mesh.close()
+
+
+def test_solver_api_rejects_bad_use(ctx):
+    """Host-side checks of the solver calls: a workspace smaller than planned or misaligned, a
+    switch to an ILU(0) kind the workspace was not planned for, an unknown kind, applying the
+    preconditioner before it is set up; a zero right-hand side returns zero at once."""
+    from paper_1308_3995_gb300 import hdg
+    wl = G.small_variant(G.WORKLOADS["euler_p3_16k"], 3, 4)
+    case, om, U, Lam, mesh, sysm, Ut, Lt = setup(ctx, wl, 10.0)
+    sysm.condense(Ut, Lt)
+    need = hdg.Solver.workspace_bytes(mesh, 20, 0)
+    assert hdg.Solver.workspace_bytes(mesh, 20, 2) > need and hdg.Solver.workspace_bytes(mesh, 20, 3) > need
+    buf = torch.empty(need + 512, dtype=torch.uint8, device="cuda:0")
+    with pytest.raises(hdg.HdgError) as ei:
+        hdg.Solver(sysm, 20, 0, workspace=(buf.data_ptr(), need - 256))
+    assert ei.value.status == hdg.HDG_EINVAL
+    with pytest.raises(hdg.HdgError) as ei:
+        hdg.Solver(sysm, 20, 0, workspace=(buf.data_ptr() + 8, need))
+    assert ei.value.status == hdg.HDG_EINVAL
+    s = hdg.Solver(sysm, 20, 0, workspace=(buf.data_ptr(), need))
+    with pytest.raises(hdg.HdgError) as ei:
+        s.set_preconditioner(2)                     # not planned in the caller's workspace
+    assert ei.value.status == hdg.HDG_ENOMEM
+    with pytest.raises(hdg.HdgError) as ei:
+        s.set_preconditioner(4)
+    assert ei.value.status == hdg.HDG_EINVAL
+    r = torch.randn(mesh.lam_len, dtype=torch.float64, device="cuda:0")
+    z = torch.empty_like(r)
+    with pytest.raises(hdg.HdgError) as ei:
+        s.precond_apply(r, z)                       # no setup yet
+    assert ei.value.status == hdg.HDG_EINVAL
+    s.setup()
+    s.precond_apply(r, z)
+    x = torch.ones(mesh.lam_len, dtype=torch.float64, device="cuda:0")
+    it, rel = s.solve(x, rtol=1e-10, rhs=torch.zeros_like(r))
+    torch.cuda.synchronize()
+    assert it == 0 and float(x.abs().max()) == 0.0
+    s.close(); sysm.close(); mesh.close()
+
+
+def test_source_and_cfl_are_frozen_by_a_captured_graph(ctx):
+    """A captured step holds the system's parameters: changing the CFL or the source afterwards is
+    refused (HDG_EINVAL) instead of silently not taking effect."""
+    from paper_1308_3995_gb300 import hdg
+    wl = G.small_variant(G.WORKLOADS["euler_p3_16k"], 3, 4)
+    case, om, U, Lam, mesh, sysm, Ut, Lt = setup(ctx, wl, 10.0)
+    dLt = torch.zeros(mesh.lam_len, dtype=torch.float64, device="cuda:0")
+    dUt = torch.empty(mesh.u_len, dtype=torch.float64, device="cuda:0")
+    sysm.graph_create(Ut, Lt, dLt, dUt)
+    with pytest.raises(hdg.HdgError) as ei:
+        sysm.set_cfl(5.0)
+    assert ei.value.status == hdg.HDG_EINVAL
+    with pytest.raises(hdg.HdgError) as ei:
+        sysm.set_source(torch.zeros(mesh.u_len, dtype=torch.float64, device="cuda:0"))
+    assert ei.value.status == hdg.HDG_EINVAL
+    sysm.close(); mesh.close()
