@@ -41,12 +41,15 @@ EXPORTS = ["hdg_create", "hdg_destroy", "hdg_last_error", "hdg_mesh_create", "hd
 
 
 class HdgError(RuntimeError):
+    """A non-OK hdg_status with the library's last error message; ``status`` holds the code."""
+
     def __init__(self, status, msg):
         super().__init__(f"{STATUS_NAMES.get(status, status)}: {msg}")
         self.status = status
 
 
 class hdg_params(ctypes.Structure):
+    """The C struct hdg_params (include/hdg.h), field for field."""
     _fields_ = [("model", ctypes.c_int32), ("precision", ctypes.c_int32), ("gamma", ctypes.c_double),
                 ("prandtl", ctypes.c_double), ("reynolds", ctypes.c_double), ("mach", ctypes.c_double),
                 ("alpha", ctypes.c_double), ("cfl", ctypes.c_double), ("t_inf", ctypes.c_double),
@@ -56,6 +59,9 @@ class hdg_params(ctypes.Structure):
 
 @dataclass
 class Params:
+    """Physical and numerical parameters of a system (hdg_params): model, arithmetic, gas
+    constants, Mach number, stabilisation alpha, pseudo-time CFL (<= 0: pure Newton), shock
+    capturing and the free-stream angle of attack."""
     model: int = HDG_EULER
     precision: int = HDG_FP64
     gamma: float = 1.4
@@ -72,6 +78,7 @@ class Params:
     aoa: float = 0.0         # free-stream angle of attack [degrees]: the far-field state
 
     def c(self) -> hdg_params:
+        """The C struct for a call."""
         return hdg_params(self.model, self.precision, self.gamma, self.prandtl, self.reynolds, self.mach,
                           self.alpha, self.cfl, self.t_inf, self.refine_tol, self.refine_max, 0,
                           self.sc_eps0, self.sc_beta, self.aoa)
@@ -213,6 +220,7 @@ class Solver:
 
     @staticmethod
     def workspace_bytes(mesh: "Mesh", restart: int = 30, precond: int = 0) -> int:
+        """hdg_solver_workspace_bytes: device bytes of a solver on this mesh (for create_ws)."""
         n = int(lib().hdg_solver_workspace_bytes(mesh.h, int(restart), int(precond)))
         if n < 0:
             raise HdgError(HDG_EINVAL, "hdg_solver_workspace_bytes: invalid arguments")
@@ -241,10 +249,12 @@ class Solver:
         return int(it.value), float(rel.value)
 
     def matvec(self, x, y, stream=None, transpose=False):
+        """hdg_trace_matvec: y = K x (or K^T x) for device tensors."""
         _check(lib().hdg_trace_matvec(self.h, _ptr(x), _ptr(y), int(bool(transpose)), _stream(stream)),
                self.sys.ctx.h)
 
     def set_preconditioner(self, kind: int):
+        """hdg_solver_set_preconditioner: 0 block Jacobi, 1 block SGS, 2 block ILU(0), 3 ILU(0) binary32."""
         _check(lib().hdg_solver_set_preconditioner(self.h, int(kind)), self.sys.ctx.h)
 
     def setup(self, stream=None):
@@ -325,6 +335,7 @@ class Context:
             pass
 
     def last_error(self) -> str:
+        """hdg_last_error of this context."""
         return lib().hdg_last_error(self.h).decode()
 
 
@@ -363,10 +374,12 @@ class Mesh:
         self.elem_p = p.astype(np.int32)
 
     def footprint_bytes(self, params: Params) -> int:
+        """hdg_footprint_bytes: device bytes a system on this mesh holds (admission)."""
         P = params.c()
         return int(lib().hdg_footprint_bytes(self.h, ctypes.byref(P)))
 
     def workspace_bytes(self, params: Params) -> int:
+        """hdg_sys_workspace_bytes: bytes of caller workspace for hdg_sys_create_in."""
         P = params.c()
         return int(lib().hdg_sys_workspace_bytes(self.h, ctypes.byref(P)))
 
@@ -430,6 +443,7 @@ class System:
 
     @property
     def launches(self) -> int:
+        """hdg_sys_launches: kernel launches of the last condense + recover."""
         return int(lib().hdg_sys_launches(self.h))
 
     def set_source(self, S=None):
