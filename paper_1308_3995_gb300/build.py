@@ -62,7 +62,7 @@ def build(force: bool = False, verbose: bool = False, ptxas_info: bool = False) 
             if log:
                 print(log)
     tmp = LIB + f".tmp{os.getpid()}"
-    cmd = [nvcc, *ARCH, "-shared", "-o", tmp] + [o for o, _ in results]
+    cmd = [nvcc, *ARCH, "-shared", "-o", tmp] + [o for o, _ in results] + ["-ldl"]  # dl: NVTX loader
     r = subprocess.run(cmd, capture_output=True, text=True)
     if r.returncode != 0:
         raise RuntimeError(f"link failed:\n{r.stdout}\n{r.stderr}")

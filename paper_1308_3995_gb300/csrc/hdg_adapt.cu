@@ -126,6 +126,7 @@ extern "C" {
 
 hdg_status hdg_adapt_indicators(hdg_sys* sys, const double* U, const double* Uadj, double* eta2, double* sensor,
                                 void* stream) {
+  hdg::NvtxRange nvtx_range_("hdg::adapt_indicators");
   if (!sys) return HDG_EINVAL;
   if (!U || (!sensor && !(eta2 && Uadj))) return fail(sys->ctx, HDG_EINVAL, "hdg_adapt_indicators: null argument");
   const hdg_mesh* M = sys->mesh;
@@ -137,6 +138,7 @@ hdg_status hdg_adapt_indicators(hdg_sys* sys, const double* U, const double* Uad
 
 hdg_status hdg_adapt_mark(hdg_ctx* ctx, int32_t n, const double* eta2, const double* sensor, double theta,
                           double eps_s, int8_t* code, int32_t* n_marked, void* stream) {
+  hdg::NvtxRange nvtx_range_("hdg::adapt_mark");
   if (!ctx) return HDG_EINVAL;
   if (n < 1 || !eta2 || !sensor || !code || !(theta >= 0.0 && theta <= 1.0))
     return fail(ctx, HDG_EINVAL, "hdg_adapt_mark: bad arguments");

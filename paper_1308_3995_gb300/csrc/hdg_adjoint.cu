@@ -70,6 +70,7 @@ extern "C" {
 
 hdg_status hdg_adjoint_condense(hdg_sys* adj, const hdg_sys* primal, const double* U, const double* Lam,
                                 const double* Ftilde, void* stream) {
+  hdg::NvtxRange nvtx_range_("hdg::adjoint_condense");
   if (!adj || !primal) return HDG_EINVAL;
   hdg_ctx* ctx = adj->ctx;
   if (!U || !Lam || !Ftilde) return fail(ctx, HDG_EINVAL, "hdg_adjoint_condense: null input");

@@ -502,6 +502,7 @@ hdg_status hdg_sys_destroy(hdg_sys* S) {
 }
 
 hdg_status hdg_condense(hdg_sys* S, const double* U, const double* Lam, void* stream) {
+  hdg::NvtxRange nvtx_range_("hdg::condense");
   if (!S) return HDG_EINVAL;
   hdg_ctx* ctx = S->ctx;
   if (!U || !Lam) return fail(ctx, HDG_EINVAL, "hdg_condense: null input");
@@ -567,6 +568,7 @@ hdg_status hdg_sys_bucket_times(const hdg_sys* S, float* ms) {
 }
 
 hdg_status hdg_recover(hdg_sys* S, const double* dLam, double* dU, void* stream) {
+  hdg::NvtxRange nvtx_range_("hdg::recover");
   if (!S) return HDG_EINVAL;
   hdg_ctx* ctx = S->ctx;
   if (!dLam || !dU) return fail(ctx, HDG_EINVAL, "hdg_recover: null argument");
@@ -580,6 +582,7 @@ hdg_status hdg_recover(hdg_sys* S, const double* dLam, double* dU, void* stream)
 
 hdg_status hdg_step_host_async(hdg_sys* S, const double* U, const double* Lam, const double* dLam, double* dU,
                                void* stream) {
+  hdg::NvtxRange nvtx_range_("hdg::step_host");
   if (!S) return HDG_EINVAL;
   hdg_ctx* ctx = S->ctx;
   if (!U || !Lam || !dLam || !dU) return fail(ctx, HDG_EINVAL, "hdg_step_host_async: null argument");
@@ -606,6 +609,7 @@ hdg_status hdg_step_host(hdg_sys* S, const double* U, const double* Lam, const d
 }
 
 hdg_status hdg_autotune(hdg_sys* S, const double* U, const double* Lam, int32_t* grid_out, void* stream) {
+  hdg::NvtxRange nvtx_range_("hdg::autotune");
   if (!S) return HDG_EINVAL;
   hdg_ctx* ctx = S->ctx;
   if (!U || !Lam) return fail(ctx, HDG_EINVAL, "hdg_autotune: null input");

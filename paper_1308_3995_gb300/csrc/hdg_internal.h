@@ -6,6 +6,8 @@
 #include <string>
 #include <vector>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include "../../include/hdg.h"
 
 #ifdef __CUDACC__
@@ -15,6 +17,16 @@
 #endif
 
 namespace hdg {
+
+// Named range around a host API call for timeline tools (NVTX; a no-op unless a
+// tool is attached): the library's phases show up as hdg::condense, ... .
+struct NvtxRange {
+  explicit NvtxRange(const char* name) { nvtxRangePushA(name); }
+  ~NvtxRange() { nvtxRangePop(); }
+  NvtxRange(const NvtxRange&) = delete;
+  NvtxRange& operator=(const NvtxRange&) = delete;
+};
+
 
 constexpr int kMaxP = 4;          // element degrees 1..4
 constexpr int kMaxNt = 60;        // 3 faces x 4 fields x (4 + 1) modes

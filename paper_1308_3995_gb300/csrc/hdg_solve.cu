@@ -1011,6 +1011,7 @@ hdg_status hdg_solver_set_preconditioner(hdg_solver* S, int32_t kind) {
 }
 
 hdg_status hdg_solver_setup(hdg_solver* S, void* stream) {
+  hdg::NvtxRange nvtx_range_("hdg::solver_setup");
   if (!S) return HDG_EINVAL;
   hdg_ctx* ctx = S->sys->ctx;
   cudaStream_t st = (cudaStream_t)stream;
@@ -1057,6 +1058,7 @@ hdg_status hdg_trace_solve(hdg_solver* S, double* x, double rtol, int32_t max_it
 
 hdg_status hdg_trace_solve_ex(hdg_solver* S, const double* rhs, int32_t transpose, double* x, double rtol,
                               int32_t max_iter, int32_t* iters_out, double* rel_out, void* stream) {
+  hdg::NvtxRange nvtx_range_("hdg::trace_solve");
   if (!S || !x || !(rtol > 0.0) || max_iter < 1) return HDG_EINVAL;
   const bool tr = transpose != 0;
   hdg_ctx* ctx = S->sys->ctx;
@@ -1164,6 +1166,7 @@ hdg_status hdg_trace_solve_ex(hdg_solver* S, const double* rhs, int32_t transpos
 hdg_status hdg_solve_step_host(hdg_sys* sys, hdg_solver* S, const double* U, const double* Lam, double* dU,
                                double* dLam, double rtol, int32_t max_iter, int32_t* iters, double* rel_res,
                                void* stream) {
+  hdg::NvtxRange nvtx_range_("hdg::solve_step_host");
   if (!sys || !S) return HDG_EINVAL;
   hdg_ctx* ctx = sys->ctx;
   if (S->sys != sys) return fail(ctx, HDG_EINVAL, "hdg_solve_step_host: the solver belongs to another system");

@@ -395,3 +395,21 @@ def test_bucket_times_of_a_mixed_degree_launch(ctx):
         print(name, t)
         sysm.close()
         mesh.close()
+
+
+def test_degenerate_stabilisation_is_refused(ctx):
+    """alpha = 0 (no pseudo time) makes every local block singular -- the constant mode's rows of
+    A_K vanish, pinned on the oracle -- so the library refuses it at system creation (HDG_EINVAL)
+    instead of returning a field of zero-pivot statuses; a small positive alpha is accepted."""
+    from paper_1308_3995_gb300 import hdg
+    wl = G.small_variant(G.WORKLOADS["euler_p3_16k"], 4, 5)
+    case, om, U, Lam, dLam = build_case(wl)
+    mesh = hdg.Mesh(ctx, case.mesh.elem_xy, case.mesh.elem_vid, case.elem_p, case.nfield)
+    prm = lib_params(wl, 0.0, 0)
+    prm.alpha = 0.0
+    with pytest.raises(hdg.HdgError) as ei:
+        hdg.System(ctx, mesh, prm)
+    assert ei.value.status == hdg.HDG_EINVAL
+    prm.alpha = 1e-3
+    sysm = hdg.System(ctx, mesh, prm)
+    sysm.close(); mesh.close()

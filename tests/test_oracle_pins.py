@@ -1127,3 +1127,20 @@ def test_manufactured_solution_residual_is_high_order():
         m.set_source(None)
     assert res0[0] / res0[1] < 2 ** 2.5, res0
     assert res[0] / res[1] > 2 ** 3.5 and res[1] < 0.05 * res0[1], res
+
+
+def test_zero_stabilisation_makes_every_local_block_singular():
+    """With alpha = 0 and no pseudo time the constant mode's row of A_K is exactly zero (grad phi_0
+    = 0 and the face flux has no -alpha (lambda - w) term), so the local LU meets a zero pivot:
+    the per-element status reports it (1) instead of a result."""
+    wl, c, m, P = _case("euler_p1_256", 3, 4)
+    U, L, _ = G.case_state(c, m.face_vid, m.face_p)
+    A = m.element_blocks(P, 0, U, L)[0]
+    assert np.abs(A[0]).max() > 0                         # regular with alpha > 0
+    P.alpha = 0.0
+    A0 = m.element_blocks(P, 0, U, L)[0]
+    nb = O.n_basis(int(m.elem_p[0]))
+    for f in range(4):
+        assert np.abs(A0[f * nb]).max() == 0.0             # the constant mode's rows
+    r = m.condense(P, U, L)
+    assert np.all(r["status"] == 1)
