@@ -6,7 +6,10 @@ it, and it never imports the product package.
 
 Every function returns NumPy float64/int arrays.  The oracle follows the
 paper's definitions (arXiv:1308.3995, Sec. 2 physics, Sec. 3.2 HDG weak form,
-Sec. 3.3 pseudo time, Sec. 3.4 hybridization); see ``hdg_oracle.cpp``.
+Sec. 3.3 pseudo time, Sec. 3.4 hybridization, Sec. 4 adjoint and adaptation);
+see ``hdg_oracle.cpp``.  The block ILU(0) of the trace matrix (the paper's
+incomplete-LU preconditioner, Sec. 3.4) is written here in NumPy, in the
+textbook IKJ form.
 """
 from __future__ import annotations
 

@@ -11,7 +11,8 @@
 //   * physics: Euler convective flux and ideal-gas pressure (Sec. 2.1), viscous
 //     flux, temperature, Newtonian stress and Sutherland viscosity (Sec. 2.2);
 //   * the HDG residual N_h of Eq. (hdg_ls1)-(hdg_cont) with the combined
-//     Lax-Friedrichs/LDG-type numerical flux of Sec. 3.2 (source s = 0), the
+//     Lax-Friedrichs/LDG-type numerical flux of Sec. 3.2 (source s: zero, or a
+//     state-independent s_h given by its projection coefficients), the
 //     boundary operator of Sec. 3.2 on tagged boundary faces (Euler: slip wall
 //     and characteristic far field; Navier-Stokes: no-slip adiabatic wall;
 //     boundary states and wall viscous flux of Sec. 2.1/2.2), optionally with the
