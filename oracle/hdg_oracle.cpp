@@ -14,7 +14,8 @@
 //     Lax-Friedrichs/LDG-type numerical flux of Sec. 3.2 (source s: zero, or a
 //     state-independent s_h given by its projection coefficients), the
 //     boundary operator of Sec. 3.2 on tagged boundary faces (Euler: slip wall
-//     and characteristic far field; Navier-Stokes: no-slip adiabatic wall;
+//     and characteristic far field; Navier-Stokes: no-slip adiabatic wall and
+//     characteristic far field with the viscous flux at the far-field state;
 //     boundary states and wall viscous flux of Sec. 2.1/2.2), optionally with the
 //     shock-capturing volume term of Sec. 3.2 (artificial viscosity eps_K from
 //     the L1 norm of the strong convective residual, effective size h_K / p_K);
@@ -562,9 +563,10 @@ static void element_residual(const OMesh& M, const orc_params& P, int K, const G
         euler_flux(wb, P.gamma, fc);
         for (int k = 0; k < 2; ++k) for (int f = 0; f < 4; ++f) fv[k][f] = 0.0;
         if (ns) {
-          // no-slip adiabatic wall: q_b = q_h (the interior gradient), and the
-          // wall's viscous flux is (0, tau, 0): the energy row (tau.v_b + k grad T)
-          // vanishes as v_b = 0 and grad T . n = 0
+          // q_b = q_h (the interior gradient); at a no-slip adiabatic wall the
+          // viscous flux is (0, tau, 0): the energy row (tau.v_b + k grad T)
+          // vanishes as v_b = 0 and grad T . n = 0; at a far-field face it is
+          // f_v(w_b, q_h) whole
           T qv[2][4];
           for (int k = 0; k < 2; ++k)
             for (int f = 0; f < 4; ++f) {
@@ -572,8 +574,10 @@ static void element_residual(const OMesh& M, const orc_params& P, int K, const G
               for (int j = 0; j < np; ++j) qv[k][f] += U[(k * 4 + f) * np + j] * phi[j];
             }
           ns_viscous_flux(wb, qv, P, fv);
-          fv[0][3] = 0.0;
-          fv[1][3] = 0.0;
+          if (M.bc[K * 3 + lf] == 3) {  // adiabatic no-slip wall: (0, tau, 0)
+            fv[0][3] = 0.0;
+            fv[1][3] = 0.0;
+          }
           // -<tau.n, w_b>_dK in the q equations
           for (int k = 0; k < 2; ++k) {
             const double nk_ = (k == 0) ? nx : ny;
@@ -831,7 +835,8 @@ void orc_ns_viscous_flux(const double* w, const double* q, const orc_params* P, 
 // Build the mesh.  Returns 0 ok, 2 bad input (non-positive det J, p out of
 // range, a face not shared by exactly two elements, two elements sharing two faces).
 // elem_bc (may be null: every face interior) [n_elem][3]: 0 interior, 1 slip
-// wall, 2 far field (Euler), 3 no-slip adiabatic wall (Navier-Stokes);
+// wall (Euler), 2 far field (both models), 3 no-slip adiabatic wall
+// (Navier-Stokes);
 // boundary faces carry no trace unknowns.
 int orc_mesh_create(int n_elem, int nfield, const double* elem_xy, const int32_t* elem_vid,
                     const int8_t* elem_p, const int8_t* elem_bc, void** out) {
@@ -846,7 +851,7 @@ int orc_mesh_create(int n_elem, int nfield, const double* elem_xy, const int32_t
   for (int t = 0; elem_bc && t < 3 * n_elem; ++t) {
     M->bc[t] = elem_bc[t];
     const int b = M->bc[t];
-    const bool ok = b == 0 || (nfield == 4 && (b == 1 || b == 2)) || (nfield == 12 && b == 3);
+    const bool ok = b == 0 || (nfield == 4 && (b == 1 || b == 2)) || (nfield == 12 && (b == 2 || b == 3));
     if (!ok) { delete M; return 2; }
   }
   for (int K = 0; K < n_elem; ++K) {

@@ -379,6 +379,9 @@ WORKLOADS = {
     # triangles, p in {1,2,3,4} at 40/30/20/10 %, Mach 0.5, Re 5000, Fourier modes on the free stream
     "ns_wall_channel_8k": Workload("ns_wall_channel_8k", 64, 64, 0.2, 1, None, (0.4, 0.3, 0.2, 0.1), "fourier",
                                    0.5, 0.0, seed=77, domain="wall_channel"),
+    # Navier-Stokes with far field on all four sides (Mach 0.5 at 10 degrees + density bump); the
+    # oracle covers it, the library does not yet
+    "ns_box_8k": Workload("ns_box_8k", 64, 64, 0.2, 1, 2, None, "bump", 0.5, 10.0, seed=88, domain="box"),
 }
 
 

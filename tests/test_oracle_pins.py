@@ -1144,3 +1144,53 @@ def test_zero_stabilisation_makes_every_local_block_singular():
         assert np.abs(A0[f * nb]).max() == 0.0             # the constant mode's rows
     r = m.condense(P, U, L)
     assert np.all(r["status"] == 1)
+
+
+# ----------------------------------------------------------------------------- Navier-Stokes far field
+def _ns_box(nx, ny, **kw):
+    wl = G.small_variant(G.WORKLOADS["ns_box_8k"], nx, ny, **kw)
+    c = G.make_case(wl)
+    m = O.Mesh(c.mesh.elem_xy, c.mesh.elem_vid, c.elem_p, c.nfield, c.mesh.elem_bc)
+    P = O.Params(model=1, mach=wl.mach, alpha=wl.alpha, reynolds=wl.reynolds, prandtl=wl.prandtl, aoa=wl.aoa)
+    return wl, c, m, P
+
+
+def test_ns_far_field_free_stream_preservation():
+    """Navier-Stokes with far field on every side: the uniform free stream (q = 0) is a steady
+    state -- the far-field state equals w_inf and f_v(w_inf, 0) = 0."""
+    wl, c, m, P = _ns_box(4, 3)
+    U, L = _uniform_state(m, G.conserved(*G.free_stream(wl.mach, wl.aoa)))
+    Ru, Rl = m.global_residual(P, U, L)
+    assert np.abs(Ru).max() < 1e-13 and np.abs(Rl).max() < 1e-13
+
+
+def test_ns_far_field_jacobian_vs_central_differences():
+    """Complex-step Newton blocks of far-field elements (characteristic state, viscous flux at the
+    far-field state, gradient-equation term) agree with central finite differences."""
+    wl, c, m, P = _ns_box(4, 3, p=2)
+    U, L, _ = G.case_state(c, m.face_vid, m.face_p)
+    bel = [K for K in range(m.n_elem) if c.mesh.elem_bc[K].any()]
+    rng = np.random.default_rng(6)
+    for K in (bel[0], bel[len(bel) // 2], bel[-1]):
+        A = m.element_blocks(P, K, U, L)[0]
+        for col in rng.choice(A.shape[0], 6, replace=False):
+            h = 1e-6
+            Up, Um = U.copy(), U.copy()
+            Up[m.u_off[K] + col] += h; Um[m.u_off[K] + col] -= h
+            du = (m.element_residual(P, K, Up, L)[0] - m.element_residual(P, K, Um, L)[0]) / (2 * h)
+            assert np.abs(du - A[:, col]).max() < 1e-7 * max(1.0, np.abs(A).max())
+
+
+def test_ns_far_field_condensed_then_recovered_equals_monolithic():
+    """Sec. 3.4 on the Navier-Stokes box: the condensed solve plus reconstruction equals the
+    monolithic Newton step (CFL 10)."""
+    wl, c, m, P = _ns_box(3, 3, p=1)
+    P.cfl = 10.0
+    U, L, _ = G.case_state(c, m.face_vid, m.face_p)
+    dU, dL = m.monolithic(P, U, L)
+    r = m.condense(P, U, L)
+    assert r["status"].max() == 0
+    dLc = O.dense_solve(m.dense_K(r["K"]), r["E"])
+    dUc = m.recover(r["X"], dLc)
+    assert np.abs(dLc - dL).max() < 1e-10 * np.abs(dL).max()
+    assert np.abs(dUc - dU).max() < 1e-10 * np.abs(dU).max()
