@@ -88,3 +88,19 @@ def test_library_cfl_law_closed_forms():
     assert abs(hdg.cfl_law(6, c1=1e3, n0=4, cfl_prev=7.0, res_prev=1.0, res_cur=0.5)
                - 7.0 * (1 + 1e3 * math.log(2))) < 1e-9
     assert hdg.cfl_law(-1) < 0 and hdg.cfl_law(5, n0=4, cfl_prev=1.0, res_prev=0.0, res_cur=1.0) < 0
+
+
+def test_abi_header_is_plain_c(tmp_path):
+    """include/hdg.h is the whole boundary: it compiles as strict C99 (plain pointers, sizes and
+    POD structs, no C++ or framework types) and as C++."""
+    import shutil
+    import subprocess
+    if not shutil.which("gcc"):
+        pytest.skip("gcc not available")
+    for lang, std, ext in (("c", "-std=c99", "c"), ("c++", "-std=c++11", "cpp")):
+        src = tmp_path / f"h.{ext}"
+        src.write_text('#include "hdg.h"\nint main(void) { return (int)sizeof(hdg_params) > 0 ? 0 : 1; }\n')
+        cc = "gcc" if lang == "c" else "g++"
+        r = subprocess.run([cc, std, "-Wall", "-Wextra", "-Werror", "-pedantic", "-I", os.path.join(ROOT, "include"),
+                            "-c", str(src), "-o", str(tmp_path / f"h_{ext}.o")], capture_output=True, text=True)
+        assert r.returncode == 0, r.stderr
