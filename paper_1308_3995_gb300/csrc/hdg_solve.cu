@@ -497,6 +497,7 @@ __global__ void __launch_bounds__(kDotThreads) k_dots_slab(const double* __restr
       const double2 wb = two ? __ldg(w2 + i + 32) : make_double2(0.0, 0.0);
 #pragma unroll
       for (int k = 0; k < VPW; ++k) {
+        if (jb + k * NW >= nvec) break;  // slot without a vector (warp-uniform): no loads, no FMAs
         const double2 a = __ldg(v2[k] + i);
         const double2 b = two ? __ldg(v2[k] + i + 32) : make_double2(0.0, 0.0);
         acc[k] = fma(a.x, wa.x, acc[k]);
