@@ -1194,3 +1194,36 @@ def test_ns_far_field_condensed_then_recovered_equals_monolithic():
     dUc = m.recover(r["X"], dLc)
     assert np.abs(dLc - dL).max() < 1e-10 * np.abs(dL).max()
     assert np.abs(dUc - dU).max() < 1e-10 * np.abs(dU).max()
+
+
+def test_ns_wall_below_far_field_above_condensed_equals_monolithic():
+    """A boundary-layer setup (no-slip adiabatic wall at y = 0, far field at y = 1, x-periodic):
+    the condensed solve plus reconstruction equals the monolithic Newton step at CFL 10, and the
+    complex-step blocks of the boundary elements agree with central differences."""
+    # flow at 10 degrees, so the far field's normal velocity stays clear of the characteristic
+    # switch at v_n = 0 (not differentiated, by the reading of the far-field Jacobian)
+    wl = G.small_variant(G.WORKLOADS["ns_wall_channel_8k"], 3, 3, p=2, probs=None, aoa=10.0)
+    c = G.make_case(wl)
+    bc = G.channel_mesh(wl.nx, wl.ny, wl.jitter, wl.seed, bottom=G.BC_NO_SLIP_WALL, top=G.BC_FAR_FIELD).elem_bc
+    m = O.Mesh(c.mesh.elem_xy, c.mesh.elem_vid, c.elem_p, c.nfield, bc)
+    P = O.Params(model=1, mach=wl.mach, alpha=wl.alpha, reynolds=wl.reynolds, prandtl=wl.prandtl, cfl=10.0,
+                 aoa=wl.aoa)
+    U, L, _ = G.case_state(c, m.face_vid, m.face_p)
+    dU, dL = m.monolithic(P, U, L)
+    r = m.condense(P, U, L)
+    assert r["status"].max() == 0
+    dLc = O.dense_solve(m.dense_K(r["K"]), r["E"])
+    dUc = m.recover(r["X"], dLc)
+    assert np.abs(dLc - dL).max() < 1e-10 * np.abs(dL).max()
+    assert np.abs(dUc - dU).max() < 1e-10 * np.abs(dU).max()
+    rng = np.random.default_rng(9)
+    P.cfl = 0.0                                          # the residual carries no pseudo-time mass
+    for K in (0, m.n_elem - 1):                          # a wall element and a far-field element
+        assert bc[K].any()
+        A = m.element_blocks(P, K, U, L)[0]
+        for col in rng.choice(A.shape[0], 4, replace=False):
+            h = 1e-6
+            Up, Um = U.copy(), U.copy()
+            Up[m.u_off[K] + col] += h; Um[m.u_off[K] + col] -= h
+            du = (m.element_residual(P, K, Up, L)[0] - m.element_residual(P, K, Um, L)[0]) / (2 * h)
+            assert np.abs(du - A[:, col]).max() < 1e-7 * max(1.0, np.abs(A).max())
