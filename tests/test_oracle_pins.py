@@ -1227,3 +1227,61 @@ def test_ns_wall_below_far_field_above_condensed_equals_monolithic():
             Up[m.u_off[K] + col] += h; Um[m.u_off[K] + col] -= h
             du = (m.element_residual(P, K, Up, L)[0] - m.element_residual(P, K, Um, L)[0]) / (2 * h)
             assert np.abs(du - A[:, col]).max() < 1e-7 * max(1.0, np.abs(A).max())
+
+
+# ----------------------------------------------------------------------------- pseudo-time mass (Sec. 3.3)
+def _one_triangle(nfield, p, xy):
+    """A single hand-placed triangle whose three faces are far-field boundaries (no trace unknowns)."""
+    return O.Mesh(np.array(xy, float).reshape(1, 6), np.array([[0, 1, 2]]), np.array([p]), nfield,
+                  np.array([[2, 2, 2]]))
+
+
+@pytest.mark.parametrize("model,reynolds,p", [(0, 5000.0, 2), (0, 5000.0, 3), (1, 5000.0, 2), (1, 10.0, 1),
+                                              (1, 0.5, 3)])
+def test_pseudo_time_mass_closed_form(model, reynolds, p):
+    """Sec. 3.3: backward-Euler pseudo time adds (phi_i, phi_j)_K / dt_K = det J / dt_K on the diagonal of
+    the W rows only, with dt_K = CFL |K| / (lambda_c + 4 lambda_v) from the element-mean state,
+    lambda_c = (|v| + c) * perimeter and lambda_v = gamma mu / (Pr rho) * perimeter^2 / |K|.  The expected
+    increment is written out from the vertex coordinates; a factor 4 -> 1, perimeter^2 -> perimeter,
+    |K| -> det J, a mean state other than sqrt(2) * (mode-0 coefficient), or the mass on the Q rows of the
+    mixed form each changes it by far more than the tolerance (the low Reynolds numbers make lambda_v
+    comparable to, and larger than, lambda_c)."""
+    gam, pr, mach, t_inf, cfl = 1.4, 0.72, 0.5, 288.15, 7.5
+    x0, y0, x1, y1, x2, y2 = 0.025, 0.01, 0.205, 0.045, 0.065, 0.165   # perimeter 0.53, |K| 0.013
+    detJ = (x1 - x0) * (y2 - y0) - (x2 - x0) * (y1 - y0)
+    area = 0.5 * detJ
+    perim = math.hypot(x1 - x0, y1 - y0) + math.hypot(x2 - x1, y2 - y1) + math.hypot(x0 - x2, y0 - y2)
+    rho, u, v, pres = 1.2, 0.31, -0.17, 0.9
+    E = pres / (gam - 1) + 0.5 * rho * (u * u + v * v)
+    c = math.sqrt(gam * pres / rho)
+    lam_c = (math.hypot(u, v) + c) * perim
+    lam_v = 0.0
+    if model == 1:
+        T = gam * pres / rho
+        S = 110.4 / t_inf
+        mu = mach / reynolds * T ** 1.5 * (1 + S) / (T + S)
+        lam_v = gam * mu / (pr * rho) * perim ** 2 / area
+    dt = cfl * area / (lam_c + 4 * lam_v)
+    expected = detJ / dt
+
+    nfield = 12 if model == 1 else 4
+    m = _one_triangle(nfield, p, [x0, y0, x1, y1, x2, y2])
+    nb = O.n_basis(p)
+    rng = np.random.default_rng(7 + p)
+    U = 1e-2 * rng.standard_normal(m.u_len)          # higher modes and gradients: must not enter dt_K
+    woff = 8 * nb if model == 1 else 0
+    for f, wf in enumerate((rho, rho * u, rho * v, E)):
+        U[woff + f * nb] = wf / math.sqrt(2)           # element mean = sqrt(2) * mode-0 coefficient
+    Lam = np.zeros(m.lam_len)
+    P0 = O.Params(model=model, mach=mach, alpha=1.5, reynolds=reynolds, prandtl=pr, gamma=gam, t_inf=t_inf)
+    P1 = O.Params(model=model, mach=mach, alpha=1.5, reynolds=reynolds, prandtl=pr, gamma=gam, t_inf=t_inf,
+                  cfl=cfl)
+    A0 = m.element_blocks(P0, 0, U, Lam)[0]
+    A1 = m.element_blocks(P1, 0, U, Lam)[0]
+    dA = A1 - A0
+    n = m.n(0)
+    want = np.zeros((n, n))
+    want[np.arange(woff, n), np.arange(woff, n)] = expected
+    assert np.abs(dA - want).max() <= 1e-12 * expected
+    if model == 1 and reynolds < 100:
+        assert 4 * lam_v > 0.05 * lam_c                 # the viscous part is not negligible here
