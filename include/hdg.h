@@ -62,6 +62,9 @@
  *     it creates are freed by the matching destroy call.
  *   - A context is used from one host thread at a time.  Calls on different
  *     systems may run on different streams concurrently.
+ *   - Every call that touches the GPU makes its context's device current for
+ *     the duration of the call and restores the calling thread's current
+ *     device before it returns.
  */
 #ifndef HDG_H_
 #define HDG_H_
@@ -456,8 +459,10 @@ double hdg_cfl_law(int32_t n, double c0, double c1, int32_t n0, double cfl_prev,
  * serving loops with a latency budget (cudaMalloc and cudaFree can synchronise
  * the whole device and take unbounded time) and hosts whose device memory is
  * owned by another allocator or fixed at start-up.  It does the work of
- * hdg_condense (same kernels, bitwise the same results) on the mesh's device,
- * enqueued on `stream`, but writes to CALLER device buffers: X [x_len],
+ * hdg_condense for a system without a source term (same kernels, bitwise the
+ * same results; a source set on some system with hdg_sys_set_source is not
+ * seen here: s = 0) on the mesh's device, enqueued on `stream`, but writes to
+ * CALLER device buffers: X [x_len],
  * K_vals [k_len], E [lam_len], res_u [u_len], res_lam [lam_len],
  * elem_status [n_elem] (sizes from hdg_mesh_sizes; U, Lam as in hdg_condense).
  * It calls no cudaMalloc, cudaFree or other allocating routine: the per-face
@@ -469,8 +474,12 @@ double hdg_cfl_law(int32_t n, double c0, double c1, int32_t n0, double cfl_prev,
  *     about 19,000 faces at p_e = 4, 29,000 at p_e = 3).  Only the FP64 Euler
  *     path is supported (else HDG_ENOTSUP).
  *   - The first call on a device resolves the array's device address
- *     (cudaGetSymbolAddress, with that device made current); make that first
- *     call before any stream capture on the device.
+ *     (cudaGetSymbolAddress, with that device made current) and keeps it for
+ *     the life of the process; make that first call before any stream capture
+ *     on the device.  A cudaDeviceReset of that device invalidates the kept
+ *     address: the call is not supported after one.
+ *   - The mesh's device is made current for the call; the calling thread's
+ *     current device is restored before it returns.
  *   - Every call shares the one array, which keeps the last call's contents;
  *     the call clears the part that must start at zero (the arrival counters)
  *     on `stream` before its kernels.  Calls whose work overlaps on the GPU

@@ -129,6 +129,7 @@ hdg_status hdg_adapt_indicators(hdg_sys* sys, const double* U, const double* Uad
   hdg::NvtxRange nvtx_range_("hdg::adapt_indicators");
   if (!sys) return HDG_EINVAL;
   if (!U || (!sensor && !(eta2 && Uadj))) return fail(sys->ctx, HDG_EINVAL, "hdg_adapt_indicators: null argument");
+  HDG_ON_DEVICE(sys->ctx, sys->ctx->device);
   const hdg_mesh* M = sys->mesh;
   k_indicators<<<(M->n_elem + 255) / 256, 256, 0, (cudaStream_t)stream>>>(M->n_elem, M->nfield, M->dm.u_off, U,
                                                                           sys->ds.res_u, Uadj, eta2, sensor);
@@ -142,6 +143,7 @@ hdg_status hdg_adapt_mark(hdg_ctx* ctx, int32_t n, const double* eta2, const dou
   if (!ctx) return HDG_EINVAL;
   if (n < 1 || !eta2 || !sensor || !code || !(theta >= 0.0 && theta <= 1.0))
     return fail(ctx, HDG_EINVAL, "hdg_adapt_mark: bad arguments");
+  HDG_ON_DEVICE(ctx, ctx->device);
   cudaStream_t st = (cudaStream_t)stream;
   int sms = 0;
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, ctx->device);

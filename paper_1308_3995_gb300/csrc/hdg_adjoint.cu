@@ -74,6 +74,7 @@ hdg_status hdg_adjoint_condense(hdg_sys* adj, const hdg_sys* primal, const doubl
   if (!adj || !primal) return HDG_EINVAL;
   hdg_ctx* ctx = adj->ctx;
   if (!U || !Lam || !Ftilde) return fail(ctx, HDG_EINVAL, "hdg_adjoint_condense: null input");
+  HDG_ON_DEVICE(ctx, ctx->device);
   const hdg_mesh* M = adj->mesh;
   if (primal->mesh != M) return fail(ctx, HDG_EINVAL, "hdg_adjoint_condense: systems on different meshes");
   if (primal->ph.precision != adj->ph.precision || primal->ph.cfl != adj->ph.cfl ||

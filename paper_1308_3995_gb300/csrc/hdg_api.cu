@@ -91,8 +91,9 @@ hdg_status hdg_create(hdg_ctx** out, int device) {
   *out = nullptr;
   hdg_ctx* ctx = new hdg_ctx();
   ctx->device = device;
-  cudaError_t e = cudaSetDevice(device);
-  if (e != cudaSuccess) { delete ctx; return HDG_ECUDA; }
+  hdg::DeviceGuard dg(device);
+  if (!dg.ok()) { delete ctx; return HDG_ECUDA; }
+  cudaError_t e;
   build_tables(ctx->tab);
   e = cudaMalloc(&ctx->d_tab, sizeof(double) * ctx->tab.data.size());
   if (e != cudaSuccess) { delete ctx; return HDG_ENOMEM; }
@@ -115,7 +116,7 @@ hdg_status hdg_create(hdg_ctx** out, int device) {
 
 hdg_status hdg_destroy(hdg_ctx* ctx) {
   if (!ctx) return HDG_EINVAL;
-  cudaSetDevice(ctx->device);
+  hdg::DeviceGuard dg(ctx->device);
   cudaFree(ctx->d_tab);
   cudaFree(ctx->d_tab_ff);
   delete ctx;
@@ -146,7 +147,7 @@ hdg_status hdg_mesh_create_bc(hdg_ctx* ctx, int32_t n_elem, int32_t nfield, cons
       return fail(ctx, HDG_ENOTSUP, "hdg_mesh_create_bc: Navier-Stokes boundaries are no-slip adiabatic walls (kind 3)");
     any_bc |= b != 0;
   }
-  if (cudaSetDevice(ctx->device) != cudaSuccess) return fail(ctx, HDG_ECUDA, "cudaSetDevice failed");
+  HDG_ON_DEVICE(ctx, ctx->device);
   hdg_mesh* M = new hdg_mesh();
   M->ctx = ctx;
   M->n_elem = n_elem;
@@ -306,7 +307,7 @@ hdg_status hdg_mesh_create_bc(hdg_ctx* ctx, int32_t n_elem, int32_t nfield, cons
 
 hdg_status hdg_mesh_destroy(hdg_mesh* M) {
   if (!M) return HDG_EINVAL;
-  cudaSetDevice(M->ctx->device);
+  hdg::DeviceGuard dg(M->ctx->device);
   free_all(M->allocs);
   delete M;
   return HDG_OK;
@@ -368,7 +369,6 @@ hdg_status sys_validate(hdg_ctx* ctx, const hdg_mesh* M, const hdg_params* P, co
     return fail(ctx, HDG_EINVAL, w + ": need gamma > 1, alpha > 0, mach > 0");
   if (P->sc_eps0 > 0.0 && !(std::isfinite(P->sc_eps0) && std::isfinite(P->sc_beta)))
     return fail(ctx, HDG_EINVAL, w + ": shock capturing needs finite sc_eps0 and sc_beta");
-  if (cudaSetDevice(ctx->device) != cudaSuccess) return fail(ctx, HDG_ECUDA, "cudaSetDevice failed");
   return HDG_OK;
 }
 
@@ -445,6 +445,7 @@ int64_t hdg_sys_workspace_bytes(const hdg_mesh* M, const hdg_params* P) {
 hdg_status hdg_sys_create(hdg_ctx* ctx, const hdg_mesh* M, const hdg_params* P, hdg_sys** out) {
   if (!ctx || !M || !P || !out) return HDG_EINVAL;
   *out = nullptr;
+  HDG_ON_DEVICE(ctx, ctx->device);
   hdg_status st = sys_validate(ctx, M, P, "hdg_sys_create");
   if (st != HDG_OK) return st;
   hdg_sys* S = sys_new(ctx, M, P);
@@ -462,6 +463,7 @@ hdg_status hdg_sys_create_in(hdg_ctx* ctx, const hdg_mesh* M, const hdg_params* 
                              int64_t workspace_bytes, hdg_sys** out) {
   if (!ctx || !M || !P || !out) return HDG_EINVAL;
   *out = nullptr;
+  HDG_ON_DEVICE(ctx, ctx->device);
   hdg_status st = sys_validate(ctx, M, P, "hdg_sys_create_in");
   if (st != HDG_OK) return st;
   const int64_t need = hdg_sys_workspace_bytes(M, P);
@@ -484,7 +486,7 @@ hdg_status hdg_sys_create_in(hdg_ctx* ctx, const hdg_mesh* M, const hdg_params* 
 
 hdg_status hdg_sys_destroy(hdg_sys* S) {
   if (!S) return HDG_EINVAL;
-  cudaSetDevice(S->ctx->device);
+  hdg::DeviceGuard dg(S->ctx->device);
   if (S->gexec) cudaGraphExecDestroy(S->gexec);
   if (S->graph) cudaGraphDestroy(S->graph);
   if (S->have_streams) {
@@ -506,6 +508,7 @@ hdg_status hdg_condense(hdg_sys* S, const double* U, const double* Lam, void* st
   if (!S) return HDG_EINVAL;
   hdg_ctx* ctx = S->ctx;
   if (!U || !Lam) return fail(ctx, HDG_EINVAL, "hdg_condense: null input");
+  HDG_ON_DEVICE(ctx, ctx->device);
   const hdg_mesh* M = S->mesh;
   cudaStream_t st = (cudaStream_t)stream;
   if (S->need_zero) {
@@ -557,6 +560,7 @@ hdg_status hdg_sys_bucket_times(const hdg_sys* S, float* ms) {
   if (!S || !ms) return HDG_EINVAL;
   for (int p = 0; p <= kMaxP; ++p) ms[p] = -1.0f;
   if (!S->timed) return HDG_OK;
+  HDG_ON_DEVICE(S->ctx, S->ctx->device);
   const hdg_mesh* M = S->mesh;
   for (int p = 1; p <= kMaxP; ++p) {
     if (!M->bucket_n[p]) continue;
@@ -572,6 +576,7 @@ hdg_status hdg_recover(hdg_sys* S, const double* dLam, double* dU, void* stream)
   if (!S) return HDG_EINVAL;
   hdg_ctx* ctx = S->ctx;
   if (!dLam || !dU) return fail(ctx, HDG_EINVAL, "hdg_recover: null argument");
+  HDG_ON_DEVICE(ctx, ctx->device);
   const hdg_mesh* M = S->mesh;
   std::string err;
   const int n = launch_recover_buckets(M->dm, S->ds.X, dLam, dU, M->d_bucket, M->bucket_n, stream, &err);
@@ -586,6 +591,7 @@ hdg_status hdg_step_host_async(hdg_sys* S, const double* U, const double* Lam, c
   if (!S) return HDG_EINVAL;
   hdg_ctx* ctx = S->ctx;
   if (!U || !Lam || !dLam || !dU) return fail(ctx, HDG_EINVAL, "hdg_step_host_async: null argument");
+  HDG_ON_DEVICE(ctx, ctx->device);
   const hdg_mesh* M = S->mesh;
   cudaStream_t st = (cudaStream_t)stream;
   const size_t d = sizeof(double);
@@ -602,6 +608,8 @@ hdg_status hdg_step_host_async(hdg_sys* S, const double* U, const double* Lam, c
 
 hdg_status hdg_step_host(hdg_sys* S, const double* U, const double* Lam, const double* dLam, double* dU,
                          void* stream) {
+  if (!S) return HDG_EINVAL;
+  HDG_ON_DEVICE(S->ctx, S->ctx->device);
   const hdg_status rc = hdg_step_host_async(S, U, Lam, dLam, dU, stream);
   if (rc != HDG_OK) return rc;
   HDG_CK(S->ctx, cudaStreamSynchronize((cudaStream_t)stream));
@@ -613,6 +621,7 @@ hdg_status hdg_autotune(hdg_sys* S, const double* U, const double* Lam, int32_t*
   if (!S) return HDG_EINVAL;
   hdg_ctx* ctx = S->ctx;
   if (!U || !Lam) return fail(ctx, HDG_EINVAL, "hdg_autotune: null input");
+  HDG_ON_DEVICE(ctx, ctx->device);
   if (S->gexec) return fail(ctx, HDG_EINVAL, "hdg_autotune: a captured graph holds the launch shapes");
   const hdg_mesh* M = S->mesh;
   cudaStream_t st = (cudaStream_t)stream;
@@ -673,6 +682,7 @@ hdg_status hdg_graph_create(hdg_sys* S, const double* U, const double* Lam, cons
   if (!S) return HDG_EINVAL;
   hdg_ctx* ctx = S->ctx;
   if (!U || !Lam || !dLam || !dU) return fail(ctx, HDG_EINVAL, "hdg_graph_create: null argument");
+  HDG_ON_DEVICE(ctx, ctx->device);
   const hdg_mesh* M = S->mesh;
   if (S->gexec) { cudaGraphExecDestroy(S->gexec); S->gexec = nullptr; }
   if (S->graph) { cudaGraphDestroy(S->graph); S->graph = nullptr; }
@@ -705,6 +715,7 @@ hdg_status hdg_graph_create(hdg_sys* S, const double* U, const double* Lam, cons
 hdg_status hdg_graph_launch(hdg_sys* S, void* stream) {
   if (!S) return HDG_EINVAL;
   if (!S->gexec) return fail(S->ctx, HDG_EINVAL, "hdg_graph_launch: no graph (call hdg_graph_create)");
+  HDG_ON_DEVICE(S->ctx, S->ctx->device);
   HDG_CK(S->ctx, cudaGraphLaunch(S->gexec, (cudaStream_t)stream));
   return HDG_OK;
 }

@@ -6,6 +6,7 @@
 #include <string>
 #include <vector>
 
+#include <cuda_runtime.h>
 #include <nvtx3/nvToolsExt.h>
 
 #include "../../include/hdg.h"
@@ -27,6 +28,35 @@ struct NvtxRange {
   NvtxRange& operator=(const NvtxRange&) = delete;
 };
 
+// Makes `device` current for the lifetime of the guard and restores the
+// calling thread's current device afterwards, so that no entry point leaves a
+// multi-GPU host thread on another GPU.  ok() is false when the switch failed.
+class DeviceGuard {
+ public:
+  explicit DeviceGuard(int device) {
+    if (cudaGetDevice(&prev_) != cudaSuccess) prev_ = -1;
+    if (prev_ != device) {
+      ok_ = cudaSetDevice(device) == cudaSuccess;
+      switched_ = ok_ && prev_ >= 0;
+    }
+  }
+  ~DeviceGuard() {
+    if (switched_) cudaSetDevice(prev_);
+  }
+  bool ok() const { return ok_; }
+  DeviceGuard(const DeviceGuard&) = delete;
+  DeviceGuard& operator=(const DeviceGuard&) = delete;
+
+ private:
+  int prev_ = -1;
+  bool ok_ = true, switched_ = false;
+};
+
+// Entry-point prologue: `dev` current until the enclosing function returns;
+// `fail` is the calling translation unit's error helper.
+#define HDG_ON_DEVICE(ctx, dev)                                                     \
+  ::hdg::DeviceGuard hdg_device_guard_(dev);                                        \
+  if (!hdg_device_guard_.ok()) return fail(ctx, HDG_ECUDA, "cudaSetDevice failed")
 
 constexpr int kMaxP = 4;          // element degrees 1..4
 constexpr int kMaxNt = 60;        // 3 faces x 4 fields x (4 + 1) modes

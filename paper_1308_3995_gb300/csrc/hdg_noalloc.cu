@@ -29,8 +29,9 @@ static __device__ __align__(256) unsigned char g_noalloc_work[kWorkBytes];
 std::mutex g_mu;
 void* g_work_addr[kMaxDevices] = {};
 
-// Device address of the work array on `device`, resolved once per device with
-// that device current.
+// Device address of the work array on `device`, resolved once per device.
+// The caller has made `device` current (DeviceGuard), so the lookup leaves the
+// thread's current device as it found it.
 hdg_status work_address(int device, void** out, std::string* err) {
   if (device < 0 || device >= kMaxDevices) {
     *err = "hdg_condense_noalloc: device ordinal out of range";
@@ -38,9 +39,8 @@ hdg_status work_address(int device, void** out, std::string* err) {
   }
   std::lock_guard<std::mutex> lk(g_mu);
   if (!g_work_addr[device]) {
-    cudaError_t e = cudaSetDevice(device);
     void* p = nullptr;
-    if (e == cudaSuccess) e = cudaGetSymbolAddress(&p, g_noalloc_work);
+    const cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_work);
     if (e != cudaSuccess || !p) {
       *err = std::string("hdg_condense_noalloc: cudaGetSymbolAddress failed: ") + cudaGetErrorString(e);
       return HDG_ECUDA;
@@ -86,6 +86,13 @@ extern "C" hdg_status hdg_condense_noalloc(const hdg_mesh* mesh, const hdg_param
               " bytes of work space, more than the fixed limit of " + std::to_string(kWorkBytes) +
               " bytes (64 MiB); use hdg_sys_create + hdg_condense for it";
     return HDG_EINVAL;
+  }
+  // the mesh's device is current for the memset and the launches; the
+  // caller's current device is restored on every return path
+  hdg::DeviceGuard dg(pr.device);
+  if (!dg.ok()) {
+    *pr.err = "hdg_condense_noalloc: cudaSetDevice failed";
+    return HDG_ECUDA;
   }
   void* base = nullptr;
   hdg_status st = work_address(pr.device, &base, pr.err);

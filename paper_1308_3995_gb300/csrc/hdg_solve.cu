@@ -813,7 +813,7 @@ hdg_status solver_build(hdg_sys* sys, int32_t restart, int32_t precond, void* ws
   if (restart < 1 || restart > kMaxRestart) return fail(ctx, HDG_EINVAL, "hdg_solver_create: restart must be in 1..64");
   if (precond < 0 || precond > 3) return fail(ctx, HDG_EINVAL, "hdg_solver_create: preconditioner kind must be 0..3");
   const hdg_mesh* M = sys->mesh;
-  if (cudaSetDevice(ctx->device) != cudaSuccess) return fail(ctx, HDG_ECUDA, "cudaSetDevice failed");
+  HDG_ON_DEVICE(ctx, ctx->device);
   int sms = 0;
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, ctx->device);
   const SolverPlan P = plan_solver(M, restart, precond, sms);
@@ -962,7 +962,7 @@ int64_t hdg_solver_workspace_bytes(const hdg_mesh* mesh, int32_t restart, int32_
 
 hdg_status hdg_solver_destroy(hdg_solver* S) {
   if (!S) return HDG_EINVAL;
-  cudaSetDevice(S->sys->ctx->device);
+  hdg::DeviceGuard dg(S->sys->ctx->device);
   for (void* p : S->allocs) cudaFree(p);
   if (S->hpin) {
     if (S->hpin_pageable) delete[] S->hpin;
@@ -979,7 +979,7 @@ hdg_status hdg_solver_set_preconditioner(hdg_solver* S, int32_t kind) {
     hdg_ctx* ctx = S->sys->ctx;
     if (S->external_ws)
       return fail(ctx, HDG_ENOMEM, "hdg_solver_set_preconditioner: the caller's workspace was planned without these factors");
-    if (cudaSetDevice(ctx->device) != cudaSuccess) return fail(ctx, HDG_ECUDA, "cudaSetDevice failed");
+    HDG_ON_DEVICE(ctx, ctx->device);
     const size_t vs = need64 ? sizeof(double) : sizeof(float);
     void *F = nullptr, *di = nullptr, *t2 = nullptr;
     if (cudaMalloc(&F, vs * std::max<int64_t>(S->k_vals, 2)) != cudaSuccess) F = nullptr;
@@ -1015,6 +1015,7 @@ hdg_status hdg_solver_setup(hdg_solver* S, void* stream) {
   hdg::NvtxRange nvtx_range_("hdg::solver_setup");
   if (!S) return HDG_EINVAL;
   hdg_ctx* ctx = S->sys->ctx;
+  HDG_ON_DEVICE(ctx, ctx->device);
   cudaStream_t st = (cudaStream_t)stream;
   hdg_status rs;
   if ((rs = setup_enqueue(S, st)) != HDG_OK) return rs;
@@ -1035,6 +1036,7 @@ hdg_status hdg_solver_precond_apply(hdg_solver* S, const double* r, double* z, i
   hdg_ctx* ctx = S->sys->ctx;
   if (!S->factored) return fail(ctx, HDG_EINVAL, "hdg_solver_precond_apply: no preconditioner set up for this kind");
   if (r == S->tmp2 || z == S->tmp2) return HDG_EINVAL;
+  HDG_ON_DEVICE(ctx, ctx->device);
   prec_rhs(S, transpose != 0, r, z, (cudaStream_t)stream);
   return ck(ctx, cudaGetLastError(), "preconditioner apply");
 }
@@ -1048,6 +1050,7 @@ hdg_status hdg_solver_colors(const hdg_solver* S, int32_t* face_color, int32_t* 
 
 hdg_status hdg_trace_matvec(hdg_solver* S, const double* x, double* y, int32_t transpose, void* stream) {
   if (!S || !x || !y) return HDG_EINVAL;
+  HDG_ON_DEVICE(S->sys->ctx, S->sys->ctx->device);
   face_op(S->f, transpose != 0, x, nullptr, y, 2, (cudaStream_t)stream);
   return ck(S->sys->ctx, cudaGetLastError(), "k_face_op");
 }
@@ -1063,6 +1066,7 @@ hdg_status hdg_trace_solve_ex(hdg_solver* S, const double* rhs, int32_t transpos
   if (!S || !x || !(rtol > 0.0) || max_iter < 1) return HDG_EINVAL;
   const bool tr = transpose != 0;
   hdg_ctx* ctx = S->sys->ctx;
+  HDG_ON_DEVICE(ctx, ctx->device);
   cudaStream_t st = (cudaStream_t)stream;
   const int64_t n = S->n;
   const int R = S->restart;
@@ -1172,6 +1176,7 @@ hdg_status hdg_solve_step_host(hdg_sys* sys, hdg_solver* S, const double* U, con
   hdg_ctx* ctx = sys->ctx;
   if (S->sys != sys) return fail(ctx, HDG_EINVAL, "hdg_solve_step_host: the solver belongs to another system");
   if (!U || !Lam || !dU || !dLam) return fail(ctx, HDG_EINVAL, "hdg_solve_step_host: null argument");
+  HDG_ON_DEVICE(ctx, ctx->device);
   const hdg_mesh* M = sys->mesh;
   cudaStream_t st = (cudaStream_t)stream;
   const size_t d = sizeof(double);
@@ -1195,6 +1200,7 @@ hdg_status hdg_solve_step_host(hdg_sys* sys, hdg_solver* S, const double* U, con
 hdg_status hdg_newton_update(hdg_sys* sys, double* U, double* Lam, const double* dU, const double* dLam,
                              void* stream) {
   if (!sys || !U || !Lam || !dU || !dLam) return HDG_EINVAL;
+  HDG_ON_DEVICE(sys->ctx, sys->ctx->device);
   const hdg_mesh* M = sys->mesh;
   int sms = 0;
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, sys->ctx->device);
@@ -1206,6 +1212,7 @@ hdg_status hdg_newton_update(hdg_sys* sys, double* U, double* Lam, const double*
 hdg_status hdg_residual_norm(hdg_sys* sys, double* norm, void* stream) {
   if (!sys || !norm) return HDG_EINVAL;
   hdg_ctx* ctx = sys->ctx;
+  HDG_ON_DEVICE(ctx, ctx->device);
   const hdg_mesh* M = sys->mesh;
   cudaStream_t st = (cudaStream_t)stream;
   int sms = 0;
