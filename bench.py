@@ -33,16 +33,83 @@ sys.path.insert(0, ROOT)
 METRIC = "condensed elements/sec per p; p50/p99 solve latency vs plain FP64 at 1e-10 rel"
 FP64_PEAK_TFLOPS = 1.25     # nominal GB300 binary64 rate (1.255 measured by an FMA-chain microbenchmark)
 L2_FLUSH_BYTES = 256 << 20  # > 129 MB L2
-HBM_PEAK_GBS = 6674.8       # measured copy bandwidth of the GB300s (MEASURED_PEAKS.json)
-# dram__bytes_read.sum + dram__bytes_write.sum per condensation launch from ncu
-# (profiles/), scaled to the full workload by elements; only for unchanged kernels
-TRAFFIC_PER_LAUNCH = {("euler_p3_16k", 0): 12611072 + 522575360}
+FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12   # 80.5: 152 SMs x 128 FP32 lanes x FMA x 2.07 GHz
+HBM_PEAK_GBS = 6778.0       # measured copy bandwidth of the GB300s (MEASURED_PEAKS.json)
+
+# Counters from ncu captures of the condensation kernels (profiles/k_condense_flops_per_element.md and
+# profiles/k_condense_euler_f64_euler_p3.md), valid only while the kernel sources hash to KERNEL_SRC_SHA
+# (kernel_src_sha()); afterwards the bench reports them as stale (null) instead of quoting old numbers.
+KERNEL_SRC_FILES = ("hdg_kernels.cu", "hdg_ns.cuh", "hdg_ns.cu", "hdg_ns_ff.cu", "hdg_lu.cuh", "hdg_arith.cuh",
+                    "hdg_physics.cuh", "hdg_internal.h")
+KERNEL_SRC_SHA = "3bdced85fe84ffcb"
+# executed floating-point work per element, (binary64 flops, binary32 flops): 2 DFMA + DADD + DMUL and
+# 2 FFMA + FADD + FMUL from the SASS instruction counters (no paired FFMA2/FADD2/FMUL2 were issued),
+# one launch of each kernel on a 1,024-triangle uniform-degree periodic mesh (bench.py --profile-variants)
+EXEC_FLOPS_PER_ELEM = {
+    ("euler", 1, 0): (28856, 0), ("euler", 1, 1): (1050, 225596),
+    ("euler", 2, 0): (115375, 0), ("euler", 2, 1): (894, 905360),
+    ("euler", 3, 0): (369117, 0), ("euler", 3, 1): (1102, 2881454),
+    ("euler", 4, 0): (997455, 0), ("euler", 4, 1): (1134, 7737784),
+    ("ns", 1, 0): (99055, 0), ("ns", 1, 1): (2055, 924634),
+    ("ns", 2, 0): (394331, 0), ("ns", 2, 1): (2235, 3395648),
+    ("ns", 3, 0): (1231919, 0), ("ns", 3, 1): (1601, 10179794),
+    ("ns", 4, 0): (3228811, 0), ("ns", 4, 1): (1901, 26052176)}
+# dram__bytes_read.sum + dram__bytes_write.sum of one full-size condensation launch (1-pass capture)
+TRAFFIC_PER_LAUNCH = {("euler_p3_16k", 0): 12024832 + 522256640}
+
+
+def kernel_src_sha() -> str:
+    import hashlib
+    h = hashlib.sha256()
+    for f in KERNEL_SRC_FILES:
+        h.update(f.encode())
+        with open(os.path.join(ROOT, "paper_1308_3995_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def counters_current() -> bool:
+    return kernel_src_sha() == KERNEL_SRC_SHA
 
 
 def dense_condensation_flops(n: int, nt: int) -> float:
-    """Algorithmic FP64 flops of one element's dense condensation:
-    LU 2/3 n^3, local solves 2 n^2 (nt+1), Schur 2 nt^2 n, condensed RHS 2 nt n."""
+    """Flops of one element's condensation written densely (no structure used):
+    LU 2/3 n^3, local solves 2 n^2 (nt+1), Schur 2 nt^2 n, condensed RHS 2 nt n.
+    Context only: the kernels exploit the method's block structure, see below."""
     return 2.0 / 3.0 * n ** 3 + 2.0 * n * n * (nt + 1) + 2.0 * nt * nt * n + 2.0 * nt * n
+
+
+def condensation_flops(nfield: int, p: int, nt: int) -> float:
+    """Flops of one element's condensation (Sec. 3.4) as the method's structure
+    makes it, counting multiply and add separately (an FMA is 2).
+
+    Euler (n = 4 n_p): LU of A_K 2/3 n^3; local solves X = A_K^{-1}[B | F]
+    2 n^2 (nt+1); Schur S = D - C X_B and E = H - C X_F with C = alpha <psi, phi>
+    per field, so a trace row has n_p non-zeros: 2 nt (nt+1) n_p.
+
+    Navier-Stokes (n = 12 n_p, q eliminated inside the element with the pivot
+    block det J * I; m = 4 n_p; A_wq and C_q have zero rows for the mass field,
+    A_qw, B_q and C_w couple a field only to itself):
+      A' = A_ww - A_wq A_qw / det            2 (3 n_p)(4 n_p)(2 n_p)
+      R'_w = R_w - A_wq [B_q | F_q] / det    2 (3 n_p) nt (2 n_p) + 2 (3 n_p)(8 n_p)
+      LU of A' and solves                    2/3 m^3 + 2 m^2 (nt+1)
+      X_q = (R_q - A_qw X_w) / det           2 (8 n_p)(nt+1) n_p
+      C' = C_w - C_q A_qw / det              2 (3 nt/4)(4 n_p)(2 n_p)
+      S = D - C_q B_q / det - C' X_w,B       2 (3 nt/4) nt (2 n_p) + 2 nt m nt
+      E = H - C_q F_q / det - C' X_w,F       2 (3 nt/4)(8 n_p) + 2 nt m"""
+    npb = (p + 1) * (p + 2) // 2
+    if nfield == 4:
+        n = 4 * npb
+        return 2.0 / 3.0 * n ** 3 + 2.0 * n * n * (nt + 1) + 2.0 * nt * (nt + 1) * npb
+    m = 4 * npb
+    f = 2.0 * (3 * npb) * (4 * npb) * (2 * npb)
+    f += 2.0 * (3 * npb) * nt * (2 * npb) + 2.0 * (3 * npb) * (8 * npb)
+    f += 2.0 / 3.0 * m ** 3 + 2.0 * m * m * (nt + 1)
+    f += 2.0 * (8 * npb) * (nt + 1) * npb
+    f += 2.0 * (0.75 * nt) * (4 * npb) * (2 * npb)
+    f += 2.0 * (0.75 * nt) * nt * (2 * npb) + 2.0 * nt * m * nt
+    f += 2.0 * (0.75 * nt) * (8 * npb) + 2.0 * nt * m
+    return f
 
 
 def algorithmic_bytes(n: int, nt: int) -> float:
@@ -302,14 +369,31 @@ class Measured:
         return self.mesh.n_elem
 
     def algorithmic(self):
+        """Per launch: the condensation algebra in flops (condensation_flops), the FP64 HBM bytes, and
+        the executed flops of the kernel's own pipe from the ncu instruction counts (None when the
+        kernel sources changed since the counters were taken).  Elements whose trace is longer than a
+        uniform-degree element's (p_e = max on mixed meshes) get the uniform-degree count scaled by the
+        ratio of their condensation algebra (marked 'scaled')."""
         from collections import Counter
         m, c = self.mesh, self.case
         nts = Counter()
         for K in range(m.n_elem):
-            nts[(int(m.elem_p[K]), int(sum(4 * (m.face_p[e] + 1) for e in m.elem_face[K])))] += 1
-        fl = sum(k * dense_condensation_flops(c.nfield * (p + 1) * (p + 2) // 2, nt) for (p, nt), k in nts.items())
+            nts[(int(m.elem_p[K]), int(sum(4 * (m.face_p[e] + 1) for e in m.elem_face[K] if e >= 0)))] += 1
+        fl = sum(k * condensation_flops(c.nfield, p, nt) for (p, nt), k in nts.items())
         by = sum(k * algorithmic_bytes(c.nfield * (p + 1) * (p + 2) // 2, nt) for (p, nt), k in nts.items())
-        return fl, by
+        model = "euler" if c.nfield == 4 else "ns"
+        prec = 0 if self.precision == 0 else 1
+        ex, scaled = None, False
+        if counters_current() and self.prm.sc_eps0 <= 0.0:
+            ex = 0.0
+            for (p, nt), k in nts.items():
+                per = EXEC_FLOPS_PER_ELEM[(model, p, prec)][prec]
+                nt_u = 12 * (p + 1)
+                if nt != nt_u:
+                    per *= condensation_flops(c.nfield, p, nt) / condensation_flops(c.nfield, p, nt_u)
+                    scaled = True
+                ex += k * per
+        return fl, by, ex, scaled
 
     def summary(self):
         tot = sum(self.step_ms)
@@ -318,14 +402,23 @@ class Measured:
         def pct(q):
             return lat[min(len(lat) - 1, max(0, int(math.ceil(q / 100.0 * len(lat))) - 1))]
         p99 = pct(99)
-        fl, by = self.algorithmic()
+        fl, by, ex, scaled = self.algorithmic()
         cond_s = statistics.mean(self.cond_ms) * 1e-3
+        pipe, peak = ("fp64", FP64_PEAK_TFLOPS) if self.precision == 0 else ("fp32", FP32_PEAK_TFLOPS)
+        work = {"condensation_algebra_gflop_per_launch": fl / 1e9,
+                "condensation_algebra_tflops": fl / cond_s / 1e12,
+                "executed_gflop_per_launch": None if ex is None else ex / 1e9,
+                "executed_tflops": None if ex is None else ex / cond_s / 1e12,
+                "pipe": pipe, "pipe_peak_tflops": peak,
+                "pipe_frac": None if ex is None else ex / cond_s / 1e12 / peak,
+                "counters": ("stale: kernel sources changed since the ncu counts" if not counters_current() else
+                             "n/a with shock capturing" if self.prm.sc_eps0 > 0.0 else
+                             "scaled from uniform-degree counts" if scaled else "ncu instruction counts")}
         return {"elements_per_s": self.n_elem * len(self.step_ms) / (tot * 1e-3), "ms_per_step": tot / len(lat),
                 "p50_step_ms": lat[len(lat) // 2], "p10_step_ms": pct(10), "p90_step_ms": pct(90),
                 "p99_step_ms": p99, "condense_ms": 1e3 * cond_s,
                 "recover_ms": statistics.mean(self.rec_ms), "elem_status_nonzero": self.status_bad,
-                "fp64_equiv_tflops": fl / cond_s / 1e12, "algorithmic_gflop_per_launch": fl / 1e9,
-                "algorithmic_mb_per_launch": by / 1e6,
+                "work": work, "algorithmic_mb_per_launch": by / 1e6,
                 "launch_shapes": {str(p): ("one CTA per element" if v == 0 else f"persistent, {v} CTAs/SM")
                                   for p, v in self.shapes.items()},
                 **({"buckets_in_last_step": {
@@ -601,15 +694,28 @@ def run_ours(args, wl, ws, rank, local):
     h2d = 8 * (main_m.mesh.u_len + 2 * main_m.mesh.lam_len)
     d2h = 8 * main_m.mesh.u_len
 
-    # roofline of the dominant kernel (condensation), FP64 pipe
-    fl, by = main_m.algorithmic()
+    # roofline of the dominant kernel (condensation): bound by its arithmetic pipe
+    fl, by, ex, _ = main_m.algorithmic()
     cond_s = summ["condense_ms"] * 1e-3
-    achieved = fl / cond_s / 1e12
-    roof = {"bound": "alu", "achieved": achieved, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
-            "frac": achieved / FP64_PEAK_TFLOPS, "traffic": TRAFFIC_PER_LAUNCH.get((wl.name, args.precision)),
-            "kernel": "k_condense_euler<3, double> (FP64 pipe)", "algorithmic_flops_per_launch": fl,
+    peak = FP64_PEAK_TFLOPS if args.precision == 0 else FP32_PEAK_TFLOPS
+    work = ex if ex is not None else fl
+    achieved = work / cond_s / 1e12
+    fresh = counters_current()
+    roof = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
+            "traffic": TRAFFIC_PER_LAUNCH.get((wl.name, args.precision)) if fresh else None,
+            "kernel": f"k_condense_{'euler' if wl.model == 0 else 'ns'} "
+                      f"({'binary64 on the FP64 pipe' if args.precision == 0 else 'float-float on the FP32 pipe'})",
+            "flops_counted": ("executed flops of the kernel (ncu instruction counts per element x elements): "
+                              "the condensation algebra plus the quadrature assembly" if ex is not None else
+                              "condensation algebra only (instruction counts stale or unavailable)"),
+            "flops_per_launch": work, "condensation_algebra_flops_per_launch": fl,
+            "algebra_only_frac": fl / cond_s / 1e12 / peak if args.precision == 0 else None,
             "algorithmic_bytes_per_launch": by, "launch_ms": 1e3 * cond_s, "achieved_hbm_gbs": by / cond_s / 1e9,
-            "peak_note": "FP64 1.25 TFLOP/s nominal; 1.255 measured by an FMA-chain microbenchmark"}
+            "hbm_frac": by / cond_s / 1e9 / HBM_PEAK_GBS,
+            "peak_note": ("FP64 1.25 TFLOP/s nominal (1.255 measured by an FMA-chain microbenchmark)"
+                          if args.precision == 0 else
+                          "FP32 80.5 TFLOP/s from unit counts (152 SMs x 128 lanes x FMA x 2.07 GHz); "
+                          "73.5 measured by an FMA-chain microbenchmark")}
     extra = {"precision": "fp64" if args.precision == 0 else "float-float", "sc_eps0": args.sc_eps0,
              "launch_shapes": summ["launch_shapes"]}
     extra.update({k: summ[k] for k in ("p50_step_ms", "p10_step_ms", "p90_step_ms", "p99_step_ms", "condense_ms",
@@ -642,12 +748,28 @@ def run_ours(args, wl, ws, rank, local):
             row = {}
             for prec, nm in ((hdg.HDG_FP64, "fp64"), (hdg.HDG_FLOAT2, "float2")):
                 mp = Measured(ctx, wp, prec, dev, flush).run(5, 2, stream)
-                row[nm] = mp.summary()["elements_per_s"]
+                sm = mp.summary()
+                row[nm] = sm["elements_per_s"]
+                row[f"{nm}_pipe_frac"] = sm["work"]["pipe_frac"]
                 if check:
                     acc[f"{wp.name}_{nm}"] = oracle_accuracy(mp)
                 mp.close()
             per_p[str(p)] = row
         line["elements_per_s_per_p"] = per_p
+        # Navier-Stokes mixed form per degree (uniform p, 16,384 triangles): elements/s and pipe fraction
+        ns_per_p = {}
+        for p in (1, 2, 3, 4):
+            wp = G.small_variant(G.WORKLOADS["ns_mixp_65k"], 64, 128, p=p, probs=None, name=f"ns_p{p}_16k")
+            row = {}
+            for prec, nm in ((hdg.HDG_FP64, "fp64"), (hdg.HDG_FLOAT2, "float2")):
+                mp = Measured(ctx, wp, prec, dev, flush).run(3, 1, stream)
+                sm = mp.summary()
+                row[nm] = sm["elements_per_s"]
+                row[f"{nm}_pipe_frac"] = sm["work"]["pipe_frac"]
+                row[f"{nm}_algebra_tflops"] = sm["work"]["condensation_algebra_tflops"]
+                mp.close()
+            ns_per_p[str(p)] = row
+        line["ns_elements_per_s_per_p"] = ns_per_p
         # Navier-Stokes mixed form, degree mix 40/30/20/10 % (65,536 triangles)
         ns = {}
         for prec, nm in ((hdg.HDG_FP64, "fp64"), (hdg.HDG_FLOAT2, "float2")):
@@ -702,6 +824,43 @@ def run_ours(args, wl, ws, rank, local):
     return 0
 
 
+# ----------------------------------------------------------------------------- profiling driver
+PROFILE_VARIANTS = [("euler", p, prec) for p in (1, 2, 3, 4) for prec in (0, 1)] + \
+                   [("ns", p, prec) for p in (1, 2, 3, 4) for prec in (0, 1)]
+
+
+def run_profile_variants(args):
+    """One condensation launch of every element kernel (Euler and Navier-Stokes, p = 1..4, binary64 and
+    float-float), each on a small uniform-degree periodic mesh (args.cells, default 16x32 cells: 1,024
+    triangles), in PROFILE_VARIANTS order and without autotuning or warm-up: the command that the
+    instruction-count capture (ncu -k regex:k_condense) runs.  Prints the launch order as one JSON line."""
+    import torch
+
+    from paper_1308_3995_gb300 import hdg
+    from paper_1308_3995_gb300 import inputs as G
+    dev = torch.device("cuda:0")
+    ctx = hdg.Context(0)
+    nx, ny = (int(v) for v in (args.cells or "16x32").lower().split("x"))
+    order = []
+    for model, p, prec in PROFILE_VARIANTS:
+        base = G.WORKLOADS["euler_p3_16k" if model == "euler" else "ns_mixp_65k"]
+        wl = G.small_variant(base, nx, ny, p=p, probs=None)
+        c = G.make_case(wl)
+        mesh = hdg.Mesh(ctx, c.mesh.elem_xy, c.mesh.elem_vid, c.elem_p, c.nfield, c.mesh.elem_bc)
+        U, Lam, _ = G.case_state(c, mesh.face_vid, mesh.face_p)
+        prm = hdg.Params(model=wl.model, precision=prec, mach=wl.mach, alpha=wl.alpha, reynolds=wl.reynolds,
+                         prandtl=wl.prandtl, aoa=wl.aoa)
+        sysm = hdg.System(ctx, mesh, prm)
+        sysm.condense(torch.from_numpy(U).to(dev), torch.from_numpy(Lam).to(dev))
+        torch.cuda.synchronize()
+        order.append({"model": model, "p": p, "precision": prec, "elements": mesh.n_elem,
+                      "launches": sysm.launches})
+        sysm.close()
+        mesh.close()
+    print(json.dumps({"profile_variants": order}), flush=True)
+    return 0
+
+
 def main(argv=None):
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -721,7 +880,11 @@ def main(argv=None):
     ap.add_argument("--serving-only", action="store_true", help="run only the serving section")
     ap.add_argument("--solve-only", action="store_true", help="run only the trace-solve section")
     ap.add_argument("--no-autotune", action="store_true", help="default launch shapes (no hdg_autotune)")
+    ap.add_argument("--profile-variants", action="store_true",
+                    help="one launch of every element kernel on a small mesh (instruction-count capture)")
     args = ap.parse_args(argv)
+    if args.profile_variants:
+        return run_profile_variants(args)
     from paper_1308_3995_gb300 import inputs as G
     wl = G.WORKLOADS[args.workload]
     if args.cells:

@@ -29,13 +29,18 @@ _c_i32_p = ctypes.POINTER(ctypes.c_int32)
 _c_i64_p = ctypes.POINTER(ctypes.c_int64)
 
 
+_LIBX = os.path.join(_HERE, "liboracle_ext.so")
+
+
 def build(force: bool = False) -> str:
-    """Compile the oracle with g++ (plain C++17, no FMA contraction)."""
-    if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < os.path.getmtime(_SRC):
-        tmp = _LIB + f".tmp{os.getpid()}"
-        subprocess.check_call(["g++", "-O2", "-std=c++17", "-ffp-contract=off", "-fPIC", "-shared",
-                               "-pthread", "-o", tmp, _SRC])
-        os.replace(tmp, _LIB)
+    """Compile the oracle with g++ (plain C++17, no FMA contraction): the binary64
+    build, and the same source in long double (``-DORC_EXTENDED``)."""
+    for lib_path, extra in ((_LIB, []), (_LIBX, ["-DORC_EXTENDED"])):
+        if force or not os.path.exists(lib_path) or os.path.getmtime(lib_path) < os.path.getmtime(_SRC):
+            tmp = lib_path + f".tmp{os.getpid()}"
+            subprocess.check_call(["g++", "-O2", "-std=c++17", "-ffp-contract=off", "-fPIC", "-shared",
+                                   "-pthread", *extra, "-o", tmp, _SRC])
+            os.replace(tmp, lib_path)
     return _LIB
 
 
@@ -452,3 +457,73 @@ def block_ilu0_apply(L, U, perm, r, transpose=False):
     z = np.empty_like(zp)
     z[perm] = zp
     return z
+
+
+# --------------------------------------------------------------------------- extended precision
+_libx = None
+
+
+def libx():
+    """The oracle compiled in long double (80-bit extended on x86-64, binary128 on aarch64)."""
+    global _libx
+    if _libx is None:
+        build()
+        L = ctypes.CDLL(_LIBX)
+        L.orc_mesh_create.argtypes = [ctypes.c_int, ctypes.c_int, _c_double_p, _c_i32_p,
+                                      ctypes.POINTER(ctypes.c_int8), ctypes.POINTER(ctypes.c_int8),
+                                      ctypes.POINTER(ctypes.c_void_p)]
+        L.orc_mesh_destroy.argtypes = [ctypes.c_void_p]
+        L.orc_mesh_destroy.restype = None
+        P = ctypes.POINTER(OrcParams)
+        L.orcx_element_condense.argtypes = [ctypes.c_void_p, P, ctypes.c_int] + [_c_double_p] * 7
+        L.orcx_face_E.argtypes = [ctypes.c_void_p, P, ctypes.c_int, _c_double_p, _c_double_p, _c_double_p]
+        L.orcx_mantissa_bits.argtypes = []
+        _libx = L
+    return _libx
+
+
+def mantissa_bits_ext() -> int:
+    return int(libx().orcx_mantissa_bits())
+
+
+class ExtMesh:
+    """The same mesh in the extended-precision build: the definition evaluated in long double
+    (tables, geometry, residual, complex-step Jacobian, LU, Schur), inputs and results binary64.
+    Sizes and layouts are those of ``Mesh`` on the same arrays."""
+
+    def __init__(self, mesh: Mesh):
+        self.m = mesh
+        bc = mesh.elem_bc
+        h = ctypes.c_void_p()
+        st = libx().orc_mesh_create(mesh.n_elem, mesh.nfield, _d(mesh.elem_xy), _i32(mesh.elem_vid),
+                                    np.ascontiguousarray(mesh.elem_p, dtype=np.int8).ctypes.data_as(
+                                        ctypes.POINTER(ctypes.c_int8)),
+                                    bc.ctypes.data_as(ctypes.POINTER(ctypes.c_int8)) if bc is not None else None,
+                                    ctypes.byref(h))
+        if st != 0:
+            raise ValueError(f"extended oracle rejected the mesh (status {st})")
+        self._h = h
+
+    def __del__(self):
+        h = getattr(self, "_h", None)
+        if h is not None and _libx is not None:
+            _libx.orc_mesh_destroy(h)
+            self._h = None
+
+    def element_condense(self, params, K, U, Lam, dLam):
+        """X [n, nt+1] (row-major, X_F last), S [nt, nt], E_K [nt] and dU_K = X_F - X_B dLam_K [n]."""
+        n, nt = self.m.n(K), self.m.nt(K)
+        X, S, E, dU = np.zeros((n, nt + 1)), np.zeros((nt, nt)), np.zeros(nt), np.zeros(n)
+        P = params.c()
+        st = libx().orcx_element_condense(self._h, ctypes.byref(P), int(K), _d(_f64(U)), _d(_f64(Lam)),
+                                          _d(_f64(dLam)), _d(X), _d(S), _d(E), _d(dU))
+        return X, S, E, dU, st
+
+    def face_E(self, params, f, U, Lam):
+        """Assembled E of face f (both sides' contributions summed in long double)."""
+        out = np.zeros(4 * (int(self.m.face_p[f]) + 1))
+        P = params.c()
+        st = libx().orcx_face_E(self._h, ctypes.byref(P), int(f), _d(_f64(U)), _d(_f64(Lam)), _d(out))
+        if st != 0:
+            raise ValueError(f"extended oracle: status {st} on face {f}")
+        return out

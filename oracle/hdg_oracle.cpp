@@ -42,11 +42,23 @@
 #include <complex>
 #include <cstdint>
 #include <cstring>
+#include <limits>
 #include <mutex>
 #include <thread>
 #include <vector>
 
-typedef std::complex<double> cplx;
+// Scalar type of the arithmetic.  The default build computes in binary64.  The
+// same source compiled with -DORC_EXTENDED computes in long double (80-bit
+// extended on x86-64, binary128 on aarch64): a higher-precision evaluation of
+// the same definition, used to measure the rounding error of binary64 results.
+#ifdef ORC_EXTENDED
+typedef long double real;
+#define RLIT(x) x##L
+#else
+typedef double real;
+#define RLIT(x) x
+#endif
+typedef std::complex<real> cplx;
 
 extern "C" {
 typedef struct {
@@ -70,35 +82,41 @@ typedef struct {
 // of the symmetric tridiagonal Jacobi matrix of the orthogonal polynomials,
 // the weights mu0 * (first eigenvector component)^2.
 // ---------------------------------------------------------------------------
-static void sym_eig_jacobi(int n, std::vector<double>& a, std::vector<double>& v) {
+// squared off-diagonal norm at which the Jacobi iteration stops
+#ifdef ORC_EXTENDED
+static const real kJacobiOffTol = 1e-70L;
+#else
+static const real kJacobiOffTol = 1e-34;
+#endif
+static void sym_eig_jacobi(int n, std::vector<real>& a, std::vector<real>& v) {
   // cyclic Jacobi rotations on a symmetric n x n row-major matrix a;
   // on exit the diagonal holds eigenvalues and the columns of v eigenvectors.
   v.assign(n * n, 0.0);
   for (int i = 0; i < n; ++i) v[i * n + i] = 1.0;
   for (int sweep = 0; sweep < 100; ++sweep) {
-    double off = 0.0;
+    real off = 0.0;
     for (int i = 0; i < n; ++i)
       for (int j = i + 1; j < n; ++j) off += a[i * n + j] * a[i * n + j];
-    if (off < 1e-34) break;
+    if (off < kJacobiOffTol) break;
     for (int p = 0; p < n; ++p)
       for (int q = p + 1; q < n; ++q) {
-        double apq = a[p * n + q];
+        real apq = a[p * n + q];
         if (std::fabs(apq) < 1e-300) continue;
-        double theta = (a[q * n + q] - a[p * n + p]) / (2.0 * apq);
-        double t = (theta >= 0 ? 1.0 : -1.0) / (std::fabs(theta) + std::sqrt(theta * theta + 1.0));
-        double c = 1.0 / std::sqrt(t * t + 1.0), s = t * c;
+        real theta = (a[q * n + q] - a[p * n + p]) / (2.0 * apq);
+        real t = (theta >= 0 ? 1.0 : -1.0) / (std::fabs(theta) + std::sqrt(theta * theta + 1.0));
+        real c = 1.0 / std::sqrt(t * t + 1.0), s = t * c;
         for (int k = 0; k < n; ++k) {  // columns p, q
-          double akp = a[k * n + p], akq = a[k * n + q];
+          real akp = a[k * n + p], akq = a[k * n + q];
           a[k * n + p] = c * akp - s * akq;
           a[k * n + q] = s * akp + c * akq;
         }
         for (int k = 0; k < n; ++k) {  // rows p, q
-          double apk = a[p * n + k], aqk = a[q * n + k];
+          real apk = a[p * n + k], aqk = a[q * n + k];
           a[p * n + k] = c * apk - s * aqk;
           a[q * n + k] = s * apk + c * aqk;
         }
         for (int k = 0; k < n; ++k) {
-          double vkp = v[k * n + p], vkq = v[k * n + q];
+          real vkp = v[k * n + p], vkq = v[k * n + q];
           v[k * n + p] = c * vkp - s * vkq;
           v[k * n + q] = s * vkp + c * vkq;
         }
@@ -107,22 +125,22 @@ static void sym_eig_jacobi(int n, std::vector<double>& a, std::vector<double>& v
 }
 
 // n-point Gauss-Jacobi rule for weight (1-x)^al (1+x)^be on [-1,1], ascending nodes.
-static void gauss_jacobi(int n, double al, double be, double* x, double* w) {
-  std::vector<double> J(n * n, 0.0), V;
+static void gauss_jacobi(int n, real al, real be, real* x, real* w) {
+  std::vector<real> J(n * n, 0.0), V;
   for (int k = 0; k < n; ++k) {
-    double s = 2.0 * k + al + be;
+    real s = 2.0 * k + al + be;
     J[k * n + k] = (k == 0) ? (be - al) / (al + be + 2.0) : (be * be - al * al) / (s * (s + 2.0));
     if (k >= 1) {
-      double kk = k;
-      double num = 4.0 * kk * (kk + al) * (kk + be) * (kk + al + be);
-      double den = s * s * (s + 1.0) * (s - 1.0);
+      real kk = k;
+      real num = 4.0 * kk * (kk + al) * (kk + be) * (kk + al + be);
+      real den = s * s * (s + 1.0) * (s - 1.0);
       J[k * n + k - 1] = J[(k - 1) * n + k] = std::sqrt(num / den);
     }
   }
   sym_eig_jacobi(n, J, V);
-  double mu0 = std::pow(2.0, al + be + 1.0) * std::tgamma(al + 1.0) * std::tgamma(be + 1.0) /
+  real mu0 = std::pow(2.0, al + be + 1.0) * std::tgamma(al + 1.0) * std::tgamma(be + 1.0) /
                std::tgamma(al + be + 2.0);
-  std::vector<std::pair<double, double>> xw(n);
+  std::vector<std::pair<real, real>> xw(n);
   for (int k = 0; k < n; ++k) xw[k] = {J[k * n + k], mu0 * V[0 * n + k] * V[0 * n + k]};
   std::sort(xw.begin(), xw.end());
   for (int k = 0; k < n; ++k) { x[k] = xw[k].first; w[k] = xw[k].second; }
@@ -132,20 +150,20 @@ static void gauss_jacobi(int n, double al, double be, double* x, double* w) {
 // Jacobi polynomials P_n^{(a,b)}(x) by the three-term recurrence, and their
 // derivative d/dx P_n^{(a,b)} = (n+a+b+1)/2 P_{n-1}^{(a+1,b+1)}.
 // ---------------------------------------------------------------------------
-static double jacobi_p(int n, double a, double b, double x) {
+static real jacobi_p(int n, real a, real b, real x) {
   if (n == 0) return 1.0;
-  double p0 = 1.0, p1 = (a + 1.0) + (a + b + 2.0) * (x - 1.0) / 2.0;
+  real p0 = 1.0, p1 = (a + 1.0) + (a + b + 2.0) * (x - 1.0) / 2.0;
   for (int m = 2; m <= n; ++m) {
-    double c = 2.0 * m + a + b;
-    double a1 = 2.0 * m * (m + a + b) * (c - 2.0);
-    double a2 = (c - 1.0) * (c * (c - 2.0) * x + a * a - b * b);
-    double a3 = 2.0 * (m + a - 1.0) * (m + b - 1.0) * c;
-    double p2 = (a2 * p1 - a3 * p0) / a1;
+    real c = 2.0 * m + a + b;
+    real a1 = 2.0 * m * (m + a + b) * (c - 2.0);
+    real a2 = (c - 1.0) * (c * (c - 2.0) * x + a * a - b * b);
+    real a3 = 2.0 * (m + a - 1.0) * (m + b - 1.0) * c;
+    real p2 = (a2 * p1 - a3 * p0) / a1;
     p0 = p1; p1 = p2;
   }
   return p1;
 }
-static double jacobi_dp(int n, double a, double b, double x) {
+static real jacobi_dp(int n, real a, real b, real x) {
   if (n == 0) return 0.0;
   return 0.5 * (n + a + b + 1.0) * jacobi_p(n - 1, a + 1.0, b + 1.0, x);
 }
@@ -157,27 +175,27 @@ static inline int n_basis(int p) { return (p + 1) * (p + 2) / 2; }
 //   a = 2 xi/(1-eta) - 1, b = 2 eta - 1, c_ij = sqrt(2 (2i+1)(i+j+1)),
 // ordered k = 0..p, j = 0..k, i = k-j.  Gradients by the chain rule through
 // the collapsed coordinates (valid for eta < 1, i.e. away from vertex (0,1)).
-static void dubiner(int p, double xi, double eta, double* phi, double* dxi, double* deta) {
-  double om = 1.0 - eta;           // (1-b)/2
-  double a = 2.0 * xi / om - 1.0;  // collapsed coordinate
-  double b = 2.0 * eta - 1.0;
+static void dubiner(int p, real xi, real eta, real* phi, real* dxi, real* deta) {
+  real om = 1.0 - eta;           // (1-b)/2
+  real a = 2.0 * xi / om - 1.0;  // collapsed coordinate
+  real b = 2.0 * eta - 1.0;
   int m = 0;
   for (int k = 0; k <= p; ++k)
     for (int j = 0; j <= k; ++j) {
       int i = k - j;
-      double c = std::sqrt(2.0 * (2 * i + 1) * (i + j + 1));
-      double Pa = jacobi_p(i, 0, 0, a), dPa = jacobi_dp(i, 0, 0, a);
-      double Pb = jacobi_p(j, 2 * i + 1, 0, b), dPb = jacobi_dp(j, 2 * i + 1, 0, b);
-      double omi = std::pow(om, i);
+      real c = std::sqrt(2.0 * (2 * i + 1) * (i + j + 1));
+      real Pa = jacobi_p(i, 0, 0, a), dPa = jacobi_dp(i, 0, 0, a);
+      real Pb = jacobi_p(j, 2 * i + 1, 0, b), dPb = jacobi_dp(j, 2 * i + 1, 0, b);
+      real omi = std::pow(om, i);
       phi[m] = c * Pa * omi * Pb;
       if (dxi) {
         // d/dxi: da/dxi = 2/(1-eta)
-        double omi1 = (i >= 1) ? std::pow(om, i - 1) : 0.0;
+        real omi1 = (i >= 1) ? std::pow(om, i - 1) : 0.0;
         dxi[m] = c * dPa * 2.0 * omi1 * Pb;
         // d/deta: da/deta = (1+a)/(1-eta); d(om^i)/deta = -i om^(i-1); db/deta = 2
-        double t1 = (i >= 1) ? dPa * (1.0 + a) * omi1 * Pb : 0.0;
-        double t2 = (i >= 1) ? -Pa * i * omi1 * Pb : 0.0;
-        double t3 = Pa * omi * dPb * 2.0;
+        real t1 = (i >= 1) ? dPa * (1.0 + a) * omi1 * Pb : 0.0;
+        real t2 = (i >= 1) ? -Pa * i * omi1 * Pb : 0.0;
+        real t3 = Pa * omi * dPb * 2.0;
         deta[m] = c * (t1 + t2 + t3);
       }
       ++m;
@@ -185,13 +203,13 @@ static void dubiner(int p, double xi, double eta, double* phi, double* dxi, doub
 }
 
 // Orthonormal Legendre trace basis on [0,1]: psi_k(s) = sqrt(2k+1) P_k(2s-1).
-static void legendre01(int pe, double s, double* psi) {
+static void legendre01(int pe, real s, real* psi) {
   for (int k = 0; k <= pe; ++k) psi[k] = std::sqrt(2.0 * k + 1.0) * jacobi_p(k, 0, 0, 2.0 * s - 1.0);
 }
 
 // Reference point on local face lf at local parameter t (face lf runs from
 // local vertex lf to lf+1 mod 3).
-static void face_point(int lf, double t, double* xi, double* eta) {
+static void face_point(int lf, real t, real* xi, real* eta) {
   if (lf == 0) { *xi = t; *eta = 0.0; }
   else if (lf == 1) { *xi = 1.0 - t; *eta = t; }
   else { *xi = 0.0; *eta = 1.0 - t; }
@@ -202,20 +220,20 @@ static void face_point(int lf, double t, double* xi, double* eta) {
 // ---------------------------------------------------------------------------
 struct VolTab {
   int p = 0, np = 0, nq = 0;
-  std::vector<double> w, phi, dxi, deta;  // [nq], [nq][np]
+  std::vector<real> w, phi, dxi, deta;  // [nq], [nq][np]
 };
 struct EdgeTab {  // element degree p, edge degree pe
   int np = 0, nk = 0, ne = 0;
-  std::vector<double> s, w, psi;          // [ne], [ne], [ne][nk]
-  std::vector<double> phi[3][2];          // [lf][flip] -> [ne][np]
+  std::vector<real> s, w, psi;          // [ne], [ne], [ne][nk]
+  std::vector<real> phi[3][2];          // [lf][flip] -> [ne][np]
 };
 static VolTab g_vol[6];
 static EdgeTab g_edge[6][6];
 static std::once_flag g_once;
 
-static void tri_rule(int p, std::vector<double>& xi, std::vector<double>& eta, std::vector<double>& w) {
+static void tri_rule(int p, std::vector<real>& xi, std::vector<real>& eta, std::vector<real>& w) {
   int n = p + 2;
-  std::vector<double> xa(n), wa(n), xb(n), wb(n);
+  std::vector<real> xa(n), wa(n), xb(n), wb(n);
   gauss_jacobi(n, 0.0, 0.0, xa.data(), wa.data());
   gauss_jacobi(n, 1.0, 0.0, xb.data(), wb.data());
   xi.clear(); eta.clear(); w.clear();
@@ -226,9 +244,9 @@ static void tri_rule(int p, std::vector<double>& xi, std::vector<double>& eta, s
       w.push_back(wa[i] * wb[j] / 8.0);
     }
 }
-static void edge_rule(int pe, std::vector<double>& s, std::vector<double>& w) {
+static void edge_rule(int pe, std::vector<real>& s, std::vector<real>& w) {
   int n = pe + 2;
-  std::vector<double> x(n), wx(n);
+  std::vector<real> x(n), wx(n);
   gauss_jacobi(n, 0.0, 0.0, x.data(), wx.data());
   s.resize(n); w.resize(n);
   for (int i = 0; i < n; ++i) { s[i] = (1.0 + x[i]) / 2.0; w[i] = wx[i] / 2.0; }
@@ -237,7 +255,7 @@ static void edge_rule(int pe, std::vector<double>& s, std::vector<double>& w) {
 static void init_tables() {
   for (int p = 1; p <= 5; ++p) {
     VolTab& V = g_vol[p];
-    std::vector<double> xi, eta;
+    std::vector<real> xi, eta;
     tri_rule(p, xi, eta, V.w);
     V.p = p; V.np = n_basis(p); V.nq = (int)V.w.size();
     V.phi.resize(V.nq * V.np); V.dxi.resize(V.nq * V.np); V.deta.resize(V.nq * V.np);
@@ -256,7 +274,7 @@ static void init_tables() {
         for (int fl = 0; fl < 2; ++fl) {
           E.phi[lf][fl].resize(E.ne * E.np);
           for (int g = 0; g < E.ne; ++g) {
-            double t = fl ? 1.0 - E.s[g] : E.s[g], xi, eta;
+            real t = fl ? 1.0 - E.s[g] : E.s[g], xi, eta;
             face_point(lf, t, &xi, &eta);
             dubiner(p, xi, eta, &E.phi[lf][fl][g * E.np], nullptr, nullptr);
           }
@@ -269,12 +287,12 @@ static void ensure_tables() { std::call_once(g_once, init_tables); }
 // Physics (Sec. 2), templated so that the complex-step derivative works.
 // w = (rho, rho u, rho v, E); f[k][f] = flux in direction k of field f.
 // ---------------------------------------------------------------------------
-static const double CS_H_SC = 1e-30;  // complex step of the divergence in sc_epsilon
+static const real CS_H_SC = 1e-30;  // complex step of the divergence in sc_epsilon
 template <class T>
-static void euler_flux(const T* w, double gam, T f[2][4]) {
+static void euler_flux(const T* w, real gam, T f[2][4]) {
   T rho = w[0], mx = w[1], my = w[2], E = w[3];
   T u = mx / rho, v = my / rho;
-  T p = (gam - 1.0) * (E - 0.5 * (mx * u + my * v));
+  T p = (gam - 1.0) * (E - real(0.5) * (mx * u + my * v));
   f[0][0] = mx;      f[0][1] = mx * u + p; f[0][2] = mx * v;     f[0][3] = u * (E + p);
   f[1][0] = my;      f[1][1] = my * u;     f[1][2] = my * v + p; f[1][3] = v * (E + p);
 }
@@ -282,25 +300,25 @@ static void euler_flux(const T* w, double gam, T f[2][4]) {
 // viscous flux f_v(w, q) with q[k][f] = d w_f / d x_k (conserved-variable gradient)
 template <class T>
 static void ns_viscous_flux(const T* w, const T q[2][4], const orc_params& P, T fv[2][4]) {
-  const double gam = P.gamma;
+  const real gam = P.gamma;
   T rho = w[0], u = w[1] / w[0], v = w[2] / w[0], E = w[3];
-  T p = (gam - 1.0) * (E - 0.5 * rho * (u * u + v * v));
+  T p = (gam - 1.0) * (E - real(0.5) * rho * (u * u + v * v));
   T dudx[2], dvdx[2], dTdx[2];
   for (int k = 0; k < 2; ++k) {
     T dr = q[k][0];
     dudx[k] = (q[k][1] - u * dr) / rho;
     dvdx[k] = (q[k][2] - v * dr) / rho;
-    T dp = (gam - 1.0) * (q[k][3] - (u * q[k][1] + v * q[k][2]) + 0.5 * (u * u + v * v) * dr);
+    T dp = (gam - 1.0) * (q[k][3] - (u * q[k][1] + v * q[k][2]) + real(0.5) * (u * u + v * v) * dr);
     dTdx[k] = gam * (dp / rho - p * dr / (rho * rho));
   }
   T Tt = gam * p / rho;                                // T / T_inf
-  double S = 110.4 / P.t_inf;                          // Sutherland C2 / T_inf
-  double mu_inf = P.mach / P.reynolds;
+  real S = RLIT(110.4) / P.t_inf;                          // Sutherland C2 / T_inf
+  real mu_inf = P.mach / P.reynolds;
   T mu = mu_inf * Tt * std::sqrt(Tt) * (1.0 + S) / (Tt + S);
   T kappa = mu / ((gam - 1.0) * P.prandtl);
   T div = dudx[0] + dvdx[1];
-  T txx = mu * (2.0 * dudx[0] - (2.0 / 3.0) * div);
-  T tyy = mu * (2.0 * dvdx[1] - (2.0 / 3.0) * div);
+  T txx = mu * (real(2) * dudx[0] - (real(2) / 3) * div);
+  T tyy = mu * (real(2) * dvdx[1] - (real(2) / 3) * div);
   T txy = mu * (dudx[1] + dvdx[0]);
   fv[0][0] = 0.0; fv[0][1] = txx; fv[0][2] = txy; fv[0][3] = txx * u + txy * v + kappa * dTdx[0];
   fv[1][0] = 0.0; fv[1][1] = txy; fv[1][2] = tyy; fv[1][3] = txy * u + tyy * v + kappa * dTdx[1];
@@ -312,7 +330,7 @@ static void ns_viscous_flux(const T* w, const T q[2][4], const orc_params& P, T 
 // ---------------------------------------------------------------------------
 struct OMesh {
   int ne = 0, nf = 0, nfield = 4;
-  std::vector<double> xy;        // [ne][3][2]
+  std::vector<real> xy;        // [ne][3][2]
   std::vector<int> vid, p;       // [ne][3], [ne]
   std::vector<int> face_lo, face_hi, face_el0, face_el1, face_lf0, face_lf1, face_p;
   std::vector<int> elem_face;    // [ne][3], -1 on a boundary face
@@ -320,15 +338,15 @@ struct OMesh {
   std::vector<int64_t> u_off, lam_off, x_off, k_blkoff;
   std::vector<int> k_col;        // [nf][5]
   int64_t u_len = 0, lam_len = 0, x_len = 0, k_len = 0;
-  std::vector<double> src;       // [u_len] source s_h in U's layout (w part), empty: s = 0
+  std::vector<real> src;       // [u_len] source s_h in U's layout (w part), empty: s = 0
 };
 
 struct Geom {
-  double J[2][2], Jinv[2][2], detJ, nrm[3][2], len[3], area, perim;
+  real J[2][2], Jinv[2][2], detJ, nrm[3][2], len[3], area, perim;
 };
 static void elem_geom(const OMesh& M, int K, Geom& g) {
-  const double* c = &M.xy[K * 6];
-  double x0 = c[0], y0 = c[1], x1 = c[2], y1 = c[3], x2 = c[4], y2 = c[5];
+  const real* c = &M.xy[K * 6];
+  real x0 = c[0], y0 = c[1], x1 = c[2], y1 = c[3], x2 = c[4], y2 = c[5];
   g.J[0][0] = x1 - x0; g.J[0][1] = x2 - x0;
   g.J[1][0] = y1 - y0; g.J[1][1] = y2 - y0;
   g.detJ = g.J[0][0] * g.J[1][1] - g.J[0][1] * g.J[1][0];
@@ -337,7 +355,7 @@ static void elem_geom(const OMesh& M, int K, Geom& g) {
   g.perim = 0;
   for (int lf = 0; lf < 3; ++lf) {
     int a = lf, b = (lf + 1) % 3;
-    double dx = c[2 * b] - c[2 * a], dy = c[2 * b + 1] - c[2 * a + 1];
+    real dx = c[2 * b] - c[2 * a], dy = c[2 * b + 1] - c[2 * a + 1];
     g.len[lf] = std::sqrt(dx * dx + dy * dy);
     g.nrm[lf][0] = dy / g.len[lf];
     g.nrm[lf][1] = -dx / g.len[lf];
@@ -369,22 +387,22 @@ static inline int elem_flip(const OMesh& M, int K, int lf) {
 // the polynomial w_h is the chain rule sum_k (d f_k / d w)(w) d w / d x_k,
 // each term taken as the complex-step derivative of f_k along d w / d x_k.
 // For Navier-Stokes the gradient d w / d x_k is the q_h unknown.
-static double sc_epsilon(const OMesh& M, const orc_params& P, int K, const Geom& g, const double* U) {
+static real sc_epsilon(const OMesh& M, const orc_params& P, int K, const Geom& g, const real* U) {
   if (!(P.sc_eps0 > 0.0)) return 0.0;
   const int p = M.p[K], np = n_basis(p);
   const bool ns = (M.nfield == 12);
   const int woff = ns ? 8 * np : 0;
   const VolTab& V = g_vol[p];
-  double integral = 0.0;
+  real integral = 0.0;
   for (int q = 0; q < V.nq; ++q) {
-    const double* phi = &V.phi[q * np];
-    double w[4], grad[2][4];
+    const real* phi = &V.phi[q * np];
+    real w[4], grad[2][4];
     for (int f = 0; f < 4; ++f) {
       w[f] = 0.0;
       grad[0][f] = 0.0;
       grad[1][f] = 0.0;
       for (int j = 0; j < np; ++j) {
-        const double dx = V.dxi[q * np + j], de = V.deta[q * np + j];
+        const real dx = V.dxi[q * np + j], de = V.deta[q * np + j];
         w[f] += U[woff + f * np + j] * phi[j];
         if (ns) {
           grad[0][f] += U[f * np + j] * phi[j];
@@ -395,18 +413,18 @@ static double sc_epsilon(const OMesh& M, const orc_params& P, int K, const Geom&
         }
       }
     }
-    double div[4] = {0.0, 0.0, 0.0, 0.0};
+    real div[4] = {0.0, 0.0, 0.0, 0.0};
     for (int k = 0; k < 2; ++k) {
       cplx wc[4], fc[2][4];
       for (int f = 0; f < 4; ++f) wc[f] = cplx(w[f], CS_H_SC * grad[k][f]);
       euler_flux(wc, P.gamma, fc);
       for (int f = 0; f < 4; ++f) div[f] += fc[k][f].imag() / CS_H_SC;
     }
-    double d = 0.0;
+    real d = 0.0;
     for (int f = 0; f < 4; ++f) d += std::fabs(div[f]);
     integral += V.w[q] * g.detJ * d;
   }
-  const double hK = std::max(g.len[0], std::max(g.len[1], g.len[2]));
+  const real hK = std::max(g.len[0], std::max(g.len[1], g.len[2]));
   return P.sc_eps0 * std::pow(hK / p, 2.0 - P.sc_beta) / g.area * integral;
 }
 
@@ -420,10 +438,10 @@ static double sc_epsilon(const OMesh& M, const orc_params& P, int K, const Geom&
 //   (1, u - c n, H - c v_n), (1, u, v, |v|^2/2), (0, t, v_t), (1, u + c n, H + c v_n),
 // t = (-n_y, n_x), eigenvalues v_n - c, v_n, v_n, v_n + c.  The upwinding
 // decision uses the real part (it is not differentiated).
-static double re(double x) { return x; }
-static double re(const cplx& x) { return x.real(); }
+static real re(real x) { return x; }
+static real re(const cplx& x) { return x.real(); }
 template <class T>
-static void boundary_state(int kind, const T* w, double nx, double ny, const orc_params& P, T* wb) {
+static void boundary_state(int kind, const T* w, real nx, real ny, const orc_params& P, T* wb) {
   if (kind == 3) {  // no-slip wall (Sec. 2.2): w_b = (rho, 0, 0, E)
     wb[0] = w[0]; wb[1] = 0.0; wb[2] = 0.0; wb[3] = w[3];
     return;
@@ -433,18 +451,18 @@ static void boundary_state(int kind, const T* w, double nx, double ny, const orc
     wb[0] = w[0]; wb[1] = w[1] - mn * nx; wb[2] = w[2] - mn * ny; wb[3] = w[3];
     return;
   }
-  const double gam = P.gamma, a = P.aoa * 3.14159265358979323846 / 180.0;
-  const double ui = P.mach * std::cos(a), vi = P.mach * std::sin(a), pi = 1.0 / gam;
-  const double winf[4] = {1.0, ui, vi, pi / (gam - 1.0) + 0.5 * (ui * ui + vi * vi)};
+  const real gam = P.gamma, a = P.aoa * RLIT(3.14159265358979323846264338327950288) / 180.0;
+  const real ui = P.mach * std::cos(a), vi = P.mach * std::sin(a), pi = 1.0 / gam;
+  const real winf[4] = {1.0, ui, vi, pi / (gam - 1.0) + 0.5 * (ui * ui + vi * vi)};
   T rho = w[0], u = w[1] / rho, v = w[2] / rho;
-  T p = (gam - 1.0) * (w[3] - 0.5 * rho * (u * u + v * v));
+  T p = (gam - 1.0) * (w[3] - real(0.5) * rho * (u * u + v * v));
   T c = std::sqrt(gam * p / rho), H = (w[3] + p) / rho;
   T vn = u * nx + v * ny, vt = -u * ny + v * nx;
   T Q[4][4] = {{1.0, 1.0, 0.0, 1.0},
                {u - c * nx, u, -ny, u + c * nx},
                {v - c * ny, v, nx, v + c * ny},
-               {H - c * vn, 0.5 * (u * u + v * v), vt, H + c * vn}};
-  const double lam[4] = {re(vn - c), re(vn), re(vn), re(vn + c)};
+               {H - c * vn, real(0.5) * (u * u + v * v), vt, H + c * vn}};
+  const real lam[4] = {re(vn - c), re(vn), re(vn), re(vn + c)};
   // y = Q^{-1} (w_inf - w): Gaussian elimination with partial pivoting (by real part)
   T A[4][5];
   for (int i = 0; i < 4; ++i) {
@@ -477,7 +495,7 @@ static void boundary_state(int kind, const T* w, double nx, double ny, const orc
 // eps is the element's shock-capturing viscosity (0: none), a constant here.
 template <class T>
 static void element_residual(const OMesh& M, const orc_params& P, int K, const Geom& g,
-                             const T* U, const T* L, T* Nu, T* Nl, double eps) {
+                             const T* U, const T* L, T* Nu, T* Nl, real eps) {
   const int p = M.p[K], np = n_basis(p);
   const bool ns = (M.nfield == 12);
   const int woff = ns ? 8 * np : 0;
@@ -486,13 +504,13 @@ static void element_residual(const OMesh& M, const orc_params& P, int K, const G
   for (int r = 0; r < n; ++r) Nu[r] = 0.0;
   for (int r = 0; r < nt; ++r) Nl[r] = 0.0;
   const VolTab& V = g_vol[p];
-  std::vector<double> gx(np), gy(np);
+  std::vector<real> gx(np), gy(np);
   // volume terms
   for (int q = 0; q < V.nq; ++q) {
-    const double* phi = &V.phi[q * np];
-    const double wq = V.w[q] * g.detJ;
+    const real* phi = &V.phi[q * np];
+    const real wq = V.w[q] * g.detJ;
     for (int j = 0; j < np; ++j) {
-      double dx = V.dxi[q * np + j], de = V.deta[q * np + j];
+      real dx = V.dxi[q * np + j], de = V.deta[q * np + j];
       gx[j] = g.Jinv[0][0] * dx + g.Jinv[1][0] * de;
       gy[j] = g.Jinv[0][1] * dx + g.Jinv[1][1] * de;
     }
@@ -536,7 +554,7 @@ static void element_residual(const OMesh& M, const orc_params& P, int K, const G
       for (int k = 0; k < 2; ++k)
         for (int f = 0; f < 4; ++f)
           for (int i = 0; i < np; ++i) {
-            double gk = (k == 0) ? gx[i] : gy[i];
+            real gk = (k == 0) ? gx[i] : gy[i];
             Nu[(k * 4 + f) * np + i] += wq * (phi[i] * qv[k][f] + gk * w[f]);
           }
   }
@@ -550,10 +568,10 @@ static void element_residual(const OMesh& M, const orc_params& P, int K, const G
     if (e < 0) {  // boundary operator of Sec. 3.2: <tau.n, w_b> + <phi, (f_c(w_b) - f_v(w_b, q_b)).n>, no lambda
       const EdgeTab& Eb = g_edge[p][p];
       const int fl = elem_flip(M, K, lf);
-      const double nx = g.nrm[lf][0], ny = g.nrm[lf][1];
+      const real nx = g.nrm[lf][0], ny = g.nrm[lf][1];
       for (int gq = 0; gq < Eb.ne; ++gq) {
-        const double we = Eb.w[gq] * g.len[lf];
-        const double* phi = &Eb.phi[lf][fl][gq * np];
+        const real we = Eb.w[gq] * g.len[lf];
+        const real* phi = &Eb.phi[lf][fl][gq * np];
         T w[4], wb[4], fc[2][4], fv[2][4];
         for (int f = 0; f < 4; ++f) {
           w[f] = 0.0;
@@ -580,7 +598,7 @@ static void element_residual(const OMesh& M, const orc_params& P, int K, const G
           }
           // -<tau.n, w_b>_dK in the q equations
           for (int k = 0; k < 2; ++k) {
-            const double nk_ = (k == 0) ? nx : ny;
+            const real nk_ = (k == 0) ? nx : ny;
             for (int f = 0; f < 4; ++f)
               for (int j = 0; j < np; ++j) Nu[(k * 4 + f) * np + j] -= we * phi[j] * nk_ * wb[f];
           }
@@ -594,11 +612,11 @@ static void element_residual(const OMesh& M, const orc_params& P, int K, const G
     int pe = M.face_p[e], nk = pe + 1;
     int fl = elem_flip(M, K, lf);
     const EdgeTab& Et = g_edge[p][pe];
-    const double nx = g.nrm[lf][0], ny = g.nrm[lf][1];
+    const real nx = g.nrm[lf][0], ny = g.nrm[lf][1];
     for (int gq = 0; gq < Et.ne; ++gq) {
-      const double we = Et.w[gq] * g.len[lf];
-      const double* phi = &Et.phi[lf][fl][gq * np];
-      const double* psi = &Et.psi[gq * nk];
+      const real we = Et.w[gq] * g.len[lf];
+      const real* phi = &Et.phi[lf][fl][gq * np];
+      const real* psi = &Et.psi[gq * nk];
       T w[4], lam[4], qv[2][4], fc[2][4], fv[2][4], fh[4];
       for (int f = 0; f < 4; ++f) {
         w[f] = 0.0;
@@ -619,12 +637,12 @@ static void element_residual(const OMesh& M, const orc_params& P, int K, const G
       }
       // numerical flux  (f_c(lam) - f_v(lam, q)).n - alpha (lam - w)
       for (int f = 0; f < 4; ++f)
-        fh[f] = nx * (fc[0][f] - fv[0][f]) + ny * (fc[1][f] - fv[1][f]) - P.alpha * (lam[f] - w[f]);
+        fh[f] = nx * (fc[0][f] - fv[0][f]) + ny * (fc[1][f] - fv[1][f]) - real(P.alpha) * (lam[f] - w[f]);
       for (int f = 0; f < 4; ++f)
         for (int j = 0; j < np; ++j) Nu[woff + f * np + j] += we * phi[j] * fh[f];
       if (ns)  // -<tau.n, lambda>_dK
         for (int k = 0; k < 2; ++k) {
-          double nk_ = (k == 0) ? nx : ny;
+          real nk_ = (k == 0) ? nx : ny;
           for (int f = 0; f < 4; ++f)
             for (int j = 0; j < np; ++j) Nu[(k * 4 + f) * np + j] -= we * phi[j] * nk_ * lam[f];
         }
@@ -637,19 +655,19 @@ static void element_residual(const OMesh& M, const orc_params& P, int K, const G
 }
 
 // local time step of Sec. 3.3 from the element-mean state (real part of U)
-static double local_dt(const OMesh& M, const orc_params& P, int K, const Geom& g, const double* U) {
+static real local_dt(const OMesh& M, const orc_params& P, int K, const Geom& g, const real* U) {
   const int np = n_basis(M.p[K]);
   const int woff = (M.nfield == 12) ? 8 * np : 0;
-  const double c0 = std::sqrt(2.0);  // value of the constant orthonormal mode
-  double rho = c0 * U[woff], u = c0 * U[woff + np] / rho, v = c0 * U[woff + 2 * np] / rho,
+  const real c0 = std::sqrt(real(2));  // value of the constant orthonormal mode
+  real rho = c0 * U[woff], u = c0 * U[woff + np] / rho, v = c0 * U[woff + 2 * np] / rho,
          E = c0 * U[woff + 3 * np];
-  double p = (P.gamma - 1.0) * (E - 0.5 * rho * (u * u + v * v));
-  double c = std::sqrt(P.gamma * p / rho);
-  double lam_c = (std::sqrt(u * u + v * v) + c) * g.perim;
-  double lam_v = 0.0;
+  real p = (P.gamma - 1.0) * (E - 0.5 * rho * (u * u + v * v));
+  real c = std::sqrt(P.gamma * p / rho);
+  real lam_c = (std::sqrt(u * u + v * v) + c) * g.perim;
+  real lam_v = 0.0;
   if (M.nfield == 12) {
-    double Tt = P.gamma * p / rho, S = 110.4 / P.t_inf;
-    double mu = (P.mach / P.reynolds) * Tt * std::sqrt(Tt) * (1.0 + S) / (Tt + S);
+    real Tt = P.gamma * p / rho, S = RLIT(110.4) / P.t_inf;
+    real mu = (P.mach / P.reynolds) * Tt * std::sqrt(Tt) * (1.0 + S) / (Tt + S);
     lam_v = P.gamma * mu / (P.prandtl * rho) * g.perim * g.perim / g.area;
   }
   return P.cfl * g.area / (lam_c + 4.0 * lam_v);
@@ -657,10 +675,10 @@ static double local_dt(const OMesh& M, const orc_params& P, int K, const Geom& g
 
 // Element blocks: A = dNu/dU, B = dNu/dL, C = dNl/dU, D = dNl/dL (complex
 // step, exact to rounding), F = -Nu, H = -Nl; pseudo-time mass on the W block.
-static const double CS_H = 1e-30;
-static void element_blocks(const OMesh& M, const orc_params& P, int K, const double* U, const double* L,
-                           std::vector<double>& A, std::vector<double>& B, std::vector<double>& C,
-                           std::vector<double>& D, std::vector<double>& F, std::vector<double>& H) {
+static const real CS_H = 1e-30;
+static void element_blocks(const OMesh& M, const orc_params& P, int K, const real* U, const real* L,
+                           std::vector<real>& A, std::vector<real>& B, std::vector<real>& C,
+                           std::vector<real>& D, std::vector<real>& F, std::vector<real>& H) {
   Geom g;
   elem_geom(M, K, g);
   const int n = elem_n(M, K), nt = elem_nt(M, K);
@@ -669,7 +687,7 @@ static void element_blocks(const OMesh& M, const orc_params& P, int K, const dou
   std::vector<cplx> Uc(n), Lc(nt), Nu(n), Nl(nt);
   for (int r = 0; r < n; ++r) Uc[r] = U[r];
   for (int r = 0; r < nt; ++r) Lc[r] = L[r];
-  const double eps = sc_epsilon(M, P, K, g, U);  // frozen: not differentiated
+  const real eps = sc_epsilon(M, P, K, g, U);  // frozen: not differentiated
   element_residual<cplx>(M, P, K, g, Uc.data(), Lc.data(), Nu.data(), Nl.data(), eps);
   for (int r = 0; r < n; ++r) F[r] = -Nu[r].real();
   for (int r = 0; r < nt; ++r) H[r] = -Nl[r].real();
@@ -678,16 +696,16 @@ static void element_blocks(const OMesh& M, const orc_params& P, int K, const dou
     element_residual<cplx>(M, P, K, g, Uc.data(), Lc.data(), Nu.data(), Nl.data(), eps);
     if (c < n) Uc[c] = U[c]; else Lc[c - n] = L[c - n];
     for (int r = 0; r < n; ++r) {
-      double d = Nu[r].imag() / CS_H;
+      real d = Nu[r].imag() / CS_H;
       if (c < n) A[r * n + c] = d; else B[r * nt + (c - n)] = d;
     }
     for (int r = 0; r < nt; ++r) {
-      double d = Nl[r].imag() / CS_H;
+      real d = Nl[r].imag() / CS_H;
       if (c < n) C[r * n + c] = d; else D[r * nt + (c - n)] = d;
     }
   }
   if (P.cfl > 0.0) {
-    double dt = local_dt(M, P, K, g, U);
+    real dt = local_dt(M, P, K, g, U);
     const int np = n_basis(M.p[K]);
     const int woff = (M.nfield == 12) ? 8 * np : 0;
     for (int r = woff; r < n; ++r) A[r * n + r] += g.detJ / dt;
@@ -695,11 +713,11 @@ static void element_blocks(const OMesh& M, const orc_params& P, int K, const dou
 }
 
 // dense LU with partial pivoting (first maximal |pivot| wins), in place
-static int lu_factor(int n, std::vector<double>& A, std::vector<int>& piv) {
+static int lu_factor(int n, std::vector<real>& A, std::vector<int>& piv) {
   piv.resize(n);
   for (int k = 0; k < n; ++k) {
     int r = k;
-    double best = std::fabs(A[k * n + k]);
+    real best = std::fabs(A[k * n + k]);
     for (int i = k + 1; i < n; ++i)
       if (std::fabs(A[i * n + k]) > best) { best = std::fabs(A[i * n + k]); r = i; }
     piv[k] = r;
@@ -708,25 +726,25 @@ static int lu_factor(int n, std::vector<double>& A, std::vector<int>& piv) {
       for (int j = 0; j < n; ++j) std::swap(A[k * n + j], A[r * n + j]);
     for (int i = k + 1; i < n; ++i) {
       A[i * n + k] /= A[k * n + k];
-      double lik = A[i * n + k];
+      real lik = A[i * n + k];
       for (int j = k + 1; j < n; ++j) A[i * n + j] -= lik * A[k * n + j];
     }
   }
   return 0;
 }
 // solve A x = b for nrhs columns of the row-major n x nrhs matrix X (in place)
-static void lu_solve(int n, const std::vector<double>& LU, const std::vector<int>& piv, int nrhs, double* X) {
+static void lu_solve(int n, const std::vector<real>& LU, const std::vector<int>& piv, int nrhs, real* X) {
   for (int k = 0; k < n; ++k)
     if (piv[k] != k)
       for (int c = 0; c < nrhs; ++c) std::swap(X[k * nrhs + c], X[piv[k] * nrhs + c]);
   for (int c = 0; c < nrhs; ++c) {
     for (int i = 0; i < n; ++i) {
-      double s = X[i * nrhs + c];
+      real s = X[i * nrhs + c];
       for (int j = 0; j < i; ++j) s -= LU[i * n + j] * X[j * nrhs + c];
       X[i * nrhs + c] = s;
     }
     for (int i = n - 1; i >= 0; --i) {
-      double s = X[i * nrhs + c];
+      real s = X[i * nrhs + c];
       for (int j = i + 1; j < n; ++j) s -= LU[i * n + j] * X[j * nrhs + c];
       X[i * nrhs + c] = s / LU[i * n + i];
     }
@@ -734,7 +752,7 @@ static void lu_solve(int n, const std::vector<double>& LU, const std::vector<int
 }
 
 // gather of element K's trace vector from the global Lambda (faces in local order)
-static void gather_trace(const OMesh& M, int K, const double* Lam, std::vector<double>& L) {
+static void gather_trace(const OMesh& M, int K, const real* Lam, std::vector<real>& L) {
   L.clear();
   for (int lf = 0; lf < 3; ++lf) {
     int e = M.elem_face[K * 3 + lf];
@@ -746,12 +764,12 @@ static void gather_trace(const OMesh& M, int K, const double* Lam, std::vector<d
 
 // Condensation of one element: X = A^{-1}[B | F] (n x (nt+1), row-major),
 // S = D - C X_B (nt x nt), Ek = H - C X_F (nt).  Returns 1 on a zero pivot.
-static int element_condense(const OMesh& M, const orc_params& P, int K, const double* U, const double* Lam,
-                            std::vector<double>& X, std::vector<double>& S, std::vector<double>& Ek,
-                            std::vector<double>* Nu_out, std::vector<double>* Nl_out) {
-  std::vector<double> L, A, B, C, D, F, H;
+static int element_condense(const OMesh& M, const orc_params& P, int K, const real* U, const real* Lam,
+                            std::vector<real>& X, std::vector<real>& S, std::vector<real>& Ek,
+                            std::vector<real>* Nu_out, std::vector<real>* Nl_out) {
+  std::vector<real> L, A, B, C, D, F, H;
   gather_trace(M, K, Lam, L);
-  const double* UK = U + M.u_off[K];
+  const real* UK = U + M.u_off[K];
   element_blocks(M, P, K, UK, L.data(), A, B, C, D, F, H);
   const int n = elem_n(M, K), nt = elem_nt(M, K), nr = nt + 1;
   if (Nu_out) { Nu_out->resize(n); for (int r = 0; r < n; ++r) (*Nu_out)[r] = -F[r]; }
@@ -769,11 +787,11 @@ static int element_condense(const OMesh& M, const orc_params& P, int K, const do
   lu_solve(n, A, piv, nr, X.data());
   for (int r = 0; r < nt; ++r) {
     for (int c = 0; c < nt; ++c) {
-      double s = D[r * nt + c];
+      real s = D[r * nt + c];
       for (int k = 0; k < n; ++k) s -= C[r * n + k] * X[k * nr + c];
       S[r * nt + c] = s;
     }
-    double s = H[r];
+    real s = H[r];
     for (int k = 0; k < n; ++k) s -= C[r * n + k] * X[k * nr + nt];
     Ek[r] = s;
   }
@@ -784,6 +802,7 @@ static int element_condense(const OMesh& M, const orc_params& P, int K, const do
 // C interface (ctypes)
 // ---------------------------------------------------------------------------
 extern "C" {
+#ifndef ORC_EXTENDED
 
 // n-point Gauss-Jacobi rule, weight (1-x)^alpha (1+x)^beta on [-1,1]
 int orc_gauss_jacobi(int n, double alpha, double beta, double* x, double* w) {
@@ -831,6 +850,8 @@ void orc_ns_viscous_flux(const double* w, const double* q, const orc_params* P, 
   ns_viscous_flux(w, qq, *P, ff);
   std::memcpy(fv, ff, sizeof(ff));
 }
+
+#endif  // ORC_EXTENDED
 
 // Build the mesh.  Returns 0 ok, 2 bad input (non-positive det J, p out of
 // range, a face not shared by exactly two elements, two elements sharing two faces).
@@ -961,6 +982,7 @@ void orc_mesh_arrays(void* h, int32_t* face_vid, int32_t* face_el, int32_t* face
   if (k_blkoff) std::copy(M->k_blkoff.begin(), M->k_blkoff.end(), k_blkoff);
 }
 
+#ifndef ORC_EXTENDED
 // Residual of element K (real): Nu [n], Nl [nt] (this element's share of the trace rows).
 int orc_element_residual(void* h, const orc_params* P, int K, const double* U, const double* Lam,
                          double* Nu, double* Nl) {
@@ -1286,4 +1308,64 @@ int orc_dense_solve(int n, const double* A, double* b) {
   return 0;
 }
 
+#else  // ORC_EXTENDED
+// The extended-precision build exposes the mesh calls above and the local
+// condensation of chosen elements: inputs are binary64 (as given to the
+// binary64 oracle), everything else -- tables, geometry, residual, complex-step
+// Jacobian, LU, Schur -- runs in long double; the results are returned rounded
+// to binary64 (relative 1.1e-16, far below the errors this build measures).
+
+// Condensation of element K: X [n][nt+1], S [nt][nt], Ek [nt] (as orc_element_condense),
+// and the reconstruction dU_K = X_F - X_B dLambda_K [n] (Eq. ls).  Returns 0 ok / 1 zero pivot.
+int orcx_element_condense(void* h, const orc_params* P, int K, const double* U, const double* Lam,
+                          const double* dLam, double* X, double* S, double* Ek, double* dU) {
+  OMesh* M = (OMesh*)h;
+  const int n = elem_n(*M, K), nt = elem_nt(*M, K), nr = nt + 1;
+  std::vector<real> Ur(M->u_len), Lr(M->lam_len), dLr(M->lam_len), x, s, e;
+  for (int64_t i = 0; i < M->u_len; ++i) Ur[i] = U[i];
+  for (int64_t i = 0; i < M->lam_len; ++i) { Lr[i] = Lam[i]; dLr[i] = dLam[i]; }
+  const int st = element_condense(*M, *P, K, Ur.data(), Lr.data(), x, s, e, nullptr, nullptr);
+  for (size_t i = 0; i < x.size(); ++i) X[i] = (double)x[i];
+  for (size_t i = 0; i < s.size(); ++i) S[i] = (double)s[i];
+  for (size_t i = 0; i < e.size(); ++i) Ek[i] = (double)e[i];
+  std::vector<real> dl;
+  gather_trace(*M, K, dLr.data(), dl);
+  for (int r = 0; r < n; ++r) {
+    real acc = x[r * nr + nt];
+    for (int c = 0; c < nt; ++c) acc -= x[r * nr + c] * dl[c];
+    dU[r] = (double)acc;
+  }
+  return st;
+}
+
+// Assembled condensed right-hand side of face f, E_f = sum over its two sides of
+// the element contributions E_K (Sec. 3.4), summed in long double: Ef [4(p_e+1)].
+int orcx_face_E(void* h, const orc_params* P, int f, const double* U, const double* Lam, double* Ef) {
+  OMesh* M = (OMesh*)h;
+  if (f < 0 || f >= M->nf) return 2;
+  const int len = face_len(*M, f);
+  std::vector<real> Ur(M->u_len), Lr(M->lam_len), acc(len, 0.0L);
+  for (int64_t i = 0; i < M->u_len; ++i) Ur[i] = U[i];
+  for (int64_t i = 0; i < M->lam_len; ++i) Lr[i] = Lam[i];
+  int st = 0;
+  for (int sd = 0; sd < 2; ++sd) {
+    const int K = sd ? M->face_el1[f] : M->face_el0[f];
+    std::vector<real> x, s, e;
+    st |= element_condense(*M, *P, K, Ur.data(), Lr.data(), x, s, e, nullptr, nullptr);
+    int roff = 0;
+    for (int a = 0; a < 3; ++a) {
+      const int ea = M->elem_face[K * 3 + a];
+      if (ea < 0) continue;
+      if (ea == f)
+        for (int r = 0; r < len; ++r) acc[r] += e[roff + r];
+      roff += face_len(*M, ea);
+    }
+  }
+  for (int r = 0; r < len; ++r) Ef[r] = (double)acc[r];
+  return st;
+}
+
+// Number of significand bits of the build's scalar type (64 on x86-64, 113 on aarch64).
+int orcx_mantissa_bits(void) { return std::numeric_limits<real>::digits; }
+#endif  // ORC_EXTENDED
 }  // extern "C"

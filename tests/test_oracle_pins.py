@@ -1285,3 +1285,49 @@ def test_pseudo_time_mass_closed_form(model, reynolds, p):
     assert np.abs(dA - want).max() <= 1e-12 * expected
     if model == 1 and reynolds < 100:
         assert 4 * lam_v > 0.05 * lam_c                 # the viscous part is not negligible here
+
+
+# ----------------------------------------------------------------------------- extended-precision build
+def test_extended_build_has_a_longer_significand():
+    assert O.mantissa_bits_ext() >= 64   # 80-bit extended (x86-64) or binary128 (aarch64)
+
+
+@pytest.mark.parametrize("model", [0, 1])
+def test_extended_build_preserves_free_stream_to_its_own_precision(model):
+    """Free stream on a jittered mixed-degree mesh: E_f vanishes in exact arithmetic up to the rounding of
+    the inputs (mode-0 coefficients w/sqrt(2) and traces w are binary64 numbers: about 3e-17 of the flux).
+    The binary64 build adds its arithmetic rounding (about 1e-15); the long double build must stay at
+    least 10 times closer to zero, which shows that it really evaluates tables, geometry and residual in
+    the longer format."""
+    wl, c, m, P = _case("ns_mixp_65k", 4, 4, model=model)
+    mx = O.ExtMesh(m)
+    winf = G.conserved(*G.free_stream(0.7, 3.0))
+    U, L = _uniform_state(m, winf)
+    P.mach = 0.7
+    scale = np.abs(O.euler_flux(winf)).max()
+    r = m.condense(P, U, L)
+    worst64 = np.abs(r["E"]).max() / scale
+    worstx = max(np.abs(mx.face_E(P, f, U, L)).max() for f in range(0, m.n_face, 3)) / scale
+    assert worst64 > 0 and worstx < 0.1 * max(worst64, 1e-16)
+
+
+@pytest.mark.parametrize("name,nx,ny", [("euler_p3_16k", 6, 8), ("ns_mixp_65k", 6, 6)])
+def test_extended_build_matches_binary64_oracle(name, nx, ny):
+    """Both builds evaluate one definition: the local solves X_B agree to binary64 accuracy; the
+    residual-type outputs X_F, dU, E (differences of O(flux) terms) agree to their conditioning."""
+    wl, c, m, P = _case(name, nx, ny)
+    mx = O.ExtMesh(m)
+    U, L, dL = G.case_state(c, m.face_vid, m.face_p)
+    r = m.condense(P, U, L)
+    dU = m.recover(r["X"], dL)
+    for K in range(0, m.n_elem, 7):
+        X, S, E, dUx, st = mx.element_condense(P, K, U, L, dL)
+        n, nt = m.n(K), m.nt(K)
+        Xo = r["X"][m.x_off[K]:m.x_off[K + 1]].reshape(n, nt + 1)
+        assert st == 0
+        assert np.linalg.norm(Xo[:, :nt] - X[:, :nt]) <= 1e-13 * np.linalg.norm(X[:, :nt])
+        assert np.linalg.norm(Xo[:, nt] - X[:, nt]) <= 1e-11 * np.linalg.norm(X[:, nt])
+        assert np.linalg.norm(dU[m.u_off[K]:m.u_off[K + 1]] - dUx) <= 1e-11 * np.linalg.norm(dUx)
+    for f in range(0, m.n_face, 11):
+        Ex = mx.face_E(P, f, U, L)
+        assert np.linalg.norm(r["E"][m.lam_off[f]:m.lam_off[f + 1]] - Ex) <= 1e-11 * np.linalg.norm(Ex)
