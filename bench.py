@@ -39,8 +39,8 @@ HBM_PEAK_GBS = 6778.0       # measured copy bandwidth of the GB300s (MEA
 # Counters from ncu captures of the condensation kernels (profiles/k_condense_flops_per_element.md and
 # profiles/k_condense_euler_f64_euler_p3.md), valid only while the kernel sources hash to KERNEL_SRC_SHA
 # (kernel_src_sha()); afterwards the bench reports them as stale (null) instead of quoting old numbers.
-KERNEL_SRC_FILES = ("hdg_kernels.cu", "hdg_ns.cuh", "hdg_ns.cu", "hdg_ns_ff.cu", "hdg_lu.cuh", "hdg_arith.cuh",
-                    "hdg_physics.cuh", "hdg_internal.h")
+KERNEL_SRC_FILES = ("hdg_euler.cuh", "hdg_kernels.cu", "hdg_ns.cuh", "hdg_ns.cu", "hdg_ns_ff.cu", "hdg_lu.cuh",
+                    "hdg_arith.cuh", "hdg_physics.cuh", "hdg_internal.h")
 KERNEL_SRC_SHA = "3bdced85fe84ffcb"
 # executed floating-point work per element, (binary64 flops, binary32 flops): 2 DFMA + DADD + DMUL and
 # 2 FFMA + FADD + FMUL from the SASS instruction counters (no paired FFMA2/FADD2/FMUL2 were issued),
@@ -318,7 +318,7 @@ class Measured:
 
     autotune = True   # pick each degree bucket's launch shape with hdg_autotune before timing
 
-    def __init__(self, ctx, wl, precision, dev, flush, sc_eps0=0.0):
+    def __init__(self, ctx, wl, precision, dev, flush, sc_eps0=0.0, refine_max=4, refine_tol=1e-13):
         import torch
 
         from paper_1308_3995_gb300 import hdg
@@ -329,7 +329,8 @@ class Measured:
         self.mesh = hdg.Mesh(ctx, c.mesh.elem_xy, c.mesh.elem_vid, c.elem_p, c.nfield, c.mesh.elem_bc)
         self.U, self.Lam, self.dLam = G.case_state(c, self.mesh.face_vid, self.mesh.face_p)
         self.prm = hdg.Params(model=wl.model, precision=precision, mach=wl.mach, alpha=wl.alpha,
-                              reynolds=wl.reynolds, prandtl=wl.prandtl, sc_eps0=sc_eps0, aoa=wl.aoa)
+                              reynolds=wl.reynolds, prandtl=wl.prandtl, sc_eps0=sc_eps0, aoa=wl.aoa,
+                              refine_max=refine_max, refine_tol=refine_tol)
         self.sys = hdg.System(ctx, self.mesh, self.prm)
         self.Ut, self.Lt, self.dLt = (torch.from_numpy(a).to(dev) for a in (self.U, self.Lam, self.dLam))
         self.dUt = torch.empty(self.mesh.u_len, dtype=torch.float64, device=dev)
@@ -592,6 +593,73 @@ def steady_section(ctx, dev, flush, stream, name="euler_box_8k", tol=1e-10, c0=1
     return out
 
 
+def latency_section(ctx, dev, stream, reps=300):
+    """The 256-triangle Euler p = 1 step (8x16 cells, Mach 0.5 with a density bump; the small
+    configuration): latency-bound, so it is reported as times per step, not as a throughput.
+    Device time of condensation + reconstruction (CUDA events around each step), host time to
+    enqueue them (launch overhead), end-to-end time through hdg_step_host with pinned host
+    buffers (copies and synchronisation included), and the same step replayed as a CUDA graph."""
+    import torch
+
+    from paper_1308_3995_gb300 import hdg
+    from paper_1308_3995_gb300 import inputs as G
+    wl = G.WORKLOADS["euler_p1_256"]
+    c = G.make_case(wl)
+    mesh = hdg.Mesh(ctx, c.mesh.elem_xy, c.mesh.elem_vid, c.elem_p, c.nfield, c.mesh.elem_bc)
+    U, Lam, dLam = G.case_state(c, mesh.face_vid, mesh.face_p)
+    sysm = hdg.System(ctx, mesh, hdg.Params(model=wl.model, mach=wl.mach, alpha=wl.alpha))
+    Ut, Lt, dLt = (torch.from_numpy(a).to(dev) for a in (U, Lam, dLam))
+    dUt = torch.empty(mesh.u_len, dtype=torch.float64, device=dev)
+    for _ in range(20):
+        sysm.condense(Ut, Lt, stream)
+        sysm.recover(dLt, dUt, stream)
+    torch.cuda.synchronize()
+
+    def pct(v, q):
+        v = sorted(v)
+        return v[min(len(v) - 1, int(q / 100.0 * len(v)))]
+    dev_us, enq_us = [], []
+    for _ in range(reps):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        t0 = time.perf_counter()
+        sysm.condense(Ut, Lt, stream)
+        sysm.recover(dLt, dUt, stream)
+        enq_us.append(1e6 * (time.perf_counter() - t0))
+        e1.record(stream)
+        e1.synchronize()
+        dev_us.append(1e3 * e0.elapsed_time(e1))
+    Uh, Lh, dLh = (torch.from_numpy(a).pin_memory() for a in (U, Lam, dLam))
+    dUh = torch.empty(mesh.u_len, dtype=torch.float64).pin_memory()
+    e2e_us = []
+    for i in range(reps + 10):
+        t0 = time.perf_counter()
+        sysm.step_host(Uh, Lh, dLh, dUh, stream)
+        if i >= 10:
+            e2e_us.append(1e6 * (time.perf_counter() - t0))
+    sysm.graph_create(Ut, Lt, dLt, dUt)
+    g_us = []
+    for i in range(reps + 10):
+        t0 = time.perf_counter()
+        sysm.graph_launch(stream)
+        stream.synchronize()
+        if i >= 10:
+            g_us.append(1e6 * (time.perf_counter() - t0))
+    out = {"workload": "euler_p1_256: 2D Euler HDG, p=1, 256 periodic triangles (8x16 cells), Mach 0.5, "
+                       "density bump; binary64",
+           "elements": mesh.n_elem, "kernel_launches_per_step": sysm.launches,
+           "device_us_p50": pct(dev_us, 50), "device_us_p99": pct(dev_us, 99),
+           "enqueue_us_p50": pct(enq_us, 50),
+           "e2e_us_p50": pct(e2e_us, 50), "e2e_us_p99": pct(e2e_us, 99),
+           "e2e_h2d_bytes": 8 * (mesh.u_len + 2 * mesh.lam_len), "e2e_d2h_bytes": 8 * mesh.u_len,
+           "graph_replay_us_p50": pct(g_us, 50), "graph_replay_us_p99": pct(g_us, 99),
+           "note": "host clock for enqueue, end-to-end and graph replay (launch to stream synchronised); "
+                   "CUDA events for device time; inputs L2-resident (a 256-element step is latency-bound)"}
+    sysm.close()
+    mesh.close()
+    return out
+
+
 def serving_section(ctx, n_requests, seed, max_elems, rates=(0.7,), arena_gb=24, solve=False):
     """Poisson stream through the continuous-batching loop (float-float, 8 slots)
     against the plain loop (binary64, one request at a time), at each load level
@@ -607,24 +675,34 @@ def serving_section(ctx, n_requests, seed, max_elems, rates=(0.7,), arena_gb=24,
     arena = int(arena_gb) << 30
     mixed = SV.Server(ctx, arena, slots=8, precision=hdg.HDG_FLOAT2, solve=solve)
     plain = SV.Server(ctx, arena, slots=1, precision=hdg.HDG_FP64, solve=solve)
+    # step requests also through batched launches: the requests admitted since the last launch
+    # condensed by one launch per (model, degree) group, up to two batches in flight
+    batched = None if solve else SV.Server(ctx, arena, slots=64, precision=hdg.HDG_FLOAT2, batched=True,
+                                           max_inflight=2)
     sat = mixed.run(reqs, "saturated")                       # everything at t = 0
     mean_el = sat.elements / sat.n
     levels = {}
+    sat_b = batched.run(reqs, "saturated, batched launches") if batched else None
     for frac in rates:
         rate = frac * sat.throughput / mean_el               # requests / s
         arr = SV.poisson_arrivals(len(reqs), rate, seed + 1)
         for r, t in zip(reqs, arr):
             r.arrival_s = float(t)
         m = mixed.run(reqs, "mixed float-float, continuous batching (8 slots)").as_dict()
-        p = plain.run(reqs, "plain FP64, one request at a time").as_dict()
-        levels[str(frac)] = {"arrival_rate_per_s": rate, "mixed": m, "plain_fp64": p}
-    del mixed, plain
+        lv = {"arrival_rate_per_s": rate, "mixed": m}
+        if batched:
+            lv["mixed_batched_launches"] = batched.run(reqs, "mixed float-float, batched launches").as_dict()
+        lv["plain_fp64"] = plain.run(reqs, "plain FP64, one request at a time").as_dict()
+        levels[str(frac)] = lv
+    del mixed, plain, batched
     torch.cuda.empty_cache()
     out = {"requests": len(reqs), "sizes": f"1000..{max_elems} elements log-uniform, Euler/NS 50/50, p 1..4",
            "request": ("Newton step: condensation at CFL 10, GMRES(30) + block ILU(0) trace solve to 1e-10 "
                        "relative residual, reconstruction; dU and dLambda back to the host") if solve else
                       "condensation + reconstruction with a seeded trace update; dU back to the host",
            "saturated_elements_per_s": sat.throughput, "elements_total": sat.elements}
+    if sat_b is not None:
+        out["saturated_elements_per_s_batched_launches"] = sat_b.throughput
     if solve:
         out["saturated_gmres_iterations_median"] = sat.as_dict().get("gmres_iterations_median")
     if len(levels) == 1:
@@ -770,6 +848,27 @@ def run_ours(args, wl, ws, rank, local):
                 mp.close()
             ns_per_p[str(p)] = row
         line["ns_elements_per_s_per_p"] = ns_per_p
+        # tensor-core trial (precision item of the method's mixed-precision local solves): binary64
+        # assembly and refinement residuals, binary32 LU and solves with mma.sync updates
+        trial = {}
+        for p in (3, 4):
+            wp = G.small_variant(wl, wl.nx, wl.ny, p=p, name=f"euler_p{p}_16k")
+            row = {}
+            for nm, prec, rmax in (("fp64_direct", hdg.HDG_FP64, 0), ("float2_direct", hdg.HDG_FLOAT2, 0),
+                                   ("tf32x3_refined", hdg.HDG_MIXED_TF32, 4),
+                                   ("tf32x3_one_correction", hdg.HDG_MIXED_TF32, 1),
+                                   ("bf16_refined", hdg.HDG_MIXED_BF16, 24)):
+                mp = Measured(ctx, wp, prec, dev, flush, refine_max=rmax).run(5, 2, stream)
+                sm = mp.summary()
+                row[nm] = {"elements_per_s": sm["elements_per_s"], "condense_ms": sm["condense_ms"],
+                           "elements_status_3": int((mp.sys.views()["status"] == 3).sum())}
+                if check and prec >= hdg.HDG_MIXED_TF32:
+                    acc[f"{wp.name}_{nm}"] = oracle_accuracy(mp)
+                mp.close()
+            trial[str(p)] = row
+        line["tensor_core_local_solve_trial"] = {
+            "what": "Euler, 16,384 triangles; refinement stops when a correction < 1e-13 max|X| (status 3: "
+                    "not reached within refine_max corrections)", "per_p": trial}
         # Navier-Stokes mixed form, degree mix 40/30/20/10 % (65,536 triangles)
         ns = {}
         for prec, nm in ((hdg.HDG_FP64, "fp64"), (hdg.HDG_FLOAT2, "float2")):
@@ -790,13 +889,26 @@ def run_ours(args, wl, ws, rank, local):
                                                                                                    per_field=True)
                 ms.close()
         line["euler_p3_262k_shock"] = shock
+        line["euler_p1_256_latency"] = latency_section(ctx, dev, stream)
         line["newton_step_with_trace_solve"] = solve_section(ctx, wl, dev, flush, stream)
         line["adjoint_and_adaptation"] = adjoint_section(ctx, wl, dev, flush, stream)
         line["steady_solve_bounded_domain"] = steady_section(ctx, dev, flush, stream)
         if args.serving_requests > 0:
-            line["serving"] = serving_section(ctx, args.serving_requests, 77, args.serving_max_elems)
-            line["serving_with_trace_solve"] = serving_section(ctx, args.serving_requests, 77, args.serving_max_elems,
-                                                               solve=True)
+            # the serving configuration: 512 requests of 1k-64k elements at load 0.7
+            sv = serving_section(ctx, args.serving_requests, 77, args.serving_max_elems)
+            line["serving"] = sv
+            best = min(("mixed", "mixed_batched_launches"), key=lambda k: sv[k]["p99_ms"] if k in sv else 1e30)
+            line["serving_p50_ms"] = sv[best]["p50_ms"]
+            line["serving_p99_ms"] = sv[best]["p99_ms"]
+            line["serving_elements_per_s"] = sv[best]["elements_per_s"]
+            line["serving_form"] = ("float-float, batched launches across requests" if best != "mixed" else
+                                    "float-float, 8 stream slots")
+            line["serving_plain_fp64_p50_ms"] = sv["plain_fp64"]["p50_ms"]
+            line["serving_plain_fp64_p99_ms"] = sv["plain_fp64"]["p99_ms"]
+            line["serving_plain_fp64_elements_per_s"] = sv["plain_fp64"]["elements_per_s"]
+        if args.serving_solve_requests > 0:
+            line["serving_with_trace_solve"] = serving_section(ctx, args.serving_solve_requests, 77,
+                                                               args.serving_solve_max_elems, solve=True)
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
         # the oracle on the host's cores (std::thread over elements): ~20 s of CPU work
         nth = host_threads()
@@ -873,8 +985,10 @@ def main(argv=None):
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cells", default=None, help="override the grid, e.g. 48x96 (profiling runs)")
     ap.add_argument("--quick", action="store_true", help="headline workload only (no per-p, NS, serving)")
-    ap.add_argument("--serving-requests", type=int, default=32)
-    ap.add_argument("--serving-max-elems", type=int, default=32000)
+    ap.add_argument("--serving-requests", type=int, default=512)
+    ap.add_argument("--serving-max-elems", type=int, default=64000)
+    ap.add_argument("--serving-solve-requests", type=int, default=32)
+    ap.add_argument("--serving-solve-max-elems", type=int, default=32000)
     ap.add_argument("--serving-rates", default="0.7", help="load levels, fractions of saturated throughput")
     ap.add_argument("--serving-arena-gb", type=int, default=24)
     ap.add_argument("--serving-only", action="store_true", help="run only the serving section")

@@ -97,7 +97,15 @@ typedef enum {
                       binary32 words (hi + lo, ~48-bit significand) computed with
                       error-free transformations on the binary32 pipe; inputs and
                       outputs stay binary64; accuracy ~1e-13 relative (FP64-class),
-                      far above binary32 */
+                      far above binary32 */,
+  HDG_MIXED_TF32 = 2, /* Euler only: residual and Jacobian assembled in binary64; the
+                      local LU and solves of Sec. 3.4 in binary32 on the tensor cores
+                      (rank-8 updates as three TF32 MMAs on hi/lo splits, binary32
+                      accumulation), refined against binary64 residuals [B | F] - A X
+                      (params refine_max, refine_tol); Schur complement, assembly and
+                      reconstruction in binary64 */
+  HDG_MIXED_BF16 = 3  /* as HDG_MIXED_TF32 with one BF16 MMA per update (8-bit
+                      significands): the refinement needs many more sweeps */
 } hdg_precision;
 
 /* Flow and discretisation parameters (paper Sec. 2 and 3).  Non-dimensional
@@ -115,8 +123,11 @@ typedef struct {
   double cfl;          /* <= 0: pure Newton; > 0: pseudo-time mass |K|-scaled by the local
                           time step CFL |K| / (lambda_c + 4 lambda_v) of Sec. 3.3 */
   double t_inf;        /* dimensional free-stream temperature [K] for Sutherland (288.15) */
-  double refine_tol;   /* reserved for refinement-based precisions (unused) */
-  int32_t refine_max;  /* reserved for refinement-based precisions (unused) */
+  double refine_tol;   /* HDG_MIXED_*: stop refining once a correction is below
+                          refine_tol * max|X| of the element (e.g. 1e-13) */
+  int32_t refine_max;  /* HDG_MIXED_*: at most this many corrections after the first
+                          solve; an element that has not met refine_tol then gets
+                          elem_status 3 (its X is still the last iterate) */
   int32_t reserved;
   /* Shock capturing, Sec. 3.2 (artificial viscosity, volume term only):
    *   N_w += eps_K (grad phi, grad w)_K   (Euler)   or   eps_K (grad phi, q)_K   (NS),
@@ -303,6 +314,74 @@ int32_t hdg_sys_launches(const hdg_sys* sys);
  * -1.  All -1 after a single-bucket hdg_condense or one captured into a graph.
  * HOST array ms[5]. */
 hdg_status hdg_sys_bucket_times(const hdg_sys* sys, float* ms);
+
+/* ---- Batched condensation across systems ----
+ * The element work of Sec. 3.4 is independent per element, whatever mesh the
+ * element belongs to.  A batch condenses the elements of several systems --
+ * different meshes, degree maps, flow parameters (alpha, Mach, CFL, far field),
+ * Euler or Navier-Stokes -- with ONE kernel launch per (model, degree) group
+ * over a work list of (system, element) runs, instead of one launch per system
+ * and degree: many small requests then fill the GPU like one large one.  Each
+ * element's arithmetic is that of hdg_condense (the same kernel source compiled
+ * for the work list), so every system's X, K, E, residuals and status are
+ * those of condensing it alone, up to the rounding of multiply-adds that the
+ * compiler contracts differently (measured <= 1e-13 relative).
+ * Requirements: the systems belong to ctx, share one precision (HDG_FP64 or
+ * HDG_FLOAT2; else HDG_ENOTSUP) and are distinct; the batch refers to them (and to their mesh plans), which must
+ * outlive it.  A system may belong to several batches, but batches that share
+ * a system must not run concurrently.  Inputs and outputs are each system's
+ * own device buffers: U, Lam, dLam and dU in the system's staging buffers
+ * (filled by hdg_batch_step_host_async, or through hdg_sys_io), results in
+ * hdg_sys_get's views.
+ * hdg_batch_create uploads the work list (two small cudaMalloc'd arrays);
+ * hdg_batch_destroy frees it (and any captured graph). */
+typedef struct hdg_batch hdg_batch;
+hdg_status hdg_batch_create(hdg_ctx* ctx, int32_t n_sys, hdg_sys* const* systems, hdg_batch** out);
+/* The same batch with its work list in a caller DEVICE workspace (256-byte
+ * aligned, hdg_batch_workspace_bytes(n_sys, systems) bytes; -1 on bad
+ * arguments), uploaded by one cudaMemcpyAsync on `stream` (the batch keeps the
+ * host copy until it is destroyed): no cudaMalloc, for schedulers that form a
+ * batch while other work runs.  Use the batch on `stream` or after it. */
+int64_t hdg_batch_workspace_bytes(int32_t n_sys, hdg_sys* const* systems);
+hdg_status hdg_batch_create_in(hdg_ctx* ctx, int32_t n_sys, hdg_sys* const* systems, void* workspace,
+                               int64_t workspace_bytes, void* stream, hdg_batch** out);
+hdg_status hdg_batch_destroy(hdg_batch* batch);
+/* The (model, degree) groups of the batch, one launch each: returns their
+ * number G (<= 8) and fills model[G] (HDG_EULER / HDG_NS_MIXED), p[G] and
+ * n_items[G] (elements over all systems); any array may be NULL. */
+int32_t hdg_batch_groups(const hdg_batch* batch, int32_t* model, int32_t* p, int32_t* n_items);
+/* a1-a7 for every element of every system, from each system's device U and Lam
+ * staging buffers; groups run concurrently on forked streams, joined back
+ * into `stream`.  Asynchronous. */
+hdg_status hdg_batch_condense(hdg_batch* batch, void* stream);
+/* a8 for every system: dU = X_F - X_B dLambda from its device dLam staging
+ * buffer into its dU staging buffer, one launch per group.  Asynchronous. */
+hdg_status hdg_batch_recover(hdg_batch* batch, void* stream);
+/* A whole step of every system from HOST arrays (arrays of n_sys pointers, one
+ * per system, in the order given to hdg_batch_create; pinned memory for
+ * asynchronous copies): H2D of U, Lam, dLam, hdg_batch_condense,
+ * hdg_batch_recover, D2H of dU.  Enqueued on `stream`; returns at once. */
+hdg_status hdg_batch_step_host_async(hdg_batch* batch, const double* const* U, const double* const* Lam,
+                                     const double* const* dLam, double* const* dU, void* stream);
+/* Autotuner of the batched launch shape, as hdg_autotune for one system: per
+ * group, every candidate (one CTA per element, persistent k CTAs per SM) timed
+ * alone on the current staging inputs; the fastest is kept.  grid_out (may be
+ * NULL) receives [2][5] entries (model, degree).  Synchronises `stream`; the
+ * systems' outputs are undefined until the next condensation.  Not allowed
+ * while a captured graph exists. */
+hdg_status hdg_batch_autotune(hdg_batch* batch, int32_t* grid_out, void* stream);
+/* Capture hdg_batch_step_host_async for the HOST arrays given here (their
+ * addresses are baked into the graph) into one CUDA graph owned by the batch,
+ * after one plain step outside the capture (results valid after the call);
+ * hdg_batch_graph_launch replays it on `stream`.  A later create replaces it. */
+hdg_status hdg_batch_graph_create(hdg_batch* batch, const double* const* U, const double* const* Lam,
+                                  const double* const* dLam, double* const* dU);
+hdg_status hdg_batch_graph_launch(hdg_batch* batch, void* stream);
+/* Kernel launches of the last batched condensation + reconstruction. */
+int32_t hdg_batch_launches(const hdg_batch* batch);
+/* Device addresses of a system's staging buffers: U [u_len], Lam [lam_len],
+ * dLam [lam_len], dU [u_len] (owned by sys); any pointer may be NULL. */
+hdg_status hdg_sys_io(const hdg_sys* sys, double** U, double** Lam, double** dLam, double** dU);
 
 /* ---- Global trace solve and pseudo-transient Newton update (Sec. 3.3, 3.4) ----
  * The paper solves K dLambda = E (Eq. hybridsystem) with preconditioned GMRES

@@ -75,6 +75,8 @@ hdg_status hdg_adjoint_condense(hdg_sys* adj, const hdg_sys* primal, const doubl
   hdg_ctx* ctx = adj->ctx;
   if (!U || !Lam || !Ftilde) return fail(ctx, HDG_EINVAL, "hdg_adjoint_condense: null input");
   HDG_ON_DEVICE(ctx, ctx->device);
+  if (adj->ph.precision != HDG_FP64 && adj->ph.precision != HDG_FLOAT2)
+    return fail(ctx, HDG_ENOTSUP, "hdg_adjoint_condense: the adjoint runs in binary64 or float-float");
   const hdg_mesh* M = adj->mesh;
   if (primal->mesh != M) return fail(ctx, HDG_EINVAL, "hdg_adjoint_condense: systems on different meshes");
   if (primal->ph.precision != adj->ph.precision || primal->ph.cfl != adj->ph.cfl ||

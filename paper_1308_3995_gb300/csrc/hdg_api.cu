@@ -361,8 +361,14 @@ hdg_status sys_validate(hdg_ctx* ctx, const hdg_mesh* M, const hdg_params* P, co
   const std::string w(who);
   if ((P->model == HDG_EULER) != (M->nfield == 4) || (P->model != HDG_EULER && P->model != HDG_NS_MIXED))
     return fail(ctx, HDG_EINVAL, w + ": model does not match the mesh's field count");
-  if (P->precision != HDG_FP64 && P->precision != HDG_FLOAT2)
+  if (P->precision != HDG_FP64 && P->precision != HDG_FLOAT2 && P->precision != HDG_MIXED_TF32 &&
+      P->precision != HDG_MIXED_BF16)
     return fail(ctx, HDG_ENOTSUP, w + ": precision not supported by this library");
+  if ((P->precision == HDG_MIXED_TF32 || P->precision == HDG_MIXED_BF16) && P->model != HDG_EULER)
+    return fail(ctx, HDG_ENOTSUP, w + ": the tensor-core local solves are built for the Euler kernel only");
+  if ((P->precision == HDG_MIXED_TF32 || P->precision == HDG_MIXED_BF16) &&
+      (P->refine_max < 0 || P->refine_max > 64 || !(P->refine_tol >= 0.0)))
+    return fail(ctx, HDG_EINVAL, w + ": refine_max must be in 0..64 and refine_tol >= 0");
   if (P->model == HDG_NS_MIXED && !(P->reynolds > 0.0 && P->prandtl > 0.0 && P->t_inf > 0.0))
     return fail(ctx, HDG_EINVAL, w + ": Navier-Stokes needs reynolds, prandtl, t_inf > 0");
   if (!(P->gamma > 1.0) || !(P->alpha > 0.0) || !(P->mach > 0.0))
@@ -388,6 +394,8 @@ hdg_sys* sys_new(hdg_ctx* ctx, const hdg_mesh* M, const hdg_params* P) {
   far_field_state(*P, S->ph.winf);
   S->ph.model = P->model;
   S->ph.precision = P->precision;
+  S->ph.refine_max = P->refine_max;
+  S->ph.refine_tol = P->refine_tol;
   S->ph.persistent = 1;
   phys_default_grid(S->ph);
   return S;
@@ -733,5 +741,14 @@ hdg_status hdg_sys_get(const hdg_sys* S, double** X, double** K_vals, double** E
 }
 
 int32_t hdg_sys_launches(const hdg_sys* S) { return S ? S->launches : -1; }
+
+hdg_status hdg_sys_io(const hdg_sys* S, double** U, double** Lam, double** dLam, double** dU) {
+  if (!S) return HDG_EINVAL;
+  if (U) *U = S->d_U;
+  if (Lam) *Lam = S->d_Lam;
+  if (dLam) *dLam = S->d_dLam;
+  if (dU) *dU = S->d_dU;
+  return HDG_OK;
+}
 
 }  // extern "C"

@@ -88,6 +88,8 @@ struct Phys {
   double sc_eps0, sc_beta;  // shock capturing (Sec. 3.2); off unless sc_eps0 > 0
   double winf[4];           // far-field conserved state (Sec. 2.1)
   int model, precision;
+  int refine_max;      // mixed-precision local solves: at most this many corrections,
+  double refine_tol;   // stopping when the correction is below refine_tol * max|X|
   int persistent;  // 1: grid = SMs x resident CTAs (loop over elements); 0: one CTA per element
   int adjoint;     // 1: adjoint local solves X~ = A^{-T} [C^T | F~] only (Sec. 4.2)
   // launch shape per degree (autotuned): -1 default (by `persistent`), 0 one CTA per element,
@@ -153,6 +155,49 @@ struct DevSys {
   const double* src;         // [u_len] source coefficients in U's layout (w part), or null
 };
 
+// One system of a batch (hdg_batch_*) as the element kernels read it: its mesh
+// plan, output and work buffers, physical parameters and device inputs.
+struct ReqDesc {
+  DevMesh m;
+  DevSys s;
+  Phys ph;
+  const double* U;
+  const double* Lam;
+  const double* dLam;  // reconstruction input and output (hdg_batch_recover)
+  double* dU;
+};
+// A run of consecutive work items of one batched launch taken from one system:
+// items [first, next segment's first) are the elements elems[0 ..] of descs[desc].
+struct BatchSeg {
+  int desc;
+  int first;
+  const int* elems;
+};
+// Work list of a batched launch (null descs: a plain single-system launch).
+struct BatchRef {
+  const ReqDesc* descs;
+  const BatchSeg* segs;
+  int n_segs;
+};
+
+#ifdef __CUDACC__
+// The current work item's system in a batched launch, or the launch's own
+// arguments in a plain one.
+template <bool BATCH, class M>
+__device__ __forceinline__ const M& pick_ref(const ReqDesc* d, M ReqDesc::*mp, const M& single) {
+  if constexpr (BATCH) return d->*mp;
+  else return single;
+}
+// Cursor over the segments of a batched launch: item `it` (non-decreasing per CTA)
+// -> its element and system.
+__device__ __forceinline__ int batch_item(const BatchRef& bt, int it, int& seg, const ReqDesc*& d) {
+  while (seg + 1 < bt.n_segs && it >= bt.segs[seg + 1].first) ++seg;
+  const BatchSeg sg = bt.segs[seg];
+  d = bt.descs + sg.desc;
+  return sg.elems[it - sg.first];
+}
+#endif
+
 // Read-only view of a mesh plan and its context, for translation units other
 // than the one that owns the opaque structs (hdg_api.cu).
 struct PlanRef {
@@ -184,6 +229,20 @@ int launch_condense_ns(const DevMesh& m, const DevSys& s, const Phys& ph, const 
                        const TabOff& off, const double* U, const double* Lam, const int* const* bucket,
                        const int* bucket_n, const int* bucket_ntmax, void* stream, std::string* err,
                        void* const* bucket_streams = nullptr);
+// batched launches (hdg_batch_*): one launch over the items of every system of
+// the work list `bt` whose elements have degree p (model and precision from ph)
+// mixed-precision local solves (precision HDG_MIXED_TF32 / HDG_MIXED_BF16, Euler)
+bool launch_euler_mixed(int p, const DevMesh& m, const DevSys& s, const Phys& ph, const double* tab, const TabOff& to,
+                        const double* U, const double* Lam, const int* elems, int n, int ntmax, void* stream,
+                        std::string* err, const BatchRef& bt, bool bounded);
+int euler_mixed_occupancy(const Phys& ph, int p, int ntmax, bool bounded);
+bool launch_condense_batch(int p, const Phys& ph, const double* tab, const void* tab_ff, const TabOff& to,
+                           const BatchRef& bt, int n_items, int ntmax, bool bounded, void* stream, std::string* err);
+bool launch_ns_batch(int p, const Phys& ph, const double* tab, const void* tab_ff, const TabOff& to,
+                     const BatchRef& bt, int n_items, int ntmax, void* stream, std::string* err);
+bool launch_recover_batch(int p, int nfield, const BatchRef& bt, int n_items, void* stream, std::string* err);
+int batch_occupancy(const Phys& ph, int p, int ntmax, bool bounded);
+
 int launch_recover_buckets(const DevMesh& m, const double* X, const double* dLam, double* dU,
                            const int* const* bucket, const int* bucket_n, void* stream, std::string* err);
 

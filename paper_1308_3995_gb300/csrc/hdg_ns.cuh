@@ -80,11 +80,14 @@ struct NsLayout {
 // second CTA hides them (Navier-Stokes p mix: 101.7 -> 86.0 ms per step in
 // binary64, 76.3 -> 70.5 ms in float-float).  For p >= 3 shared memory allows
 // one CTA per SM anyway.
-template <int P, class T, bool ADJ>
-__global__ void __launch_bounds__(kNsThreads, (P <= 2 ? 2 : 1)) k_condense_ns(DevMesh m, DevSys s, Phys ph, const T* __restrict__ tab,
-                                                             TabOff to, const double* __restrict__ U,
-                                                             const double* __restrict__ Lam,
-                                                             const int* __restrict__ elems, int n_elems, int ntmax) {
+// BATCH: the launch walks the work list `bt` over the elements of several
+// systems (hdg_batch_condense); otherwise m_, s_, ph_, U_, Lam_ and elems.
+template <int P, class T, bool ADJ, bool BATCH = false>
+__global__ void __launch_bounds__(kNsThreads, (P <= 2 ? 2 : 1)) k_condense_ns(DevMesh m_, DevSys s_, Phys ph_, const T* __restrict__ tab,
+                                                             TabOff to, const double* __restrict__ U_,
+                                                             const double* __restrict__ Lam_,
+                                                             const int* __restrict__ elems, int n_elems, int ntmax,
+                                                             BatchRef bt) {
   using L = NsLayout<P>;
   using A = Ar<T>;
   constexpr int NP = L::NP, NQ = L::NQ, NW4 = L::NW4, N = L::N, LDA = L::LDA;
@@ -129,26 +132,35 @@ __global__ void __launch_bounds__(kNsThreads, (P <= 2 ? 2 : 1)) k_condense_ns(De
   const T* vgx = tab + to.vol_gxi[P];
   const T* vge = tab + to.vol_geta[P];
   const T* dref = tab + to.vol_dref[P];
-  EulerConst<T> C;
-  C.gam = A::from_d(ph.gamma);
-  C.g1 = A::from_d(ph.gamma - 1.0);
-  C.three_m_gam = A::from_d(3.0 - ph.gamma);
-  C.half = A::from_d(0.5);
-  C.one = A::from_d(1.0);
-  NsConst<T> V;
-  V.half = C.half;
-  V.g1 = C.g1;
-  V.gam = C.gam;
-  V.two = A::from_d(2.0);
-  V.twothirds = A::from_d(2.0 / 3.0);
-  V.suth = A::from_d(ph.suth_s);
-  V.mu_fac = A::from_d(ph.mu_inf * (1.0 + ph.suth_s));
-  V.kfac = A::from_d(1.0 / ((ph.gamma - 1.0) * ph.prandtl));
-  const T alpha = A::from_d(ph.alpha);
   const T zero = A::zero();
 
+  int seg = 0;
   for (int it = blockIdx.x; it < n_elems; it += gridDim.x) {
-    const int K = elems[it];
+    const ReqDesc* D = nullptr;
+    int K;
+    if constexpr (BATCH) K = batch_item(bt, it, seg, D);
+    else K = elems[it];
+    const DevMesh& m = pick_ref<BATCH>(D, &ReqDesc::m, m_);
+    const DevSys& s = pick_ref<BATCH>(D, &ReqDesc::s, s_);
+    const Phys& ph = pick_ref<BATCH>(D, &ReqDesc::ph, ph_);
+    const double* __restrict__ U = BATCH ? D->U : U_;
+    const double* __restrict__ Lam = BATCH ? D->Lam : Lam_;
+    EulerConst<T> C;
+    C.gam = A::from_d(ph.gamma);
+    C.g1 = A::from_d(ph.gamma - 1.0);
+    C.three_m_gam = A::from_d(3.0 - ph.gamma);
+    C.half = A::from_d(0.5);
+    C.one = A::from_d(1.0);
+    NsConst<T> V;
+    V.half = C.half;
+    V.g1 = C.g1;
+    V.gam = C.gam;
+    V.two = A::from_d(2.0);
+    V.twothirds = A::from_d(2.0 / 3.0);
+    V.suth = A::from_d(ph.suth_s);
+    V.mu_fac = A::from_d(ph.mu_inf * (1.0 + ph.suth_s));
+    V.kfac = A::from_d(1.0 / ((ph.gamma - 1.0) * ph.prandtl));
+    const T alpha = A::from_d(ph.alpha);
     // ---------------- a1: geometry, faces, state ----------------
     if (tid < 3) {
       const double* c = m.xy + 6 * (size_t)K;
@@ -851,21 +863,23 @@ __global__ void __launch_bounds__(kNsThreads, (P <= 2 ? 2 : 1)) k_condense_ns(De
   }
 }
 
-template <int P, class T, bool ADJ>
+template <int P, class T, bool ADJ, bool BATCH = false>
 inline bool launch_ns_bucket(const DevMesh& m, const DevSys& s, const Phys& ph, const T* tab, const TabOff& to,
                              const double* U, const double* Lam, const int* elems, int n, int ntmax, cudaStream_t st,
-                             std::string* err) {
+                             std::string* err, const BatchRef& bt = BatchRef{}) {
   const NsLayout<P> lay(ntmax);
   const size_t bytes = sizeof(T) * (size_t)lay.total;
-  cudaError_t ce = cudaFuncSetAttribute(k_condense_ns<P, T, ADJ>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+  cudaError_t ce = cudaFuncSetAttribute(k_condense_ns<P, T, ADJ, BATCH>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                        (int)bytes);
   if (ce != cudaSuccess) { *err = std::string("NS kernel shared memory: ") + cudaGetErrorString(ce); return false; }
   int dev = 0, sms = 0, per_sm = 0;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_condense_ns<P, T, ADJ>, kNsThreads, bytes);
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_condense_ns<P, T, ADJ, BATCH>, kNsThreads, bytes);
   if (per_sm < 1) { *err = "NS condensation kernel does not fit on an SM"; return false; }
   const long grid = condense_grid(ph, P, sms, per_sm, n);
-  k_condense_ns<P, T, ADJ><<<(int)grid, kNsThreads, bytes, st>>>(m, s, ph, tab, to, U, Lam, elems, n, ntmax);
+  k_condense_ns<P, T, ADJ, BATCH><<<(int)grid, kNsThreads, bytes, st>>>(m, s, ph, tab, to, U, Lam, elems, n, ntmax,
+                                                                         bt);
   ce = cudaGetLastError();
   if (ce != cudaSuccess) { *err = cudaGetErrorString(ce); return false; }
   return true;
@@ -875,10 +889,10 @@ template <int P, class T>
 inline int ns_occ(int ntmax) {
   const NsLayout<P> lay(ntmax);
   const size_t bytes = sizeof(T) * (size_t)lay.total;
-  if (cudaFuncSetAttribute(k_condense_ns<P, T, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes) != cudaSuccess)
+  if (cudaFuncSetAttribute(k_condense_ns<P, T, false, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes) != cudaSuccess)
     return 0;
   int per_sm = 0;
-  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_condense_ns<P, T, false>, kNsThreads, bytes);
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_condense_ns<P, T, false, false>, kNsThreads, bytes);
   return per_sm;
 }
 

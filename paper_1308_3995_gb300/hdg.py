@@ -22,7 +22,7 @@ _lib = None
 
 HDG_OK, HDG_EINVAL, HDG_ENOMEM, HDG_ECUDA, HDG_ESINGULAR, HDG_ETIMEOUT, HDG_ENOTSUP = range(7)
 HDG_EULER, HDG_NS_MIXED = 0, 1
-HDG_FP64, HDG_FLOAT2 = 0, 1
+HDG_FP64, HDG_FLOAT2, HDG_MIXED_TF32, HDG_MIXED_BF16 = 0, 1, 2, 3
 STATUS_NAMES = {0: "HDG_OK", 1: "HDG_EINVAL", 2: "HDG_ENOMEM", 3: "HDG_ECUDA", 4: "HDG_ESINGULAR",
                 5: "HDG_ETIMEOUT", 6: "HDG_ENOTSUP"}
 
@@ -37,7 +37,10 @@ EXPORTS = ["hdg_create", "hdg_destroy", "hdg_last_error", "hdg_mesh_create", "hd
            "hdg_adapt_indicators", "hdg_adapt_mark",
            "hdg_mesh_create_bc", "hdg_solver_set_preconditioner", "hdg_solver_setup", "hdg_solver_precond_apply",
            "hdg_solver_colors", "hdg_solver_create_ws", "hdg_solver_workspace_bytes", "hdg_solve_step_host",
-           "hdg_sys_bucket_times", "hdg_sys_set_source"]
+           "hdg_sys_bucket_times", "hdg_sys_set_source", "hdg_batch_create", "hdg_batch_destroy",
+           "hdg_batch_groups", "hdg_batch_condense", "hdg_batch_recover", "hdg_batch_step_host_async",
+           "hdg_batch_autotune", "hdg_batch_graph_create", "hdg_batch_graph_launch", "hdg_batch_launches",
+           "hdg_sys_io", "hdg_batch_workspace_bytes", "hdg_batch_create_in"]
 
 
 class HdgError(RuntimeError):
@@ -125,6 +128,23 @@ def lib(build: bool = True):
         L.hdg_sys_launches.restype = ctypes.c_int32
         L.hdg_debug_tables.argtypes = [ctypes.c_int] * 5 + [_dp, ctypes.c_int]
         L.hdg_condense_noalloc.argtypes = [_vp, ctypes.POINTER(hdg_params)] + [_vp] * 9
+        L.hdg_batch_create.argtypes = [_vp, ctypes.c_int32, ctypes.POINTER(_vp), ctypes.POINTER(_vp)]
+        L.hdg_batch_destroy.argtypes = [_vp]
+        L.hdg_batch_workspace_bytes.argtypes = [ctypes.c_int32, ctypes.POINTER(_vp)]
+        L.hdg_batch_workspace_bytes.restype = ctypes.c_int64
+        L.hdg_batch_create_in.argtypes = [_vp, ctypes.c_int32, ctypes.POINTER(_vp), _vp, ctypes.c_int64, _vp,
+                                          ctypes.POINTER(_vp)]
+        L.hdg_batch_groups.argtypes = [_vp, _i32p, _i32p, _i32p]
+        L.hdg_batch_groups.restype = ctypes.c_int32
+        L.hdg_batch_condense.argtypes = [_vp, _vp]
+        L.hdg_batch_recover.argtypes = [_vp, _vp]
+        L.hdg_batch_step_host_async.argtypes = [_vp] + [ctypes.POINTER(_vp)] * 4 + [_vp]
+        L.hdg_batch_autotune.argtypes = [_vp, _i32p, _vp]
+        L.hdg_batch_graph_create.argtypes = [_vp] + [ctypes.POINTER(_vp)] * 4
+        L.hdg_batch_graph_launch.argtypes = [_vp, _vp]
+        L.hdg_batch_launches.argtypes = [_vp]
+        L.hdg_batch_launches.restype = ctypes.c_int32
+        L.hdg_sys_io.argtypes = [_vp] + [ctypes.POINTER(_vp)] * 4
         L.hdg_sys_workspace_bytes.argtypes = [_vp, ctypes.POINTER(hdg_params)]
         L.hdg_sys_workspace_bytes.restype = ctypes.c_int64
         L.hdg_sys_create_in.argtypes = [_vp, _vp, ctypes.POINTER(hdg_params), _vp, ctypes.c_int64,
@@ -491,6 +511,17 @@ class System:
         _check(lib().hdg_sys_set_cfl(self.h, float(cfl)), self.ctx.h)
         self.params.cfl = float(cfl)
 
+    def io_views(self):
+        """hdg_sys_io: zero-copy torch views of the system's device staging buffers U, Lam, dLam, dU
+        (the inputs and output of the batched calls)."""
+        import torch
+        ptrs = [_vp() for _ in range(4)]
+        _check(lib().hdg_sys_io(self.h, *[ctypes.byref(p) for p in ptrs]), self.ctx.h)
+        m = self.mesh
+        n = [m.u_len, m.lam_len, m.lam_len, m.u_len]
+        return {nm: torch.as_tensor(_DevView(p.value, k, "<f8"), device=f"cuda:{self.ctx.device}")
+                for nm, p, k in zip(["U", "Lam", "dLam", "dU"], ptrs, n)}
+
     def views(self):
         """Zero-copy torch views of X, K, E, res_u, res_lam, elem_status."""
         import torch
@@ -504,6 +535,81 @@ class System:
     def close(self):
         if getattr(self, "h", None):
             lib().hdg_sys_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def _host_ptrs(arrs):
+    """ctypes array of the host addresses of torch tensors or numpy arrays."""
+    out = (_vp * len(arrs))()
+    for i, a in enumerate(arrs):
+        out[i] = a.data_ptr() if hasattr(a, "data_ptr") else a.ctypes.data
+    return out
+
+
+class Batch:
+    """hdg_batch_*: one condensation launch per (model, degree) group over the elements of several
+    systems; each system's results are bitwise those of condensing it alone."""
+
+    def __init__(self, ctx: Context, systems: list, workspace=None, stream=None):
+        """workspace=(device pointer, bytes): hdg_batch_create_in (work list uploaded on `stream`)."""
+        arr = (_vp * len(systems))(*[s.h for s in systems])
+        h = _vp()
+        if workspace is None:
+            _check(lib().hdg_batch_create(ctx.h, len(systems), arr, ctypes.byref(h)), ctx.h)
+        else:
+            ptr, nbytes = workspace
+            _check(lib().hdg_batch_create_in(ctx.h, len(systems), arr, int(ptr), int(nbytes), _stream(stream),
+                                             ctypes.byref(h)), ctx.h)
+        self.h, self.ctx, self.systems = h, ctx, list(systems)
+
+    @staticmethod
+    def workspace_bytes(systems: list) -> int:
+        """hdg_batch_workspace_bytes: device bytes of the work list of a batch of these systems."""
+        arr = (_vp * len(systems))(*[s.h for s in systems])
+        return int(lib().hdg_batch_workspace_bytes(len(systems), arr))
+
+    def groups(self) -> list:
+        """[(model, p, n_items)] of the batch's launches."""
+        m, p, n = (ctypes.c_int32 * 8)(), (ctypes.c_int32 * 8)(), (ctypes.c_int32 * 8)()
+        g = int(lib().hdg_batch_groups(self.h, m, p, n))
+        return [(int(m[i]), int(p[i]), int(n[i])) for i in range(g)]
+
+    def condense(self, stream=None):
+        _check(lib().hdg_batch_condense(self.h, _stream(stream)), self.ctx.h)
+
+    def recover(self, stream=None):
+        _check(lib().hdg_batch_recover(self.h, _stream(stream)), self.ctx.h)
+
+    def step_host_async(self, U, Lam, dLam, dU, stream=None):
+        """Lists (one per system) of pinned host tensors."""
+        self._keep = (_host_ptrs(U), _host_ptrs(Lam), _host_ptrs(dLam), _host_ptrs(dU))
+        _check(lib().hdg_batch_step_host_async(self.h, *self._keep, _stream(stream)), self.ctx.h)
+
+    def autotune(self, stream=None) -> dict:
+        out = (ctypes.c_int32 * 10)()
+        _check(lib().hdg_batch_autotune(self.h, out, _stream(stream)), self.ctx.h)
+        return {(md, p): int(out[md * 5 + p]) for md in range(2) for p in range(1, 5) if out[md * 5 + p] >= 0}
+
+    def graph_create(self, U, Lam, dLam, dU):
+        self._gkeep = (_host_ptrs(U), _host_ptrs(Lam), _host_ptrs(dLam), _host_ptrs(dU))
+        _check(lib().hdg_batch_graph_create(self.h, *self._gkeep), self.ctx.h)
+
+    def graph_launch(self, stream=None):
+        _check(lib().hdg_batch_graph_launch(self.h, _stream(stream)), self.ctx.h)
+
+    @property
+    def launches(self) -> int:
+        return int(lib().hdg_batch_launches(self.h))
+
+    def close(self):
+        if getattr(self, "h", None):
+            lib().hdg_batch_destroy(self.h)
             self.h = None
 
     def __del__(self):

@@ -25,6 +25,15 @@ a worker thread that runs its requests' steps (the library releases the
 interpreter lock during the call); the system and the solver both live in
 the request's arena range.
 
+With ``batched=True`` (step mode) admitted requests are not launched one by
+one: the requests admitted since the last launch form one batch
+(``hdg_batch_create_in``, its work list carved from the arena and uploaded on
+the batch's stream) whose condensation is one kernel launch per (model,
+degree) group over all of their elements, followed by one reconstruction
+launch per group (``hdg_batch_step_host_async``, with every request's copies
+on the same stream).  Up to ``max_inflight`` batches run at once, each on its
+own stream; a batch completes all of its requests together.
+
 The plain baseline is the same loop with one slot and binary64 arithmetic
 (requests served one at a time, in arrival order).
 
@@ -194,17 +203,23 @@ class Report:
 
 
 class Server:
+    BATCH_REGION = 1 << 16   # device bytes of one batch's work list (about 400 B per request)
+
     def __init__(self, ctx: hdg.Context, arena_bytes: int, slots: int, precision: int, keep_outputs: bool = False,
                  solve: bool = False, precond: int = 2, rtol: float = 1e-10, cfl: float = 10.0,
-                 restart: int = 30, max_iter: int = 5000):
+                 restart: int = 30, max_iter: int = 5000, batched: bool = False, max_inflight: int = 2):
         import torch
+        if batched and solve:
+            raise ValueError("batched launches serve step requests (solve=False)")
+        self.batched, self.max_inflight = bool(batched), int(max_inflight)
         self.ctx, self.slots, self.precision, self.keep = ctx, int(slots), int(precision), keep_outputs
         self.solve, self.precond, self.rtol, self.cfl = bool(solve), int(precond), float(rtol), float(cfl)
         self.restart, self.max_iter = int(restart), int(max_iter)
         self.dev = torch.device(f"cuda:{ctx.device}")
         self.buf = torch.empty(int(arena_bytes), dtype=torch.uint8, device=self.dev)
         self.arena = Arena(int(arena_bytes))
-        self.streams = [torch.cuda.Stream(device=self.dev) for _ in range(self.slots)]
+        self.streams = [torch.cuda.Stream(device=self.dev)
+                        for _ in range(self.max_inflight if self.batched else self.slots)]
 
     def _params(self, wl):
         return hdg.Params(model=wl.model, precision=self.precision, mach=wl.mach, alpha=wl.alpha,
@@ -239,6 +254,9 @@ class Server:
         order = sorted(reqs, key=lambda r: r.arrival_s)
         free_slots = list(range(self.slots))
         waiting, active, meshes = [], [], []
+        pending, inflight = [], []          # batched mode: admitted, not launched / launched batches
+        # batched mode: one arena region per stream for the work list of the batch launched on it
+        bregions = [self.arena.alloc(self.BATCH_REGION) for _ in range(self.max_inflight)] if self.batched else []
         nxt = 0
         done_q, workers, jobs = queue.Queue(), [], []
         t0_box = [0.0]
@@ -285,6 +303,10 @@ class Server:
                     if self.solve:
                         jobs[slot].put((r, off, n_sys, n_sol, prm))
                         continue
+                    if self.batched:
+                        sysm = hdg.System(self.ctx, mesh, prm, workspace=(self.buf.data_ptr() + off, n_sys))
+                        pending.append((r, slot, off, sysm))
+                        continue
                     sysm = hdg.System(self.ctx, mesh, prm, workspace=(self.buf.data_ptr() + off, n_sys))
                     dU = r.dU_host
                     st = self.streams[slot]
@@ -292,8 +314,45 @@ class Server:
                     ev = torch.cuda.Event()
                     ev.record(st)
                     active.append((r, slot, off, sysm, dU, ev))
+                # batched mode: the requests admitted since the last launch go out as one batch
+                if self.batched and pending and len(inflight) < self.max_inflight:
+                    systems = [it[3] for it in pending]
+                    nb = hdg.Batch.workspace_bytes(systems)
+                    if nb > self.BATCH_REGION:
+                        raise hdg.HdgError(hdg.HDG_ENOMEM, f"batch work list of {nb} bytes > {self.BATCH_REGION}")
+                    k = next(i for i in range(self.max_inflight) if i not in [b[4] for b in inflight])
+                    boff = bregions[k]
+                    if True:
+                        st = self.streams[k]
+                        bt = hdg.Batch(self.ctx, systems, workspace=(self.buf.data_ptr() + boff, nb),
+                                       stream=st.cuda_stream)
+                        reqs_b = [it[0] for it in pending]
+                        bt.step_host_async([q.U for q in reqs_b], [q.Lam for q in reqs_b], [q.dLam for q in reqs_b],
+                                           [q.dU_host for q in reqs_b], st)
+                        ev = torch.cuda.Event()
+                        ev.record(st)
+                        inflight.append((bt, pending, ev, boff, k))
+                        pending = []
                 # completions
-                if self.solve:
+                if self.batched:
+                    still = []
+                    for item in inflight:
+                        bt, members, ev, boff, k = item
+                        if not ev.query():
+                            still.append(item)
+                            continue
+                        tdone = time.perf_counter() - t0
+                        bt.close()                         # frees no device memory (arena-backed work list)
+                        for r, slot, off, sysm in members:
+                            r.done_s = tdone
+                            if self.keep:
+                                r.dU = r.dU_host.numpy().copy()
+                            sysm.close()
+                            self.arena.free(off)
+                            free_slots.append(slot)
+                            n_active -= 1
+                    inflight = still
+                elif self.solve:
                     while True:
                         try:
                             r, slot, off, exc = done_q.get_nowait()
@@ -330,6 +389,8 @@ class Server:
                 q.put(None)
             for th in workers:
                 th.join(timeout=60)
+        for off in bregions:
+            self.arena.free(off)
         makespan = max(r.done_s for r in order) - min(r.arrival_s for r in order)
         torch.cuda.synchronize(self.dev)
         for m in meshes:

@@ -93,6 +93,42 @@ def test_each_result_is_the_same_alone_and_in_the_mix():
         plain.run([r], "plain")
         err = np.linalg.norm(r.dU - in_mix[r.rid]) / np.linalg.norm(r.dU)
         assert err < 1e-10, (r.rid, err)
+    # the served float-float steps against the oracle's condensation and reconstruction
+    _check_against_oracle(sorted(reqs, key=lambda q: q.n_elem)[:2], in_mix, 1e-10)
+
+
+def _check_against_oracle(reqs, results, bar):
+    import oracle as O
+    from hdg_testlib import oracle_params
+    for r in reqs:
+        c = r.case
+        om = O.Mesh(c.mesh.elem_xy, c.mesh.elem_vid, c.elem_p, c.nfield, c.mesh.elem_bc)
+        res = om.condense(oracle_params(r.wl), r.U.numpy(), r.Lam.numpy())
+        dU = om.recover(res["X"], r.dLam.numpy())
+        err = np.linalg.norm(results[r.rid] - dU) / np.linalg.norm(dU)
+        assert err < bar, (r.rid, err)
+
+
+@pytest.mark.gpu
+def test_batched_launches_give_each_result_as_alone():
+    """Requests admitted together are condensed by one launch per (model, degree) group; each
+    result is the one the request gets alone (own launches, one slot) within 1e-12, and matches
+    the oracle at the mixed-precision bar."""
+    from paper_1308_3995_gb300 import hdg
+    ctx = hdg.Context(0)
+    reqs = SV.prepare(ctx, _small_stream(10, seed=13))
+    batched = SV.Server(ctx, arena_bytes=2 << 30, slots=8, precision=hdg.HDG_FLOAT2, keep_outputs=True,
+                        batched=True, max_inflight=2)
+    rep = batched.run(reqs, "batched")
+    assert rep.n == 10 and batched.arena.bytes_used == 0
+    in_batch = {r.rid: r.dU.copy() for r in reqs}
+    alone = SV.Server(ctx, arena_bytes=2 << 30, slots=1, precision=hdg.HDG_FLOAT2, keep_outputs=True)
+    for r in reqs:
+        r.arrival_s = 0.0
+        alone.run([r], "alone")
+        err = np.linalg.norm(r.dU - in_batch[r.rid]) / np.linalg.norm(r.dU)
+        assert err <= 1e-12, (r.rid, err)
+    _check_against_oracle(sorted(reqs, key=lambda q: q.n_elem)[:2], in_batch, 1e-10)
 
 
 @pytest.mark.gpu
@@ -120,21 +156,24 @@ def test_admission_waits_for_arena_room_and_rejects_oversize():
 
 @pytest.mark.gpu
 def test_solve_mode_requests_match_the_oracle_newton_step():
-    """Requests as whole Newton steps (condensation at CFL 10, GPU trace solve to 1e-10 with
-    block ILU(0), reconstruction): each result is bitwise the same alone and in the mix, and the
-    smallest ones agree with the oracle's dense solve of its own K, E and its reconstruction."""
+    """Requests as whole Newton steps (condensation at CFL 10, GPU trace solve with block ILU(0),
+    here to a relative residual of 1e-13, reconstruction): each result is bitwise the same alone and
+    in the mix, and the smallest ones agree with the oracle's dense solve of its own K, E and its
+    reconstruction within the mixed-precision bar 1e-10."""
     import oracle as O
     from hdg_testlib import oracle_params
     from paper_1308_3995_gb300 import hdg
     ctx = hdg.Context(0)
     wls = SV.request_workloads(6, seed=21, min_elems=60, max_elems=400)
     reqs = SV.prepare(ctx, [SV.Request(i, 0.002 * i, w) for i, w in enumerate(wls)])
-    mixed = SV.Server(ctx, arena_bytes=2 << 30, slots=3, precision=hdg.HDG_FLOAT2, keep_outputs=True, solve=True)
+    mixed = SV.Server(ctx, arena_bytes=2 << 30, slots=3, precision=hdg.HDG_FLOAT2, keep_outputs=True, solve=True,
+                      rtol=1e-13)
     rep = mixed.run(reqs, "mixed-solve")
     assert rep.n == 6 and len(rep.gmres_iterations) == 6 and min(rep.gmres_iterations) > 0
     assert mixed.arena.bytes_used == 0
     in_mix = {r.rid: (r.dU.copy(), r.dLam_host.numpy().copy()) for r in reqs}
-    alone = SV.Server(ctx, arena_bytes=2 << 30, slots=1, precision=hdg.HDG_FLOAT2, keep_outputs=True, solve=True)
+    alone = SV.Server(ctx, arena_bytes=2 << 30, slots=1, precision=hdg.HDG_FLOAT2, keep_outputs=True, solve=True,
+                      rtol=1e-13)
     for r in reqs:
         r.arrival_s = 0.0
         alone.run([r], "alone")
@@ -148,4 +187,4 @@ def test_solve_mode_requests_match_the_oracle_newton_step():
         eL = np.linalg.norm(in_mix[r.rid][1] - dL) / np.linalg.norm(dL)
         eU = np.linalg.norm(in_mix[r.rid][0] - dU) / np.linalg.norm(dU)
         print(r.wl.name, r.n_elem, "elements, iterations", r.iters, f"dLambda {eL:.1e} dU {eU:.1e}")
-        assert eL < 1e-7 and eU < 1e-7
+        assert eL < 1e-10 and eU < 1e-10
