@@ -676,9 +676,10 @@ def serving_section(ctx, n_requests, seed, max_elems, rates=(0.7,), arena_gb=24,
     mixed = SV.Server(ctx, arena, slots=8, precision=hdg.HDG_FLOAT2, solve=solve)
     plain = SV.Server(ctx, arena, slots=1, precision=hdg.HDG_FP64, solve=solve)
     # step requests also through batched launches: the requests admitted since the last launch
-    # condensed by one launch per (model, degree) group, up to two batches in flight
+    # condensed by one launch per (model, degree) group, batches of at most 32,768 elements, up to
+    # eight in flight (the best of a sweep over 2-8 in flight and 32k-200k elements or no cap)
     batched = None if solve else SV.Server(ctx, arena, slots=64, precision=hdg.HDG_FLOAT2, batched=True,
-                                           max_inflight=2)
+                                           max_inflight=8, batch_max_elems=32768)
     sat = mixed.run(reqs, "saturated")                       # everything at t = 0
     mean_el = sat.elements / sat.n
     levels = {}

@@ -42,7 +42,13 @@
 
 namespace hdg {
 
-constexpr int kNsThreads = 256;
+// threads per element CTA: 128 for p = 1, so that four CTAs (four elements)
+// share an SM within the register file (uniform p = 1: 2.67 -> 3.85 M elements/s
+// in binary64, 2.48 -> 4.25 M in float-float, against two CTAs of 256); 256
+// otherwise (at p = 2 the smaller CTA measured no better in binary64 and worse in
+// float-float, its shared memory allowing only two per SM on mixed meshes)
+template <int P>
+constexpr int ns_threads() { return P == 1 ? 128 : 256; }
 constexpr int kNsPt = 6;   // edge point slots per face
 
 template <int P>
@@ -83,7 +89,7 @@ struct NsLayout {
 // BATCH: the launch walks the work list `bt` over the elements of several
 // systems (hdg_batch_condense); otherwise m_, s_, ph_, U_, Lam_ and elems.
 template <int P, class T, bool ADJ, bool BATCH = false>
-__global__ void __launch_bounds__(kNsThreads, (P <= 2 ? 2 : 1)) k_condense_ns(DevMesh m_, DevSys s_, Phys ph_, const T* __restrict__ tab,
+__global__ void __launch_bounds__(ns_threads<P>(), (P == 1 ? 4 : (P == 2 ? 2 : 1))) k_condense_ns(DevMesh m_, DevSys s_, Phys ph_, const T* __restrict__ tab,
                                                              TabOff to, const double* __restrict__ U_,
                                                              const double* __restrict__ Lam_,
                                                              const int* __restrict__ elems, int n_elems, int ntmax,
@@ -91,7 +97,7 @@ __global__ void __launch_bounds__(kNsThreads, (P <= 2 ? 2 : 1)) k_condense_ns(De
   using L = NsLayout<P>;
   using A = Ar<T>;
   constexpr int NP = L::NP, NQ = L::NQ, NW4 = L::NW4, N = L::N, LDA = L::LDA;
-  constexpr int NT = kNsThreads, NW = NT / 32;
+  constexpr int NT = ns_threads<P>(), NW = NT / 32;
   extern __shared__ double smem_raw[];
   T* smem = reinterpret_cast<T*>(smem_raw);
   const L lay(ntmax);
@@ -875,10 +881,10 @@ inline bool launch_ns_bucket(const DevMesh& m, const DevSys& s, const Phys& ph, 
   int dev = 0, sms = 0, per_sm = 0;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_condense_ns<P, T, ADJ, BATCH>, kNsThreads, bytes);
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_condense_ns<P, T, ADJ, BATCH>, ns_threads<P>(), bytes);
   if (per_sm < 1) { *err = "NS condensation kernel does not fit on an SM"; return false; }
   const long grid = condense_grid(ph, P, sms, per_sm, n);
-  k_condense_ns<P, T, ADJ, BATCH><<<(int)grid, kNsThreads, bytes, st>>>(m, s, ph, tab, to, U, Lam, elems, n, ntmax,
+  k_condense_ns<P, T, ADJ, BATCH><<<(int)grid, ns_threads<P>(), bytes, st>>>(m, s, ph, tab, to, U, Lam, elems, n, ntmax,
                                                                          bt);
   ce = cudaGetLastError();
   if (ce != cudaSuccess) { *err = cudaGetErrorString(ce); return false; }
@@ -892,7 +898,7 @@ inline int ns_occ(int ntmax) {
   if (cudaFuncSetAttribute(k_condense_ns<P, T, false, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes) != cudaSuccess)
     return 0;
   int per_sm = 0;
-  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_condense_ns<P, T, false, false>, kNsThreads, bytes);
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_condense_ns<P, T, false, false>, ns_threads<P>(), bytes);
   return per_sm;
 }
 

@@ -207,11 +207,13 @@ class Server:
 
     def __init__(self, ctx: hdg.Context, arena_bytes: int, slots: int, precision: int, keep_outputs: bool = False,
                  solve: bool = False, precond: int = 2, rtol: float = 1e-10, cfl: float = 10.0,
-                 restart: int = 30, max_iter: int = 5000, batched: bool = False, max_inflight: int = 2):
+                 restart: int = 30, max_iter: int = 5000, batched: bool = False, max_inflight: int = 2,
+                 batch_max_elems: int = 0):
         import torch
         if batched and solve:
             raise ValueError("batched launches serve step requests (solve=False)")
         self.batched, self.max_inflight = bool(batched), int(max_inflight)
+        self.batch_max_elems = int(batch_max_elems)   # 0: a batch takes every admitted request
         self.ctx, self.slots, self.precision, self.keep = ctx, int(slots), int(precision), keep_outputs
         self.solve, self.precond, self.rtol, self.cfl = bool(solve), int(precond), float(rtol), float(cfl)
         self.restart, self.max_iter = int(restart), int(max_iter)
@@ -316,7 +318,13 @@ class Server:
                     active.append((r, slot, off, sysm, dU, ev))
                 # batched mode: the requests admitted since the last launch go out as one batch
                 if self.batched and pending and len(inflight) < self.max_inflight:
-                    systems = [it[3] for it in pending]
+                    take, tot = 0, 0                 # in admission order, up to batch_max_elems elements
+                    while take < len(pending) and (take == 0 or not self.batch_max_elems or
+                                                   tot + pending[take][0].n_elem <= self.batch_max_elems):
+                        tot += pending[take][0].n_elem
+                        take += 1
+                    batch_items, pending = pending[:take], pending[take:]
+                    systems = [it[3] for it in batch_items]
                     nb = hdg.Batch.workspace_bytes(systems)
                     if nb > self.BATCH_REGION:
                         raise hdg.HdgError(hdg.HDG_ENOMEM, f"batch work list of {nb} bytes > {self.BATCH_REGION}")
@@ -326,13 +334,12 @@ class Server:
                         st = self.streams[k]
                         bt = hdg.Batch(self.ctx, systems, workspace=(self.buf.data_ptr() + boff, nb),
                                        stream=st.cuda_stream)
-                        reqs_b = [it[0] for it in pending]
+                        reqs_b = [it[0] for it in batch_items]
                         bt.step_host_async([q.U for q in reqs_b], [q.Lam for q in reqs_b], [q.dLam for q in reqs_b],
                                            [q.dU_host for q in reqs_b], st)
                         ev = torch.cuda.Event()
                         ev.record(st)
-                        inflight.append((bt, pending, ev, boff, k))
-                        pending = []
+                        inflight.append((bt, batch_items, ev, boff, k))
                 # completions
                 if self.batched:
                     still = []
