@@ -445,9 +445,14 @@ def solve_section(ctx, wl, dev, flush, stream, cfl=10.0, rtol=1e-10, reps=3):
     m.sys.set_cfl(cfl)
     x = torch.zeros(m.mesh.lam_len, dtype=torch.float64, device=dev)
     y = torch.empty_like(x)
-    out = {"workload": wl.name, "cfl": cfl, "rtol": rtol, "restart": 30}
-    for precond, nm in ((0, "block_jacobi"), (1, "block_sgs"), (2, "block_ilu0"), (3, "block_ilu0_f32")):
+    out = {"workload": wl.name, "cfl": cfl, "rtol": rtol, "restart": 30,
+           "arithmetic": "binary64; *_ff: GMRES products, sweeps and Gram-Schmidt in double-word arithmetic on the "
+                         "binary32 pipe (hdg_solver_set_arithmetic 1)"}
+    for precond, nm, arith in ((0, "block_jacobi", 0), (0, "block_jacobi_ff", 1), (1, "block_sgs", 0),
+                               (1, "block_sgs_ff", 1), (2, "block_ilu0", 0), (2, "block_ilu0_ff", 1),
+                               (3, "block_ilu0_f32", 0), (3, "block_ilu0_f32_ff", 1)):
         solver = hdg.Solver(m.sys, restart=30, precond=precond)
+        solver.set_arithmetic(arith)
         res = []
         for r in range(reps + 1):
             U, L = m.Ut.clone(), m.Lt.clone()
@@ -456,15 +461,20 @@ def solve_section(ctx, wl, dev, flush, stream, cfl=10.0, rtol=1e-10, reps=3):
             t0 = time.perf_counter()
             m.sys.condense(U, L, stream)
             x.zero_()
+            torch.cuda.synchronize()
+            t1 = time.perf_counter()
             it, rel = solver.solve(x, rtol=rtol, max_iter=3000, stream=stream)
+            t2 = time.perf_counter()
             m.sys.recover(x, m.dUt, stream)
             m.sys.newton_update(U, L, m.dUt, x, stream)
             torch.cuda.synchronize()
             if r > 0:
-                res.append((time.perf_counter() - t0, it, rel))
-        out[nm] = {"newton_step_ms": 1e3 * statistics.median(t for t, _, _ in res),
-                   "gmres_iterations": res[-1][1], "rel_residual": res[-1][2]}
-        if precond == 0:
+                res.append((time.perf_counter() - t0, t2 - t1, it, rel))
+        it_ = res[-1][2]
+        solve_ms = 1e3 * statistics.median(t for _, t, _, _ in res)
+        out[nm] = {"newton_step_ms": 1e3 * statistics.median(t for t, _, _, _ in res), "solve_ms": solve_ms,
+                   "gmres_iterations": it_, "ms_per_iteration": solve_ms / max(it_, 1), "rel_residual": res[-1][3]}
+        if precond == 0 and arith == 0:
             # matrix-vector product bandwidth (K values + x gathers + y), CUDA events on the stream
             nmv = 20
             k_bytes = 8 * m.mesh.k_len
@@ -478,7 +488,7 @@ def solve_section(ctx, wl, dev, flush, stream, cfl=10.0, rtol=1e-10, reps=3):
             mv_s = ev0.elapsed_time(ev1) * 1e-3 / nmv
             out["matvec"] = {"k_mb": k_bytes / 1e6, "ms": 1e3 * mv_s, "k_gbs": k_bytes / mv_s / 1e9,
                              "frac_of_hbm": k_bytes / mv_s / 1e9 / HBM_PEAK_GBS}
-        if precond >= 2:
+        if precond >= 2 and arith == 0:
             # factorization (copy of K + one launch per color) and one application M^{-1} r
             ev0, ev1, ev2 = (torch.cuda.Event(enable_timing=True) for _ in range(3))
             ev0.record(stream)

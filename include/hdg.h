@@ -448,6 +448,35 @@ hdg_status hdg_trace_solve(hdg_solver* solver, double* dLam, double rtol, int32_
  * the same factors).  Returns HDG_EINVAL for any other kind. */
 hdg_status hdg_solver_set_preconditioner(hdg_solver* solver, int32_t kind);
 
+/* Arithmetic of the GMRES iterations of hdg_trace_solve / hdg_trace_solve_ex /
+ * hdg_solve_step_host (no counterpart in the paper, which solves in binary64):
+ * 0 binary64 throughout (default); 1 double-word ("float-float") arithmetic on
+ * the binary32 pipe for the preconditioned products, the preconditioner
+ * sweeps, the Gram-Schmidt dot products and updates and the solution update.
+ * Under 1 every solve first copies K (and, for kind 2, the binary64 ILU
+ * factors and their pivot inverses) into float-float pairs (hi, lo: the
+ * leading 24 and next 23 significand bits, integer split,
+ * |hi + lo - v| < 2^-46 |v|), kind 3's binary32 factors as they are, each
+ * block reordered for the product kernel (for K or for K^T, by the solve's
+ * transpose flag); kinds 0 and 1 compute their block pivot inverses in
+ * binary32 (a fixed preconditioner: the system solved and the accuracy
+ * reached are unchanged, only the convergence rate may differ).  The solve
+ * then runs on float-float copies of E and x, the Krylov basis stored as
+ * pairs in the same 8 bytes per value; x is rounded back to binary64 at the
+ * end.  Relative error of a product or dot product ~2^-46 of the magnitudes
+ * summed.  On GB300 a binary64 product of 0.25 flop per byte is bound by the
+ * binary64 pipe before HBM; in arith 1 it streams the same bytes on the
+ * binary32 pipe.  The first call with arith 1 (and a later change to kind 2
+ * or 3) allocates the copies: 8 bytes per value of K and of the pivot
+ * inverses (twice that for kinds 2 and 3) plus two vectors; HDG_ENOMEM if
+ * that fails or if the solver lives in a caller's workspace
+ * (hdg_solver_create_ws plans no room for them).  After a solve in arith 1
+ * with kind 0 or 1 the binary64 pivot inverses are not current:
+ * hdg_solver_precond_apply then needs hdg_solver_setup first.  The
+ * Hessenberg least-squares problem and hdg_trace_matvec stay binary64.
+ * HDG_EINVAL for any other value. */
+hdg_status hdg_solver_set_arithmetic(hdg_solver* solver, int32_t arith);
+
 /* Factor the preconditioner of the solver's kind for the system's current K
  * (enqueued on `stream`, then `stream` is synchronised).  hdg_trace_solve*
  * does this itself at every call; it is needed before

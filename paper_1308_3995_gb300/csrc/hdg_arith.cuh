@@ -71,6 +71,26 @@ __device__ __forceinline__ double ff_to_double(ff v) {
   return __longlong_as_double((long long)d);
 }
 
+// binary64 -> float-float without the FP64 pipe: hi = the leading 24
+// significand bits of d, lo = the next 23 (both truncated, so |lo| < ulp(hi)
+// and |hi + lo - d| < 2^-46 |d|), from the two 32-bit halves of the bit
+// pattern: hi by re-basing the exponent, lo as the integer of the next 23 bits
+// (made a float exactly by the 2^23 magic-number subtraction) times 2^(e - 46).
+// |d| < 2^-126 flushes to zero; for 2^-126 <= |d| < 2^-80 lo is dropped (24
+// bits kept); |d| >= 2^128 becomes +-inf; NaN stays NaN.
+__device__ __forceinline__ ff ff_split_double(double d) {
+  const unsigned int hw = (unsigned int)__double2hiint(d), lw = (unsigned int)__double2loint(d);
+  const unsigned int sign = hw & 0x80000000u;
+  const unsigned int ex = (hw >> 20) & 0x7ffu;
+  if (ex <= 896u) return {__uint_as_float(sign), 0.0f};
+  if (ex >= 1151u)
+    return {__uint_as_float(sign | 0x7f800000u | ((ex == 2047u && ((hw & 0xfffffu) | lw)) ? 0x400000u : 0u)), 0.0f};
+  const float hi = __uint_as_float(sign | ((ex - 896u) << 23) | ((hw & 0xfffffu) << 3) | (lw >> 29));
+  const float r = __uint_as_float(0x4b000000u | ((lw & 0x1fffffffu) >> 6)) - 8388608.0f;  // exact, < 2^23
+  const float lo = (ex >= 943u) ? r * __uint_as_float((ex - 942u) << 23) : 0.0f;       // r * 2^(e - 46)
+  return {hi, __uint_as_float(__float_as_uint(lo) | sign)};
+}
+
 template <class T>
 struct Ar;
 

@@ -2,53 +2,56 @@
 // pseudo-transient Newton update (Sec. 3.3) on the GPU.
 //
 // The paper uses ILU(n)-preconditioned GMRES from PETSc on the CPU.  Here:
-// restarted GMRES, left-preconditioned, binary64 throughout, with one of
+// restarted GMRES, left-preconditioned, with one of
 //   0 block Jacobi (the inverses of K's diagonal face blocks),
 //   1 multicolor block symmetric Gauss-Seidel,
 //   2 block ILU(0) in the multicolor order of the faces (faces of one color
 //     share no element, so their rows are uncoupled: each color is factored,
-//     and swept in the triangular solves, by one launch).
+//     and swept in the triangular solves, by one launch),
+//   3 the same with binary32 factors,
+// and one of two arithmetics for the products and Krylov updates:
+//   0 binary64 (the FP64 pipe), vectors in binary64;
+//   1 double-word (float-float) arithmetic on the binary32 pipe, on a
+//     float-float copy of K (and of the factors) made once per solve, vectors
+//     stored as float-float pairs in the same 8 bytes per value.
 // Kernels:
 //   k_bj_invert   one warp per face: Gauss-Jordan with partial pivoting of the
 //                 face's diagonal block (m = 4 (p_e + 1) <= 20 rows);
 //   k_ilu_row     one warp per face of one color: the face's block row of the
 //                 incomplete factors, then the inverse of its pivot block;
 //   k_face_op     one warp per face: t = (K x)_e (each block staged through
-//                 shared memory with coalesced loads, one lane per row, the
-//                 five blocks of the face row in column order; optionally only
-//                 the blocks of earlier or of later colors), then, by mode,
-//                 y_e = t, Dinv_e t, Dinv_e (b_e - t), Dinv_e b_e or b_e - t;
-//   k_dots_slab   dot products of one vector with the Krylov vectors, one
-//                 contiguous slab of rows per block, vectors over its warps;
-//                 k_reduce sums the per-block partials in a fixed order
-//                 (bitwise reproducible);
-//   k_axpy_v      w -= V c (c on the device), fused with ||w||^2 for the
-//                 second Gram-Schmidt pass (reduced by the last block to
-//                 finish, in a fixed order);
-//   k_multiaxpy   x += V y at the end of a restart cycle.
-// The Arnoldi process uses classical Gram-Schmidt with one
-// re-orthogonalisation pass; the small Hessenberg
-// least-squares problem (Givens rotations) is solved on the host, one residual
-// estimate read back per iteration.
+//   (_ff)         shared memory with coalesced loads, the five blocks of the
+//                 face row in column order; optionally only the blocks of
+//                 earlier or of later colors), then, by mode, y_e = t,
+//                 Dinv_e t, Dinv_e (b_e - t), Dinv_e b_e or b_e - t;
+//   hdg_krylov.cuh  the Arnoldi process as delayed classical Gram-Schmidt
+//                 with re-orthogonalisation: per iteration one reduction
+//                 pass (with the Hessenberg column, its Givens rotation and
+//                 the residual estimate in its last block) and one update
+//                 pass over the basis; the triangular least-squares solve
+//                 k_lsq and x += V y, all on the device (the state is read
+//                 back once per chunk of iterations).
 #include <cuda_runtime.h>
 
 #include <algorithm>
 #include <cmath>
 #include <cstring>
 #include <string>
+#include <type_traits>
 #include <vector>
 
+#include "hdg_arith.cuh"
 #include "hdg_internal.h"
+#include "hdg_krylov.cuh"
 #include "hdg_objects.h"
 
 using namespace hdg;
+using namespace hdg::krylov;
 
 namespace {
 
-constexpr int kMaxRestart = 64;
 constexpr int kFaceWarps = 4;          // faces per CTA in the per-face kernels
 constexpr int kMaxM = 4 * (kMaxP + 1);  // largest face block (20)
-constexpr int kDotThreads = 256;
 constexpr int kDotChunk = 8;           // vectors per k_dots block row
 
 // MT: value type of the stored matrix and pivot inverses (binary64, or binary32
@@ -68,6 +71,16 @@ struct FaceDevT {
   int* bad;                 // set to 1 if a diagonal block is singular
 };
 using FaceDev = FaceDevT<double>;
+
+// Lane order of the double-word face operator's matrix copies: a face with m
+// rows splits a warp into nseg segments (32 / m rounded down to a power of
+// two); lane r + m sg takes row r and the columns sg, sg + nseg, ...; entry
+// (r, c) of one of its blocks sits at lane_order(r, c, m) within the block.
+__host__ __device__ __forceinline__ int lane_segments(int m) { return m <= 8 ? 4 : (m <= 16 ? 2 : 1); }
+__host__ __device__ __forceinline__ int64_t lane_order(int r, int c, int m) {
+  const int ns = lane_segments(m);
+  return (int64_t)(c / ns) * (m * ns) + r + m * (c % ns);
+}
 
 // ---------------------------------------------------------------- block Jacobi
 // Gauss-Jordan inversion with partial pivoting (largest |a_rk|, first on ties)
@@ -114,39 +127,52 @@ __device__ bool warp_gj_invert(VT (*a)[2 * kMaxM + 1], int m, int lane) {
   return true;
 }
 
-template <class VT>
-__device__ void load_aug(VT (*a)[2 * kMaxM + 1], const VT* D, int m, int lane) {
+template <class VT, class DT>
+__device__ void load_aug(VT (*a)[2 * kMaxM + 1], const DT* D, int m, int lane) {
   const int m2 = 2 * m;
   for (int t = lane; t < m * m2; t += 32) {
     const int r = t / m2, c = t - r * m2;
-    a[r][c] = (c < m) ? D[r * m + c] : (c - m == r ? (VT)1 : (VT)0);
+    a[r][c] = (c < m) ? (VT)D[r * m + c] : (c - m == r ? (VT)1 : (VT)0);
   }
   __syncwarp();
 }
 
-template <class VT>
-__device__ void store_inverse(VT (*a)[2 * kMaxM + 1], VT* out, int m, int lane) {
+__device__ __forceinline__ double out_value(double v, double*) { return v; }
+__device__ __forceinline__ float out_value(float v, float*) { return v; }
+__device__ __forceinline__ float2 out_value(float v, float2*) { return make_float2(v, 0.0f); }
+
+// order: -1 row-major; 0 the lane order of k_face_op_ff; 1 the lane order of the transpose
+template <class VT, class OT>
+__device__ void store_inverse(VT (*a)[2 * kMaxM + 1], OT* out, int m, int lane, int order = -1) {
   for (int t = lane; t < m * m; t += 32) {
     const int r = t / m, c = t - r * m;
-    out[t] = a[r][m + c];
+    const int64_t at = order < 0 ? t : (order == 0 ? lane_order(r, c, m) : lane_order(c, r, m));
+    out[at] = out_value(a[r][m + c], out);
   }
 }
 
-__global__ void __launch_bounds__(32 * kFaceWarps) k_bj_invert(FaceDev f) {
-  __shared__ double s_aug[kFaceWarps][kMaxM][2 * kMaxM + 1];
+// VT: arithmetic of the inversion, OT: the stored inverses (dinv, at
+// f.dinv_off, in the given order).  binary64, row-major, for the binary64
+// solve; binary32 arithmetic stored as float-float pairs (lo = 0) in the lane
+// order of k_face_op_ff for the double-word solve, whose preconditioner is
+// then a fixed binary32 operator (it changes the iteration's convergence
+// rate, not the system solved).
+template <class VT, class OT>
+__global__ void __launch_bounds__(32 * kFaceWarps) k_bj_invert(FaceDev f, OT* dinv, int order) {
+  __shared__ VT s_aug[kFaceWarps][kMaxM][2 * kMaxM + 1];
   const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int e = blockIdx.x * kFaceWarps + w;
   if (e >= f.n_face) return;
   const int m = 4 * (f.face_p[e] + 1);
   int b = 0;
   while (b < 4 && f.k_col[5 * e + b] != e) ++b;
-  double(*a)[2 * kMaxM + 1] = s_aug[w];
+  VT(*a)[2 * kMaxM + 1] = s_aug[w];
   load_aug(a, f.K + f.k_blkoff[5 * e + b], m, lane);
   if (!warp_gj_invert(a, m, lane)) {
     if (lane == 0) *f.bad = 1;
     return;  // the whole warp leaves together
   }
-  store_inverse(a, f.dinv + f.dinv_off[e], m, lane);
+  store_inverse(a, dinv + f.dinv_off[e], m, lane, order);
 }
 
 // ---------------------------------------------------------------- block ILU(0)
@@ -393,165 +419,181 @@ __global__ void __launch_bounds__(kDotThreads) k_reduce(const double* __restrict
   if (threadIdx.x == 0) out[blockIdx.x] = s[0];
 }
 
-// w[i] += sgn * sum_j c[j] V_j[i]
-__global__ void k_multiaxpy(const double* __restrict__ V, int64_t ldv, int nvec, const double* __restrict__ c,
-                            double sgn, double* __restrict__ w, int64_t n) {
-  __shared__ double s_c[kMaxRestart + 1];
-  for (int j = threadIdx.x; j < nvec; j += blockDim.x) s_c[j] = sgn * c[j];
-  __syncthreads();
-  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
-    double a = w[i];
-    for (int j = 0; j < nvec; ++j) a = fma(s_c[j], V[(int64_t)j * ldv + i], a);
-    w[i] = a;
+// ---------------------------------------------------------------- float-float face operator
+// k_face_op with every vector stored as float-float pairs (float2: hi, lo) and
+// the matrix as the solver's double-word copy of K (or of the ILU factors;
+// MT = float2) or its binary32 ILU factors (MT = float), products and sums in
+// compensated double-word multiply-adds on the binary32 pipe.
+// The copy is stored in lane order: a face with m rows splits its 32 lanes
+// into nseg = 32 / m (rounded down to a power of two) segments, lane
+// r + m sg taking row r and the columns c = sg, sg + nseg, ...; entry (r, c)
+// of each block in the face's row (of K, or of K^T for products with K^T:
+// block (col, e) transposed) and of its pivot inverse sits at
+// (c / nseg) (m nseg) + r + m (c % nseg) within the block.  Every load of the
+// warp is then one contiguous run straight into registers: no staging, no
+// index arithmetic.  Relative error of a product ~2^-46 of the magnitudes
+// summed.
+using AF = Ar<ff>;
+
+__device__ __forceinline__ float2 to_mt(double v, float2*) {
+  const ff p = ff_split_double(v);
+  return make_float2(p.hi, p.lo);
+}
+__device__ __forceinline__ float to_mt(float v, float*) { return v; }
+
+__device__ __forceinline__ ff to_ff(float2 v) { return ff{v.x, v.y}; }
+__device__ __forceinline__ ff to_ff(float v) { return ff{v, 0.0f}; }
+__device__ __forceinline__ ff shfl_down_ff(ff v, int o) {
+  return ff{__shfl_down_sync(0xffffffffu, v.hi, o), __shfl_down_sync(0xffffffffu, v.lo, o)};
+}
+__device__ __forceinline__ float2 from_ff(ff v) { return make_float2(v.hi, v.lo); }
+
+// acc += the lane's share of one block's product: NT = MB / NSEG columns per
+// lane (compile-time: every load is a constant offset from one base, all
+// issued before the first multiply-add), two accumulation chains
+template <int M, int MB, bool INPLACE, class MT>
+__device__ __forceinline__ void lane_block_product(const MT* __restrict__ blk, const float2* xc, ff& t, ff& t2) {
+  constexpr int NSEG = (M <= 8 ? 4 : (M <= 16 ? 2 : 1)), NT = MB / NSEG, MN = M * NSEG;
+  MT a[NT];
+  float2 xv[NT];
+#pragma unroll
+  for (int u = 0; u < NT; ++u) {
+    a[u] = __ldcs(blk + u * MN);
+    // in place (a Gauss-Seidel sweep) x is written by this launch: no read-only cache path
+    xv[u] = INPLACE ? xc[u * NSEG] : __ldg(xc + u * NSEG);
   }
+#pragma unroll
+  for (int u = 0; u < NT; ++u) AF::madd((u & 1) ? t2 : t, to_ff(a[u]), to_ff(xv[u]));
 }
 
-__global__ void k_scale(double* __restrict__ v, double s, int64_t n) {
-  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
-    v[i] *= s;
-}
-
-// ---------------------------------------------------------------- Krylov kernels
-// Vectors of the trace space have an even length (4 (p_e + 1) per face) and
-// start 32-byte aligned, so they are read as double2.  The norm fused into
-// the second Gram-Schmidt update is reduced in one launch: warp shuffles, the
-// warps of a block in order, one partial per block, and the last block to
-// finish (a ticket taken after a fence) sums the partials in a fixed order and
-// resets the ticket -- bitwise reproducible.
-
-// out[j] = sum over blocks of part[j][b], j < nout (called by the last block only):
-// every thread takes a strided share of the partials, then a fixed-order tree
-__device__ void finish_reduction(const double* part, int nout, int nblk, double* out, unsigned* ticket) {
-  __shared__ double s_fin[kDotThreads];
-  for (int j = 0; j < nout; ++j) {
-    double v = 0.0;
-    for (int b = threadIdx.x; b < nblk; b += blockDim.x) v += __ldcg(part + (int64_t)j * nblk + b);
-    s_fin[threadIdx.x] = v;
-    __syncthreads();
-    for (int st = blockDim.x / 2; st > 0; st >>= 1) {
-      if (threadIdx.x < st) s_fin[threadIdx.x] += s_fin[threadIdx.x + st];
-      __syncthreads();
-    }
-    if (threadIdx.x == 0) out[j] = s_fin[0];
-    __syncthreads();
-  }
-  if (threadIdx.x == 0) *ticket = 0u;
-}
-
-// block-wide sum of acc[0..nj) into part[j0 + j][blockIdx] (blockIdx flattened over x), then
-// the last block finishes every output; returns nothing useful to the caller
-template <int NA>
-__device__ void block_partials(const double (&acc)[NA], int nj, int j0, double* part, int nout, int nblk,
-                               double* out, unsigned* ticket) {
-  __shared__ double s_red[NA][kDotThreads / 32];
-  __shared__ bool s_last;
-  const int lane = threadIdx.x & 31, wp = threadIdx.x >> 5, nw = blockDim.x >> 5;
-#pragma unroll
-  for (int j = 0; j < NA; ++j) {
-    double v = acc[j];
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
-    if (lane == 0) s_red[j][wp] = v;
-  }
-  __syncthreads();
-  if (threadIdx.x < nj) {
-    double v = 0.0;
-    for (int k = 0; k < nw; ++k) v += s_red[threadIdx.x][k];
-    part[(int64_t)(j0 + threadIdx.x) * gridDim.x + blockIdx.x] = v;
-  }
-  __threadfence();
-  __syncthreads();
-  if (threadIdx.x == 0) s_last = atomicAdd(ticket, 1u) == gridDim.x * gridDim.y - 1;
-  __syncthreads();
-  if (s_last) {
-    __threadfence();
-    finish_reduction(part, nout, nblk, out, ticket);
-  }
-}
-
-// part[j][block] = V_j . w over the block's slab of rows, j < nvec: each block
-// owns a contiguous slab (its slice of w stays in L1 while its warps stream
-// their vectors: warp k takes vectors k, k + 8, ..., four at a time, two
-// double2 rows per lane in flight for each); k_reduce sums the partials.
-__global__ void __launch_bounds__(kDotThreads) k_dots_slab(const double* __restrict__ V, int64_t ldv, int nvec,
-                                                           const double* __restrict__ w, int64_t n,
-                                                           double* __restrict__ part) {
-  constexpr int NW = kDotThreads / 32, VPW = 4;  // warps per block, vectors per warp per sweep
-  const int lane = threadIdx.x & 31, wp = threadIdx.x >> 5;
-  const int64_t n2 = n >> 1;
-  const int64_t per = (n2 + gridDim.x - 1) / gridDim.x;
-  const int64_t b0 = min(n2, (int64_t)blockIdx.x * per), b1 = min(n2, b0 + per);
-  const double2* w2 = reinterpret_cast<const double2*>(w);
-  for (int jb = wp; jb < nvec; jb += NW * VPW) {
-    const double2* v2[VPW];
-    double acc[VPW];
-#pragma unroll
-    for (int k = 0; k < VPW; ++k) {
-      const int j = min(jb + k * NW, nvec - 1);
-      v2[k] = reinterpret_cast<const double2*>(V + (int64_t)j * ldv);
-      acc[k] = 0.0;
-    }
-    for (int64_t i = b0 + lane; i < b1; i += 64) {
-      const bool two = i + 32 < b1;
-      const double2 wa = __ldg(w2 + i);
-      const double2 wb = two ? __ldg(w2 + i + 32) : make_double2(0.0, 0.0);
-#pragma unroll
-      for (int k = 0; k < VPW; ++k) {
-        if (jb + k * NW >= nvec) break;  // slot without a vector (warp-uniform): no loads, no FMAs
-        const double2 a = __ldg(v2[k] + i);
-        const double2 b = two ? __ldg(v2[k] + i + 32) : make_double2(0.0, 0.0);
-        acc[k] = fma(a.x, wa.x, acc[k]);
-        acc[k] = fma(a.y, wa.y, acc[k]);
-        acc[k] = fma(b.x, wb.x, acc[k]);
-        acc[k] = fma(b.y, wb.y, acc[k]);
+template <int M, bool TR, bool INPLACE, class MT>
+__device__ __forceinline__ void face_op_ff_body(const FaceDevT<MT>& f, const float2* x, const float2* __restrict__ bvec,
+                                                float2* y, int mode, int e, int skip_diag, int tri, ff* s_t) {
+  constexpr int NSEG = (M <= 8 ? 4 : (M <= 16 ? 2 : 1)), MN = M * NSEG;
+  const int lane = threadIdx.x & 31;
+  const int sg = lane / M;
+  const bool act = sg < NSEG;
+  const int64_t lo = f.lam_off[e];
+  const int ce = tri ? f.fcolor[e] : 0;
+  ff t = AF::zero(), t2 = AF::zero();
+  if (mode != 3) {
+    int mcol = -1, mmb = 0;
+    long long moff = 0, mxo = 0;
+    if (lane < 5) {
+      const int col = f.k_col[5 * e + lane];
+      bool ok = col >= 0 && !(skip_diag && col == e);
+      if (ok && tri) {
+        const int cc = f.fcolor[col];
+        ok = (tri == 1) ? cc < ce : cc > ce;
+      }
+      if (ok) {
+        mcol = col;
+        mmb = 4 * (f.face_p[col] + 1);
+        moff = TR ? f.k_tblk[5 * e + lane] : f.k_blkoff[5 * e + lane];
+        mxo = f.lam_off[col];
       }
     }
-#pragma unroll
-    for (int k = 0; k < VPW; ++k) {
-      double v = acc[k];
-#pragma unroll
-      for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
-      const int j = jb + k * NW;
-      if (lane == 0 && j < nvec) {
-        if (blockIdx.x == 0 && (n & 1)) v = fma(V[(int64_t)j * ldv + n - 1], w[n - 1], v);  // odd tail
-        part[(int64_t)j * gridDim.x + blockIdx.x] = v;
+    for (int b = 0; b < 5; ++b) {
+      const int col = __shfl_sync(0xffffffffu, mcol, b);
+      if (col < 0) continue;
+      const int mb = __shfl_sync(0xffffffffu, mmb, b);
+      const MT* blk = f.K + __shfl_sync(0xffffffffu, moff, b) + lane;
+      const float2* xc = x + __shfl_sync(0xffffffffu, mxo, b) + sg;
+      if (act) {
+        switch (mb) {
+          case 8: lane_block_product<M, 8, INPLACE>(blk, xc, t, t2); break;
+          case 12: lane_block_product<M, 12, INPLACE>(blk, xc, t, t2); break;
+          case 16: lane_block_product<M, 16, INPLACE>(blk, xc, t, t2); break;
+          default: lane_block_product<M, 20, INPLACE>(blk, xc, t, t2); break;
+        }
       }
     }
   }
+  t = AF::add(AF::norm(t), AF::norm(t2));
+  // the NSEG partial sums of row r sit in lanes r, r + M, ...
+#pragma unroll
+  for (int o = M * (NSEG >> 1); o >= M; o >>= 1) t = AF::add(t, shfl_down_ff(t, o));
+  if (lane < M) {
+    if (mode == 1 || mode == 4) t = AF::sub(to_ff(bvec[lo + lane]), t);
+    if (mode == 3) t = AF::norm(to_ff(bvec[lo + lane]));
+    s_t[lane] = t;
+  }
+  __syncwarp();
+  if (mode == 2 || mode == 4) {
+    if (lane < M) y[lo + lane] = from_ff(t);
+    return;
+  }
+  ff v = AF::zero(), v2 = AF::zero();
+  if (act) {  // the pivot inverse (or its transpose) in the same lane order
+    constexpr int NT = M / NSEG;
+    const MT* di = f.dinv + f.dinv_off[e] + lane;
+    MT a[NT];
+#pragma unroll
+    for (int u = 0; u < NT; ++u) a[u] = __ldg(di + u * MN);
+#pragma unroll
+    for (int u = 0; u < NT; ++u) AF::madd((u & 1) ? v2 : v, to_ff(a[u]), s_t[sg + u * NSEG]);
+  }
+  v = AF::add(AF::norm(v), AF::norm(v2));
+#pragma unroll
+  for (int o = M * (NSEG >> 1); o >= M; o >>= 1) v = AF::add(v, shfl_down_ff(v, o));
+  if (lane < M) y[lo + lane] = from_ff(v);
 }
 
-// w -= V c (j < nvec, c on the device); with NORM, out[0] = ||w||^2 of the updated w
-template <bool NORM>
-__global__ void __launch_bounds__(kDotThreads) k_axpy_v(const double* __restrict__ V, int64_t ldv, int nvec,
-                                                        const double* __restrict__ c, double* __restrict__ w,
-                                                        int64_t n, double* __restrict__ part,
-                                                        double* __restrict__ out, unsigned* ticket) {
-  __shared__ double s_c[kMaxRestart + 1];
-  for (int j = threadIdx.x; j < nvec; j += blockDim.x) s_c[j] = c[j];
-  __syncthreads();
-  double acc[1] = {0.0};
-  const int64_t n2 = n >> 1;
-  double2* w2 = reinterpret_cast<double2*>(w);
-  for (int64_t i = blockIdx.x * (int64_t)kDotThreads + threadIdx.x; i < n2; i += (int64_t)gridDim.x * kDotThreads) {
-    double2 a = w2[i];
-    for (int j = 0; j < nvec; ++j) {
-      const double2 v = __ldg(reinterpret_cast<const double2*>(V + (int64_t)j * ldv) + i);
-      a.x = fma(-s_c[j], v.x, a.x);
-      a.y = fma(-s_c[j], v.y, a.y);
-    }
-    w2[i] = a;
-    if (NORM) {
-      acc[0] = fma(a.x, a.x, acc[0]);
-      acc[0] = fma(a.y, a.y, acc[0]);
+template <bool TR, bool INPLACE, class MT>
+__global__ void __launch_bounds__(32 * kFaceWarps) k_face_op_ff(FaceDevT<MT> f, const float2* x,
+                                                                  const float2* __restrict__ bvec, float2* y,
+                                                                  int mode, const int* __restrict__ faces, int nfaces,
+                                                                  int skip_diag, int tri) {
+  __shared__ ff s_t[kFaceWarps][kMaxM];
+  const int w = threadIdx.x >> 5;
+  const int ei = blockIdx.x * kFaceWarps + w;
+  if (ei >= (faces ? nfaces : f.n_face)) return;
+  const int e = faces ? faces[ei] : ei;
+  switch (f.face_p[e]) {  // m = 4 (p + 1): the face's rows fix the lane order
+    case 1: face_op_ff_body<8, TR, INPLACE>(f, x, bvec, y, mode, e, skip_diag, tri, s_t[w]); break;
+    case 2: face_op_ff_body<12, TR, INPLACE>(f, x, bvec, y, mode, e, skip_diag, tri, s_t[w]); break;
+    case 3: face_op_ff_body<16, TR, INPLACE>(f, x, bvec, y, mode, e, skip_diag, tri, s_t[w]); break;
+    default: face_op_ff_body<20, TR, INPLACE>(f, x, bvec, y, mode, e, skip_diag, tri, s_t[w]); break;
+  }
+}
+
+// dst = the face blocks of src (K's layout: K, or the ILU factors) converted
+// to MT and placed in the lane order of k_face_op_ff, for products with K
+// (tr = 0: face e's blocks (e, col)) or with K^T (tr = 1: blocks (col, e)
+// transposed).  One warp per face; every stored block is written once.
+template <class IT, class MT>
+__global__ void __launch_bounds__(32 * kFaceWarps) k_lane_order_blocks(FaceDevT<double> f, const IT* __restrict__ src,
+                                                                       MT* __restrict__ dst, int tr) {
+  const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int e = blockIdx.x * kFaceWarps + w;
+  if (e >= f.n_face) return;
+  const int me = 4 * (f.face_p[e] + 1);
+  for (int b = 0; b < 5; ++b) {
+    const int col = f.k_col[5 * e + b];
+    if (col < 0) continue;
+    const int mc = 4 * (f.face_p[col] + 1);
+    const int64_t o = tr ? f.k_tblk[5 * e + b] : f.k_blkoff[5 * e + b];
+    const int N = tr ? me : mc;  // stored columns (rows: tr ? mc : me)
+    for (int idx = lane; idx < me * mc; idx += 32) {
+      const int i = idx / N, j = idx - i * N;
+      dst[o + (tr ? lane_order(j, i, me) : lane_order(i, j, me))] = to_mt(__ldcs(src + o + idx), (MT*)nullptr);
     }
   }
-  if ((n & 1) && blockIdx.x == 0 && threadIdx.x == 0) {
-    double a = w[n - 1];
-    for (int j = 0; j < nvec; ++j) a = fma(-s_c[j], V[(int64_t)j * ldv + n - 1], a);
-    w[n - 1] = a;
-    if (NORM) acc[0] = fma(a, a, acc[0]);
+}
+
+// the same for the pivot inverses (m x m at dinv_off[e]; tr: transposed)
+template <class IT, class MT>
+__global__ void __launch_bounds__(32 * kFaceWarps) k_lane_order_dinv(FaceDevT<double> f, const IT* __restrict__ src,
+                                                                     MT* __restrict__ dst, int tr) {
+  const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int e = blockIdx.x * kFaceWarps + w;
+  if (e >= f.n_face) return;
+  const int m = 4 * (f.face_p[e] + 1);
+  const int64_t o = f.dinv_off[e];
+  for (int idx = lane; idx < m * m; idx += 32) {
+    const int i = idx / m, j = idx - i * m;
+    dst[o + (tr ? lane_order(j, i, m) : lane_order(i, j, m))] = to_mt(__ldcs(src + o + idx), (MT*)nullptr);
   }
-  if (NORM) block_partials<1>(acc, 1, 0, part, 1, gridDim.x, out, ticket);
 }
 
 __global__ void k_axpy2(double* __restrict__ U, const double* __restrict__ dU, int64_t nu, double* __restrict__ L,
@@ -581,16 +623,17 @@ struct hdg_solver {
   int sms = 0;
   int dot_blocks = 0;
   FaceDev f{};
-  double* V = nullptr;        // [restart + 1][n]
+  double* V = nullptr;        // [restart + 1][n] (float-float pairs in the same bytes under arith 1)
   double* partial = nullptr;  // [restart + 1][dot_blocks]
   unsigned* ticket = nullptr; // last-block ticket of the fused reductions (zero between launches)
-  double* h = nullptr;        // [2 (restart + 1) + 2] device results of the reductions
-  double* coef = nullptr;     // [restart + 1] coefficients from the host
+  double* h = nullptr;        // Arnoldi state (ArnoldiViews)
+  double* coef = nullptr;     // [restart + 1] spare
   double* zero = nullptr;     // [n] zeros
   double* tmp = nullptr;      // [n] work vector of the Gauss-Seidel and ILU preconditioners
   double* tmp2 = nullptr;     // [n] second work vector of the ILU preconditioner
   double* hpin = nullptr;     // pinned host mirror of h / coef
   int precond = 0;            // 0 block Jacobi, 1 multicolor block SGS, 2 block ILU(0), 3 ILU(0) in binary32
+  int arith = 0;              // GMRES products and Krylov updates: 0 binary64, 1 double-word on the binary32 pipe
   bool factored = false;      // a setup has been enqueued for the current kind
   int* colors = nullptr;      // faces grouped by color
   std::vector<int> color_off; // [n_colors + 1]
@@ -599,6 +642,13 @@ struct hdg_solver {
   double* F = nullptr;
   FaceDevT<float> fi32{};     // the same in binary32 (mixed-precision ILU(0), kind 3)
   float* F32 = nullptr;
+  // arith 1: float-float copies of K and its pivot inverses, of the binary64
+  // ILU factors, and of the solution and right-hand side of a solve
+  FaceDevT<float2> fff{};
+  FaceDevT<float2> fiff{};
+  FaceDevT<float> fi32ff{};   // kind 3: the binary32 factors in lane order (in fiff's buffers)
+  float2* xff = nullptr;      // [n]
+  float2* eff = nullptr;      // [n]
   bool external_ws = false;   // device buffers carved from the caller's workspace
   bool hpin_pageable = false; // host mirror from new[] (caller's workspace) or pinned
   int64_t k_vals = 0;         // doubles in K
@@ -613,6 +663,7 @@ hdg_status ck(hdg_ctx* ctx, cudaError_t e, const char* what) {
   return HDG_OK;
 }
 
+// y by mode from K x (see k_face_op), binary64 vectors: the binary64 kernels
 template <class MT>
 void face_op(const FaceDevT<MT>& fd, bool tr, const double* x, const double* b, double* y, int mode, cudaStream_t st,
              const int* faces = nullptr, int nfaces = 0, int skip_diag = 0, int tri = 0) {
@@ -628,18 +679,48 @@ void face_op(const FaceDevT<MT>& fd, bool tr, const double* x, const double* b, 
     else k_face_op<false, false, MT><<<fb, 32 * kFaceWarps, 0, st>>>(fd, x, b, y, mode, faces, nfaces, skip_diag, tri);
   }
 }
+// the same with float-float vectors: the double-word kernels
+template <class MT>
+void face_op(const FaceDevT<MT>& fd, bool tr, const float2* x, const float2* b, float2* y, int mode, cudaStream_t st,
+             const int* faces = nullptr, int nfaces = 0, int skip_diag = 0, int tri = 0) {
+  const int nf = faces ? nfaces : fd.n_face;
+  if (nf == 0) return;
+  const int fb = (nf + kFaceWarps - 1) / kFaceWarps;
+  const bool inplace = x == y;
+  if (tr) {
+    if (inplace) k_face_op_ff<true, true, MT><<<fb, 32 * kFaceWarps, 0, st>>>(fd, x, b, y, mode, faces, nfaces, skip_diag, tri);
+    else k_face_op_ff<true, false, MT><<<fb, 32 * kFaceWarps, 0, st>>>(fd, x, b, y, mode, faces, nfaces, skip_diag, tri);
+  } else {
+    if (inplace) k_face_op_ff<false, true, MT><<<fb, 32 * kFaceWarps, 0, st>>>(fd, x, b, y, mode, faces, nfaces, skip_diag, tri);
+    else k_face_op_ff<false, false, MT><<<fb, 32 * kFaceWarps, 0, st>>>(fd, x, b, y, mode, faces, nfaces, skip_diag, tri);
+  }
+}
+
+// The solver's views for a vector storage VS: K (and the pivot inverses of
+// block Jacobi / SGS), the binary64 ILU factors, and its work vectors.
+inline const FaceDev& kview(const hdg_solver* S, const double*) { return S->f; }
+inline const FaceDevT<float2>& kview(const hdg_solver* S, const float2*) { return S->fff; }
+inline const FaceDev& iview(const hdg_solver* S, const double*) { return S->fi; }
+inline const FaceDevT<float2>& iview(const hdg_solver* S, const float2*) { return S->fiff; }
+inline const FaceDevT<float>& i32view(const hdg_solver* S, const double*) { return S->fi32; }
+inline const FaceDevT<float>& i32view(const hdg_solver* S, const float2*) { return S->fi32ff; }
+template <class VS>
+VS* vec(double* p) {
+  return reinterpret_cast<VS*>(p);
+}
 
 // z = M^{-1} r for the multicolor block symmetric Gauss-Seidel preconditioner:
 // from z = 0, a forward sweep over the colors, then a backward one; each color
 // is one launch (its faces are mutually uncoupled, so the sweep is exact Gauss-Seidel).
-void sgs_apply(hdg_solver* S, bool tr, const double* r, double* z, cudaStream_t st) {
-  cudaMemsetAsync(z, 0, sizeof(double) * S->n, st);
+template <class VS>
+void sgs_apply(hdg_solver* S, bool tr, const VS* r, VS* z, cudaStream_t st) {
+  cudaMemsetAsync(z, 0, sizeof(VS) * S->n, st);  // all-zero bytes: 0 in both storages
   const int nc = (int)S->color_off.size() - 1;
   for (int pass = 0; pass < 2; ++pass)
     for (int k = 0; k < nc; ++k) {
       const int c = pass == 0 ? k : nc - 1 - k;
       const int o0 = S->color_off[c], o1 = S->color_off[c + 1];
-      face_op(S->f, tr, z, r, z, 1, st, S->colors + o0, o1 - o0, 1);
+      face_op(kview(S, z), tr, z, r, z, 1, st, S->colors + o0, o1 - o0, 1, 0);
     }
 }
 
@@ -648,68 +729,82 @@ void sgs_apply(hdg_solver* S, bool tr, const double* r, double* z, cudaStream_t 
 // earlier colors; transposed, U^T y = r), then a backward one into z
 // (U z = y: z_e = U_ee^{-1} (y_e - sum of U_ej z_j over later colors;
 // transposed, L^T z = y).  r and z must not be tmp2.
-template <class MT>
-void ilu_sweeps(hdg_solver* S, const FaceDevT<MT>& fi, bool tr, const double* r, double* z, cudaStream_t st) {
+template <class MT, class VS>
+void ilu_sweeps(hdg_solver* S, const FaceDevT<MT>& fi, bool tr, const VS* r, VS* z, cudaStream_t st) {
+  VS* t2 = vec<VS>(S->tmp2);
   const int nc = (int)S->color_off.size() - 1;
   for (int c = 0; c < nc; ++c) {
     const int o0 = S->color_off[c], o1 = S->color_off[c + 1];
-    face_op(fi, tr, S->tmp2, r, S->tmp2, tr ? 1 : 4, st, S->colors + o0, o1 - o0, 0, 1);
+    face_op(fi, tr, t2, r, t2, tr ? 1 : 4, st, S->colors + o0, o1 - o0, 0, 1);
   }
   for (int c = nc - 1; c >= 0; --c) {
     const int o0 = S->color_off[c], o1 = S->color_off[c + 1];
-    face_op(fi, tr, z, S->tmp2, z, tr ? 4 : 1, st, S->colors + o0, o1 - o0, 0, 2);
+    face_op(fi, tr, z, t2, z, tr ? 4 : 1, st, S->colors + o0, o1 - o0, 0, 2);
   }
 }
-void ilu_apply(hdg_solver* S, bool tr, const double* r, double* z, cudaStream_t st) {
-  if (S->precond == 3) ilu_sweeps(S, S->fi32, tr, r, z, st);  // binary32 factors, binary64 products
-  else ilu_sweeps(S, S->fi, tr, r, z, st);
+template <class VS>
+void ilu_apply(hdg_solver* S, bool tr, const VS* r, VS* z, cudaStream_t st) {
+  if (S->precond == 3) ilu_sweeps(S, i32view(S, z), tr, r, z, st);  // binary32 factors
+  else ilu_sweeps(S, iview(S, z), tr, r, z, st);
 }
 
 // w = M^{-1} b for the solver's preconditioner
-void prec_rhs(hdg_solver* S, bool tr, const double* b, double* w, cudaStream_t st) {
-  if (S->precond == 0) face_op(S->f, tr, S->zero, b, w, 3, st);
+template <class VS>
+void prec_rhs(hdg_solver* S, bool tr, const VS* b, VS* w, cudaStream_t st) {
+  if (S->precond == 0) face_op(kview(S, w), tr, vec<VS>(S->zero), b, w, 3, st);
   else if (S->precond == 1) sgs_apply(S, tr, b, w, st);
   else ilu_apply(S, tr, b, w, st);
 }
 // w = M^{-1} K v (block Jacobi: one fused launch)
-void prec_op(hdg_solver* S, bool tr, const double* v, double* w, cudaStream_t st) {
+template <class VS>
+void prec_op(hdg_solver* S, bool tr, const VS* v, VS* w, cudaStream_t st) {
   if (S->precond == 0) {
-    face_op(S->f, tr, v, nullptr, w, 0, st);
+    face_op(kview(S, w), tr, v, (const VS*)nullptr, w, 0, st);
   } else {
-    face_op(S->f, tr, v, nullptr, S->tmp, 2, st);
-    prec_rhs(S, tr, S->tmp, w, st);
+    face_op(kview(S, w), tr, v, (const VS*)nullptr, vec<VS>(S->tmp), 2, st);
+    prec_rhs(S, tr, (const VS*)vec<VS>(S->tmp), w, st);
   }
 }
 // w = M^{-1} (b - K x)
-void prec_res(hdg_solver* S, bool tr, const double* x, const double* b, double* w, cudaStream_t st) {
+template <class VS>
+void prec_res(hdg_solver* S, bool tr, const VS* x, const VS* b, VS* w, cudaStream_t st) {
   if (S->precond == 0) {
-    face_op(S->f, tr, x, b, w, 1, st);
+    face_op(kview(S, w), tr, x, b, w, 1, st);
   } else {
-    face_op(S->f, tr, x, b, S->tmp, 4, st);
-    prec_rhs(S, tr, S->tmp, w, st);
+    face_op(kview(S, w), tr, x, b, vec<VS>(S->tmp), 4, st);
+    prec_rhs(S, tr, (const VS*)vec<VS>(S->tmp), w, st);
   }
 }
 
 // the binary32 factor view: K's layout and tables, values and pivot inverses in binary32
-void set_fi32(hdg_solver* S, float* dinv32) {
-  const FaceDev& f = S->f;
-  S->fi32.n_face = f.n_face;
-  S->fi32.face_p = f.face_p;
-  S->fi32.lam_off = f.lam_off;
-  S->fi32.k_col = f.k_col;
-  S->fi32.k_blkoff = f.k_blkoff;
-  S->fi32.dinv_off = f.dinv_off;
-  S->fi32.k_tblk = f.k_tblk;
-  S->fi32.fcolor = f.fcolor;
-  S->fi32.K = S->F32;
-  S->fi32.dinv = dinv32;
-  S->fi32.bad = f.bad;
+template <class MT>
+void set_view(FaceDevT<MT>& v, const FaceDev& f, const MT* K, MT* dinv) {
+  v.n_face = f.n_face;
+  v.face_p = f.face_p;
+  v.lam_off = f.lam_off;
+  v.k_col = f.k_col;
+  v.k_blkoff = f.k_blkoff;
+  v.dinv_off = f.dinv_off;
+  v.k_tblk = f.k_tblk;
+  v.fcolor = f.fcolor;
+  v.K = K;
+  v.dinv = dinv;
+  v.bad = f.bad;
+}
+void set_fi32(hdg_solver* S, float* dinv32) { set_view(S->fi32, S->f, (const float*)S->F32, dinv32); }
+
+void split_copy(const hdg_solver* S, const double* a, float2* b, int64_t n, cudaStream_t st) {
+  if (n > 0) k_split<<<grid_for(n, 256, 8 * S->sms), 256, 0, st>>>(a, b, n);
 }
 
-// enqueue the factorization of the preconditioner for the current K; a
-// singular pivot block sets f.bad (cleared first)
-hdg_status setup_enqueue(hdg_solver* S, cudaStream_t st) {
+// enqueue the factorization of the preconditioner for the current K (a
+// singular pivot block sets f.bad, cleared first); for arith 1 the
+// lane-ordered double-word copies of K and of the factors the sweeps use, for
+// products with K (tr = 0) or K^T (block Jacobi / SGS: pivot inverses
+// computed in binary32, stored as pairs)
+hdg_status setup_enqueue(hdg_solver* S, cudaStream_t st, int arith, int tr = 0) {
   hdg_ctx* ctx = S->sys->ctx;
+  const int nf = (S->f.n_face + kFaceWarps - 1) / kFaceWarps;
   hdg_status rs;
   if ((rs = ck(ctx, cudaMemsetAsync(S->f.bad, 0, sizeof(int), st), "cudaMemsetAsync")) != HDG_OK) return rs;
   if (S->precond == 2 || S->precond == 3) {
@@ -728,24 +823,32 @@ hdg_status setup_enqueue(hdg_solver* S, cudaStream_t st) {
       if (f32) k_ilu_row<float><<<nb, 32 * kFaceWarps, 0, st>>>(S->fi32, S->F32, S->colors + o0, n);
       else k_ilu_row<double><<<nb, 32 * kFaceWarps, 0, st>>>(S->fi, S->F, S->colors + o0, n);
     }
+  } else if (arith == 1) {
+    k_bj_invert<float, float2><<<nf, 32 * kFaceWarps, 0, st>>>(S->f, S->fff.dinv, tr);
   } else {
-    k_bj_invert<<<(S->f.n_face + kFaceWarps - 1) / kFaceWarps, 32 * kFaceWarps, 0, st>>>(S->f);
+    k_bj_invert<double, double><<<nf, 32 * kFaceWarps, 0, st>>>(S->f, S->f.dinv, -1);
+  }
+  if (arith == 1) {  // the lane-ordered copies k_face_op_ff reads
+    k_lane_order_blocks<double, float2><<<nf, 32 * kFaceWarps, 0, st>>>(S->f, S->f.K, const_cast<float2*>(S->fff.K), tr);
+    if (S->precond == 2) {
+      k_lane_order_blocks<double, float2><<<nf, 32 * kFaceWarps, 0, st>>>(S->f, S->F, const_cast<float2*>(S->fiff.K), tr);
+      k_lane_order_dinv<double, float2><<<nf, 32 * kFaceWarps, 0, st>>>(S->f, S->fi.dinv, S->fiff.dinv, tr);
+    } else if (S->precond == 3) {
+      k_lane_order_blocks<float, float><<<nf, 32 * kFaceWarps, 0, st>>>(S->f, S->F32, const_cast<float*>(S->fi32ff.K), tr);
+      k_lane_order_dinv<float, float><<<nf, 32 * kFaceWarps, 0, st>>>(S->f, S->fi32.dinv, S->fi32ff.dinv, tr);
+    }
   }
   if ((rs = ck(ctx, cudaGetLastError(), "preconditioner setup")) != HDG_OK) return rs;
-  S->factored = true;
+  // the binary64 factors (hdg_solver_precond_apply) are current unless the
+  // pivot inverses were computed for the double-word solve only
+  S->factored = !(arith == 1 && S->precond <= 1);
   return HDG_OK;
 }
 
-// out[0..nvec) = V_j . w for j < nvec (device), one launch, enqueued on st
-void multidot(hdg_solver* S, const double* V, int nvec, const double* w, int64_t n, double* out, cudaStream_t st) {
-  k_dots_slab<<<S->dot_blocks, kDotThreads, 0, st>>>(V, S->n, nvec, w, n, S->partial);
-  k_reduce<<<nvec, kDotThreads, 0, st>>>(S->partial, S->dot_blocks, out);
-}
-// w -= V c (nvec columns); with norm2 != null also norm2[0] = ||w||^2 afterwards
-void axpy_v(hdg_solver* S, const double* V, int nvec, const double* c, double* w, int64_t n, double* norm2,
-            cudaStream_t st) {
-  if (norm2) k_axpy_v<true><<<S->dot_blocks, kDotThreads, 0, st>>>(V, S->n, nvec, c, w, n, S->partial, norm2, S->ticket);
-  else k_axpy_v<false><<<S->dot_blocks, kDotThreads, 0, st>>>(V, S->n, nvec, c, w, n, S->partial, nullptr, S->ticket);
+// out[j] = V_j . w for j < nvec (device), one launch
+template <class VS>
+void dots(hdg_solver* S, const VS* V, int nvec, const VS* w, double* out, cudaStream_t st) {
+  k_dots<VS><<<S->dot_blocks, kDotThreads, 0, st>>>(V, S->n, nvec, w, S->n, S->partial, out, S->ticket);
 }
 
 }  // namespace
@@ -771,7 +874,8 @@ SolverPlan plan_solver(const hdg_mesh* M, int restart, int precond, int sms) {
   p.n = M->lam_len;
   for (int e = 0; e < M->n_face; ++e) p.dinv_len += (int64_t)(4 * (M->face_p[e] + 1)) * (4 * (M->face_p[e] + 1));
   p.k_vals = M->k_blkoff.empty() ? 0 : M->k_blkoff.back();
-  p.dot_blocks = std::max(1, std::min<int>(2 * std::max(sms, 1), (int)((p.n / 2 + kDotThreads - 1) / kDotThreads)));
+  // one wave of the Krylov kernels (two 256-thread blocks per SM at <= 128 registers), grid-stride beyond
+  p.dot_blocks = std::max(1, std::min<int>(2 * std::max(sms, 1), (int)((p.n / 2 + 2 * kDotThreads - 1) / (2 * kDotThreads))));
   p.kc = take(sizeof(int) * 5 * nf);
   p.kb = take(sizeof(int64_t) * M->k_blkoff.size());
   p.kt = take(sizeof(int64_t) * 5 * nf);
@@ -780,8 +884,8 @@ SolverPlan plan_solver(const hdg_mesh* M, int restart, int precond, int sms) {
   p.bad = take(sizeof(int));
   p.ticket = take(sizeof(unsigned));
   p.V = take(sizeof(double) * nr * p.n);
-  p.part = take(sizeof(double) * nr * p.dot_blocks);
-  p.h = take(sizeof(double) * (2 * nr + 2));
+  p.part = take(sizeof(double) * 2 * nr * p.dot_blocks);  // two rows per basis vector in an Arnoldi reduction
+  p.h = take(sizeof(double) * arnoldi_doubles(restart));
   p.coef = take(sizeof(double) * nr);
   p.zero = take(sizeof(double) * p.n);
   p.tmp = take(sizeof(double) * p.n);
@@ -877,9 +981,9 @@ hdg_status solver_build(hdg_sys* sys, int32_t restart, int32_t precond, void* ws
   }
   const size_t nr = (size_t)restart + 1;
   if (S->external_ws) {  // no pinned allocation (its release may synchronise the device)
-    S->hpin = new double[2 * nr + 2];
+    S->hpin = new double[std::max<size_t>(2 * nr + 2, 16)];
     S->hpin_pageable = true;
-  } else if (cudaMallocHost((void**)&S->hpin, sizeof(double) * (2 * nr + 2)) != cudaSuccess) {
+  } else if (cudaMallocHost((void**)&S->hpin, sizeof(double) * std::max<size_t>(2 * nr + 2, 16)) != cudaSuccess) {
     S->hpin = nullptr;
     hdg_solver_destroy(S);
     return fail(ctx, HDG_ENOMEM, "hdg_solver_create: pinned host allocation failed");
@@ -937,6 +1041,124 @@ hdg_status solver_build(hdg_sys* sys, int32_t restart, int32_t precond, void* ws
   S->precond = precond;
   *out = S;
   return HDG_OK;
+}
+
+// The double-word copies of arith 1, allocated on first use: K and its pivot
+// inverses, the solution and right-hand side of a solve, and (block ILU(0))
+// the factors and their pivot inverses.
+hdg_status ensure_ff(hdg_solver* S, int kind) {
+  hdg_ctx* ctx = S->sys->ctx;
+  const bool need_k = !S->fff.K, need_i = (kind == 2 || kind == 3) && !S->fiff.K;
+  if (!need_k && !need_i) return HDG_OK;
+  if (S->external_ws)
+    return fail(ctx, HDG_ENOMEM, "hdg_solver_set_arithmetic: the caller's workspace was planned without the float-float copies");
+  HDG_ON_DEVICE(ctx, ctx->device);
+  const size_t kv = sizeof(float2) * std::max<int64_t>(S->k_vals, 2), dv = sizeof(float2) * std::max<int64_t>(S->dinv_len, 2);
+  auto up = [](size_t sz) { return (sz + 255) / 256 * 256; };
+  const size_t bytes = up(kv) + up(dv) + (need_k ? 2 * up(sizeof(float2) * (size_t)S->n) : 0);
+  void* p = nullptr;
+  if (cudaMalloc(&p, bytes) != cudaSuccess)
+    return fail(ctx, HDG_ENOMEM, "hdg_solver_set_arithmetic: device allocation of the float-float copies failed");
+  S->allocs.push_back(p);
+  char* b = (char*)p;
+  auto take = [&b](size_t sz) {
+    char* at = b;
+    b += (sz + 255) / 256 * 256;
+    return (void*)at;
+  };
+  if (need_k) {
+    float2* K = (float2*)take(kv);
+    float2* di = (float2*)take(dv);
+    set_view(S->fff, S->f, (const float2*)K, di);
+    S->xff = (float2*)take(sizeof(float2) * S->n);
+    S->eff = (float2*)take(sizeof(float2) * S->n);
+  } else {
+    float2* K = (float2*)take(kv);
+    float2* di = (float2*)take(dv);
+    set_view(S->fiff, S->f, (const float2*)K, di);
+    set_view(S->fi32ff, S->f, (const float*)K, (float*)di);
+  }
+  return need_k && need_i ? ensure_ff(S, kind) : HDG_OK;
+}
+
+// Restarted, left-preconditioned GMRES on vectors of storage VS (binary64, or
+// float-float pairs under arith 1): x += the solution of M^{-1} K dx =
+// M^{-1} (E - K x) to rtol of ||M^{-1} E||.  Each restart forms the true
+// residual r0 = M^{-1} (E - K x) and its norm on the host's side of the
+// loop; the cycle then runs the Arnoldi process as delayed classical
+// Gram-Schmidt with re-orthogonalisation (hdg_krylov.cuh), step j being
+//   z = M^{-1} K u_j (prec_op), one reduction pass with the bookkeeping in its
+//   last block (k_dcgs_reduce), one update pass (k_dcgs_update),
+// and a last reduction-only step R that finishes column R - 1.  The host
+// enqueues kChunk steps and reads the state back once per chunk (at most
+// kChunk - 1 steps past convergence are computed and discarded: their
+// columns are not part of the solution update).
+template <class VS>
+hdg_status gmres(hdg_solver* S, bool tr, const VS* E, VS* x, double rtol, int max_iter, int& it, double& rel,
+                 cudaStream_t st) {
+  hdg_ctx* ctx = S->sys->ctx;
+  const int64_t n = S->n;
+  const int R = S->restart;
+  const int vb = grid_for(n, 256, 8 * S->sms);
+  VS* V = vec<VS>(S->V);
+  hdg_status rs;
+  // the preconditioner's factors of the current K
+  if ((rs = setup_enqueue(S, st, std::is_same<VS, float2>::value ? 1 : 0, tr ? 1 : 0)) != HDG_OK) return rs;
+  // ||M^-1 E||
+  prec_rhs(S, tr, E, V, st);
+  dots(S, (const VS*)V, 1, (const VS*)V, S->h, st);
+  if ((rs = ck(ctx, cudaMemcpyAsync(S->hpin, S->h, sizeof(double), cudaMemcpyDeviceToHost, st), "cudaMemcpyAsync")) != HDG_OK) return rs;
+  if ((rs = ck(ctx, cudaMemcpyAsync(&S->hpin[1], S->f.bad, sizeof(int), cudaMemcpyDeviceToHost, st), "cudaMemcpyAsync")) != HDG_OK) return rs;
+  if ((rs = ck(ctx, cudaStreamSynchronize(st), "cudaStreamSynchronize")) != HDG_OK) return rs;
+  int bad = 0;
+  std::memcpy(&bad, &S->hpin[1], sizeof(int));
+  if (bad) {
+    S->factored = false;
+    return fail(ctx, HDG_ESINGULAR, "hdg_trace_solve: a pivot block of the preconditioner is singular");
+  }
+  const double bnorm = std::sqrt(S->hpin[0]);
+  it = 0;
+  rel = 0.0;
+  if (!(bnorm > 0.0)) {  // E = 0: the solution is 0
+    if ((rs = ck(ctx, cudaMemsetAsync(x, 0, sizeof(VS) * n, st), "cudaMemsetAsync")) != HDG_OK) return rs;
+    return ck(ctx, cudaStreamSynchronize(st), "cudaStreamSynchronize");
+  }
+  constexpr int kChunk = 4;
+  const ArnoldiViews av = arnoldi_views(S->h, R);
+  rel = 1.0;
+  while (true) {
+    // r0 = M^-1 (E - K x) (the candidate u_0), beta = ||r0||
+    prec_res(S, tr, (const VS*)x, E, V, st);
+    dots(S, (const VS*)V, 1, (const VS*)V, S->h, st);
+    if ((rs = ck(ctx, cudaMemcpyAsync(S->hpin, S->h, sizeof(double), cudaMemcpyDeviceToHost, st), "cudaMemcpyAsync")) != HDG_OK) return rs;
+    if ((rs = ck(ctx, cudaStreamSynchronize(st), "cudaStreamSynchronize")) != HDG_OK) return rs;
+    const double beta = std::sqrt(S->hpin[0]);
+    rel = beta / bnorm;
+    if (!(rel > rtol) || it >= max_iter) break;
+    k_cycle_init<<<1, 1, 0, st>>>(S->h, R, beta, bnorm, rtol, it, max_iter);
+    for (int j0 = 0; j0 <= R; j0 += kChunk) {
+      const int j1 = std::min(R + 1, j0 + kChunk);
+      for (int j = j0; j < j1; ++j) {
+        const bool prod = j < R;
+        if (prod) prec_op(S, tr, (const VS*)(V + (int64_t)j * n), V + (int64_t)(j + 1) * n, st);
+        k_dcgs_reduce<VS><<<S->dot_blocks, kDotThreads, 0, st>>>(V, n, j, prod ? 1 : 0, n, S->partial, S->h, R,
+                                                                 S->ticket);
+        if (prod) k_dcgs_update<VS><<<S->dot_blocks, kDotThreads, 0, st>>>(V, n, j, n, S->h, R);
+      }
+      if ((rs = ck(ctx, cudaMemcpyAsync(S->hpin, av.sc, sizeof(double) * kArnoldiScalars, cudaMemcpyDeviceToHost, st),
+                   "cudaMemcpyAsync")) != HDG_OK)
+        return rs;
+      if ((rs = ck(ctx, cudaStreamSynchronize(st), "cudaStreamSynchronize")) != HDG_OK) return rs;
+      it = (int)S->hpin[6];
+      rel = S->hpin[1];
+      if (S->hpin[4] != 0.0) break;
+    }
+    // x += V y, H y = g (upper triangular), on the device
+    k_lsq<<<1, 256, 0, st>>>(S->h, R);
+    k_update_x<VS><<<vb, kDotThreads, 0, st>>>(V, n, av.y, av.sc + 5, x, n);
+  }
+  if ((rs = ck(ctx, cudaGetLastError(), "trace solve kernels")) != HDG_OK) return rs;
+  return (rel > rtol) ? fail(ctx, HDG_ETIMEOUT, "hdg_trace_solve: max_iter reached before rtol") : HDG_OK;
 }
 
 }  // namespace
@@ -1006,8 +1228,22 @@ hdg_status hdg_solver_set_preconditioner(hdg_solver* S, int32_t kind) {
       set_fi32(S, (float*)di);
     }
   }
+  if (S->arith == 1) {
+    hdg_status rs = ensure_ff(S, kind);
+    if (rs != HDG_OK) return rs;
+  }
   if (kind != S->precond) S->factored = false;
   S->precond = kind;
+  return HDG_OK;
+}
+
+hdg_status hdg_solver_set_arithmetic(hdg_solver* S, int32_t arith) {
+  if (!S || arith < 0 || arith > 1) return HDG_EINVAL;
+  if (arith == 1) {
+    hdg_status rs = ensure_ff(S, S->precond);
+    if (rs != HDG_OK) return rs;
+  }
+  S->arith = arith;
   return HDG_OK;
 }
 
@@ -1018,7 +1254,7 @@ hdg_status hdg_solver_setup(hdg_solver* S, void* stream) {
   HDG_ON_DEVICE(ctx, ctx->device);
   cudaStream_t st = (cudaStream_t)stream;
   hdg_status rs;
-  if ((rs = setup_enqueue(S, st)) != HDG_OK) return rs;
+  if ((rs = setup_enqueue(S, st, 0)) != HDG_OK) return rs;
   if ((rs = ck(ctx, cudaMemcpyAsync(S->hpin, S->f.bad, sizeof(int), cudaMemcpyDeviceToHost, st), "cudaMemcpyAsync")) != HDG_OK)
     return rs;
   if ((rs = ck(ctx, cudaStreamSynchronize(st), "cudaStreamSynchronize")) != HDG_OK) return rs;
@@ -1037,7 +1273,7 @@ hdg_status hdg_solver_precond_apply(hdg_solver* S, const double* r, double* z, i
   if (!S->factored) return fail(ctx, HDG_EINVAL, "hdg_solver_precond_apply: no preconditioner set up for this kind");
   if (r == S->tmp2 || z == S->tmp2) return HDG_EINVAL;
   HDG_ON_DEVICE(ctx, ctx->device);
-  prec_rhs(S, transpose != 0, r, z, (cudaStream_t)stream);
+  prec_rhs<double>(S, transpose != 0, r, z, (cudaStream_t)stream);  // binary64: the public apply
   return ck(ctx, cudaGetLastError(), "preconditioner apply");
 }
 
@@ -1064,108 +1300,32 @@ hdg_status hdg_trace_solve_ex(hdg_solver* S, const double* rhs, int32_t transpos
                               int32_t max_iter, int32_t* iters_out, double* rel_out, void* stream) {
   hdg::NvtxRange nvtx_range_("hdg::trace_solve");
   if (!S || !x || !(rtol > 0.0) || max_iter < 1) return HDG_EINVAL;
-  const bool tr = transpose != 0;
   hdg_ctx* ctx = S->sys->ctx;
   HDG_ON_DEVICE(ctx, ctx->device);
   cudaStream_t st = (cudaStream_t)stream;
-  const int64_t n = S->n;
-  const int R = S->restart;
-  const int vb = grid_for(n, 256, 8 * S->sms);
-  hdg_status rs;
   if (iters_out) *iters_out = 0;
   if (rel_out) *rel_out = 0.0;
-  // the preconditioner's factors of the current K
-  if ((rs = setup_enqueue(S, st)) != HDG_OK) return rs;
-  // ||M^-1 E||
   const double* E = rhs ? rhs : S->sys->ds.E;
-  prec_rhs(S, tr, E, S->V, st);
-  multidot(S, S->V, 1, S->V, n, S->h, st);
-  int bad = 0;
-  if ((rs = ck(ctx, cudaMemcpyAsync(S->hpin, S->h, sizeof(double), cudaMemcpyDeviceToHost, st), "cudaMemcpyAsync")) != HDG_OK) return rs;
-  if ((rs = ck(ctx, cudaMemcpyAsync(&S->hpin[1], S->f.bad, sizeof(int), cudaMemcpyDeviceToHost, st), "cudaMemcpyAsync")) != HDG_OK) return rs;
-  if ((rs = ck(ctx, cudaStreamSynchronize(st), "cudaStreamSynchronize")) != HDG_OK) return rs;
-  std::memcpy(&bad, &S->hpin[1], sizeof(int));
-  if (bad) {
-    S->factored = false;
-    return fail(ctx, HDG_ESINGULAR, "hdg_trace_solve: a pivot block of the preconditioner is singular");
-  }
-  const double bnorm = std::sqrt(S->hpin[0]);
-  if (!(bnorm > 0.0)) {  // E = 0: the solution is 0
-    if ((rs = ck(ctx, cudaMemsetAsync(x, 0, sizeof(double) * n, st), "cudaMemsetAsync")) != HDG_OK) return rs;
-    return ck(ctx, cudaStreamSynchronize(st), "cudaStreamSynchronize");
-  }
-  std::vector<double> H((size_t)(R + 1) * R), cs(R), sn(R), g(R + 1), y(R);
   int it = 0;
   double rel = 1.0;
-  while (true) {
-    // r0 = M^-1 (E - K x), beta = ||r0||
-    prec_res(S, tr, x, E, S->V, st);
-    multidot(S, S->V, 1, S->V, n, S->h, st);
-    if ((rs = ck(ctx, cudaMemcpyAsync(S->hpin, S->h, sizeof(double), cudaMemcpyDeviceToHost, st), "cudaMemcpyAsync")) != HDG_OK) return rs;
-    if ((rs = ck(ctx, cudaStreamSynchronize(st), "cudaStreamSynchronize")) != HDG_OK) return rs;
-    const double beta = std::sqrt(S->hpin[0]);
-    rel = beta / bnorm;
-    if (!(rel > rtol) || it >= max_iter) break;
-    k_scale<<<vb, 256, 0, st>>>(S->V, 1.0 / beta, n);
-    std::fill(g.begin(), g.end(), 0.0);
-    g[0] = beta;
-    int jn = 0;  // columns of H built in this cycle
-    for (int j = 0; j < R && it < max_iter; ++j) {
-      double* vj = S->V + (int64_t)j * n;
-      double* w = S->V + (int64_t)(j + 1) * n;
-      prec_op(S, tr, vj, w, st);
-      // classical Gram-Schmidt, twice (the second pass fused with ||w||^2); a
-      // reorthogonalise-when-needed test (Daniel et al., ||w'||^2 < ||w||^2 / 2)
-      // fires in almost every iteration of these trace systems, so both passes
-      // always run and one read-back per iteration suffices
-      multidot(S, S->V, j + 1, w, n, S->h, st);
-      axpy_v(S, S->V, j + 1, S->h, w, n, nullptr, st);
-      multidot(S, S->V, j + 1, w, n, S->h + (R + 1), st);
-      axpy_v(S, S->V, j + 1, S->h + (R + 1), w, n, S->h + 2 * (R + 1), st);
-      if ((rs = ck(ctx, cudaMemcpyAsync(S->hpin, S->h, sizeof(double) * (2 * (R + 1) + 1), cudaMemcpyDeviceToHost, st),
-                   "cudaMemcpyAsync")) != HDG_OK)
-        return rs;
-      if ((rs = ck(ctx, cudaStreamSynchronize(st), "cudaStreamSynchronize")) != HDG_OK) return rs;
-      ++it;
-      double* col = &H[(size_t)j * (R + 1)];  // column j of H, rows 0..j+1
-      for (int i = 0; i <= j; ++i) col[i] = S->hpin[i] + S->hpin[(R + 1) + i];
-      const double hn = std::sqrt(S->hpin[2 * (R + 1)]);
-      col[j + 1] = hn;
-      for (int i = 0; i < j; ++i) {  // earlier rotations
-        const double a = col[i], b = col[i + 1];
-        col[i] = cs[i] * a + sn[i] * b;
-        col[i + 1] = -sn[i] * a + cs[i] * b;
-      }
-      const double den = std::hypot(col[j], col[j + 1]);
-      cs[j] = den > 0.0 ? col[j] / den : 1.0;
-      sn[j] = den > 0.0 ? col[j + 1] / den : 0.0;
-      col[j] = den;
-      col[j + 1] = 0.0;
-      g[j + 1] = -sn[j] * g[j];
-      g[j] = cs[j] * g[j];
-      jn = j + 1;
-      rel = std::fabs(g[j + 1]) / bnorm;
-      if (!(rel > rtol) || !(hn > 0.0)) break;
-      k_scale<<<vb, 256, 0, st>>>(w, 1.0 / hn, n);
+  hdg_status rs;
+  if (S->arith == 1) {
+    // the solve runs on float-float copies of E and x; x is written back at the end
+    split_copy(S, E, S->eff, S->n, st);
+    split_copy(S, x, S->xff, S->n, st);
+    rs = gmres<float2>(S, transpose != 0, S->eff, S->xff, rtol, max_iter, it, rel, st);
+    if (rs == HDG_OK || rs == HDG_ETIMEOUT) {
+      k_join<<<grid_for(S->n, 256, 8 * S->sms), 256, 0, st>>>(S->xff, x, S->n);
+      hdg_status r2 = ck(ctx, cudaStreamSynchronize(st), "cudaStreamSynchronize");
+      if (r2 != HDG_OK) return r2;
     }
-    // x += V y, H y = g (upper triangular)
-    for (int i = jn - 1; i >= 0; --i) {
-      double s = g[i];
-      for (int k = i + 1; k < jn; ++k) s -= H[(size_t)k * (R + 1) + i] * y[k];
-      y[i] = s / H[(size_t)i * (R + 1) + i];
-    }
-    std::memcpy(S->hpin, y.data(), sizeof(double) * jn);
-    if ((rs = ck(ctx, cudaMemcpyAsync(S->coef, S->hpin, sizeof(double) * jn, cudaMemcpyHostToDevice, st),
-                 "cudaMemcpyAsync")) != HDG_OK)
-      return rs;
-    k_multiaxpy<<<vb, 256, 0, st>>>(S->V, n, jn, S->coef, 1.0, x, n);
-    // the pinned buffer is reused next cycle: wait for the copy
-    if ((rs = ck(ctx, cudaStreamSynchronize(st), "cudaStreamSynchronize")) != HDG_OK) return rs;
+  } else {
+    rs = gmres<double>(S, transpose != 0, E, x, rtol, max_iter, it, rel, st);
   }
-  if ((rs = ck(ctx, cudaGetLastError(), "trace solve kernels")) != HDG_OK) return rs;
+  if (rs != HDG_OK && rs != HDG_ETIMEOUT) return rs;
   if (iters_out) *iters_out = it;
   if (rel_out) *rel_out = rel;
-  return (rel > rtol) ? fail(ctx, HDG_ETIMEOUT, "hdg_trace_solve: max_iter reached before rtol") : HDG_OK;
+  return rs;
 }
 
 hdg_status hdg_solve_step_host(hdg_sys* sys, hdg_solver* S, const double* U, const double* Lam, double* dU,

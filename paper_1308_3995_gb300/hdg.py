@@ -40,7 +40,7 @@ EXPORTS = ["hdg_create", "hdg_destroy", "hdg_last_error", "hdg_mesh_create", "hd
            "hdg_sys_bucket_times", "hdg_sys_set_source", "hdg_batch_create", "hdg_batch_destroy",
            "hdg_batch_groups", "hdg_batch_condense", "hdg_batch_recover", "hdg_batch_step_host_async",
            "hdg_batch_autotune", "hdg_batch_graph_create", "hdg_batch_graph_launch", "hdg_batch_launches",
-           "hdg_sys_io", "hdg_batch_workspace_bytes", "hdg_batch_create_in"]
+           "hdg_sys_io", "hdg_batch_workspace_bytes", "hdg_batch_create_in", "hdg_solver_set_arithmetic"]
 
 
 class HdgError(RuntimeError):
@@ -155,6 +155,7 @@ def lib(build: bool = True):
                                       ctypes.POINTER(ctypes.c_double), _vp]
         L.hdg_trace_matvec.argtypes = [_vp, _vp, _vp, ctypes.c_int32, _vp]
         L.hdg_solver_set_preconditioner.argtypes = [_vp, ctypes.c_int32]
+        L.hdg_solver_set_arithmetic.argtypes = [_vp, ctypes.c_int32]
         L.hdg_solver_setup.argtypes = [_vp, _vp]
         L.hdg_solver_precond_apply.argtypes = [_vp, _vp, _vp, ctypes.c_int32, _vp]
         L.hdg_solver_colors.argtypes = [_vp, ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(ctypes.c_int32)]
@@ -276,6 +277,13 @@ class Solver:
     def set_preconditioner(self, kind: int):
         """hdg_solver_set_preconditioner: 0 block Jacobi, 1 block SGS, 2 block ILU(0), 3 ILU(0) binary32."""
         _check(lib().hdg_solver_set_preconditioner(self.h, int(kind)), self.sys.ctx.h)
+
+    BINARY64, FLOAT_FLOAT = 0, 1
+
+    def set_arithmetic(self, arith: int):
+        """hdg_solver_set_arithmetic: GMRES products and Krylov updates in binary64 (0) or in
+        double-word arithmetic on the binary32 pipe (1)."""
+        _check(lib().hdg_solver_set_arithmetic(self.h, int(arith)), self.sys.ctx.h)
 
     def setup(self, stream=None):
         """Factor the preconditioner for the system's current K (synchronises the stream)."""

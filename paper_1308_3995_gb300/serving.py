@@ -19,8 +19,8 @@ With ``solve=True`` a request is a whole pseudo-transient Newton step of
 Sec. 3.3 instead: condensation at a finite CFL, the GPU trace solve of
 K dLambda = E to a relative residual of 1e-10 (GMRES, block ILU(0) by
 default), reconstruction, and dU, dLambda copied back
-(``hdg_solve_step_host``).  The trace solve reads one residual estimate per
-GMRES iteration, so the call blocks its host thread: each stream slot then has
+(``hdg_solve_step_host``).  The trace solve reads its residual estimate back every few GMRES
+iterations, so the call blocks its host thread: each stream slot then has
 a worker thread that runs its requests' steps (the library releases the
 interpreter lock during the call); the system and the solver both live in
 the request's arena range.
@@ -208,12 +208,14 @@ class Server:
     def __init__(self, ctx: hdg.Context, arena_bytes: int, slots: int, precision: int, keep_outputs: bool = False,
                  solve: bool = False, precond: int = 2, rtol: float = 1e-10, cfl: float = 10.0,
                  restart: int = 30, max_iter: int = 5000, batched: bool = False, max_inflight: int = 2,
-                 batch_max_elems: int = 0):
+                 batch_max_elems: int = 0, solver_arith: int | None = None):
         import torch
         if batched and solve:
             raise ValueError("batched launches serve step requests (solve=False)")
         self.batched, self.max_inflight = bool(batched), int(max_inflight)
         self.batch_max_elems = int(batch_max_elems)   # 0: a batch takes every admitted request
+        # GMRES arithmetic of solve requests (hdg_solver_set_arithmetic): binary64 unless asked
+        self.solver_arith = 0 if solver_arith is None else int(solver_arith)
         self.ctx, self.slots, self.precision, self.keep = ctx, int(slots), int(precision), keep_outputs
         self.solve, self.precond, self.rtol, self.cfl = bool(solve), int(precond), float(rtol), float(cfl)
         self.restart, self.max_iter = int(restart), int(max_iter)
@@ -241,6 +243,7 @@ class Server:
                 base = self.buf.data_ptr() + off
                 sysm = hdg.System(self.ctx, r.mesh, prm, workspace=(base, n_sys))
                 sol = hdg.Solver(sysm, self.restart, self.precond, workspace=(base + n_sys, n_sol))
+                sol.set_arithmetic(self.solver_arith)
                 r.iters, _ = sol.step_host(r.U, r.Lam, r.dU_host, r.dLam_host, self.rtol, self.max_iter, st)
                 r.done_s = time.perf_counter() - t0_box[0]
                 if self.keep:
