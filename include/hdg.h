@@ -65,6 +65,10 @@
  *   - Every call that touches the GPU makes its context's device current for
  *     the duration of the call and restores the calling thread's current
  *     device before it returns.
+ *   - A call reports the CUDA errors of its own work: a pending non-sticky
+ *     error (cudaGetLastError) left by an earlier call of the caller or of
+ *     another library is discarded on entry.  Sticky errors (a faulted
+ *     context) are not cleared and fail the call.
  */
 #ifndef HDG_H_
 #define HDG_H_

@@ -53,10 +53,15 @@ class DeviceGuard {
 };
 
 // Entry-point prologue: `dev` current until the enclosing function returns;
-// `fail` is the calling translation unit's error helper.
+// `fail` is the calling translation unit's error helper.  A pending
+// non-sticky error left by an earlier call outside this entry point (the
+// caller's, or another library's) is discarded first, so that the launch
+// checks below report only this call's own errors (a sticky error -- a
+// kernel fault -- cannot be cleared and still surfaces).
 #define HDG_ON_DEVICE(ctx, dev)                                                     \
   ::hdg::DeviceGuard hdg_device_guard_(dev);                                        \
-  if (!hdg_device_guard_.ok()) return fail(ctx, HDG_ECUDA, "cudaSetDevice failed")
+  if (!hdg_device_guard_.ok()) return fail(ctx, HDG_ECUDA, "cudaSetDevice failed"); \
+  (void)cudaGetLastError()
 
 constexpr int kMaxP = 4;          // element degrees 1..4
 constexpr int kMaxNt = 60;        // 3 faces x 4 fields x (4 + 1) modes

@@ -1,8 +1,8 @@
 // Krylov-vector kernels of the GMRES trace solve (Sec. 3.4): dot products
 // with the basis, the Arnoldi process as delayed classical Gram-Schmidt with
 // re-orthogonalisation (one reduction and one update pass per iteration, the
-// Hessenberg bookkeeping on the device), and the solution update.  Every kernel is written once over the storage type ST of
-// the vectors:
+// Hessenberg bookkeeping on the device), and the solution update.  Every
+// kernel is written once over the storage type ST of the vectors:
 //   double  binary64 values, binary64 arithmetic (the FP64 pipe);
 //   float2  float-float pairs (hi, lo) in the same 8 bytes per value,
 //           double-word arithmetic Ar<ff> on the binary32 pipe.
@@ -13,9 +13,9 @@
 // Dot products: every thread takes its own pair rows (a grid-stride loop) for
 // a group of up to eight vectors, all their loads in flight together; the
 // block sums each vector's values through shared memory into one partial per
-// block in part[row][block]; the last block to finish (a ticket taken after a
-// fence) sums every row, one warp per row, in a fixed order -- the results are
-// bitwise reproducible.
+// block in part[row][block]; the partials are then summed in two levels by
+// the last blocks to finish (tickets taken after fences) in a fixed order --
+// the results are bitwise reproducible.
 #pragma once
 #include <cuda_runtime.h>
 
@@ -115,20 +115,57 @@ __device__ __forceinline__ void finish_rows(const double* part, int nrows, int n
   if (threadIdx.x == 0) *ticket = 0u;
 }
 
-// After every block has written its partials part[j][blockIdx.x], j < nrows,
-// the last block to finish sums them.
-__device__ __forceinline__ bool last_block_finish(const double* part, int nrows, double* out, double* last_out,
-                                                  unsigned* ticket) {
-  __shared__ bool s_last;
+// Two-level finish.  After every block has written its partials
+// part[j][blockIdx.x], j < nrows: the last block of each group of kFinGroup
+// consecutive blocks (a ticket per group, taken after a fence) sums its
+// group's partials into gpart[j][group] (group_finish); for a complete sum
+// the last group to finish (ticket[0]) then sums those into out
+// (finish_rows).  Each level is one round of loads and at most kFinGroup (or
+// the number of groups) blocks contend for one ticket.  ticket: 1 + groups
+// counters, zero between launches (re-armed here).
+constexpr int kFinGroup = 16;
+__host__ __device__ __forceinline__ int fin_groups(int nblk) { return (nblk + kFinGroup - 1) / kFinGroup; }
+
+// The first level: true in the block that wrote its group's sums.
+__device__ __forceinline__ bool group_finish(const double* part, int nrows, double* gpart, unsigned* ticket) {
+  __shared__ bool s_glast;
+  const int nblk = gridDim.x, grp = blockIdx.x / kFinGroup, ng = fin_groups(nblk);
+  const int b0 = grp * kFinGroup, gsize = min(kFinGroup, nblk - b0);
   __threadfence();
   __syncthreads();
-  if (threadIdx.x == 0) s_last = atomicAdd(ticket, 1u) == gridDim.x - 1;
+  if (threadIdx.x == 0) s_glast = atomicAdd(ticket + 1 + grp, 1u) == (unsigned)gsize - 1u;
   __syncthreads();
-  if (s_last) {
-    __threadfence();
-    finish_rows(part, nrows, gridDim.x, out, last_out, ticket);
+  if (!s_glast) return false;
+  __threadfence();
+  int tpr = 16;
+  while (tpr > 1 && tpr * nrows > (int)blockDim.x) tpr >>= 1;
+  const int sub = threadIdx.x & (tpr - 1);
+  for (int r0 = 0; r0 < nrows; r0 += blockDim.x / tpr) {
+    const int j = r0 + threadIdx.x / tpr;
+    double v = 0.0;
+    if (j < nrows)
+      for (int b = sub; b < gsize; b += tpr) v += __ldcg(part + (int64_t)j * nblk + b0 + b);
+    for (int o = tpr >> 1; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+    if (sub == 0 && j < nrows) gpart[(int64_t)j * ng + grp] = v;
   }
-  return s_last;
+  if (threadIdx.x == 0) ticket[1 + grp] = 0u;
+  return true;
+}
+
+// Both levels: true in the one block that wrote the complete sums.
+__device__ __forceinline__ bool last_block_finish(const double* part, int nrows, double* gpart, double* out,
+                                                  double* last_out, unsigned* ticket) {
+  __shared__ bool s_last;
+  if (!group_finish(part, nrows, gpart, ticket)) return false;
+  __threadfence();
+  __syncthreads();
+  const int ng = fin_groups(gridDim.x);
+  if (threadIdx.x == 0) s_last = atomicAdd(ticket, 1u) == (unsigned)ng - 1u;
+  __syncthreads();
+  if (!s_last) return false;
+  __threadfence();
+  finish_rows(gpart, nrows, ng, out, last_out, ticket);
+  return true;
 }
 
 constexpr int kGroup = 8;  // vectors per pass of the dot-product kernels (one per warp in the block reduction)
@@ -220,9 +257,9 @@ __device__ __forceinline__ void block_dots(const ST* __restrict__ V, int64_t ldv
 template <class ST>
 __global__ void __launch_bounds__(kDotThreads, 2) k_dots(const ST* __restrict__ V, int64_t ldv, int nvec,
                                                       const ST* __restrict__ w, int64_t n, double* __restrict__ part,
-                                                      double* __restrict__ out, unsigned* ticket) {
+                                                      double* gpart, double* __restrict__ out, unsigned* ticket) {
   block_dots<ST, true>(V, ldv, nvec, w, n >> 1, part);
-  last_block_finish(part, nvec, out, nullptr, ticket);
+  last_block_finish(part, nvec, gpart, out, nullptr, ticket);
 }
 
 // ---------------------------------------------------------------- device-side Arnoldi bookkeeping
@@ -240,9 +277,9 @@ __global__ void __launch_bounds__(kDotThreads, 2) k_dots(const ST* __restrict__ 
 // and the next candidate is u_{j+1} = (z - V_j c - v_j d) / rho.  One
 // update pass writes v_j and u_{j+1}: two passes over the basis per
 // iteration instead of four.  The norms come from the Pythagorean identity
-// (V orthonormal).  Everything but the two passes runs here, on the device,
-// in the last block of the reduction; the host reads the state back once per
-// chunk of iterations.
+// (V orthonormal).  Everything but the two passes runs on the device in one
+// extra block of the update launch, alongside the update; the host reads the
+// state back once per chunk of iterations.
 // Views into the solver's h buffer:
 //   red [2 (R+1)] the reduction's outputs (a_k = V_k . u, k <= j, then b_k = V_k . z),
 //   h1 [R+1] the first projection of the column being built,
@@ -287,14 +324,65 @@ __global__ void k_cycle_init(double* h, int R, double beta, double bnorm, double
   a.sc[8] = 0.0;
 }
 
-// Step j's bookkeeping, run by one whole block after the reduction: finish
-// column j - 1 (j >= 1) with its Givens rotation and the residual estimate
-// |g_j| / ||M^-1 E||, then (with_z: a product z was formed) start column j.
-// The recurrences over the rotations run in one thread on operands the block
-// loaded into shared memory.
-__device__ __forceinline__ void dcgs_step(double* h, int R, int j, int with_z) {
-  __shared__ double s_s[kMaxRestart + 1], s_c[kMaxRestart + 1], s_col[kMaxRestart + 1];
-  __shared__ double s_cs[kMaxRestart], s_sn[kMaxRestart], s_rho, s_stat;
+// The sums of step j's reduction in one block's shared memory (every block
+// of the update computes the same values in the same order): s_k = V_k . u
+// and c_k = V_k . z (k < j), alpha = u . u, gamma = u . z, rho =
+// sqrt(alpha - s^T s) (0 when that is not positive), d = (gamma - s^T c) / rho.
+struct DcgsSums {
+  double s[kMaxRestart + 1], c[kMaxRestart + 1];
+  double alpha, gamma, rho, d;
+};
+
+// Sum the group partials gpart[row][0..ng) (rows: a_0..a_j, then b_0..b_j
+// with_z) into t, tpr threads per row in group order; then s^T s and s^T c by
+// warp 0 (strided lane shares, a shuffle tree).
+__device__ __forceinline__ void dcgs_sums(const double* __restrict__ gpart, int ng, int j, int with_z, DcgsSums& t) {
+  const int nv = j + 1, nrows = with_z ? 2 * nv : nv;
+  int tpr = 32;
+  while (tpr > 1 && tpr * nrows > (int)blockDim.x) tpr >>= 1;
+  const int sub = threadIdx.x & (tpr - 1);
+  for (int r0 = 0; r0 < nrows; r0 += blockDim.x / tpr) {
+    const int r = r0 + threadIdx.x / tpr;
+    double v = 0.0;
+    if (r < nrows)
+      for (int b = sub; b < ng; b += tpr) v += __ldcg(gpart + (int64_t)r * ng + b);
+    for (int o = tpr >> 1; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+    if (sub == 0 && r < nrows) {
+      if (r < j) t.s[r] = v;
+      else if (r == j) t.alpha = v;
+      else if (r < nv + j) t.c[r - nv] = v;
+      else t.gamma = v;
+    }
+  }
+  __syncthreads();
+  if (threadIdx.x < 32) {
+    double ss = 0.0, scv = 0.0;
+    for (int q = threadIdx.x; q < j; q += 32) {
+      ss = fma(t.s[q], t.s[q], ss);
+      if (with_z) scv = fma(t.s[q], t.c[q], scv);
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      ss += __shfl_down_sync(0xffffffffu, ss, o);
+      scv += __shfl_down_sync(0xffffffffu, scv, o);
+    }
+    if (threadIdx.x == 0) {
+      const double rho2 = t.alpha - ss;
+      t.rho = rho2 > 0.0 ? sqrt(rho2) : 0.0;
+      t.d = (with_z && t.rho > 0.0) ? (t.gamma - scv) / t.rho : 0.0;
+    }
+  }
+  __syncthreads();
+}
+
+// Step j's bookkeeping, run by one whole block from the sums t: finish
+// column j - 1 (j >= 1) -- raw column h1 + s with h_{j,j-1} = rho, its
+// Givens rotation, the residual estimate |g_j| / ||M^-1 E|| and the stopping
+// test --, then (with_z: a product z was formed) start column j: h1_j.  The
+// recurrence over the rotations runs in one thread, in registers, on operands
+// the block loaded into shared memory.
+__device__ __forceinline__ void dcgs_step(double* h, int R, int j, int with_z, const DcgsSums& t) {
+  __shared__ double s_col[kMaxRestart + 1], s_cs[kMaxRestart], s_sn[kMaxRestart], s_stat;
   ArnoldiViews a = arnoldi_views(h, R);
   double* sc = a.sc;
   const double st = sc[4], its = sc[6], itmax = sc[7];
@@ -304,37 +392,31 @@ __device__ __forceinline__ void dcgs_step(double* h, int R, int j, int with_z) {
     return;
   }
   const int nr = R + 1;
-  for (int k = threadIdx.x; k < j; k += blockDim.x) {
-    s_s[k] = a.red[k];
-    if (with_z) s_c[k] = a.red[j + 1 + k];
-    s_col[k] = a.h1[k] + s_s[k];
-  }
+  const double rho = t.rho;
+  for (int k = threadIdx.x; k < j; k += blockDim.x) s_col[k] = a.h1[k] + t.s[k];
   for (int k = threadIdx.x; k + 1 < j; k += blockDim.x) {
     s_cs[k] = a.cs[k];
     s_sn[k] = a.sn[k];
   }
+  if (j >= 1) {  // the raw column, written in parallel
+    double* raw = a.Hraw + (size_t)(j - 1) * nr;
+    for (int k = threadIdx.x; k <= j; k += blockDim.x) raw[k] = k < j ? a.h1[k] + t.s[k] : rho;
+  }
   __syncthreads();
   if (threadIdx.x == 0) {
-    double ss = 0.0;
-    for (int k = 0; k < j; ++k) ss = fma(s_s[k], s_s[k], ss);
-    const double rho = sqrt(fmax(a.red[j] - ss, 0.0));
     double stat = 0.0;
     if (j == 0) {
       a.g[0] = rho;
       if (!(rho > 0.0)) stat = 1.0;
     } else {
-      // column j - 1: raw, then rotated by the earlier rotations and a new one
-      double* raw = a.Hraw + (size_t)(j - 1) * nr;
-      for (int k = 0; k < j; ++k) raw[k] = s_col[k];
-      raw[j] = rho;
-      s_col[j] = rho;
-      for (int k = 0; k + 1 < j; ++k) {
-        const double x = s_col[k], z = s_col[k + 1];
+      double x = s_col[0];
+      for (int k = 0; k + 1 < j; ++k) {  // earlier rotations, carried in registers
+        const double z = s_col[k + 1];
         s_col[k] = s_cs[k] * x + s_sn[k] * z;
-        s_col[k + 1] = -s_sn[k] * x + s_cs[k] * z;
+        x = -s_sn[k] * x + s_cs[k] * z;
       }
-      const double den = hypot(s_col[j - 1], s_col[j]);
-      const double cr = den > 0.0 ? s_col[j - 1] / den : 1.0, sr = den > 0.0 ? s_col[j] / den : 0.0;
+      const double den = hypot(x, rho);
+      const double cr = den > 0.0 ? x / den : 1.0, sr = den > 0.0 ? rho / den : 0.0;
       a.cs[j - 1] = cr;
       a.sn[j - 1] = sr;
       s_col[j - 1] = den;
@@ -342,8 +424,6 @@ __device__ __forceinline__ void dcgs_step(double* h, int R, int j, int with_z) {
       const double gj = a.g[j - 1];
       a.g[j] = -sr * gj;
       a.g[j - 1] = cr * gj;
-      double* col = a.H + (size_t)(j - 1) * nr;
-      for (int k = 0; k <= j; ++k) col[k] = s_col[k];
       sc[5] = j;
       sc[6] = its + 1.0;
       const double rel = fabs(a.g[j]) / sc[2];
@@ -351,30 +431,27 @@ __device__ __forceinline__ void dcgs_step(double* h, int R, int j, int with_z) {
       if (!(rel > sc[3]) || !(rho > 0.0)) stat = 1.0;
     }
     if (stat != 0.0) sc[4] = stat;
-    s_rho = rho;
     s_stat = stat;
   }
   __syncthreads();
+  if (j >= 1) {
+    double* col = a.H + (size_t)(j - 1) * nr;
+    for (int k = threadIdx.x; k <= j; k += blockDim.x) col[k] = s_col[k];
+  }
   if (s_stat != 0.0 || !with_z) return;
   // start column j: its first projection h1_j
-  const double rho = s_rho, rinv = 1.0 / rho;
+  const double rinv = 1.0 / rho;
   for (int k = threadIdx.x; k < j; k += blockDim.x) {
     double hs = 0.0;  // (H_top s)_k: column i has rows <= i + 1
-    for (int i = (k > 0 ? k - 1 : 0); i < j; ++i) hs = fma(a.Hraw[(size_t)i * nr + k], s_s[i], hs);
-    a.h1[k] = (s_c[k] - hs) * rinv;
+    for (int i = (k > 0 ? k - 1 : 0); i < j; ++i) hs = fma(a.Hraw[(size_t)i * nr + k], t.s[i], hs);
+    a.h1[k] = (t.c[k] - hs) * rinv;
   }
-  if (threadIdx.x == 0) {
-    double sdotc = 0.0;
-    for (int k = 0; k < j; ++k) sdotc = fma(s_s[k], s_c[k], sdotc);
-    const double d = (a.red[2 * j + 1] - sdotc) * rinv;
-    a.h1[j] = d * rinv - (j >= 1 ? s_s[j - 1] : 0.0);
-    sc[0] = rinv;
-    sc[8] = d;
-  }
+  if (threadIdx.x == 0) a.h1[j] = t.d * rinv - (j >= 1 ? t.s[j - 1] : 0.0);
 }
 
 // H y = g (upper triangular, the cycle's columns): H and g loaded into shared
-// memory by the block, the back substitution by one thread on them
+// memory by the block, the back substitution column by column (y_i, then
+// every thread removes column i from the rows above it)
 __global__ void k_lsq(double* h, int R) {
   __shared__ double s_h[(kMaxRestart + 1) * kMaxRestart], s_y[kMaxRestart + 1];
   ArnoldiViews a = arnoldi_views(h, R);
@@ -382,26 +459,27 @@ __global__ void k_lsq(double* h, int R) {
   for (int t = threadIdx.x; t < jn * (R + 1); t += blockDim.x) s_h[t] = a.H[t];
   for (int t = threadIdx.x; t < jn; t += blockDim.x) s_y[t] = a.g[t];
   __syncthreads();
-  if (threadIdx.x == 0)
-    for (int i = jn - 1; i >= 0; --i) {
-      double v = s_y[i];
-      for (int k = i + 1; k < jn; ++k) v -= s_h[(size_t)k * (R + 1) + i] * s_y[k];
-      s_y[i] = v / s_h[(size_t)i * (R + 1) + i];
-    }
-  __syncthreads();
+  for (int i = jn - 1; i >= 0; --i) {
+    const double* col = s_h + (size_t)i * (R + 1);
+    const double yi = s_y[i] / col[i];  // every thread, the same value
+    __syncthreads();
+    if (threadIdx.x == 0) s_y[i] = yi;
+    for (int q = threadIdx.x; q < i; q += blockDim.x) s_y[q] -= col[q] * yi;
+    __syncthreads();
+  }
   for (int t = threadIdx.x; t < jn; t += blockDim.x) a.y[t] = s_y[t];
 }
 
 // DCGS2 reduction of step j: a_k = V_k . u and b_k = V_k . z for k <= j
 // (u = V_j, the candidate; z = V_{j+1} = A u, with_z; without it only the
-// a_k: the last step of a cycle, which finishes its last column), then the
-// step's bookkeeping (dcgs_step) by the last block to finish.  Every thread
-// takes its own pair rows, four basis vectors and both right-hand vectors at
-// a time (two rows' loads in flight).
+// a_k: the last step of a cycle, which finishes its last column), summed to
+// one value per group of kFinGroup blocks (gpart; the update sums those).
+// Every thread takes its own pair rows, four basis vectors and both
+// right-hand vectors at a time (two rows' loads in flight).
 template <class ST>
 __global__ void __launch_bounds__(kDotThreads, 2) k_dcgs_reduce(const ST* __restrict__ V, int64_t ldv, int j,
                                                                 int with_z, int64_t n, double* __restrict__ part,
-                                                                double* h, int R, unsigned* ticket) {
+                                                                double* gpart, unsigned* ticket) {
   using K = KV<ST>;
   using A = typename K::A;
   using AR = Ar<A>;
@@ -457,38 +535,48 @@ __global__ void __launch_bounds__(kDotThreads, 2) k_dcgs_reduce(const ST* __rest
     }
     block_rows_partial(acc, valid, row, part);
   }
-  const ArnoldiViews av = arnoldi_views(h, R);
-  if (last_block_finish(part, with_z ? 2 * nv : nv, av.red, nullptr, ticket)) {
-    __syncthreads();  // the outputs written by the block's warps
-    dcgs_step(h, R, j, with_z);
-  }
+  group_finish(part, with_z ? 2 * nv : nv, gpart, ticket);
 }
 
-// DCGS2 update of step j: v_j = (u - V_j s) / rho into slot j and
-// u_{j+1} = (z - V_j c - v_j d) / rho into slot j + 1 (s, c from the
-// reduction, 1 / rho and d from dcgs_step), one pass over the basis;
-// skipped once the cycle has stopped.  Slots below j are only read.
+// DCGS2 update of step j, one launch of nupd + 1 blocks: every block sums
+// the reduction's group partials itself (dcgs_sums: the same values in every
+// block); blocks below nupd write v_j = (u - V_j s) / rho into slot j and
+// u_{j+1} = (z - V_j c - v_j d) / rho into slot j + 1 (with_z; one pass over
+// the basis), while block nupd runs the step's Hessenberg bookkeeping
+// (dcgs_step) alongside.  The update is skipped once the cycle has stopped
+// or at a breakdown (rho = 0); a stop decided by this very step may or may
+// not skip it, and the two slots are then not part of the solution either
+// way.  Slots below j are only read.
 template <class ST>
-__global__ void __launch_bounds__(kDotThreads) k_dcgs_update(ST* V, int64_t ldv, int j, int64_t n, const double* h,
+__global__ void __launch_bounds__(kDotThreads) k_dcgs_update(ST* V, int64_t ldv, int j, int with_z, int64_t n,
+                                                             const double* __restrict__ gpart, int ng, double* h,
                                                              int R) {
   using K = KV<ST>;
   using A = typename K::A;
   using AR = Ar<A>;
   using P = typename K::P;
-  const ArnoldiViews av = arnoldi_views(const_cast<double*>(h), R);
-  if (av.sc[4] != 0.0) return;
+  __shared__ DcgsSums t;
   __shared__ A s_s[kMaxRestart + 1], s_c[kMaxRestart + 1];
-  for (int k = threadIdx.x; k < j; k += blockDim.x) {
-    s_s[k] = K::from_d(av.red[k]);
-    s_c[k] = K::from_d(av.red[j + 1 + k]);
+  const ArnoldiViews av = arnoldi_views(h, R);
+  const int nupd = gridDim.x - 1;
+  if (av.sc[4] != 0.0) return;
+  dcgs_sums(gpart, ng, j, with_z, t);
+  if ((int)blockIdx.x == nupd) {
+    dcgs_step(h, R, j, with_z, t);
+    return;
+  }
+  if (!with_z || !(t.rho > 0.0)) return;
+  for (int q = threadIdx.x; q < j; q += blockDim.x) {
+    s_s[q] = K::from_d(t.s[q]);
+    s_c[q] = K::from_d(t.c[q]);
   }
   __syncthreads();
-  const A rinv = K::from_d(av.sc[0]), d = K::from_d(av.sc[8]);
+  const A rinv = K::from_d(1.0 / t.rho), d = K::from_d(t.d);
   const ST* Vr = V;  // slots < j: read-only in this launch
   P* u2 = pairs(V + (int64_t)j * ldv);
   P* z2 = pairs(V + (int64_t)(j + 1) * ldv);
   const int64_t n2 = n >> 1;
-  for (int64_t i = blockIdx.x * (int64_t)kDotThreads + threadIdx.x; i < n2; i += (int64_t)gridDim.x * kDotThreads) {
+  for (int64_t i = blockIdx.x * (int64_t)kDotThreads + threadIdx.x; i < n2; i += (int64_t)nupd * kDotThreads) {
     const P ui = u2[i], zi = z2[i];
     A ux = K::x(ui), uy = K::y(ui), zx = K::x(zi), zy = K::y(zi);
     for (int k0 = 0; k0 < j; k0 += kGroup) {

@@ -26,16 +26,17 @@
 //                 Dinv_e t, Dinv_e (b_e - t), Dinv_e b_e or b_e - t;
 //   hdg_krylov.cuh  the Arnoldi process as delayed classical Gram-Schmidt
 //                 with re-orthogonalisation: per iteration one reduction
-//                 pass (with the Hessenberg column, its Givens rotation and
-//                 the residual estimate in its last block) and one update
-//                 pass over the basis; the triangular least-squares solve
-//                 k_lsq and x += V y, all on the device (the state is read
-//                 back once per chunk of iterations).
+//                 pass and one update pass over the basis (the Hessenberg
+//                 column, its Givens rotation and the residual estimate in
+//                 an extra block of the update launch); the triangular
+//                 least-squares solve k_lsq and x += V y, all on the device
+//                 (the state is read back once per chunk of iterations).
 #include <cuda_runtime.h>
 
 #include <algorithm>
 #include <cmath>
 #include <cstring>
+#include <map>
 #include <string>
 #include <type_traits>
 #include <vector>
@@ -624,8 +625,9 @@ struct hdg_solver {
   int dot_blocks = 0;
   FaceDev f{};
   double* V = nullptr;        // [restart + 1][n] (float-float pairs in the same bytes under arith 1)
-  double* partial = nullptr;  // [restart + 1][dot_blocks]
-  unsigned* ticket = nullptr; // last-block ticket of the fused reductions (zero between launches)
+  double* partial = nullptr;  // [2 (restart + 1)][dot_blocks] per-block partial sums
+  double* gpart = nullptr;    // [2 (restart + 1)][groups] group sums of the two-level finish
+  unsigned* ticket = nullptr; // [1 + groups] tickets of the two-level finish (zero between launches)
   double* h = nullptr;        // Arnoldi state (ArnoldiViews)
   double* coef = nullptr;     // [restart + 1] spare
   double* zero = nullptr;     // [n] zeros
@@ -649,6 +651,11 @@ struct hdg_solver {
   FaceDevT<float> fi32ff{};   // kind 3: the binary32 factors in lane order (in fiff's buffers)
   float2* xff = nullptr;      // [n]
   float2* eff = nullptr;      // [n]
+  // CUDA graphs of the GMRES chunks, captured on first use: key (chunk start,
+  // arithmetic, preconditioner kind, transpose); chunk launches replay them
+  cudaStream_t cap = nullptr;
+  std::map<long long, cudaGraphExec_t> chunk_graphs;
+  bool graphs_off = false;    // a capture failed once: launch directly
   bool external_ws = false;   // device buffers carved from the caller's workspace
   bool hpin_pageable = false; // host mirror from new[] (caller's workspace) or pinned
   int64_t k_vals = 0;         // doubles in K
@@ -848,7 +855,7 @@ hdg_status setup_enqueue(hdg_solver* S, cudaStream_t st, int arith, int tr = 0) 
 // out[j] = V_j . w for j < nvec (device), one launch
 template <class VS>
 void dots(hdg_solver* S, const VS* V, int nvec, const VS* w, double* out, cudaStream_t st) {
-  k_dots<VS><<<S->dot_blocks, kDotThreads, 0, st>>>(V, S->n, nvec, w, S->n, S->partial, out, S->ticket);
+  k_dots<VS><<<S->dot_blocks, kDotThreads, 0, st>>>(V, S->n, nvec, w, S->n, S->partial, S->gpart, out, S->ticket);
 }
 
 }  // namespace
@@ -882,9 +889,10 @@ SolverPlan plan_solver(const hdg_mesh* M, int restart, int precond, int sms) {
   p.dof = take(sizeof(int64_t) * nf);
   p.dinv = take(sizeof(double) * p.dinv_len);
   p.bad = take(sizeof(int));
-  p.ticket = take(sizeof(unsigned));
+  p.ticket = take(sizeof(unsigned) * (1 + fin_groups(p.dot_blocks)));
   p.V = take(sizeof(double) * nr * p.n);
-  p.part = take(sizeof(double) * 2 * nr * p.dot_blocks);  // two rows per basis vector in an Arnoldi reduction
+  // two rows per basis vector in an Arnoldi reduction; then the group sums of the two-level finish
+  p.part = take(sizeof(double) * 2 * nr * (p.dot_blocks + fin_groups(p.dot_blocks)));
   p.h = take(sizeof(double) * arnoldi_doubles(restart));
   p.coef = take(sizeof(double) * nr);
   p.zero = take(sizeof(double) * p.n);
@@ -996,7 +1004,7 @@ hdg_status solver_build(hdg_sys* sys, int32_t restart, int32_t precond, void* ws
   if (st == HDG_OK) st = ck(ctx, cudaMemcpy(dof, dinv_off.data(), sizeof(int64_t) * dinv_off.size(), cudaMemcpyHostToDevice), "cudaMemcpy");
   if (st == HDG_OK) st = ck(ctx, cudaMemcpy(kt, tblk.data(), sizeof(int64_t) * tblk.size(), cudaMemcpyHostToDevice), "cudaMemcpy");
   if (st == HDG_OK) st = ck(ctx, cudaMemset(base + P.zero, 0, sizeof(double) * S->n), "cudaMemset");
-  if (st == HDG_OK) st = ck(ctx, cudaMemset(base + P.ticket, 0, sizeof(unsigned)), "cudaMemset");
+  if (st == HDG_OK) st = ck(ctx, cudaMemset(base + P.ticket, 0, sizeof(unsigned) * (1 + fin_groups(P.dot_blocks))), "cudaMemset");
   if (st == HDG_OK && !by_color.empty())
     st = ck(ctx, cudaMemcpy(cols, by_color.data(), sizeof(int) * by_color.size(), cudaMemcpyHostToDevice), "cudaMemcpy");
   if (st == HDG_OK && !color.empty())
@@ -1018,6 +1026,7 @@ hdg_status solver_build(hdg_sys* sys, int32_t restart, int32_t precond, void* ws
   S->f.bad = (int*)(base + P.bad);
   S->V = (double*)(base + P.V);
   S->partial = (double*)(base + P.part);
+  S->gpart = S->partial + (size_t)2 * nr * P.dot_blocks;
   S->ticket = (unsigned*)(base + P.ticket);
   S->h = (double*)(base + P.h);
   S->coef = (double*)(base + P.coef);
@@ -1081,18 +1090,73 @@ hdg_status ensure_ff(hdg_solver* S, int kind) {
   return need_k && need_i ? ensure_ff(S, kind) : HDG_OK;
 }
 
+// Steps j0 .. j1 - 1 of a GMRES cycle, enqueued on st: z = M^{-1} K u_j, the
+// reduction, the update with the bookkeeping block (the last step R of a
+// cycle: the reduction and the bookkeeping alone).
+template <class VS>
+void enqueue_chunk(hdg_solver* S, bool tr, int j0, int j1, cudaStream_t st) {
+  const int64_t n = S->n;
+  const int R = S->restart;
+  VS* V = vec<VS>(S->V);
+  for (int j = j0; j < j1; ++j) {
+    const bool prod = j < R;
+    if (prod) prec_op(S, tr, (const VS*)(V + (int64_t)j * n), V + (int64_t)(j + 1) * n, st);
+    k_dcgs_reduce<VS><<<S->dot_blocks, kDotThreads, 0, st>>>(V, n, j, prod ? 1 : 0, n, S->partial, S->gpart,
+                                                             S->ticket);
+    k_dcgs_update<VS><<<(prod ? S->dot_blocks : 0) + 1, kDotThreads, 0, st>>>(
+        V, n, j, prod ? 1 : 0, n, S->gpart, fin_groups(S->dot_blocks), S->h, R);
+  }
+}
+
+// The chunk's launches as an instantiated CUDA graph (captured on the
+// solver's own stream on first use, kept until the solver is destroyed), or
+// null: a solver in a caller's workspace launches directly (instantiation may
+// allocate), and so does every solver after a capture that failed.  The
+// graph's arguments are the solver's own buffers, fixed for its lifetime.
+template <class VS>
+cudaGraphExec_t chunk_graph(hdg_solver* S, bool tr, int j0, int j1) {
+  if (S->external_ws || S->graphs_off) return nullptr;
+  const int arith = std::is_same<VS, float2>::value ? 1 : 0;
+  const long long key = (long long)j0 | ((long long)arith << 8) | ((long long)S->precond << 9) | ((long long)tr << 12);
+  auto it = S->chunk_graphs.find(key);
+  if (it != S->chunk_graphs.end()) return it->second;
+  if (!S->cap && cudaStreamCreateWithFlags(&S->cap, cudaStreamNonBlocking) != cudaSuccess) {
+    S->cap = nullptr;
+    S->graphs_off = true;
+    cudaGetLastError();
+    return nullptr;
+  }
+  cudaGraph_t g = nullptr;
+  cudaGraphExec_t ge = nullptr;
+  bool ok = cudaStreamBeginCapture(S->cap, cudaStreamCaptureModeThreadLocal) == cudaSuccess;
+  if (ok) {
+    enqueue_chunk<VS>(S, tr, j0, j1, S->cap);
+    ok = cudaStreamEndCapture(S->cap, &g) == cudaSuccess && g;
+  }
+  if (ok) ok = cudaGraphInstantiate(&ge, g, 0) == cudaSuccess;
+  if (g) cudaGraphDestroy(g);
+  if (!ok) {
+    if (ge) cudaGraphExecDestroy(ge);
+    S->graphs_off = true;
+    cudaGetLastError();  // the failure is handled: direct launches from now on
+    return nullptr;
+  }
+  S->chunk_graphs[key] = ge;
+  return ge;
+}
+
 // Restarted, left-preconditioned GMRES on vectors of storage VS (binary64, or
 // float-float pairs under arith 1): x += the solution of M^{-1} K dx =
 // M^{-1} (E - K x) to rtol of ||M^{-1} E||.  Each restart forms the true
 // residual r0 = M^{-1} (E - K x) and its norm on the host's side of the
 // loop; the cycle then runs the Arnoldi process as delayed classical
 // Gram-Schmidt with re-orthogonalisation (hdg_krylov.cuh), step j being
-//   z = M^{-1} K u_j (prec_op), one reduction pass with the bookkeeping in its
-//   last block (k_dcgs_reduce), one update pass (k_dcgs_update),
+//   z = M^{-1} K u_j (prec_op), one reduction pass (k_dcgs_reduce), one
+//   update pass with the Hessenberg bookkeeping in an extra block (k_dcgs_update),
 // and a last reduction-only step R that finishes column R - 1.  The host
-// enqueues kChunk steps and reads the state back once per chunk (at most
-// kChunk - 1 steps past convergence are computed and discarded: their
-// columns are not part of the solution update).
+// launches kChunk steps at a time (a captured graph per chunk) and reads the
+// state back once per chunk (at most kChunk - 1 steps past convergence are
+// computed and discarded: their columns are not part of the solution update).
 template <class VS>
 hdg_status gmres(hdg_solver* S, bool tr, const VS* E, VS* x, double rtol, int max_iter, int& it, double& rel,
                  cudaStream_t st) {
@@ -1138,12 +1202,11 @@ hdg_status gmres(hdg_solver* S, bool tr, const VS* E, VS* x, double rtol, int ma
     k_cycle_init<<<1, 1, 0, st>>>(S->h, R, beta, bnorm, rtol, it, max_iter);
     for (int j0 = 0; j0 <= R; j0 += kChunk) {
       const int j1 = std::min(R + 1, j0 + kChunk);
-      for (int j = j0; j < j1; ++j) {
-        const bool prod = j < R;
-        if (prod) prec_op(S, tr, (const VS*)(V + (int64_t)j * n), V + (int64_t)(j + 1) * n, st);
-        k_dcgs_reduce<VS><<<S->dot_blocks, kDotThreads, 0, st>>>(V, n, j, prod ? 1 : 0, n, S->partial, S->h, R,
-                                                                 S->ticket);
-        if (prod) k_dcgs_update<VS><<<S->dot_blocks, kDotThreads, 0, st>>>(V, n, j, n, S->h, R);
+      cudaGraphExec_t ge = chunk_graph<VS>(S, tr, j0, j1);
+      if (ge) {
+        if ((rs = ck(ctx, cudaGraphLaunch(ge, st), "cudaGraphLaunch")) != HDG_OK) return rs;
+      } else {
+        enqueue_chunk<VS>(S, tr, j0, j1, st);
       }
       if ((rs = ck(ctx, cudaMemcpyAsync(S->hpin, av.sc, sizeof(double) * kArnoldiScalars, cudaMemcpyDeviceToHost, st),
                    "cudaMemcpyAsync")) != HDG_OK)
@@ -1185,6 +1248,8 @@ int64_t hdg_solver_workspace_bytes(const hdg_mesh* mesh, int32_t restart, int32_
 hdg_status hdg_solver_destroy(hdg_solver* S) {
   if (!S) return HDG_EINVAL;
   hdg::DeviceGuard dg(S->sys->ctx->device);
+  for (auto& kv : S->chunk_graphs) cudaGraphExecDestroy(kv.second);
+  if (S->cap) cudaStreamDestroy(S->cap);
   for (void* p : S->allocs) cudaFree(p);
   if (S->hpin) {
     if (S->hpin_pageable) delete[] S->hpin;
