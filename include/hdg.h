@@ -170,13 +170,16 @@ hdg_status hdg_mesh_create(hdg_ctx* ctx, int32_t n_elem, int32_t nfield, const d
  * l of each element -- 0 interior; Euler (nfield = 4): 1 slip wall, 2 far
  * field (characteristic upwinding against the free stream of hdg_params.mach /
  * aoa); Navier-Stokes (nfield = 12): 3 no-slip adiabatic wall (w_b = (rho, 0,
- * 0, E), wall viscous flux (0, tau, 0)).  A boundary face carries no trace
+ * 0, E), wall viscous flux (0, tau, 0)), 2 far field (the same characteristic
+ * state, the viscous flux f_v(w_b, q) at it whole, q the interior gradient;
+ * the gradient equations' boundary term -<tau.n, w_b(w)> couples the fields
+ * through d w_b / d w).  A boundary face carries no trace
  * unknowns: the element gets the boundary operator of Sec. 3.2 and its
  * Jacobian instead, elem_face is -1 there, and rows of K next to a boundary
  * keep their five slots with the unused ones marked k_col = -1 (empty blocks,
  * after the used columns).  Every untagged face must be shared by exactly two
  * elements.  HDG_EINVAL for a kind outside 0..3 or kind 3 on an Euler mesh;
- * HDG_ENOTSUP for kinds 1, 2 on a Navier-Stokes mesh. */
+ * HDG_ENOTSUP for kind 1 (slip wall) on a Navier-Stokes mesh. */
 hdg_status hdg_mesh_create_bc(hdg_ctx* ctx, int32_t n_elem, int32_t nfield, const double* elem_xy,
                               const int32_t* elem_vid, const int8_t* elem_p, const int8_t* elem_bc,
                               hdg_mesh** out);

@@ -143,8 +143,9 @@ hdg_status hdg_mesh_create_bc(hdg_ctx* ctx, int32_t n_elem, int32_t nfield, cons
     if (b < 0 || b > 3) return fail(ctx, HDG_EINVAL, "hdg_mesh_create_bc: boundary kind not in 0..3");
     if (b == 3 && nfield == 4)
       return fail(ctx, HDG_EINVAL, "hdg_mesh_create_bc: the no-slip wall (kind 3) is a Navier-Stokes boundary");
-    if ((b == 1 || b == 2) && nfield == 12)
-      return fail(ctx, HDG_ENOTSUP, "hdg_mesh_create_bc: Navier-Stokes boundaries are no-slip adiabatic walls (kind 3)");
+    if (b == 1 && nfield == 12)
+      return fail(ctx, HDG_ENOTSUP,
+                  "hdg_mesh_create_bc: Navier-Stokes boundaries are no-slip adiabatic walls (kind 3) or far field (kind 2)");
     any_bc |= b != 0;
   }
   HDG_ON_DEVICE(ctx, ctx->device);

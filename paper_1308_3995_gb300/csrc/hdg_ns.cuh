@@ -28,6 +28,14 @@
 // equations see -<tau.n, w_b>, so A_qw of the fields rho and E gains
 // -n_k |e| <phi_i, phi_j>_e (D_k^wall below) and A_ww gains the wall flux's
 // Jacobian in its columns rho and E.
+// Characteristic far field (Sec. 2.1, viscous flux at the far-field state):
+// w_b(w) by characteristic upwinding against the free stream, the flux
+// (f_c(w_b) - f_v(w_b, q)) . n whole, its Jacobian (d f / d w_b)(d w_b / d w)
+// in all four columns of A_ww; the gradient equations see -<tau.n, w_b(w)>, so
+// A_qw gains -n_k sum_x phi_i(x) (we d w_b / d w)_fg(x) phi_j(x) over the edge
+// points x, which couples the fields: its products in the q elimination, in
+// C', in X_q and in the adjoint's transposed elimination run through the
+// values at those points (a low-rank update of the field-diagonal blocks).
 #pragma once
 
 #include <cuda_runtime.h>
@@ -47,6 +55,59 @@ namespace hdg {
 // in binary64, 2.48 -> 4.25 M in float-float, against two CTAs of 256); 256
 // otherwise (at p = 2 the smaller CTA measured no better in binary64 and worse in
 // float-float, its shared memory allowing only two per SM on mixed meshes)
+// One far-field edge point of the Navier-Stokes kernel (Sec. 2.1): w_b(w) by
+// characteristic upwinding against the free stream and d w_b / d w, the flux
+// (f_c(w_b) - f_v(w_b, q)) . n whole (we times it into fhat[4]), d fhat / d w =
+// (d f / d w_b)(d w_b / d w) (al[16]), -n . d f_v / d q at w_b (aq[24], rows
+// 1..3), and for the gradient equations we w_b and we d w_b / d w (fb[20]).
+// Not inlined: only far-field points call it, so its registers stay out of
+// the element kernel's allocation.
+template <class T>
+__device__ __noinline__ void ns_farfield_point(const T* w, const T (*qv)[4], T nx, T ny, T we, const double* winf_d,
+                                               const EulerConst<T>& C, const NsConst<T>& V, T* fhat, T* al, T* aq,
+                                               T* fb) {
+  using A = Ar<T>;
+  const T zero = A::zero();
+  T winf[4], wb[4], dwb[4][4], fx[4], fy[4], Ax[16], Ay[16], fv[2][4], dw[2][4][4], dq[2][4][8], q2[2][4];
+#pragma unroll
+  for (int f = 0; f < 4; ++f) {
+    winf[f] = A::from_d(winf_d[f]);
+    q2[0][f] = qv[0][f];
+    q2[1][f] = qv[1][f];
+  }
+  boundary_state_jac(2, w, nx, ny, winf, C, wb, dwb);
+  euler_flux_jac(wb, C, fx, fy, Ax, Ay);
+  visc_all(wb, q2, V, fv, dw, dq);
+#pragma unroll
+  for (int f = 0; f < 4; ++f)
+    fhat[f] = A::mul(we, A::add(A::mul(nx, A::sub(fx[f], fv[0][f])), A::mul(ny, A::sub(fy[f], fv[1][f]))));
+#pragma unroll
+  for (int f = 0; f < 4; ++f) {
+    T an[4];
+#pragma unroll
+    for (int g = 0; g < 4; ++g)
+      an[g] = A::add(A::mul(nx, A::sub(Ax[f * 4 + g], dw[0][f][g])), A::mul(ny, A::sub(Ay[f * 4 + g], dw[1][f][g])));
+#pragma unroll
+    for (int g = 0; g < 4; ++g) {
+      T v = zero;
+#pragma unroll
+      for (int h = 0; h < 4; ++h) A::madd(v, an[h], dwb[h][g]);
+      al[f * 4 + g] = A::mul(we, A::norm(v));
+    }
+  }
+#pragma unroll
+  for (int f = 1; f < 4; ++f)
+#pragma unroll
+    for (int kg = 0; kg < 8; ++kg)
+      aq[(f - 1) * 8 + kg] = A::neg(A::mul(we, A::add(A::mul(nx, dq[0][f][kg]), A::mul(ny, dq[1][f][kg]))));
+#pragma unroll
+  for (int f = 0; f < 4; ++f) {
+    fb[f] = A::mul(we, wb[f]);
+#pragma unroll
+    for (int g = 0; g < 4; ++g) fb[4 + f * 4 + g] = A::mul(we, dwb[f][g]);
+  }
+}
+
 template <int P>
 constexpr int ns_threads() { return P == 1 ? 128 : 256; }
 constexpr int kNsPt = 6;   // edge point slots per face
@@ -55,7 +116,7 @@ template <int P>
 struct NsLayout {
   static constexpr int NP = n_basis(P), NQ = (P + 2) * (P + 2), NW4 = 4 * NP, N = 12 * NP, LDA = NW4 + 1;
   int ldr, lds, ldc;
-  int oA, oR, oCp, oS, oU, oNu, oL, oNl, oE, oDk, oPv, oPf, oW, oZ, oBc, oCc, total;
+  int oA, oR, oCp, oS, oU, oNu, oL, oNl, oE, oDk, oPv, oPf, oW, oZ, oBc, oCc, oFb, oYf, nyf, total;
   HDG_HD NsLayout(int ntmax) {
     ldr = (ntmax + 1) | 1;
     lds = (ntmax + 1) | 1;
@@ -76,7 +137,10 @@ struct NsLayout {
     oZ = oW + 3 * kNsPt * 16 * 5;
     oBc = oZ + 4 * NP * NQ;
     oCc = oBc + NW4 * NP;
-    total = oCc + ntmax * NP;
+    oFb = oCc + ntmax * NP;
+    oYf = oFb + 3 * kNsPt * 20;   // far-field point data: weighted w_b (4) and weighted d w_b / d w (16)
+    nyf = (NW4 > ntmax + 1 ? NW4 : ntmax + 1) * 3 * kNsPt;  // values at the far-field points of rows or columns
+    total = oYf + nyf;
   }
 };
 
@@ -125,9 +189,12 @@ __global__ void __launch_bounds__(ns_threads<P>(), (P == 1 ? 4 : (P == 2 ? 2 : 1
   T* sZ = smem + lay.oZ;     // [4][NP][NQ]
   T* sBc = smem + lay.oBc;   // A_wq block column [4 n_p][n_p]
   T* sCc = smem + lay.oCc;   // C_q block column [nt][n_p]
+  T* sFb = smem + lay.oFb;   // [18][20] far-field points: we w_b (4), we d w_b / d w (16)
+  T* sYf = smem + lay.oYf;   // [rows or columns][far-field points] products with phi at those points
 
   __shared__ T g_det, g_ic, g_Ji[2][2], g_n[3][2], g_len[3], g_mt;
-  __shared__ int g_e[3], g_pe[3], g_nk[3], g_toff[4], g_fl[3], g_side[3], g_old[3], g_wall;
+  __shared__ int g_e[3], g_pe[3], g_nk[3], g_toff[4], g_fl[3], g_side[3], g_old[3], g_bc[3], g_wall, g_bnd, g_nff;
+  __shared__ unsigned char g_ffa[3 * kNsPt], g_ffq[3 * kNsPt];  // far-field point x: face, point
   __shared__ unsigned char g_cf[kMaxNt], g_cg[kMaxNt], g_cl[kMaxNt];
   __shared__ T s_pinv[64];
   __shared__ int s_bad;
@@ -184,6 +251,7 @@ __global__ void __launch_bounds__(ns_threads<P>(), (P == 1 ? 4 : (P == 2 ? 2 : 1
       g_nk[a] = e >= 0 ? g_pe[a] + 1 : 0;   // and no trace unknowns
       g_fl[a] = (info >> a) & 1;
       g_side[a] = (info >> (3 + a)) & 1;
+      g_bc[a] = e >= 0 ? 0 : (m.elem_bc ? (m.elem_bc[K] >> (2 * a)) & 3 : 3);  // boundary: 2 far field, 3 wall
       if (tid == 0) {
         const double J00 = c[2] - c[0], J01 = c[4] - c[0], J10 = c[3] - c[1], J11 = c[5] - c[1];
         const double det = J00 * J11 - J01 * J10;
@@ -222,7 +290,17 @@ __global__ void __launch_bounds__(ns_threads<P>(), (P == 1 ? 4 : (P == 2 ? 2 : 1
       g_toff[1] = 4 * g_nk[0];
       g_toff[2] = 4 * (g_nk[0] + g_nk[1]);
       g_toff[3] = 4 * (g_nk[0] + g_nk[1] + g_nk[2]);
-      g_wall = (g_e[0] < 0) || (g_e[1] < 0) || (g_e[2] < 0);
+      g_wall = (g_bc[0] == 3) || (g_bc[1] == 3) || (g_bc[2] == 3);
+      g_bnd = (g_e[0] < 0) || (g_e[1] < 0) || (g_e[2] < 0);
+      int nff = 0;
+      for (int a = 0; a < 3; ++a)
+        if (g_bc[a] == 2)
+          for (int q = 0; q < P + 2; ++q) {
+            g_ffa[nff] = (unsigned char)a;
+            g_ffq[nff] = (unsigned char)q;
+            ++nff;
+          }
+      g_nff = nff;
     }
     {
       const double* uk = U + m.u_off[K];
@@ -309,6 +387,11 @@ __global__ void __launch_bounds__(ns_threads<P>(), (P == 1 ? 4 : (P == 2 ? 2 : 1
           if (f < 4) qv[0][f] = acc; else if (f < 8) qv[1][f - 4] = acc; else w[f - 8] = acc;
         }
         const T nx = g_n[a][0], ny = g_n[a][1];
+        if (g_e[a] < 0 && g_bc[a] == 2) {
+          // characteristic far field (Sec. 2.1): its own frame (see ns_farfield_point)
+          ns_farfield_point(w, qv, nx, ny, we, ph.winf, C, V, sFhat + t * 4, sAl + t * 16, sAq + t * 24, sFb + t * 20);
+          continue;
+        }
         if (g_e[a] < 0) {
           // no-slip adiabatic wall: w_b = (rho, 0, 0, E), f_v(w_b, q) with its energy row zero
           const T wb[4] = {w[0], zero, zero, w[3]};
@@ -412,6 +495,13 @@ __global__ void __launch_bounds__(ns_threads<P>(), (P == 1 ? 4 : (P == 2 ? 2 : 1
       for (int j = 0; j < NP; ++j) A::madd(acc, sDk[k * NP * NP + i * NP + j], sU[(8 + f) * NP + j]);
       for (int a = 0; a < 3; ++a) {
         const T sc = A::mul(g_n[a][k], g_len[a]);
+        if (g_bc[a] == 2) {  // far field: -n_k <phi_i, w_b,f(w)>_e at the edge points
+          const T* phe = tab + to.edge_phi[P][P][a][g_fl[a]];
+          T s2 = zero;
+          for (int q = 0; q < P + 2; ++q) A::madd(s2, phe[q * NP + i], sFb[(a * kNsPt + q) * 20 + f]);
+          A::msub(acc, g_n[a][k], A::norm(s2));
+          continue;
+        }
         if (g_e[a] < 0) {  // wall: -n_k <phi_i, w_b,f>_e, w_b = (rho, 0, 0, E)
           if (f == 0 || f == 3) {
             const T* fm = tab + to.face_mass[P][P][a];
@@ -546,11 +636,14 @@ __global__ void __launch_bounds__(ns_threads<P>(), (P == 1 ? 4 : (P == 2 ? 2 : 1
         T* p = &sA[(f * NP + i) * LDA + f * NP + j];
         *p = A::add(*p, v);
       }
-      if (g_wall) {
-        // wall flux Jacobian <phi_i, (d f_hat_b / d w)_fg phi_j>_e in the columns g = rho, E
-        T wv[4][2], b0 = zero, b1 = zero;
+      if (g_bnd) {
+        // boundary flux Jacobian <phi_i, (d f_hat_b / d w)_fg phi_j>_e: walls fill the columns
+        // g = rho, E (the others are zero in sAl), the far field all four
+        T wv[4][4], b0 = zero, b1 = zero;
 #pragma unroll
-        for (int f = 0; f < 4; ++f) wv[f][0] = wv[f][1] = zero;
+        for (int f = 0; f < 4; ++f)
+#pragma unroll
+          for (int g = 0; g < 4; ++g) wv[f][g] = zero;
         for (int a = 0; a < 3; ++a) {
           if (g_e[a] >= 0) continue;
           const T* phe = tab + to.edge_phi[P][P][a][g_fl[a]];
@@ -558,24 +651,27 @@ __global__ void __launch_bounds__(ns_threads<P>(), (P == 1 ? 4 : (P == 2 ? 2 : 1
             const T pp = A::mul(phe[q * NP + i], phe[q * NP + j]);
             const T* al = sAl + (a * kNsPt + q) * 16;
 #pragma unroll
-            for (int f = 0; f < 4; ++f) {
-              A::madd(wv[f][0], pp, al[f * 4]);
-              A::madd(wv[f][1], pp, al[f * 4 + 3]);
-            }
+            for (int f = 0; f < 4; ++f)
+#pragma unroll
+              for (int g = 0; g < 4; ++g) A::madd(wv[f][g], pp, al[f * 4 + g]);
           }
-          const T fmv = A::mul(g_len[a], tab[to.face_mass[P][P][a] + t]);
-          A::madd(b0, g_n[a][0], fmv);
-          A::madd(b1, g_n[a][1], fmv);
+          if (g_bc[a] == 3) {  // D_k^wall: the wall term of the gradient equations
+            const T fmv = A::mul(g_len[a], tab[to.face_mass[P][P][a] + t]);
+            A::madd(b0, g_n[a][0], fmv);
+            A::madd(b1, g_n[a][1], fmv);
+          }
         }
 #pragma unroll
-        for (int f = 0; f < 4; ++f) {
-          T* p0 = &sA[(f * NP + i) * LDA + j];
-          T* p3 = &sA[(f * NP + i) * LDA + 3 * NP + j];
-          *p0 = A::norm(A::add(*p0, A::norm(wv[f][0])));
-          *p3 = A::norm(A::add(*p3, A::norm(wv[f][1])));
+        for (int f = 0; f < 4; ++f)
+#pragma unroll
+          for (int g = 0; g < 4; ++g) {
+            T* pg = &sA[(f * NP + i) * LDA + g * NP + j];
+            *pg = A::norm(A::add(*pg, A::norm(wv[f][g])));
+          }
+        if (g_wall) {
+          sDw[t] = A::norm(A::sub(sDk[t], A::norm(b0)));
+          sDw[NP * NP + t] = A::norm(A::sub(sDk[NP * NP + t], A::norm(b1)));
         }
-        sDw[t] = A::norm(A::sub(sDk[t], A::norm(b0)));
-        sDw[NP * NP + t] = A::norm(A::sub(sDk[NP * NP + t], A::norm(b1)));
       }
     }
     for (int t = tid; t < NW4; t += NT)  // F_w, or the adjoint right-hand side F~_w
@@ -741,6 +837,88 @@ __global__ void __launch_bounds__(ns_threads<P>(), (P == 1 ? 4 : (P == 2 ? 2 : 1
           }
         }
         __syncthreads();
+        if (g_nff) {
+          // far field: A_qw of block (k', g) also holds -n_k' sum_x phi_i(x) (we J)_{g,g2}(x) phi_j(x)
+          // for every field g2 (the characteristic state couples the fields).  Its products go
+          // through the far-field points x: Y[r][x] = sum_i' M[r][i'] phi_i'(x) for the block
+          // column M = A_wq (then C_q), and the update sum_x Y[r][x] coef(x, g2) phi_j(x).
+          const int nff = g_nff;
+          for (int t = tid; t < NW4 * nff; t += NT) {  // Y from the A_wq block column
+            const int r = t / nff, x = t - r * nff, a = g_ffa[x];
+            const T* phx = tab + to.edge_phi[P][P][a][g_fl[a]] + g_ffq[x] * NP;
+            T acc = zero;
+            for (int i2 = 0; i2 < NP; ++i2) A::madd(acc, sBc[r * NP + i2], phx[i2]);
+            sYf[t] = A::norm(acc);
+          }
+          __syncthreads();
+          // (i') A'[r][(g2, j)] -= 1/det sum_x Y[r][x] (-n_k' (we J)_{g,g2}(x)) phi_j(x)
+          for (int t = tid; t < NW4 * NW4; t += NT) {
+            const int r = t / NW4, c = t - r * NW4, g2 = c / NP, jj = c - g2 * NP;
+            T acc = zero;
+            for (int x = 0; x < nff; ++x) {
+              const int a = g_ffa[x], pt = a * kNsPt + g_ffq[x];
+              const T phj = tab[to.edge_phi[P][P][a][g_fl[a]] + g_ffq[x] * NP + jj];
+              const T coef = A::mul(A::neg(g_n[a][kd]), sFb[pt * 20 + 4 + gq * 4 + g2]);
+              A::madd(acc, A::mul(coef, phj), sYf[r * nff + x]);
+            }
+            T* p = &sA[r * LDA + c];
+            A::msub(*p, ic, A::norm(acc));
+            *p = A::norm(*p);
+          }
+          __syncthreads();
+          if (adjoint) {
+            // G'_w[(g2, j)][c] -= 1/det sum_x (-n_k' (we J)_{g,g2}(x)) phi_j(x) sum_i' phi_i'(x) G_q[i'][c]
+            const double* ftq = s.ftilde + m.u_off[K] + kk * NP;
+            for (int t = tid; t < nff * nr1; t += NT) {
+              const int x = t / nr1, c = t - x * nr1, a = g_ffa[x];
+              const T* phx = tab + to.edge_phi[P][P][a][g_fl[a]] + g_ffq[x] * NP;
+              T acc = zero;
+              for (int i2 = 0; i2 < NP; ++i2)
+                A::madd(acc, phx[i2], (c < nt) ? sCc[c * NP + i2] : A::from_d(ftq[i2]));
+              sYf[t] = A::norm(acc);
+            }
+            __syncthreads();
+            for (int t = tid; t < NW4 * nr1; t += NT) {
+              const int rr = t / nr1, c = t - rr * nr1, g2 = rr / NP, jj = rr - g2 * NP;
+              T acc = zero;
+              for (int x = 0; x < nff; ++x) {
+                const int a = g_ffa[x], pt = a * kNsPt + g_ffq[x];
+                const T phj = tab[to.edge_phi[P][P][a][g_fl[a]] + g_ffq[x] * NP + jj];
+                const T coef = A::mul(A::neg(g_n[a][kd]), sFb[pt * 20 + 4 + gq * 4 + g2]);
+                A::madd(acc, A::mul(coef, phj), sYf[x * nr1 + c]);
+              }
+              T* p = &sR[rr * ldr + c];
+              A::msub(*p, ic, A::norm(acc));
+              *p = A::norm(*p);
+            }
+          } else {
+            // (iv') C'[r][(g2, j)] -= 1/det sum_x Yc[r][x] (-n_k' (we J)_{g,g2}(x)) phi_j(x)
+            for (int t = tid; t < nt * nff; t += NT) {
+              const int r = t / nff, x = t - r * nff, a = g_ffa[x];
+              const T* phx = tab + to.edge_phi[P][P][a][g_fl[a]] + g_ffq[x] * NP;
+              T acc = zero;
+              if (g_cg[r] != 0)
+                for (int i2 = 0; i2 < NP; ++i2) A::madd(acc, sCc[r * NP + i2], phx[i2]);
+              sYf[t] = A::norm(acc);
+            }
+            __syncthreads();
+            for (int t = tid; t < nt * NW4; t += NT) {
+              const int r = t / NW4, c = t - r * NW4, g2 = c / NP, jj = c - g2 * NP;
+              if (g_cg[r] == 0) continue;  // C_q row of field 0 is zero
+              T acc = zero;
+              for (int x = 0; x < nff; ++x) {
+                const int a = g_ffa[x], pt = a * kNsPt + g_ffq[x];
+                const T phj = tab[to.edge_phi[P][P][a][g_fl[a]] + g_ffq[x] * NP + jj];
+                const T coef = A::mul(A::neg(g_n[a][kd]), sFb[pt * 20 + 4 + gq * 4 + g2]);
+                A::madd(acc, A::mul(coef, phj), sYf[r * nff + x]);
+              }
+              T* p = &sCp[r * ldc + c];
+              A::msub(*p, ic, A::norm(acc));
+              *p = A::norm(*p);
+            }
+          }
+          __syncthreads();
+        }
       }
       if (pass == 1) break;
       if (adjoint) {  // the adjoint solves with the transposed Schur matrix A'^T (Sec. 4.2)
@@ -779,11 +957,33 @@ __global__ void __launch_bounds__(ns_threads<P>(), (P == 1 ? 4 : (P == 2 ? 2 : 1
       __syncthreads();
       continue;
     }
-    // X_q = (R_q - A_qw X_w) / det
-    {
+    // X_q = (R_q - A_qw X_w) / det; with far-field faces A_qw also holds
+    // -n_k sum_x phi_i(x) (we J)_fg(x) phi_j(x), applied through the points in column chunks:
+    // Tf[x][f][c] = sum_g (we J)_fg(x) X_w,g(x, c)
+    const int nff = g_nff;
+    const int cch = nff ? max(1, lay.nyf / (4 * nff)) : nr1;
+    for (int c0 = 0; c0 < nr1; c0 += cch) {
+      const int nc = min(cch, nr1 - c0);
+      if (nff) {
+        for (int t = tid; t < nff * 4 * nc; t += NT) {
+          const int x = t / (4 * nc), rem = t - x * 4 * nc, f = rem / nc, cc = rem - f * nc;
+          const int a = g_ffa[x], pt = a * kNsPt + g_ffq[x];
+          const T* phx = tab + to.edge_phi[P][P][a][g_fl[a]] + g_ffq[x] * NP;
+          T acc = zero;
+#pragma unroll
+          for (int g = 0; g < 4; ++g) {
+            T xw = zero;
+            for (int j = 0; j < NP; ++j) A::madd(xw, phx[j], sR[(g * NP + j) * ldr + c0 + cc]);
+            A::madd(acc, sFb[pt * 20 + 4 + f * 4 + g], A::norm(xw));
+          }
+          sYf[t] = A::norm(acc);
+        }
+        __syncthreads();
+      }
       double* xk = s.X + m.x_off[K];
-      for (int t = tid; t < 8 * NP * nr1; t += NT) {
-        const int c = t / (8 * NP), r = t - c * (8 * NP), kf = r / NP, i = r - kf * NP, k = kf >> 2, f = kf & 3;
+      for (int t = tid; t < 8 * NP * nc; t += NT) {
+        const int c = c0 + t / (8 * NP), r = t - (t / (8 * NP)) * (8 * NP), kf = r / NP, i = r - kf * NP, k = kf >> 2,
+                  f = kf & 3;
         T acc = zero;
         if (c == nt) {
           acc = A::neg(sNu[r]);                           // F_q
@@ -794,10 +994,16 @@ __global__ void __launch_bounds__(ns_threads<P>(), (P == 1 ? 4 : (P == 2 ? 2 : 1
         }
         const T* Dq = ((g_wall && (f == 0 || f == 3)) ? sDw : sDk) + k * NP * NP;
         for (int j = 0; j < NP; ++j) A::msub(acc, Dq[i * NP + j], sR[(f * NP + j) * ldr + c]);
+        for (int x = 0; x < nff; ++x) {  // - (far-field part of A_qw) X_w
+          const int a = g_ffa[x];
+          const T phi_i = tab[to.edge_phi[P][P][a][g_fl[a]] + g_ffq[x] * NP + i];
+          A::madd(acc, A::mul(g_n[a][k], phi_i), sYf[(x * 4 + f) * nc + (c - c0)]);
+        }
         const T v = A::mul(A::norm(acc), ic);
         xk[(size_t)c * N + r] = A::to_d(v);
         bad |= A::bad(v);
       }
+      __syncthreads();
     }
     // ---------------- a6/a7: S = S0 - C' X_w,B, E = E0 - C' X_w,F, assembly ----------------
     for (int r = ty; r < nt; r += NW) {

@@ -345,7 +345,8 @@ class Workload:
     seed: int = 1234
     extra: dict = field(default_factory=dict)
     # "channel": slip wall at y = 0, far field at y = 1; "box": far field all round;
-    # "wall_channel": no-slip adiabatic walls at y = 0 and y = 1 (Navier-Stokes)
+    # "wall_channel": no-slip adiabatic walls at y = 0 and y = 1 (Navier-Stokes);
+    # "wall_far_channel": a no-slip adiabatic wall at y = 0, far field at y = 1 (Navier-Stokes)
     domain: str = "periodic"
 
     @property
@@ -379,8 +380,7 @@ WORKLOADS = {
     # triangles, p in {1,2,3,4} at 40/30/20/10 %, Mach 0.5, Re 5000, Fourier modes on the free stream
     "ns_wall_channel_8k": Workload("ns_wall_channel_8k", 64, 64, 0.2, 1, None, (0.4, 0.3, 0.2, 0.1), "fourier",
                                    0.5, 0.0, seed=77, domain="wall_channel"),
-    # Navier-Stokes with far field on all four sides (Mach 0.5 at 10 degrees + density bump); the
-    # oracle covers it, the library does not yet
+    # Navier-Stokes with far field on all four sides (Mach 0.5 at 10 degrees + density bump)
     "ns_box_8k": Workload("ns_box_8k", 64, 64, 0.2, 1, 2, None, "bump", 0.5, 10.0, seed=88, domain="box"),
 }
 
@@ -409,6 +409,8 @@ def make_case(wl: Workload) -> Case:
         mesh = channel_mesh(wl.nx, wl.ny, wl.jitter, wl.seed)
     elif wl.domain == "wall_channel":
         mesh = channel_mesh(wl.nx, wl.ny, wl.jitter, wl.seed, bottom=BC_NO_SLIP_WALL, top=BC_NO_SLIP_WALL)
+    elif wl.domain == "wall_far_channel":   # a boundary layer: no-slip wall below, far field above
+        mesh = channel_mesh(wl.nx, wl.ny, wl.jitter, wl.seed, bottom=BC_NO_SLIP_WALL, top=BC_FAR_FIELD)
     elif wl.domain == "box":
         mesh = box_mesh(wl.nx, wl.ny, wl.jitter, wl.seed)
     else:

@@ -193,8 +193,8 @@ def test_channel_adjoint_matches_transposed_monolithic(ctx):
 
 
 def test_boundary_kinds_checked_against_the_model(ctx):
-    """Navier-Stokes meshes take no-slip walls only (slip wall / far field: HDG_ENOTSUP); the no-slip
-    wall is not an Euler boundary (HDG_EINVAL)."""
+    """Navier-Stokes meshes take no-slip walls and far field, not the slip wall (HDG_ENOTSUP: the
+    channel's bottom); the no-slip wall is not an Euler boundary (HDG_EINVAL)."""
     from paper_1308_3995_gb300 import hdg
     wl = G.small_variant(G.WORKLOADS["euler_channel_8k"], 4, 3, model=1)
     case = G.make_case(wl)
@@ -267,3 +267,104 @@ def test_ns_wall_channel_newton_step_matches_oracle_monolithic(ctx):
     print(wl.name, "iterations", it, f"dU {eU:.1e} dLambda {eL:.1e}")
     assert eU < 1e-9 and eL < 1e-9
     solver.close(); sysm.close(); mesh.close()
+
+
+# ----------------------------------------------------------------------------- Navier-Stokes far field
+def _ns_far(kind, nx, ny, **kw):
+    """The Navier-Stokes box (far field on all four sides, corner elements with two far-field faces)
+    or the boundary layer (no-slip wall below, far field above; flow at 10 degrees so that the far
+    field's normal velocity stays clear of the characteristic switch at v_n = 0)."""
+    if kind == "box":
+        return G.small_variant(G.WORKLOADS["ns_box_8k"], nx, ny, **kw)
+    return G.small_variant(G.WORKLOADS["ns_wall_channel_8k"], nx, ny, domain="wall_far_channel", aoa=10.0, **kw)
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+@pytest.mark.parametrize("kind,p,cfl,sc", [("box", 1, 0.0, 0.0), ("box", 2, 10.0, 0.0), ("box", 3, 0.0, 0.0),
+                                           ("box", 4, 0.0, 0.0), ("box", None, 10.0, 0.0), ("box", 2, 0.0, 0.2),
+                                           ("layer", 2, 0.0, 0.0), ("layer", None, 10.0, 0.0)])
+def test_ns_far_field_parity(ctx, precision, kind, p, cfl, sc):
+    """Navier-Stokes characteristic far field (Sec. 2.1, 3.2), every element and face against the
+    oracle: the far-field flux with the viscous flux at the far-field state, its Jacobian in all four
+    columns, and the gradient equations' far-field term that couples the fields inside the in-element
+    q elimination (A', C', X_q)."""
+    kw = {"p": p, "probs": None} if p else {"p": None, "probs": (0.4, 0.3, 0.2, 0.1)}
+    wl = _ns_far(kind, 5, 4, **kw)
+    case, om, U, Lam, dLam, mesh, sysm = _setup(ctx, wl, cfl, precision, sc)
+    assert (case.mesh.elem_bc == 2).any()
+    g = _run(sysm, mesh, U, Lam, dLam)
+    assert np.all(g["status"] == 0)
+    chk = ParityChecker(om, oracle_params(wl, cfl, sc), U, Lam, dLam, g)
+    errs = chk.run(range(om.n_elem), range(om.n_face))
+    print(wl.name, p, cfl, sc, ["fp64", "float2"][precision], {k: f"{v:.1e}" for k, v in errs.items()})
+    for k, v in errs.items():
+        assert v < [TOL, TOL_MIXED][precision], (k, v)
+    sysm.close(); mesh.close()
+
+
+def test_ns_far_field_free_stream_residual_vanishes(ctx):
+    """The uniform free stream with zero gradient is a steady state of the far-field box on the GPU."""
+    wl = _ns_far("box", 6, 5, p=3)
+    case, om, U, Lam, dLam, mesh, sysm = _setup(ctx, wl)
+    w0 = G.conserved(*G.free_stream(wl.mach, wl.aoa))
+    nb = 10
+    U = np.zeros(mesh.u_len); L = np.zeros(mesh.lam_len)
+    for f in range(4):
+        U.reshape(-1, 12 * nb)[:, 8 * nb + f * nb] = w0[f] / np.sqrt(2)
+        L.reshape(-1, 16)[:, f * 4] = w0[f]
+    g = _run(sysm, mesh, U, L, dLam)
+    assert np.abs(g["res_u"]).max() < 1e-13 and np.abs(g["res_lam"]).max() < 1e-13
+    sysm.close(); mesh.close()
+
+
+@pytest.mark.parametrize("kind", ["box", "layer"])
+def test_ns_far_field_newton_step_matches_oracle_monolithic(ctx, kind):
+    """One pseudo-transient Newton step (CFL 10) with far-field faces: GPU condensation, GMRES + block
+    ILU(0) trace solve, reconstruction -- against the oracle's monolithic step."""
+    from paper_1308_3995_gb300 import hdg
+    wl = _ns_far(kind, 3, 3)
+    case, om, U, Lam, dLam, mesh, sysm = _setup(ctx, wl, 10.0)
+    dev = torch.device("cuda:0")
+    Ut, Lt = torch.from_numpy(U).to(dev), torch.from_numpy(Lam).to(dev)
+    sysm.condense(Ut, Lt)
+    solver = hdg.Solver(sysm, restart=40, precond=2)
+    x = torch.zeros(mesh.lam_len, dtype=torch.float64, device=dev)
+    it, rel = solver.solve(x, rtol=1e-13, max_iter=2000)
+    dUt = torch.empty(mesh.u_len, dtype=torch.float64, device=dev)
+    sysm.recover(x, dUt)
+    torch.cuda.synchronize()
+    dU, dL = om.monolithic(oracle_params(wl, 10.0), U, Lam)
+    eU, eL = rel_err(dUt.cpu().numpy(), dU), rel_err(x.cpu().numpy(), dL)
+    print(wl.name, "iterations", it, f"dU {eU:.1e} dLambda {eL:.1e}")
+    assert eU < 1e-9 and eL < 1e-9
+    solver.close(); sysm.close(); mesh.close()
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+def test_ns_far_field_adjoint_matches_transposed_monolithic(ctx, precision):
+    """The hybridized adjoint (Sec. 4.2) with far-field faces: the transposed q elimination with the
+    field-coupling far-field term, K^T solve and reconstruction, against the dense solve of the
+    transposed monolithic Jacobian of the oracle."""
+    from paper_1308_3995_gb300 import hdg
+    wl = _ns_far("box", 3, 3, p=2)
+    cfl = 10.0
+    case, om, U, Lam, dLam, mesh, primal = _setup(ctx, wl, cfl, precision)
+    adj = hdg.System(ctx, mesh, lib_params(wl, cfl, precision))
+    dev = torch.device("cuda:0")
+    Ut, Lt = torch.from_numpy(U).to(dev), torch.from_numpy(Lam).to(dev)
+    Ft = np.random.default_rng(13).standard_normal(mesh.u_len)
+    primal.condense(Ut, Lt)
+    adj.adjoint_condense(primal, Ut, Lt, torch.from_numpy(Ft).to(dev))
+    solver = hdg.Solver(primal, restart=40, precond=2)
+    lt = torch.zeros(mesh.lam_len, dtype=torch.float64, device=dev)
+    ut = torch.zeros(mesh.u_len, dtype=torch.float64, device=dev)
+    solver.solve(lt, rtol=1e-14, max_iter=2000, rhs=adj.views()["E"], transpose=True)
+    adj.recover(lt, ut)
+    torch.cuda.synchronize()
+    _, _, J = om.monolithic(oracle_params(wl, cfl), U, Lam, want_matrix=True)
+    z = np.linalg.solve(J.T, np.concatenate([Ft, np.zeros(om.lam_len)]))
+    eu, el = rel_err(ut.cpu().numpy(), z[:om.u_len]), rel_err(lt.cpu().numpy(), z[om.u_len:])
+    print(wl.name, ["fp64", "float2"][precision], f"adjoint U~ {eu:.1e} Lambda~ {el:.1e}")
+    tol = [1e-10, 1e-9][precision]
+    assert eu < tol and el < tol
+    solver.close(); adj.close(); primal.close(); mesh.close()
