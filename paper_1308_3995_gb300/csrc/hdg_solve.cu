@@ -450,21 +450,35 @@ __device__ __forceinline__ ff shfl_down_ff(ff v, int o) {
 __device__ __forceinline__ float2 from_ff(ff v) { return make_float2(v.hi, v.lo); }
 
 // acc += the lane's share of one block's product: NT = MB / NSEG columns per
-// lane (compile-time: every load is a constant offset from one base, all
-// issued before the first multiply-add), two accumulation chains
+// lane (compile-time: every load is a constant offset from one base, issued
+// in batches of up to eight before their multiply-adds), two accumulation
+// chains.  x of the block's column face is loaded once, one value per lane
+// (coalesced), and handed to the lanes that need it by shuffles, so the
+// batch's registers hold only the matrix values.
+// Every lane of the warp takes part (the shuffles); a lane past the segments
+// (sg >= NSEG) loads no matrix value and its sums are never read.
 template <int M, int MB, bool INPLACE, class MT>
-__device__ __forceinline__ void lane_block_product(const MT* __restrict__ blk, const float2* xc, ff& t, ff& t2) {
-  constexpr int NSEG = (M <= 8 ? 4 : (M <= 16 ? 2 : 1)), NT = MB / NSEG, MN = M * NSEG;
-  MT a[NT];
-  float2 xv[NT];
+__device__ __forceinline__ void lane_block_product(const MT* __restrict__ blk, const float2* xcol, int lane, int sg,
+                                                   ff& t, ff& t2) {
+  constexpr int NSEG = (M <= 8 ? 4 : (M <= 16 ? 2 : 1)), NT = MB / NSEG, MN = M * NSEG, NB = 8;
+  const bool act = sg < NSEG;
+  // in place (a Gauss-Seidel sweep) x is written by this launch: no read-only cache path
+  const float2 xl = lane < MB ? (INPLACE ? xcol[lane] : __ldg(xcol + lane)) : make_float2(0.0f, 0.0f);
 #pragma unroll
-  for (int u = 0; u < NT; ++u) {
-    a[u] = __ldcs(blk + u * MN);
-    // in place (a Gauss-Seidel sweep) x is written by this launch: no read-only cache path
-    xv[u] = INPLACE ? xc[u * NSEG] : __ldg(xc + u * NSEG);
+  for (int k0 = 0; k0 < NT; k0 += NB) {
+    MT a[NB];
+#pragma unroll
+    for (int u = 0; u < NB; ++u)
+      if (k0 + u < NT) a[u] = act ? __ldcs(blk + (k0 + u) * MN) : MT{};
+#pragma unroll
+    for (int u = 0; u < NB; ++u) {
+      if (k0 + u < NT) {
+        const int c = sg + (k0 + u) * NSEG;
+        const ff xv{__shfl_sync(0xffffffffu, xl.x, c), __shfl_sync(0xffffffffu, xl.y, c)};
+        AF::madd(((k0 + u) & 1) ? t2 : t, to_ff(a[u]), xv);
+      }
+    }
   }
-#pragma unroll
-  for (int u = 0; u < NT; ++u) AF::madd((u & 1) ? t2 : t, to_ff(a[u]), to_ff(xv[u]));
 }
 
 template <int M, bool TR, bool INPLACE, class MT>
@@ -499,14 +513,13 @@ __device__ __forceinline__ void face_op_ff_body(const FaceDevT<MT>& f, const flo
       if (col < 0) continue;
       const int mb = __shfl_sync(0xffffffffu, mmb, b);
       const MT* blk = f.K + __shfl_sync(0xffffffffu, moff, b) + lane;
-      const float2* xc = x + __shfl_sync(0xffffffffu, mxo, b) + sg;
-      if (act) {
-        switch (mb) {
-          case 8: lane_block_product<M, 8, INPLACE>(blk, xc, t, t2); break;
-          case 12: lane_block_product<M, 12, INPLACE>(blk, xc, t, t2); break;
-          case 16: lane_block_product<M, 16, INPLACE>(blk, xc, t, t2); break;
-          default: lane_block_product<M, 20, INPLACE>(blk, xc, t, t2); break;
-        }
+      const float2* xcol = x + __shfl_sync(0xffffffffu, mxo, b);
+      // the whole warp takes part (the shuffles); lanes past the segments compute and drop
+      switch (mb) {
+        case 8: lane_block_product<M, 8, INPLACE>(blk, xcol, lane, sg, t, t2); break;
+        case 12: lane_block_product<M, 12, INPLACE>(blk, xcol, lane, sg, t, t2); break;
+        case 16: lane_block_product<M, 16, INPLACE>(blk, xcol, lane, sg, t, t2); break;
+        default: lane_block_product<M, 20, INPLACE>(blk, xcol, lane, sg, t, t2); break;
       }
     }
   }
