@@ -684,7 +684,7 @@ def serving_section(ctx, n_requests, seed, max_elems, rates=(0.7,), arena_gb=24,
     reqs = SV.prepare(ctx, [SV.Request(i, 0.0, w) for i, w in enumerate(wls)])
     arena = int(arena_gb) << 30
     mixed = SV.Server(ctx, arena, slots=8, precision=hdg.HDG_FLOAT2, solve=solve)
-    plain = SV.Server(ctx, arena, slots=1, precision=hdg.HDG_FP64, solve=solve)
+    plain = SV.Server(ctx, arena, slots=1, precision=hdg.HDG_FP64, solve=solve, solver_arith=0)
     # step requests also through batched launches: the requests admitted since the last launch
     # condensed by one launch per (model, degree) group, batches of at most 32,768 elements, up to
     # eight in flight (the best of a sweep over 2-8 in flight and 32k-200k elements or no cap)

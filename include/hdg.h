@@ -423,11 +423,26 @@ hdg_status hdg_solver_create_ws(hdg_sys* sys, int32_t restart, int32_t precond, 
  * (-1 for invalid arguments). */
 int64_t hdg_solver_workspace_bytes(const hdg_mesh* mesh, int32_t restart, int32_t precond);
 
+/* hdg_solver_create_ws with the GMRES arithmetic `arith` of
+ * hdg_solver_set_arithmetic (0 binary64, 1 float-float) planned into the
+ * caller's workspace: with arith 1 the workspace also holds the double-word
+ * copies (8 bytes per value of K and of the pivot inverses, twice that for
+ * kinds 2 and 3, plus two vectors), the solver starts in arith 1 and creating
+ * it still allocates no device memory.  Sizes from
+ * hdg_solver_workspace_bytes_arith (-1 for invalid arguments); arith 0 is
+ * hdg_solver_create_ws / hdg_solver_workspace_bytes.  HDG_EINVAL for another
+ * arith or a short or misaligned workspace.  (No counterpart in the paper,
+ * which solves in binary64.) */
+hdg_status hdg_solver_create_ws_arith(hdg_sys* sys, int32_t restart, int32_t precond, int32_t arith, void* workspace,
+                                      int64_t bytes, hdg_solver** out);
+int64_t hdg_solver_workspace_bytes_arith(const hdg_mesh* mesh, int32_t restart, int32_t precond, int32_t arith);
+
 /* Solve K dLam = E for the DEVICE vector dLam [lam_len] (its input value is
  * the initial guess; pass zeros for none), on `stream`.  Stops when the
  * preconditioned residual ||M^-1 (E - K dLam)||_2 <= rtol ||M^-1 E||_2 or after
- * max_iter iterations.  The call synchronises `stream` (it reads one
- * residual estimate per iteration) and returns the iteration count and the
+ * max_iter iterations.  The call synchronises `stream` (it reads the
+ * residual estimate back once per chunk of four iterations; the Arnoldi
+ * bookkeeping runs on the device) and returns the iteration count and the
  * final preconditioned relative residual in *iters / *rel_res (either may be
  * NULL).  Returns HDG_OK when converged, HDG_ETIMEOUT when max_iter was
  * reached first, HDG_ESINGULAR when a pivot block of the preconditioner (a
@@ -476,8 +491,8 @@ hdg_status hdg_solver_set_preconditioner(hdg_solver* solver, int32_t kind);
  * binary32 pipe.  The first call with arith 1 (and a later change to kind 2
  * or 3) allocates the copies: 8 bytes per value of K and of the pivot
  * inverses (twice that for kinds 2 and 3) plus two vectors; HDG_ENOMEM if
- * that fails or if the solver lives in a caller's workspace
- * (hdg_solver_create_ws plans no room for them).  After a solve in arith 1
+ * that fails or if the solver lives in a caller's workspace planned without
+ * them (hdg_solver_create_ws; hdg_solver_create_ws_arith plans them).  After a solve in arith 1
  * with kind 0 or 1 the binary64 pivot inverses are not current:
  * hdg_solver_precond_apply then needs hdg_solver_setup first.  The
  * Hessenberg least-squares problem and hdg_trace_matvec stay binary64.

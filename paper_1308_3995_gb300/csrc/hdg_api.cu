@@ -294,6 +294,8 @@ hdg_status hdg_mesh_create_bc(hdg_ctx* ctx, int32_t n_elem, int32_t nfield, cons
   d.xy = dxy; d.elem_face = def; d.elem_info = dinfo; d.face_p = dfp;
   d.u_off = duo; d.lam_off = dlo; d.x_off = dxo; d.kblk = dkb; d.dblk_off = ddb;
   d.elem_bc = dbc;
+  d.far = 0;
+  for (int t = 0; elem_bc && t < 3 * n_elem; ++t) d.far |= elem_bc[t] == 2;
   for (int p = 1; p <= kMaxP; ++p) {
     M->bucket_n[p] = (int)bucket[p].size();
     if (M->bucket_n[p] && (st = upload(ctx, M->allocs, bucket[p], &M->d_bucket[p]))) {

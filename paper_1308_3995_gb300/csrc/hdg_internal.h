@@ -140,6 +140,7 @@ struct DevMesh {
   const int64_t* dblk_off;   // [n_face]: offset of a face's diagonal block in the half-1 scratch
   const uint8_t* elem_bc;    // [n_elem] or null: bits 2l..2l+1 boundary kind of local face l
                              // (0 interior, 1 slip wall, 2 far field); elem_face is -1 there
+  int far;                   // 1 if any face is a far-field boundary (kind 2)
 };
 
 // Per-system output and work buffers handed to kernels by value.

@@ -1080,7 +1080,8 @@ inline bool launch_ns_bucket(const DevMesh& m, const DevSys& s, const Phys& ph, 
                              const double* U, const double* Lam, const int* elems, int n, int ntmax, cudaStream_t st,
                              std::string* err, const BatchRef& bt = BatchRef{}) {
   const NsLayout<P> lay(ntmax);
-  const size_t bytes = sizeof(T) * (size_t)lay.total;
+  // the far-field regions close the layout: a mesh without far-field faces leaves them out
+  const size_t bytes = sizeof(T) * (size_t)((BATCH || m.far) ? lay.total : lay.oFb);
   cudaError_t ce = cudaFuncSetAttribute(k_condense_ns<P, T, ADJ, BATCH>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                         (int)bytes);
   if (ce != cudaSuccess) { *err = std::string("NS kernel shared memory: ") + cudaGetErrorString(ce); return false; }

@@ -879,10 +879,12 @@ namespace {
 struct SolverPlan {
   int64_t n = 0, dinv_len = 0, k_vals = 0;
   int dot_blocks = 0;
-  size_t kc, kb, kt, dof, dinv, bad, ticket, V, part, h, coef, zero, tmp, cols, fcol, F, dinv2, tmp2, total;
+  size_t kc, kb, kt, dof, dinv, bad, ticket, V, part, h, coef, zero, tmp, cols, fcol, F, dinv2, tmp2;
+  size_t kff, dinvff, xff, eff, fff, dinv2ff;  // arith 1: the double-word copies (0 when not planned)
+  size_t total;
 };
 
-SolverPlan plan_solver(const hdg_mesh* M, int restart, int precond, int sms) {
+SolverPlan plan_solver(const hdg_mesh* M, int restart, int precond, int sms, int arith = 0) {
   SolverPlan p{};
   size_t o = 0;
   auto take = [&o](size_t bytes) {
@@ -919,6 +921,17 @@ SolverPlan plan_solver(const hdg_mesh* M, int restart, int precond, int sms) {
     p.dinv2 = take(vs * p.dinv_len);
     p.tmp2 = take(sizeof(double) * p.n);
   }
+  p.kff = p.dinvff = p.xff = p.eff = p.fff = p.dinv2ff = 0;
+  if (arith == 1) {  // the double-word copies of the float-float solve
+    p.kff = take(sizeof(float2) * p.k_vals);
+    p.dinvff = take(sizeof(float2) * p.dinv_len);
+    p.xff = take(sizeof(float2) * p.n);
+    p.eff = take(sizeof(float2) * p.n);
+    if (precond == 2 || precond == 3) {
+      p.fff = take(sizeof(float2) * p.k_vals);
+      p.dinv2ff = take(sizeof(float2) * p.dinv_len);
+    }
+  }
   p.total = o;
   return p;
 }
@@ -930,7 +943,7 @@ extern "C" hdg_status hdg_solver_destroy(hdg_solver* S);
 namespace {
 
 // Plan, place (one cudaMalloc, or the caller's workspace) and fill the solver's state.
-hdg_status solver_build(hdg_sys* sys, int32_t restart, int32_t precond, void* ws, int64_t ws_bytes,
+hdg_status solver_build(hdg_sys* sys, int32_t restart, int32_t precond, int32_t arith, void* ws, int64_t ws_bytes,
                         hdg_solver** out) {
   if (!sys || !out) return HDG_EINVAL;
   *out = nullptr;
@@ -941,7 +954,8 @@ hdg_status solver_build(hdg_sys* sys, int32_t restart, int32_t precond, void* ws
   HDG_ON_DEVICE(ctx, ctx->device);
   int sms = 0;
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, ctx->device);
-  const SolverPlan P = plan_solver(M, restart, precond, sms);
+  if (arith < 0 || arith > 1) return fail(ctx, HDG_EINVAL, "hdg_solver_create_ws_arith: arithmetic must be 0 or 1");
+  const SolverPlan P = plan_solver(M, restart, precond, sms, arith);
   if (ws && ((uintptr_t)ws % 256 != 0 || ws_bytes < (int64_t)P.total))
     return fail(ctx, HDG_EINVAL,
                 "hdg_solver_create_ws: workspace smaller than hdg_solver_workspace_bytes or not 256-byte aligned");
@@ -1061,6 +1075,16 @@ hdg_status solver_build(hdg_sys* sys, int32_t restart, int32_t precond, void* ws
     set_fi32(S, (float*)(base + P.dinv2));
   }
   S->precond = precond;
+  if (arith == 1) {  // the planned double-word copies (ensure_ff finds them in place)
+    set_view(S->fff, S->f, (const float2*)(base + P.kff), (float2*)(base + P.dinvff));
+    S->xff = (float2*)(base + P.xff);
+    S->eff = (float2*)(base + P.eff);
+    if (precond == 2 || precond == 3) {
+      set_view(S->fiff, S->f, (const float2*)(base + P.fff), (float2*)(base + P.dinv2ff));
+      set_view(S->fi32ff, S->f, (const float*)(base + P.fff), (float*)(base + P.dinv2ff));
+    }
+    S->arith = 1;
+  }
   *out = S;
   return HDG_OK;
 }
@@ -1242,13 +1266,13 @@ hdg_status gmres(hdg_solver* S, bool tr, const VS* E, VS* x, double rtol, int ma
 extern "C" {
 
 hdg_status hdg_solver_create(hdg_sys* sys, int32_t restart, hdg_solver** out) {
-  return solver_build(sys, restart, 0, nullptr, 0, out);
+  return solver_build(sys, restart, 0, 0, nullptr, 0, out);
 }
 
 hdg_status hdg_solver_create_ws(hdg_sys* sys, int32_t restart, int32_t precond, void* workspace, int64_t bytes,
                                 hdg_solver** out) {
   if (!workspace) return HDG_EINVAL;
-  return solver_build(sys, restart, precond, workspace, bytes, out);
+  return solver_build(sys, restart, precond, 0, workspace, bytes, out);
 }
 
 int64_t hdg_solver_workspace_bytes(const hdg_mesh* mesh, int32_t restart, int32_t precond) {
@@ -1256,6 +1280,19 @@ int64_t hdg_solver_workspace_bytes(const hdg_mesh* mesh, int32_t restart, int32_
   int sms = 0;
   if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, mesh->ctx->device) != cudaSuccess) return -1;
   return (int64_t)plan_solver(mesh, restart, precond, sms).total;
+}
+
+hdg_status hdg_solver_create_ws_arith(hdg_sys* sys, int32_t restart, int32_t precond, int32_t arith, void* workspace,
+                                      int64_t bytes, hdg_solver** out) {
+  if (!workspace) return HDG_EINVAL;
+  return solver_build(sys, restart, precond, arith, workspace, bytes, out);
+}
+
+int64_t hdg_solver_workspace_bytes_arith(const hdg_mesh* mesh, int32_t restart, int32_t precond, int32_t arith) {
+  if (!mesh || restart < 1 || restart > kMaxRestart || precond < 0 || precond > 3 || arith < 0 || arith > 1) return -1;
+  int sms = 0;
+  if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, mesh->ctx->device) != cudaSuccess) return -1;
+  return (int64_t)plan_solver(mesh, restart, precond, sms, arith).total;
 }
 
 hdg_status hdg_solver_destroy(hdg_solver* S) {

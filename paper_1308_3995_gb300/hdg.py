@@ -36,7 +36,8 @@ EXPORTS = ["hdg_create", "hdg_destroy", "hdg_last_error", "hdg_mesh_create", "hd
            "hdg_sys_set_cfl", "hdg_cfl_law", "hdg_autotune", "hdg_trace_solve_ex", "hdg_adjoint_condense",
            "hdg_adapt_indicators", "hdg_adapt_mark",
            "hdg_mesh_create_bc", "hdg_solver_set_preconditioner", "hdg_solver_setup", "hdg_solver_precond_apply",
-           "hdg_solver_colors", "hdg_solver_create_ws", "hdg_solver_workspace_bytes", "hdg_solve_step_host",
+           "hdg_solver_colors", "hdg_solver_create_ws", "hdg_solver_workspace_bytes",
+           "hdg_solver_create_ws_arith", "hdg_solver_workspace_bytes_arith", "hdg_solve_step_host",
            "hdg_sys_bucket_times", "hdg_sys_set_source", "hdg_batch_create", "hdg_batch_destroy",
            "hdg_batch_groups", "hdg_batch_condense", "hdg_batch_recover", "hdg_batch_step_host_async",
            "hdg_batch_autotune", "hdg_batch_graph_create", "hdg_batch_graph_launch", "hdg_batch_launches",
@@ -165,6 +166,11 @@ def lib(build: bool = True):
                                            ctypes.POINTER(_vp)]
         L.hdg_solver_workspace_bytes.argtypes = [_vp, ctypes.c_int32, ctypes.c_int32]
         L.hdg_solver_workspace_bytes.restype = ctypes.c_int64
+        L.hdg_solver_create_ws_arith.argtypes = [_vp, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32, _vp,
+                                                 ctypes.c_int64, ctypes.POINTER(_vp)]
+        L.hdg_solver_create_ws_arith.restype = ctypes.c_int
+        L.hdg_solver_workspace_bytes_arith.argtypes = [_vp, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32]
+        L.hdg_solver_workspace_bytes_arith.restype = ctypes.c_int64
         L.hdg_solve_step_host.argtypes = [_vp, _vp, _vp, _vp, _vp, _vp, ctypes.c_double, ctypes.c_int32,
                                           ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(ctypes.c_double), _vp]
         L.hdg_trace_solve_ex.argtypes = [_vp, _vp, ctypes.c_int32, _vp, ctypes.c_double, ctypes.c_int32,
@@ -224,25 +230,29 @@ class Solver:
 
     BLOCK_JACOBI, BLOCK_SGS, BLOCK_ILU0, BLOCK_ILU0_F32 = 0, 1, 2, 3
 
-    def __init__(self, system: "System", restart: int = 30, precond: int = 0, workspace=None):
+    def __init__(self, system: "System", restart: int = 30, precond: int = 0, workspace=None, arith: int = 0):
         """precond: 0 block Jacobi, 1 multicolor block symmetric Gauss-Seidel, 2 block ILU(0)
         in the multicolor order, 3 the same with binary32 factors.  workspace: optional (device pointer, bytes) holding every
-        device buffer (hdg_solver_create_ws; size from ``workspace_bytes``)."""
+        device buffer (hdg_solver_create_ws_arith; size from ``workspace_bytes`` with the same arith).
+        arith: the GMRES arithmetic (0 binary64, 1 float-float; hdg_solver_set_arithmetic)."""
         h = _vp()
         if workspace is None:
             _check(lib().hdg_solver_create(system.h, int(restart), ctypes.byref(h)), system.ctx.h)
             self.h, self.sys = h, system
             _check(lib().hdg_solver_set_preconditioner(h, int(precond)), system.ctx.h)
+            if arith:
+                self.set_arithmetic(arith)
         else:
             ptr, nbytes = workspace
-            _check(lib().hdg_solver_create_ws(system.h, int(restart), int(precond), ctypes.c_void_p(int(ptr)),
-                                              int(nbytes), ctypes.byref(h)), system.ctx.h)
+            _check(lib().hdg_solver_create_ws_arith(system.h, int(restart), int(precond), int(arith),
+                                                    ctypes.c_void_p(int(ptr)), int(nbytes), ctypes.byref(h)),
+                   system.ctx.h)
             self.h, self.sys = h, system
 
     @staticmethod
-    def workspace_bytes(mesh: "Mesh", restart: int = 30, precond: int = 0) -> int:
-        """hdg_solver_workspace_bytes: device bytes of a solver on this mesh (for create_ws)."""
-        n = int(lib().hdg_solver_workspace_bytes(mesh.h, int(restart), int(precond)))
+    def workspace_bytes(mesh: "Mesh", restart: int = 30, precond: int = 0, arith: int = 0) -> int:
+        """hdg_solver_workspace_bytes_arith: device bytes of a solver on this mesh (for a workspace)."""
+        n = int(lib().hdg_solver_workspace_bytes_arith(mesh.h, int(restart), int(precond), int(arith)))
         if n < 0:
             raise HdgError(HDG_EINVAL, "hdg_solver_workspace_bytes: invalid arguments")
         return n

@@ -35,7 +35,8 @@ on the same stream).  Up to ``max_inflight`` batches run at once, each on its
 own stream; a batch completes all of its requests together.
 
 The plain baseline is the same loop with one slot and binary64 arithmetic
-(requests served one at a time, in arrival order).
+(requests served one at a time, in arrival order; its trace solves in binary64
+too, ``solver_arith=0``).
 
 Latency is measured on the host clock from a request's arrival time to the
 moment its completion event is observed; throughput is elements / makespan.
@@ -214,8 +215,10 @@ class Server:
             raise ValueError("batched launches serve step requests (solve=False)")
         self.batched, self.max_inflight = bool(batched), int(max_inflight)
         self.batch_max_elems = int(batch_max_elems)   # 0: a batch takes every admitted request
-        # GMRES arithmetic of solve requests (hdg_solver_set_arithmetic): binary64 unless asked
-        self.solver_arith = 0 if solver_arith is None else int(solver_arith)
+        # GMRES arithmetic of solve requests (hdg_solver_set_arithmetic): float-float (about twice as fast
+        # per iteration, same converged solution) unless asked; its double-word copies are planned into
+        # the request's arena region
+        self.solver_arith = 1 if solver_arith is None else int(solver_arith)
         self.ctx, self.slots, self.precision, self.keep = ctx, int(slots), int(precision), keep_outputs
         self.solve, self.precond, self.rtol, self.cfl = bool(solve), int(precond), float(rtol), float(cfl)
         self.restart, self.max_iter = int(restart), int(max_iter)
@@ -242,8 +245,8 @@ class Server:
             try:
                 base = self.buf.data_ptr() + off
                 sysm = hdg.System(self.ctx, r.mesh, prm, workspace=(base, n_sys))
-                sol = hdg.Solver(sysm, self.restart, self.precond, workspace=(base + n_sys, n_sol))
-                sol.set_arithmetic(self.solver_arith)
+                sol = hdg.Solver(sysm, self.restart, self.precond, workspace=(base + n_sys, n_sol),
+                                 arith=self.solver_arith)
                 r.iters, _ = sol.step_host(r.U, r.Lam, r.dU_host, r.dLam_host, self.rtol, self.max_iter, st)
                 r.done_s = time.perf_counter() - t0_box[0]
                 if self.keep:
@@ -293,7 +296,7 @@ class Server:
                     mesh = r.mesh
                     prm = self._params(wl)
                     n_sys = Arena._round(mesh.workspace_bytes(prm))
-                    n_sol = hdg.Solver.workspace_bytes(mesh, self.restart, self.precond) if self.solve else 0
+                    n_sol = hdg.Solver.workspace_bytes(mesh, self.restart, self.precond, self.solver_arith) if self.solve else 0
                     need = n_sys + n_sol
                     if need > self.arena.capacity:
                         raise hdg.HdgError(hdg.HDG_ENOMEM, f"request {r.rid} needs {need} bytes, arena holds "

@@ -152,3 +152,29 @@ def test_float_float_refused_in_a_callers_workspace(ctx):
     it, rel = solver.solve(x, rtol=1e-10, max_iter=500)        # still binary64 and working
     assert rel <= 1e-10
     solver.close()
+
+
+@pytest.mark.parametrize("precond", [0, 2, 3])
+def test_float_float_solver_planned_in_a_callers_workspace(ctx, precond):
+    """hdg_solver_create_ws_arith(..., arith 1, ...): the double-word copies planned into the caller's
+    workspace (a larger plan than binary64's), the solver starts in float-float arithmetic and matches
+    the dense oracle solve, twice in a row."""
+    from paper_1308_3995_gb300 import hdg
+    wl = G.small_variant(G.WORKLOADS["ns_mixp_65k"], 4, 5)
+    om, U, Lam, mesh, sysm = _setup(ctx, wl, 10.0)
+    r = om.condense(oracle_params(wl, 10.0), U, Lam)
+    ref = O.dense_solve(om.dense_K(r["K"]), r["E"])
+    n0 = hdg.Solver.workspace_bytes(mesh, 30, precond, 0)
+    n1 = hdg.Solver.workspace_bytes(mesh, 30, precond, 1)
+    assert n1 > n0
+    ws = torch.empty(n1 // 8 + 64, dtype=torch.float64, device="cuda:0")
+    solver = hdg.Solver(sysm, restart=30, precond=precond, workspace=(ws.data_ptr(), n1), arith=1)
+    solver.set_arithmetic(1)                    # already planned: no allocation, no error
+    for _ in range(2):
+        x = torch.zeros(mesh.lam_len, dtype=torch.float64, device="cuda:0")
+        it, rel = solver.solve(x, rtol=1e-12, max_iter=2000)
+        assert rel <= 1e-12 and rel_err(x.cpu().numpy(), ref) < 1e-10
+    solver.close()
+    with pytest.raises(hdg.HdgError) as ei:      # a binary64-sized workspace is too short for arith 1
+        hdg.Solver(sysm, restart=30, precond=precond, workspace=(ws.data_ptr(), n0), arith=1)
+    assert ei.value.status == hdg.HDG_EINVAL
