@@ -3,6 +3,10 @@
 
 namespace hdg {
 
+bool launch_ns_far(int p, const DevMesh& m, const DevSys& s, const Phys& ph, const double* tab, const TabOff& to,
+                   const double* U, const double* Lam, const int* elems, int n, int ntmax, cudaStream_t st,
+                   std::string* err);
+
 bool launch_ns_ff(int p, const DevMesh& m, const DevSys& s, const Phys& ph, const void* tab, const TabOff& to,
                   const double* U, const double* Lam, const int* elems, int n, int ntmax, cudaStream_t st,
                   std::string* err);
@@ -30,7 +34,8 @@ int launch_condense_ns(const DevMesh& m, const DevSys& s, const Phys& ph, const 
     if (ph.adjoint)
       ok = launch_ns_adjoint(p, m, s, ph, tab, tab_ff, to, U, Lam, bucket[p], bucket_n[p], bucket_ntmax[p], st, err);
     else if (ph.precision == HDG_FP64)
-      ok = launch_ns_p<double>(p, m, s, ph, tab, to, U, Lam, bucket[p], bucket_n[p], bucket_ntmax[p], st, err);
+      ok = m.far ? launch_ns_far(p, m, s, ph, tab, to, U, Lam, bucket[p], bucket_n[p], bucket_ntmax[p], st, err)
+                 : launch_ns_p<double>(p, m, s, ph, tab, to, U, Lam, bucket[p], bucket_n[p], bucket_ntmax[p], st, err);
     else
       ok = launch_ns_ff(p, m, s, ph, tab_ff, to, U, Lam, bucket[p], bucket_n[p], bucket_ntmax[p], st, err);
     if (!ok) return -1;

@@ -152,7 +152,10 @@ struct NsLayout {
 // one CTA per SM anyway.
 // BATCH: the launch walks the work list `bt` over the elements of several
 // systems (hdg_batch_condense); otherwise m_, s_, ph_, U_, Lam_ and elems.
-template <int P, class T, bool ADJ, bool BATCH = false>
+// FAR: the far-field boundary code is compiled in (meshes with far-field
+// faces, and every batch); without it the kernel is the one of periodic and
+// wall-bounded meshes, with none of that code's registers.
+template <int P, class T, bool ADJ, bool BATCH = false, bool FAR = BATCH>
 __global__ void __launch_bounds__(ns_threads<P>(), (P == 1 ? 4 : (P == 2 ? 2 : 1))) k_condense_ns(DevMesh m_, DevSys s_, Phys ph_, const T* __restrict__ tab,
                                                              TabOff to, const double* __restrict__ U_,
                                                              const double* __restrict__ Lam_,
@@ -293,7 +296,7 @@ __global__ void __launch_bounds__(ns_threads<P>(), (P == 1 ? 4 : (P == 2 ? 2 : 1
       g_wall = (g_bc[0] == 3) || (g_bc[1] == 3) || (g_bc[2] == 3);
       g_bnd = (g_e[0] < 0) || (g_e[1] < 0) || (g_e[2] < 0);
       int nff = 0;
-      for (int a = 0; a < 3; ++a)
+      for (int a = 0; FAR && a < 3; ++a)
         if (g_bc[a] == 2)
           for (int q = 0; q < P + 2; ++q) {
             g_ffa[nff] = (unsigned char)a;
@@ -387,7 +390,7 @@ __global__ void __launch_bounds__(ns_threads<P>(), (P == 1 ? 4 : (P == 2 ? 2 : 1
           if (f < 4) qv[0][f] = acc; else if (f < 8) qv[1][f - 4] = acc; else w[f - 8] = acc;
         }
         const T nx = g_n[a][0], ny = g_n[a][1];
-        if (g_e[a] < 0 && g_bc[a] == 2) {
+        if (FAR && g_e[a] < 0 && g_bc[a] == 2) {
           // characteristic far field (Sec. 2.1): its own frame (see ns_farfield_point)
           ns_farfield_point(w, qv, nx, ny, we, ph.winf, C, V, sFhat + t * 4, sAl + t * 16, sAq + t * 24, sFb + t * 20);
           continue;
@@ -495,7 +498,7 @@ __global__ void __launch_bounds__(ns_threads<P>(), (P == 1 ? 4 : (P == 2 ? 2 : 1
       for (int j = 0; j < NP; ++j) A::madd(acc, sDk[k * NP * NP + i * NP + j], sU[(8 + f) * NP + j]);
       for (int a = 0; a < 3; ++a) {
         const T sc = A::mul(g_n[a][k], g_len[a]);
-        if (g_bc[a] == 2) {  // far field: -n_k <phi_i, w_b,f(w)>_e at the edge points
+        if (FAR && g_bc[a] == 2) {  // far field: -n_k <phi_i, w_b,f(w)>_e at the edge points
           const T* phe = tab + to.edge_phi[P][P][a][g_fl[a]];
           T s2 = zero;
           for (int q = 0; q < P + 2; ++q) A::madd(s2, phe[q * NP + i], sFb[(a * kNsPt + q) * 20 + f]);
@@ -837,7 +840,7 @@ __global__ void __launch_bounds__(ns_threads<P>(), (P == 1 ? 4 : (P == 2 ? 2 : 1
           }
         }
         __syncthreads();
-        if (g_nff) {
+        if (FAR && g_nff) {
           // far field: A_qw of block (k', g) also holds -n_k' sum_x phi_i(x) (we J)_{g,g2}(x) phi_j(x)
           // for every field g2 (the characteristic state couples the fields).  Its products go
           // through the far-field points x: Y[r][x] = sum_i' M[r][i'] phi_i'(x) for the block
@@ -960,7 +963,7 @@ __global__ void __launch_bounds__(ns_threads<P>(), (P == 1 ? 4 : (P == 2 ? 2 : 1
     // X_q = (R_q - A_qw X_w) / det; with far-field faces A_qw also holds
     // -n_k sum_x phi_i(x) (we J)_fg(x) phi_j(x), applied through the points in column chunks:
     // Tf[x][f][c] = sum_g (we J)_fg(x) X_w,g(x, c)
-    const int nff = g_nff;
+    const int nff = FAR ? g_nff : 0;
     const int cch = nff ? max(1, lay.nyf / (4 * nff)) : nr1;
     for (int c0 = 0; c0 < nr1; c0 += cch) {
       const int nc = min(cch, nr1 - c0);
@@ -1003,7 +1006,7 @@ __global__ void __launch_bounds__(ns_threads<P>(), (P == 1 ? 4 : (P == 2 ? 2 : 1
         xk[(size_t)c * N + r] = A::to_d(v);
         bad |= A::bad(v);
       }
-      __syncthreads();
+      if (nff) __syncthreads();  // the next chunk rewrites sYf
     }
     // ---------------- a6/a7: S = S0 - C' X_w,B, E = E0 - C' X_w,F, assembly ----------------
     for (int r = ty; r < nt; r += NW) {
@@ -1075,33 +1078,33 @@ __global__ void __launch_bounds__(ns_threads<P>(), (P == 1 ? 4 : (P == 2 ? 2 : 1
   }
 }
 
-template <int P, class T, bool ADJ, bool BATCH = false>
+template <int P, class T, bool ADJ, bool BATCH = false, bool FAR = BATCH>
 inline bool launch_ns_bucket(const DevMesh& m, const DevSys& s, const Phys& ph, const T* tab, const TabOff& to,
                              const double* U, const double* Lam, const int* elems, int n, int ntmax, cudaStream_t st,
                              std::string* err, const BatchRef& bt = BatchRef{}) {
   const NsLayout<P> lay(ntmax);
-  // the far-field regions close the layout: a mesh without far-field faces leaves them out
-  const size_t bytes = sizeof(T) * (size_t)((BATCH || m.far) ? lay.total : lay.oFb);
-  cudaError_t ce = cudaFuncSetAttribute(k_condense_ns<P, T, ADJ, BATCH>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+  // the far-field regions close the layout: an instance without far-field code leaves them out
+  const size_t bytes = sizeof(T) * (size_t)(FAR ? lay.total : lay.oFb);
+  cudaError_t ce = cudaFuncSetAttribute(k_condense_ns<P, T, ADJ, BATCH, FAR>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                         (int)bytes);
   if (ce != cudaSuccess) { *err = std::string("NS kernel shared memory: ") + cudaGetErrorString(ce); return false; }
   int dev = 0, sms = 0, per_sm = 0;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_condense_ns<P, T, ADJ, BATCH>, ns_threads<P>(), bytes);
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_condense_ns<P, T, ADJ, BATCH, FAR>, ns_threads<P>(), bytes);
   if (per_sm < 1) { *err = "NS condensation kernel does not fit on an SM"; return false; }
   const long grid = condense_grid(ph, P, sms, per_sm, n);
-  k_condense_ns<P, T, ADJ, BATCH><<<(int)grid, ns_threads<P>(), bytes, st>>>(m, s, ph, tab, to, U, Lam, elems, n, ntmax,
-                                                                         bt);
+  k_condense_ns<P, T, ADJ, BATCH, FAR><<<(int)grid, ns_threads<P>(), bytes, st>>>(m, s, ph, tab, to, U, Lam, elems, n,
+                                                                              ntmax, bt);
   ce = cudaGetLastError();
   if (ce != cudaSuccess) { *err = cudaGetErrorString(ce); return false; }
   return true;
 }
 
 template <int P, class T>
-inline int ns_occ(int ntmax) {
+inline int ns_occ(int ntmax) {  // the instance without far-field code
   const NsLayout<P> lay(ntmax);
-  const size_t bytes = sizeof(T) * (size_t)lay.total;
+  const size_t bytes = sizeof(T) * (size_t)lay.oFb;
   if (cudaFuncSetAttribute(k_condense_ns<P, T, false, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes) != cudaSuccess)
     return 0;
   int per_sm = 0;
@@ -1120,15 +1123,15 @@ inline int ns_occ_p(int p, int ntmax) {
   return 0;
 }
 
-template <class T, bool ADJ = false>
+template <class T, bool ADJ = false, bool FAR = false>
 inline bool launch_ns_p(int p, const DevMesh& m, const DevSys& s, const Phys& ph, const T* tab, const TabOff& to,
                         const double* U, const double* Lam, const int* elems, int n, int ntmax, cudaStream_t st,
                         std::string* err) {
   switch (p) {
-    case 1: return launch_ns_bucket<1, T, ADJ>(m, s, ph, tab, to, U, Lam, elems, n, ntmax, st, err);
-    case 2: return launch_ns_bucket<2, T, ADJ>(m, s, ph, tab, to, U, Lam, elems, n, ntmax, st, err);
-    case 3: return launch_ns_bucket<3, T, ADJ>(m, s, ph, tab, to, U, Lam, elems, n, ntmax, st, err);
-    case 4: return launch_ns_bucket<4, T, ADJ>(m, s, ph, tab, to, U, Lam, elems, n, ntmax, st, err);
+    case 1: return launch_ns_bucket<1, T, ADJ, false, FAR>(m, s, ph, tab, to, U, Lam, elems, n, ntmax, st, err);
+    case 2: return launch_ns_bucket<2, T, ADJ, false, FAR>(m, s, ph, tab, to, U, Lam, elems, n, ntmax, st, err);
+    case 3: return launch_ns_bucket<3, T, ADJ, false, FAR>(m, s, ph, tab, to, U, Lam, elems, n, ntmax, st, err);
+    case 4: return launch_ns_bucket<4, T, ADJ, false, FAR>(m, s, ph, tab, to, U, Lam, elems, n, ntmax, st, err);
   }
   *err = "degree out of range";
   return false;

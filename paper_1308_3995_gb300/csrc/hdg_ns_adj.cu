@@ -8,11 +8,16 @@ bool launch_ns_adjoint_ff(int p, const DevMesh& m, const DevSys& s, const Phys& 
                           const TabOff& to, const double* U, const double* Lam, const int* elems, int n, int ntmax,
                           cudaStream_t st, std::string* err);
 
+bool launch_ns_adjoint_far(int p, const DevMesh& m, const DevSys& s, const Phys& ph, const double* tab,
+                           const TabOff& to, const double* U, const double* Lam, const int* elems, int n, int ntmax,
+                           cudaStream_t st, std::string* err);
+
 bool launch_ns_adjoint(int p, const DevMesh& m, const DevSys& s, const Phys& ph, const double* tab,
                        const void* tab_ff, const TabOff& to, const double* U, const double* Lam, const int* elems,
                        int n, int ntmax, cudaStream_t st, std::string* err) {
   if (ph.precision == HDG_FP64)
-    return launch_ns_p<double, true>(p, m, s, ph, tab, to, U, Lam, elems, n, ntmax, st, err);
+    return m.far ? launch_ns_adjoint_far(p, m, s, ph, tab, to, U, Lam, elems, n, ntmax, st, err)
+                 : launch_ns_p<double, true>(p, m, s, ph, tab, to, U, Lam, elems, n, ntmax, st, err);
   return launch_ns_adjoint_ff(p, m, s, ph, tab_ff, to, U, Lam, elems, n, ntmax, st, err);
 }
 
