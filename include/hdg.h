@@ -396,9 +396,13 @@ hdg_status hdg_sys_io(const hdg_sys* sys, double** U, double** Lam, double** dLa
  * with restarted GMRES, left-preconditioned by block Jacobi (default: M = the
  * diagonal face blocks of K, inverted once per solve by Gauss-Jordan with
  * partial pivoting), multicolor block SGS or block ILU(0) (see
- * hdg_solver_set_preconditioner).  Arnoldi uses classical Gram-Schmidt with one
- * re-orthogonalisation pass; the Hessenberg least-squares problem (Givens
- * rotations) is solved on the host.  Everything is binary64. */
+ * hdg_solver_set_preconditioner).  Arnoldi uses classical Gram-Schmidt with
+ * one re-orthogonalisation pass, run delayed (one reduction and one update
+ * pass over the basis per iteration); the Hessenberg columns, their Givens
+ * rotations and the least-squares solve run on the device, the residual
+ * estimate is read back once per chunk of four iterations.  Binary64 by
+ * default; double-word arithmetic on the binary32 pipe with
+ * hdg_solver_set_arithmetic. */
 typedef struct hdg_solver hdg_solver;
 
 /* Allocate the solver's device state for `sys` (Krylov basis of restart+1
