@@ -285,10 +285,10 @@ __global__ void __launch_bounds__(kDotThreads, 2) k_dots(const ST* __restrict__ 
 //   h1 [R+1] the first projection of the column being built,
 //   Hraw [(R+1) R] the Hessenberg matrix (column-major), H [(R+1) R] its
 //   rotated (triangular) form, cs, sn [R], g [R+1], y [R], sc [kArnoldiScalars]:
-//   sc[0] 1 / rho, sc[1] residual estimate, sc[2] ||M^-1 E||, sc[3] rtol,
-//   sc[4] 0 running / 1 converged or breakdown / 2 out of iterations, sc[5]
-//   columns of H built in the cycle, sc[6] iterations so far, sc[7] max_iter,
-//   sc[8] d = v_j^T z.
+//   sc[1] residual estimate, sc[2] ||M^-1 E||, sc[3] rtol, sc[4] 0 running /
+//   1 converged or breakdown / 2 out of iterations, sc[5] columns of H built
+//   in the cycle, sc[6] iterations so far, sc[7] max_iter (sc[0], sc[8], sc[9]
+//   unused: every block of the update derives 1 / rho and d from the sums).
 constexpr int kArnoldiScalars = 10;
 struct ArnoldiViews {
   double *red, *h1, *Hraw, *H, *cs, *sn, *g, *y, *sc;
