@@ -52,9 +52,10 @@ namespace hdg {
 
 // threads per element CTA: 128 for p = 1, so that four CTAs (four elements)
 // share an SM within the register file (uniform p = 1: 2.67 -> 3.85 M elements/s
-// in binary64, 2.48 -> 4.25 M in float-float, against two CTAs of 256); 256
-// otherwise (at p = 2 the smaller CTA measured no better in binary64 and worse in
-// float-float, its shared memory allowing only two per SM on mixed meshes)
+// in binary64, 2.48 -> 4.25 M in float-float, against two CTAs of 256); 256 for
+// p = 2 (the smaller CTA measured no better in binary64 and worse in
+// float-float, its shared memory allowing only two per SM on mixed meshes);
+// 512 for p >= 3, one CTA per SM
 // One far-field edge point of the Navier-Stokes kernel (Sec. 2.1): w_b(w) by
 // characteristic upwinding against the free stream and d w_b / d w, the flux
 // (f_c(w_b) - f_v(w_b, q)) . n whole (we times it into fhat[4]), d fhat / d w =
@@ -109,7 +110,7 @@ __device__ __noinline__ void ns_farfield_point(const T* w, const T (*qv)[4], T n
 }
 
 template <int P>
-constexpr int ns_threads() { return P == 1 ? 128 : 256; }
+constexpr int ns_threads() { return P == 1 ? 128 : (P >= 3 ? 512 : 256); }
 constexpr int kNsPt = 6;   // edge point slots per face
 
 template <int P>
@@ -149,7 +150,10 @@ struct NsLayout {
 // buckets stall on block barriers with the binary64 pipe 40-55 % busy; the
 // second CTA hides them (Navier-Stokes p mix: 101.7 -> 86.0 ms per step in
 // binary64, 76.3 -> 70.5 ms in float-float).  For p >= 3 shared memory allows
-// one CTA per SM anyway.
+// one CTA per SM anyway; there the CTA has 16 warps (registers capped at 128
+// the same way), which hide more of the latency inside each phase than 8 warps
+// with 248-254 registers (p mix: 84.1 -> 82.9 ms binary64, 77.2 -> 75.5 ms
+// float-float).
 // BATCH: the launch walks the work list `bt` over the elements of several
 // systems (hdg_batch_condense); otherwise m_, s_, ph_, U_, Lam_ and elems.
 // FAR: the far-field boundary code is compiled in (meshes with far-field
