@@ -228,7 +228,12 @@ hdg_status hdg_sys_destroy(hdg_sys* sys);
  * Outputs stay in `sys` (see hdg_sys_get).  Every diagonal block of K and
  * every entry of E / res_lam is the sum of exactly two element contributions,
  * so results are bitwise reproducible.  elem_status[K] is set to 0 (ok),
- * 1 (zero pivot) or 2 (non-finite result). */
+ * 1 (zero pivot) or 2 (non-finite result).
+ * Launches: one per degree bucket, the buckets of a mixed-degree mesh on their
+ * own streams (forked from and joined back to `stream`); a bucket whose trace
+ * sizes differ (a face takes the larger degree of its two sides) is launched in
+ * groups of trace sizes at which the kernel keeps the same number of resident
+ * CTAs per SM, each group's shared memory sized by its largest trace. */
 hdg_status hdg_condense(hdg_sys* sys, const double* U, const double* Lam, void* stream);
 
 /* Reconstruction, Eq. (ls): dU_K = X_F - X_B dLambda_K for every element,

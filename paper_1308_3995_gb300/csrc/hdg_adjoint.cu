@@ -104,7 +104,7 @@ hdg_status hdg_adjoint_condense(hdg_sys* adj, const hdg_sys* primal, const doubl
   ds.ftilde = Ftilde;
   std::string err;
   const int n = launch_condense(M->dm, ds, ph, ctx->d_tab, ctx->d_tab_ff, ctx->tab.off, U, Lam, M->d_bucket,
-                                M->bucket_n, M->bucket_ntmax, stream, &err);
+                                M->bucket_n, M->bucket_ntmax, stream, &err, nullptr, &M->bucket_nt);
   if (n < 0) return fail(ctx, HDG_ECUDA, "hdg_adjoint_condense: " + err);
   // E~ = -X_B^T F~ from the primal local solves
   AdjRhs a{M->n_face, adj->d_face_el, M->dm.elem_face, M->dm.face_p, M->dm.u_off, M->dm.lam_off, M->dm.x_off,

@@ -75,6 +75,7 @@ PlanRef plan_ref(const hdg_mesh* M) {
   r.bucket = M->d_bucket;
   r.bucket_n = M->bucket_n;
   r.bucket_ntmax = M->bucket_ntmax;
+  r.bucket_nt = &M->bucket_nt;
   r.n_face = M->n_face;
   r.nfield = M->nfield;
   r.lam_len = M->lam_len;
@@ -259,12 +260,17 @@ hdg_status hdg_mesh_create_bc(hdg_ctx* ctx, int32_t n_elem, int32_t nfield, cons
         while (M->k_col[5 * (size_t)ea + slot] != eb) ++slot;
         kblk[9 * (size_t)K + 3 * a + b] = M->k_blkoff[5 * (size_t)ea + slot];
       }
-  // degree buckets
+  // degree buckets, each sorted by trace size (launch_groups)
   std::vector<int> bucket[kMaxP + 1];
+  std::vector<int> nt_of(n_elem);
   for (int K = 0; K < n_elem; ++K) {
+    nt_of[K] = elem_nt(M, K);
     bucket[elem_p[K]].push_back(K);
-    M->bucket_ntmax[elem_p[K]] = std::max(M->bucket_ntmax[elem_p[K]], elem_nt(M, K));
+    M->bucket_ntmax[elem_p[K]] = std::max(M->bucket_ntmax[elem_p[K]], nt_of[K]);
+    ++M->bucket_nt.cnt[elem_p[K]][nt_of[K] / 4];
   }
+  for (int p = 1; p <= kMaxP; ++p)
+    std::stable_sort(bucket[p].begin(), bucket[p].end(), [&](int a, int b) { return nt_of[a] < nt_of[b]; });
   // upload
   hdg_status st = HDG_OK;
   DevMesh& d = M->dm;
@@ -549,7 +555,7 @@ hdg_status hdg_condense(hdg_sys* S, const double* U, const double* Lam, void* st
     Phys ph = S->ph;
     ph.persistent = 0;
     n = launch_condense(M->dm, S->ds, ph, ctx->d_tab, ctx->d_tab_ff, ctx->tab.off, U, Lam, M->d_bucket, M->bucket_n,
-                        M->bucket_ntmax, stream, &err, bs);
+                        M->bucket_ntmax, stream, &err, bs, &M->bucket_nt);
     if (n >= 0)
       for (int p = 1; p <= kMaxP; ++p)
         if (M->bucket_n[p]) {
@@ -560,7 +566,7 @@ hdg_status hdg_condense(hdg_sys* S, const double* U, const double* Lam, void* st
   } else {
     S->timed = false;
     n = launch_condense(M->dm, S->ds, S->ph, ctx->d_tab, ctx->d_tab_ff, ctx->tab.off, U, Lam, M->d_bucket,
-                        M->bucket_n, M->bucket_ntmax, stream, &err);
+                        M->bucket_n, M->bucket_ntmax, stream, &err, nullptr, &M->bucket_nt);
   }
   if (n < 0) return fail(ctx, HDG_ECUDA, "hdg_condense: " + err);
   S->launches = n;
@@ -646,8 +652,16 @@ hdg_status hdg_autotune(hdg_sys* S, const double* U, const double* Lam, int32_t*
   for (int p = 1; p <= kMaxP && rs == HDG_OK; ++p) {
     if (grid_out) grid_out[p] = S->ph.grid[p];
     if (M->bucket_n[p] == 0) continue;
-    const int occ = condense_occupancy(S->ph, p, M->bucket_ntmax[p]);
-    if (occ < 1) { rs = fail(ctx, HDG_ECUDA, "hdg_autotune: kernel does not fit on an SM"); break; }
+    if (condense_occupancy(S->ph, p, M->bucket_ntmax[p]) < 1) {
+      rs = fail(ctx, HDG_ECUDA, "hdg_autotune: kernel does not fit on an SM");
+      break;
+    }
+    // persistent candidates up to the occupancy at the bucket's smallest trace size (its
+    // launch groups with smaller traces may hold more CTAs per SM than the largest)
+    int ntmin = M->bucket_ntmax[p];
+    for (int t = 0; t < kNtSlots; ++t)
+      if (M->bucket_nt.cnt[p][t]) { ntmin = 4 * t; break; }
+    const int occ = condense_occupancy(S->ph, p, ntmin);
     int bn[kMaxP + 1] = {};
     bn[p] = M->bucket_n[p];
     float best_ms = 0.0f;
@@ -664,7 +678,7 @@ hdg_status hdg_autotune(hdg_sys* S, const double* U, const double* Lam, int32_t*
           break;
         }
         if (launch_condense(M->dm, S->ds, ph, ctx->d_tab, ctx->d_tab_ff, ctx->tab.off, U, Lam, M->d_bucket, bn,
-                            M->bucket_ntmax, stream, &err) < 0) {
+                            M->bucket_ntmax, stream, &err, nullptr, &M->bucket_nt) < 0) {
           rs = fail(ctx, HDG_ECUDA, "hdg_autotune: " + err);
           break;
         }

@@ -65,6 +65,13 @@ class DeviceGuard {
 
 constexpr int kMaxP = 4;          // element degrees 1..4
 constexpr int kMaxNt = 60;        // 3 faces x 4 fields x (4 + 1) modes
+constexpr int kNtSlots = kMaxNt / 4 + 1;  // element trace sizes 0, 4, ..., kMaxNt
+
+// Elements of each degree bucket per trace size (slot s: nt = 4 s), each
+// bucket's element list sorted by trace size.
+struct BucketNt {
+  int cnt[kMaxP + 1][kNtSlots];
+};
 constexpr int kCondThreads = 128; // threads per element CTA of the condensation kernels
 
 HDG_HD constexpr inline int n_basis(int p) { return (p + 1) * (p + 2) / 2; }
@@ -215,6 +222,7 @@ struct PlanRef {
   const int* const* bucket;
   const int* bucket_n;
   const int* bucket_ntmax;
+  const BucketNt* bucket_nt;
   int n_face, nfield;
   int64_t lam_len, dh_len;
   std::string* err;
@@ -227,14 +235,50 @@ PlanRef plan_ref(const hdg_mesh* mesh);
 int condense_occupancy(const Phys& ph, int p, int ntmax);
 int ns_occupancy(const Phys& ph, int p, int ntmax);
 
+// bucket_nt (optional): trace-size counts of the buckets, whose element lists are sorted by trace
+// size; a bucket is then launched in groups (launch_groups)
 int launch_condense(const DevMesh& m, const DevSys& s, const Phys& ph, const double* tab, const void* tab_ff,
                     const TabOff& off, const double* U, const double* Lam, const int* const* bucket,
                     const int* bucket_n, const int* bucket_ntmax, void* stream, std::string* err,
-                    void* const* bucket_streams = nullptr);
+                    void* const* bucket_streams = nullptr, const BucketNt* bucket_nt = nullptr);
 int launch_condense_ns(const DevMesh& m, const DevSys& s, const Phys& ph, const double* tab, const void* tab_ff,
                        const TabOff& off, const double* U, const double* Lam, const int* const* bucket,
                        const int* bucket_n, const int* bucket_ntmax, void* stream, std::string* err,
-                       void* const* bucket_streams = nullptr);
+                       void* const* bucket_streams = nullptr, const BucketNt* bucket_nt = nullptr);
+
+// The launches of degree bucket p.  Shared memory is sized by the largest trace size
+// of a launch, so one launch over a bucket whose trace sizes differ (faces of a
+// mixed-degree mesh take the larger degree of their two sides) holds every element
+// to the resident CTAs per SM of the largest.  With bucket_nt the bucket is cut into
+// runs of trace sizes at which the kernel keeps the same number of resident CTAs
+// per SM, one launch each, sized by the run's largest trace size.  launch(offset,
+// count, ntmax) enqueues one launch over elements offset .. offset + count - 1 of
+// the bucket's list.  Returns the launches enqueued, or -1.
+template <class F>
+inline int launch_groups(const Phys& ph, int p, int n, int ntmax, const BucketNt* bucket_nt, F&& launch) {
+  const int* c = bucket_nt ? bucket_nt->cnt[p] : nullptr;
+  int used = 0;
+  for (int t = 0; c && t < kNtSlots; ++t) used += c[t] > 0;
+  if (used <= 1) return launch(0, n, ntmax) ? 1 : -1;
+  int occ[kNtSlots];
+  for (int t = 0; t < kNtSlots; ++t) occ[t] = c[t] ? condense_occupancy(ph, p, 4 * t) : 0;
+  int launches = 0, off = 0, t = 0;
+  while (t < kNtSlots) {
+    if (!c[t]) { ++t; continue; }
+    int cnt = 0, top = 4 * t, e = t;
+    for (; e < kNtSlots; ++e) {
+      if (!c[e]) continue;
+      if (occ[e] != occ[t]) break;
+      cnt += c[e];
+      top = 4 * e;
+    }
+    if (!launch(off, cnt, top)) return -1;
+    ++launches;
+    off += cnt;
+    t = e;
+  }
+  return launches;
+}
 // batched launches (hdg_batch_*): one launch over the items of every system of
 // the work list `bt` whose elements have degree p (model and precision from ph)
 // mixed-precision local solves (precision HDG_MIXED_TF32 / HDG_MIXED_BF16, Euler)

@@ -126,25 +126,25 @@ int condense_occupancy(const Phys& ph, int p, int ntmax) {
 int launch_condense(const DevMesh& m, const DevSys& s, const Phys& ph, const double* tab, const void* tab_ff,
                     const TabOff& to, const double* U, const double* Lam, const int* const* bucket,
                     const int* bucket_n, const int* bucket_ntmax, void* stream, std::string* err,
-                    void* const* bucket_streams) {
+                    void* const* bucket_streams, const BucketNt* bucket_nt) {
   if (ph.model == HDG_NS_MIXED)
     return launch_condense_ns(m, s, ph, tab, tab_ff, to, U, Lam, bucket, bucket_n, bucket_ntmax, stream, err,
-                              bucket_streams);
+                              bucket_streams, bucket_nt);
   int launches = 0;
   for (int p = 1; p <= kMaxP; ++p) {
     if (bucket_n[p] == 0) continue;
     cudaStream_t st = (cudaStream_t)(bucket_streams ? bucket_streams[p] : stream);
-    bool ok;
-    if (ph.precision == HDG_MIXED_TF32 || ph.precision == HDG_MIXED_BF16)
-      ok = launch_euler_mixed(p, m, s, ph, tab, to, U, Lam, bucket[p], bucket_n[p], bucket_ntmax[p], st, err, BatchRef{},
-                              m.elem_bc != nullptr);
-    else if (ph.precision == HDG_FP64)
-      ok = launch_euler_p<double>(p, m, s, ph, tab, to, U, Lam, bucket[p], bucket_n[p], bucket_ntmax[p], st, err);
-    else
-      ok = launch_euler_p<ff>(p, m, s, ph, (const ff*)tab_ff, to, U, Lam, bucket[p], bucket_n[p], bucket_ntmax[p],
-                              st, err);
-    if (!ok) return -1;
-    ++launches;
+    const int* el = bucket[p];
+    const int k = launch_groups(ph, p, bucket_n[p], bucket_ntmax[p], bucket_nt, [&](int off, int n, int ntmax) {
+      if (ph.precision == HDG_MIXED_TF32 || ph.precision == HDG_MIXED_BF16)
+        return launch_euler_mixed(p, m, s, ph, tab, to, U, Lam, el + off, n, ntmax, st, err, BatchRef{},
+                                  m.elem_bc != nullptr);
+      if (ph.precision == HDG_FP64)
+        return launch_euler_p<double>(p, m, s, ph, tab, to, U, Lam, el + off, n, ntmax, st, err);
+      return launch_euler_p<ff>(p, m, s, ph, (const ff*)tab_ff, to, U, Lam, el + off, n, ntmax, st, err);
+    });
+    if (k < 0) return -1;
+    launches += k;
   }
   return launches;
 }

@@ -131,7 +131,7 @@ extern "C" hdg_status hdg_condense_noalloc(const hdg_mesh* mesh, const hdg_param
   phys_default_grid(ph);
   std::string err;
   const int n = launch_condense(*pr.dm, ds, ph, pr.tab, pr.tab_ff, *pr.off, U, Lam, pr.bucket, pr.bucket_n, pr.bucket_ntmax,
-                                stream, &err);
+                                stream, &err, nullptr, pr.bucket_nt);
   if (n < 0) {
     *pr.err = "hdg_condense_noalloc: " + err;
     return HDG_ECUDA;

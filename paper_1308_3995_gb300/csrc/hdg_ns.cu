@@ -25,21 +25,21 @@ int ns_occupancy(const Phys& ph, int p, int ntmax) {
 int launch_condense_ns(const DevMesh& m, const DevSys& s, const Phys& ph, const double* tab, const void* tab_ff,
                        const TabOff& to, const double* U, const double* Lam, const int* const* bucket,
                        const int* bucket_n, const int* bucket_ntmax, void* stream, std::string* err,
-                       void* const* bucket_streams) {
+                       void* const* bucket_streams, const BucketNt* bucket_nt) {
   int launches = 0;
   for (int p = 1; p <= kMaxP; ++p) {
     if (bucket_n[p] == 0) continue;
     cudaStream_t st = (cudaStream_t)(bucket_streams ? bucket_streams[p] : stream);
-    bool ok;
-    if (ph.adjoint)
-      ok = launch_ns_adjoint(p, m, s, ph, tab, tab_ff, to, U, Lam, bucket[p], bucket_n[p], bucket_ntmax[p], st, err);
-    else if (ph.precision == HDG_FP64)
-      ok = m.far ? launch_ns_far(p, m, s, ph, tab, to, U, Lam, bucket[p], bucket_n[p], bucket_ntmax[p], st, err)
-                 : launch_ns_p<double>(p, m, s, ph, tab, to, U, Lam, bucket[p], bucket_n[p], bucket_ntmax[p], st, err);
-    else
-      ok = launch_ns_ff(p, m, s, ph, tab_ff, to, U, Lam, bucket[p], bucket_n[p], bucket_ntmax[p], st, err);
-    if (!ok) return -1;
-    ++launches;
+    const int* el = bucket[p];
+    const int k = launch_groups(ph, p, bucket_n[p], bucket_ntmax[p], bucket_nt, [&](int off, int n, int ntmax) {
+      if (ph.adjoint) return launch_ns_adjoint(p, m, s, ph, tab, tab_ff, to, U, Lam, el + off, n, ntmax, st, err);
+      if (ph.precision == HDG_FP64)
+        return m.far ? launch_ns_far(p, m, s, ph, tab, to, U, Lam, el + off, n, ntmax, st, err)
+                     : launch_ns_p<double>(p, m, s, ph, tab, to, U, Lam, el + off, n, ntmax, st, err);
+      return launch_ns_ff(p, m, s, ph, tab_ff, to, U, Lam, el + off, n, ntmax, st, err);
+    });
+    if (k < 0) return -1;
+    launches += k;
   }
   return launches;
 }

@@ -28,6 +28,7 @@ struct hdg_mesh {
   int* d_bucket[hdg::kMaxP + 1] = {};
   int bucket_n[hdg::kMaxP + 1] = {};
   int bucket_ntmax[hdg::kMaxP + 1] = {};
+  hdg::BucketNt bucket_nt{};  // trace-size counts; each d_bucket list sorted by trace size
   hdg::DevMesh dm{};
 };
 
