@@ -41,21 +41,21 @@ HBM_PEAK_GBS = 6778.0       # measured copy bandwidth of the GB300s (MEA
 # (kernel_src_sha()); afterwards the bench reports them as stale (null) instead of quoting old numbers.
 KERNEL_SRC_FILES = ("hdg_euler.cuh", "hdg_kernels.cu", "hdg_ns.cuh", "hdg_ns.cu", "hdg_ns_ff.cu", "hdg_lu.cuh",
                     "hdg_arith.cuh", "hdg_physics.cuh", "hdg_internal.h")
-KERNEL_SRC_SHA = "57a6d61c547ee98b"
+KERNEL_SRC_SHA = "e607c906ea5f6fa4"
 # executed floating-point work per element, (binary64 flops, binary32 flops): 2 DFMA + DADD + DMUL and
 # 2 FFMA + FADD + FMUL from the SASS instruction counters (no paired FFMA2/FADD2/FMUL2 were issued),
 # one launch of each kernel on a 1,024-triangle uniform-degree periodic mesh (bench.py --profile-variants)
 EXEC_FLOPS_PER_ELEM = {
-    ("euler", 1, 0): (28856, 0), ("euler", 1, 1): (1050, 224496),
-    ("euler", 2, 0): (115403, 0), ("euler", 2, 1): (1206, 904880),
-    ("euler", 3, 0): (369078, 0), ("euler", 3, 1): (1414, 2881094),
-    ("euler", 4, 0): (997399, 0), ("euler", 4, 1): (1674, 7737944),
-    ("ns", 1, 0): (98527, 0), ("ns", 1, 1): (3123, 915414),
+    ("euler", 1, 0): (28472, 0), ("euler", 1, 1): (1050, 221616),
+    ("euler", 2, 0): (114635, 0), ("euler", 2, 1): (1206, 899120),
+    ("euler", 3, 0): (368566, 0), ("euler", 3, 1): (1414, 2877254),
+    ("euler", 4, 0): (997143, 0), ("euler", 4, 1): (1674, 7736024),
+    ("ns", 1, 0): (98143, 0), ("ns", 1, 1): (3123, 912534),
     ("ns", 2, 0): (396503, 0), ("ns", 2, 1): (6119, 3395168),
-    ("ns", 3, 0): (1232575, 0), ("ns", 3, 1): (6359, 10179814),
-    ("ns", 4, 0): (3229297, 0), ("ns", 4, 1): (6659, 26052336)}
+    ("ns", 3, 0): (1263656, 0), ("ns", 3, 1): (11991, 10373734),
+    ("ns", 4, 0): (3276121, 0), ("ns", 4, 1): (12291, 26361456)}
 # dram__bytes_read.sum + dram__bytes_write.sum of one full-size condensation launch (1-pass capture)
-TRAFFIC_PER_LAUNCH = {("euler_p3_16k", 0): 11923712 + 522423552}
+TRAFFIC_PER_LAUNCH = {("euler_p3_16k", 0): 12038656 + 522595840}
 
 
 def kernel_src_sha() -> str:
