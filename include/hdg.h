@@ -332,8 +332,10 @@ hdg_status hdg_sys_bucket_times(const hdg_sys* sys, float* ms);
  * element belongs to.  A batch condenses the elements of several systems --
  * different meshes, degree maps, flow parameters (alpha, Mach, CFL, far field),
  * Euler or Navier-Stokes -- with ONE kernel launch per (model, degree) group
- * over a work list of (system, element) runs, instead of one launch per system
- * and degree: many small requests then fill the GPU like one large one.  Each
+ * (one per run of trace sizes with equal occupancy, where the group's trace
+ * sizes differ) over a work list of (system, element) segments, instead of one
+ * launch per system and degree: many small requests then fill the GPU like one
+ * large one.  Each
  * element's arithmetic is that of hdg_condense (the same kernel source compiled
  * for the work list), so every system's X, K, E, residuals and status are
  * those of condensing it alone, up to the rounding of multiply-adds that the
@@ -358,16 +360,19 @@ int64_t hdg_batch_workspace_bytes(int32_t n_sys, hdg_sys* const* systems);
 hdg_status hdg_batch_create_in(hdg_ctx* ctx, int32_t n_sys, hdg_sys* const* systems, void* workspace,
                                int64_t workspace_bytes, void* stream, hdg_batch** out);
 hdg_status hdg_batch_destroy(hdg_batch* batch);
-/* The (model, degree) groups of the batch, one launch each: returns their
- * number G (<= 8) and fills model[G] (HDG_EULER / HDG_NS_MIXED), p[G] and
- * n_items[G] (elements over all systems); any array may be NULL. */
+/* The (model, degree) groups of the batch: returns their number G (<= 8) and
+ * fills model[G] (HDG_EULER / HDG_NS_MIXED), p[G] and n_items[G] (elements
+ * over all systems); any array may be NULL.  A group whose trace sizes differ
+ * is launched in runs of trace sizes at which the kernel keeps the same number
+ * of resident CTAs per SM (as hdg_condense does for a system's buckets). */
 int32_t hdg_batch_groups(const hdg_batch* batch, int32_t* model, int32_t* p, int32_t* n_items);
 /* a1-a7 for every element of every system, from each system's device U and Lam
  * staging buffers; groups run concurrently on forked streams, joined back
  * into `stream`.  Asynchronous. */
 hdg_status hdg_batch_condense(hdg_batch* batch, void* stream);
 /* a8 for every system: dU = X_F - X_B dLambda from its device dLam staging
- * buffer into its dU staging buffer, one launch per group.  Asynchronous. */
+ * buffer into its dU staging buffer, one launch per run of each group.
+ * Asynchronous. */
 hdg_status hdg_batch_recover(hdg_batch* batch, void* stream);
 /* A whole step of every system from HOST arrays (arrays of n_sys pointers, one
  * per system, in the order given to hdg_batch_create; pinned memory for

@@ -1,8 +1,9 @@
 // Batched condensation across systems (hdg_batch_*): the elements of several
 // systems -- different meshes, degree maps, flow parameters, Euler or
-// Navier-Stokes -- are condensed by one launch per (model, degree) group over a
-// work list of (system, element) segments, instead of one launch per system
-// and degree.  Each element's arithmetic is that of hdg_condense (the same
+// Navier-Stokes -- are condensed by one launch per (model, degree) group (one
+// per run of trace sizes with equal occupancy, where they differ) over a work
+// list of (system, element) segments, instead of one launch per system and
+// degree.  Each element's arithmetic is that of hdg_condense (the same
 // kernel source, instantiated for the work list), so every system's results
 // are those of condensing it alone up to the compiler's contraction of
 // multiply-adds.  The step of a batch can be captured into one CUDA graph and
@@ -21,10 +22,18 @@ using namespace hdg;
 
 namespace {
 
-// one (model, degree) group of a batch: its segments are d_seg[seg_off .. seg_off + n_segs)
+// one launch of a group: its segments are d_seg[seg_off .. seg_off + n_segs), items
+// numbered from 0, shared memory sized by trace size ntmax
+struct Run {
+  int seg_off, n_segs, n_items, ntmax;
+};
+// one (model, degree) group of a batch, launched as runs of trace sizes at which the
+// batched kernel keeps the same resident CTAs per SM (as launch_groups does for the
+// degree buckets of one system; each system's bucket list is sorted by trace size)
 struct Group {
-  int model, p, n_items, n_segs, seg_off, ntmax, nfield;
+  int model, p, n_items, nfield;
   bool bounded;
+  std::vector<Run> runs;
 };
 
 hdg_status fail(hdg_ctx* ctx, hdg_status st, const std::string& msg) {
@@ -71,7 +80,7 @@ Phys group_phys(const hdg_batch* B, const Group& g) {
   return ph;
 }
 
-BatchRef group_ref(const hdg_batch* B, const Group& g) { return BatchRef{B->d_desc, B->d_seg + g.seg_off, g.n_segs}; }
+BatchRef run_ref(const hdg_batch* B, const Run& r) { return BatchRef{B->d_desc, B->d_seg + r.seg_off, r.n_segs}; }
 
 hdg_status ensure_streams(hdg_batch* B) {
   if (B->have_streams) return HDG_OK;
@@ -92,6 +101,7 @@ hdg_status condense_groups(hdg_batch* B, cudaStream_t st) {
       S->need_zero = false;
     }
   std::string err;
+  int launches = 0;
   const bool fork = B->groups.size() > 1;
   if (fork) {
     // the (model, degree) groups run concurrently, one CTA per item, like the
@@ -105,24 +115,29 @@ hdg_status condense_groups(hdg_batch* B, cudaStream_t st) {
     cudaStream_t gs = fork ? B->gstream[i] : st;
     if (fork) HDG_BCK(ctx, cudaStreamWaitEvent(gs, B->fork, 0));
     const Phys ph = group_phys(B, g);
-    if (!launch_condense_batch(g.p, ph, ctx->d_tab, ctx->d_tab_ff, ctx->tab.off, group_ref(B, g), g.n_items, g.ntmax,
-                               g.bounded, gs, &err))
-      return fail(ctx, HDG_ECUDA, "hdg_batch_condense: " + err);
+    for (const Run& r : g.runs) {
+      if (!launch_condense_batch(g.p, ph, ctx->d_tab, ctx->d_tab_ff, ctx->tab.off, run_ref(B, r), r.n_items, r.ntmax,
+                                 g.bounded, gs, &err))
+        return fail(ctx, HDG_ECUDA, "hdg_batch_condense: " + err);
+      ++launches;
+    }
     if (fork) {
       HDG_BCK(ctx, cudaEventRecord(B->gevent[i], gs));
       HDG_BCK(ctx, cudaStreamWaitEvent(st, B->gevent[i], 0));
     }
   }
-  B->launches = (int)B->groups.size();
+  B->launches = launches;
   return HDG_OK;
 }
 
 hdg_status recover_groups(hdg_batch* B, cudaStream_t st) {
   std::string err;
   for (const Group& g : B->groups)
-    if (!launch_recover_batch(g.p, g.nfield, group_ref(B, g), g.n_items, st, &err))
-      return fail(B->ctx, HDG_ECUDA, "hdg_batch_recover: " + err);
-  B->launches += (int)B->groups.size();
+    for (const Run& r : g.runs) {
+      if (!launch_recover_batch(g.p, g.nfield, run_ref(B, r), r.n_items, st, &err))
+        return fail(B->ctx, HDG_ECUDA, "hdg_batch_recover: " + err);
+      ++B->launches;
+    }
   return HDG_OK;
 }
 
@@ -202,18 +217,47 @@ hdg_status batch_plan(hdg_ctx* ctx, int32_t n_sys, hdg_sys* const* systems, hdg_
   segs->clear();
   for (int md = 0; md < 2; ++md)
     for (int p = 1; p <= kMaxP; ++p) {
-      Group g{md, p, 0, 0, (int)segs->size(), 0, md == HDG_NS_MIXED ? 12 : 4, false};
+      Group g{md, p, 0, md == HDG_NS_MIXED ? 12 : 4, false, {}};
+      int cnt[kNtSlots] = {};
       for (int i = 0; i < n_sys; ++i) {
         const hdg_sys* S = systems[i];
         const hdg_mesh* M = S->mesh;
         if (S->ph.model != md || M->bucket_n[p] == 0) continue;
-        segs->push_back(BatchSeg{i, g.n_items, M->d_bucket[p]});
+        for (int t = 0; t < kNtSlots; ++t) cnt[t] += M->bucket_nt.cnt[p][t];
         g.n_items += M->bucket_n[p];
-        g.ntmax = std::max(g.ntmax, M->bucket_ntmax[p]);
         g.bounded |= M->has_bc;
-        ++g.n_segs;
       }
-      if (g.n_segs) B->groups.push_back(g);
+      if (!g.n_items) continue;
+      // runs of trace sizes with equal resident CTAs per SM of the batched kernel
+      Phys ph = systems[0]->ph;
+      ph.model = md;
+      int occ[kNtSlots];
+      for (int t = 0; t < kNtSlots; ++t) occ[t] = cnt[t] ? batch_occupancy(ph, p, 4 * t, g.bounded) : 0;
+      for (int t = 0; t < kNtSlots;) {
+        if (!cnt[t]) { ++t; continue; }
+        int e = t, top = 4 * t;
+        for (; e < kNtSlots; ++e) {
+          if (!cnt[e]) continue;
+          if (occ[e] != occ[t]) break;
+          top = 4 * e;
+        }
+        Run r{(int)segs->size(), 0, 0, top};
+        for (int i = 0; i < n_sys; ++i) {
+          const hdg_sys* S = systems[i];
+          const hdg_mesh* M = S->mesh;
+          if (S->ph.model != md || M->bucket_n[p] == 0) continue;
+          int off = 0, n = 0;
+          for (int u = 0; u < t; ++u) off += M->bucket_nt.cnt[p][u];
+          for (int u = t; u < e; ++u) n += M->bucket_nt.cnt[p][u];
+          if (n == 0) continue;
+          segs->push_back(BatchSeg{i, r.n_items, M->d_bucket[p] + off});
+          r.n_items += n;
+          ++r.n_segs;
+        }
+        g.runs.push_back(r);
+        t = e;
+      }
+      B->groups.push_back(g);
     }
   *out = B;
   return HDG_OK;
@@ -254,10 +298,11 @@ hdg_status hdg_batch_create(hdg_ctx* ctx, int32_t n_sys, hdg_sys* const* systems
 
 int64_t hdg_batch_workspace_bytes(int32_t n_sys, hdg_sys* const* systems) {
   if (!systems || n_sys < 1) return -1;
-  size_t n_seg = 0;
+  size_t n_seg = 0;  // at most one segment per (system, degree, trace size)
   for (int i = 0; i < n_sys; ++i) {
     if (!systems[i]) return -1;
-    for (int p = 1; p <= kMaxP; ++p) n_seg += systems[i]->mesh->bucket_n[p] > 0;
+    for (int p = 1; p <= kMaxP; ++p)
+      for (int t = 0; t < kNtSlots; ++t) n_seg += systems[i]->mesh->bucket_nt.cnt[p][t] > 0;
   }
   return (int64_t)work_list_bytes((size_t)n_sys, n_seg);
 }
@@ -348,7 +393,12 @@ hdg_status hdg_batch_autotune(hdg_batch* B, int32_t* grid_out, void* stream) {
   for (size_t gi = 0; gi < B->groups.size() && rs == HDG_OK; ++gi) {
     const Group& g = B->groups[gi];
     Phys ph = group_phys(B, g);
-    const int occ = batch_occupancy(ph, g.p, g.ntmax, g.bounded);
+    int occ = 0;  // persistent candidates up to the largest occupancy of the group's runs
+    for (const Run& r : g.runs) {
+      const int o = batch_occupancy(ph, g.p, r.ntmax, g.bounded);
+      if (o < 1) { occ = 0; break; }
+      occ = std::max(occ, o);
+    }
     if (occ < 1) { rs = fail(ctx, HDG_ECUDA, "hdg_batch_autotune: kernel does not fit on an SM"); break; }
     float best_ms = 0.0f;
     int best = -1;
@@ -361,11 +411,11 @@ hdg_status hdg_batch_autotune(hdg_batch* B, int32_t* grid_out, void* stream) {
           if (cudaMemsetAsync(S->ds.face_cnt, 0, 4 * (size_t)S->mesh->n_face, st) != cudaSuccess)
             rs = fail(ctx, HDG_ECUDA, "hdg_batch_autotune: memset failed");
         if (rs != HDG_OK || cudaEventRecord(e0, st) != cudaSuccess) break;
-        if (!launch_condense_batch(g.p, ph, ctx->d_tab, ctx->d_tab_ff, ctx->tab.off, group_ref(B, g), g.n_items,
-                                   g.ntmax, g.bounded, st, &err)) {
-          rs = fail(ctx, HDG_ECUDA, "hdg_batch_autotune: " + err);
-          break;
-        }
+        for (const Run& r : g.runs)
+          if (rs == HDG_OK && !launch_condense_batch(g.p, ph, ctx->d_tab, ctx->d_tab_ff, ctx->tab.off, run_ref(B, r),
+                                                     r.n_items, r.ntmax, g.bounded, st, &err))
+            rs = fail(ctx, HDG_ECUDA, "hdg_batch_autotune: " + err);
+        if (rs != HDG_OK) break;
         float ms = 0.0f;
         if (cudaEventRecord(e1, st) != cudaSuccess || cudaEventSynchronize(e1) != cudaSuccess ||
             cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess) {

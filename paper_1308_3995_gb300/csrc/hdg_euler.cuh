@@ -693,8 +693,8 @@ inline bool launch_euler_bucket(const DevMesh& m, const DevSys& s, const Phys& p
   const int ldr = ldr_for(ntmax), nkmax = nkmax_for(P, ntmax, BATCH ? bounded : m.elem_bc != nullptr);
   const EulerLayout<P> lay(ldr, nkmax, LS != 0);
   const size_t bytes = sizeof(T) * (size_t)lay.total;
-  cudaError_t ce = cudaFuncSetAttribute(k_condense_euler<P, T, LS, BATCH>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                        (int)bytes);
+  const size_t cap = sizeof(T) * (size_t)EulerLayout<P>(ldr_for(kMaxNt), kMaxP + 1, LS != 0).total;
+  cudaError_t ce = set_smem_cap(k_condense_euler<P, T, LS, BATCH>, cap, bytes);
   if (ce != cudaSuccess) { *err = cudaGetErrorString(ce); return false; }
   int dev = 0, sms = 0, per_sm = 0;
   cudaGetDevice(&dev);

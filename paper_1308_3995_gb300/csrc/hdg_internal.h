@@ -123,6 +123,19 @@ inline void phys_default_grid(Phys& ph) {
   for (int p = 0; p <= kMaxP; ++p) ph.grid[p] = -1;
 }
 
+// Dynamic shared-memory cap of a kernel instance (cudaFuncAttributeMaxDynamicSharedMemorySize).
+// The attribute belongs to the instance, not to a launch, so host threads that launch or query
+// the instance at once must not lower it under one another: every launch and occupancy query
+// sets the same value, the instance's largest layout (trace size kMaxNt), and passes its own
+// size, which is below it.  Only if the device refuses that value is the caller's size set.
+template <class K>
+inline cudaError_t set_smem_cap(K* kernel, size_t max_bytes, size_t bytes) {
+  if (cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)max_bytes) == cudaSuccess)
+    return cudaSuccess;
+  (void)cudaGetLastError();
+  return cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+}
+
 // number of CTAs of a condensation launch of n elements of degree p
 inline long condense_grid(const Phys& ph, int p, int sms, int per_sm, int n) {
   const int g = ph.grid[p];

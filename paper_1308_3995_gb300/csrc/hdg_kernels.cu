@@ -102,9 +102,8 @@ template <int P, class T>
 static int euler_occupancy(int ntmax) {
   const EulerLayout<P> lay(ldr_for(ntmax), nkmax_for(P, ntmax));
   const size_t bytes = sizeof(T) * (size_t)lay.total;
-  if (cudaFuncSetAttribute(k_condense_euler<P, T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes) !=
-      cudaSuccess)
-    return 0;
+  const size_t cap = sizeof(T) * (size_t)EulerLayout<P>(ldr_for(kMaxNt), kMaxP + 1).total;
+  if (set_smem_cap(k_condense_euler<P, T>, cap, bytes) != cudaSuccess) return 0;
   int per_sm = 0;
   cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_condense_euler<P, T>, kCondThreads, bytes);
   return per_sm;
@@ -195,9 +194,8 @@ template <int P, class T>
 static int euler_batch_occupancy(int ntmax, bool bounded) {
   const EulerLayout<P> lay(ldr_for(ntmax), nkmax_for(P, ntmax, bounded));
   const size_t bytes = sizeof(T) * (size_t)lay.total;
-  if (cudaFuncSetAttribute(k_condense_euler<P, T, 0, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes) !=
-      cudaSuccess)
-    return 0;
+  const size_t cap = sizeof(T) * (size_t)EulerLayout<P>(ldr_for(kMaxNt), kMaxP + 1).total;
+  if (set_smem_cap(k_condense_euler<P, T, 0, true>, cap, bytes) != cudaSuccess) return 0;
   int per_sm = 0;
   cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_condense_euler<P, T, 0, true>, kCondThreads, bytes);
   return per_sm;

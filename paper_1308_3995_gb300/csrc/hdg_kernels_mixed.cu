@@ -37,9 +37,8 @@ template <int P, int LS>
 static int mixed_occ(int ntmax, bool bounded) {
   const EulerLayout<P> lay(ldr_for(ntmax), nkmax_for(P, ntmax, bounded), true);
   const size_t bytes = sizeof(double) * (size_t)lay.total;
-  if (cudaFuncSetAttribute(k_condense_euler<P, double, LS>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes) !=
-      cudaSuccess)
-    return 0;
+  const size_t cap = sizeof(double) * (size_t)EulerLayout<P>(ldr_for(kMaxNt), kMaxP + 1, true).total;
+  if (set_smem_cap(k_condense_euler<P, double, LS>, cap, bytes) != cudaSuccess) return 0;
   int per_sm = 0;
   cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_condense_euler<P, double, LS>, kCondThreads, bytes);
   return per_sm;

